@@ -1,0 +1,20 @@
+"""GB300-native row-wise assembly of isogeometric mass and stiffness matrices
+with weighted Gaussian quadrature rules (one rule per row, the row's B-spline
+as the measure), evaluated by sum factorisation into each row's band.
+
+The compute path is the C-ABI library ``libwq.so`` (``include/wq.h``); the
+Python names mirror its entry points and only marshal arguments.  Importing
+this package does not load the library; the first call does, and fails
+loudly if it has not been built.
+"""
+__all__ = ["inputs"]
+
+
+def __getattr__(name):
+    if name in ("inputs",):
+        import importlib
+
+        return importlib.import_module(f"{__name__}.{name}")
+    from . import binding
+
+    return getattr(binding, name)
