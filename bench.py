@@ -1,0 +1,349 @@
+"""Benchmark: 3D cubic weighted-Gaussian mass+stiffness assembly, nnz/s.
+
+One step = one fused mass+stiffness assembly (geometry-factor fold and the
+row kernels, all rows) of the named synthetic workload through the C-ABI.
+Default workload: 64^3 elements, C2 cubic (p = 3), separable map
+xhat + 0.05 sin(pi xhat) per coordinate, c = exp(0.3 (x+y+z)) with
+lognormal(0.1) noise as a cubic spline on the same mesh, FP64 throughout.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload 3d_p3_64] [--prec fp64|mixed] [--no-cpu-baseline]
+
+Prints one JSON line.  value = assembled non-zeros (M and K) per second over
+all ranks, device time (CUDA events around each step on the launching
+stream, L2 flushed before each step by writing a 256 MiB buffer); e2e = the
+same through host buffers (pinned H2D of geometry and coefficients, D2H of
+both bands, inside the timed region).  Under torchrun every rank assembles
+its own copy of the workload (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "3D cubic WQ mass+stiffness assembled nnz/s"
+# peaks
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz = 1.259
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 80.5
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def band_nnz_rows(nel, p, rows_idx):
+    """Number of in-range band entries of the given rows (one matrix)."""
+    import numpy as np
+
+    n = [v + p for v in nel]
+    r1 = rows_idx % n[0]
+    r2 = (rows_idx // n[0]) % n[1]
+    r3 = rows_idx // (n[0] * n[1])
+    cnt = np.ones_like(rows_idx)
+    for r, m in ((r1, n[0]), (r2, n[1]), (r3, n[2])):
+        cnt = cnt * (np.minimum(m - 1, r + p) - np.maximum(0, r - p) + 1)
+    return int(cnt.sum())
+
+
+def cpu_sample_rows(nel, p, stride):
+    """Every `stride`-th x3-slab of rows (interior and boundary rows alike)."""
+    n = [v + p for v in nel]
+    slab = n[0] * n[1]
+    return [(s * slab, (s + 1) * slab) for s in range(0, n[2], stride)]
+
+
+def run_cpu_baseline(w, g, c, stride, max_slabs=None):
+    """Times the FP64 oracle on a sample of slabs with all host cores."""
+    import numpy as np
+
+    import oracle
+
+    nel, p = w["nel"], w["p"]
+    ranges = cpu_sample_rows(nel, p, stride)
+    if max_slabs:
+        ranges = ranges[:max_slabs]
+    nnz = 0
+    t0 = time.perf_counter()
+    outs = []
+    for rb, re in ranges:
+        M, K, _ = oracle.assemble(3, p, nel, g, c, rb, re)
+        outs.append((rb, re, M, K))
+        nnz += 2 * band_nnz_rows(nel, p, np.arange(rb, re))
+    dt = time.perf_counter() - t0
+    rows = sum(re - rb for rb, re in ranges)
+    return {"value": nnz / dt, "unit": "nnz/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{len(ranges)} x3-slabs (every {stride}th, {rows} rows of {int(np.prod([v + p for v in nel]))}), "
+                      f"{dt:.1f} s wall"}, outs
+
+
+def reference_arm(args):
+    """The oracle as it stands, on the host cores, for the same workload."""
+    import numpy as np
+
+    from paper_1710_01048_gb300 import inputs
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w, g, c = inputs.workload(args.workload)
+    nel, p = w["nel"], w["p"]
+    n = [v + p for v in nel]
+    slab = n[0] * n[1]
+    # each step: one x3-slab of rows (a bounded sample of the workload)
+    import oracle
+
+    oracle.build()
+    for i in range(args.warmup):
+        oracle.assemble(3, p, nel, g, c, slab * (i % n[2]), slab * (i % n[2] + 1))
+    t = []
+    nnz = 0
+    for i in range(args.steps):
+        s = (n[2] // 2 + i) % n[2]
+        t0 = time.perf_counter()
+        oracle.assemble(3, p, nel, g, c, slab * s, slab * (s + 1))
+        t.append(time.perf_counter() - t0)
+        nnz += 2 * band_nnz_rows(nel, p, np.arange(slab * s, slab * (s + 1)))
+    total = sum(t)
+    value = nnz / total
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "nel": list(nel), "degree": p, "precision": "fp64"},
+           "cpu_baseline": {"value": value, "unit": "nnz/s", "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": f"one x3-slab ({slab} rows) per step"},
+           "e2e": {"value": value, "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="3d_p3_64")
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-stride", type=int, default=8)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import numpy as np
+    import torch
+
+    from paper_1710_01048_gb300 import binding as wq
+    from paper_1710_01048_gb300 import inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w, g, c = inputs.workload(args.workload)
+    dim, p, nel = w["dim"], w["p"], w["nel"]
+    R = wq.Rules(dim, p, nel)
+    rows, band = R.rows, R.band
+    nnz_step = 2 * R.nnz  # M and K
+    gd = [torch.from_numpy(x).cuda() for x in g]
+    cd = torch.from_numpy(c).cuda()
+    dt = torch.float64 if args.prec == "fp64" else torch.float32
+    M = torch.empty((rows, band), dtype=dt, device="cuda")
+    K = torch.empty((rows, band), dtype=dt, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        wq.assemble(R, gd, cd, args.prec, out=(M, K), stream=stream, check=False)
+
+    for _ in range(args.warmup):
+        step()
+    st = wq.wq_status_check(R.handle, wq._stream_handle(stream))
+    if st != wq.WQ_OK:
+        raise wq.WqError(st, "warm-up")
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for e0, e1 in evs:
+        flush.fill_(1)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    ms_step = float(np.mean(ms))
+    st = wq.wq_status_check(R.handle, wq._stream_handle(stream))
+    if st != wq.WQ_OK:
+        raise wq.WqError(st, "timed steps")
+    gpu_launches = 3 * args.steps  # fold + interior-line rows + boundary-line rows per step
+
+    # end to end through host buffers: pinned inputs H2D, both bands D2H
+    gh = [torch.from_numpy(x).pin_memory() for x in g]
+    ch = torch.from_numpy(c).pin_memory()
+    Mh = torch.empty((rows, band), dtype=dt).pin_memory()
+    Kh = torch.empty((rows, band), dtype=dt).pin_memory()
+    h2d = sum(x.numel() * 8 for x in gh) + ch.numel() * 8
+    d2h = 2 * rows * band * M.element_size()
+    e2e_steps = max(3, min(args.steps, 10))
+
+    def e2e_step():
+        for dst, src in zip(gd, gh):
+            dst.copy_(src, non_blocking=True)
+        cd.copy_(ch, non_blocking=True)
+        step()
+        Mh.copy_(M, non_blocking=True)
+        Kh.copy_(K, non_blocking=True)
+
+    e2e_step()
+    barrier()
+    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0e.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    t1e.record(stream)
+    barrier()
+    e2e_ms = t0e.elapsed_time(t1e) / e2e_steps
+
+    # max over ranks
+    if dist is not None:
+        tt = torch.tensor([ms_step, e2e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_step, e2e_ms = tt.tolist()
+
+    value = world * nnz_step / (ms_step * 1e-3)
+    e2e_value = world * nnz_step / (e2e_ms * 1e-3)
+
+    # roofline of the assembly call (fold + the two row launches; the fold is
+    # a few microseconds): algorithmic contraction flops / device time
+    flops, coef_flops = R.flops()
+    peaks = measured_peaks()
+    if args.prec == "fp64":
+        achieved = flops / (ms_step * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (not in MEASURED_PEAKS.json)",
+                "achieved_incl_coef_eval": (flops + coef_flops) / (ms_step * 1e-3) / 1e12}
+    else:
+        bytes_step = 2 * rows * band * 4
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        achieved = bytes_step / (ms_step * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
+                else "fallback 6.8 TB/s",
+                "fp32_tflops": (flops + coef_flops) / (ms_step * 1e-3) / 1e12, "fp32_peak_tflops": FP32_PEAK_TFLOPS}
+
+    out = {"metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f32", "data": "synthetic",
+           "config": {"workload": args.workload, "nel": list(nel), "degree": p, "rows": rows, "band": band,
+                      "nnz_per_matrix": R.nnz, "precision": args.prec,
+                      "l2": "256 MiB buffer written before each timed step; each step also writes "
+                            f"{2 * rows * band * M.element_size() / 1e9:.2f} GB of band output"},
+           "roofline": roof,
+           "e2e": {"value": e2e_value, "unit": "nnz/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+           "clocks": clocks, "gpu_launches": gpu_launches, "ms_per_step_min": float(np.min(ms))}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu, outs = run_cpu_baseline(w, g, c, args.cpu_stride, max_slabs=None)
+        out["cpu_baseline"] = cpu
+        # accuracy of this run's bands on the sampled rows against the oracle
+        emax = 0.0
+        for rb, re, Mo, Ko in outs:
+            for A, O in ((M[rb:re], Mo), (K[rb:re], Ko)):
+                d = A.double().cpu().numpy() - O
+                emax = max(emax, float(np.max(np.abs(d)) / np.max(np.abs(O))))
+        out["max_rel_err_vs_oracle"] = emax
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    R.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

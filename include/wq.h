@@ -1,0 +1,192 @@
+/*
+ * wq.h -- C ABI of libwq: row-wise assembly of isogeometric mass and
+ * stiffness matrices with weighted Gaussian quadrature on GB300 (sm_103a).
+ *
+ * Method (Barton, Puzyrev, Deng, Calo, "Efficient mass and stiffness matrix
+ * assembly via weighted Gaussian quadrature rules for B-splines"):
+ *   - uniform open knot vectors of maximal continuity per direction
+ *     (Sec. 2.2, Eq. 3), degree p in {2, 3}, dimension d in {2, 3};
+ *   - row i of the mass matrix M (Eq. Mass) and of the stiffness matrix K
+ *     (Eq. Stiffness) is integrated by its own quadrature rule, Gaussian with
+ *     respect to B_i (mass, Sec. 3.1, Eq. GaussQuadSys) or B_i' (stiffness,
+ *     Sec. 3.2, Eq. GaussQuadSysStiff): p+1 nodes per direction, one per
+ *     element of supp B_i; rows whose weight function touches the boundary
+ *     use Gauss-Legendre on each element of the support (Remark closing
+ *     Sec. 3);
+ *   - the multivariate rule is the tensor product of the 1D rules (Eq.
+ *     Decompo) and is applied by sum factorisation, one direction at a time,
+ *     into the row's (2p+1)^d band (caption of Fig. 1).
+ *
+ * Inputs follow the problem statement of Sec. 2: degree and element counts
+ * (uniform knots), a geometry map (Eq. Gmap1) restricted to separable maps
+ * x_a = sum_i g_{a,i} B_i(xhat_a), and a coefficient field c multiplying the
+ * integrands (c = 1 in Eq. Mass / Eq. Stiffness), given as a degree-3 spline
+ * on the same mesh.  Only the diagonal metric terms have a weighted rule in
+ * the paper (Sec. 3.2), which is why maps must be separable.
+ *
+ * Band layout (output): rows r = r1 + n1*(r2 + n2*r3) with n_a = nel_a + p,
+ * each row holding (2p+1)^d entries; entry index
+ *   (d3+p)*(2p+1)^2 + (d2+p)*(2p+1) + (d1+p)   for column s_a = r_a + d_a,
+ * set to zero where a column index falls outside [0, n_a).
+ *
+ * Conventions for every entry point:
+ *   - return value: a wq_status; no C++ exception, exit() or device trap
+ *     crosses this boundary;
+ *   - "device" pointers are CUDA device memory on the current device, owned
+ *     by the caller; "host" pointers are ordinary host memory;
+ *   - calls that take a stream enqueue asynchronous work on it (a CUDA
+ *     stream handle, NULL = legacy default stream) and return once it is
+ *     enqueued; problems the GPU detects (a Jacobian entry <= 0, a
+ *     non-finite input) are reported by wq_status_check;
+ *   - a wq_rules object owns device tables and a small per-call scratch
+ *     area; calls that use the same wq_rules on different streams must not
+ *     overlap in time.
+ */
+#ifndef WQ_H
+#define WQ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum wq_status {
+  WQ_OK = 0,
+  WQ_ERR_ARG = 1,            /* invalid argument (null pointer, bad size, range) */
+  WQ_ERR_UNSUPPORTED = 2,    /* degree/dimension outside {2,3}, too many elements */
+  WQ_ERR_NO_CONVERGENCE = 3, /* a 1D rule failed its Newton solve or exactness check */
+  WQ_ERR_GEOMETRY = 4,       /* some J_aa <= 0 at a quadrature point (folded map); the
+                                result is still written with |J_aa| as in Eq. Mass */
+  WQ_ERR_NONFINITE = 5,      /* NaN or Inf in the geometry or coefficients */
+  WQ_ERR_CUDA = 6,           /* a CUDA runtime call failed */
+  WQ_ERR_OOM = 7,            /* device allocation failed */
+  WQ_ERR_TIMEOUT = 8         /* reserved: a bounded device wait expired */
+} wq_status;
+
+typedef enum wq_precision {
+  WQ_FP64 = 0,  /* FP64 throughout; band written as double */
+  WQ_MIXED = 1  /* Jacobian and rule tables in FP64, contractions in FP32 with
+                   compensated final sums; band written as float */
+} wq_precision;
+
+enum { WQ_KIND_MASS = 0, WQ_KIND_STIFFNESS = 1 };
+enum { WQ_RULES_HOST_ONLY = 0, WQ_RULES_DEVICE = 1 };
+
+typedef struct wq_mesh {
+  int dim;     /* 2 or 3 */
+  int degree;  /* 2 or 3 */
+  int nel[3];  /* elements per direction (entries beyond dim ignored), >= 1 */
+} wq_mesh;
+
+typedef struct wq_rules wq_rules; /* opaque */
+
+/* Human-readable name of a status code (static storage). */
+const char *wq_status_string(wq_status s);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int wq_version(void);
+
+/*
+ * The univariate weighted Gaussian rule on the cardinal support [0, p+1]
+ * (Sec. 3.1 for kind = WQ_KIND_MASS, Sec. 3.2 for kind = WQ_KIND_STIFFNESS):
+ * writes p+1 nodes tau[k] (one per unit element, ascending) and weights
+ * omega[k] (host arrays of length degree+1).  The rule satisfies
+ * sum_k omega_k N(tau_k) N(tau_k - d) = int N(y) N(y - d) dy for d = -p..p
+ * (N the cardinal B-spline, or its derivative for the stiffness kind).  The
+ * free parameters are the paper's: tau_2 = 3/2 (p = 2), omega_1 = 1 and the
+ * smaller tau_1 root (p = 3 stiffness).  Host only; returns
+ * WQ_ERR_NO_CONVERGENCE if the solve or its exactness check fails.
+ */
+wq_status wq_rule_1d(int degree, int kind, double *tau, double *omega);
+
+/*
+ * Newton solve of the same rule from a caller-chosen start (host).  start
+ * holds the unknowns of the symmetric rule: (tau_1, omega_1, omega_2) for
+ * mass p=2, (tau_1, tau_2, omega_1, omega_2) for mass p=3, (tau_1, omega_1)
+ * for stiffness p=2, (tau_1, tau_2, omega_2) for stiffness p=3.  Returns
+ * WQ_ERR_NO_CONVERGENCE unless the iteration reaches a rule with one node in
+ * each element that passes all 2p+1 exactness conditions (Sec. 3.1.2 shows
+ * a start that does not).
+ */
+wq_status wq_rule_1d_from(int degree, int kind, const double *start, double *tau, double *omega);
+
+/*
+ * Builds the per-direction row tables of a mesh: for every row of every
+ * direction and both kinds, the rule points (interior rows: the weighted
+ * Gaussian rule mapped to supp B_r; boundary rows: (p+1)-point
+ * Gauss-Legendre on each element of supp B_r), the combined weights
+ * W = h*omega*B_r^(nu)(x), and the values and derivatives of the p+1
+ * B-splines acting at each point.  flags = WQ_RULES_DEVICE also allocates
+ * and fills the device copy (current device) used by the assembly calls;
+ * WQ_RULES_HOST_ONLY builds host tables only (no CUDA call is made).
+ * *out receives a new object to be released with wq_rules_free.
+ */
+wq_status wq_rules_build(const wq_mesh *mesh, int flags, wq_rules **out);
+
+/* Releases a wq_rules object and its device memory (NULL is ignored). */
+void wq_rules_free(wq_rules *rules);
+
+/*
+ * Host view of one row's 1D rule: direction dir (0-based, < dim), kind,
+ * row index in [0, nel_dir + p).  *npts receives the point count; x, w
+ * (each >= degree*(degree+1) doubles) receive the points and combined
+ * weights W; elem (>= degree*(degree+1) ints) the element of each point.
+ * Any output pointer may be NULL.
+ */
+wq_status wq_rules_row(const wq_rules *rules, int dir, int kind, int row, int *npts, double *x, double *w,
+                       int *elem);
+
+/* Sizes of a mesh: rows = prod(nel_a + p); band = (2p+1)^dim entries per row;
+ * nnz = band entries with in-range columns (per matrix); coef = prod(nel_a + 3). */
+int64_t wq_rows(const wq_rules *rules);
+int64_t wq_band_width(const wq_rules *rules);
+int64_t wq_band_nnz(const wq_rules *rules);
+int64_t wq_coef_count(const wq_rules *rules);
+
+/*
+ * Algorithmic floating-point operation count of assembling rows
+ * [row_begin, row_end) (mass if want_m, stiffness if want_k): the
+ * multiply-adds of the sum-factorised contractions on the non-zero band
+ * structure (2 flops each), excluding coefficient evaluation, which is
+ * returned separately in *coef_flops (may be NULL).  Host only.
+ */
+double wq_flop_count(const wq_rules *rules, int want_m, int want_k, int64_t row_begin, int64_t row_end,
+                     double *coef_flops);
+
+/*
+ * Assembly of rows [row_begin, row_end) (0 <= row_begin <= row_end <= rows)
+ * into band arrays (Eq. Mass, Eq. Stiffness, weighted Gaussian rules):
+ *   geom[a]  device, n_a = nel_a + p doubles: control values of x_a (host
+ *            array of dim device pointers);
+ *   coef     device, prod(nel_a + 3) doubles, x fastest: degree-3 spline of
+ *            the coefficient c; NULL means c = 1;
+ *   M, K     device, (row_end - row_begin) * band entries, double for
+ *            WQ_FP64, float for WQ_MIXED; row row_begin is stored first;
+ *            may be NULL when row_begin == row_end (nothing is written).
+ * wq_assemble_mass_stiffness writes both (the fused path); the single-matrix
+ * forms write one.  The rules object must have been built with
+ * WQ_RULES_DEVICE on the current device.  Output buffers must not overlap
+ * the inputs.
+ */
+wq_status wq_assemble_mass(const wq_rules *rules, const double *const *geom, const double *coef,
+                           wq_precision prec, void *M, int64_t row_begin, int64_t row_end, void *stream);
+wq_status wq_assemble_stiffness(const wq_rules *rules, const double *const *geom, const double *coef,
+                                wq_precision prec, void *K, int64_t row_begin, int64_t row_end, void *stream);
+wq_status wq_assemble_mass_stiffness(const wq_rules *rules, const double *const *geom, const double *coef,
+                                     wq_precision prec, void *M, void *K, int64_t row_begin, int64_t row_end,
+                                     void *stream);
+
+/*
+ * Synchronises `stream`, then returns and clears the device-detected status
+ * of the assembly calls made with `rules` since the previous check:
+ * WQ_ERR_GEOMETRY if some J_aa <= 0, WQ_ERR_NONFINITE if some input was NaN
+ * or Inf, WQ_ERR_CUDA if a kernel failed, else WQ_OK.
+ */
+wq_status wq_status_check(const wq_rules *rules, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WQ_H */

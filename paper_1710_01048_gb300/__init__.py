@@ -7,14 +7,14 @@ Python names mirror its entry points and only marshal arguments.  Importing
 this package does not load the library; the first call does, and fails
 loudly if it has not been built.
 """
-__all__ = ["inputs"]
+import importlib
+
+_SUBMODULES = ("inputs", "binding", "build")
 
 
 def __getattr__(name):
-    if name in ("inputs",):
-        import importlib
-
+    if name in _SUBMODULES:
         return importlib.import_module(f"{__name__}.{name}")
-    from . import binding
-
-    return getattr(binding, name)
+    if name.startswith("__"):
+        raise AttributeError(name)
+    return getattr(importlib.import_module(f"{__name__}.binding"), name)

@@ -1,0 +1,287 @@
+"""ctypes binding of libwq (``include/wq.h``).
+
+The ``wq_*`` functions have the C names and signatures; they marshal
+arguments and return the C status.  ``Rules`` and ``assemble`` are thin
+conveniences over them that allocate outputs with torch (device memory and
+the current stream only).  Every numerical step runs in libwq; there is no
+fallback: if the library is not built, the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libwq.so")
+
+WQ_OK, WQ_ERR_ARG, WQ_ERR_UNSUPPORTED, WQ_ERR_NO_CONVERGENCE = 0, 1, 2, 3
+WQ_ERR_GEOMETRY, WQ_ERR_NONFINITE, WQ_ERR_CUDA, WQ_ERR_OOM, WQ_ERR_TIMEOUT = 4, 5, 6, 7, 8
+WQ_FP64, WQ_MIXED = 0, 1
+WQ_KIND_MASS, WQ_KIND_STIFFNESS = 0, 1
+WQ_RULES_HOST_ONLY, WQ_RULES_DEVICE = 0, 1
+
+# every function declared in include/wq.h
+EXPORTS = ["wq_status_string", "wq_version", "wq_rule_1d", "wq_rule_1d_from", "wq_rules_build", "wq_rules_free",
+           "wq_rules_row", "wq_rows", "wq_band_width", "wq_band_nnz", "wq_coef_count", "wq_flop_count",
+           "wq_assemble_mass", "wq_assemble_stiffness", "wq_assemble_mass_stiffness", "wq_status_check"]
+
+
+class WqError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        msg = _lib().wq_status_string(status).decode() if _loaded is not None else str(status)
+        super().__init__(f"{what}: {msg} (status {status})" if what else f"{msg} (status {status})")
+
+
+class wq_mesh(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("degree", ctypes.c_int), ("nel", ctypes.c_int * 3)]
+
+
+_loaded = None
+
+
+def _lib():
+    global _loaded
+    if _loaded is not None:
+        return _loaded
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libwq.so is not built ({LIB_PATH}); run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    try:  # load torch's CUDA runtime first when torch is present, so both share it
+        import torch  # noqa: F401
+    except ImportError:
+        pass
+    lib = ctypes.CDLL(LIB_PATH)
+    c_int, c_double, c_void_p, i64 = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64
+    PD, PI = ctypes.POINTER(c_double), ctypes.POINTER(c_int)
+    PP = ctypes.POINTER(c_void_p)
+    lib.wq_status_string.argtypes = [c_int]
+    lib.wq_status_string.restype = ctypes.c_char_p
+    lib.wq_version.restype = c_int
+    lib.wq_rule_1d.argtypes = [c_int, c_int, PD, PD]
+    lib.wq_rule_1d_from.argtypes = [c_int, c_int, PD, PD, PD]
+    lib.wq_rules_build.argtypes = [ctypes.POINTER(wq_mesh), c_int, ctypes.POINTER(c_void_p)]
+    lib.wq_rules_free.argtypes = [c_void_p]
+    lib.wq_rules_free.restype = None
+    lib.wq_rules_row.argtypes = [c_void_p, c_int, c_int, c_int, PI, PD, PD, PI]
+    for f in ("wq_rows", "wq_band_width", "wq_band_nnz", "wq_coef_count"):
+        getattr(lib, f).argtypes = [c_void_p]
+        getattr(lib, f).restype = i64
+    lib.wq_flop_count.argtypes = [c_void_p, c_int, c_int, i64, i64, PD]
+    lib.wq_flop_count.restype = c_double
+    lib.wq_assemble_mass.argtypes = [c_void_p, PP, c_void_p, c_int, c_void_p, i64, i64, c_void_p]
+    lib.wq_assemble_stiffness.argtypes = [c_void_p, PP, c_void_p, c_int, c_void_p, i64, i64, c_void_p]
+    lib.wq_assemble_mass_stiffness.argtypes = [c_void_p, PP, c_void_p, c_int, c_void_p, c_void_p, i64, i64,
+                                               c_void_p]
+    lib.wq_status_check.argtypes = [c_void_p, c_void_p]
+    for f in EXPORTS:
+        if f not in ("wq_status_string", "wq_version", "wq_rules_free", "wq_rows", "wq_band_width", "wq_band_nnz",
+                     "wq_coef_count", "wq_flop_count"):
+            getattr(lib, f).restype = c_int
+    _loaded = lib
+    return lib
+
+
+def library():
+    """The loaded ctypes library (loads it on first use)."""
+    return _lib()
+
+
+def _pd(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(st, what):
+    if st != WQ_OK:
+        raise WqError(st, what)
+
+
+# ------------------------------------------------------------------ C names
+def wq_status_string(status):
+    return _lib().wq_status_string(status).decode()
+
+
+def wq_version():
+    return _lib().wq_version()
+
+
+def wq_rule_1d(degree, kind):
+    """(tau, omega) of the cardinal rule (numpy arrays)."""
+    tau = np.zeros(degree + 1)
+    om = np.zeros(degree + 1)
+    _check(_lib().wq_rule_1d(degree, kind, _pd(tau), _pd(om)), "wq_rule_1d")
+    return tau, om
+
+
+def wq_rule_1d_from(degree, kind, start):
+    """(status, tau, omega) of a Newton solve from `start`."""
+    s = np.ascontiguousarray(start, dtype=np.float64)
+    tau = np.zeros(degree + 1)
+    om = np.zeros(degree + 1)
+    st = _lib().wq_rule_1d_from(degree, kind, _pd(s), _pd(tau), _pd(om))
+    return st, tau, om
+
+
+def wq_rules_build(dim, degree, nel, flags=WQ_RULES_DEVICE):
+    """Raw handle (int) of a new wq_rules; release with wq_rules_free."""
+    m = wq_mesh(dim, degree, (ctypes.c_int * 3)(*(list(nel) + [1] * (3 - len(nel)))))
+    h = ctypes.c_void_p()
+    _check(_lib().wq_rules_build(ctypes.byref(m), flags, ctypes.byref(h)), "wq_rules_build")
+    return h.value
+
+
+def wq_rules_free(handle):
+    _lib().wq_rules_free(handle)
+
+
+def wq_rules_row(handle, dir, kind, row):
+    """(x, W, elem) of one row's 1D rule."""
+    n = ctypes.c_int(0)
+    x = np.zeros(16)
+    w = np.zeros(16)
+    e = np.zeros(16, dtype=np.int32)
+    _check(_lib().wq_rules_row(handle, dir, kind, row, ctypes.byref(n), _pd(x), _pd(w),
+                               e.ctypes.data_as(ctypes.POINTER(ctypes.c_int))), "wq_rules_row")
+    k = n.value
+    return x[:k].copy(), w[:k].copy(), e[:k].copy()
+
+
+def wq_rows(handle):
+    return _lib().wq_rows(handle)
+
+
+def wq_band_width(handle):
+    return _lib().wq_band_width(handle)
+
+
+def wq_band_nnz(handle):
+    return _lib().wq_band_nnz(handle)
+
+
+def wq_coef_count(handle):
+    return _lib().wq_coef_count(handle)
+
+
+def wq_flop_count(handle, want_m, want_k, row_begin, row_end):
+    """(contraction flops, coefficient-evaluation flops)."""
+    cf = ctypes.c_double(0.0)
+    f = _lib().wq_flop_count(handle, int(want_m), int(want_k), int(row_begin), int(row_end), ctypes.byref(cf))
+    return f, cf.value
+
+
+def _geom_array(geom_ptrs):
+    arr = (ctypes.c_void_p * 3)(*(list(geom_ptrs) + [None] * (3 - len(geom_ptrs))))
+    return ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)), arr
+
+
+def wq_assemble_mass(handle, geom_ptrs, coef_ptr, prec, M_ptr, row_begin, row_end, stream):
+    g, keep = _geom_array(geom_ptrs)
+    return _lib().wq_assemble_mass(handle, g, coef_ptr, prec, M_ptr, row_begin, row_end, stream)
+
+
+def wq_assemble_stiffness(handle, geom_ptrs, coef_ptr, prec, K_ptr, row_begin, row_end, stream):
+    g, keep = _geom_array(geom_ptrs)
+    return _lib().wq_assemble_stiffness(handle, g, coef_ptr, prec, K_ptr, row_begin, row_end, stream)
+
+
+def wq_assemble_mass_stiffness(handle, geom_ptrs, coef_ptr, prec, M_ptr, K_ptr, row_begin, row_end, stream):
+    g, keep = _geom_array(geom_ptrs)
+    return _lib().wq_assemble_mass_stiffness(handle, g, coef_ptr, prec, M_ptr, K_ptr, row_begin, row_end, stream)
+
+
+def wq_status_check(handle, stream):
+    return _lib().wq_status_check(handle, stream)
+
+
+# ------------------------------------------------------------------ conveniences
+class Rules:
+    """Owns a wq_rules handle (host tables, and device tables when device=True)."""
+
+    def __init__(self, dim, degree, nel, device=True):
+        self.dim, self.degree, self.nel = int(dim), int(degree), tuple(int(v) for v in nel)
+        self.handle = wq_rules_build(self.dim, self.degree, self.nel,
+                                     WQ_RULES_DEVICE if device else WQ_RULES_HOST_ONLY)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            wq_rules_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def rows(self):
+        return wq_rows(self.handle)
+
+    @property
+    def band(self):
+        return wq_band_width(self.handle)
+
+    @property
+    def nnz(self):
+        return wq_band_nnz(self.handle)
+
+    @property
+    def ncoef(self):
+        return wq_coef_count(self.handle)
+
+    def row(self, dir, kind, r):
+        return wq_rules_row(self.handle, dir, kind, r)
+
+    def flops(self, mass=True, stiffness=True, row_begin=0, row_end=None):
+        return wq_flop_count(self.handle, mass, stiffness, row_begin, self.rows if row_end is None else row_end)
+
+
+def _stream_handle(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def assemble(rules, geom, coef=None, prec="fp64", mass=True, stiffness=True, row_begin=0, row_end=None, out=None,
+             stream=None, check=True):
+    """Assembles rows [row_begin, row_end) of M and/or K (band layout) on the
+    current CUDA device.  geom: list of dim float64 CUDA tensors (control
+    values); coef: float64 CUDA tensor of rules.ncoef values or None (c = 1).
+    Returns (M, K) torch tensors of shape (rows, band), float64 for 'fp64',
+    float32 for 'mixed'.  With check=True the stream is synchronised and a
+    device-detected problem raises WqError."""
+    import torch
+
+    if row_end is None:
+        row_end = rules.rows
+    p = WQ_FP64 if prec == "fp64" else WQ_MIXED
+    dt = torch.float64 if p == WQ_FP64 else torch.float32
+    nrows = row_end - row_begin
+    for g in geom:
+        assert g.is_cuda and g.dtype == torch.float64 and g.is_contiguous()
+    if coef is not None:
+        assert coef.is_cuda and coef.dtype == torch.float64 and coef.is_contiguous() and coef.numel() == rules.ncoef
+    dev = geom[0].device
+    if out is None:
+        M = torch.empty((nrows, rules.band), dtype=dt, device=dev) if mass else None
+        K = torch.empty((nrows, rules.band), dtype=dt, device=dev) if stiffness else None
+    else:
+        M, K = out
+    s = _stream_handle(stream)
+    gp = [g.data_ptr() for g in geom]
+    cp = ctypes.c_void_p(coef.data_ptr()) if coef is not None else None
+    if mass and stiffness:
+        st = wq_assemble_mass_stiffness(rules.handle, gp, cp, p, ctypes.c_void_p(M.data_ptr()),
+                                        ctypes.c_void_p(K.data_ptr()), row_begin, row_end, s)
+    elif mass:
+        st = wq_assemble_mass(rules.handle, gp, cp, p, ctypes.c_void_p(M.data_ptr()), row_begin, row_end, s)
+    else:
+        st = wq_assemble_stiffness(rules.handle, gp, cp, p, ctypes.c_void_p(K.data_ptr()), row_begin, row_end, s)
+    _check(st, "wq_assemble")
+    if check:
+        _check(wq_status_check(rules.handle, s), "wq_status_check")
+    return M, K

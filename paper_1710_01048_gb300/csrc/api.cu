@@ -1,0 +1,398 @@
+// C ABI of libwq: rule construction, device upload, the geometry-factor fold
+// kernel and the assembly launches.  Every entry point returns a wq_status
+// and never lets a C++ exception escape.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "launch.cuh"
+#include "wq_internal.h"
+
+using wq::HostDirKind;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Folds the geometry factor of the separable map into the 1D tables of every
+// direction and kind (Eq. Mass, Eq. Stiffness with J diagonal):
+//   mass kind:      V = W * |J_aa(x)| * B_{e+i}(x)
+//   stiffness kind: V = W / |J_aa(x)| * B'_{e+i}(x)
+// with J_aa(x) = sum_i g_{a,e+i} B'_{e+i}(x) (Eq. Gmap1).  Raises the
+// geometry bit where J_aa <= 0 and the non-finite bit where J_aa is NaN/Inf.
+struct FoldSeg {
+  const int *elem;
+  const double *w, *t0, *t1, *g;
+  double *v64;
+  float *v32;
+  int start, kind;
+};
+struct FoldArgs {
+  FoldSeg seg[6];
+  int nseg, total, np;
+  unsigned *status;
+};
+
+__global__ void fold_kernel(const FoldArgs A) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned bits = 0;
+  if (t < A.total) {
+    int s = 0;
+    while (s + 1 < A.nseg && t >= A.seg[s + 1].start) s++;
+    const FoldSeg &S = A.seg[s];
+    const int q = t - S.start, np = A.np;
+    const int e = S.elem[q];
+    double J = 0.0;
+    for (int i = 0; i < np; i++) J = fma(S.g[e + i], S.t1[(size_t)q * np + i], J);
+    if (!(J > 0.0)) bits |= isfinite(J) ? wq::kBitGeometry : wq::kBitNonFinite;
+    const double aj = fabs(J);
+    const double f = S.kind == WQ_KIND_MASS ? S.w[q] * aj : S.w[q] / aj;
+    const double *T = S.kind == WQ_KIND_MASS ? S.t0 : S.t1;
+    for (int i = 0; i < np; i++) {
+      const double v = f * T[(size_t)q * np + i];
+      S.v64[(size_t)q * np + i] = v;
+      S.v32[(size_t)q * np + i] = (float)v;
+    }
+  }
+  bits = __reduce_or_sync(0xffffffffu, bits);
+  if ((threadIdx.x & 31) == 0 && bits) atomicOr(A.status, bits);
+}
+
+wq_status upload(wq_rules *R) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return WQ_ERR_CUDA;
+  int np = R->p + 1;
+  size_t total = 0;
+  // sizes per (dir, kind): off, elem, w, t0, t1, beta, v64, v32, beta32
+  size_t off_sz[3][2][9];
+  for (int a = 0; a < R->dim; a++)
+    for (int k = 0; k < 2; k++) {
+      const HostDirKind &H = R->host[a][k];
+      size_t npts = H.elem.size();
+      size_t s[9] = {H.off.size() * sizeof(int), npts * sizeof(int), npts * sizeof(double),
+                     npts * np * sizeof(double), npts * np * sizeof(double), npts * 4 * sizeof(double),
+                     npts * np * sizeof(double), npts * np * sizeof(float), npts * 4 * sizeof(float)};
+      for (int i = 0; i < 9; i++) {
+        off_sz[a][k][i] = total;
+        total += align_up(s[i]);
+      }
+    }
+  size_t lines_int = total;
+  total += align_up(R->lines.interior.size() * sizeof(int) + sizeof(int));
+  size_t lines_bnd = total;
+  total += align_up(R->lines.boundary.size() * sizeof(int) + sizeof(int));
+  size_t status_off = total;
+  total += align_up(sizeof(unsigned));
+
+  void *block = nullptr;
+  cudaError_t e = cudaMalloc(&block, total);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? WQ_ERR_OOM : WQ_ERR_CUDA;
+  }
+  char *base = static_cast<char *>(block);
+  auto put = [&](size_t off, const void *src, size_t bytes) -> bool {
+    return bytes == 0 || cudaMemcpy(base + off, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+  };
+  bool ok = true;
+  for (int a = 0; a < R->dim; a++)
+    for (int k = 0; k < 2; k++) {
+      const HostDirKind &H = R->host[a][k];
+      size_t npts = H.elem.size();
+      std::vector<float> b32(H.beta.begin(), H.beta.end());
+      ok = ok && put(off_sz[a][k][0], H.off.data(), H.off.size() * sizeof(int));
+      ok = ok && put(off_sz[a][k][1], H.elem.data(), npts * sizeof(int));
+      ok = ok && put(off_sz[a][k][2], H.w.data(), npts * sizeof(double));
+      ok = ok && put(off_sz[a][k][3], H.t0.data(), npts * np * sizeof(double));
+      ok = ok && put(off_sz[a][k][4], H.t1.data(), npts * np * sizeof(double));
+      ok = ok && put(off_sz[a][k][5], H.beta.data(), npts * 4 * sizeof(double));
+      ok = ok && put(off_sz[a][k][8], b32.data(), npts * 4 * sizeof(float));
+      wq::DevDirKind &Dk = R->dev[a][k];
+      Dk.off = reinterpret_cast<const int *>(base + off_sz[a][k][0]);
+      Dk.elem = reinterpret_cast<const int *>(base + off_sz[a][k][1]);
+      Dk.w = reinterpret_cast<const double *>(base + off_sz[a][k][2]);
+      Dk.t0 = reinterpret_cast<const double *>(base + off_sz[a][k][3]);
+      Dk.t1 = reinterpret_cast<const double *>(base + off_sz[a][k][4]);
+      Dk.beta = reinterpret_cast<const double *>(base + off_sz[a][k][5]);
+      Dk.v64 = reinterpret_cast<double *>(base + off_sz[a][k][6]);
+      Dk.v32 = reinterpret_cast<float *>(base + off_sz[a][k][7]);
+      Dk.beta32 = reinterpret_cast<float *>(base + off_sz[a][k][8]);
+      Dk.npts = (int)npts;
+    }
+  ok = ok && put(lines_int, R->lines.interior.data(), R->lines.interior.size() * sizeof(int));
+  ok = ok && put(lines_bnd, R->lines.boundary.data(), R->lines.boundary.size() * sizeof(int));
+  ok = ok && cudaMemset(base + status_off, 0, sizeof(unsigned)) == cudaSuccess;
+  if (!ok) {
+    cudaFree(block);
+    return WQ_ERR_CUDA;
+  }
+  R->dev_lines_interior = reinterpret_cast<const int *>(base + lines_int);
+  R->dev_lines_boundary = reinterpret_cast<const int *>(base + lines_bnd);
+  R->dev_status = reinterpret_cast<unsigned *>(base + status_off);
+  R->dev_block = block;
+  R->dev_bytes = total;
+  R->device = dev;
+  R->on_device = true;
+  return WQ_OK;
+}
+
+wq_status check_launch(cudaError_t e) {
+  if (e == cudaSuccess) return WQ_OK;
+  return WQ_ERR_CUDA;
+}
+
+wq_status launch_fold(const wq_rules *R, const double *const *geom, cudaStream_t s) {
+  FoldArgs fa;
+  std::memset(&fa, 0, sizeof(fa));
+  int total = 0, ns = 0;
+  for (int a = 0; a < R->dim; a++)
+    for (int k = 0; k < 2; k++) {
+      const wq::DevDirKind &Dk = R->dev[a][k];
+      FoldSeg &S = fa.seg[ns++];
+      S.elem = Dk.elem;
+      S.w = Dk.w;
+      S.t0 = Dk.t0;
+      S.t1 = Dk.t1;
+      S.g = geom[a];
+      S.v64 = Dk.v64;
+      S.v32 = Dk.v32;
+      S.start = total;
+      S.kind = k;
+      total += Dk.npts;
+    }
+  fa.nseg = ns;
+  fa.total = total;
+  fa.np = R->p + 1;
+  fa.status = R->dev_status;
+  fold_kernel<<<(total + 255) / 256, 256, 0, s>>>(fa);
+  return check_launch(cudaGetLastError());
+}
+
+wq_status assemble(const wq_rules *R, const double *const *geom, const double *coef, wq_precision prec, void *M,
+                   void *K, int64_t rb, int64_t re, void *stream) {
+  if (!R || !geom) return WQ_ERR_ARG;
+  if (!R->on_device) return WQ_ERR_ARG;
+  if (prec != WQ_FP64 && prec != WQ_MIXED) return WQ_ERR_ARG;
+  int64_t rows = (int64_t)R->n[0] * R->n[1] * R->n[2];
+  if (rb < 0 || re > rows || rb > re) return WQ_ERR_ARG;
+  if (rb != re && !M && !K) return WQ_ERR_ARG;
+  for (int a = 0; a < R->dim; a++)
+    if (!geom[a]) return WQ_ERR_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != R->device) return WQ_ERR_ARG;
+  if (rb == re) return WQ_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  wq_status st = launch_fold(R, geom, s);
+  if (st != WQ_OK) return st;
+
+  wq::RowsArgs ra;
+  std::memset(&ra, 0, sizeof(ra));
+  for (int a = 0; a < 3; a++) {
+    int aa = a < R->dim ? a : 0;
+    for (int k = 0; k < 2; k++) {
+      const wq::DevDirKind &Dk = R->dev[aa][k];
+      ra.off[a][k] = Dk.off;
+      ra.elem[a][k] = Dk.elem;
+      ra.V[a][k] = prec == WQ_FP64 ? (const void *)Dk.v64 : (const void *)Dk.v32;
+      ra.beta[a][k] = prec == WQ_FP64 ? (const void *)Dk.beta : (const void *)Dk.beta32;
+    }
+    ra.n[a] = R->n[a];
+    ra.N[a] = R->nel[a];
+    ra.nc[a] = R->nc[a];
+  }
+  ra.coef = coef;
+  ra.M = M;
+  ra.K = K;
+  ra.row_begin = rb;
+  ra.row_end = re;
+  ra.status = R->dev_status;
+  const int n1 = R->n[0];
+  const int first_line = (int)(rb / n1), last_line = (int)((re - 1) / n1);
+  for (int cls = 0; cls < 2; cls++) {
+    const std::vector<int> &lines = cls == 0 ? R->lines.interior : R->lines.boundary;
+    auto lo = std::lower_bound(lines.begin(), lines.end(), first_line);
+    auto hi = std::upper_bound(lines.begin(), lines.end(), last_line);
+    int nl = (int)(hi - lo);
+    if (nl <= 0) continue;
+    int tmax = cls == 0 ? wq::kInteriorChunk : wq::kBoundaryChunk;
+    ra.nch = (n1 + tmax - 1) / tmax;
+    ra.T = (n1 + ra.nch - 1) / ra.nch;
+    ra.lines = (cls == 0 ? R->dev_lines_interior : R->dev_lines_boundary) + (lo - lines.begin());
+    int nblocks = nl * ra.nch;
+    cudaError_t e;
+    bool dm = M != nullptr, dk = K != nullptr;
+    if (R->p == 2)
+      e = prec == WQ_FP64 ? wq::launch_rows<2, double>(R->dim, dm, dk, cls, ra, nblocks, s)
+                          : wq::launch_rows<2, float>(R->dim, dm, dk, cls, ra, nblocks, s);
+    else
+      e = prec == WQ_FP64 ? wq::launch_rows<3, double>(R->dim, dm, dk, cls, ra, nblocks, s)
+                          : wq::launch_rows<3, float>(R->dim, dm, dk, cls, ra, nblocks, s);
+    if (e != cudaSuccess) return WQ_ERR_CUDA;
+  }
+  return WQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *wq_status_string(wq_status s) {
+  switch (s) {
+    case WQ_OK: return "ok";
+    case WQ_ERR_ARG: return "invalid argument";
+    case WQ_ERR_UNSUPPORTED: return "unsupported degree, dimension or size";
+    case WQ_ERR_NO_CONVERGENCE: return "quadrature rule did not converge or failed its exactness check";
+    case WQ_ERR_GEOMETRY: return "Jacobian entry <= 0 at a quadrature point";
+    case WQ_ERR_NONFINITE: return "non-finite geometry or coefficient";
+    case WQ_ERR_CUDA: return "CUDA runtime error";
+    case WQ_ERR_OOM: return "device allocation failed";
+    case WQ_ERR_TIMEOUT: return "bounded device wait expired";
+  }
+  return "unknown status";
+}
+
+int wq_version(void) { return 100; }
+
+wq_status wq_rule_1d(int degree, int kind, double *tau, double *omega) {
+  if (!tau || !omega) return WQ_ERR_ARG;
+  if (degree < 2 || degree > wq::kMaxP || (kind != WQ_KIND_MASS && kind != WQ_KIND_STIFFNESS))
+    return WQ_ERR_UNSUPPORTED;
+  return wq::default_rule(degree, kind, tau, omega);
+}
+
+wq_status wq_rule_1d_from(int degree, int kind, const double *start, double *tau, double *omega) {
+  if (!start || !tau || !omega) return WQ_ERR_ARG;
+  return wq::solve_rule(degree, kind, start, tau, omega);
+}
+
+wq_status wq_rules_build(const wq_mesh *mesh, int flags, wq_rules **out) {
+  if (!mesh || !out) return WQ_ERR_ARG;
+  *out = nullptr;
+  if (mesh->dim < 2 || mesh->dim > 3 || mesh->degree < 2 || mesh->degree > wq::kMaxP) return WQ_ERR_UNSUPPORTED;
+  if (flags != WQ_RULES_HOST_ONLY && flags != WQ_RULES_DEVICE) return WQ_ERR_ARG;
+  for (int a = 0; a < mesh->dim; a++) {
+    if (mesh->nel[a] < 1) return WQ_ERR_ARG;
+    if (mesh->nel[a] > wq::kMaxNel) return WQ_ERR_UNSUPPORTED;
+  }
+  int64_t rows = 1;
+  for (int a = 0; a < mesh->dim; a++) rows *= mesh->nel[a] + mesh->degree;
+  if (rows > (int64_t)1 << 31) return WQ_ERR_UNSUPPORTED;
+  wq_rules *R = nullptr;
+  try {
+    R = new wq_rules();
+    R->mesh = *mesh;
+    R->p = mesh->degree;
+    R->dim = mesh->dim;
+    for (int a = 0; a < 3; a++) {
+      R->nel[a] = a < mesh->dim ? mesh->nel[a] : 1;
+      R->n[a] = a < mesh->dim ? mesh->nel[a] + mesh->degree : 1;
+      R->nc[a] = a < mesh->dim ? mesh->nel[a] + wq::kCoefDeg : 1;
+    }
+    wq_status st = wq::build_host_tables(R);
+    if (st == WQ_OK && flags == WQ_RULES_DEVICE) st = upload(R);
+    if (st != WQ_OK) {
+      delete R;
+      return st;
+    }
+  } catch (const std::bad_alloc &) {
+    delete R;
+    return WQ_ERR_OOM;
+  } catch (...) {
+    delete R;
+    return WQ_ERR_ARG;
+  }
+  *out = R;
+  return WQ_OK;
+}
+
+void wq_rules_free(wq_rules *rules) {
+  if (!rules) return;
+  if (rules->dev_block) {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != rules->device) cudaSetDevice(rules->device);
+    cudaFree(rules->dev_block);
+    if (cur >= 0 && cur != rules->device) cudaSetDevice(cur);
+  }
+  delete rules;
+}
+
+wq_status wq_rules_row(const wq_rules *R, int dir, int kind, int row, int *npts, double *x, double *w, int *elem) {
+  if (!R || dir < 0 || dir >= R->dim || (kind != 0 && kind != 1) || row < 0 || row >= R->n[dir]) return WQ_ERR_ARG;
+  const HostDirKind &H = R->host[dir][kind];
+  int o0 = H.off[row], o1 = H.off[row + 1];
+  if (npts) *npts = o1 - o0;
+  for (int q = o0; q < o1; q++) {
+    if (x) x[q - o0] = H.x[q];
+    if (w) w[q - o0] = H.w[q];
+    if (elem) elem[q - o0] = H.elem[q];
+  }
+  return WQ_OK;
+}
+
+int64_t wq_rows(const wq_rules *R) { return R ? (int64_t)R->n[0] * R->n[1] * R->n[2] : 0; }
+
+int64_t wq_band_width(const wq_rules *R) {
+  if (!R) return 0;
+  int64_t b = 1;
+  for (int a = 0; a < R->dim; a++) b *= 2 * R->p + 1;
+  return b;
+}
+
+int64_t wq_band_nnz(const wq_rules *R) {
+  if (!R) return 0;
+  int64_t z = 1;
+  for (int a = 0; a < R->dim; a++) {
+    int64_t n = R->n[a], p = R->p;
+    int64_t per = 0;
+    for (int64_t r = 0; r < n; r++) per += std::min(n - 1, r + p) - std::max<int64_t>(0, r - p) + 1;
+    z *= per;
+  }
+  return z;
+}
+
+int64_t wq_coef_count(const wq_rules *R) { return R ? (int64_t)R->nc[0] * R->nc[1] * R->nc[2] : 0; }
+
+double wq_flop_count(const wq_rules *R, int want_m, int want_k, int64_t row_begin, int64_t row_end,
+                     double *coef_flops) {
+  if (!R || row_begin < 0 || row_end > wq_rows(R) || row_begin > row_end) return -1.0;
+  return wq::flop_count(R, want_m, want_k, row_begin, row_end, coef_flops);
+}
+
+wq_status wq_assemble_mass(const wq_rules *rules, const double *const *geom, const double *coef, wq_precision prec,
+                           void *M, int64_t row_begin, int64_t row_end, void *stream) {
+  if (row_begin != row_end && (!M)) return WQ_ERR_ARG;
+  return assemble(rules, geom, coef, prec, M, nullptr, row_begin, row_end, stream);
+}
+
+wq_status wq_assemble_stiffness(const wq_rules *rules, const double *const *geom, const double *coef,
+                                wq_precision prec, void *K, int64_t row_begin, int64_t row_end, void *stream) {
+  if (row_begin != row_end && (!K)) return WQ_ERR_ARG;
+  return assemble(rules, geom, coef, prec, nullptr, K, row_begin, row_end, stream);
+}
+
+wq_status wq_assemble_mass_stiffness(const wq_rules *rules, const double *const *geom, const double *coef,
+                                     wq_precision prec, void *M, void *K, int64_t row_begin, int64_t row_end,
+                                     void *stream) {
+  if (row_begin != row_end && (!M || !K)) return WQ_ERR_ARG;
+  return assemble(rules, geom, coef, prec, M, K, row_begin, row_end, stream);
+}
+
+wq_status wq_status_check(const wq_rules *R, void *stream) {
+  if (!R || !R->on_device) return WQ_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return WQ_ERR_CUDA;
+  unsigned bits = 0;
+  if (cudaMemcpy(&bits, R->dev_status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return WQ_ERR_CUDA;
+  if (cudaMemset(R->dev_status, 0, sizeof(unsigned)) != cudaSuccess) return WQ_ERR_CUDA;
+  if (bits & wq::kBitNonFinite) return WQ_ERR_NONFINITE;
+  if (bits & wq::kBitGeometry) return WQ_ERR_GEOMETRY;
+  return WQ_OK;
+}
+
+}  // extern "C"

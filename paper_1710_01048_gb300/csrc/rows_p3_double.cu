@@ -1,0 +1,6 @@
+// Instantiation of the row kernels for degree 3, arithmetic type double.
+#include "launch.cuh"
+
+namespace wq {
+template cudaError_t launch_rows<3, double>(int, bool, bool, int, const RowsArgs &, int, cudaStream_t);
+}

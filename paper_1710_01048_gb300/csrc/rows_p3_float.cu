@@ -1,0 +1,6 @@
+// Instantiation of the row kernels for degree 3, arithmetic type float.
+#include "launch.cuh"
+
+namespace wq {
+template cudaError_t launch_rows<3, float>(int, bool, bool, int, const RowsArgs &, int, cudaStream_t);
+}

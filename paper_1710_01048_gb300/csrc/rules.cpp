@@ -1,0 +1,438 @@
+// Host FP64 construction of the univariate weighted Gaussian rules and of the
+// per-direction row tables consumed by the assembly kernels.
+//
+// Rules (Sec. 3): a symmetric (p+1)-point rule on the cardinal support
+// [0, p+1] that is exact for the products N(y) N(y-d) (mass, Eq. GaussQuadSys)
+// or N'(y) N'(y-d) (stiffness, Eq. GaussQuadSysStiff), d = -p..p.  The right
+// hand sides are exact rationals: int N_p(y) N_p(y-d) dy = N_{2p+1}(p+1+d) and
+// int N_p'(y) N_p'(y-d) dy = -N''_{2p+1}(p+1+d).  The unknowns of the symmetric
+// rule are found by Gauss-Newton with an analytic Jacobian over the p+1
+// independent conditions d = 0..p, steps halved whenever a node would leave
+// its element (one node per element, Sec. 3.1.2 and Sec. 3.2), then checked
+// against all 2p+1 conditions.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "wq_internal.h"
+
+namespace wq {
+namespace {
+
+long long binom(int n, int k) {
+  long long r = 1;
+  for (int i = 1; i <= k; i++) r = r * (n - k + i) / i;
+  return r;
+}
+
+long long factorial(int n) {
+  long long r = 1;
+  for (int i = 2; i <= n; i++) r *= i;
+  return r;
+}
+
+// m-th derivative of the cardinal B-spline of degree n at an integer x, as an
+// exact integer numerator over (n-m)!: sum_j (-1)^j C(n+1, j) (x-j)_+^(n-m).
+long long cardinal_at_integer_num(int n, int m, int x) {
+  long long s = 0;
+  for (int j = 0; j <= n + 1; j++) {
+    int t = x - j;
+    if (t <= 0) continue;
+    long long pw = 1;
+    for (int k = 0; k < n - m; k++) pw *= t;
+    s += ((j & 1) ? -1 : 1) * binom(n + 1, j) * pw;
+  }
+  return s;
+}
+
+// Exact moment of the weight function: mass m(d) = N_{2p+1}(p+1+d),
+// stiffness k(d) = -N''_{2p+1}(p+1+d).
+double exact_moment(int p, int kind, int d) {
+  int n = 2 * p + 1;
+  d = std::abs(d);
+  if (d > p) return 0.0;
+  if (kind == WQ_KIND_MASS) return (double)cardinal_at_integer_num(n, 0, p + 1 + d) / (double)factorial(n);
+  return -(double)cardinal_at_integer_num(n, 2, p + 1 + d) / (double)factorial(n - 2);
+}
+
+// m-th derivative of the degree-p cardinal B-spline at real y by the
+// truncated-power form, evaluated on the nearer half of the support
+// (N^(m)(y) = (-1)^m N^(m)(p+1-y)) to limit cancellation.
+double cardinal(int p, int m, double y) {
+  if (!(y > 0.0 && y < (double)(p + 1))) return 0.0;
+  double sign = 1.0;
+  if (y > 0.5 * (p + 1)) {
+    y = (double)(p + 1) - y;
+    if (m & 1) sign = -1.0;
+  }
+  double s = 0.0;
+  for (int j = 0; j <= p + 1; j++) {
+    double t = y - (double)j;
+    if (t <= 0.0) break;
+    double pw = 1.0;
+    for (int k = 0; k < p - m; k++) pw *= t;
+    s += ((j & 1) ? -1.0 : 1.0) * (double)binom(p + 1, j) * pw;
+  }
+  return sign * s / (double)factorial(p - m);
+}
+
+// Affine parametrisation of the symmetric rule: tau = At*u + bt, omega = Aw*u + bw.
+struct Param {
+  int nu;  // unknowns
+  double At[4][4], bt[4], Aw[4][4], bw[4];
+};
+
+Param make_param(int p, int kind) {
+  Param P;
+  std::memset(&P, 0, sizeof(P));
+  int L = p + 1;
+  if (p == 2 && kind == WQ_KIND_MASS) {  // u = (tau1, omega1, omega2), tau2 = 3/2
+    P.nu = 3;
+    P.At[0][0] = 1; P.bt[1] = 1.5; P.At[2][0] = -1; P.bt[2] = 3;
+    P.Aw[0][1] = 1; P.Aw[1][2] = 1; P.Aw[2][1] = 1;
+  } else if (p == 3 && kind == WQ_KIND_MASS) {  // u = (tau1, tau2, omega1, omega2)
+    P.nu = 4;
+    P.At[0][0] = 1; P.At[1][1] = 1; P.At[2][1] = -1; P.bt[2] = 4; P.At[3][0] = -1; P.bt[3] = 4;
+    P.Aw[0][2] = 1; P.Aw[1][3] = 1; P.Aw[2][3] = 1; P.Aw[3][2] = 1;
+  } else if (p == 2) {  // stiffness: u = (tau1, omega1), tau2 = 3/2, omega2 = 8/9
+    P.nu = 2;
+    P.At[0][0] = 1; P.bt[1] = 1.5; P.At[2][0] = -1; P.bt[2] = 3;
+    P.Aw[0][1] = 1; P.bw[1] = 8.0 / 9.0; P.Aw[2][1] = 1;
+  } else {  // p = 3 stiffness: u = (tau1, tau2, omega2), omega1 = 1
+    P.nu = 3;
+    P.At[0][0] = 1; P.At[1][1] = 1; P.At[2][1] = -1; P.bt[2] = 4; P.At[3][0] = -1; P.bt[3] = 4;
+    P.bw[0] = 1; P.Aw[1][2] = 1; P.Aw[2][2] = 1; P.bw[3] = 1;
+  }
+  (void)L;
+  return P;
+}
+
+void expand(const Param &P, int L, const double *u, double *tau, double *om) {
+  for (int k = 0; k < L; k++) {
+    tau[k] = P.bt[k];
+    om[k] = P.bw[k];
+    for (int j = 0; j < P.nu; j++) {
+      tau[k] += P.At[k][j] * u[j];
+      om[k] += P.Aw[k][j] * u[j];
+    }
+  }
+}
+
+double residual(int p, int kind, const double *tau, const double *om, int d) {
+  int m = kind;  // the weight function's derivative order
+  double s = 0.0;
+  for (int k = 0; k <= p; k++) s += om[k] * cardinal(p, m, tau[k]) * cardinal(p, m, tau[k] - d);
+  return s - exact_moment(p, kind, d);
+}
+
+bool nodes_in_elements(int p, const double *tau) {
+  for (int k = 0; k <= p; k++)
+    if (!(tau[k] > (double)k && tau[k] < (double)(k + 1))) return false;
+  return true;
+}
+
+// Solves the small symmetric positive system (J^T J) x = r by Gaussian elimination.
+bool solve_small(int n, double A[4][4], double *b) {
+  for (int c = 0; c < n; c++) {
+    int piv = c;
+    for (int r = c + 1; r < n; r++)
+      if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+    if (A[piv][c] == 0.0) return false;
+    if (piv != c) {
+      for (int k = 0; k < n; k++) std::swap(A[c][k], A[piv][k]);
+      std::swap(b[c], b[piv]);
+    }
+    for (int r = c + 1; r < n; r++) {
+      double f = A[r][c] / A[c][c];
+      for (int k = c; k < n; k++) A[r][k] -= f * A[c][k];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int r = n - 1; r >= 0; r--) {
+    double s = b[r];
+    for (int k = r + 1; k < n; k++) s -= A[r][k] * b[k];
+    b[r] = s / A[r][r];
+  }
+  return true;
+}
+
+}  // namespace
+
+wq_status solve_rule(int p, int kind, const double *start, double *tau, double *omega) {
+  if (p < 2 || p > kMaxP || (kind != WQ_KIND_MASS && kind != WQ_KIND_STIFFNESS)) return WQ_ERR_UNSUPPORTED;
+  int L = p + 1;
+  Param P = make_param(p, kind);
+  double u[4];
+  for (int j = 0; j < P.nu; j++) u[j] = start[j];
+  int neq = p + 1;  // conditions d = 0..p
+  int m = kind;
+  for (int it = 0; it < 100; it++) {
+    double t[4], w[4];
+    expand(P, L, u, t, w);
+    double F[4], Jm[4][4];
+    for (int e = 0; e < neq; e++) {
+      int d = e;
+      F[e] = residual(p, kind, t, w, d);
+      double dFt[4], dFw[4];
+      for (int k = 0; k < L; k++) {
+        double a = cardinal(p, m, t[k]), b = cardinal(p, m, t[k] - d);
+        double da = cardinal(p, m + 1, t[k]), db = cardinal(p, m + 1, t[k] - d);
+        dFt[k] = w[k] * (da * b + a * db);
+        dFw[k] = a * b;
+      }
+      for (int j = 0; j < P.nu; j++) {
+        double s = 0.0;
+        for (int k = 0; k < L; k++) s += dFt[k] * P.At[k][j] + dFw[k] * P.Aw[k][j];
+        Jm[e][j] = s;
+      }
+    }
+    double N[4][4], g[4];
+    for (int i = 0; i < P.nu; i++) {
+      g[i] = 0.0;
+      for (int e = 0; e < neq; e++) g[i] -= Jm[e][i] * F[e];
+      for (int j = 0; j < P.nu; j++) {
+        N[i][j] = 0.0;
+        for (int e = 0; e < neq; e++) N[i][j] += Jm[e][i] * Jm[e][j];
+      }
+    }
+    if (!solve_small(P.nu, N, g)) return WQ_ERR_NO_CONVERGENCE;
+    bool inside0 = nodes_in_elements(p, t);
+    double scale = 1.0, unew[4];
+    for (int h = 0; h < 60; h++) {
+      for (int j = 0; j < P.nu; j++) unew[j] = u[j] + scale * g[j];
+      if (!inside0) break;
+      double tt[4], ww[4];
+      expand(P, L, unew, tt, ww);
+      if (nodes_in_elements(p, tt)) break;
+      scale *= 0.5;
+    }
+    double smax = 0.0;
+    for (int j = 0; j < P.nu; j++) {
+      smax = std::max(smax, std::fabs(unew[j] - u[j]));
+      u[j] = unew[j];
+      if (!std::isfinite(u[j]) || std::fabs(u[j]) > 1e6) return WQ_ERR_NO_CONVERGENCE;
+    }
+    if (smax < 1e-16 && it >= 3) break;
+  }
+  expand(P, L, u, tau, omega);
+  if (!nodes_in_elements(p, tau)) return WQ_ERR_NO_CONVERGENCE;
+  for (int d = -p; d <= p; d++)
+    if (!(std::fabs(residual(p, kind, tau, omega, d)) <= 1e-14)) return WQ_ERR_NO_CONVERGENCE;
+  if (kind == WQ_KIND_MASS)
+    for (int k = 0; k < L; k++)
+      if (!(omega[k] > 0.0)) return WQ_ERR_NO_CONVERGENCE;
+  return WQ_OK;
+}
+
+// Default rules.  p=2 stiffness has the closed form tau = (3/4, 3/2, 9/4),
+// omega = 8/9 (Sec. 3.2.1); the others start from element midpoints (the
+// p=3 stiffness tau_1 from the midpoint of [0, 1/2], on the branch of the
+// smaller root, Sec. 3.2.2).
+wq_status default_rule(int p, int kind, double *tau, double *omega) {
+  if (p < 2 || p > kMaxP || (kind != WQ_KIND_MASS && kind != WQ_KIND_STIFFNESS)) return WQ_ERR_UNSUPPORTED;
+  if (p == 2 && kind == WQ_KIND_STIFFNESS) {
+    tau[0] = 0.75; tau[1] = 1.5; tau[2] = 2.25;
+    omega[0] = omega[1] = omega[2] = 8.0 / 9.0;
+    for (int d = -p; d <= p; d++)
+      if (!(std::fabs(residual(p, kind, tau, omega, d)) <= 1e-14)) return WQ_ERR_NO_CONVERGENCE;
+    return WQ_OK;
+  }
+  double start[4];
+  if (p == 2) { start[0] = 0.5; start[1] = 1.0; start[2] = 1.0; }
+  else if (kind == WQ_KIND_MASS) { start[0] = 0.5; start[1] = 1.5; start[2] = 1.0; start[3] = 1.0; }
+  else { start[0] = 0.25; start[1] = 1.5; start[2] = 1.0; }
+  return solve_rule(p, kind, start, tau, omega);
+}
+
+namespace {
+
+// Gauss-Legendre on [-1, 1] for n = 3, 4 in closed form.
+void gauss_legendre(int n, double *x, double *w) {
+  if (n == 3) {
+    double a = std::sqrt(0.6);
+    x[0] = -a; x[1] = 0.0; x[2] = a;
+    w[0] = 5.0 / 9.0; w[1] = 8.0 / 9.0; w[2] = 5.0 / 9.0;
+  } else {  // n == 4
+    double s = 2.0 / 7.0 * std::sqrt(1.2);
+    double xi = std::sqrt(3.0 / 7.0 - s), xo = std::sqrt(3.0 / 7.0 + s);
+    double wi = (18.0 + std::sqrt(30.0)) / 36.0, wo = (18.0 - std::sqrt(30.0)) / 36.0;
+    x[0] = -xo; x[1] = -xi; x[2] = xi; x[3] = xo;
+    w[0] = wo; w[1] = wi; w[2] = wi; w[3] = wo;
+  }
+}
+
+std::vector<double> knots(int q, int N) {
+  std::vector<double> t(N + 2 * q + 1);
+  for (int i = 0; i < (int)t.size(); i++) {
+    int k = i - q;
+    t[i] = k <= 0 ? 0.0 : (k >= N ? 1.0 : (double)k / (double)N);
+  }
+  return t;
+}
+
+// Values and first derivatives of the q+1 degree-q B-splines B_e..B_{e+q}
+// acting on element e, at x, by the triangular (de Boor) recurrence.
+void basis(const std::vector<double> &t, int q, int e, double x, double *val, double *der) {
+  int i = e + q;
+  double left[8], right[8], Nt[8][8];
+  Nt[0][0] = 1.0;
+  for (int d = 1; d <= q; d++) {
+    left[d] = x - t[i + 1 - d];
+    right[d] = t[i + d] - x;
+    double saved = 0.0;
+    for (int r = 0; r < d; r++) {
+      double temp = Nt[d - 1][r] / (right[r + 1] + left[d - r]);
+      Nt[d][r] = saved + right[r + 1] * temp;
+      saved = left[d - r] * temp;
+    }
+    Nt[d][d] = saved;
+  }
+  for (int j = 0; j <= q; j++) {
+    val[j] = Nt[q][j];
+    double a = 0.0, b = 0.0;
+    if (j >= 1) {
+      double den = t[i + j] - t[i - q + j];
+      if (den > 0.0) a = Nt[q - 1][j - 1] / den;
+    }
+    if (j <= q - 1) {
+      double den = t[i + j + 1] - t[i - q + j + 1];
+      if (den > 0.0) b = Nt[q - 1][j] / den;
+    }
+    der[j] = (double)q * (a - b);
+  }
+}
+
+}  // namespace
+
+wq_status build_host_tables(wq_rules *R) {
+  int p = R->p;
+  for (int kind = 0; kind < 2; kind++) {
+    wq_status st = default_rule(p, kind, R->tau[kind], R->omega[kind]);
+    if (st != WQ_OK) return st;
+  }
+  double gx[4], gw[4];
+  gauss_legendre(p + 1, gx, gw);
+  for (int a = 0; a < R->dim; a++) {
+    int N = R->nel[a], n = R->n[a];
+    double h = 1.0 / (double)N;
+    std::vector<double> tp = knots(p, N), tc = knots(kCoefDeg, N);
+    for (int kind = 0; kind < 2; kind++) {
+      HostDirKind &H = R->host[a][kind];
+      H = HostDirKind();
+      H.off.assign(n + 1, 0);
+      for (int r = 0; r < n; r++) {
+        H.off[r] = (int)H.elem.size();
+        // points of row r: (element, x, weight factor before B_r)
+        std::vector<int> pe;
+        std::vector<double> px, pf;
+        if (r >= p && r <= N - 1) {
+          for (int k = 0; k <= p; k++) {
+            pe.push_back(r - p + k);
+            px.push_back(((double)(r - p) + R->tau[kind][k]) * h);
+            pf.push_back(h * R->omega[kind][k]);
+          }
+        } else {
+          int elo = std::max(0, r - p), ehi = std::min(N - 1, r);
+          for (int e = elo; e <= ehi; e++)
+            for (int g = 0; g <= p; g++) {
+              pe.push_back(e);
+              px.push_back(((double)e + 0.5 * (gx[g] + 1.0)) * h);
+              pf.push_back(0.5 * h * gw[g]);
+            }
+        }
+        for (size_t q = 0; q < pe.size(); q++) {
+          int e = pe[q];
+          double x = px[q];
+          double v[8], dv[8], cv[8], cd[8];
+          basis(tp, p, e, x, v, dv);
+          basis(tc, kCoefDeg, e, x, cv, cd);
+          int j = r - e;  // B_r among B_e..B_{e+p}
+          double br = kind == WQ_KIND_MASS ? v[j] : dv[j];
+          H.elem.push_back(e);
+          H.x.push_back(x);
+          H.w.push_back(pf[q] * br);
+          for (int i = 0; i <= p; i++) {
+            H.t0.push_back(v[i]);
+            H.t1.push_back(dv[i]);
+          }
+          for (int i = 0; i <= kCoefDeg; i++) H.beta.push_back(cv[i]);
+        }
+      }
+      H.off[n] = (int)H.elem.size();
+    }
+  }
+  // lines: D=3 -> (r2, r3), D=2 -> r2; interior when dirs 2..D are interior rows
+  R->lines = Lines();
+  int nl = R->dim == 3 ? R->n[1] * R->n[2] : R->n[1];
+  for (int l = 0; l < nl; l++) {
+    int r2 = l % R->n[1];
+    int r3 = R->dim == 3 ? l / R->n[1] : 0;
+    bool in2 = r2 >= p && r2 <= R->nel[1] - 1;
+    bool in3 = R->dim == 3 ? (r3 >= p && r3 <= R->nel[2] - 1) : true;
+    (in2 && in3 ? R->lines.interior : R->lines.boundary).push_back(l);
+  }
+  return WQ_OK;
+}
+
+// Flops of the sum-factorised contractions over the band's non-zero
+// structure: per row and per direction, L_a points each touching p+1 band
+// entries, and an active band width A_a (the union of the touched entries).
+// Mass uses one point grid; stiffness uses d grids whose first two stages
+// are separate and whose last stage runs over the mass- and stiffness-kind
+// points of direction 1 (the terms with mass kind in direction 1 are summed
+// before it).  Coefficient evaluation: the cubic spline of c on each grid,
+// sum-factorised over the coefficients of each line of rows.
+double flop_count(const wq_rules *R, int want_m, int want_k, int64_t row_begin, int64_t row_end,
+                  double *coef_flops) {
+  int p = R->p, D = R->dim, NP = p + 1;
+  auto pts = [&](int a, int r) { return R->host[a][0].off[r + 1] - R->host[a][0].off[r]; };
+  auto active = [&](int a, int r) {
+    int lo = std::max(0, r - p), hi = std::min(R->n[a] - 1, r + p);
+    return hi - lo + 1;
+  };
+  double fl = 0.0, cf = 0.0;
+  int ng = (want_m ? 1 : 0) + (want_k ? D : 0);
+  for (int64_t row = row_begin; row < row_end; row++) {
+    int r1 = (int)(row % R->n[0]);
+    int64_t rest = row / R->n[0];
+    int r2 = (int)(rest % R->n[1]);
+    int r3 = D == 3 ? (int)(rest / R->n[1]) : 0;
+    double L1 = pts(0, r1), L2 = pts(1, r2), L3 = D == 3 ? pts(2, r3) : 1;
+    double A2 = active(1, r2), A3 = D == 3 ? active(2, r3) : 1;
+    double fma = 0.0;
+    if (D == 3) {
+      double xy = L1 * L2 * L3 * NP + L1 * A3 * L2 * NP;  // per grid: dir-3 then dir-2 stage
+      if (want_m) fma += xy + A2 * A3 * L1 * NP;
+      if (want_k) fma += 3 * xy + A2 * A3 * 2 * L1 * NP + 0.5 * A2 * A3 * L1;  // + the (K2+K3) adds
+    } else {
+      double y = L1 * L2 * NP;
+      if (want_m) fma += y + A2 * L1 * NP;
+      if (want_k) fma += 2 * y + A2 * 2 * L1 * NP;
+    }
+    fl += 2.0 * fma;
+    cf += 2.0 * ng * L1 * L2 * L3 * (kCoefDeg + 1);
+  }
+  if (coef_flops) {
+    // per line of rows: dir-3 then dir-2 contraction of the coefficient block
+    // (one pass over the n1 + 3 coefficient columns), shared by its rows
+    double lines_part = 0.0;
+    int64_t first_line = row_begin / R->n[0], last_line = row_end > row_begin ? (row_end - 1) / R->n[0] : -1;
+    for (int64_t l = first_line; l <= last_line; l++) {
+      int r2 = (int)(l % R->n[1]);
+      int r3 = D == 3 ? (int)(l / R->n[1]) : 0;
+      double L2 = pts(1, r2), L3 = D == 3 ? pts(2, r3) : 1;
+      double nl2 = std::min(R->nel[1] - 1, r2) - std::max(0, r2 - p) + 1 + kCoefDeg;
+      double ncomb = want_k ? D : 1;
+      if (D == 3) {
+        double nl3kinds = want_k ? 2 : 1;
+        lines_part += 2.0 * R->nc[0] * (nl3kinds * nl2 * L3 * 4 + ncomb * L2 * L3 * 4);
+      } else {
+        lines_part += 2.0 * R->nc[0] * (want_k ? 2 : 1) * L2 * 4;
+      }
+    }
+    *coef_flops = cf + lines_part;
+  }
+  return fl;
+}
+
+}  // namespace wq

@@ -1,0 +1,83 @@
+// Internal data structures of libwq (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/wq.h"
+
+namespace wq {
+
+constexpr int kMaxP = 3;
+constexpr int kMaxDim = 3;
+constexpr int kMaxRowPts = kMaxP * (kMaxP + 1);  // most points of one row in one direction
+constexpr int kCoefDeg = 3;                      // the coefficient field is a cubic spline
+constexpr int kMaxNel = 1 << 16;
+
+// Status bits raised by the kernels.
+constexpr unsigned kBitGeometry = 1u;
+constexpr unsigned kBitNonFinite = 2u;
+
+// One direction and one kind (mass or stiffness) of the 1D row rules.
+// Point q of row r lies in element elem[q]; the p+1 B-splines acting there
+// are B_{elem+i}, i = 0..p; the cubic coefficient splines acting there are
+// B3_{elem+i}, i = 0..3.
+struct HostDirKind {
+  std::vector<int> off;      // n+1 offsets into the point arrays
+  std::vector<int> elem;     // npts
+  std::vector<double> x;     // npts
+  std::vector<double> w;     // npts: W = h * omega * B_r^(nu)(x)
+  std::vector<double> t0;    // npts*(p+1): B_{elem+i}(x)
+  std::vector<double> t1;    // npts*(p+1): B'_{elem+i}(x)
+  std::vector<double> beta;  // npts*4: B3_{elem+i}(x)
+};
+
+// Device view of one direction and kind (all arrays in device memory).
+struct DevDirKind {
+  const int *off;
+  const int *elem;
+  const double *w;
+  const double *t0;
+  const double *t1;
+  const double *beta;
+  double *v64;  // folded tables, npts*(p+1): W*|J| B (mass), W/|J| B' (stiffness)
+  float *v32;   // the same rounded to float
+  float *beta32;
+  int npts;
+};
+
+struct Lines {
+  std::vector<int> interior, boundary;  // sorted line ids (r2 + n2*r3, or r2 for dim 2)
+};
+
+}  // namespace wq
+
+struct wq_rules {
+  wq_mesh mesh;
+  int p = 0, dim = 0;
+  int nel[3] = {1, 1, 1};
+  int n[3] = {1, 1, 1};
+  int nc[3] = {1, 1, 1};
+  double tau[2][wq::kMaxP + 1] = {};
+  double omega[2][wq::kMaxP + 1] = {};
+  wq::HostDirKind host[3][2];
+  wq::Lines lines;
+  // device side
+  bool on_device = false;
+  int device = -1;
+  void *dev_block = nullptr;
+  size_t dev_bytes = 0;
+  wq::DevDirKind dev[3][2] = {};
+  const int *dev_lines_interior = nullptr;
+  const int *dev_lines_boundary = nullptr;
+  unsigned *dev_status = nullptr;
+};
+
+namespace wq {
+// rules.cpp
+wq_status solve_rule(int p, int kind, const double *start, double *tau, double *omega);
+wq_status default_rule(int p, int kind, double *tau, double *omega);
+wq_status build_host_tables(wq_rules *R);
+double flop_count(const wq_rules *R, int want_m, int want_k, int64_t row_begin, int64_t row_end,
+                  double *coef_flops);
+}  // namespace wq

@@ -1,0 +1,154 @@
+"""Host-side tests of libwq (no GPU): the C-ABI loads and exports every
+symbol of include/wq.h; the host rule solver reproduces the paper's rules;
+the per-row tables agree with the oracle's; bookkeeping and argument
+checks."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from conftest import ROOT, read_golden
+from paper_1710_01048_gb300 import binding as wq
+from paper_1710_01048_gb300 import build as wqbuild
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    wqbuild.build()
+
+
+def header_functions():
+    with open(os.path.join(ROOT, "include", "wq.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(wq_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = wq.library()
+    declared = header_functions()
+    assert len(declared) >= 16
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(wq.EXPORTS) == declared
+
+
+def test_status_strings():
+    for s in range(9):
+        assert len(wq.wq_status_string(s)) >= 2 and wq.wq_status_string(s) != "unknown status"
+    assert wq.wq_version() >= 100
+
+
+def _printed(golden, kind, p):
+    pre = "mass" if kind == 0 else "stiff"
+    t1, t2 = float(golden[f"{pre}_p{p}_tau1"]), float(golden[f"{pre}_p{p}_tau2"])
+    w1, w2 = float(golden[f"{pre}_p{p}_omega1"]), float(golden[f"{pre}_p{p}_omega2"])
+    if p == 2:
+        return np.array([t1, t2, 3 - t1]), np.array([w1, w2, w1])
+    return np.array([t1, t2, 4 - t2, 4 - t1]), np.array([w1, w2, w2, w1])
+
+
+@pytest.mark.parametrize("p", [2, 3])
+@pytest.mark.parametrize("kind", [0, 1])
+def test_host_rules_match_printed(golden_rules, p, kind):
+    tau, om = wq.wq_rule_1d(p, kind)
+    pt, pw = _printed(golden_rules, kind, p)
+    # four units in the last place of values up to 4
+    assert np.all(np.abs(tau - pt) <= 4 * np.spacing(np.maximum(pt, 1.0))), tau - pt
+    assert np.all(np.abs(om - pw) <= 4 * np.spacing(np.maximum(pw, 1.0))), om - pw
+
+
+def test_host_rule_bad_start_is_reported(golden_rules):
+    # the start of Eq. WQcubicIni: never a wrong rule
+    st, tau, om = wq.wq_rule_1d_from(3, 0, [1 / 3, 5 / 3, 1.0, 1.0])
+    if st == wq.WQ_OK:
+        pt, _ = _printed(golden_rules, 0, 3)
+        assert np.max(np.abs(tau - pt)) < 1e-14
+    else:
+        assert st == wq.WQ_ERR_NO_CONVERGENCE
+    # starting at the spurious root of Sec. 3.1.2 (tau_2 outside [1, 2])
+    st, _, _ = wq.wq_rule_1d_from(3, 0, [float(golden_rules[k]) for k in
+                                         ("spurious_p3_tau1", "spurious_p3_tau2", "spurious_p3_omega1",
+                                          "spurious_p3_omega2")])
+    assert st == wq.WQ_ERR_NO_CONVERGENCE
+    # a start far outside: diverges or fails the checks
+    st, _, _ = wq.wq_rule_1d_from(3, 0, [5.0, -3.0, 100.0, -7.0])
+    assert st == wq.WQ_ERR_NO_CONVERGENCE
+
+
+@pytest.mark.parametrize("p", [2, 3])
+@pytest.mark.parametrize("nel", [1, 2, 3, 5, 11])
+def test_host_row_tables_match_oracle(p, nel):
+    R = wq.Rules(2, p, (nel, 4), device=False)
+    for kind in (0, 1):
+        for r in range(nel + p):
+            x, W, e = R.row(0, kind, r)
+            xo, Wo = oracle.row_points(p, nel, kind, r)
+            assert len(x) == len(xo)
+            assert np.max(np.abs(x - xo)) < 1e-15
+            assert np.max(np.abs(W - Wo)) < 1e-14 * max(1.0, np.max(np.abs(Wo)))
+            assert np.all(e == np.floor(x * nel).astype(int))
+    R.close()
+
+
+def test_bookkeeping_counts():
+    for p in (2, 3):
+        for nel in [(4, 5), (6, 7, 8), (64, 64, 64)]:
+            R = wq.Rules(len(nel), p, nel, device=False)
+            n = [v + p for v in nel]
+            assert R.rows == int(np.prod(n))
+            assert R.band == (2 * p + 1) ** len(nel)
+            assert R.nnz == int(np.prod([v * (2 * p + 1) - p * (p + 1) for v in n]))
+            assert R.ncoef == int(np.prod([v + 3 for v in nel]))
+            R.close()
+    # 64^3 cubic: 95.4M non-zeros per matrix
+    R = wq.Rules(3, 3, (64, 64, 64), device=False)
+    assert R.nnz == 457 ** 3
+    fl, cf = R.flops()
+    # interior rows: 4 terms' sum-factorised non-zero multiply-adds
+    interior = 2 * (3 * (4 * 4 * 4 * 4 + 4 * 7 * 4 * 4) + (64 + 112) + 49 * 4 * 4 * 3 + 0.5 * 49 * 4)
+    assert fl > interior * R.rows * 0.9
+    R.close()
+
+
+def test_point_count_reduction_and_evaluation_counts():
+    """Sec. 3, Eq. Reduction and the comparison values of Sec. 4: per
+    direction an interior row uses p+1 points against the 2p+1 of a
+    Newton-Cotes-type weighted rule; counting the non-vanishing basis
+    evaluations (knots lose one function), the 2D ratios are (13/9)^2 = 2.09
+    and (25/16)^2 = 2.44 for p = 2, 3."""
+    printed = {int(r[0]): float(r[1]) for r in read_golden("counts_printed.txt")}
+    for p in (2, 3):
+        R = wq.Rules(2, p, (100, 100), device=False)
+        r = 50
+        x, W, e = R.row(0, 0, r)
+        assert len(x) == p + 1
+        wq_evals = len(x) * (p + 1)  # each point in one element: p+1 non-zero B-splines
+        nc_points = 2 * p + 1  # interior knots and midpoints of supp B_r where B_r > 0
+        nc_knots = p  # interior knots of the support: p non-zero B-splines there
+        nc_evals = (nc_points - nc_knots) * (p + 1) + nc_knots * p
+        ratio = (nc_evals / wq_evals) ** 2
+        assert abs(ratio - printed[p]) < 0.01
+        assert abs(((p + 1) / (2 * p + 1)) ** 2 - (len(x) / nc_points) ** 2) < 1e-15
+        R.close()
+
+
+def test_argument_validation():
+    with pytest.raises(wq.WqError) as ei:
+        wq.Rules(4, 3, (4, 4, 4), device=False)
+    assert ei.value.status == wq.WQ_ERR_UNSUPPORTED
+    with pytest.raises(wq.WqError) as ei:
+        wq.Rules(3, 5, (4, 4, 4), device=False)
+    assert ei.value.status == wq.WQ_ERR_UNSUPPORTED
+    with pytest.raises(wq.WqError) as ei:
+        wq.Rules(3, 3, (4, 0, 4), device=False)
+    assert ei.value.status == wq.WQ_ERR_ARG
+    R = wq.Rules(3, 2, (3, 3, 3), device=False)
+    # assembly on a host-only object is an argument error, before any CUDA call
+    st = wq.wq_assemble_mass(R.handle, [1, 1, 1], None, wq.WQ_FP64, 1, 0, 1, None)
+    assert st == wq.WQ_ERR_ARG
+    with pytest.raises(wq.WqError):
+        R.row(3, 0, 0)
+    R.close()
