@@ -185,6 +185,42 @@ wq_status wq_assemble_mass_stiffness(const wq_rules *rules, const double *const 
  */
 wq_status wq_status_check(const wq_rules *rules, void *stream);
 
+/*
+ * Assembly that allocates no device memory.  The paper has no counterpart:
+ * this is a deployment variant of wq_assemble_mass_stiffness for callers that
+ * cannot call cudaMalloc -- a host application whose device memory all
+ * belongs to its own pool or arena, or that may not allocate once it is
+ * running -- so they cannot hold the device tables a WQ_RULES_DEVICE rules
+ * object owns.  Instead, the 1D row tables, the folded geometry tables, the
+ * line lists and the status word live in one fixed 8 MiB array in device
+ * memory, declared in the library; every GPU that loads the library holds
+ * that array until the process exits.
+ *
+ *   rules        host tables from wq_rules_build (WQ_RULES_HOST_ONLY suffices;
+ *                device tables, if any, are not used);
+ *   geom, coef   as for wq_assemble_mass_stiffness (device, caller-owned);
+ *   M, K         device band outputs as there; either may be NULL to skip
+ *                that matrix, not both (unless the range is empty);
+ *   check_status 0: return once the work is enqueued on `stream`;
+ *                non-zero: synchronise `stream` and return the
+ *                device-detected status of this call (WQ_ERR_GEOMETRY,
+ *                WQ_ERR_NONFINITE) as wq_status_check would.
+ *
+ * Returns WQ_ERR_UNSUPPORTED, before touching the GPU, when the mesh's tables
+ * do not fit the 8 MiB array (about 1000 elements per direction in 3D; the
+ * line lists grow with nel_2 * nel_3).  The call makes no cudaMalloc,
+ * cudaFree or other allocating call; it copies the host tables into the
+ * array with cudaMemcpyAsync on `stream` every time.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * All calls on a device share the one array, which keeps the last call's
+ * contents: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.
+ */
+wq_status wq_assemble_noalloc(const wq_rules *rules, const double *const *geom, const double *coef,
+                              wq_precision prec, void *M, void *K, int64_t row_begin, int64_t row_end, void *stream,
+                              int check_status);
+
 #ifdef __cplusplus
 }
 #endif

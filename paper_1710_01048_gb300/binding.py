@@ -25,7 +25,8 @@ WQ_RULES_HOST_ONLY, WQ_RULES_DEVICE = 0, 1
 # every function declared in include/wq.h
 EXPORTS = ["wq_status_string", "wq_version", "wq_rule_1d", "wq_rule_1d_from", "wq_rules_build", "wq_rules_free",
            "wq_rules_row", "wq_rows", "wq_band_width", "wq_band_nnz", "wq_coef_count", "wq_flop_count",
-           "wq_assemble_mass", "wq_assemble_stiffness", "wq_assemble_mass_stiffness", "wq_status_check"]
+           "wq_assemble_mass", "wq_assemble_stiffness", "wq_assemble_mass_stiffness", "wq_status_check",
+           "wq_assemble_noalloc"]
 
 
 class WqError(RuntimeError):
@@ -76,6 +77,7 @@ def _lib():
     lib.wq_assemble_mass_stiffness.argtypes = [c_void_p, PP, c_void_p, c_int, c_void_p, c_void_p, i64, i64,
                                                c_void_p]
     lib.wq_status_check.argtypes = [c_void_p, c_void_p]
+    lib.wq_assemble_noalloc.argtypes = [c_void_p, PP, c_void_p, c_int, c_void_p, c_void_p, i64, i64, c_void_p, c_int]
     for f in EXPORTS:
         if f not in ("wq_status_string", "wq_version", "wq_rules_free", "wq_rows", "wq_band_width", "wq_band_nnz",
                      "wq_coef_count", "wq_flop_count"):
@@ -193,6 +195,13 @@ def wq_assemble_mass_stiffness(handle, geom_ptrs, coef_ptr, prec, M_ptr, K_ptr, 
 
 def wq_status_check(handle, stream):
     return _lib().wq_status_check(handle, stream)
+
+
+def wq_assemble_noalloc(handle, geom_ptrs, coef_ptr, prec, M_ptr, K_ptr, row_begin, row_end, stream, check_status):
+    """The assembly entry point that allocates no device memory (see wq.h)."""
+    g, keep = _geom_array(geom_ptrs)
+    return _lib().wq_assemble_noalloc(handle, g, coef_ptr, prec, M_ptr, K_ptr, row_begin, row_end, stream,
+                                      int(check_status))
 
 
 # ------------------------------------------------------------------ conveniences

@@ -28,7 +28,8 @@ CU_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xc
                    "--expt-relaxed-constexpr", "-I", INCLUDE]
 CXX_FLAGS = ["-O2", "-fPIC", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-I", INCLUDE]
 
-SOURCES = ["rules.cpp", "api.cu", "rows_p2_double.cu", "rows_p3_double.cu", "rows_p2_float.cu", "rows_p3_float.cu"]
+SOURCES = ["rules.cpp", "api.cu", "rows_p2_double.cu", "rows_p3_double.cu", "rows_p2_float.cu", "rows_p3_float.cu",
+           "noalloc.cu"]
 HEADERS = ["wq_internal.h", "assemble.cuh", "launch.cuh"]
 
 
