@@ -66,8 +66,13 @@ typedef enum wq_status {
 
 typedef enum wq_precision {
   WQ_FP64 = 0,  /* FP64 throughout; band written as double */
-  WQ_MIXED = 1  /* Jacobian and rule tables in FP64, contractions in FP32 with
-                   compensated final sums; band written as float */
+  WQ_MIXED = 1, /* Jacobian and rule tables in FP64, contractions in FP32;
+                   band written as float */
+  WQ_DF64 = 2   /* Jacobian and rule tables in FP64, contractions in
+                   double-float arithmetic (pairs of floats, ~48-bit
+                   significand) on the FP32 pipe; band written as double.
+                   Agrees with WQ_FP64 to ~1e-14 relative for inputs within
+                   float's exponent range (|values| in 1e-30 .. 1e30) */
 } wq_precision;
 
 enum { WQ_KIND_MASS = 0, WQ_KIND_STIFFNESS = 1 };
@@ -162,7 +167,7 @@ double wq_flop_count(const wq_rules *rules, int want_m, int want_k, int64_t row_
  *   coef     device, prod(nel_a + 3) doubles, x fastest: degree-3 spline of
  *            the coefficient c; NULL means c = 1;
  *   M, K     device, (row_end - row_begin) * band entries, double for
- *            WQ_FP64, float for WQ_MIXED; row row_begin is stored first;
+ *            WQ_FP64 and WQ_DF64, float for WQ_MIXED; row row_begin is stored first;
  *            may be NULL when row_begin == row_end (nothing is written).
  * wq_assemble_mass_stiffness writes both (the fused path); the single-matrix
  * forms write one.  The rules object must have been built with

@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libwq.so")
 
 WQ_OK, WQ_ERR_ARG, WQ_ERR_UNSUPPORTED, WQ_ERR_NO_CONVERGENCE = 0, 1, 2, 3
 WQ_ERR_GEOMETRY, WQ_ERR_NONFINITE, WQ_ERR_CUDA, WQ_ERR_OOM, WQ_ERR_TIMEOUT = 4, 5, 6, 7, 8
-WQ_FP64, WQ_MIXED = 0, 1
+WQ_FP64, WQ_MIXED, WQ_DF64 = 0, 1, 2
+PRECISIONS = {"fp64": WQ_FP64, "mixed": WQ_MIXED, "df64": WQ_DF64}
 WQ_KIND_MASS, WQ_KIND_STIFFNESS = 0, 1
 WQ_RULES_HOST_ONLY, WQ_RULES_DEVICE = 0, 1
 
@@ -260,15 +261,16 @@ def assemble(rules, geom, coef=None, prec="fp64", mass=True, stiffness=True, row
     """Assembles rows [row_begin, row_end) of M and/or K (band layout) on the
     current CUDA device.  geom: list of dim float64 CUDA tensors (control
     values); coef: float64 CUDA tensor of rules.ncoef values or None (c = 1).
-    Returns (M, K) torch tensors of shape (rows, band), float64 for 'fp64',
-    float32 for 'mixed'.  With check=True the stream is synchronised and a
+    prec: 'fp64', 'df64' (double-float on the FP32 pipe, FP64 output) or
+    'mixed' (FP32).  Returns (M, K) torch tensors of shape (rows, band),
+    float64 for 'fp64' and 'df64', float32 for 'mixed'.  With check=True the stream is synchronised and a
     device-detected problem raises WqError."""
     import torch
 
     if row_end is None:
         row_end = rules.rows
-    p = WQ_FP64 if prec == "fp64" else WQ_MIXED
-    dt = torch.float64 if p == WQ_FP64 else torch.float32
+    p = PRECISIONS[prec]
+    dt = torch.float32 if p == WQ_MIXED else torch.float64
     nrows = row_end - row_begin
     for g in geom:
         assert g.is_cuda and g.dtype == torch.float64 and g.is_contiguous()

@@ -26,11 +26,12 @@ NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
                    "--expt-relaxed-constexpr", "-I", INCLUDE]
-CXX_FLAGS = ["-O2", "-fPIC", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-I", INCLUDE]
+CXX_FLAGS = ["-O2", "-fPIC", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-I", INCLUDE,
+             "-I", os.path.join(CUDA_HOME, "include")]
 
 SOURCES = ["rules.cpp", "api.cu", "rows_p2_double.cu", "rows_p3_double.cu", "rows_p2_float.cu", "rows_p3_float.cu",
-           "noalloc.cu"]
-HEADERS = ["wq_internal.h", "assemble.cuh", "launch.cuh"]
+           "rows_p2_dd.cu", "rows_p3_dd.cu", "noalloc.cu"]
+HEADERS = ["wq_internal.h", "assemble.cuh", "launch.cuh", "dd.cuh"]
 
 
 def _newest_dep():
@@ -38,13 +39,13 @@ def _newest_dep():
     return max(os.path.getmtime(d) for d in deps)
 
 
-def _compile(src, force, verbose):
+def _compile(src, force, verbose, out, extra):
     path = os.path.join(CSRC, src)
-    obj = os.path.join(OUT, src.replace(".", "_") + ".o")
+    obj = os.path.join(out, src.replace(".", "_") + ".o")
     if not force and os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(path), _newest_dep()):
         return obj
     if src.endswith(".cu"):
-        cmd = [NVCC] + CU_FLAGS + ["-c", path, "-o", obj + ".tmp"]
+        cmd = [NVCC] + CU_FLAGS + list(extra) + ["-c", path, "-o", obj + ".tmp"]
     else:
         cmd = ["g++"] + CXX_FLAGS + ["-c", path, "-o", obj + ".tmp"]
     if verbose:
@@ -58,24 +59,27 @@ def _compile(src, force, verbose):
     return obj
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compiles and links libwq.so; returns its path.  Incremental unless force."""
+def build(force: bool = False, verbose: bool = False, out_dir: str = OUT, extra_nvcc=()) -> str:
+    """Compiles and links libwq.so into out_dir (default: the in-tree _build);
+    returns its path.  Incremental unless force.  extra_nvcc: additional nvcc
+    flags (e.g. -D tuning macros) for the CUDA sources."""
     if shutil.which(NVCC) is None and not os.path.exists(NVCC):
         raise RuntimeError(f"nvcc not found at {NVCC}")
-    os.makedirs(OUT, exist_ok=True)
+    os.makedirs(out_dir, exist_ok=True)
+    lib = os.path.join(out_dir, "libwq.so")
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, force, verbose), SOURCES))
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
+        objs = list(ex.map(lambda s: _compile(s, force, verbose, out_dir, extra_nvcc), SOURCES))
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
         lib64 = os.path.join(CUDA_HOME, "lib64")
-        tmp = LIB + f".tmp{os.getpid()}"
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [NVCC] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + ["-Xlinker", f"-rpath,{lib64}"]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -30,6 +30,7 @@ struct FoldSeg {
   const double *w, *t0, *t1, *g;
   double *v64;
   float *v32;
+  float2 *vdd;
   int start, kind;
 };
 struct FoldArgs {
@@ -55,8 +56,10 @@ __global__ void fold_kernel(const FoldArgs A) {
     const double *T = S.kind == WQ_KIND_MASS ? S.t0 : S.t1;
     for (int i = 0; i < np; i++) {
       const double v = f * T[(size_t)q * np + i];
+      const float vh = (float)v;
       S.v64[(size_t)q * np + i] = v;
-      S.v32[(size_t)q * np + i] = (float)v;
+      S.v32[(size_t)q * np + i] = vh;
+      S.vdd[(size_t)q * np + i] = make_float2(vh, (float)(v - (double)vh));
     }
   }
   bits = __reduce_or_sync(0xffffffffu, bits);
@@ -68,16 +71,17 @@ wq_status upload(wq_rules *R) {
   if (cudaGetDevice(&dev) != cudaSuccess) return WQ_ERR_CUDA;
   int np = R->p + 1;
   size_t total = 0;
-  // sizes per (dir, kind): off, elem, w, t0, t1, beta, v64, v32, beta32
-  size_t off_sz[3][2][9];
+  // sizes per (dir, kind): off, elem, w, t0, t1, beta, v64, v32, beta32, vdd, betadd
+  size_t off_sz[3][2][11];
   for (int a = 0; a < R->dim; a++)
     for (int k = 0; k < 2; k++) {
       const HostDirKind &H = R->host[a][k];
       size_t npts = H.elem.size();
-      size_t s[9] = {H.off.size() * sizeof(int), npts * sizeof(int), npts * sizeof(double),
-                     npts * np * sizeof(double), npts * np * sizeof(double), npts * 4 * sizeof(double),
-                     npts * np * sizeof(double), npts * np * sizeof(float), npts * 4 * sizeof(float)};
-      for (int i = 0; i < 9; i++) {
+      size_t s[11] = {H.off.size() * sizeof(int), npts * sizeof(int), npts * sizeof(double),
+                      npts * np * sizeof(double), npts * np * sizeof(double), npts * 4 * sizeof(double),
+                      npts * np * sizeof(double), npts * np * sizeof(float), npts * 4 * sizeof(float),
+                      npts * np * sizeof(float2), npts * 4 * sizeof(float2)};
+      for (int i = 0; i < 11; i++) {
         off_sz[a][k][i] = total;
         total += align_up(s[i]);
       }
@@ -105,6 +109,11 @@ wq_status upload(wq_rules *R) {
       const HostDirKind &H = R->host[a][k];
       size_t npts = H.elem.size();
       std::vector<float> b32(H.beta.begin(), H.beta.end());
+      std::vector<float2> bdd(H.beta.size());
+      for (size_t i = 0; i < H.beta.size(); i++) {
+        float hi = (float)H.beta[i];
+        bdd[i] = make_float2(hi, (float)(H.beta[i] - (double)hi));
+      }
       ok = ok && put(off_sz[a][k][0], H.off.data(), H.off.size() * sizeof(int));
       ok = ok && put(off_sz[a][k][1], H.elem.data(), npts * sizeof(int));
       ok = ok && put(off_sz[a][k][2], H.w.data(), npts * sizeof(double));
@@ -112,6 +121,7 @@ wq_status upload(wq_rules *R) {
       ok = ok && put(off_sz[a][k][4], H.t1.data(), npts * np * sizeof(double));
       ok = ok && put(off_sz[a][k][5], H.beta.data(), npts * 4 * sizeof(double));
       ok = ok && put(off_sz[a][k][8], b32.data(), npts * 4 * sizeof(float));
+      ok = ok && put(off_sz[a][k][10], bdd.data(), npts * 4 * sizeof(float2));
       wq::DevDirKind &Dk = R->dev[a][k];
       Dk.off = reinterpret_cast<const int *>(base + off_sz[a][k][0]);
       Dk.elem = reinterpret_cast<const int *>(base + off_sz[a][k][1]);
@@ -122,6 +132,8 @@ wq_status upload(wq_rules *R) {
       Dk.v64 = reinterpret_cast<double *>(base + off_sz[a][k][6]);
       Dk.v32 = reinterpret_cast<float *>(base + off_sz[a][k][7]);
       Dk.beta32 = reinterpret_cast<float *>(base + off_sz[a][k][8]);
+      Dk.vdd = reinterpret_cast<float2 *>(base + off_sz[a][k][9]);
+      Dk.betadd = reinterpret_cast<float2 *>(base + off_sz[a][k][10]);
       Dk.npts = (int)npts;
     }
   ok = ok && put(lines_int, R->lines.interior.data(), R->lines.interior.size() * sizeof(int));
@@ -161,6 +173,7 @@ wq_status launch_fold(const wq_rules *R, const double *const *geom, cudaStream_t
       S.g = geom[a];
       S.v64 = Dk.v64;
       S.v32 = Dk.v32;
+      S.vdd = Dk.vdd;
       S.start = total;
       S.kind = k;
       total += Dk.npts;
@@ -177,7 +190,7 @@ wq_status assemble(const wq_rules *R, const double *const *geom, const double *c
                    void *K, int64_t rb, int64_t re, void *stream) {
   if (!R || !geom) return WQ_ERR_ARG;
   if (!R->on_device) return WQ_ERR_ARG;
-  if (prec != WQ_FP64 && prec != WQ_MIXED) return WQ_ERR_ARG;
+  if (prec != WQ_FP64 && prec != WQ_MIXED && prec != WQ_DF64) return WQ_ERR_ARG;
   int64_t rows = (int64_t)R->n[0] * R->n[1] * R->n[2];
   if (rb < 0 || re > rows || rb > re) return WQ_ERR_ARG;
   if (rb != re && !M && !K) return WQ_ERR_ARG;
@@ -198,8 +211,10 @@ wq_status assemble(const wq_rules *R, const double *const *geom, const double *c
       const wq::DevDirKind &Dk = R->dev[aa][k];
       ra.off[a][k] = Dk.off;
       ra.elem[a][k] = Dk.elem;
-      ra.V[a][k] = prec == WQ_FP64 ? (const void *)Dk.v64 : (const void *)Dk.v32;
-      ra.beta[a][k] = prec == WQ_FP64 ? (const void *)Dk.beta : (const void *)Dk.beta32;
+      ra.V[a][k] = prec == WQ_FP64 ? (const void *)Dk.v64
+                   : prec == WQ_MIXED ? (const void *)Dk.v32 : (const void *)Dk.vdd;
+      ra.beta[a][k] = prec == WQ_FP64 ? (const void *)Dk.beta
+                      : prec == WQ_MIXED ? (const void *)Dk.beta32 : (const void *)Dk.betadd;
     }
     ra.n[a] = R->n[a];
     ra.N[a] = R->nel[a];
@@ -220,6 +235,7 @@ wq_status assemble(const wq_rules *R, const double *const *geom, const double *c
     int nl = (int)(hi - lo);
     if (nl <= 0) continue;
     int tmax = cls == 0 ? wq::kInteriorChunk : wq::kBoundaryChunk;
+    if (R->max_chunk_points[cls] > wq::chunk_points_bound(R->p, tmax)) return WQ_ERR_UNSUPPORTED;
     ra.nch = (n1 + tmax - 1) / tmax;
     ra.T = (n1 + ra.nch - 1) / ra.nch;
     ra.lines = (cls == 0 ? R->dev_lines_interior : R->dev_lines_boundary) + (lo - lines.begin());
@@ -227,11 +243,13 @@ wq_status assemble(const wq_rules *R, const double *const *geom, const double *c
     cudaError_t e;
     bool dm = M != nullptr, dk = K != nullptr;
     if (R->p == 2)
-      e = prec == WQ_FP64 ? wq::launch_rows<2, double>(R->dim, dm, dk, cls, ra, nblocks, s)
-                          : wq::launch_rows<2, float>(R->dim, dm, dk, cls, ra, nblocks, s);
+      e = prec == WQ_FP64   ? wq::launch_rows<2, double>(R->dim, dm, dk, cls, ra, nblocks, s)
+          : prec == WQ_MIXED ? wq::launch_rows<2, float>(R->dim, dm, dk, cls, ra, nblocks, s)
+                             : wq::launch_rows<2, wq::dd>(R->dim, dm, dk, cls, ra, nblocks, s);
     else
-      e = prec == WQ_FP64 ? wq::launch_rows<3, double>(R->dim, dm, dk, cls, ra, nblocks, s)
-                          : wq::launch_rows<3, float>(R->dim, dm, dk, cls, ra, nblocks, s);
+      e = prec == WQ_FP64   ? wq::launch_rows<3, double>(R->dim, dm, dk, cls, ra, nblocks, s)
+          : prec == WQ_MIXED ? wq::launch_rows<3, float>(R->dim, dm, dk, cls, ra, nblocks, s)
+                             : wq::launch_rows<3, wq::dd>(R->dim, dm, dk, cls, ra, nblocks, s);
     if (e != cudaSuccess) return WQ_ERR_CUDA;
   }
   return WQ_OK;
@@ -288,6 +306,8 @@ wq_status wq_rules_build(const wq_mesh *mesh, int flags, wq_rules **out) {
     R->mesh = *mesh;
     R->p = mesh->degree;
     R->dim = mesh->dim;
+    R->chunk_rows[0] = wq::kInteriorChunk;
+    R->chunk_rows[1] = wq::kBoundaryChunk;
     for (int a = 0; a < 3; a++) {
       R->nel[a] = a < mesh->dim ? mesh->nel[a] : 1;
       R->n[a] = a < mesh->dim ? mesh->nel[a] + mesh->degree : 1;

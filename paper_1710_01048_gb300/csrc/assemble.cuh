@@ -1,39 +1,50 @@
 // Row-wise weighted-quadrature assembly kernel (sum factorisation into the
-// band), templated on degree P, dimension D, point capacity of the inner
-// directions LM, and the arithmetic type R (double, or float for the mixed
-// mode).
+// band), templated on degree P, dimension D, point capacity LM of the inner
+// directions, chunk length TMAX, the terms (DO_M, DO_K) and the arithmetic
+// type R (double; float for the mixed mode; dd, double-float on the FP32
+// pipe, for FP64 accuracy at FP32 throughput).
 //
-// Work decomposition.  A CTA owns a chunk of consecutive rows along x1 that
-// share (r2, r3) -- one "line" of rows.  Rows of a line share their rule
-// points in directions 2..D, so the coefficient spline c is contracted over
-// directions D..2 once per chunk (phase A), leaving c on the (q2, q3) point
-// grid for every coefficient column l1.  Each warp then takes one row at a
-// time (phase B) and streams over blocks of P+1 points of direction 1 (an
-// interior row is one block, a boundary row one block per element):
-//   C1: c at the block's points of each grid, from the phase-A columns
-//   X : contraction over q3 into the band index j3   (D = 3)
-//   Y : contraction over q2 into j2
-//   F : contraction over q1 into j1, accumulated in registers
-// The grids are the point sets of the terms (Sec. 3.1 rule in every
-// direction for M; Sec. 3.2 rule in direction a and Sec. 3.1 elsewhere for
-// term a of K).  The folded 1D tables already hold W * |J_aa| (mass kind) or
-// W / |J_aa| (stiffness kind), so c is the only per-point factor.
+// A CTA owns a chunk of consecutive rows along x1 that share (r2, r3), one
+// "line" of rows; their rules in directions 2..D coincide.  Writing term g's
+// band entries as
+//   A_g[j1][j2][j3] = sum_{q1} V1[q1][j1] sum_{l1} b1_{q1}[l1] U_g[l1][j2][j3],
+//   U_g[l1][j2][j3] = sum_{q2,q3} c_{l1}(x_q2, x_q3) V2[q2][j2] V3[q3][j3],
+// where c_{l1}(.,.) = sum_{l2,l3} C[l1][l2][l3] b2(.)[l2] b3(.)[l3] is the
+// coefficient spline's column l1 and b the cubic B-spline values at the
+// points (Eq. Decompo applied to the weighted sums of Eq. GaussQuadSys and
+// Eq. GaussQuadSysStiff, with c as the integrand's factor), U depends only on
+// the line.  Phase A builds U for the chunk's coefficient columns, one
+// direction at a time (x3 then x2), for the two combinations the terms need:
+//   U0: mass kind in x2 and x3           (terms M and K1)
+//   U1: stiffness kind in x2 + in x3     (K2 + K3, summed)
+// one warp per column.  Phase B takes one warp per row: lane l owns the
+// band fibres (j2, j3) = l, l+32, ...; at each x1 point it forms
+//   y_M = b1M . U0,  y_K = b1M . U1,  y_S = b1S . U0
+// and accumulates A_M += V1M y_M, A_K += V1M y_K + V1S y_S over the 2P+1
+// entries j1 of the fibre; the row's band is staged in shared memory and
+// written with consecutive lanes on consecutive addresses.  The folded 1D
+// tables hold W * |J_aa| (mass kind) or W / |J_aa| (stiffness kind), so no
+// other per-point factor remains.  Rows whose x1 rule is the weighted Gaussian
+// one (P+1 points, one per element) take an unrolled path; boundary rows
+// (Gauss-Legendre per element) a general one.
 #pragma once
 
 #include <cuda_runtime.h>
 
 #include <cstdint>
 
+#include "dd.cuh"
+
 namespace wq {
 
 struct RowsArgs {
   const int *off[3][2];
   const int *elem[3][2];
-  const void *V[3][2];     // folded tables, R, npts*(P+1)
-  const void *beta[3][2];  // cubic coefficient-spline values, R, npts*4
+  const void *V[3][2];     // folded tables in the arithmetic type R, npts*(P+1)
+  const void *beta[3][2];  // cubic coefficient-spline values in R, npts*4
   int n[3], N[3], nc[3];
   const double *coef;  // may be null: c = 1
-  void *M, *K;         // R band outputs
+  void *M, *K;         // band outputs, OutT<R> (double for R = double or dd)
   long long row_begin, row_end;
   const int *lines;  // line ids of this launch
   int nch, T;        // chunks per line and chunk length
@@ -41,11 +52,11 @@ struct RowsArgs {
 };
 
 // acc[o + i] += x * v[i], i = 0..P, with a compile-time register index in
-// each case (o is uniform across the warp by construction).
+// each case.
 template <int P, int O, typename R>
 __device__ __forceinline__ void fiber_at(R (&acc)[2 * P + 1], R x, const R *__restrict__ v) {
 #pragma unroll
-  for (int i = 0; i <= P; i++) acc[O + i] = fma(x, v[i], acc[O + i]);
+  for (int i = 0; i <= P; i++) acc[O + i] = r_fma(x, v[i], acc[O + i]);
 }
 
 template <int P, typename R>
@@ -60,52 +71,72 @@ __device__ __forceinline__ void fiber_add(R (&acc)[2 * P + 1], R x, const R *__r
   }
 }
 
-template <int P, int D, int LM, int NW, int TMAX, bool DO_M, bool DO_K, typename R>
+constexpr int kRowsWarps = 8;
+
+template <int P, int D, int LM, int TMAX, bool DO_M, bool DO_K, typename R>
 struct RowsLayout {
-  static constexpr int NP = P + 1;             // points per direction-1 block
+  static constexpr int NP = P + 1;             // points of a weighted Gaussian rule
   static constexpr int NB = 2 * P + 1;         // band width per direction
-  static constexpr int NG = (DO_M ? 1 : 0) + (DO_K ? D : 0);  // point grids
-  static constexpr int NCOMBO = DO_K ? D : 1;  // (kind2, kind3) combinations of the phase-A columns
-  static constexpr int NK3 = (D == 3) ? (DO_K ? 2 : 1) : 0;
+  static constexpr int NPAIR = (D == 3) ? NB * NB : NB;  // (j2, j3) fibres of a row
+  static constexpr int BAND = NPAIR * NB;
+  static constexpr int NSLOT = (NPAIR + 31) / 32;       // fibres per lane
+  static constexpr int LS = NPAIR;             // U's stride between coefficient columns
+  static constexpr int NU = DO_K ? 2 : 1;
+  static constexpr int NK3 = (D == 3) ? (DO_K ? 2 : 1) : 0;  // kinds in x3
+  static constexpr int NCOMBO = DO_K ? D : 1;  // (kind2, kind3) combinations
   static constexpr int NL1 = TMAX + P + 3;     // coefficient columns of a chunk
   static constexpr int NL = P + 4;             // coefficient indices of one row per direction
-  static constexpr int LM2 = (D == 3) ? LM * LM : LM;
+  static constexpr int NL3 = (D == 3) ? NL : 1;
+  static constexpr int NW = kRowsWarps;
+  static constexpr int NT = 32 * NW;
+  static constexpr int MAXPTS1 = TMAX * NP + P * NP * (P - 1);  // x1 points of a chunk's rows
+  // per-warp scratch: phase A's column work (Z/Cq, then T3) or phase B's band stage
+  static constexpr int WZ = (D == 3) ? NK3 * NL * LM : 0;
+  static constexpr int WC = (D == 3) ? NCOMBO * LM * NB : NCOMBO * LM;
+  static constexpr int WX = WZ > WC ? WZ : WC;
+  static constexpr int WT = (D == 3) ? NK3 * NL * NB : 0;
+  static constexpr int WA = WX + WT;
+  static constexpr int WB = 2 * BAND;
+  static constexpr int WS = WA > WB ? WA : WB;
   // R region
-  static constexpr int P23V = 2 * 2 * LM * NP;  // [dir2/3][kind][q][i]
-  static constexpr int P23B = 2 * 2 * LM * 4;
-  static constexpr int CQ = NCOMBO * NL1 * LM2;
-  static constexpr int CB = (D == 3 ? NL * NL : NL) * NL1;
-  static constexpr int ZS = (D == 3) ? NK3 * NL1 * NL * LM : 0;
-  static constexpr int PHASE_A = CB + ZS;
-  static constexpr int BUFA = (D == 3) ? NG * NP * (LM * LM > NB * NB ? LM * LM : NB * NB) : NG * NP * LM;
-  static constexpr int BUFB = (D == 3) ? NG * NP * LM * NB : NG * NP * NB;
-  static constexpr int BLK = 2 * NP * NP + 2 * NP * 4;
-  static constexpr int WARP = BLK + BUFA + BUFB;
-  static constexpr int UNION = (PHASE_A > NW * WARP) ? PHASE_A : NW * WARP;
-  static constexpr int R_TOTAL = P23V + P23B + CQ + UNION;
-  // int region
-  static constexpr int I_P23 = 2 * 2 * LM;  // elem, o per (dir2/3, q)
-  static constexpr int I_WARP = 2 * NP;     // elem, o per block point
-  static constexpr int I_TOTAL = I_P23 + NW * I_WARP;
+  static constexpr int V23 = 2 * 2 * LM * NP;  // [dir2/3][kind][q][i]
+  static constexpr int B23 = 2 * 2 * LM * 4;
+  static constexpr int V1 = 2 * MAXPTS1 * NP;  // [kind][point][i]
+  static constexpr int B1 = 2 * MAXPTS1 * 4;
+  static constexpr int CB = NL3 * NL * NL1;    // [l3][l2][l1]
+  static constexpr int US = NU * NL1 * LS;     // [u][l1][j3*NB+j2]
+  static constexpr int R_TOTAL = V23 + B23 + V1 + B1 + CB + US + NW * WS;
+  // int region: E23[2][LM], O23[2][LM], E1[MAXPTS1], OFF1[TMAX+1]
+  static constexpr int I_TOTAL = 4 * LM + MAXPTS1 + TMAX + 1;
   static constexpr size_t BYTES = sizeof(R) * (size_t)R_TOTAL + sizeof(int) * (size_t)I_TOTAL;
 };
 
-template <int P, int D, int LM, int NW, int TMAX, bool DO_M, bool DO_K, typename R>
-__global__ void __launch_bounds__(NW * 32) rows_kernel(const RowsArgs A) {
-  using L = RowsLayout<P, D, LM, NW, TMAX, DO_M, DO_K, R>;
-  constexpr int NP = L::NP, NB = L::NB, NG = L::NG;
-  constexpr int G_M = 0;
-  constexpr int G_K1 = DO_M ? 1 : 0, G_K2 = G_K1 + 1, G_K3 = G_K1 + 2;
+// Resident CTAs per SM the compiler is asked to allow (caps registers at
+// 65536 / (threads * minblocks)).
+#ifndef WQ_ROWS_MIN_BLOCKS
+#define WQ_ROWS_MIN_BLOCKS 2
+#endif
+
+template <int P, int D, int LM, int TMAX, bool DO_M, bool DO_K, typename R>
+__global__ void __launch_bounds__(32 * kRowsWarps, WQ_ROWS_MIN_BLOCKS) rows_kernel(const RowsArgs A) {
+  using L = RowsLayout<P, D, LM, TMAX, DO_M, DO_K, R>;
+  using O = typename OutT<R>::type;
+  static_assert(sizeof(O) == sizeof(R), "the band stage shares the R region");
+  constexpr int NP = L::NP, NB = L::NB, NT = L::NT, NW = L::NW, LS = L::LS, NL = L::NL, NL1 = L::NL1;
+  constexpr int NPAIR = L::NPAIR, BAND = L::BAND;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R *sR = reinterpret_cast<R *>(smem_raw);
-  int *sI = reinterpret_cast<int *>(smem_raw + sizeof(R) * (size_t)L::R_TOTAL);
-  R *sV23 = sR;                          // [di][kind][LM][NP]
-  R *sB23 = sV23 + L::P23V;              // [di][kind][LM][4]
-  R *sCq = sB23 + L::P23B;               // [combo][NL1][LM2]
-  R *sU = sCq + L::CQ;                   // union
-  int *sE23 = sI;                        // [di][LM]
-  int *sO23 = sI + 2 * LM;               // [di][LM]
+  R *sV23 = reinterpret_cast<R *>(smem_raw);  // [di][kind][LM][NP]
+  R *sB23 = sV23 + L::V23;                    // [di][kind][LM][4]
+  R *sV1 = sB23 + L::B23;                     // [kind][MAXPTS1][NP]
+  R *sB1 = sV1 + L::V1;                       // [kind][MAXPTS1][4]
+  R *sCb = sB1 + L::B1;                       // [l3][l2][l1]
+  R *sU = sCb + L::CB;                        // [u][NL1][LS]
+  R *sW = sU + L::US;                         // [warp][WS]
+  int *sE23 = reinterpret_cast<int *>(smem_raw + sizeof(R) * (size_t)L::R_TOTAL);  // [di][LM]
+  int *sO23 = sE23 + 2 * LM;                  // [di][LM]
+  int *sE1 = sO23 + 2 * LM;                   // [MAXPTS1]
+  int *sOff1 = sE1 + L::MAXPTS1;              // [TMAX+1]
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int line = A.lines[blockIdx.x / A.nch];
@@ -119,9 +150,9 @@ __global__ void __launch_bounds__(NW * 32) rows_kernel(const RowsArgs A) {
   if (lo < A.row_begin - base) lo = A.row_begin - base;
   if (hi > A.row_end - base) hi = A.row_end - base;
   if (lo >= hi) return;
-  const int a = (int)lo, b = (int)hi;
+  const int a = (int)lo, b = (int)hi, T = b - a;
 
-  // ---------------------------------------------------------------- phase A
+  // ------------------------------------------------ tables and the coefficient block
   const int rr[2] = {r2, r3};
   int L23[2] = {1, 1}, l23lo[2] = {0, 0}, nl23[2] = {1, 1};
 #pragma unroll
@@ -134,245 +165,294 @@ __global__ void __launch_bounds__(NW * 32) rows_kernel(const RowsArgs A) {
     const int ehi = r > A.N[dir] - 1 ? A.N[dir] - 1 : r;
     l23lo[di] = elo;
     nl23[di] = ehi - elo + 4;
-    for (int t = tid; t < 2 * L23[di]; t += NW * 32) {
-      const int kind = t / L23[di], q = t % L23[di];
-      const int gq = (kind ? off1 : off0) + q;
-      const R *Vg = static_cast<const R *>(A.V[dir][kind]);
-      const R *Bg = static_cast<const R *>(A.beta[dir][kind]);
+    for (int t = tid; t < 2 * LM; t += NT) {
+      const int kind = t / LM, q = t % LM;
+      if (q < L23[di]) {
+        const int gq = (kind ? off1 : off0) + q;
+        const R *Vg = static_cast<const R *>(A.V[dir][kind]);
+        const R *Bg = static_cast<const R *>(A.beta[dir][kind]);
 #pragma unroll
-      for (int i = 0; i < NP; i++) sV23[((di * 2 + kind) * LM + q) * NP + i] = Vg[(size_t)gq * NP + i];
+        for (int i = 0; i < NP; i++) sV23[((di * 2 + kind) * LM + q) * NP + i] = Vg[(size_t)gq * NP + i];
 #pragma unroll
-      for (int i = 0; i < 4; i++) sB23[((di * 2 + kind) * LM + q) * 4 + i] = Bg[(size_t)gq * 4 + i];
-      if (kind == 0) {
-        const int e = A.elem[dir][0][gq];
-        sE23[di * LM + q] = e;
-        sO23[di * LM + q] = e - r + P;
+        for (int i = 0; i < 4; i++) sB23[((di * 2 + kind) * LM + q) * 4 + i] = Bg[(size_t)gq * 4 + i];
+        if (kind == 0) {
+          const int e = A.elem[dir][0][gq];
+          sE23[di * LM + q] = e;
+          sO23[di * LM + q] = e - r + P;
+        }
       }
     }
+  }
+  // the chunk's x1 tables: rows [a, b) hold one contiguous range of points
+  const int p1lo = A.off[0][0][a], p1hi = A.off[0][0][b];
+  const int np1 = p1hi - p1lo;
+  for (int t = tid; t <= T; t += NT) sOff1[t] = A.off[0][0][a + t] - p1lo;
+  for (int t = tid; t < 2 * np1; t += NT) {
+    const int kind = t >= np1 ? 1 : 0, q = t - kind * np1;
+    const int gq = (kind ? A.off[0][1][a] : p1lo) + q;
+    const R *Vg = static_cast<const R *>(A.V[0][kind]);
+    const R *Bg = static_cast<const R *>(A.beta[0][kind]);
+#pragma unroll
+    for (int i = 0; i < NP; i++) sV1[(kind * L::MAXPTS1 + q) * NP + i] = Vg[(size_t)gq * NP + i];
+#pragma unroll
+    for (int i = 0; i < 4; i++) sB1[(kind * L::MAXPTS1 + q) * 4 + i] = Bg[(size_t)gq * 4 + i];
+    if (kind == 0) sE1[q] = A.elem[0][0][gq];
   }
   const int elo1 = a - P < 0 ? 0 : a - P;
   const int ehi1 = (b - 1) > A.N[0] - 1 ? A.N[0] - 1 : (b - 1);
   const int l1lo = elo1, nl1 = ehi1 - elo1 + 4;
   const int L2 = L23[0], L3 = L23[1];
   const int nl2 = nl23[0], nl3 = (D == 3) ? nl23[1] : 1;
-  R *sCb = sU;             // [l3'][l2'][l1'] (runtime strides nl2, nl1)
-  R *sZ = sU + L::CB;      // [k3][NL1][NL][LM]
   {
     unsigned bad = 0;
-    const int tot = nl3 * nl2 * nl1;
-    for (int t = tid; t < tot; t += NW * 32) {
-      const int l1 = t % nl1, l2 = (t / nl1) % nl2, l3 = t / (nl1 * nl2);
-      double v = 1.0;
-      if (A.coef) {
-        const long long g = (long long)(l1lo + l1) +
-                            (long long)A.nc[0] * ((long long)(l23lo[0] + l2) + (long long)A.nc[1] * (D == 3 ? (long long)(l23lo[1] + l3) : 0LL));
-        v = A.coef[g];
-        if (!isfinite(v)) bad = 1;
+    const double *cg = A.coef;
+    for (int t = tid; t < L::NL3 * NL * NL1; t += NT) {
+      const int l1 = t % NL1, l2 = (t / NL1) % NL, l3 = t / (NL1 * NL);
+      if (l1 < nl1 && l2 < nl2 && l3 < nl3) {
+        double v = 1.0;
+        if (cg) {
+          const long long g = (long long)(l1lo + l1) +
+                              (long long)A.nc[0] * ((long long)(l23lo[0] + l2) +
+                                                    (long long)A.nc[1] * (D == 3 ? (long long)(l23lo[1] + l3) : 0LL));
+          v = cg[g];
+          if (!isfinite(v)) bad = 1;
+        }
+        sCb[t] = r_from_double<R>(v);
       }
-      sCb[t] = (R)v;
     }
     bad = __reduce_or_sync(0xffffffffu, bad);
     if (bad && lane == 0) atomicOr(A.status, 2u);
   }
   __syncthreads();
-  if constexpr (D == 3) {
-    // Z[k3][l1][l2][q3] = sum_i Cb[e3(q3)+i-l3lo][l2][l1] * beta3[k3][q3][i]
-    const int tot = L::NK3 * nl1 * nl2 * L3;
-    for (int t = tid; t < tot; t += NW * 32) {
-      const int q3 = t % L3, l2 = (t / L3) % nl2, l1 = (t / (L3 * nl2)) % nl1, k3 = t / (L3 * nl2 * nl1);
-      const int e = sE23[LM + q3] - l23lo[1];
-      const R *bb = &sB23[((1 * 2 + k3) * LM + q3) * 4];
-      R s = 0;
+
+  // ------------------------------------------------ phase A: U, one warp per coefficient column
+  R *wx = sW + warp * L::WS;  // Z, later Cq
+  R *wt = wx + L::WX;         // T3
+  for (int l1 = warp; l1 < nl1; l1 += NW) {
+    if constexpr (D == 3) {
+      // Z[k3][l2][q3] = sum_i Cb[e3(q3)+i][l2][l1] * b3[k3][q3][i]
+      for (int t = lane; t < L::NK3 * NL * LM; t += 32) {
+        const int q3 = t % LM, l2 = (t / LM) % NL, k3 = t / (LM * NL);
+        if (q3 < L3 && l2 < nl2) {
+          const int e = sE23[LM + q3] - l23lo[1];
+          const R *bb = &sB23[((1 * 2 + k3) * LM + q3) * 4];
+          R s = r_zero<R>();
 #pragma unroll
-      for (int i = 0; i < 4; i++) s = fma(sCb[((e + i) * nl2 + l2) * nl1 + l1], bb[i], s);
-      sZ[((k3 * L::NL1 + l1) * L::NL + l2) * LM + q3] = s;
-    }
-    __syncthreads();
-    // Cq[c][l1][q2][q3]; combos: 0 = (M, M), 1 = (S, M), 2 = (M, S)
-    const int tot2 = L::NCOMBO * nl1 * L2 * L3;
-    for (int t = tid; t < tot2; t += NW * 32) {
-      const int q3 = t % L3, q2 = (t / L3) % L2, l1 = (t / (L3 * L2)) % nl1, c = t / (L3 * L2 * nl1);
-      const int k2 = (c == 1) ? 1 : 0, k3 = (c == 2) ? 1 : 0;
-      const int e = sE23[q2] - l23lo[0];
-      const R *bb = &sB23[((0 * 2 + k2) * LM + q2) * 4];
-      R s = 0;
+          for (int i = 0; i < 4; i++) s = r_fma(sCb[((e + i) * NL + l2) * NL1 + l1], bb[i], s);
+          wx[t] = s;
+        }
+      }
+      __syncwarp();
+      // T3[k3][l2][j3] = sum_q3 Z[k3][l2][q3] * V3[k3][q3][j3 - o3]
+      for (int t = lane; t < L::NK3 * NL; t += 32) {
+        const int l2 = t % NL, k3 = t / NL;
+        if (l2 < nl2) {
+          R acc[NB];
 #pragma unroll
-      for (int i = 0; i < 4; i++) s = fma(sZ[((k3 * L::NL1 + l1) * L::NL + e + i) * LM + q3], bb[i], s);
-      sCq[(c * L::NL1 + l1) * L::LM2 + q2 * LM + q3] = s;
-    }
-  } else {
-    // Cq[k2][l1][q2] = sum_i Cb[e2(q2)+i-l2lo][l1] * beta2[k2][q2][i]
-    const int tot2 = L::NCOMBO * nl1 * L2;
-    for (int t = tid; t < tot2; t += NW * 32) {
-      const int q2 = t % L2, l1 = (t / L2) % nl1, c = t / (L2 * nl1);
-      const int e = sE23[q2] - l23lo[0];
-      const R *bb = &sB23[((0 * 2 + c) * LM + q2) * 4];
-      R s = 0;
+          for (int j = 0; j < NB; j++) acc[j] = r_zero<R>();
+          for (int q3 = 0; q3 < L3; q3++)
+            fiber_add<P>(acc, wx[t * LM + q3], &sV23[((1 * 2 + k3) * LM + q3) * NP], sO23[LM + q3]);
 #pragma unroll
-      for (int i = 0; i < 4; i++) s = fma(sCb[(e + i) * nl1 + l1], bb[i], s);
-      sCq[(c * L::NL1 + l1) * L::LM2 + q2] = s;
+          for (int j = 0; j < NB; j++) wt[t * NB + j] = acc[j];
+        }
+      }
+      __syncwarp();
+      // Cq[c][q2][j3] = sum_i T3[k3(c)][e2(q2)+i][j3] * b2[k2(c)][q2][i]; c = (kind2, kind3):
+      // 0 = (M, M), 1 = (S, M), 2 = (M, S)
+      for (int t = lane; t < L::NCOMBO * LM * NB; t += 32) {
+        const int j3 = t % NB, q2 = (t / NB) % LM, c = t / (NB * LM);
+        if (q2 < L2) {
+          const int k2 = (c == 1) ? 1 : 0, k3 = (c == 2) ? 1 : 0;
+          const int e = sE23[q2] - l23lo[0];
+          const R *bb = &sB23[((0 * 2 + k2) * LM + q2) * 4];
+          R s = r_zero<R>();
+#pragma unroll
+          for (int i = 0; i < 4; i++) s = r_fma(wt[(k3 * NL + e + i) * NB + j3], bb[i], s);
+          wx[t] = s;
+        }
+      }
+      __syncwarp();
+      // U0[l1][j3*NB+j2] = sum_q2 Cq[MM][q2][j3] V2M[q2][j2-o2]
+      // U1[l1][j3*NB+j2] = sum_q2 Cq[SM][q2][j3] V2S[q2][..] + Cq[MS][q2][j3] V2M[q2][..]
+      for (int t = lane; t < L::NU * NB; t += 32) {
+        const int j3 = t % NB, u = t / NB;
+        R acc[NB];
+#pragma unroll
+        for (int j = 0; j < NB; j++) acc[j] = r_zero<R>();
+        for (int q2 = 0; q2 < L2; q2++) {
+          const int o = sO23[q2];
+          const R *vM = &sV23[((0 * 2 + 0) * LM + q2) * NP];
+          if (u == 0) {
+            fiber_add<P>(acc, wx[(0 * LM + q2) * NB + j3], vM, o);
+          } else {
+            fiber_add<P>(acc, wx[(1 * LM + q2) * NB + j3], &sV23[((0 * 2 + 1) * LM + q2) * NP], o);
+            fiber_add<P>(acc, wx[(2 * LM + q2) * NB + j3], vM, o);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < NB; j++) sU[(u * NL1 + l1) * LS + j3 * NB + j] = acc[j];
+      }
+    } else {
+      // Cq[k2][q2] = sum_i Cb[e2(q2)+i][l1] * b2[k2][q2][i]
+      for (int t = lane; t < L::NCOMBO * LM; t += 32) {
+        const int q2 = t % LM, c = t / LM;
+        if (q2 < L2) {
+          const int e = sE23[q2] - l23lo[0];
+          const R *bb = &sB23[((0 * 2 + c) * LM + q2) * 4];
+          R s = r_zero<R>();
+#pragma unroll
+          for (int i = 0; i < 4; i++) s = r_fma(sCb[(e + i) * NL1 + l1], bb[i], s);
+          wx[t] = s;
+        }
+      }
+      __syncwarp();
+      // U0[l1][j2] = sum_q2 Cq[M][q2] V2M[q2][..];  U1[l1][j2] = sum_q2 Cq[S][q2] V2S[q2][..]
+      if (lane < L::NU) {
+        const int u = lane;
+        R acc[NB];
+#pragma unroll
+        for (int j = 0; j < NB; j++) acc[j] = r_zero<R>();
+        for (int q2 = 0; q2 < L2; q2++)
+          fiber_add<P>(acc, wx[u * LM + q2], &sV23[((0 * 2 + u) * LM + q2) * NP], sO23[q2]);
+#pragma unroll
+        for (int j = 0; j < NB; j++) sU[(u * NL1 + l1) * LS + j] = acc[j];
+      }
     }
+    __syncwarp();
   }
   __syncthreads();
 
-  // ---------------------------------------------------------------- phase B
-  R *wR = sU + warp * L::WARP;
-  R *blkV = wR;                   // [kind][NP][NP]
-  R *blkB = blkV + 2 * NP * NP;   // [kind][NP][4]
-  R *bufA = blkB + 2 * NP * 4;
-  R *bufB = bufA + L::BUFA;
-  int *blkE = sI + L::I_P23 + warp * L::I_WARP;
-  int *blkO = blkE + NP;
-
-  const R *V1[2] = {static_cast<const R *>(A.V[0][0]), static_cast<const R *>(A.V[0][1])};
-  const R *B1[2] = {static_cast<const R *>(A.beta[0][0]), static_cast<const R *>(A.beta[0][1])};
-  constexpr int NPAIR = (D == 3) ? NB * NB : NB;
-  constexpr int NSLOT = (NPAIR + 31) / 32;
-
-  for (int r1 = a + warp; r1 < b; r1 += NW) {
-    const int offM = A.off[0][0][r1], offS = A.off[0][1][r1];
-    const int nblk = (A.off[0][0][r1 + 1] - offM) / NP;
-    R accM[NSLOT][NB], accK[NSLOT][NB];
+  // ------------------------------------------------ phase B: one warp per row
+  const R *U0 = sU;
+  const R *U1 = sU + NL1 * LS;
+  O *stM = reinterpret_cast<O *>(sW + warp * L::WS);  // [BAND]
+  O *stK = stM + BAND;
+  constexpr int QUNROLL = sizeof(R) == 4 ? NP : 1;  // keep double-float code compact
+  for (int rl = warp; rl < T; rl += NW) {
+    const int r1 = a + rl;
+    const int q0 = sOff1[rl], q1end = sOff1[rl + 1];
+    const R *bm0 = &sB1[(0 * L::MAXPTS1 + q0) * 4];
+    const R *bs0 = &sB1[(1 * L::MAXPTS1 + q0) * 4];
+    const R *vm0 = &sV1[(0 * L::MAXPTS1 + q0) * NP];
+    const R *vs0 = &sV1[(1 * L::MAXPTS1 + q0) * NP];
+    if (r1 >= P && r1 <= A.N[0] - 1) {
+      // weighted Gaussian rule in x1: point q in element r1-P+q, band offset q;
+      // sliding windows over the coefficient columns (w) and the entries j1 (acc)
+      const int kb = (r1 - P) - l1lo;
 #pragma unroll
-    for (int s = 0; s < NSLOT; s++)
-#pragma unroll
-      for (int j = 0; j < NB; j++) { accM[s][j] = 0; accK[s][j] = 0; }
-
-    for (int blk = 0; blk < nblk; blk++) {
-      __syncwarp();
-      for (int t = lane; t < 2 * NP; t += 32) {
-        const int kind = t / NP, qb = t % NP;
-        const int gq = (kind ? offS : offM) + blk * NP + qb;
-#pragma unroll
-        for (int i = 0; i < NP; i++) blkV[(kind * NP + qb) * NP + i] = V1[kind][(size_t)gq * NP + i];
-#pragma unroll
-        for (int i = 0; i < 4; i++) blkB[(kind * NP + qb) * 4 + i] = B1[kind][(size_t)gq * 4 + i];
-        if (kind == 0) {
-          const int e = A.elem[0][0][gq];
-          blkE[qb] = e - l1lo;
-          blkO[qb] = e - r1 + P;
-        }
-      }
-      __syncwarp();
-      if constexpr (D == 3) {
-        // C1: c[g][qb][q2][q3]
-        const int totc = NG * NP * L2 * L3;
-        for (int t = lane; t < totc; t += 32) {
-          const int q3 = t % L3, q2 = (t / L3) % L2, qb = (t / (L3 * L2)) % NP, g = t / (L3 * L2 * NP);
-          const int combo = (DO_K && g == G_K2) ? 1 : ((DO_K && g == G_K3) ? 2 : 0);
-          const int k1 = (DO_K && g == G_K1) ? 1 : 0;
-          const R *cq = &sCq[(combo * L::NL1 + blkE[qb]) * L::LM2 + q2 * LM + q3];
-          const R *bb = &blkB[(k1 * NP + qb) * 4];
-          R s = 0;
-#pragma unroll
-          for (int i = 0; i < 4; i++) s = fma(cq[i * L::LM2], bb[i], s);
-          bufA[((g * NP + qb) * LM + q2) * LM + q3] = s;
-        }
-        __syncwarp();
-        // X: contraction over q3 -> j3
-        const int totx = NG * NP * L2;
-        for (int t = lane; t < totx; t += 32) {
-          const int q2 = t % L2, qb = (t / L2) % NP, g = t / (L2 * NP);
-          const int k3 = (DO_K && g == G_K3) ? 1 : 0;
-          R acc[NB];
-#pragma unroll
-          for (int j = 0; j < NB; j++) acc[j] = 0;
-          const R *cin = &bufA[((g * NP + qb) * LM + q2) * LM];
-          for (int q3 = 0; q3 < L3; q3++)
-            fiber_add<P>(acc, cin[q3], &sV23[((1 * 2 + k3) * LM + q3) * NP], sO23[LM + q3]);
-          R *xo = &bufB[((g * NP + qb) * LM + q2) * NB];
-#pragma unroll
-          for (int j = 0; j < NB; j++) xo[j] = acc[j];
-        }
-        __syncwarp();
-        // Y: contraction over q2 -> j2; output pair index j3*NB + j2
-        const int toty = NG * NP * NB;
-        for (int t = lane; t < toty; t += 32) {
-          const int j3 = t % NB, qb = (t / NB) % NP, g = t / (NB * NP);
-          const int k2 = (DO_K && g == G_K2) ? 1 : 0;
-          R acc[NB];
-#pragma unroll
-          for (int j = 0; j < NB; j++) acc[j] = 0;
-          const R *xin = &bufB[((g * NP + qb) * LM) * NB + j3];
-          for (int q2 = 0; q2 < L2; q2++)
-            fiber_add<P>(acc, xin[q2 * NB], &sV23[((0 * 2 + k2) * LM + q2) * NP], sO23[q2]);
-          R *yo = &bufA[(g * NP + qb) * NB * NB + j3 * NB];
-#pragma unroll
-          for (int j = 0; j < NB; j++) yo[j] = acc[j];
-        }
-      } else {
-        // C1: c[g][qb][q2]
-        const int totc = NG * NP * L2;
-        for (int t = lane; t < totc; t += 32) {
-          const int q2 = t % L2, qb = (t / L2) % NP, g = t / (L2 * NP);
-          const int k2 = (DO_K && g == G_K2) ? 1 : 0;
-          const int k1 = (DO_K && g == G_K1) ? 1 : 0;
-          const R *cq = &sCq[(k2 * L::NL1 + blkE[qb]) * L::LM2 + q2];
-          const R *bb = &blkB[(k1 * NP + qb) * 4];
-          R s = 0;
-#pragma unroll
-          for (int i = 0; i < 4; i++) s = fma(cq[i * L::LM2], bb[i], s);
-          bufA[(g * NP + qb) * LM + q2] = s;
-        }
-        __syncwarp();
-        // Y: contraction over q2 -> j2
-        const int toty = NG * NP;
-        for (int t = lane; t < toty; t += 32) {
-          const int qb = t % NP, g = t / NP;
-          const int k2 = (DO_K && g == G_K2) ? 1 : 0;
-          R acc[NB];
-#pragma unroll
-          for (int j = 0; j < NB; j++) acc[j] = 0;
-          const R *cin = &bufA[(g * NP + qb) * LM];
-          for (int q2 = 0; q2 < L2; q2++)
-            fiber_add<P>(acc, cin[q2], &sV23[((0 * 2 + k2) * LM + q2) * NP], sO23[q2]);
-          R *yo = &bufB[(g * NP + qb) * NB];
-#pragma unroll
-          for (int j = 0; j < NB; j++) yo[j] = acc[j];
-        }
-      }
-      __syncwarp();
-      // F: contraction over q1 -> j1, accumulated per owned pair
-      const R *Y = (D == 3) ? bufA : bufB;
-      constexpr int YS = (D == 3) ? NB * NB : NB;  // stride of one (g, qb) slice
-#pragma unroll
-      for (int s = 0; s < NSLOT; s++) {
+      for (int s = 0; s < L::NSLOT; s++) {
         const int pr = lane + 32 * s;
         if (pr < NPAIR) {
+          R w0[4], w1[4], aM[NP], aK[NP];
 #pragma unroll
-          for (int qb = 0; qb < NP; qb++) {
-            const int o = blkO[qb];
-            const R *vM = &blkV[(0 * NP + qb) * NP];
-            if constexpr (DO_M) fiber_add<P>(accM[s], Y[(G_M * NP + qb) * YS + pr], vM, o);
-            if constexpr (DO_K) {
-              R y = Y[(G_K2 * NP + qb) * YS + pr];
-              if constexpr (D == 3) y += Y[(G_K3 * NP + qb) * YS + pr];
-              fiber_add<P>(accK[s], y, vM, o);
-              fiber_add<P>(accK[s], Y[(G_K1 * NP + qb) * YS + pr], &blkV[(1 * NP + qb) * NP], o);
+          for (int i = 0; i < 4; i++) {
+            w0[i] = U0[(kb + i) * LS + pr];
+            w1[i] = DO_K ? U1[(kb + i) * LS + pr] : r_zero<R>();
+          }
+#pragma unroll
+          for (int i = 0; i < NP; i++) { aM[i] = r_zero<R>(); aK[i] = r_zero<R>(); }
+#pragma unroll QUNROLL
+          for (int q = 0; q < NP; q++) {
+            R bm[4], vm[NP];
+#pragma unroll
+            for (int i = 0; i < 4; i++) bm[i] = bm0[q * 4 + i];
+#pragma unroll
+            for (int i = 0; i < NP; i++) vm[i] = vm0[q * NP + i];
+            if constexpr (DO_M) {
+              R y = r_zero<R>();
+#pragma unroll
+              for (int i = 0; i < 4; i++) y = r_fma(bm[i], w0[i], y);
+#pragma unroll
+              for (int i = 0; i < NP; i++) aM[i] = r_fma(vm[i], y, aM[i]);
             }
+            if constexpr (DO_K) {
+              R bs[4], vs[NP];
+#pragma unroll
+              for (int i = 0; i < 4; i++) bs[i] = bs0[q * 4 + i];
+#pragma unroll
+              for (int i = 0; i < NP; i++) vs[i] = vs0[q * NP + i];
+              R yk = r_zero<R>(), ys = r_zero<R>();
+#pragma unroll
+              for (int i = 0; i < 4; i++) {
+                yk = r_fma(bm[i], w1[i], yk);
+                ys = r_fma(bs[i], w0[i], ys);
+              }
+#pragma unroll
+              for (int i = 0; i < NP; i++) aK[i] = r_fma(vs[i], ys, r_fma(vm[i], yk, aK[i]));
+            }
+            // entry j1 = q is complete
+            if constexpr (DO_M) stM[pr * NB + q] = r_out(aM[0]);
+            if constexpr (DO_K) stK[pr * NB + q] = r_out(aK[0]);
+#pragma unroll
+            for (int i = 0; i < NP - 1; i++) { aM[i] = aM[i + 1]; aK[i] = aK[i + 1]; }
+            aM[NP - 1] = r_zero<R>();
+            aK[NP - 1] = r_zero<R>();
+#pragma unroll
+            for (int i = 0; i < 3; i++) { w0[i] = w0[i + 1]; w1[i] = w1[i + 1]; }
+            if (q < P) {
+              w0[3] = U0[(kb + q + 4) * LS + pr];
+              if constexpr (DO_K) w1[3] = U1[(kb + q + 4) * LS + pr];
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < P; i++) {
+            if constexpr (DO_M) stM[pr * NB + NP + i] = r_out(aM[i]);
+            if constexpr (DO_K) stK[pr * NB + NP + i] = r_out(aK[i]);
+          }
+        }
+      }
+    } else {
+      // Gauss-Legendre on each element of supp B_r1: any number of points
+#pragma unroll
+      for (int s = 0; s < L::NSLOT; s++) {
+        const int pr = lane + 32 * s;
+        if (pr < NPAIR) {
+          R accM[NB], accK[NB];
+#pragma unroll
+          for (int j = 0; j < NB; j++) { accM[j] = r_zero<R>(); accK[j] = r_zero<R>(); }
+          for (int q = q0; q < q1end; q++) {
+            const int e = sE1[q];
+            const int k0 = e - l1lo, o = e - r1 + P;
+            const R *bm = &sB1[(0 * L::MAXPTS1 + q) * 4];
+            const R *vm = &sV1[(0 * L::MAXPTS1 + q) * NP];
+            if constexpr (DO_M) {
+              R y = r_zero<R>();
+#pragma unroll
+              for (int i = 0; i < 4; i++) y = r_fma(bm[i], U0[(k0 + i) * LS + pr], y);
+              fiber_add<P>(accM, y, vm, o);
+            }
+            if constexpr (DO_K) {
+              const R *bs = &sB1[(1 * L::MAXPTS1 + q) * 4];
+              R yk = r_zero<R>(), ys = r_zero<R>();
+#pragma unroll
+              for (int i = 0; i < 4; i++) {
+                yk = r_fma(bm[i], U1[(k0 + i) * LS + pr], yk);
+                ys = r_fma(bs[i], U0[(k0 + i) * LS + pr], ys);
+              }
+              fiber_add<P>(accK, yk, vm, o);
+              fiber_add<P>(accK, ys, &sV1[(1 * L::MAXPTS1 + q) * NP], o);
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < NB; j++) {
+            if constexpr (DO_M) stM[pr * NB + j] = r_out(accM[j]);
+            if constexpr (DO_K) stK[pr * NB + j] = r_out(accK[j]);
           }
         }
       }
     }
-    // write the row's band: entry pair*NB + j1
-    const long long orow = base + r1 - A.row_begin;
-    constexpr int BAND = (D == 3) ? NB * NB * NB : NB * NB;
-#pragma unroll
-    for (int s = 0; s < NSLOT; s++) {
-      const int pr = lane + 32 * s;
-      if (pr < NPAIR) {
-        if constexpr (DO_M) {
-          R *out = static_cast<R *>(A.M) + orow * BAND + pr * NB;
-#pragma unroll
-          for (int j = 0; j < NB; j++) out[j] = accM[s][j];
-        }
-        if constexpr (DO_K) {
-          R *out = static_cast<R *>(A.K) + orow * BAND + pr * NB;
-#pragma unroll
-          for (int j = 0; j < NB; j++) out[j] = accK[s][j];
-        }
-      }
+    __syncwarp();
+    // the row's band is contiguous in the output: consecutive lanes, consecutive addresses
+    const long long orow = (base + r1 - A.row_begin) * BAND;
+    if constexpr (DO_M) {
+      O *gM = static_cast<O *>(A.M) + orow;
+      for (int i = lane; i < BAND; i += 32) gM[i] = stM[i];
     }
+    if constexpr (DO_K) {
+      O *gK = static_cast<O *>(A.K) + orow;
+      for (int i = lane; i < BAND; i += 32) gK[i] = stK[i];
+    }
+    __syncwarp();
   }
 }
 

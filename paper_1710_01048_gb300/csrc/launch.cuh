@@ -1,20 +1,26 @@
 // Dispatch from runtime (dimension, terms, line class) to the row-kernel
-// instantiations.  Interior lines (rows whose inner-direction rules have
-// P+1 points) run 8 warps per CTA and chunks of up to 16 rows; boundary lines
-// (up to P(P+1) points per inner direction) run 4 warps and chunks of 8.
+// instantiations.  Interior lines (inner-direction rules with P+1 points)
+// run chunks of up to kInteriorChunk rows; boundary lines (up to P(P+1)
+// points per inner direction) chunks of up to kBoundaryChunk rows.  Each CTA
+// has (2P+1) threads per row of its chunk.
 #pragma once
 
 #include "assemble.cuh"
 
 namespace wq {
 
-constexpr int kInteriorWarps = 8, kInteriorChunk = 16;
-constexpr int kBoundaryWarps = 4, kBoundaryChunk = 8;
+constexpr int kInteriorChunk = 24;
+constexpr int kBoundaryChunk = 16;
 
-template <int P, int D, int LM, int NW, int TMAX, bool DO_M, bool DO_K, typename R>
+// Upper bound on the x1 points of one chunk's rows that the kernel's shared
+// memory holds (checked by the host against the actual tables).
+constexpr int chunk_points_bound(int p, int tmax) { return tmax * (p + 1) + p * (p + 1) * (p - 1); }
+
+template <int P, int D, int LM, int TMAX, bool DO_M, bool DO_K, typename R>
 cudaError_t launch_one(const RowsArgs &a, int nblocks, cudaStream_t s) {
-  using L = RowsLayout<P, D, LM, NW, TMAX, DO_M, DO_K, R>;
-  auto kern = rows_kernel<P, D, LM, NW, TMAX, DO_M, DO_K, R>;
+  using L = RowsLayout<P, D, LM, TMAX, DO_M, DO_K, R>;
+  static_assert(L::MAXPTS1 == chunk_points_bound(P, TMAX), "chunk bound");
+  auto kern = rows_kernel<P, D, LM, TMAX, DO_M, DO_K, R>;
   static bool configured = false;  // one attribute call per instantiation and process
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
@@ -22,14 +28,14 @@ cudaError_t launch_one(const RowsArgs &a, int nblocks, cudaStream_t s) {
     configured = true;
   }
   if (nblocks <= 0) return cudaSuccess;
-  kern<<<nblocks, NW * 32, L::BYTES, s>>>(a);
+  kern<<<nblocks, L::NT, L::BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int P, int D, bool DO_M, bool DO_K, typename R>
 cudaError_t launch_class(int cls, const RowsArgs &a, int nblocks, cudaStream_t s) {
-  if (cls == 0) return launch_one<P, D, P + 1, kInteriorWarps, kInteriorChunk, DO_M, DO_K, R>(a, nblocks, s);
-  return launch_one<P, D, P *(P + 1), kBoundaryWarps, kBoundaryChunk, DO_M, DO_K, R>(a, nblocks, s);
+  if (cls == 0) return launch_one<P, D, P + 1, kInteriorChunk, DO_M, DO_K, R>(a, nblocks, s);
+  return launch_one<P, D, P *(P + 1), kBoundaryChunk, DO_M, DO_K, R>(a, nblocks, s);
 }
 
 template <int P, typename R>
@@ -44,22 +50,11 @@ cudaError_t launch_rows(int D, bool do_m, bool do_k, int cls, const RowsArgs &a,
   return launch_class<P, 3, false, true, R>(cls, a, nblocks, s);
 }
 
-// Maximum dynamic shared memory any instantiation of this (P, R) needs.
-template <int P, typename R>
-constexpr size_t max_rows_smem() {
-  size_t m = 0;
-  size_t v[] = {
-      RowsLayout<P, 3, P *(P + 1), kBoundaryWarps, kBoundaryChunk, true, true, R>::BYTES,
-      RowsLayout<P, 3, P + 1, kInteriorWarps, kInteriorChunk, true, true, R>::BYTES,
-      RowsLayout<P, 2, P *(P + 1), kBoundaryWarps, kBoundaryChunk, true, true, R>::BYTES,
-      RowsLayout<P, 2, P + 1, kInteriorWarps, kInteriorChunk, true, true, R>::BYTES};
-  for (size_t x : v) m = x > m ? x : m;
-  return m;
-}
-
 extern template cudaError_t launch_rows<2, double>(int, bool, bool, int, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_rows<3, double>(int, bool, bool, int, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_rows<2, float>(int, bool, bool, int, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_rows<3, float>(int, bool, bool, int, const RowsArgs &, int, cudaStream_t);
+extern template cudaError_t launch_rows<2, dd>(int, bool, bool, int, const RowsArgs &, int, cudaStream_t);
+extern template cudaError_t launch_rows<3, dd>(int, bool, bool, int, const RowsArgs &, int, cudaStream_t);
 
 }  // namespace wq

@@ -232,6 +232,7 @@ extern "C" wq_status wq_assemble_noalloc(const wq_rules *R, const double *const 
     const int nl = (int)(hi - lo);
     if (nl <= 0) continue;
     const int tmax = cls == 0 ? wq::kInteriorChunk : wq::kBoundaryChunk;
+    if (R->max_chunk_points[cls] > wq::chunk_points_bound(R->p, tmax)) return WQ_ERR_UNSUPPORTED;
     ra.nch = (n1 + tmax - 1) / tmax;
     ra.T = (n1 + ra.nch - 1) / ra.nch;
     ra.lines = reinterpret_cast<const int *>(base + (cls == 0 ? L.lines_in : L.lines_bd)) + (lo - lines.begin());

@@ -361,6 +361,16 @@ wq_status build_host_tables(wq_rules *R) {
       H.off[n] = (int)H.elem.size();
     }
   }
+  // the most x1 points any chunk of `t` consecutive rows holds (chunks start at
+  // multiples of t, as the assembly launches cut them)
+  for (int cls = 0; cls < 2; cls++) {
+    const int t = R->chunk_rows[cls];
+    const std::vector<int> &off = R->host[0][0].off;
+    const int n1 = R->n[0], nch = (n1 + t - 1) / t, tt = (n1 + nch - 1) / nch;
+    int mx = 0;
+    for (int c = 0; c * tt < n1; c++) mx = std::max(mx, off[std::min(n1, (c + 1) * tt)] - off[c * tt]);
+    R->max_chunk_points[cls] = mx;
+  }
   // lines: D=3 -> (r2, r3), D=2 -> r2; interior when dirs 2..D are interior rows
   R->lines = Lines();
   int nl = R->dim == 3 ? R->n[1] * R->n[2] : R->n[1];

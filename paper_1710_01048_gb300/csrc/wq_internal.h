@@ -1,6 +1,8 @@
 // Internal data structures of libwq (not part of the C ABI).
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstdint>
 #include <vector>
 
@@ -43,6 +45,8 @@ struct DevDirKind {
   double *v64;  // folded tables, npts*(p+1): W*|J| B (mass), W/|J| B' (stiffness)
   float *v32;   // the same rounded to float
   float *beta32;
+  float2 *vdd;     // the folded tables as double-float pairs (hi, lo)
+  float2 *betadd;  // the cubic values as double-float pairs
   int npts;
 };
 
@@ -62,6 +66,8 @@ struct wq_rules {
   double omega[2][wq::kMaxP + 1] = {};
   wq::HostDirKind host[3][2];
   wq::Lines lines;
+  int chunk_rows[2] = {1, 1};        // chunk length limits of the two line classes
+  int max_chunk_points[2] = {0, 0};  // most x1 points in one chunk, per class
   // device side
   bool on_device = false;
   int device = -1;

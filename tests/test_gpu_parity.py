@@ -1,7 +1,8 @@
 """Parity of the CUDA path (through the C-ABI) with the FP64 oracle.
 
-FP64 mode: max-entry and Frobenius relative errors <= 1e-12 per matrix (the
-target the method's FP64 path is held to).  Mixed mode: <= 1e-6.  Sizes span
+FP64 mode and the double-float mode (df64, FP64 output): max-entry and
+Frobenius relative errors <= 1e-12 per matrix (the target the method's FP64
+path is held to).  Mixed mode: <= 1e-6.  Sizes span
 several row chunks per line, both line classes (interior / boundary) and
 ragged chunk tails; tiny meshes make every row a boundary row.  At the
 benchmark size the comparison runs on sampled row ranges, plus invariants
@@ -41,63 +42,68 @@ def check(A, O, tol, what):
     return em, ef
 
 
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
 @pytest.mark.parametrize("coef", ["sincos", "one"])
-def test_2d_cubic_32x32(coef):
+def test_2d_cubic_32x32(coef, prec):
     p, nel = 3, (32, 32)
     g, c = inputs.make(2, p, nel, 0.0, coef)
-    M, K = gpu_assemble(2, p, nel, g, c)
+    M, K = gpu_assemble(2, p, nel, g, c, prec)
     Mo, Ko, _ = oracle.assemble(2, p, nel, g, c)
     check(M, Mo, FP64_TOL, "M")
     check(K, Ko, FP64_TOL, "K")
 
 
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
 @pytest.mark.parametrize("p", [2, 3])
 @pytest.mark.parametrize("nel", [(20, 7, 6), (9, 11, 8), (37, 5, 5)])
-def test_3d_full_parity(p, nel):
+def test_3d_full_parity(p, nel, prec):
     g, c = inputs.make(3, p, nel, 0.05, "exp", 0.1, seed=3)
-    M, K = gpu_assemble(3, p, nel, g, c)
+    M, K = gpu_assemble(3, p, nel, g, c, prec)
     Mo, Ko, off = oracle.assemble(3, p, nel, g, c)
     assert off < 1e-13
     check(M, Mo, FP64_TOL, "M")
     check(K, Ko, FP64_TOL, "K")
 
 
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
 @pytest.mark.parametrize("p", [2, 3])
 @pytest.mark.parametrize("nel", [(1, 1, 1), (2, 1, 3), (3, 3, 3), (1, 4, 2), (4, 4, 1)])
-def test_tiny_meshes_all_boundary(p, nel):
+def test_tiny_meshes_all_boundary(p, nel, prec):
     g, c = inputs.make(3, p, nel, 0.03, "exp", 0.2, seed=1)
-    M, K = gpu_assemble(3, p, nel, g, c)
+    M, K = gpu_assemble(3, p, nel, g, c, prec)
     Mo, Ko, _ = oracle.assemble(3, p, nel, g, c)
     check(M, Mo, FP64_TOL, "M")
     check(K, Ko, FP64_TOL, "K")
 
 
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
 @pytest.mark.parametrize("p", [2, 3])
-def test_2d_meshes(p):
+def test_2d_meshes(p, prec):
     for nel in [(1, 1), (5, 2), (40, 13)]:
         g, c = inputs.make(2, p, nel, 0.04, "exp", 0.1, seed=2)
-        M, K = gpu_assemble(2, p, nel, g, c)
+        M, K = gpu_assemble(2, p, nel, g, c, prec)
         Mo, Ko, _ = oracle.assemble(2, p, nel, g, c)
         check(M, Mo, FP64_TOL, f"M {nel}")
         check(K, Ko, FP64_TOL, f"K {nel}")
 
 
-def test_row_ranges_and_single_matrices():
+@pytest.mark.parametrize("prec", ["fp64", "df64", "mixed"])
+def test_row_ranges_and_single_matrices(prec):
     p, nel = 3, (23, 9, 7)
     g, c = inputs.make(3, p, nel, 0.05, "exp", 0.1, seed=4)
-    Mf, Kf = gpu_assemble(3, p, nel, g, c)
+    Mf, Kf = gpu_assemble(3, p, nel, g, c, prec)
     rows = Mf.shape[0]
     rng = np.random.default_rng(0)
     for _ in range(6):
         rb = int(rng.integers(0, rows))
         re = int(rng.integers(rb, rows + 1))
-        M, K = gpu_assemble(3, p, nel, g, c, rb=rb, re=re)
+        M, K = gpu_assemble(3, p, nel, g, c, prec, rb=rb, re=re)
         assert np.array_equal(M, Mf[rb:re]) and np.array_equal(K, Kf[rb:re])
-    M, _ = gpu_assemble(3, p, nel, g, c, stiffness=False)
-    _, K = gpu_assemble(3, p, nel, g, c, mass=False)
+    M, _ = gpu_assemble(3, p, nel, g, c, prec, stiffness=False)
+    _, K = gpu_assemble(3, p, nel, g, c, prec, mass=False)
     assert np.array_equal(M, Mf) and np.array_equal(K, Kf)
     # empty range
-    M, K = gpu_assemble(3, p, nel, g, c, rb=10, re=10)
+    M, K = gpu_assemble(3, p, nel, g, c, prec, rb=10, re=10)
     assert M.shape[0] == 0 and K.shape[0] == 0
 
 
@@ -110,14 +116,15 @@ def test_constant_coefficient_null_pointer():
     check(K, Ko, FP64_TOL, "K")
 
 
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
 @pytest.mark.parametrize("name", ["3d_p3_64", "3d_p2_64"])
-def test_benchmark_size_sampled(name):
+def test_benchmark_size_sampled(name, prec):
     w, g, c = inputs.workload(name)
     p, nel = w["p"], w["nel"]
     R = wq.Rules(3, p, nel)
     gd = [torch.from_numpy(x).cuda() for x in g]
     cd = torch.from_numpy(c).cuda()
-    M, K = wq.assemble(R, gd, cd, "fp64")
+    M, K = wq.assemble(R, gd, cd, prec)
     rows = R.rows
     n1 = nel[0] + p
     n12 = n1 * (nel[1] + p)
