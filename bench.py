@@ -1,13 +1,16 @@
 """Benchmark: 3D cubic weighted-Gaussian mass+stiffness assembly, nnz/s.
 
-One step = one fused mass+stiffness assembly (geometry-factor fold and the
-row kernels, all rows) of the named synthetic workload through the C-ABI.
-Default workload: 64^3 elements, C2 cubic (p = 3), separable map
+One step = one fused mass+stiffness assembly (coefficient check, geometry
+fold and the row kernels, all rows) of the named synthetic workload through
+the C-ABI.  Default workload: 64^3 elements, C2 cubic (p = 3), separable map
 xhat + 0.05 sin(pi xhat) per coordinate, c = exp(0.3 (x+y+z)) with
-lognormal(0.1) noise as a cubic spline on the same mesh, FP64 throughout.
+lognormal(0.1) noise as a cubic spline on the same mesh, FP64-accurate bands
+(double output, <= 1e-12 relative to the FP64 oracle) computed in
+double-float arithmetic on the FP32 pipe (--prec df64).  The plain FP64 form
+and the FP32 mixed mode are timed beside it ("variants").
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload 3d_p3_64] [--prec fp64|mixed] [--no-cpu-baseline]
+                    [--workload 3d_p3_64] [--prec df64|fp64|mixed] [--no-cpu-baseline]
 
 Prints one JSON line.  value = assembled non-zeros (M and K) per second over
 all ranks, device time (CUDA events around each step on the launching
@@ -192,7 +195,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="3d_p3_64")
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "df64", "mixed"])
+    ap.add_argument("--prec", default="df64", choices=["fp64", "df64", "mixed"])
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-stride", type=int, default=8)
     args = ap.parse_args()
@@ -261,7 +265,40 @@ def main():
     st = wq.wq_status_check(R.handle, wq._stream_handle(stream))
     if st != wq.WQ_OK:
         raise wq.WqError(st, "timed steps")
-    gpu_launches = 3 * args.steps  # fold + interior-line rows + boundary-line rows per step
+    # coefficient check/convert + fold + interior-line rows + boundary-line rows per step
+    gpu_launches = 4 * args.steps
+
+    # the other precisions on the same workload, a few steps each
+    variants = {}
+    if not args.no_variants:
+        for vp in ("fp64", "df64", "mixed"):
+            if vp == args.prec:
+                continue
+            vdt = torch.float32 if vp == "mixed" else torch.float64
+            Mv = torch.empty((rows, band), dtype=vdt, device="cuda")
+            Kv = torch.empty((rows, band), dtype=vdt, device="cuda")
+            for _ in range(3):
+                wq.assemble(R, gd, cd, vp, out=(Mv, Kv), stream=stream, check=False)
+            vms = []
+            for _ in range(max(3, min(args.steps, 10))):
+                flush.fill_(1)
+                v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                v0.record(stream)
+                wq.assemble(R, gd, cd, vp, out=(Mv, Kv), stream=stream, check=False)
+                v1.record(stream)
+                vms.append((v0, v1))
+            torch.cuda.synchronize()
+            vm = float(np.mean([x.elapsed_time(y) for x, y in vms]))
+            ev = {"ms_per_step": vm, "value": world * nnz_step / (vm * 1e-3), "unit": "nnz/s",
+                  "dtype": {"fp64": "f64", "df64": "f32x2", "mixed": "f32"}[vp]}
+            if vp == "mixed":
+                # accuracy of the FP32 bands against this run's FP64-accurate bands
+                ev["max_rel_err_vs_fp64_bands"] = max(
+                    float(((Mv.double() - M.double()).abs().max() / M.double().abs().max()).item()),
+                    float(((Kv.double() - K.double()).abs().max() / K.double().abs().max()).item()))
+            variants[vp] = ev
+            del Mv, Kv
+        torch.cuda.empty_cache()
 
     # end to end through host buffers: pinned inputs H2D, both bands D2H
     gh = [torch.from_numpy(x).pin_memory() for x in g]
@@ -335,7 +372,8 @@ def main():
                             f"{2 * rows * band * M.element_size() / 1e9:.2f} GB of band output"},
            "roofline": roof,
            "e2e": {"value": e2e_value, "unit": "nnz/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-           "clocks": clocks, "gpu_launches": gpu_launches, "ms_per_step_min": float(np.min(ms))}
+           "clocks": clocks, "gpu_launches": gpu_launches, "ms_per_step_min": float(np.min(ms)),
+           "variants": variants}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, outs = run_cpu_baseline(w, g, c, args.cpu_stride, max_slabs=None)

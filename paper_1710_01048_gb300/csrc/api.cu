@@ -66,6 +66,26 @@ __global__ void fold_kernel(const FoldArgs A) {
   if ((threadIdx.x & 31) == 0 && bits) atomicOr(A.status, bits);
 }
 
+// Checks the coefficients for NaN/Inf and writes them in the arithmetic type
+// of the call (float for the mixed mode, double-float pairs for df64; the
+// FP64 mode reads the caller's array directly).
+__global__ void coef_prepare_kernel(const double *__restrict__ c, size_t n, int prec, float *c32, float2 *cdd,
+                                    unsigned *status) {
+  unsigned bad = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double v = c[i];
+    if (!isfinite(v)) bad = 1;
+    if (prec == WQ_MIXED) {
+      c32[i] = (float)v;
+    } else if (prec == WQ_DF64) {
+      const float h = (float)v;
+      cdd[i] = make_float2(h, (float)(v - (double)h));
+    }
+  }
+  bad = __reduce_or_sync(0xffffffffu, bad);
+  if (bad && (threadIdx.x & 31) == 0) atomicOr(status, wq::kBitNonFinite);
+}
+
 wq_status upload(wq_rules *R) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return WQ_ERR_CUDA;
@@ -92,6 +112,11 @@ wq_status upload(wq_rules *R) {
   total += align_up(R->lines.boundary.size() * sizeof(int) + sizeof(int));
   size_t status_off = total;
   total += align_up(sizeof(unsigned));
+  const size_t ncoef = (size_t)R->nc[0] * R->nc[1] * R->nc[2];
+  size_t coef32_off = total;
+  total += align_up(ncoef * sizeof(float));
+  size_t coefdd_off = total;
+  total += align_up(ncoef * sizeof(float2));
 
   void *block = nullptr;
   cudaError_t e = cudaMalloc(&block, total);
@@ -146,6 +171,8 @@ wq_status upload(wq_rules *R) {
   R->dev_lines_interior = reinterpret_cast<const int *>(base + lines_int);
   R->dev_lines_boundary = reinterpret_cast<const int *>(base + lines_bnd);
   R->dev_status = reinterpret_cast<unsigned *>(base + status_off);
+  R->dev_coef32 = reinterpret_cast<float *>(base + coef32_off);
+  R->dev_coefdd = reinterpret_cast<float2 *>(base + coefdd_off);
   R->dev_block = block;
   R->dev_bytes = total;
   R->device = dev;
@@ -221,6 +248,14 @@ wq_status assemble(const wq_rules *R, const double *const *geom, const double *c
     ra.nc[a] = R->nc[a];
   }
   ra.coef = coef;
+  if (coef) {
+    const size_t ncoef = (size_t)R->nc[0] * R->nc[1] * R->nc[2];
+    const int blocks = (int)std::min<size_t>((ncoef + 255) / 256, 152 * 8);
+    coef_prepare_kernel<<<blocks, 256, 0, s>>>(coef, ncoef, prec, R->dev_coef32, R->dev_coefdd, R->dev_status);
+    if (cudaGetLastError() != cudaSuccess) return WQ_ERR_CUDA;
+    ra.coefR = prec == WQ_FP64 ? (const void *)coef
+               : prec == WQ_MIXED ? (const void *)R->dev_coef32 : (const void *)R->dev_coefdd;
+  }
   ra.M = M;
   ra.K = K;
   ra.row_begin = rb;

@@ -32,6 +32,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "dd.cuh"
 
@@ -44,6 +45,7 @@ struct RowsArgs {
   const void *beta[3][2];  // cubic coefficient-spline values in R, npts*4
   int n[3], N[3], nc[3];
   const double *coef;  // may be null: c = 1
+  const void *coefR;   // the same already in the arithmetic type R (and checked), or null
   void *M, *K;         // band outputs, OutT<R> (double for R = double or dd)
   long long row_begin, row_end;
   const int *lines;  // line ids of this launch
@@ -73,6 +75,30 @@ __device__ __forceinline__ void fiber_add(R (&acc)[2 * P + 1], R x, const R *__r
 
 constexpr int kRowsWarps = 8;
 
+// acc[j] += x * vd[j] over the whole band width, vd zero outside the point's
+// P+1 columns (used where the band offset varies from point to point).
+template <int NB, typename R>
+__device__ __forceinline__ void fiber_dense(R (&acc)[NB], R x, const R *__restrict__ vd) {
+#pragma unroll
+  for (int j = 0; j < NB; j++) acc[j] = r_fma(x, vd[j], acc[j]);
+}
+
+// One point's update of a band fibre whose offset o varies from point to
+// point: for double, P+1 multiply-adds through a switch on o (the FP64 pipe
+// is the bound); for float and double-float, the dense NB-wide form (a
+// little more arithmetic, no branching or code replication).
+template <int P, typename R>
+__device__ __forceinline__ void fiber_point(R (&acc)[2 * P + 1], R x, const R *__restrict__ v,
+                                            const R *__restrict__ vd, int o) {
+  if constexpr (sizeof(R) == 8 && !std::is_same<R, dd>::value) fiber_add<P>(acc, x, v, o);
+  else fiber_dense<2 * P + 1>(acc, x, vd);
+}
+
+// Rounds a region size up to whole 16-byte units of R.
+template <typename R> constexpr int pad16(int n) {
+  return (n * (int)sizeof(R) + 15) / 16 * 16 / (int)sizeof(R);
+}
+
 template <int P, int D, int LM, int TMAX, bool DO_M, bool DO_K, typename R>
 struct RowsLayout {
   static constexpr int NP = P + 1;             // points of a weighted Gaussian rule
@@ -97,28 +123,36 @@ struct RowsLayout {
   static constexpr int WT = (D == 3) ? NK3 * NL * NB : 0;
   static constexpr int WA = WX + WT;
   static constexpr int WB = 2 * BAND;
-  static constexpr int WS = WA > WB ? WA : WB;
+  static constexpr int WS = pad16<R>(WA > WB ? WA : WB);
   // R region
-  static constexpr int V23 = 2 * 2 * LM * NP;  // [dir2/3][kind][q][i]
-  static constexpr int B23 = 2 * 2 * LM * 4;
-  static constexpr int V1 = 2 * MAXPTS1 * NP;  // [kind][point][i]
-  static constexpr int B1 = 2 * MAXPTS1 * 4;
-  static constexpr int CB = NL3 * NL * NL1;    // [l3][l2][l1]
-  static constexpr int US = NU * NL1 * LS;     // [u][l1][j3*NB+j2]
-  static constexpr int R_TOTAL = V23 + B23 + V1 + B1 + CB + US + NW * WS;
+  static constexpr bool INNER_GAUSS = (LM == P + 1);  // interior line: o = q in x2, x3
+  // every region is a whole number of 16-byte units, so 4-wide float rows stay aligned
+  static constexpr int V23 = pad16<R>(2 * 2 * LM * NP);  // [dir2/3][kind][q][i]
+  static constexpr int V23D = INNER_GAUSS ? 0 : pad16<R>(2 * 2 * LM * NB);  // zero-padded [..][q][j]
+  static constexpr int B23 = pad16<R>(2 * 2 * LM * 4);
+  static constexpr int V1 = pad16<R>(2 * MAXPTS1 * NP);  // [kind][point][i]
+  static constexpr int V1D = pad16<R>(2 * MAXPTS1 * NB);  // zero-padded [kind][point][j]
+  static constexpr int B1 = pad16<R>(2 * MAXPTS1 * 4);
+  static constexpr int CB = pad16<R>(NL3 * NL * NL1);    // [l3][l2][l1]
+  static constexpr int US = pad16<R>(NU * NL1 * LS);     // [u][l1][j3*NB+j2]
+  static constexpr int R_TOTAL = V23 + V23D + B23 + V1 + V1D + B1 + CB + US + NW * WS;
   // int region: E23[2][LM], O23[2][LM], E1[MAXPTS1], OFF1[TMAX+1]
   static constexpr int I_TOTAL = 4 * LM + MAXPTS1 + TMAX + 1;
   static constexpr size_t BYTES = sizeof(R) * (size_t)R_TOTAL + sizeof(int) * (size_t)I_TOTAL;
 };
 
 // Resident CTAs per SM the compiler is asked to allow (caps registers at
-// 65536 / (threads * minblocks)).
+// 65536 / (threads * minblocks)): three for float, two for 8-byte types.
+#ifndef WQ_ROWS_MIN_BLOCKS_F32
+#define WQ_ROWS_MIN_BLOCKS_F32 3
+#endif
 #ifndef WQ_ROWS_MIN_BLOCKS
 #define WQ_ROWS_MIN_BLOCKS 2
 #endif
 
 template <int P, int D, int LM, int TMAX, bool DO_M, bool DO_K, typename R>
-__global__ void __launch_bounds__(32 * kRowsWarps, WQ_ROWS_MIN_BLOCKS) rows_kernel(const RowsArgs A) {
+__global__ void __launch_bounds__(32 * kRowsWarps, sizeof(R) == 4 ? WQ_ROWS_MIN_BLOCKS_F32 : WQ_ROWS_MIN_BLOCKS)
+    rows_kernel(const RowsArgs A) {
   using L = RowsLayout<P, D, LM, TMAX, DO_M, DO_K, R>;
   using O = typename OutT<R>::type;
   static_assert(sizeof(O) == sizeof(R), "the band stage shares the R region");
@@ -127,9 +161,11 @@ __global__ void __launch_bounds__(32 * kRowsWarps, WQ_ROWS_MIN_BLOCKS) rows_kern
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R *sV23 = reinterpret_cast<R *>(smem_raw);  // [di][kind][LM][NP]
-  R *sB23 = sV23 + L::V23;                    // [di][kind][LM][4]
+  R *sV23d = sV23 + L::V23;                   // [di][kind][LM][NB] (boundary lines)
+  R *sB23 = sV23d + L::V23D;                  // [di][kind][LM][4]
   R *sV1 = sB23 + L::B23;                     // [kind][MAXPTS1][NP]
-  R *sB1 = sV1 + L::V1;                       // [kind][MAXPTS1][4]
+  R *sV1d = sV1 + L::V1;                      // [kind][MAXPTS1][NB]
+  R *sB1 = sV1d + L::V1D;                     // [kind][MAXPTS1][4]
   R *sCb = sB1 + L::B1;                       // [l3][l2][l1]
   R *sU = sCb + L::CB;                        // [u][NL1][LS]
   R *sW = sU + L::US;                         // [warp][WS]
@@ -175,8 +211,15 @@ __global__ void __launch_bounds__(32 * kRowsWarps, WQ_ROWS_MIN_BLOCKS) rows_kern
         for (int i = 0; i < NP; i++) sV23[((di * 2 + kind) * LM + q) * NP + i] = Vg[(size_t)gq * NP + i];
 #pragma unroll
         for (int i = 0; i < 4; i++) sB23[((di * 2 + kind) * LM + q) * 4 + i] = Bg[(size_t)gq * 4 + i];
+        const int e = A.elem[dir][0][gq];
+        if constexpr (!L::INNER_GAUSS) {
+          const int o = e - r + P;
+#pragma unroll
+          for (int j = 0; j < NB; j++)
+            sV23d[((di * 2 + kind) * LM + q) * NB + j] =
+                (j >= o && j <= o + P) ? Vg[(size_t)gq * NP + (j - o)] : r_zero<R>();
+        }
         if (kind == 0) {
-          const int e = A.elem[dir][0][gq];
           sE23[di * LM + q] = e;
           sO23[di * LM + q] = e - r + P;
         }
@@ -187,6 +230,7 @@ __global__ void __launch_bounds__(32 * kRowsWarps, WQ_ROWS_MIN_BLOCKS) rows_kern
   const int p1lo = A.off[0][0][a], p1hi = A.off[0][0][b];
   const int np1 = p1hi - p1lo;
   for (int t = tid; t <= T; t += NT) sOff1[t] = A.off[0][0][a + t] - p1lo;
+  __syncthreads();  // sOff1 complete
   for (int t = tid; t < 2 * np1; t += NT) {
     const int kind = t >= np1 ? 1 : 0, q = t - kind * np1;
     const int gq = (kind ? A.off[0][1][a] : p1lo) + q;
@@ -196,7 +240,18 @@ __global__ void __launch_bounds__(32 * kRowsWarps, WQ_ROWS_MIN_BLOCKS) rows_kern
     for (int i = 0; i < NP; i++) sV1[(kind * L::MAXPTS1 + q) * NP + i] = Vg[(size_t)gq * NP + i];
 #pragma unroll
     for (int i = 0; i < 4; i++) sB1[(kind * L::MAXPTS1 + q) * 4 + i] = Bg[(size_t)gq * 4 + i];
-    if (kind == 0) sE1[q] = A.elem[0][0][gq];
+    const int e = A.elem[0][0][p1lo + q];
+    if (kind == 0) sE1[q] = e;
+    // the point's row: the last rl with sOff1[rl] <= q
+    int lo_r = 0, hi_r = T - 1;
+    while (lo_r < hi_r) {
+      const int mid = (lo_r + hi_r + 1) >> 1;
+      if (sOff1[mid] <= q) lo_r = mid; else hi_r = mid - 1;
+    }
+    const int o = e - (a + lo_r) + P;
+#pragma unroll
+    for (int j = 0; j < NB; j++)
+      sV1d[(kind * L::MAXPTS1 + q) * NB + j] = (j >= o && j <= o + P) ? Vg[(size_t)gq * NP + (j - o)] : r_zero<R>();
   }
   const int elo1 = a - P < 0 ? 0 : a - P;
   const int ehi1 = (b - 1) > A.N[0] - 1 ? A.N[0] - 1 : (b - 1);
@@ -206,18 +261,22 @@ __global__ void __launch_bounds__(32 * kRowsWarps, WQ_ROWS_MIN_BLOCKS) rows_kern
   {
     unsigned bad = 0;
     const double *cg = A.coef;
+    const R *cr = static_cast<const R *>(A.coefR);
     for (int t = tid; t < L::NL3 * NL * NL1; t += NT) {
       const int l1 = t % NL1, l2 = (t / NL1) % NL, l3 = t / (NL1 * NL);
       if (l1 < nl1 && l2 < nl2 && l3 < nl3) {
-        double v = 1.0;
-        if (cg) {
-          const long long g = (long long)(l1lo + l1) +
-                              (long long)A.nc[0] * ((long long)(l23lo[0] + l2) +
-                                                    (long long)A.nc[1] * (D == 3 ? (long long)(l23lo[1] + l3) : 0LL));
-          v = cg[g];
+        const long long g = (long long)(l1lo + l1) +
+                            (long long)A.nc[0] * ((long long)(l23lo[0] + l2) +
+                                                  (long long)A.nc[1] * (D == 3 ? (long long)(l23lo[1] + l3) : 0LL));
+        if (cr) {
+          sCb[t] = cr[g];
+        } else if (cg) {
+          const double v = cg[g];
           if (!isfinite(v)) bad = 1;
+          sCb[t] = r_from_double<R>(v);
+        } else {
+          sCb[t] = r_from_double<R>(1.0);
         }
-        sCb[t] = r_from_double<R>(v);
       }
     }
     bad = __reduce_or_sync(0xffffffffu, bad);
@@ -250,8 +309,16 @@ __global__ void __launch_bounds__(32 * kRowsWarps, WQ_ROWS_MIN_BLOCKS) rows_kern
           R acc[NB];
 #pragma unroll
           for (int j = 0; j < NB; j++) acc[j] = r_zero<R>();
-          for (int q3 = 0; q3 < L3; q3++)
-            fiber_add<P>(acc, wx[t * LM + q3], &sV23[((1 * 2 + k3) * LM + q3) * NP], sO23[LM + q3]);
+          if constexpr (L::INNER_GAUSS) {
+            fiber_at<P, 0>(acc, wx[t * LM + 0], &sV23[((1 * 2 + k3) * LM + 0) * NP]);
+            fiber_at<P, 1>(acc, wx[t * LM + 1], &sV23[((1 * 2 + k3) * LM + 1) * NP]);
+            fiber_at<P, 2>(acc, wx[t * LM + 2], &sV23[((1 * 2 + k3) * LM + 2) * NP]);
+            if constexpr (P >= 3) fiber_at<P, (P >= 3 ? 3 : 0)>(acc, wx[t * LM + 3], &sV23[((1 * 2 + k3) * LM + 3) * NP]);
+          } else {
+            for (int q3 = 0; q3 < L3; q3++)
+              fiber_point<P>(acc, wx[t * LM + q3], &sV23[((1 * 2 + k3) * LM + q3) * NP],
+                             &sV23d[((1 * 2 + k3) * LM + q3) * NB], sO23[LM + q3]);
+          }
 #pragma unroll
           for (int j = 0; j < NB; j++) wt[t * NB + j] = acc[j];
         }
@@ -279,14 +346,33 @@ __global__ void __launch_bounds__(32 * kRowsWarps, WQ_ROWS_MIN_BLOCKS) rows_kern
         R acc[NB];
 #pragma unroll
         for (int j = 0; j < NB; j++) acc[j] = r_zero<R>();
-        for (int q2 = 0; q2 < L2; q2++) {
-          const int o = sO23[q2];
-          const R *vM = &sV23[((0 * 2 + 0) * LM + q2) * NP];
+        if constexpr (L::INNER_GAUSS) {
           if (u == 0) {
-            fiber_add<P>(acc, wx[(0 * LM + q2) * NB + j3], vM, o);
+            fiber_at<P, 0>(acc, wx[(0 * LM + 0) * NB + j3], &sV23[(0 * LM + 0) * NP]);
+            fiber_at<P, 1>(acc, wx[(0 * LM + 1) * NB + j3], &sV23[(0 * LM + 1) * NP]);
+            fiber_at<P, 2>(acc, wx[(0 * LM + 2) * NB + j3], &sV23[(0 * LM + 2) * NP]);
+            if constexpr (P >= 3) fiber_at<P, (P >= 3 ? 3 : 0)>(acc, wx[(0 * LM + 3) * NB + j3], &sV23[(0 * LM + 3) * NP]);
           } else {
-            fiber_add<P>(acc, wx[(1 * LM + q2) * NB + j3], &sV23[((0 * 2 + 1) * LM + q2) * NP], o);
-            fiber_add<P>(acc, wx[(2 * LM + q2) * NB + j3], vM, o);
+#pragma unroll
+            for (int c = 1; c <= 2; c++) {
+              const int k = (c == 1) ? 1 : 0;  // kind of x2 in combination c
+              fiber_at<P, 0>(acc, wx[(c * LM + 0) * NB + j3], &sV23[(k * LM + 0) * NP]);
+              fiber_at<P, 1>(acc, wx[(c * LM + 1) * NB + j3], &sV23[(k * LM + 1) * NP]);
+              fiber_at<P, 2>(acc, wx[(c * LM + 2) * NB + j3], &sV23[(k * LM + 2) * NP]);
+              if constexpr (P >= 3) fiber_at<P, (P >= 3 ? 3 : 0)>(acc, wx[(c * LM + 3) * NB + j3], &sV23[(k * LM + 3) * NP]);
+            }
+          }
+        } else {
+          for (int q2 = 0; q2 < L2; q2++) {
+            const int o = sO23[q2];
+            const R *vM = &sV23[(0 * LM + q2) * NP], *vMd = &sV23d[(0 * LM + q2) * NB];
+            if (u == 0) {
+              fiber_point<P>(acc, wx[(0 * LM + q2) * NB + j3], vM, vMd, o);
+            } else {
+              fiber_point<P>(acc, wx[(1 * LM + q2) * NB + j3], &sV23[(1 * LM + q2) * NP],
+                             &sV23d[(1 * LM + q2) * NB], o);
+              fiber_point<P>(acc, wx[(2 * LM + q2) * NB + j3], vM, vMd, o);
+            }
           }
         }
 #pragma unroll
@@ -312,8 +398,15 @@ __global__ void __launch_bounds__(32 * kRowsWarps, WQ_ROWS_MIN_BLOCKS) rows_kern
         R acc[NB];
 #pragma unroll
         for (int j = 0; j < NB; j++) acc[j] = r_zero<R>();
-        for (int q2 = 0; q2 < L2; q2++)
-          fiber_add<P>(acc, wx[u * LM + q2], &sV23[((0 * 2 + u) * LM + q2) * NP], sO23[q2]);
+        if constexpr (L::INNER_GAUSS) {
+          fiber_at<P, 0>(acc, wx[u * LM + 0], &sV23[(u * LM + 0) * NP]);
+          fiber_at<P, 1>(acc, wx[u * LM + 1], &sV23[(u * LM + 1) * NP]);
+          fiber_at<P, 2>(acc, wx[u * LM + 2], &sV23[(u * LM + 2) * NP]);
+          if constexpr (P >= 3) fiber_at<P, (P >= 3 ? 3 : 0)>(acc, wx[u * LM + 3], &sV23[(u * LM + 3) * NP]);
+        } else {
+          for (int q2 = 0; q2 < L2; q2++)
+            fiber_point<P>(acc, wx[u * LM + q2], &sV23[(u * LM + q2) * NP], &sV23d[(u * LM + q2) * NB], sO23[q2]);
+        }
 #pragma unroll
         for (int j = 0; j < NB; j++) sU[(u * NL1 + l1) * LS + j] = acc[j];
       }
@@ -339,65 +432,80 @@ __global__ void __launch_bounds__(32 * kRowsWarps, WQ_ROWS_MIN_BLOCKS) rows_kern
       // weighted Gaussian rule in x1: point q in element r1-P+q, band offset q;
       // sliding windows over the coefficient columns (w) and the entries j1 (acc)
       const int kb = (r1 - P) - l1lo;
+      constexpr int NS = L::NSLOT;
+      int prs[NS];
+      R w0[NS][4], w1[NS][4], aM[NS][NP], aK[NS][NP];
 #pragma unroll
-      for (int s = 0; s < L::NSLOT; s++) {
-        const int pr = lane + 32 * s;
-        if (pr < NPAIR) {
-          R w0[4], w1[4], aM[NP], aK[NP];
+      for (int s = 0; s < NS; s++) {
+        // a lane past the last fibre repeats it and does not store
+        prs[s] = lane + 32 * s < NPAIR ? lane + 32 * s : NPAIR - 1;
 #pragma unroll
-          for (int i = 0; i < 4; i++) {
-            w0[i] = U0[(kb + i) * LS + pr];
-            w1[i] = DO_K ? U1[(kb + i) * LS + pr] : r_zero<R>();
-          }
+        for (int i = 0; i < 4; i++) {
+          w0[s][i] = U0[(kb + i) * LS + prs[s]];
+          w1[s][i] = DO_K ? U1[(kb + i) * LS + prs[s]] : r_zero<R>();
+        }
 #pragma unroll
-          for (int i = 0; i < NP; i++) { aM[i] = r_zero<R>(); aK[i] = r_zero<R>(); }
+        for (int i = 0; i < NP; i++) { aM[s][i] = r_zero<R>(); aK[s][i] = r_zero<R>(); }
+      }
 #pragma unroll QUNROLL
-          for (int q = 0; q < NP; q++) {
-            R bm[4], vm[NP];
+      for (int q = 0; q < NP; q++) {
+        R bm[4], vm[NP], bs[4], vs[NP];
+        if constexpr (std::is_same<R, float>::value && NP == 4) {
+          const float4 b4m = reinterpret_cast<const float4 *>(bm0)[q], b4s = reinterpret_cast<const float4 *>(bs0)[q];
+          const float4 v4m = reinterpret_cast<const float4 *>(vm0)[q], v4s = reinterpret_cast<const float4 *>(vs0)[q];
+          bm[0] = b4m.x; bm[1] = b4m.y; bm[2] = b4m.z; bm[3] = b4m.w;
+          bs[0] = b4s.x; bs[1] = b4s.y; bs[2] = b4s.z; bs[3] = b4s.w;
+          vm[0] = v4m.x; vm[1] = v4m.y; vm[2] = v4m.z; vm[3] = v4m.w;
+          vs[0] = v4s.x; vs[1] = v4s.y; vs[2] = v4s.z; vs[3] = v4s.w;
+        } else {
 #pragma unroll
-            for (int i = 0; i < 4; i++) bm[i] = bm0[q * 4 + i];
+          for (int i = 0; i < 4; i++) { bm[i] = bm0[q * 4 + i]; bs[i] = bs0[q * 4 + i]; }
 #pragma unroll
-            for (int i = 0; i < NP; i++) vm[i] = vm0[q * NP + i];
-            if constexpr (DO_M) {
-              R y = r_zero<R>();
+          for (int i = 0; i < NP; i++) { vm[i] = vm0[q * NP + i]; vs[i] = vs0[q * NP + i]; }
+        }
 #pragma unroll
-              for (int i = 0; i < 4; i++) y = r_fma(bm[i], w0[i], y);
+        for (int s = 0; s < NS; s++) {
+          if constexpr (DO_M) {
+            R y = r_zero<R>();
 #pragma unroll
-              for (int i = 0; i < NP; i++) aM[i] = r_fma(vm[i], y, aM[i]);
-            }
-            if constexpr (DO_K) {
-              R bs[4], vs[NP];
+            for (int i = 0; i < 4; i++) y = r_fma(bm[i], w0[s][i], y);
 #pragma unroll
-              for (int i = 0; i < 4; i++) bs[i] = bs0[q * 4 + i];
-#pragma unroll
-              for (int i = 0; i < NP; i++) vs[i] = vs0[q * NP + i];
-              R yk = r_zero<R>(), ys = r_zero<R>();
-#pragma unroll
-              for (int i = 0; i < 4; i++) {
-                yk = r_fma(bm[i], w1[i], yk);
-                ys = r_fma(bs[i], w0[i], ys);
-              }
-#pragma unroll
-              for (int i = 0; i < NP; i++) aK[i] = r_fma(vs[i], ys, r_fma(vm[i], yk, aK[i]));
-            }
-            // entry j1 = q is complete
-            if constexpr (DO_M) stM[pr * NB + q] = r_out(aM[0]);
-            if constexpr (DO_K) stK[pr * NB + q] = r_out(aK[0]);
-#pragma unroll
-            for (int i = 0; i < NP - 1; i++) { aM[i] = aM[i + 1]; aK[i] = aK[i + 1]; }
-            aM[NP - 1] = r_zero<R>();
-            aK[NP - 1] = r_zero<R>();
-#pragma unroll
-            for (int i = 0; i < 3; i++) { w0[i] = w0[i + 1]; w1[i] = w1[i + 1]; }
-            if (q < P) {
-              w0[3] = U0[(kb + q + 4) * LS + pr];
-              if constexpr (DO_K) w1[3] = U1[(kb + q + 4) * LS + pr];
-            }
+            for (int i = 0; i < NP; i++) aM[s][i] = r_fma(vm[i], y, aM[s][i]);
           }
+          if constexpr (DO_K) {
+            R yk = r_zero<R>(), ys = r_zero<R>();
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+              yk = r_fma(bm[i], w1[s][i], yk);
+              ys = r_fma(bs[i], w0[s][i], ys);
+            }
+#pragma unroll
+            for (int i = 0; i < NP; i++) aK[s][i] = r_fma(vs[i], ys, r_fma(vm[i], yk, aK[s][i]));
+          }
+          // entry j1 = q is complete
+          if (lane + 32 * s < NPAIR) {
+            if constexpr (DO_M) stM[prs[s] * NB + q] = r_out(aM[s][0]);
+            if constexpr (DO_K) stK[prs[s] * NB + q] = r_out(aK[s][0]);
+          }
+#pragma unroll
+          for (int i = 0; i < NP - 1; i++) { aM[s][i] = aM[s][i + 1]; aK[s][i] = aK[s][i + 1]; }
+          aM[s][NP - 1] = r_zero<R>();
+          aK[s][NP - 1] = r_zero<R>();
+#pragma unroll
+          for (int i = 0; i < 3; i++) { w0[s][i] = w0[s][i + 1]; w1[s][i] = w1[s][i + 1]; }
+          if (q < P) {
+            w0[s][3] = U0[(kb + q + 4) * LS + prs[s]];
+            if constexpr (DO_K) w1[s][3] = U1[(kb + q + 4) * LS + prs[s]];
+          }
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < NS; s++) {
+        if (lane + 32 * s < NPAIR) {
 #pragma unroll
           for (int i = 0; i < P; i++) {
-            if constexpr (DO_M) stM[pr * NB + NP + i] = r_out(aM[i]);
-            if constexpr (DO_K) stK[pr * NB + NP + i] = r_out(aK[i]);
+            if constexpr (DO_M) stM[prs[s] * NB + NP + i] = r_out(aM[s][i]);
+            if constexpr (DO_K) stK[prs[s] * NB + NP + i] = r_out(aK[s][i]);
           }
         }
       }
@@ -414,12 +522,12 @@ __global__ void __launch_bounds__(32 * kRowsWarps, WQ_ROWS_MIN_BLOCKS) rows_kern
             const int e = sE1[q];
             const int k0 = e - l1lo, o = e - r1 + P;
             const R *bm = &sB1[(0 * L::MAXPTS1 + q) * 4];
-            const R *vm = &sV1[(0 * L::MAXPTS1 + q) * NP];
+            const R *vm = &sV1[(0 * L::MAXPTS1 + q) * NP], *vmd = &sV1d[(0 * L::MAXPTS1 + q) * NB];
             if constexpr (DO_M) {
               R y = r_zero<R>();
 #pragma unroll
               for (int i = 0; i < 4; i++) y = r_fma(bm[i], U0[(k0 + i) * LS + pr], y);
-              fiber_add<P>(accM, y, vm, o);
+              fiber_point<P>(accM, y, vm, vmd, o);
             }
             if constexpr (DO_K) {
               const R *bs = &sB1[(1 * L::MAXPTS1 + q) * 4];
@@ -429,8 +537,8 @@ __global__ void __launch_bounds__(32 * kRowsWarps, WQ_ROWS_MIN_BLOCKS) rows_kern
                 yk = r_fma(bm[i], U1[(k0 + i) * LS + pr], yk);
                 ys = r_fma(bs[i], U0[(k0 + i) * LS + pr], ys);
               }
-              fiber_add<P>(accK, yk, vm, o);
-              fiber_add<P>(accK, ys, &sV1[(1 * L::MAXPTS1 + q) * NP], o);
+              fiber_point<P>(accK, yk, vm, vmd, o);
+              fiber_point<P>(accK, ys, &sV1[(1 * L::MAXPTS1 + q) * NP], &sV1d[(1 * L::MAXPTS1 + q) * NB], o);
             }
           }
 #pragma unroll

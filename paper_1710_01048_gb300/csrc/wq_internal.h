@@ -77,6 +77,8 @@ struct wq_rules {
   const int *dev_lines_interior = nullptr;
   const int *dev_lines_boundary = nullptr;
   unsigned *dev_status = nullptr;
+  float *dev_coef32 = nullptr;   // the coefficients rounded to float (mixed mode)
+  float2 *dev_coefdd = nullptr;  // the coefficients as double-float pairs (df64 mode)
 };
 
 namespace wq {
