@@ -183,6 +183,29 @@ wq_status wq_assemble_mass_stiffness(const wq_rules *rules, const double *const 
                                      void *stream);
 
 /*
+ * Adjoint of the assembly with respect to the coefficient spline: every band
+ * entry of M and K (Eq. Mass, Eq. Stiffness with the weighted Gaussian rules)
+ * is linear in the coefficients C of c, so for band weights G, H the
+ * functional
+ *   J(C) = sum over rows [row_begin, row_end) and band entries of
+ *          G .* K(C) + H .* M(C)
+ * has the gradient dJ/dC = A^T (G, H), A the linear map C -> (K, M) that the
+ * forward calls apply.  This is the backward pass of the assembly.
+ *   geom       as for wq_assemble_mass_stiffness;
+ *   G, H       device band arrays laid out like K and M of those rows (double
+ *              for WQ_FP64 and WQ_DF64, float for WQ_MIXED); either may be
+ *              NULL (a zero weight);
+ *   grad       device, prod(nel_a + 3) doubles, x fastest; overwritten (it is
+ *              cleared on `stream`, then accumulated with atomic adds, so the
+ *              summation order, and the last bits of the result, may change
+ *              from call to call).
+ * The same row-range, device and stream rules as the forward calls apply;
+ * an empty range, or G and H both NULL, gives grad = 0.
+ */
+wq_status wq_assemble_adjoint(const wq_rules *rules, const double *const *geom, wq_precision prec, const void *G,
+                              const void *H, double *grad, int64_t row_begin, int64_t row_end, void *stream);
+
+/*
  * Synchronises `stream`, then returns and clears the device-detected status
  * of the assembly calls made with `rules` since the previous check:
  * WQ_ERR_GEOMETRY if some J_aa <= 0, WQ_ERR_NONFINITE if some input was NaN

@@ -27,7 +27,7 @@ WQ_RULES_HOST_ONLY, WQ_RULES_DEVICE = 0, 1
 EXPORTS = ["wq_status_string", "wq_version", "wq_rule_1d", "wq_rule_1d_from", "wq_rules_build", "wq_rules_free",
            "wq_rules_row", "wq_rows", "wq_band_width", "wq_band_nnz", "wq_coef_count", "wq_flop_count",
            "wq_assemble_mass", "wq_assemble_stiffness", "wq_assemble_mass_stiffness", "wq_status_check",
-           "wq_assemble_noalloc"]
+           "wq_assemble_noalloc", "wq_assemble_adjoint"]
 
 
 class WqError(RuntimeError):
@@ -79,6 +79,7 @@ def _lib():
                                                c_void_p]
     lib.wq_status_check.argtypes = [c_void_p, c_void_p]
     lib.wq_assemble_noalloc.argtypes = [c_void_p, PP, c_void_p, c_int, c_void_p, c_void_p, i64, i64, c_void_p, c_int]
+    lib.wq_assemble_adjoint.argtypes = [c_void_p, PP, c_int, c_void_p, c_void_p, c_void_p, i64, i64, c_void_p]
     for f in EXPORTS:
         if f not in ("wq_status_string", "wq_version", "wq_rules_free", "wq_rows", "wq_band_width", "wq_band_nnz",
                      "wq_coef_count", "wq_flop_count"):
@@ -205,6 +206,11 @@ def wq_assemble_noalloc(handle, geom_ptrs, coef_ptr, prec, M_ptr, K_ptr, row_beg
                                       int(check_status))
 
 
+def wq_assemble_adjoint(handle, geom_ptrs, prec, G_ptr, H_ptr, grad_ptr, row_begin, row_end, stream):
+    g, keep = _geom_array(geom_ptrs)
+    return _lib().wq_assemble_adjoint(handle, g, prec, G_ptr, H_ptr, grad_ptr, row_begin, row_end, stream)
+
+
 # ------------------------------------------------------------------ conveniences
 class Rules:
     """Owns a wq_rules handle (host tables, and device tables when device=True)."""
@@ -296,3 +302,67 @@ def assemble(rules, geom, coef=None, prec="fp64", mass=True, stiffness=True, row
     if check:
         _check(wq_status_check(rules.handle, s), "wq_status_check")
     return M, K
+
+
+def assemble_adjoint(rules, geom, G=None, H=None, prec="fp64", row_begin=0, row_end=None, out=None, stream=None,
+                     check=True):
+    """Gradient of J(C) = sum G * K(C) + H * M(C) over rows [row_begin,
+    row_end) with respect to the coefficient spline's C (the backward pass of
+    assemble).  G, H: CUDA tensors of shape (rows in range, band), float64
+    for 'fp64'/'df64', float32 for 'mixed', or None.  Returns a float64 CUDA
+    tensor of rules.ncoef values (written into `out` if given)."""
+    import torch
+
+    if row_end is None:
+        row_end = rules.rows
+    p = PRECISIONS[prec]
+    dt = torch.float32 if p == WQ_MIXED else torch.float64
+    nrows = row_end - row_begin
+    for g in geom:
+        assert g.is_cuda and g.dtype == torch.float64 and g.is_contiguous()
+    for X in (G, H):
+        if X is not None:
+            assert X.is_cuda and X.dtype == dt and X.is_contiguous() and tuple(X.shape) == (nrows, rules.band)
+    grad = out if out is not None else torch.empty(rules.ncoef, dtype=torch.float64, device=geom[0].device)
+    s = _stream_handle(stream)
+    st = wq_assemble_adjoint(rules.handle, [g.data_ptr() for g in geom], p,
+                             ctypes.c_void_p(G.data_ptr()) if G is not None else None,
+                             ctypes.c_void_p(H.data_ptr()) if H is not None else None,
+                             ctypes.c_void_p(grad.data_ptr()), row_begin, row_end, s)
+    _check(st, "wq_assemble_adjoint")
+    if check:
+        _check(wq_status_check(rules.handle, s), "wq_status_check")
+    return grad
+
+
+def _autograd_function():
+    import torch
+
+    class _Assemble(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, coef, rules, geom, prec):
+            M, K = assemble(rules, geom, coef, prec)
+            ctx.rules, ctx.geom, ctx.prec = rules, geom, prec
+            return M, K
+
+        @staticmethod
+        def backward(ctx, dM, dK):
+            dt = torch.float32 if ctx.prec == "mixed" else torch.float64
+            H = dM.to(dt).contiguous() if dM is not None else None
+            G = dK.to(dt).contiguous() if dK is not None else None
+            grad = assemble_adjoint(ctx.rules, ctx.geom, G, H, ctx.prec)
+            return grad, None, None, None
+
+    return _Assemble
+
+
+_ASSEMBLE_FN = None
+
+
+def assemble_differentiable(rules, geom, coef, prec="fp64"):
+    """(M, K) = assemble(rules, geom, coef, prec) as a torch autograd
+    operation of coef: backward calls wq_assemble_adjoint."""
+    global _ASSEMBLE_FN
+    if _ASSEMBLE_FN is None:
+        _ASSEMBLE_FN = _autograd_function()
+    return _ASSEMBLE_FN.apply(coef, rules, list(geom), prec)

@@ -1,0 +1,358 @@
+// Adjoint of the row-wise assembly: the gradient of
+//   J(c) = sum_rows sum_band G .* K(c) + H .* M(c)
+// with respect to the coefficients C of the cubic spline c.  Every band entry
+// is linear in C, so dJ/dC = A^T applied to (G, H), where A is the forward
+// map of rows_kernel.  Per chunk of a line of rows the forward map factors as
+//   C block --(phase A: x3 then x2 stages)--> U --(phase B: x1 stage)--> bands,
+// and the adjoint runs the transposed stages in reverse order:
+//   1. x1 stage transposed, per row and band fibre (j2, j3):
+//        yM[q] = sum_j1 H[j1] V1M[q][j1],  yK[q] = sum_j1 G[j1] V1M[q][j1],
+//        yS[q] = sum_j1 G[j1] V1S[q][j1]
+//      accumulated into Ubar0[l1] += b1M[q][l1] yM[q] + b1S[q][l1] yS[q] and
+//      Ubar1[l1] += b1M[q][l1] yK[q].  Rows at least 7 apart touch disjoint
+//      coefficient columns, so the rows are taken in 7 phases and every
+//      shared-memory update is exclusive.
+//   2. x2 then x3 stages transposed, one warp per coefficient column, giving
+//      the chunk's block of dJ/dC, added to the gradient in global memory.
+#pragma once
+
+#include "assemble.cuh"
+
+namespace wq {
+
+struct AdjArgs {
+  RowsArgs rows;         // tables, sizes, row range, line list, chunking (M, K, coef unused)
+  const void *G, *H;     // band weights, OutT<R>, rows [row_begin, row_end); either may be null
+  double *grad;          // prod(nel_a + 3) coefficients, accumulated into
+};
+
+template <int P, int D, int LM, int TMAX, typename R>
+struct AdjLayout {
+  using F = RowsLayout<P, D, LM, TMAX, true, true, R>;
+  static constexpr int NP = P + 1, NB = 2 * P + 1;
+  static constexpr int NPAIR = F::NPAIR, BAND = F::BAND, NSLOT = F::NSLOT;
+  static constexpr int NL1 = F::NL1, NL = P + 4, NW = F::NW, NT = F::NT, MAXPTS1 = F::MAXPTS1;
+  static constexpr int NPHASE = P + 4;  // rows this far apart touch disjoint columns
+  // per-warp scratch: a row slice of G and H (phase 1) or the column work (phase 2)
+  static constexpr int WG = 2 * 32 * NB;                                   // [H|G][32 fibres][NB]
+  static constexpr int WQ = (D == 3) ? 3 * LM * NB : 2 * LM;               // Cqbar
+  static constexpr int WT = (D == 3) ? 2 * NL * NB : 0;                    // T3bar
+  static constexpr int WZ = (D == 3) ? 2 * NL * LM : 0;                    // Zbar
+  static constexpr int WS = pad16<R>((WG > WQ + WT + WZ) ? WG : WQ + WT + WZ);
+  static constexpr int V23 = F::V23, V23D = F::V23D, B23 = F::B23, V1 = F::V1, V1D = F::V1D, B1 = F::B1;
+  static constexpr int UB = pad16<R>(2 * NL1 * NPAIR);                     // [u][l1][pair]
+  static constexpr int R_TOTAL = V23 + V23D + B23 + V1 + V1D + B1 + UB + NW * WS;
+  static constexpr int I_TOTAL = 4 * LM + MAXPTS1 + TMAX + 1;
+  static constexpr size_t BYTES = sizeof(R) * (size_t)R_TOTAL + sizeof(int) * (size_t)I_TOTAL;
+};
+
+template <typename R> __device__ __forceinline__ R r_from_out(typename OutT<R>::type v) { return (R)v; }
+template <> __device__ __forceinline__ dd r_from_out<dd>(double v) { return dd_from_double(v); }
+__device__ __forceinline__ double r_to_double(double a) { return a; }
+__device__ __forceinline__ double r_to_double(float a) { return (double)a; }
+__device__ __forceinline__ double r_to_double(dd a) { return dd_to_double(a); }
+
+template <int P, int D, int LM, int TMAX, typename R>
+__global__ void __launch_bounds__(32 * kRowsWarps, sizeof(R) == 4 ? 2 : 1) adjoint_kernel(const AdjArgs AA) {
+  using L = AdjLayout<P, D, LM, TMAX, R>;
+  using O = typename OutT<R>::type;
+  const RowsArgs &A = AA.rows;
+  constexpr int NP = L::NP, NB = L::NB, NT = L::NT, NW = L::NW, NL = L::NL, NL1 = L::NL1;
+  constexpr int NPAIR = L::NPAIR, BAND = L::BAND;
+  constexpr bool INNER_GAUSS = (LM == P + 1);
+  const bool hasG = AA.G != nullptr, hasH = AA.H != nullptr;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R *sV23 = reinterpret_cast<R *>(smem_raw);
+  R *sV23d = sV23 + L::V23;
+  R *sB23 = sV23d + L::V23D;
+  R *sV1 = sB23 + L::B23;
+  R *sV1d = sV1 + L::V1;
+  R *sB1 = sV1d + L::V1D;
+  R *sUb = sB1 + L::B1;  // [u][NL1][NPAIR]
+  R *sW = sUb + L::UB;
+  int *sE23 = reinterpret_cast<int *>(smem_raw + sizeof(R) * (size_t)L::R_TOTAL);
+  int *sO23 = sE23 + 2 * LM;
+  int *sE1 = sO23 + 2 * LM;
+  int *sOff1 = sE1 + L::MAXPTS1;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int line = A.lines[blockIdx.x / A.nch];
+  const int ch = blockIdx.x % A.nch;
+  const int n1 = A.n[0];
+  const int r2 = (D == 3) ? line % A.n[1] : line;
+  const int r3 = (D == 3) ? line / A.n[1] : 0;
+  const long long base = (long long)line * n1;
+  long long lo = (long long)ch * A.T, hi = lo + A.T;
+  if (hi > n1) hi = n1;
+  if (lo < A.row_begin - base) lo = A.row_begin - base;
+  if (hi > A.row_end - base) hi = A.row_end - base;
+  if (lo >= hi) return;
+  const int a = (int)lo, b = (int)hi, T = b - a;
+
+  // ------------------------------------------------ tables (as in the forward kernel)
+  const int rr[2] = {r2, r3};
+  int L23[2] = {1, 1}, l23lo[2] = {0, 0}, nl23[2] = {1, 1};
+#pragma unroll
+  for (int di = 0; di < D - 1; di++) {
+    const int dir = di + 1, r = rr[di];
+    const int off0 = A.off[dir][0][r];
+    const int off1 = A.off[dir][1][r];
+    L23[di] = INNER_GAUSS ? P + 1 : A.off[dir][0][r + 1] - off0;
+    const int elo = r - P < 0 ? 0 : r - P;
+    const int ehi = r > A.N[dir] - 1 ? A.N[dir] - 1 : r;
+    l23lo[di] = elo;
+    nl23[di] = ehi - elo + 4;
+    for (int t = tid; t < 2 * LM; t += NT) {
+      const int kind = t / LM, q = t % LM;
+      if (q < L23[di]) {
+        const int gq = (kind ? off1 : off0) + q;
+        const R *Vg = static_cast<const R *>(A.V[dir][kind]);
+        const R *Bg = static_cast<const R *>(A.beta[dir][kind]);
+#pragma unroll
+        for (int i = 0; i < NP; i++) sV23[((di * 2 + kind) * LM + q) * NP + i] = Vg[(size_t)gq * NP + i];
+#pragma unroll
+        for (int i = 0; i < 4; i++) sB23[((di * 2 + kind) * LM + q) * 4 + i] = Bg[(size_t)gq * 4 + i];
+        const int e = A.elem[dir][0][gq];
+        if constexpr (!INNER_GAUSS) {
+          const int o = e - r + P;
+#pragma unroll
+          for (int j = 0; j < NB; j++)
+            sV23d[((di * 2 + kind) * LM + q) * NB + j] =
+                (j >= o && j <= o + P) ? Vg[(size_t)gq * NP + (j - o)] : r_zero<R>();
+        }
+        if (kind == 0) {
+          sE23[di * LM + q] = e;
+          sO23[di * LM + q] = e - r + P;
+        }
+      }
+    }
+  }
+  const int p1lo = A.off[0][0][a], p1hi = A.off[0][0][b];
+  const int np1 = p1hi - p1lo;
+  for (int t = tid; t <= T; t += NT) sOff1[t] = A.off[0][0][a + t] - p1lo;
+  const int elo1 = a - P < 0 ? 0 : a - P;
+  const int ehi1 = (b - 1) > A.N[0] - 1 ? A.N[0] - 1 : (b - 1);
+  const int l1lo = elo1, nl1 = ehi1 - elo1 + 4;
+  for (int t = tid; t < 2 * NL1 * NPAIR; t += NT) sUb[t] = r_zero<R>();
+  __syncthreads();  // sOff1 complete
+  for (int t = tid; t < 2 * np1; t += NT) {
+    const int kind = t >= np1 ? 1 : 0, q = t - kind * np1;
+    const int gq = (kind ? A.off[0][1][a] : p1lo) + q;
+    const R *Vg = static_cast<const R *>(A.V[0][kind]);
+    const R *Bg = static_cast<const R *>(A.beta[0][kind]);
+#pragma unroll
+    for (int i = 0; i < NP; i++) sV1[(kind * L::MAXPTS1 + q) * NP + i] = Vg[(size_t)gq * NP + i];
+#pragma unroll
+    for (int i = 0; i < 4; i++) sB1[(kind * L::MAXPTS1 + q) * 4 + i] = Bg[(size_t)gq * 4 + i];
+    const int e = A.elem[0][0][p1lo + q];
+    if (kind == 0) sE1[q] = e;
+    int lo_r = 0, hi_r = T - 1;
+    while (lo_r < hi_r) {
+      const int mid = (lo_r + hi_r + 1) >> 1;
+      if (sOff1[mid] <= q) lo_r = mid; else hi_r = mid - 1;
+    }
+    const int o = e - (a + lo_r) + P;
+#pragma unroll
+    for (int j = 0; j < NB; j++)
+      sV1d[(kind * L::MAXPTS1 + q) * NB + j] = (j >= o && j <= o + P) ? Vg[(size_t)gq * NP + (j - o)] : r_zero<R>();
+  }
+  const int L2 = L23[0], L3 = L23[1];
+  const int nl2 = nl23[0], nl3 = (D == 3) ? nl23[1] : 1;
+  __syncthreads();
+
+  // ------------------------------------------------ 1. x1 stage transposed, rows in phases
+  R *ws = sW + warp * L::WS;  // [0: H | 1: G][32][NB]
+  R *Ub0 = sUb, *Ub1 = sUb + NL1 * NPAIR;
+  const O *Hg = static_cast<const O *>(AA.H);
+  const O *Gg = static_cast<const O *>(AA.G);
+  for (int ph = 0; ph < L::NPHASE; ph++) {
+    const int nrows_ph = (T - ph + L::NPHASE - 1) / L::NPHASE;  // rows ph, ph+NPHASE, ...
+    for (int item = warp; item < nrows_ph * L::NSLOT; item += NW) {
+      const int rl = ph + (item / L::NSLOT) * L::NPHASE, s = item % L::NSLOT;
+      const int r1 = a + rl;
+      const int f0 = 32 * s, nf = (NPAIR - f0) < 32 ? (NPAIR - f0) : 32;
+      // this slot's fibres of the row: NB consecutive entries each, one contiguous run
+      const long long grow = (base + r1 - A.row_begin) * BAND + (long long)f0 * NB;
+      for (int i = lane; i < nf * NB; i += 32) {
+        ws[i] = hasH ? r_from_out<R>(Hg[grow + i]) : r_zero<R>();
+        ws[32 * NB + i] = hasG ? r_from_out<R>(Gg[grow + i]) : r_zero<R>();
+      }
+      __syncwarp();
+      if (lane < nf) {
+        const int pr = f0 + lane;
+        const R *hv = &ws[lane * NB];
+        const R *gv = &ws[32 * NB + lane * NB];
+        const int q0 = sOff1[rl], q1e = sOff1[rl + 1];
+        for (int q = q0; q < q1e; q++) {
+          const int e = sE1[q], k0 = e - l1lo;
+          const R *vm = &sV1d[(0 * L::MAXPTS1 + q) * NB], *vs = &sV1d[(1 * L::MAXPTS1 + q) * NB];
+          R yM = r_zero<R>(), yK = r_zero<R>(), yS = r_zero<R>();
+#pragma unroll
+          for (int j = 0; j < NB; j++) {
+            yM = r_fma(hv[j], vm[j], yM);
+            yK = r_fma(gv[j], vm[j], yK);
+            yS = r_fma(gv[j], vs[j], yS);
+          }
+          const R *bm = &sB1[(0 * L::MAXPTS1 + q) * 4], *bs = &sB1[(1 * L::MAXPTS1 + q) * 4];
+#pragma unroll
+          for (int i = 0; i < 4; i++) {
+            R *u0 = &Ub0[(k0 + i) * NPAIR + pr];
+            *u0 = r_fma(bs[i], yS, r_fma(bm[i], yM, *u0));
+            R *u1 = &Ub1[(k0 + i) * NPAIR + pr];
+            *u1 = r_fma(bm[i], yK, *u1);
+          }
+        }
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+
+  // ------------------------------------------------ 2. x2, x3 stages transposed, warp per column
+  R *wq = sW + warp * L::WS;  // Cqbar
+  R *wt = wq + L::WQ;         // T3bar
+  R *wz = wt + L::WT;         // Zbar
+  for (int l1 = warp; l1 < nl1; l1 += NW) {
+    R cb[2];  // this lane's block entries (l2, l3) = lane, lane + 32
+    if constexpr (D == 3) {
+      // Cqbar[c][q2][j3] = sum_j2 Ubar[u(c)][l1][j3*NB+j2] V2_{k2(c)}[q2][j2 - o2];
+      // c = 0: (M, M) from Ubar0 with V2M; 1: (S, M) from Ubar1 with V2S; 2: (M, S) from Ubar1 with V2M
+      for (int t = lane; t < 3 * LM * NB; t += 32) {
+        const int j3 = t % NB, q2 = (t / NB) % LM, c = t / (NB * LM);
+        if (q2 < L2) {
+          const R *ub = (c == 0 ? Ub0 : Ub1) + l1 * NPAIR + j3 * NB;
+          const int k2 = (c == 1) ? 1 : 0;
+          const R *vd = INNER_GAUSS ? nullptr : &sV23d[(k2 * LM + q2) * NB];
+          R s = r_zero<R>();
+          if constexpr (INNER_GAUSS) {
+#pragma unroll
+            for (int i = 0; i < NP; i++) s = r_fma(ub[q2 + i], sV23[(k2 * LM + q2) * NP + i], s);
+          } else {
+#pragma unroll
+            for (int j = 0; j < NB; j++) s = r_fma(ub[j], vd[j], s);
+          }
+          wq[t] = s;
+        }
+      }
+      __syncwarp();
+      // T3bar[k3][l2][j3] = sum_{c: kind3(c) = k3} sum_q2 Cqbar[c][q2][j3] b2_{k2(c)}[q2][l2 - e2(q2)]
+      for (int t = lane; t < 2 * NL * NB; t += 32) {
+        const int j3 = t % NB, l2 = (t / NB) % NL, k3 = t / (NB * NL);
+        R s = r_zero<R>();
+        if (l2 < nl2) {
+          for (int q2 = 0; q2 < L2; q2++) {
+            const int i = l2 - (sE23[q2] - l23lo[0]);
+            if (i >= 0 && i < 4) {
+              if (k3 == 0) {
+                s = r_fma(wq[(0 * LM + q2) * NB + j3], sB23[((0 * 2 + 0) * LM + q2) * 4 + i], s);
+                s = r_fma(wq[(1 * LM + q2) * NB + j3], sB23[((0 * 2 + 1) * LM + q2) * 4 + i], s);
+              } else {
+                s = r_fma(wq[(2 * LM + q2) * NB + j3], sB23[((0 * 2 + 0) * LM + q2) * 4 + i], s);
+              }
+            }
+          }
+        }
+        wt[t] = s;
+      }
+      __syncwarp();
+      // Zbar[k3][l2][q3] = sum_j3 T3bar[k3][l2][j3] V3_k3[q3][j3 - o3]
+      for (int t = lane; t < 2 * NL * LM; t += 32) {
+        const int q3 = t % LM, l2 = (t / LM) % NL, k3 = t / (LM * NL);
+        if (q3 < L3 && l2 < nl2) {
+          const R *tb = &wt[(k3 * NL + l2) * NB];
+          R s = r_zero<R>();
+          if constexpr (INNER_GAUSS) {
+#pragma unroll
+            for (int i = 0; i < NP; i++) s = r_fma(tb[q3 + i], sV23[((1 * 2 + k3) * LM + q3) * NP + i], s);
+          } else {
+            const R *vd = &sV23d[((1 * 2 + k3) * LM + q3) * NB];
+#pragma unroll
+            for (int j = 0; j < NB; j++) s = r_fma(tb[j], vd[j], s);
+          }
+          wz[t] = s;
+        }
+      }
+      __syncwarp();
+      // Cbar[l2][l3] = sum_k3 sum_q3 Zbar[k3][l2][q3] b3_k3[q3][l3 - e3(q3)]
+#pragma unroll
+      for (int s2 = 0; s2 < 2; s2++) {
+        const int t = lane + 32 * s2;
+        const int l3 = t % NL, l2 = t / NL;
+        R s = r_zero<R>();
+        if (t < NL * NL && l2 < nl2 && l3 < nl3) {
+          for (int q3 = 0; q3 < L3; q3++) {
+            const int i = l3 - (sE23[LM + q3] - l23lo[1]);
+            if (i >= 0 && i < 4) {
+              s = r_fma(wz[(0 * NL + l2) * LM + q3], sB23[((1 * 2 + 0) * LM + q3) * 4 + i], s);
+              s = r_fma(wz[(1 * NL + l2) * LM + q3], sB23[((1 * 2 + 1) * LM + q3) * 4 + i], s);
+            }
+          }
+        }
+        cb[s2] = s;
+      }
+#pragma unroll
+      for (int s2 = 0; s2 < 2; s2++) {
+        const int t = lane + 32 * s2;
+        const int l3 = t % NL, l2 = t / NL;
+        if (t < NL * NL && l2 < nl2 && l3 < nl3) {
+          const long long g = (long long)(l1lo + l1) +
+                              (long long)A.nc[0] * ((long long)(l23lo[0] + l2) + (long long)A.nc[1] * (l23lo[1] + l3));
+          atomicAdd(&AA.grad[g], r_to_double(cb[s2]));
+        }
+      }
+    } else {
+      // Cqbar[c][q2] = sum_j2 Ubar[c][l1][j2] V2_c[q2][j2 - o2], c = kind2
+      for (int t = lane; t < 2 * LM; t += 32) {
+        const int q2 = t % LM, c = t / LM;
+        if (q2 < L2) {
+          const R *ub = (c == 0 ? Ub0 : Ub1) + l1 * NPAIR;
+          R s = r_zero<R>();
+          if constexpr (INNER_GAUSS) {
+#pragma unroll
+            for (int i = 0; i < NP; i++) s = r_fma(ub[q2 + i], sV23[(c * LM + q2) * NP + i], s);
+          } else {
+            const R *vd = &sV23d[(c * LM + q2) * NB];
+#pragma unroll
+            for (int j = 0; j < NB; j++) s = r_fma(ub[j], vd[j], s);
+          }
+          wq[t] = s;
+        }
+      }
+      __syncwarp();
+      // Cbar[l2] = sum_c sum_q2 Cqbar[c][q2] b2_c[q2][l2 - e2(q2)]
+      if (lane < nl2) {
+        const int l2 = lane;
+        R s = r_zero<R>();
+        for (int q2 = 0; q2 < L2; q2++) {
+          const int i = l2 - (sE23[q2] - l23lo[0]);
+          if (i >= 0 && i < 4) {
+            s = r_fma(wq[0 * LM + q2], sB23[(0 * LM + q2) * 4 + i], s);
+            s = r_fma(wq[1 * LM + q2], sB23[(1 * LM + q2) * 4 + i], s);
+          }
+        }
+        const long long g = (long long)(l1lo + l1) + (long long)A.nc[0] * (long long)(l23lo[0] + l2);
+        atomicAdd(&AA.grad[g], r_to_double(s));
+      }
+      (void)cb;
+    }
+    __syncwarp();
+  }
+}
+
+template <int P, int D, int LM, int TMAX, typename R>
+cudaError_t launch_adjoint_one(const AdjArgs &a, int nblocks, cudaStream_t s) {
+  using L = AdjLayout<P, D, LM, TMAX, R>;
+  auto kern = adjoint_kernel<P, D, LM, TMAX, R>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (nblocks <= 0) return cudaSuccess;
+  kern<<<nblocks, L::NT, L::BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace wq

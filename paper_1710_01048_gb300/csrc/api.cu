@@ -213,6 +213,47 @@ wq_status launch_fold(const wq_rules *R, const double *const *geom, cudaStream_t
   return check_launch(cudaGetLastError());
 }
 
+// Table pointers and sizes of a rules object for one arithmetic type.
+void fill_tables(const wq_rules *R, wq_precision prec, wq::RowsArgs &ra) {
+  std::memset(&ra, 0, sizeof(ra));
+  for (int a = 0; a < 3; a++) {
+    int aa = a < R->dim ? a : 0;
+    for (int k = 0; k < 2; k++) {
+      const wq::DevDirKind &Dk = R->dev[aa][k];
+      ra.off[a][k] = Dk.off;
+      ra.elem[a][k] = Dk.elem;
+      ra.V[a][k] = prec == WQ_FP64 ? (const void *)Dk.v64
+                   : prec == WQ_MIXED ? (const void *)Dk.v32 : (const void *)Dk.vdd;
+      ra.beta[a][k] = prec == WQ_FP64 ? (const void *)Dk.beta
+                      : prec == WQ_MIXED ? (const void *)Dk.beta32 : (const void *)Dk.betadd;
+    }
+    ra.n[a] = R->n[a];
+    ra.N[a] = R->nel[a];
+    ra.nc[a] = R->nc[a];
+  }
+}
+
+// Line range and chunking of one line class for rows [rb, re); returns the
+// number of CTAs (0 if the class has no line in the range).
+int chunk_class(const wq_rules *R, int cls, int64_t rb, int64_t re, wq::RowsArgs &ra, wq_status *st) {
+  const int n1 = R->n[0];
+  const int first_line = (int)(rb / n1), last_line = (int)((re - 1) / n1);
+  const std::vector<int> &lines = cls == 0 ? R->lines.interior : R->lines.boundary;
+  auto lo = std::lower_bound(lines.begin(), lines.end(), first_line);
+  auto hi = std::upper_bound(lines.begin(), lines.end(), last_line);
+  const int nl = (int)(hi - lo);
+  if (nl <= 0) return 0;
+  const int tmax = cls == 0 ? wq::kInteriorChunk : wq::kBoundaryChunk;
+  if (R->max_chunk_points[cls] > wq::chunk_points_bound(R->p, tmax)) {
+    *st = WQ_ERR_UNSUPPORTED;
+    return 0;
+  }
+  ra.nch = (n1 + tmax - 1) / tmax;
+  ra.T = (n1 + ra.nch - 1) / ra.nch;
+  ra.lines = (cls == 0 ? R->dev_lines_interior : R->dev_lines_boundary) + (lo - lines.begin());
+  return nl * ra.nch;
+}
+
 wq_status assemble(const wq_rules *R, const double *const *geom, const double *coef, wq_precision prec, void *M,
                    void *K, int64_t rb, int64_t re, void *stream) {
   if (!R || !geom) return WQ_ERR_ARG;
@@ -231,22 +272,7 @@ wq_status assemble(const wq_rules *R, const double *const *geom, const double *c
   if (st != WQ_OK) return st;
 
   wq::RowsArgs ra;
-  std::memset(&ra, 0, sizeof(ra));
-  for (int a = 0; a < 3; a++) {
-    int aa = a < R->dim ? a : 0;
-    for (int k = 0; k < 2; k++) {
-      const wq::DevDirKind &Dk = R->dev[aa][k];
-      ra.off[a][k] = Dk.off;
-      ra.elem[a][k] = Dk.elem;
-      ra.V[a][k] = prec == WQ_FP64 ? (const void *)Dk.v64
-                   : prec == WQ_MIXED ? (const void *)Dk.v32 : (const void *)Dk.vdd;
-      ra.beta[a][k] = prec == WQ_FP64 ? (const void *)Dk.beta
-                      : prec == WQ_MIXED ? (const void *)Dk.beta32 : (const void *)Dk.betadd;
-    }
-    ra.n[a] = R->n[a];
-    ra.N[a] = R->nel[a];
-    ra.nc[a] = R->nc[a];
-  }
+  fill_tables(R, prec, ra);
   ra.coef = coef;
   if (coef) {
     const size_t ncoef = (size_t)R->nc[0] * R->nc[1] * R->nc[2];
@@ -261,20 +287,11 @@ wq_status assemble(const wq_rules *R, const double *const *geom, const double *c
   ra.row_begin = rb;
   ra.row_end = re;
   ra.status = R->dev_status;
-  const int n1 = R->n[0];
-  const int first_line = (int)(rb / n1), last_line = (int)((re - 1) / n1);
   for (int cls = 0; cls < 2; cls++) {
-    const std::vector<int> &lines = cls == 0 ? R->lines.interior : R->lines.boundary;
-    auto lo = std::lower_bound(lines.begin(), lines.end(), first_line);
-    auto hi = std::upper_bound(lines.begin(), lines.end(), last_line);
-    int nl = (int)(hi - lo);
-    if (nl <= 0) continue;
-    int tmax = cls == 0 ? wq::kInteriorChunk : wq::kBoundaryChunk;
-    if (R->max_chunk_points[cls] > wq::chunk_points_bound(R->p, tmax)) return WQ_ERR_UNSUPPORTED;
-    ra.nch = (n1 + tmax - 1) / tmax;
-    ra.T = (n1 + ra.nch - 1) / ra.nch;
-    ra.lines = (cls == 0 ? R->dev_lines_interior : R->dev_lines_boundary) + (lo - lines.begin());
-    int nblocks = nl * ra.nch;
+    wq_status cst = WQ_OK;
+    const int nblocks = chunk_class(R, cls, rb, re, ra, &cst);
+    if (cst != WQ_OK) return cst;
+    if (nblocks == 0) continue;
     cudaError_t e;
     bool dm = M != nullptr, dk = K != nullptr;
     if (R->p == 2)
@@ -436,6 +453,51 @@ wq_status wq_assemble_mass_stiffness(const wq_rules *rules, const double *const 
                                      void *stream) {
   if (row_begin != row_end && (!M || !K)) return WQ_ERR_ARG;
   return assemble(rules, geom, coef, prec, M, K, row_begin, row_end, stream);
+}
+
+wq_status wq_assemble_adjoint(const wq_rules *R, const double *const *geom, wq_precision prec, const void *G,
+                              const void *H, double *grad, int64_t row_begin, int64_t row_end, void *stream) {
+  if (!R || !geom || !grad) return WQ_ERR_ARG;
+  if (!R->on_device) return WQ_ERR_ARG;
+  if (prec != WQ_FP64 && prec != WQ_MIXED && prec != WQ_DF64) return WQ_ERR_ARG;
+  const int64_t rows = (int64_t)R->n[0] * R->n[1] * R->n[2];
+  if (row_begin < 0 || row_end > rows || row_begin > row_end) return WQ_ERR_ARG;
+  for (int a = 0; a < R->dim; a++)
+    if (!geom[a]) return WQ_ERR_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != R->device) return WQ_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t ncoef = (size_t)R->nc[0] * R->nc[1] * R->nc[2];
+  if (cudaMemsetAsync(grad, 0, ncoef * sizeof(double), s) != cudaSuccess) return WQ_ERR_CUDA;
+  if (row_begin == row_end || (!G && !H)) return WQ_OK;
+  wq_status st = launch_fold(R, geom, s);
+  if (st != WQ_OK) return st;
+  wq::AdjArgs aa;
+  std::memset(&aa, 0, sizeof(aa));
+  fill_tables(R, prec, aa.rows);
+  aa.rows.row_begin = row_begin;
+  aa.rows.row_end = row_end;
+  aa.rows.status = R->dev_status;
+  aa.G = G;
+  aa.H = H;
+  aa.grad = grad;
+  for (int cls = 0; cls < 2; cls++) {
+    wq_status cst = WQ_OK;
+    const int nblocks = chunk_class(R, cls, row_begin, row_end, aa.rows, &cst);
+    if (cst != WQ_OK) return cst;
+    if (nblocks == 0) continue;
+    cudaError_t e;
+    if (R->p == 2)
+      e = prec == WQ_FP64   ? wq::launch_adjoint<2, double>(R->dim, cls, aa, nblocks, s)
+          : prec == WQ_MIXED ? wq::launch_adjoint<2, float>(R->dim, cls, aa, nblocks, s)
+                             : wq::launch_adjoint<2, wq::dd>(R->dim, cls, aa, nblocks, s);
+    else
+      e = prec == WQ_FP64   ? wq::launch_adjoint<3, double>(R->dim, cls, aa, nblocks, s)
+          : prec == WQ_MIXED ? wq::launch_adjoint<3, float>(R->dim, cls, aa, nblocks, s)
+                             : wq::launch_adjoint<3, wq::dd>(R->dim, cls, aa, nblocks, s);
+    if (e != cudaSuccess) return WQ_ERR_CUDA;
+  }
+  return WQ_OK;
 }
 
 wq_status wq_status_check(const wq_rules *R, void *stream) {

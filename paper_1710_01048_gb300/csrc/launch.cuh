@@ -5,6 +5,7 @@
 // has (2P+1) threads per row of its chunk.
 #pragma once
 
+#include "adjoint.cuh"
 #include "assemble.cuh"
 
 namespace wq {
@@ -50,11 +51,27 @@ cudaError_t launch_rows(int D, bool do_m, bool do_k, int cls, const RowsArgs &a,
   return launch_class<P, 3, false, true, R>(cls, a, nblocks, s);
 }
 
+template <int P, typename R>
+cudaError_t launch_adjoint(int D, int cls, const AdjArgs &a, int nblocks, cudaStream_t s) {
+  if (D == 2) {
+    if (cls == 0) return launch_adjoint_one<P, 2, P + 1, kInteriorChunk, R>(a, nblocks, s);
+    return launch_adjoint_one<P, 2, P *(P + 1), kBoundaryChunk, R>(a, nblocks, s);
+  }
+  if (cls == 0) return launch_adjoint_one<P, 3, P + 1, kInteriorChunk, R>(a, nblocks, s);
+  return launch_adjoint_one<P, 3, P *(P + 1), kBoundaryChunk, R>(a, nblocks, s);
+}
+
 extern template cudaError_t launch_rows<2, double>(int, bool, bool, int, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_rows<3, double>(int, bool, bool, int, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_rows<2, float>(int, bool, bool, int, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_rows<3, float>(int, bool, bool, int, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_rows<2, dd>(int, bool, bool, int, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_rows<3, dd>(int, bool, bool, int, const RowsArgs &, int, cudaStream_t);
+extern template cudaError_t launch_adjoint<2, double>(int, int, const AdjArgs &, int, cudaStream_t);
+extern template cudaError_t launch_adjoint<3, double>(int, int, const AdjArgs &, int, cudaStream_t);
+extern template cudaError_t launch_adjoint<2, float>(int, int, const AdjArgs &, int, cudaStream_t);
+extern template cudaError_t launch_adjoint<3, float>(int, int, const AdjArgs &, int, cudaStream_t);
+extern template cudaError_t launch_adjoint<2, dd>(int, int, const AdjArgs &, int, cudaStream_t);
+extern template cudaError_t launch_adjoint<3, dd>(int, int, const AdjArgs &, int, cudaStream_t);
 
 }  // namespace wq
