@@ -206,6 +206,62 @@ wq_status wq_assemble_adjoint(const wq_rules *rules, const double *const *geom, 
                               const void *H, double *grad, int64_t row_begin, int64_t row_end, void *stream);
 
 /*
+ * Batched assembly of many independent 3D patches (each its own mesh,
+ * degree, map and coefficient; every row of every patch is assembled as in
+ * wq_assemble_mass_stiffness, with the weighted Gaussian rules of Sec. 3).
+ * The paper treats one patch; the batch is a throughput form of the same
+ * computation.  A plan (wq_batch) holds the patches' work list and folded
+ * tables and a CUDA graph of one batched geometry fold and one persistent
+ * row launch that takes work items (chunks of lines of rows) from a global
+ * counter.  Its results are bit-identical to one wq_assemble_mass_stiffness
+ * call per patch with the same precision.
+ */
+typedef struct wq_batch wq_batch;
+typedef struct {
+  const wq_rules *rules;  /* WQ_RULES_DEVICE, dim 3, current device; patches may share one; must outlive the plan */
+  const double *geom[3];  /* device control values of the patch's map (n_a doubles each) */
+  const double *coef;     /* device coefficient spline, prod(nel_a + 3) doubles, or NULL (c = 1) */
+  void *M, *K;            /* device band outputs for all rows of the patch (double for WQ_FP64 and WQ_DF64,
+                             float for WQ_MIXED); both required */
+} wq_patch;
+
+/*
+ * Creates a plan for `npatch` patches (the array is copied; the buffers it
+ * points to are read at every launch, so new input values in the same
+ * buffers are picked up).  Allocates the plan's device memory once and
+ * captures the graph with the default configuration.  WQ_ERR_ARG for a
+ * missing pointer, a 2D or host-only rules object, or another device.
+ */
+wq_status wq_batch_create(const wq_patch *patches, int npatch, wq_precision prec, wq_batch **out);
+/* Enqueues the plan's graph on `stream` (asynchronous). */
+wq_status wq_batch_launch(wq_batch *batch, void *stream);
+/* Synchronises `stream`, returns and clears the plan's device status (as wq_status_check). */
+wq_status wq_batch_status(wq_batch *batch, void *stream);
+/*
+ * Launch configuration: config[0] = chunk length of interior lines (1..24),
+ * config[1] = chunk length of boundary lines (1..16), config[2] = resident
+ * CTAs per SM of the persistent launch (1..config[4]), config[3] = item order
+ * (0: patch order, 1: costliest line classes first).  get writes config[0..4],
+ * config[4] being the most CTAs per SM the kernel can hold; set reads
+ * config[0..3], synchronises the device, rebuilds the work list and
+ * recaptures the graph.
+ */
+wq_status wq_batch_get_config(const wq_batch *batch, int *config);
+wq_status wq_batch_set_config(wq_batch *batch, const int *config);
+/*
+ * Autotuner: times every configuration of a fixed candidate set (chunk
+ * lengths 24/16/12/8 and 16/8, the two largest CTA counts, both orders),
+ * each `reps` times on `stream` after one warm-up (the plan's outputs are
+ * written), keeps the fastest and recaptures the graph.  *best_ms (may be
+ * NULL) receives its mean time.  Synchronises the device.
+ */
+wq_status wq_batch_tune(wq_batch *batch, void *stream, int reps, double *best_ms);
+/* Synchronises the plan's device and frees the plan. */
+void wq_batch_free(wq_batch *batch);
+/* One-shot form: create, launch on `stream`, check the status, free. */
+wq_status wq_assemble_batch(const wq_patch *patches, int npatch, wq_precision prec, void *stream);
+
+/*
  * Synchronises `stream`, then returns and clears the device-detected status
  * of the assembly calls made with `rules` since the previous check:
  * WQ_ERR_GEOMETRY if some J_aa <= 0, WQ_ERR_NONFINITE if some input was NaN

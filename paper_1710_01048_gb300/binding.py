@@ -27,7 +27,8 @@ WQ_RULES_HOST_ONLY, WQ_RULES_DEVICE = 0, 1
 EXPORTS = ["wq_status_string", "wq_version", "wq_rule_1d", "wq_rule_1d_from", "wq_rules_build", "wq_rules_free",
            "wq_rules_row", "wq_rows", "wq_band_width", "wq_band_nnz", "wq_coef_count", "wq_flop_count",
            "wq_assemble_mass", "wq_assemble_stiffness", "wq_assemble_mass_stiffness", "wq_status_check",
-           "wq_assemble_noalloc", "wq_assemble_adjoint"]
+           "wq_assemble_noalloc", "wq_assemble_adjoint", "wq_batch_create", "wq_batch_launch", "wq_batch_status",
+           "wq_batch_get_config", "wq_batch_set_config", "wq_batch_tune", "wq_batch_free", "wq_assemble_batch"]
 
 
 class WqError(RuntimeError):
@@ -39,6 +40,11 @@ class WqError(RuntimeError):
 
 class wq_mesh(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("degree", ctypes.c_int), ("nel", ctypes.c_int * 3)]
+
+
+class wq_patch(ctypes.Structure):
+    _fields_ = [("rules", ctypes.c_void_p), ("geom", ctypes.c_void_p * 3), ("coef", ctypes.c_void_p),
+                ("M", ctypes.c_void_p), ("K", ctypes.c_void_p)]
 
 
 _loaded = None
@@ -80,9 +86,19 @@ def _lib():
     lib.wq_status_check.argtypes = [c_void_p, c_void_p]
     lib.wq_assemble_noalloc.argtypes = [c_void_p, PP, c_void_p, c_int, c_void_p, c_void_p, i64, i64, c_void_p, c_int]
     lib.wq_assemble_adjoint.argtypes = [c_void_p, PP, c_int, c_void_p, c_void_p, c_void_p, i64, i64, c_void_p]
+    PPatch = ctypes.POINTER(wq_patch)
+    lib.wq_batch_create.argtypes = [PPatch, c_int, c_int, ctypes.POINTER(c_void_p)]
+    lib.wq_batch_launch.argtypes = [c_void_p, c_void_p]
+    lib.wq_batch_status.argtypes = [c_void_p, c_void_p]
+    lib.wq_batch_get_config.argtypes = [c_void_p, PI]
+    lib.wq_batch_set_config.argtypes = [c_void_p, PI]
+    lib.wq_batch_tune.argtypes = [c_void_p, c_void_p, c_int, PD]
+    lib.wq_batch_free.argtypes = [c_void_p]
+    lib.wq_batch_free.restype = None
+    lib.wq_assemble_batch.argtypes = [PPatch, c_int, c_int, c_void_p]
     for f in EXPORTS:
         if f not in ("wq_status_string", "wq_version", "wq_rules_free", "wq_rows", "wq_band_width", "wq_band_nnz",
-                     "wq_coef_count", "wq_flop_count"):
+                     "wq_coef_count", "wq_flop_count", "wq_batch_free"):
             getattr(lib, f).restype = c_int
     _loaded = lib
     return lib
@@ -366,3 +382,72 @@ def assemble_differentiable(rules, geom, coef, prec="fp64"):
     if _ASSEMBLE_FN is None:
         _ASSEMBLE_FN = _autograd_function()
     return _ASSEMBLE_FN.apply(coef, rules, list(geom), prec)
+
+
+# ------------------------------------------------------------------ batches
+def _patch_array(patches):
+    """patches: sequence of (rules, geom list of 3 CUDA tensors, coef tensor or None, M, K)."""
+    arr = (wq_patch * len(patches))()
+    for i, (rules, geom, coef, M, K) in enumerate(patches):
+        arr[i].rules = rules.handle
+        for a in range(3):
+            arr[i].geom[a] = geom[a].data_ptr()
+        arr[i].coef = coef.data_ptr() if coef is not None else None
+        arr[i].M = M.data_ptr()
+        arr[i].K = K.data_ptr()
+    return arr
+
+
+class Batch:
+    """A batched-assembly plan (wq_batch): patches are tuples (rules, geom,
+    coef, M, K) of Rules objects and CUDA tensors that must stay alive while
+    the plan is used; launch() replays the plan's CUDA graph."""
+
+    def __init__(self, patches, prec="fp64"):
+        self._keep = list(patches)
+        arr = _patch_array(self._keep)
+        h = ctypes.c_void_p()
+        _check(_lib().wq_batch_create(arr, len(self._keep), PRECISIONS[prec], ctypes.byref(h)), "wq_batch_create")
+        self.handle = h
+        self.prec = prec
+
+    def launch(self, stream=None):
+        _check(_lib().wq_batch_launch(self.handle, _stream_handle(stream)), "wq_batch_launch")
+
+    def status(self, stream=None):
+        return _lib().wq_batch_status(self.handle, _stream_handle(stream))
+
+    def check(self, stream=None):
+        _check(self.status(stream), "wq_batch_status")
+
+    @property
+    def config(self):
+        c = (ctypes.c_int * 5)()
+        _check(_lib().wq_batch_get_config(self.handle, c), "wq_batch_get_config")
+        return dict(chunk_interior=c[0], chunk_boundary=c[1], ctas_per_sm=c[2], order=c[3], max_ctas_per_sm=c[4])
+
+    def set_config(self, chunk_interior, chunk_boundary, ctas_per_sm, order):
+        c = (ctypes.c_int * 4)(chunk_interior, chunk_boundary, ctas_per_sm, order)
+        _check(_lib().wq_batch_set_config(self.handle, c), "wq_batch_set_config")
+
+    def tune(self, reps=2, stream=None):
+        ms = ctypes.c_double()
+        _check(_lib().wq_batch_tune(self.handle, _stream_handle(stream), int(reps), ctypes.byref(ms)), "wq_batch_tune")
+        return ms.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib().wq_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def assemble_batch(patches, prec="fp64", stream=None):
+    """One-shot batched assembly (wq_assemble_batch) of (rules, geom, coef, M, K) tuples."""
+    arr = _patch_array(patches)
+    _check(_lib().wq_assemble_batch(arr, len(patches), PRECISIONS[prec], _stream_handle(stream)), "wq_assemble_batch")

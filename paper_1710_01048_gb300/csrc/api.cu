@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 
+#include "fold.cuh"
 #include "launch.cuh"
 #include "wq_internal.h"
 
@@ -19,12 +20,8 @@ constexpr size_t kAlign = 256;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-// Folds the geometry factor of the separable map into the 1D tables of every
-// direction and kind (Eq. Mass, Eq. Stiffness with J diagonal):
-//   mass kind:      V = W * |J_aa(x)| * B_{e+i}(x)
-//   stiffness kind: V = W / |J_aa(x)| * B'_{e+i}(x)
-// with J_aa(x) = sum_i g_{a,e+i} B'_{e+i}(x) (Eq. Gmap1).  Raises the
-// geometry bit where J_aa <= 0 and the non-finite bit where J_aa is NaN/Inf.
+// Folds the geometry factor into the 1D tables of every direction and kind
+// (one thread per point, wq::fold_point).
 struct FoldSeg {
   const int *elem;
   const double *w, *t0, *t1, *g;
@@ -46,21 +43,7 @@ __global__ void fold_kernel(const FoldArgs A) {
     int s = 0;
     while (s + 1 < A.nseg && t >= A.seg[s + 1].start) s++;
     const FoldSeg &S = A.seg[s];
-    const int q = t - S.start, np = A.np;
-    const int e = S.elem[q];
-    double J = 0.0;
-    for (int i = 0; i < np; i++) J = fma(S.g[e + i], S.t1[(size_t)q * np + i], J);
-    if (!(J > 0.0)) bits |= isfinite(J) ? wq::kBitGeometry : wq::kBitNonFinite;
-    const double aj = fabs(J);
-    const double f = S.kind == WQ_KIND_MASS ? S.w[q] * aj : S.w[q] / aj;
-    const double *T = S.kind == WQ_KIND_MASS ? S.t0 : S.t1;
-    for (int i = 0; i < np; i++) {
-      const double v = f * T[(size_t)q * np + i];
-      const float vh = (float)v;
-      S.v64[(size_t)q * np + i] = v;
-      S.v32[(size_t)q * np + i] = vh;
-      S.vdd[(size_t)q * np + i] = make_float2(vh, (float)(v - (double)vh));
-    }
+    bits = wq::fold_point(t - S.start, A.np, S.kind, S.elem, S.w, S.t0, S.t1, S.g, S.v64, S.v32, S.vdd);
   }
   bits = __reduce_or_sync(0xffffffffu, bits);
   if ((threadIdx.x & 31) == 0 && bits) atomicOr(A.status, bits);

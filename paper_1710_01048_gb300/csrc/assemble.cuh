@@ -150,16 +150,18 @@ struct RowsLayout {
 #define WQ_ROWS_MIN_BLOCKS 2
 #endif
 
+// The work of one CTA: chunk `bid` of the launch's line list (line
+// bid / nch, chunk bid % nch), in the dynamic shared memory `smem_raw`
+// (RowsLayout::BYTES).  Called by rows_kernel with bid = blockIdx.x and by
+// the persistent batch kernel once per work item.
 template <int P, int D, int LM, int TMAX, bool DO_M, bool DO_K, typename R>
-__global__ void __launch_bounds__(32 * kRowsWarps, sizeof(R) == 4 ? WQ_ROWS_MIN_BLOCKS_F32 : WQ_ROWS_MIN_BLOCKS)
-    rows_kernel(const RowsArgs A) {
+__device__ __forceinline__ void rows_block(const RowsArgs &A, const int bid, unsigned char *smem_raw) {
   using L = RowsLayout<P, D, LM, TMAX, DO_M, DO_K, R>;
   using O = typename OutT<R>::type;
   static_assert(sizeof(O) == sizeof(R), "the band stage shares the R region");
   constexpr int NP = L::NP, NB = L::NB, NT = L::NT, NW = L::NW, LS = L::LS, NL = L::NL, NL1 = L::NL1;
   constexpr int NPAIR = L::NPAIR, BAND = L::BAND;
 
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   R *sV23 = reinterpret_cast<R *>(smem_raw);  // [di][kind][LM][NP]
   R *sV23d = sV23 + L::V23;                   // [di][kind][LM][NB] (boundary lines)
   R *sB23 = sV23d + L::V23D;                  // [di][kind][LM][4]
@@ -175,8 +177,8 @@ __global__ void __launch_bounds__(32 * kRowsWarps, sizeof(R) == 4 ? WQ_ROWS_MIN_
   int *sOff1 = sE1 + L::MAXPTS1;              // [TMAX+1]
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int line = A.lines[blockIdx.x / A.nch];
-  const int ch = blockIdx.x % A.nch;
+  const int line = A.lines[bid / A.nch];
+  const int ch = bid % A.nch;
   const int n1 = A.n[0];
   const int r2 = (D == 3) ? line % A.n[1] : line;
   const int r3 = (D == 3) ? line / A.n[1] : 0;
@@ -562,6 +564,13 @@ __global__ void __launch_bounds__(32 * kRowsWarps, sizeof(R) == 4 ? WQ_ROWS_MIN_
     }
     __syncwarp();
   }
+}
+
+template <int P, int D, int LM, int TMAX, bool DO_M, bool DO_K, typename R>
+__global__ void __launch_bounds__(32 * kRowsWarps, sizeof(R) == 4 ? WQ_ROWS_MIN_BLOCKS_F32 : WQ_ROWS_MIN_BLOCKS)
+    rows_kernel(const RowsArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  rows_block<P, D, LM, TMAX, DO_M, DO_K, R>(A, blockIdx.x, smem_raw);
 }
 
 }  // namespace wq

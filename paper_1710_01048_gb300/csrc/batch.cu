@@ -1,0 +1,431 @@
+// Batched assembly of many independent 3D patches: the plan object
+// (wq_batch), its batched geometry fold, the persistent row launch captured
+// in a CUDA graph, and the autotuner of the launch's tile parameters.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "batch.cuh"
+#include "fold.cuh"
+#include "wq_internal.h"
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// One (patch, direction, kind) table of the batched fold.
+struct BFold {
+  const int *elem;
+  const double *w, *t0, *t1, *g;
+  double *v64;
+  float *v32;
+  float2 *vdd;
+  int start, np, kind;
+};
+
+__global__ void batch_fold_kernel(const BFold *__restrict__ segs, int nseg, int total, unsigned *status) {
+  unsigned bits = 0;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (segs[mid].start <= t) lo = mid; else hi = mid - 1;
+    }
+    const BFold &S = segs[lo];
+    bits |= wq::fold_point(t - S.start, S.np, S.kind, S.elem, S.w, S.t0, S.t1, S.g, S.v64, S.v32, S.vdd);
+  }
+  bits = __reduce_or_sync(0xffffffffu, bits);
+  if ((threadIdx.x & 31) == 0 && bits) atomicOr(status, bits);
+}
+
+// Work of one item (a chunk of a line), relative, for the ordering heuristic:
+// degree-3 boundary lines are the most expensive, degree-2 interior the least.
+int cost_rank(int p, int cls) { return p == 3 ? (cls == 1 ? 0 : 1) : (cls == 1 ? 2 : 3); }
+
+}  // namespace
+
+struct wq_batch {
+  int npatch = 0;
+  wq_precision prec = WQ_FP64;
+  int device = -1, nsm = 0, max_ctas = 1;
+  std::vector<wq_patch> patches;
+  // device block: fold segments, batch segments, per-patch folded tables, counter, status
+  void *dev_block = nullptr;
+  BFold *dev_fold = nullptr;
+  int nfold = 0, fold_total = 0;
+  wq::BatchSeg *dev_segs = nullptr;
+  int nseg = 0, nitems = 0;
+  unsigned *dev_counter = nullptr, *dev_status = nullptr;
+  std::vector<wq::RowsArgs> base_args;  // per patch, without class/chunking
+  int config[4] = {wq::kInteriorChunk, wq::kBoundaryChunk, 1, 1};
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+wq_status prepare(wq_batch *B) {
+  int ctas = 0;
+  cudaError_t e = B->prec == WQ_FP64 ? wq::batch_prepare<double>(&ctas)
+                  : B->prec == WQ_MIXED ? wq::batch_prepare<float>(&ctas) : wq::batch_prepare<wq::dd>(&ctas);
+  if (e != cudaSuccess || ctas < 1) return WQ_ERR_CUDA;
+  B->max_ctas = ctas;
+  return WQ_OK;
+}
+
+// Most x1 points of one chunk when the lines of n1 rows are cut into chunks of
+// at most t rows (as the launch cuts them).
+int chunk_points(const wq_rules *R, int t) {
+  const std::vector<int> &off = R->host[0][0].off;
+  const int n1 = R->n[0], nch = (n1 + t - 1) / t, tt = (n1 + nch - 1) / nch;
+  int mx = 0;
+  for (int c = 0; c * tt < n1; c++) mx = std::max(mx, off[std::min(n1, (c + 1) * tt)] - off[c * tt]);
+  return mx;
+}
+
+// Builds the segment list for the current configuration and uploads it.
+wq_status build_segments(wq_batch *B) {
+  const int tint = B->config[0], tbnd = B->config[1], order = B->config[3];
+  std::vector<wq::BatchSeg> segs;
+  for (int i = 0; i < B->npatch; i++) {
+    const wq_rules *R = B->patches[i].rules;
+    for (int cls = 0; cls < 2; cls++) {
+      const std::vector<int> &lines = cls == 0 ? R->lines.interior : R->lines.boundary;
+      if (lines.empty()) continue;
+      const int t = cls == 0 ? tint : tbnd;
+      const int tmax = cls == 0 ? wq::kInteriorChunk : wq::kBoundaryChunk;
+      if (t < 1 || t > tmax) return WQ_ERR_ARG;
+      if (chunk_points(R, t) > wq::chunk_points_bound(R->p, tmax)) return WQ_ERR_UNSUPPORTED;
+      wq::BatchSeg S;
+      std::memset(&S, 0, sizeof(S));
+      S.a = B->base_args[i];
+      S.a.nch = (R->n[0] + t - 1) / t;
+      S.a.T = (R->n[0] + S.a.nch - 1) / S.a.nch;
+      S.a.lines = cls == 0 ? R->dev_lines_interior : R->dev_lines_boundary;
+      S.p = R->p;
+      S.cls = cls;
+      S.nitems = (int)lines.size() * S.a.nch;
+      segs.push_back(S);
+    }
+  }
+  if (order == 1)
+    std::stable_sort(segs.begin(), segs.end(), [](const wq::BatchSeg &x, const wq::BatchSeg &y) {
+      return cost_rank(x.p, x.cls) < cost_rank(y.p, y.cls);
+    });
+  long long total = 0;
+  for (wq::BatchSeg &S : segs) {
+    S.first_item = (int)total;
+    total += S.nitems;
+  }
+  if (total > 0x7fffffffLL) return WQ_ERR_UNSUPPORTED;
+  if (cudaDeviceSynchronize() != cudaSuccess) return WQ_ERR_CUDA;  // no launch still reads the old list
+  if (!segs.empty() &&
+      cudaMemcpy(B->dev_segs, segs.data(), segs.size() * sizeof(wq::BatchSeg), cudaMemcpyHostToDevice) != cudaSuccess)
+    return WQ_ERR_CUDA;
+  B->nseg = (int)segs.size();
+  B->nitems = (int)total;
+  return WQ_OK;
+}
+
+wq_status enqueue(const wq_batch *B, cudaStream_t s) {
+  if (B->fold_total > 0) {
+    const int blocks = std::min((B->fold_total + 255) / 256, B->nsm * 8);
+    batch_fold_kernel<<<blocks, 256, 0, s>>>(B->dev_fold, B->nfold, B->fold_total, B->dev_status);
+    if (cudaGetLastError() != cudaSuccess) return WQ_ERR_CUDA;
+  }
+  if (cudaMemsetAsync(B->dev_counter, 0, sizeof(unsigned), s) != cudaSuccess) return WQ_ERR_CUDA;
+  const int grid = B->nsm * B->config[2];
+  cudaError_t e = B->prec == WQ_FP64
+                      ? wq::launch_batch<double>(B->dev_segs, B->nseg, B->nitems, B->dev_counter, grid, s)
+                  : B->prec == WQ_MIXED
+                      ? wq::launch_batch<float>(B->dev_segs, B->nseg, B->nitems, B->dev_counter, grid, s)
+                      : wq::launch_batch<wq::dd>(B->dev_segs, B->nseg, B->nitems, B->dev_counter, grid, s);
+  return e == cudaSuccess ? WQ_OK : WQ_ERR_CUDA;
+}
+
+void drop_graph(wq_batch *B) {
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  B->exec = nullptr;
+  B->graph = nullptr;
+}
+
+// Captures fold + counter reset + persistent launch into a CUDA graph.
+wq_status capture(wq_batch *B) {
+  drop_graph(B);
+  if (cudaStreamBeginCapture(B->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return WQ_ERR_CUDA;
+  wq_status st = enqueue(B, B->cap_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(B->cap_stream, &g);
+  if (st != WQ_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return WQ_ERR_CUDA;
+  }
+  B->graph = g;
+  if (cudaGraphInstantiate(&B->exec, g, 0) != cudaSuccess) {
+    drop_graph(B);
+    return WQ_ERR_CUDA;
+  }
+  return WQ_OK;
+}
+
+wq_status apply_config(wq_batch *B, const int *cfg) {
+  int old[4];
+  std::memcpy(old, B->config, sizeof(old));
+  std::memcpy(B->config, cfg, sizeof(old));
+  if (B->config[2] < 1 || B->config[2] > B->max_ctas || (B->config[3] != 0 && B->config[3] != 1)) {
+    std::memcpy(B->config, old, sizeof(old));
+    return WQ_ERR_ARG;
+  }
+  wq_status st = build_segments(B);
+  if (st != WQ_OK) {
+    std::memcpy(B->config, old, sizeof(old));
+    build_segments(B);
+    return st;
+  }
+  return capture(B);
+}
+
+void destroy(wq_batch *B) {
+  if (!B) return;
+  drop_graph(B);
+  if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
+  if (B->dev_block) cudaFree(B->dev_block);
+  delete B;
+}
+
+}  // namespace
+
+extern "C" {
+
+wq_status wq_batch_create(const wq_patch *patches, int npatch, wq_precision prec, wq_batch **out) {
+  if (!out) return WQ_ERR_ARG;
+  *out = nullptr;
+  if (!patches || npatch < 1) return WQ_ERR_ARG;
+  if (prec != WQ_FP64 && prec != WQ_MIXED && prec != WQ_DF64) return WQ_ERR_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return WQ_ERR_CUDA;
+  for (int i = 0; i < npatch; i++) {
+    const wq_patch &P = patches[i];
+    const wq_rules *R = P.rules;
+    if (!R || !R->on_device || R->device != dev || R->dim != 3) return WQ_ERR_ARG;
+    if (!P.M || !P.K || !P.geom[0] || !P.geom[1] || !P.geom[2]) return WQ_ERR_ARG;
+  }
+  wq_batch *B = new (std::nothrow) wq_batch();
+  if (!B) return WQ_ERR_OOM;
+  B->npatch = npatch;
+  B->prec = prec;
+  B->device = dev;
+  B->patches.assign(patches, patches + npatch);
+  if (cudaDeviceGetAttribute(&B->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    destroy(B);
+    return WQ_ERR_CUDA;
+  }
+  wq_status st = prepare(B);
+  if (st != WQ_OK) {
+    destroy(B);
+    return st;
+  }
+  // device block layout
+  size_t total = 0;
+  const size_t fold_off = total;
+  total += align_up(sizeof(BFold) * 6 * (size_t)npatch);
+  const size_t seg_off = total;
+  total += align_up(sizeof(wq::BatchSeg) * 2 * (size_t)npatch);
+  const size_t cnt_off = total;
+  total += align_up(2 * sizeof(unsigned));
+  std::vector<size_t> tab_off(6 * (size_t)npatch);
+  for (int i = 0; i < npatch; i++) {
+    const wq_rules *R = patches[i].rules;
+    const size_t np = (size_t)R->p + 1;
+    for (int a = 0; a < 3; a++)
+      for (int k = 0; k < 2; k++) {
+        tab_off[(size_t)i * 6 + a * 2 + k] = total;
+        const size_t m = (size_t)R->dev[a][k].npts * np;
+        total += align_up(m * sizeof(double)) + align_up(m * sizeof(float)) + align_up(m * sizeof(float2));
+      }
+  }
+  if (cudaMalloc(&B->dev_block, total) != cudaSuccess) {
+    cudaGetLastError();
+    destroy(B);
+    return WQ_ERR_OOM;
+  }
+  char *base = static_cast<char *>(B->dev_block);
+  B->dev_fold = reinterpret_cast<BFold *>(base + fold_off);
+  B->dev_segs = reinterpret_cast<wq::BatchSeg *>(base + seg_off);
+  B->dev_counter = reinterpret_cast<unsigned *>(base + cnt_off);
+  B->dev_status = B->dev_counter + 1;
+  std::vector<BFold> folds;
+  int start = 0;
+  B->base_args.resize(npatch);
+  for (int i = 0; i < npatch; i++) {
+    const wq_patch &P = patches[i];
+    const wq_rules *R = P.rules;
+    const size_t np = (size_t)R->p + 1;
+    wq::RowsArgs &ra = B->base_args[i];
+    std::memset(&ra, 0, sizeof(ra));
+    for (int a = 0; a < 3; a++) {
+      for (int k = 0; k < 2; k++) {
+        const wq::DevDirKind &Dk = R->dev[a][k];
+        const size_t m = (size_t)Dk.npts * np;
+        char *t = base + tab_off[(size_t)i * 6 + a * 2 + k];
+        double *v64 = reinterpret_cast<double *>(t);
+        float *v32 = reinterpret_cast<float *>(t + align_up(m * sizeof(double)));
+        float2 *vdd = reinterpret_cast<float2 *>(t + align_up(m * sizeof(double)) + align_up(m * sizeof(float)));
+        BFold F;
+        F.elem = Dk.elem;
+        F.w = Dk.w;
+        F.t0 = Dk.t0;
+        F.t1 = Dk.t1;
+        F.g = P.geom[a];
+        F.v64 = v64;
+        F.v32 = v32;
+        F.vdd = vdd;
+        F.start = start;
+        F.np = (int)np;
+        F.kind = k;
+        start += Dk.npts;
+        folds.push_back(F);
+        ra.off[a][k] = Dk.off;
+        ra.elem[a][k] = Dk.elem;
+        ra.V[a][k] = prec == WQ_FP64 ? (const void *)v64 : prec == WQ_MIXED ? (const void *)v32 : (const void *)vdd;
+        ra.beta[a][k] = prec == WQ_FP64   ? (const void *)Dk.beta
+                        : prec == WQ_MIXED ? (const void *)Dk.beta32 : (const void *)Dk.betadd;
+      }
+      ra.n[a] = R->n[a];
+      ra.N[a] = R->nel[a];
+      ra.nc[a] = R->nc[a];
+    }
+    ra.coef = P.coef;
+    ra.coefR = nullptr;  // checked and converted inside the row kernel
+    ra.M = P.M;
+    ra.K = P.K;
+    ra.row_begin = 0;
+    ra.row_end = (long long)R->n[0] * R->n[1] * R->n[2];
+    ra.status = B->dev_status;
+  }
+  B->nfold = (int)folds.size();
+  B->fold_total = start;
+  bool ok = cudaMemcpy(B->dev_fold, folds.data(), folds.size() * sizeof(BFold), cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && cudaMemset(B->dev_counter, 0, 2 * sizeof(unsigned)) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+  if (!ok) {
+    destroy(B);
+    return WQ_ERR_CUDA;
+  }
+  const int cfg[4] = {wq::kInteriorChunk, wq::kBoundaryChunk, B->max_ctas, 1};
+  st = apply_config(B, cfg);
+  if (st != WQ_OK) {
+    destroy(B);
+    return st;
+  }
+  *out = B;
+  return WQ_OK;
+}
+
+void wq_batch_free(wq_batch *batch) {
+  if (!batch) return;
+  const int dev = batch->device;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != dev) cudaSetDevice(dev);
+  cudaDeviceSynchronize();
+  destroy(batch);
+  if (cur >= 0 && cur != dev) cudaSetDevice(cur);
+}
+
+wq_status wq_batch_launch(wq_batch *B, void *stream) {
+  if (!B || !B->exec) return WQ_ERR_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != B->device) return WQ_ERR_ARG;
+  return cudaGraphLaunch(B->exec, static_cast<cudaStream_t>(stream)) == cudaSuccess ? WQ_OK : WQ_ERR_CUDA;
+}
+
+wq_status wq_batch_status(wq_batch *B, void *stream) {
+  if (!B) return WQ_ERR_ARG;
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return WQ_ERR_CUDA;
+  unsigned bits = 0;
+  if (cudaMemcpy(&bits, B->dev_status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return WQ_ERR_CUDA;
+  if (cudaMemset(B->dev_status, 0, sizeof(unsigned)) != cudaSuccess) return WQ_ERR_CUDA;
+  if (bits & wq::kBitNonFinite) return WQ_ERR_NONFINITE;
+  if (bits & wq::kBitGeometry) return WQ_ERR_GEOMETRY;
+  return WQ_OK;
+}
+
+wq_status wq_batch_get_config(const wq_batch *B, int *config) {
+  if (!B || !config) return WQ_ERR_ARG;
+  std::memcpy(config, B->config, sizeof(B->config));
+  config[4] = B->max_ctas;
+  return WQ_OK;
+}
+
+wq_status wq_batch_set_config(wq_batch *B, const int *config) {
+  if (!B || !config) return WQ_ERR_ARG;
+  return apply_config(B, config);
+}
+
+wq_status wq_batch_tune(wq_batch *B, void *stream, int reps, double *best_ms) {
+  if (!B || reps < 1) return WQ_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int tints[] = {24, 16, 12, 8};
+  const int tbnds[] = {16, 8};
+  std::vector<int> ctas;
+  for (int c = B->max_ctas; c >= 1 && (int)ctas.size() < 2; c--) ctas.push_back(c);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return WQ_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return WQ_ERR_CUDA;
+  }
+  int best[4];
+  std::memcpy(best, B->config, sizeof(best));
+  float best_t = -1.0f;
+  wq_status st = WQ_OK;
+  for (int order = 0; order < 2 && st == WQ_OK; order++)
+    for (int c : ctas)
+      for (int ti : tints)
+        for (int tb : tbnds) {
+          if (st != WQ_OK) break;
+          const int cfg[4] = {ti, tb, c, order};
+          std::memcpy(B->config, cfg, sizeof(cfg));
+          if (build_segments(B) != WQ_OK) continue;  // a chunk length this batch's tables do not fit
+          st = enqueue(B, s);  // warm-up
+          float tsum = 0.0f;
+          for (int r = 0; r < reps && st == WQ_OK; r++) {
+            cudaEventRecord(e0, s);
+            st = enqueue(B, s);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = WQ_ERR_CUDA;
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            tsum += ms;
+          }
+          if (st == WQ_OK && (best_t < 0.0f || tsum / reps < best_t)) {
+            best_t = tsum / reps;
+            std::memcpy(best, cfg, sizeof(best));
+          }
+        }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != WQ_OK) return st;
+  if (best_ms) *best_ms = best_t;
+  return apply_config(B, best);
+}
+
+wq_status wq_assemble_batch(const wq_patch *patches, int npatch, wq_precision prec, void *stream) {
+  wq_batch *B = nullptr;
+  wq_status st = wq_batch_create(patches, npatch, prec, &B);
+  if (st != WQ_OK) return st;
+  st = wq_batch_launch(B, stream);
+  if (st == WQ_OK) st = wq_batch_status(B, stream);
+  wq_batch_free(B);
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,154 @@
+"""Batched assembly (wq_batch_*): one persistent launch for many patches,
+replayed from a CUDA graph, with an autotuned launch configuration.
+
+Every patch's bands must be bit-identical to a single-patch
+wq_assemble_mass_stiffness call in the same precision (the batch runs the
+same per-chunk arithmetic), whatever the chunk lengths, CTA count or item
+order; a few patches are also compared with the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1710_01048_gb300 import binding as wq
+from paper_1710_01048_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SMALL = [(2, (6, 5, 4)), (3, (14, 9, 7)), (3, (1, 1, 1)), (2, (3, 12, 2)), (3, (25, 4, 6)), (2, (9, 9, 9)),
+         (3, (2, 3, 11)), (3, (14, 9, 7))]  # the last shares its mesh with the second
+
+
+def make_patches(specs, prec, seed=0):
+    dt = torch.float32 if prec == "mixed" else torch.float64
+    rules_cache, patches, host = {}, [], []
+    for i, (p, nel) in enumerate(specs):
+        key = (p, nel)
+        if key not in rules_cache:
+            rules_cache[key] = wq.Rules(3, p, nel)
+        R = rules_cache[key]
+        g, c = inputs.make(3, p, nel, 0.02 + 0.01 * (i % 5), "exp", 0.1, seed=seed + i)
+        gd = [torch.from_numpy(x).cuda() for x in g]
+        cd = torch.from_numpy(c).cuda()
+        M = torch.full((R.rows, R.band), float("nan"), dtype=dt, device="cuda")
+        K = torch.full((R.rows, R.band), float("nan"), dtype=dt, device="cuda")
+        patches.append((R, gd, cd, M, K))
+        host.append((g, c))
+    return patches, host
+
+
+def assert_matches_single(patches, prec):
+    for R, gd, cd, M, K in patches:
+        Ms, Ks = wq.assemble(R, gd, cd, prec)
+        assert torch.equal(M, Ms) and torch.equal(K, Ks)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64", "mixed"])
+def test_batch_equals_single_patch_calls(prec):
+    patches, host = make_patches(SMALL, prec)
+    B = wq.Batch(patches, prec)
+    B.launch()
+    B.check()
+    assert_matches_single(patches, prec)
+    if prec == "fp64":
+        for k in (1, 4):
+            R, _, _, M, K = patches[k]
+            g, c = host[k]
+            Mo, Ko, _ = oracle.assemble(3, R.degree, R.nel, g, c)
+            for A, O in ((M, Mo), (K, Ko)):
+                d = A.cpu().numpy() - O
+                assert np.max(np.abs(d)) <= 1e-12 * np.max(np.abs(O))
+    B.close()
+
+
+def test_batch_configurations_and_tuner():
+    patches, _ = make_patches(SMALL, "fp64", seed=3)
+    B = wq.Batch(patches, "fp64")
+    mx = B.config["max_ctas_per_sm"]
+    assert mx >= 1
+    for cfg in [(24, 16, mx, 1), (8, 8, 1, 0), (13, 5, mx, 0), (1, 1, 1, 1)]:
+        for _, _, _, M, K in patches:
+            M.fill_(float("nan"))
+            K.fill_(float("nan"))
+        B.set_config(*cfg)
+        c = B.config
+        assert (c["chunk_interior"], c["chunk_boundary"], c["ctas_per_sm"], c["order"]) == cfg
+        B.launch()
+        B.check()
+        assert_matches_single(patches, "fp64")
+    with pytest.raises(wq.WqError):
+        B.set_config(25, 16, 1, 0)  # longer than the compiled chunk capacity
+    with pytest.raises(wq.WqError):
+        B.set_config(24, 16, mx + 1, 0)
+    ms = B.tune(reps=1)
+    assert ms > 0
+    for _, _, _, M, K in patches:
+        M.fill_(float("nan"))
+        K.fill_(float("nan"))
+    B.launch()
+    B.check()
+    assert_matches_single(patches, "fp64")
+    B.close()
+
+
+def test_graph_replay_reads_new_inputs_and_one_shot():
+    patches, _ = make_patches(SMALL[:4], "df64", seed=5)
+    B = wq.Batch(patches, "df64")
+    B.launch()
+    # new coefficient and geometry values in the same buffers
+    for R, gd, cd, M, K in patches:
+        cd.mul_(1.5).add_(0.25)
+        gd[0].mul_(1.1)
+    B.launch()
+    B.check()
+    assert_matches_single(patches, "df64")
+    B.close()
+    for _, _, _, M, K in patches:
+        M.zero_()
+        K.zero_()
+    wq.assemble_batch(patches, "df64")
+    assert_matches_single(patches, "df64")
+
+
+def test_batch_status_and_arguments():
+    patches, _ = make_patches(SMALL[:3], "fp64", seed=7)
+    patches[1][2][5] = float("nan")
+    B = wq.Batch(patches, "fp64")
+    B.launch()
+    assert B.status() == wq.WQ_ERR_NONFINITE
+    patches[1][2][5] = 1.0
+    B.launch()
+    assert B.status() == wq.WQ_OK
+    B.close()
+    # a 2D rules object is rejected
+    R2 = wq.Rules(2, 3, (5, 5))
+    g = [torch.ones(8, dtype=torch.float64, device="cuda")] * 3
+    M = torch.empty((R2.rows, R2.band), dtype=torch.float64, device="cuda")
+    with pytest.raises(wq.WqError) as ei:
+        wq.Batch([(R2, g, None, M, M)], "fp64")
+    assert ei.value.status == wq.WQ_ERR_ARG
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_256_patches(prec):
+    # 256 patches, element counts log-uniform in [8, 48] per direction,
+    # degree 2 or 3, geometry amplitude U[0, 0.08]
+    specs = inputs.batch_patches(256, seed=0)
+    dt = torch.float32 if prec == "mixed" else torch.float64
+    rules, patches = {}, []
+    for s in specs:
+        key = (s["p"], s["nel"])
+        if key not in rules:
+            rules[key] = wq.Rules(3, s["p"], s["nel"])
+        R = rules[key]
+        gd = [torch.from_numpy(x).cuda() for x in s["geom"]]
+        cd = torch.from_numpy(s["coef"]).cuda()
+        M = torch.empty((R.rows, R.band), dtype=dt, device="cuda")
+        K = torch.empty((R.rows, R.band), dtype=dt, device="cuda")
+        patches.append((R, gd, cd, M, K))
+    B = wq.Batch(patches, prec)
+    B.tune(reps=1)
+    B.launch()
+    B.check()
+    assert_matches_single(patches, prec)
+    B.close()
