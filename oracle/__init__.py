@@ -67,6 +67,8 @@ def _load():
     lib.wqo_assemble_gl.argtypes = [I, I, PI, PD, PD, PD, PD, I, LL, LL, PD, PD, I]
     lib.wqo_gradient.argtypes = [I, I, PI, PD, PD, PD, PD, PD, PD]
     lib.wqo_row_points.argtypes = [I, I, I, I, PD, PD]
+    lib.wqo_rule_nc.argtypes = [I, I, PD, PD, PD]
+    lib.wqo_assemble_rule.argtypes = [I, I, I, PI, PD, PD, PD, PD, LL, LL, PD, PD, I]
     _lib = lib
     return lib
 
@@ -142,6 +144,43 @@ def rule_newton(p: int, kind: int, u0, shifts):
     st = _load().wqo_rule_newton(p, kind, _pd(u), len(u), ds.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                                  _pd(tau), _pd(om), ctypes.byref(res))
     return st, tau, om, res.value
+
+
+def rule_nc(p: int, kind: int):
+    """The Newton-Cotes-type weighted rule on the cardinal support: nodes y
+    (knots and element midpoints, 2p+1) and weights v with the weight
+    function's value folded in; the stiffness rule's centre weight is 0.
+    Returns (y, v, max residual of the 2p+1 exactness conditions)."""
+    y = np.zeros(2 * p + 1)
+    v = np.zeros(2 * p + 1)
+    res = ctypes.c_double(0.0)
+    st = _load().wqo_rule_nc(p, kind, _pd(y), _pd(v), ctypes.byref(res))
+    if st:
+        raise RuntimeError(f"oracle NC rule failed (status {st})")
+    return y, v, res.value
+
+
+def assemble_rule(mode, dim, p, nel, geom, coef=None, row_begin=0, row_end=None, mass=True, stiffness=True,
+                  threads=0):
+    """assemble() with the comparison rules: mode 'gl' = (p+1)-point
+    Gauss-Legendre on every element of supp B_r for every row, 'nc' = the
+    Newton-Cotes-type weighted rules on interior rows.  Returns (M, K)."""
+    code = {"gl": 1, "nc": 2}[mode]
+    nel = [int(v) for v in nel]
+    n = [nel[a] + p for a in range(dim)]
+    nrows = int(np.prod(n))
+    if row_end is None:
+        row_end = nrows
+    band = (2 * p + 1) ** dim
+    M = np.zeros((row_end - row_begin, band)) if mass else None
+    K = np.zeros((row_end - row_begin, band)) if stiffness else None
+    g = _geom_args(dim, geom)
+    nel_c = (ctypes.c_int * 3)(*(nel + [1] * (3 - dim)))
+    st = _load().wqo_assemble_rule(code, dim, p, nel_c, _pd(g[0]), _pd(g[1]), _pd(g[2]), _pd(_f64(coef)), row_begin,
+                                   row_end, _pd(M), _pd(K), int(threads))
+    if st:
+        raise RuntimeError(f"oracle assemble_rule failed (status {st})")
+    return M, K
 
 
 def row_points(p: int, nel: int, kind: int, r: int):

@@ -40,7 +40,7 @@
 #endif
 
 #define MAXP 3
-#define MAXL (MAXP * (MAXP + 1)) /* most rule points of one row in one direction */
+#define MAXL ((MAXP + 1) * (MAXP + 1)) /* most rule points of one row in one direction (RULE_GL) */
 #define MAXKNOTS 4096
 
 /* ------------------------------------------------------------------ */
@@ -339,6 +339,45 @@ int wqo_rule_newton(int p, int nu, double *u, int n, const int *ds, double *tau,
 }
 
 /* ------------------------------------------------------------------ */
+/* Newton-Cotes-type weighted rules (the comparison rules of Sec. 1, 4) */
+/* ------------------------------------------------------------------ */
+
+/* The row-wise weighted rules of Newton-Cotes type that Sec. 1 and Sec. 4
+ * compare against: on the cardinal support [0, p+1], nodes at the interior
+ * knots and the element midpoints, y_k = (k+1)/2 for k = 0..2p, and weights
+ * v_k with the weight function's value folded in, such that
+ *   sum_k v_k N^(nu)(y_k - d) = int N^(nu)(y) N^(nu)(y - d) dy,  d = -p..p
+ * (one node per interacting function, so the system is square and linear).
+ * Stiffness: N'(y) vanishes at the centre y = (p+1)/2, so that node gets
+ * weight 0 and the other 2p weights solve the conditions d = -p..p-1; the
+ * last one then holds because the translates' derivatives sum to zero.
+ * Returns 0 when all 2p+1 conditions hold to 1e-14 (*max_resid). */
+int wqo_rule_nc(int p, int nu, double *y, double *v, double *max_resid) {
+  if (p < 2 || p > MAXP || (nu != 0 && nu != 1)) return 2;
+  int nn = 2 * p + 1, centre = p;
+  for (int k = 0; k < nn; k++) { y[k] = 0.5 * (double)(k + 1); v[k] = 0.0; }
+  int cols[2 * MAXP + 1], nu_k = 0;
+  for (int k = 0; k < nn; k++)
+    if (!(nu == 1 && k == centre)) cols[nu_k++] = k;
+  double A[(2 * MAXP + 1) * (2 * MAXP + 1)], b[2 * MAXP + 1];
+  for (int e = 0; e < nu_k; e++) {
+    int d = -p + e;
+    for (int j = 0; j < nu_k; j++) A[e * nu_k + j] = cardinal(p, nu, y[cols[j]] - (double)d);
+    b[e] = moment(p, nu, d);
+  }
+  if (solve_dense(nu_k, A, b)) return 3;
+  for (int j = 0; j < nu_k; j++) v[cols[j]] = b[j];
+  double mr = 0.0;
+  for (int d = -p; d <= p; d++) {
+    double sres = -moment(p, nu, d);
+    for (int k = 0; k < nn; k++) sres += v[k] * cardinal(p, nu, y[k] - (double)d);
+    if (!(fabs(sres) <= mr)) mr = fabs(sres);
+  }
+  if (max_resid) *max_resid = mr;
+  return mr <= 1e-14 ? 0 : 3;
+}
+
+/* ------------------------------------------------------------------ */
 /* Per-row 1D rules                                                    */
 /* ------------------------------------------------------------------ */
 
@@ -358,19 +397,53 @@ static int dir_init(dir1d *D, int p, int N) {
   return 0;
 }
 
+/* Which rule the interior rows use: the weighted Gaussian rules of Sec. 3
+ * (the method), Gauss-Legendre on every element of supp B_r for every row
+ * (the element-wise Gauss point set), or the Newton-Cotes-type weighted
+ * rules (wqo_rule_nc).  Rows touching the boundary use Gauss-Legendre in
+ * all three. */
+enum { RULE_WQ = 0, RULE_GL = 1, RULE_NC = 2 };
+
+typedef struct {
+  int mode;
+  double tau[2][2 * MAXP + 1], om[2][2 * MAXP + 1];  /* WQ: nodes and weights; NC: nodes and folded weights */
+} rule_set;
+
+static int rule_set_init(rule_set *S, int p, int mode) {
+  double res;
+  S->mode = mode;
+  for (int nu = 0; nu < 2; nu++) {
+    if (mode == RULE_NC) {
+      if (wqo_rule_nc(p, nu, S->tau[nu], S->om[nu], &res)) return 3;
+    } else if (wqo_rule(p, nu, S->tau[nu], S->om[nu], &res)) {
+      return 3;
+    }
+  }
+  return 0;
+}
+
 /* Quadrature points and weights of row r in one direction.  Interior rows
- * (all knots of B_r distinct: p <= r <= N-1) use the weighted Gaussian rule
- * mapped to supp B_r: x_k = (r - p + tau_k) h, W_k = h omega_k B_r^(nu)(x_k)
- * (the weight function is not folded into omega, Eq. GaussQuadSys).  Other
- * rows use (p+1)-point Gauss-Legendre on each element of supp B_r, W =
- * (h/2) w_g B_r^(nu)(x) (Remark on boundary functions, Sec. 3). */
-static int row_rule(const dir1d *D, const double *tau, const double *om, int nu, int r, double *x, double *W) {
+ * (all knots of B_r distinct: p <= r <= N-1) use, in RULE_WQ, the weighted
+ * Gaussian rule mapped to supp B_r: x_k = (r - p + tau_k) h, W_k = h omega_k
+ * B_r^(nu)(x_k) (the weight function is not folded into omega, Eq.
+ * GaussQuadSys); in RULE_NC the nodes y_k of wqo_rule_nc, W_k = h^(1-nu) v_k
+ * (v_k carries N^(nu)(y_k); B_r^(nu)(x) = h^-nu N^(nu)(y)).  Other rows, and
+ * every row in RULE_GL, use (p+1)-point Gauss-Legendre on each element of
+ * supp B_r, W = (h/2) w_g B_r^(nu)(x) (Remark on boundary functions, Sec. 3). */
+static int row_rule(const dir1d *D, const rule_set *S, int nu, int r, double *x, double *W) {
   int p = D->p;
   double h = D->h;
-  if (r >= p && r <= D->N - 1) {
+  if (S->mode != RULE_GL && r >= p && r <= D->N - 1) {
+    if (S->mode == RULE_NC) {
+      for (int k = 0; k <= 2 * p; k++) {
+        x[k] = ((double)(r - p) + S->tau[nu][k]) * h;
+        W[k] = (nu ? 1.0 : h) * S->om[nu][k];
+      }
+      return 2 * p + 1;
+    }
     for (int k = 0; k <= p; k++) {
-      x[k] = ((double)(r - p) + tau[k]) * h;
-      W[k] = h * om[k] * bspl(D->t, D->nt, r, p, nu, x[k]);
+      x[k] = ((double)(r - p) + S->tau[nu][k]) * h;
+      W[k] = h * S->om[nu][k] * bspl(D->t, D->nt, r, p, nu, x[k]);
     }
     return p + 1;
   }
@@ -388,7 +461,8 @@ static int row_rule(const dir1d *D, const double *tau, const double *om, int nu,
   return L;
 }
 
-/* The element holding x (points are never on element boundaries here). */
+/* The element holding x.  A point on a knot (the Newton-Cotes-type nodes)
+ * may land in either neighbour; the splines evaluated there are continuous. */
 static int element_of(const dir1d *D, double x) {
   int e = (int)floor(x * (double)D->N);
   if (e < 0) e = 0;
@@ -523,20 +597,20 @@ static int setup_problem(problem *P, int dim, int p, const int *nel, const doubl
   return 0;
 }
 
-/* Assembles rows [row_begin, row_end) of M and/or K in band layout with the
- * weighted Gaussian rules.  g1..g3: 1D control values of the separable map
- * (n_a = nel_a + p each); coef: degree-3 coefficient spline on the same mesh
- * (prod (nel_a + 3) values, x fastest) or NULL for c = 1.  Returns 0, 2 for
- * bad arguments, 3 if a rule fails its check. */
-int wqo_assemble(int dim, int p, const int *nel, const double *g1, const double *g2, const double *g3,
-                 const double *coef, long long row_begin, long long row_end, double *M, double *K,
-                 double *offdiag_max, int nthreads) {
+/* Assembles rows [row_begin, row_end) of M and/or K in band layout, each row
+ * with its own rule (mode: RULE_WQ, the weighted Gaussian rules; RULE_GL or
+ * RULE_NC, the comparison rules).  g1..g3: 1D control values of the
+ * separable map (n_a = nel_a + p each); coef: degree-3 coefficient spline on
+ * the same mesh (prod (nel_a + 3) values, x fastest) or NULL for c = 1.
+ * Returns 0, 2 for bad arguments, 3 if a rule fails its check. */
+static int assemble_mode(int mode, int dim, int p, const int *nel, const double *g1, const double *g2,
+                         const double *g3, const double *coef, long long row_begin, long long row_end, double *M,
+                         double *K, double *offdiag_max, int nthreads) {
   problem P;
   int st = setup_problem(&P, dim, p, nel, g1, g2, g3, coef);
   if (st) return st;
-  double tauM[MAXP + 1], omM[MAXP + 1], tauS[MAXP + 1], omS[MAXP + 1], res;
-  if (wqo_rule(p, 0, tauM, omM, &res)) return 3;
-  if (wqo_rule(p, 1, tauS, omS, &res)) return 3;
+  rule_set RS;
+  if (rule_set_init(&RS, p, mode)) return 3;
   int nb = 2 * p + 1;
   int band = 1;
   long long nrows = 1;
@@ -562,7 +636,7 @@ int wqo_assemble(int dim, int p, const int *nel, const double *g1, const double 
           continue;
         }
         const dir1d *D = &P.dir[a];
-        L[a][nu] = row_rule(D, nu ? tauS : tauM, nu ? omS : omM, nu, ri[a], x[a][nu], W[a][nu]);
+        L[a][nu] = row_rule(D, &RS, nu, ri[a], x[a][nu], W[a][nu]);
         for (int k = 0; k < L[a][nu]; k++)
           for (int d = -p; d <= p; d++) {
             int s = ri[a] + d;
@@ -606,6 +680,22 @@ int wqo_assemble(int dim, int p, const int *nel, const double *g1, const double 
   }
   if (offdiag_max) *offdiag_max = offd_all;
   return 0;
+}
+
+int wqo_assemble(int dim, int p, const int *nel, const double *g1, const double *g2, const double *g3,
+                 const double *coef, long long row_begin, long long row_end, double *M, double *K,
+                 double *offdiag_max, int nthreads) {
+  return assemble_mode(RULE_WQ, dim, p, nel, g1, g2, g3, coef, row_begin, row_end, M, K, offdiag_max, nthreads);
+}
+
+/* The same assembly with the comparison rules: mode 1 = Gauss-Legendre on
+ * every element of supp B_r for every row, mode 2 = Newton-Cotes-type
+ * weighted rules on the interior rows. */
+int wqo_assemble_rule(int mode, int dim, int p, const int *nel, const double *g1, const double *g2,
+                      const double *g3, const double *coef, long long row_begin, long long row_end, double *M,
+                      double *K, int nthreads) {
+  if (mode != RULE_GL && mode != RULE_NC) return 2;
+  return assemble_mode(mode, dim, p, nel, g1, g2, g3, coef, row_begin, row_end, M, K, NULL, nthreads);
 }
 
 /* ------------------------------------------------------------------ */
@@ -740,9 +830,8 @@ int wqo_gradient(int dim, int p, const int *nel, const double *g1, const double 
   problem P;
   int st = setup_problem(&P, dim, p, nel, g1, g2, g3, NULL);
   if (st) return st;
-  double tauM[MAXP + 1], omM[MAXP + 1], tauS[MAXP + 1], omS[MAXP + 1], res;
-  if (wqo_rule(p, 0, tauM, omM, &res)) return 3;
-  if (wqo_rule(p, 1, tauS, omS, &res)) return 3;
+  rule_set RS;
+  if (rule_set_init(&RS, p, RULE_WQ)) return 3;
   int nb = 2 * p + 1, band = 1;
   long long nrows = 1, ncoef = 1;
   int n[3] = {1, 1, 1}, nc[3] = {1, 1, 1};
@@ -763,7 +852,7 @@ int wqo_gradient(int dim, int p, const int *nel, const double *g1, const double 
           continue;
         }
         const dir1d *D = &P.dir[a];
-        L[a][nu] = row_rule(D, nu ? tauS : tauM, nu ? omS : omM, nu, ri[a], x[a][nu], W[a][nu]);
+        L[a][nu] = row_rule(D, &RS, nu, ri[a], x[a][nu], W[a][nu]);
         for (int k = 0; k < L[a][nu]; k++)
           for (int d = -p; d <= p; d++) {
             int s = ri[a] + d;
@@ -820,8 +909,8 @@ int wqo_gradient(int dim, int p, const int *nel, const double *g1, const double 
 int wqo_row_points(int p, int N, int nu, int r, double *x, double *W) {
   dir1d D;
   if (dir_init(&D, p, N)) return -1;
-  double tau[MAXP + 1], om[MAXP + 1], res;
-  if (wqo_rule(p, nu, tau, om, &res)) return -1;
+  rule_set RS;
+  if (rule_set_init(&RS, p, RULE_WQ)) return -1;
   if (r < 0 || r >= D.n) return -1;
-  return row_rule(&D, tau, om, nu, r, x, W);
+  return row_rule(&D, &RS, nu, r, x, W);
 }
