@@ -300,6 +300,40 @@ def main():
             del Mv, Kv
         torch.cuda.empty_cache()
 
+        # the comparison rules (FP64, same kernel's general-points class):
+        # Gauss-Legendre on every element of each row's support, and the
+        # Newton-Cotes-type weighted rules; with the quadrature-point counts
+        Mv = torch.empty((rows, band), dtype=torch.float64, device="cuda")
+        Kv = torch.empty((rows, band), dtype=torch.float64, device="cuda")
+        points = {}
+        for mode in ("wq", "nc", "gl"):
+            Rm = R if mode == "wq" else wq.Rules(dim, p, nel, rule=mode)
+            total = 1
+            for a in range(dim):
+                total *= sum(len(Rm.row(a, 0, r)[0]) for r in range(nel[a] + p))
+            points[mode] = {"points_per_interior_row_and_direction": len(Rm.row(0, 0, p)[0]),
+                            "rule_points_total": total}
+            if mode == "wq":
+                continue
+            for _ in range(3):
+                wq.assemble(Rm, gd, cd, "fp64", out=(Mv, Kv), stream=stream, check=False)
+            vms = []
+            for _ in range(max(3, min(args.steps, 5))):
+                flush.fill_(1)
+                v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                v0.record(stream)
+                wq.assemble(Rm, gd, cd, "fp64", out=(Mv, Kv), stream=stream, check=False)
+                v1.record(stream)
+                vms.append((v0, v1))
+            torch.cuda.synchronize()
+            vm = float(np.mean([x.elapsed_time(y) for x, y in vms]))
+            variants["fp64_" + mode + "_rule"] = {"ms_per_step": vm, "value": world * nnz_step / (vm * 1e-3),
+                                                  "unit": "nnz/s", "dtype": "f64", **points[mode]}
+            Rm.close()
+        variants["rule_points"] = points
+        del Mv, Kv
+        torch.cuda.empty_cache()
+
     # end to end through host buffers: pinned inputs H2D, both bands D2H
     gh = [torch.from_numpy(x).pin_memory() for x in g]
     ch = torch.from_numpy(c).pin_memory()

@@ -76,7 +76,17 @@ typedef enum wq_precision {
 } wq_precision;
 
 enum { WQ_KIND_MASS = 0, WQ_KIND_STIFFNESS = 1 };
-enum { WQ_RULES_HOST_ONLY = 0, WQ_RULES_DEVICE = 1 };
+enum {
+  WQ_RULES_HOST_ONLY = 0,
+  WQ_RULES_DEVICE = 1,
+  /* Comparison rules (baselines; at most one, FP64 assembly only, no adjoint
+   * or batch): every row with (p+1)-point Gauss-Legendre on each element of
+   * its support (the element-wise Gauss point set), or the interior rows
+   * with the Newton-Cotes-type weighted rules of Sec. 1 / Sec. 4 (nodes at
+   * the knots and element midpoints of the support, 2p+1 per direction). */
+  WQ_RULES_GAUSS_LEGENDRE = 2,
+  WQ_RULES_NEWTON_COTES = 4
+};
 
 typedef struct wq_mesh {
   int dim;     /* 2 or 3 */
@@ -260,6 +270,27 @@ wq_status wq_batch_tune(wq_batch *batch, void *stream, int reps, double *best_ms
 void wq_batch_free(wq_batch *batch);
 /* One-shot form: create, launch on `stream`, check the status, free. */
 wq_status wq_assemble_batch(const wq_patch *patches, int npatch, wq_precision prec, void *stream);
+
+/*
+ * Valid (in-range column) band entries of rows [row_begin, row_end): the
+ * number of CSR entries of that row range.  Host only; -1 on a bad argument.
+ */
+int64_t wq_band_nnz_rows(const wq_rules *rules, int64_t row_begin, int64_t row_end);
+
+/*
+ * Converts band rows [row_begin, row_end) (the layout written by the
+ * assembly calls, band = device array of (row_end - row_begin) rows, double
+ * for WQ_FP64 and WQ_DF64, float for WQ_MIXED) to CSR on the device:
+ *   rowptr  device, row_end - row_begin + 1 int64, rowptr[0] = 0;
+ *   col     device, wq_band_nnz_rows(...) int32 global column indices,
+ *           increasing within each row;
+ *   val     device, as many values of the band's type.
+ * Only the entries whose column lies inside the mesh are kept (the band's
+ * zeros there are structural, Fig. 1's sparsity pattern).  WQ_ERR_UNSUPPORTED
+ * when the mesh has more than 2^31-1 rows (int32 columns).
+ */
+wq_status wq_band_to_csr(const wq_rules *rules, wq_precision prec, const void *band, int64_t row_begin,
+                         int64_t row_end, int64_t *rowptr, int32_t *col, void *val, void *stream);
 
 /*
  * Synchronises `stream`, then returns and clears the device-detected status

@@ -21,14 +21,15 @@ WQ_ERR_GEOMETRY, WQ_ERR_NONFINITE, WQ_ERR_CUDA, WQ_ERR_OOM, WQ_ERR_TIMEOUT = 4, 
 WQ_FP64, WQ_MIXED, WQ_DF64 = 0, 1, 2
 PRECISIONS = {"fp64": WQ_FP64, "mixed": WQ_MIXED, "df64": WQ_DF64}
 WQ_KIND_MASS, WQ_KIND_STIFFNESS = 0, 1
-WQ_RULES_HOST_ONLY, WQ_RULES_DEVICE = 0, 1
+WQ_RULES_HOST_ONLY, WQ_RULES_DEVICE, WQ_RULES_GAUSS_LEGENDRE, WQ_RULES_NEWTON_COTES = 0, 1, 2, 4
+RULE_FLAGS = {"wq": 0, "gl": WQ_RULES_GAUSS_LEGENDRE, "nc": WQ_RULES_NEWTON_COTES}
 
 # every function declared in include/wq.h
 EXPORTS = ["wq_status_string", "wq_version", "wq_rule_1d", "wq_rule_1d_from", "wq_rules_build", "wq_rules_free",
            "wq_rules_row", "wq_rows", "wq_band_width", "wq_band_nnz", "wq_coef_count", "wq_flop_count",
            "wq_assemble_mass", "wq_assemble_stiffness", "wq_assemble_mass_stiffness", "wq_status_check",
            "wq_assemble_noalloc", "wq_assemble_adjoint", "wq_batch_create", "wq_batch_launch", "wq_batch_status",
-           "wq_batch_get_config", "wq_batch_set_config", "wq_batch_tune", "wq_batch_free", "wq_assemble_batch"]
+           "wq_batch_get_config", "wq_batch_set_config", "wq_batch_tune", "wq_batch_free", "wq_assemble_batch", "wq_band_nnz_rows", "wq_band_to_csr"]
 
 
 class WqError(RuntimeError):
@@ -96,9 +97,12 @@ def _lib():
     lib.wq_batch_free.argtypes = [c_void_p]
     lib.wq_batch_free.restype = None
     lib.wq_assemble_batch.argtypes = [PPatch, c_int, c_int, c_void_p]
+    lib.wq_band_nnz_rows.argtypes = [c_void_p, i64, i64]
+    lib.wq_band_nnz_rows.restype = i64
+    lib.wq_band_to_csr.argtypes = [c_void_p, c_int, c_void_p, i64, i64, c_void_p, c_void_p, c_void_p, c_void_p]
     for f in EXPORTS:
         if f not in ("wq_status_string", "wq_version", "wq_rules_free", "wq_rows", "wq_band_width", "wq_band_nnz",
-                     "wq_coef_count", "wq_flop_count", "wq_batch_free"):
+                     "wq_coef_count", "wq_flop_count", "wq_batch_free", "wq_band_nnz_rows"):
             getattr(lib, f).restype = c_int
     _loaded = lib
     return lib
@@ -231,10 +235,14 @@ def wq_assemble_adjoint(handle, geom_ptrs, prec, G_ptr, H_ptr, grad_ptr, row_beg
 class Rules:
     """Owns a wq_rules handle (host tables, and device tables when device=True)."""
 
-    def __init__(self, dim, degree, nel, device=True):
+    def __init__(self, dim, degree, nel, device=True, rule="wq"):
+        """rule: 'wq' (the weighted Gaussian rules), or the comparison rules
+        'gl' (Gauss-Legendre on every element of each row's support) and 'nc'
+        (Newton-Cotes-type weighted rules on the interior rows)."""
         self.dim, self.degree, self.nel = int(dim), int(degree), tuple(int(v) for v in nel)
-        self.handle = wq_rules_build(self.dim, self.degree, self.nel,
-                                     WQ_RULES_DEVICE if device else WQ_RULES_HOST_ONLY)
+        self.rule = rule
+        flags = (WQ_RULES_DEVICE if device else WQ_RULES_HOST_ONLY) | RULE_FLAGS[rule]
+        self.handle = wq_rules_build(self.dim, self.degree, self.nel, flags)
 
     def close(self):
         if getattr(self, "handle", None):
@@ -451,3 +459,29 @@ def assemble_batch(patches, prec="fp64", stream=None):
     """One-shot batched assembly (wq_assemble_batch) of (rules, geom, coef, M, K) tuples."""
     arr = _patch_array(patches)
     _check(_lib().wq_assemble_batch(arr, len(patches), PRECISIONS[prec], _stream_handle(stream)), "wq_assemble_batch")
+
+
+# ------------------------------------------------------------------ CSR
+def wq_band_nnz_rows(handle, row_begin, row_end):
+    return _lib().wq_band_nnz_rows(handle, row_begin, row_end)
+
+
+def band_to_csr(rules, band, prec="fp64", row_begin=0, row_end=None, stream=None):
+    """CSR (rowptr int64, col int32, val) CUDA tensors of band rows
+    [row_begin, row_end) (wq_band_to_csr)."""
+    import torch
+
+    if row_end is None:
+        row_end = rules.rows
+    nnz = wq_band_nnz_rows(rules.handle, row_begin, row_end)
+    if nnz < 0:
+        raise WqError(WQ_ERR_ARG, "wq_band_nnz_rows")
+    dev = band.device
+    assert band.is_cuda and band.is_contiguous() and tuple(band.shape) == (row_end - row_begin, rules.band)
+    rowptr = torch.empty(row_end - row_begin + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
+    val = torch.empty(max(nnz, 1), dtype=band.dtype, device=dev)
+    _check(_lib().wq_band_to_csr(rules.handle, PRECISIONS[prec], ctypes.c_void_p(band.data_ptr()), row_begin, row_end,
+                                 ctypes.c_void_p(rowptr.data_ptr()), ctypes.c_void_p(col.data_ptr()),
+                                 ctypes.c_void_p(val.data_ptr()), _stream_handle(stream)), "wq_band_to_csr")
+    return rowptr, col[:nnz], val[:nnz]

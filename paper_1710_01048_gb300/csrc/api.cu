@@ -226,8 +226,9 @@ int chunk_class(const wq_rules *R, int cls, int64_t rb, int64_t re, wq::RowsArgs
   auto hi = std::upper_bound(lines.begin(), lines.end(), last_line);
   const int nl = (int)(hi - lo);
   if (nl <= 0) return 0;
-  const int tmax = cls == 0 ? wq::kInteriorChunk : wq::kBoundaryChunk;
-  if (R->max_chunk_points[cls] > wq::chunk_points_bound(R->p, tmax)) {
+  const int tmax = R->mode ? wq::kGeneralChunk : cls == 0 ? wq::kInteriorChunk : wq::kBoundaryChunk;
+  const int bound = R->mode ? wq::chunk_points_bound_general(R->p, tmax) : wq::chunk_points_bound(R->p, tmax);
+  if (R->max_chunk_points[cls] > bound) {
     *st = WQ_ERR_UNSUPPORTED;
     return 0;
   }
@@ -242,6 +243,7 @@ wq_status assemble(const wq_rules *R, const double *const *geom, const double *c
   if (!R || !geom) return WQ_ERR_ARG;
   if (!R->on_device) return WQ_ERR_ARG;
   if (prec != WQ_FP64 && prec != WQ_MIXED && prec != WQ_DF64) return WQ_ERR_ARG;
+  if (R->mode != wq::kModeWQ && prec != WQ_FP64) return WQ_ERR_UNSUPPORTED;
   int64_t rows = (int64_t)R->n[0] * R->n[1] * R->n[2];
   if (rb < 0 || re > rows || rb > re) return WQ_ERR_ARG;
   if (rb != re && !M && !K) return WQ_ERR_ARG;
@@ -277,14 +279,15 @@ wq_status assemble(const wq_rules *R, const double *const *geom, const double *c
     if (nblocks == 0) continue;
     cudaError_t e;
     bool dm = M != nullptr, dk = K != nullptr;
+    const int kcls = R->mode ? 2 : cls;
     if (R->p == 2)
-      e = prec == WQ_FP64   ? wq::launch_rows<2, double>(R->dim, dm, dk, cls, ra, nblocks, s)
-          : prec == WQ_MIXED ? wq::launch_rows<2, float>(R->dim, dm, dk, cls, ra, nblocks, s)
-                             : wq::launch_rows<2, wq::dd>(R->dim, dm, dk, cls, ra, nblocks, s);
+      e = prec == WQ_FP64   ? wq::launch_rows<2, double>(R->dim, dm, dk, kcls, ra, nblocks, s)
+          : prec == WQ_MIXED ? wq::launch_rows<2, float>(R->dim, dm, dk, kcls, ra, nblocks, s)
+                             : wq::launch_rows<2, wq::dd>(R->dim, dm, dk, kcls, ra, nblocks, s);
     else
-      e = prec == WQ_FP64   ? wq::launch_rows<3, double>(R->dim, dm, dk, cls, ra, nblocks, s)
-          : prec == WQ_MIXED ? wq::launch_rows<3, float>(R->dim, dm, dk, cls, ra, nblocks, s)
-                             : wq::launch_rows<3, wq::dd>(R->dim, dm, dk, cls, ra, nblocks, s);
+      e = prec == WQ_FP64   ? wq::launch_rows<3, double>(R->dim, dm, dk, kcls, ra, nblocks, s)
+          : prec == WQ_MIXED ? wq::launch_rows<3, float>(R->dim, dm, dk, kcls, ra, nblocks, s)
+                             : wq::launch_rows<3, wq::dd>(R->dim, dm, dk, kcls, ra, nblocks, s);
     if (e != cudaSuccess) return WQ_ERR_CUDA;
   }
   return WQ_OK;
@@ -327,7 +330,9 @@ wq_status wq_rules_build(const wq_mesh *mesh, int flags, wq_rules **out) {
   if (!mesh || !out) return WQ_ERR_ARG;
   *out = nullptr;
   if (mesh->dim < 2 || mesh->dim > 3 || mesh->degree < 2 || mesh->degree > wq::kMaxP) return WQ_ERR_UNSUPPORTED;
-  if (flags != WQ_RULES_HOST_ONLY && flags != WQ_RULES_DEVICE) return WQ_ERR_ARG;
+  const int rule_bits = flags & (WQ_RULES_GAUSS_LEGENDRE | WQ_RULES_NEWTON_COTES);
+  if ((flags & ~(WQ_RULES_DEVICE | WQ_RULES_GAUSS_LEGENDRE | WQ_RULES_NEWTON_COTES)) != 0) return WQ_ERR_ARG;
+  if (rule_bits == (WQ_RULES_GAUSS_LEGENDRE | WQ_RULES_NEWTON_COTES)) return WQ_ERR_ARG;
   for (int a = 0; a < mesh->dim; a++) {
     if (mesh->nel[a] < 1) return WQ_ERR_ARG;
     if (mesh->nel[a] > wq::kMaxNel) return WQ_ERR_UNSUPPORTED;
@@ -341,15 +346,17 @@ wq_status wq_rules_build(const wq_mesh *mesh, int flags, wq_rules **out) {
     R->mesh = *mesh;
     R->p = mesh->degree;
     R->dim = mesh->dim;
-    R->chunk_rows[0] = wq::kInteriorChunk;
-    R->chunk_rows[1] = wq::kBoundaryChunk;
+    R->mode = rule_bits == WQ_RULES_GAUSS_LEGENDRE ? wq::kModeGL
+              : rule_bits == WQ_RULES_NEWTON_COTES   ? wq::kModeNC : wq::kModeWQ;
+    R->chunk_rows[0] = R->mode ? wq::kGeneralChunk : wq::kInteriorChunk;
+    R->chunk_rows[1] = R->mode ? wq::kGeneralChunk : wq::kBoundaryChunk;
     for (int a = 0; a < 3; a++) {
       R->nel[a] = a < mesh->dim ? mesh->nel[a] : 1;
       R->n[a] = a < mesh->dim ? mesh->nel[a] + mesh->degree : 1;
       R->nc[a] = a < mesh->dim ? mesh->nel[a] + wq::kCoefDeg : 1;
     }
     wq_status st = wq::build_host_tables(R);
-    if (st == WQ_OK && flags == WQ_RULES_DEVICE) st = upload(R);
+    if (st == WQ_OK && (flags & WQ_RULES_DEVICE)) st = upload(R);
     if (st != WQ_OK) {
       delete R;
       return st;
@@ -442,6 +449,7 @@ wq_status wq_assemble_adjoint(const wq_rules *R, const double *const *geom, wq_p
                               const void *H, double *grad, int64_t row_begin, int64_t row_end, void *stream) {
   if (!R || !geom || !grad) return WQ_ERR_ARG;
   if (!R->on_device) return WQ_ERR_ARG;
+  if (R->mode != wq::kModeWQ) return WQ_ERR_UNSUPPORTED;
   if (prec != WQ_FP64 && prec != WQ_MIXED && prec != WQ_DF64) return WQ_ERR_ARG;
   const int64_t rows = (int64_t)R->n[0] * R->n[1] * R->n[2];
   if (row_begin < 0 || row_end > rows || row_begin > row_end) return WQ_ERR_ARG;

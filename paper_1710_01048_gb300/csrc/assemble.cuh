@@ -115,7 +115,10 @@ struct RowsLayout {
   static constexpr int NL3 = (D == 3) ? NL : 1;
   static constexpr int NW = kRowsWarps;
   static constexpr int NT = 32 * NW;
-  static constexpr int MAXPTS1 = TMAX * NP + P * NP * (P - 1);  // x1 points of a chunk's rows
+  // general class (the comparison rules): up to (P+1)^2 points per row and
+  // direction, every row through the general x1 path
+  static constexpr bool GENERAL = (LM > P * (P + 1));
+  static constexpr int MAXPTS1 = GENERAL ? TMAX * NP * NP : TMAX * NP + P * NP * (P - 1);  // x1 points of a chunk
   // per-warp scratch: phase A's column work (Z/Cq, then T3) or phase B's band stage
   static constexpr int WZ = (D == 3) ? NK3 * NL * LM : 0;
   static constexpr int WC = (D == 3) ? NCOMBO * LM * NB : NCOMBO * LM;
@@ -430,7 +433,7 @@ __device__ __forceinline__ void rows_block(const RowsArgs &A, const int bid, uns
     const R *bs0 = &sB1[(1 * L::MAXPTS1 + q0) * 4];
     const R *vm0 = &sV1[(0 * L::MAXPTS1 + q0) * NP];
     const R *vs0 = &sV1[(1 * L::MAXPTS1 + q0) * NP];
-    if (r1 >= P && r1 <= A.N[0] - 1) {
+    if (!L::GENERAL && r1 >= P && r1 <= A.N[0] - 1) {
       // weighted Gaussian rule in x1: point q in element r1-P+q, band offset q;
       // sliding windows over the coefficient columns (w) and the entries j1 (acc)
       const int kb = (r1 - P) - l1lo;

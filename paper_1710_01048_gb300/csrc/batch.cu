@@ -214,7 +214,7 @@ wq_status wq_batch_create(const wq_patch *patches, int npatch, wq_precision prec
   for (int i = 0; i < npatch; i++) {
     const wq_patch &P = patches[i];
     const wq_rules *R = P.rules;
-    if (!R || !R->on_device || R->device != dev || R->dim != 3) return WQ_ERR_ARG;
+    if (!R || !R->on_device || R->device != dev || R->dim != 3 || R->mode != wq::kModeWQ) return WQ_ERR_ARG;
     if (!P.M || !P.K || !P.geom[0] || !P.geom[1] || !P.geom[2]) return WQ_ERR_ARG;
   }
   wq_batch *B = new (std::nothrow) wq_batch();

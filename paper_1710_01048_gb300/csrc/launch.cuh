@@ -12,15 +12,18 @@ namespace wq {
 
 constexpr int kInteriorChunk = 24;
 constexpr int kBoundaryChunk = 16;
+constexpr int kGeneralChunk = 8;  // the comparison rules (kernel class 2)
 
 // Upper bound on the x1 points of one chunk's rows that the kernel's shared
 // memory holds (checked by the host against the actual tables).
 constexpr int chunk_points_bound(int p, int tmax) { return tmax * (p + 1) + p * (p + 1) * (p - 1); }
+constexpr int chunk_points_bound_general(int p, int tmax) { return tmax * (p + 1) * (p + 1); }
 
 template <int P, int D, int LM, int TMAX, bool DO_M, bool DO_K, typename R>
 cudaError_t launch_one(const RowsArgs &a, int nblocks, cudaStream_t s) {
   using L = RowsLayout<P, D, LM, TMAX, DO_M, DO_K, R>;
-  static_assert(L::MAXPTS1 == chunk_points_bound(P, TMAX), "chunk bound");
+  static_assert(L::MAXPTS1 == (L::GENERAL ? chunk_points_bound_general(P, TMAX) : chunk_points_bound(P, TMAX)),
+                "chunk bound");
   auto kern = rows_kernel<P, D, LM, TMAX, DO_M, DO_K, R>;
   static bool configured = false;  // one attribute call per instantiation and process
   if (!configured) {
@@ -36,7 +39,11 @@ cudaError_t launch_one(const RowsArgs &a, int nblocks, cudaStream_t s) {
 template <int P, int D, bool DO_M, bool DO_K, typename R>
 cudaError_t launch_class(int cls, const RowsArgs &a, int nblocks, cudaStream_t s) {
   if (cls == 0) return launch_one<P, D, P + 1, kInteriorChunk, DO_M, DO_K, R>(a, nblocks, s);
-  return launch_one<P, D, P *(P + 1), kBoundaryChunk, DO_M, DO_K, R>(a, nblocks, s);
+  if (cls == 1) return launch_one<P, D, P *(P + 1), kBoundaryChunk, DO_M, DO_K, R>(a, nblocks, s);
+  // class 2, the comparison rules: FP64 only
+  if constexpr (std::is_same<R, double>::value)
+    return launch_one<P, D, (P + 1) * (P + 1), kGeneralChunk, DO_M, DO_K, R>(a, nblocks, s);
+  return cudaErrorNotSupported;
 }
 
 template <int P, typename R>

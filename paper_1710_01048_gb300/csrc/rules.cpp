@@ -304,12 +304,68 @@ void basis(const std::vector<double> &t, int q, int e, double x, double *val, do
 
 }  // namespace
 
+// Newton-Cotes-type weighted rule on the cardinal support [0, p+1] (the
+// comparison rules of Sec. 1 and Sec. 4): nodes at the interior knots and the
+// element midpoints, y_k = (k+1)/2, k = 0..2p, one per interacting function;
+// weights v_k (the weight function's value folded in) from the square linear
+// system sum_k v_k N^(nu)(y_k - d) = exact moment(d), d = -p..p.  For the
+// stiffness kind N' vanishes at the centre y = (p+1)/2: its weight is 0 and
+// the other 2p weights solve d = -p..p-1 (the translates' derivatives sum to
+// zero, so d = p follows).  All 2p+1 conditions are checked to 1e-14.
+wq_status nc_rule(int p, int kind, double *y, double *v) {
+  const int nn = 2 * p + 1, centre = p;
+  int cols[2 * kMaxP + 1], m = 0;
+  for (int k = 0; k < nn; k++) {
+    y[k] = 0.5 * (double)(k + 1);
+    v[k] = 0.0;
+    if (!(kind == WQ_KIND_STIFFNESS && k == centre)) cols[m++] = k;
+  }
+  // Gaussian elimination with partial pivoting on the m x m system
+  double A[2 * kMaxP + 1][2 * kMaxP + 1], b[2 * kMaxP + 1];
+  for (int e = 0; e < m; e++) {
+    const int d = -p + e;
+    for (int j = 0; j < m; j++) A[e][j] = cardinal(p, kind, y[cols[j]] - (double)d);
+    b[e] = exact_moment(p, kind, d);
+  }
+  for (int c = 0; c < m; c++) {
+    int piv = c;
+    for (int r = c + 1; r < m; r++)
+      if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+    if (A[piv][c] == 0.0) return WQ_ERR_NO_CONVERGENCE;
+    for (int k = 0; k < m; k++) std::swap(A[c][k], A[piv][k]);
+    std::swap(b[c], b[piv]);
+    for (int r = c + 1; r < m; r++) {
+      const double f = A[r][c] / A[c][c];
+      for (int k = c; k < m; k++) A[r][k] -= f * A[c][k];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int r = m - 1; r >= 0; r--) {
+    double acc = b[r];
+    for (int k = r + 1; k < m; k++) acc -= A[r][k] * b[k];
+    b[r] = acc / A[r][r];
+  }
+  for (int j = 0; j < m; j++) v[cols[j]] = b[j];
+  for (int d = -p; d <= p; d++) {
+    double res = -exact_moment(p, kind, d);
+    for (int k = 0; k < nn; k++) res += v[k] * cardinal(p, kind, y[k] - (double)d);
+    if (!(std::fabs(res) <= 1e-14)) return WQ_ERR_NO_CONVERGENCE;
+  }
+  return WQ_OK;
+}
+
 wq_status build_host_tables(wq_rules *R) {
   int p = R->p;
   for (int kind = 0; kind < 2; kind++) {
     wq_status st = default_rule(p, kind, R->tau[kind], R->omega[kind]);
     if (st != WQ_OK) return st;
   }
+  double ncy[2][2 * kMaxP + 1], ncv[2][2 * kMaxP + 1];
+  if (R->mode == kModeNC)
+    for (int kind = 0; kind < 2; kind++) {
+      wq_status st = nc_rule(p, kind, ncy[kind], ncv[kind]);
+      if (st != WQ_OK) return st;
+    }
   double gx[4], gw[4];
   gauss_legendre(p + 1, gx, gw);
   for (int a = 0; a < R->dim; a++) {
@@ -325,11 +381,20 @@ wq_status build_host_tables(wq_rules *R) {
         // points of row r: (element, x, weight factor before B_r)
         std::vector<int> pe;
         std::vector<double> px, pf;
-        if (r >= p && r <= N - 1) {
+        bool folded = false;  // pf already holds the combined weight W
+        if (R->mode == kModeWQ && r >= p && r <= N - 1) {
           for (int k = 0; k <= p; k++) {
             pe.push_back(r - p + k);
             px.push_back(((double)(r - p) + R->tau[kind][k]) * h);
             pf.push_back(h * R->omega[kind][k]);
+          }
+        } else if (R->mode == kModeNC && r >= p && r <= N - 1) {
+          // W = h v (mass) or v (stiffness): B_r^(nu)(x) = h^-nu N^(nu)(y)
+          folded = true;
+          for (int k = 0; k <= 2 * p; k++) {
+            pe.push_back(r - p + (int)std::floor(ncy[kind][k]));
+            px.push_back(((double)(r - p) + ncy[kind][k]) * h);
+            pf.push_back(kind == WQ_KIND_MASS ? h * ncv[kind][k] : ncv[kind][k]);
           }
         } else {
           int elo = std::max(0, r - p), ehi = std::min(N - 1, r);
@@ -347,7 +412,7 @@ wq_status build_host_tables(wq_rules *R) {
           basis(tp, p, e, x, v, dv);
           basis(tc, kCoefDeg, e, x, cv, cd);
           int j = r - e;  // B_r among B_e..B_{e+p}
-          double br = kind == WQ_KIND_MASS ? v[j] : dv[j];
+          double br = folded ? 1.0 : (kind == WQ_KIND_MASS ? v[j] : dv[j]);
           H.elem.push_back(e);
           H.x.push_back(x);
           H.w.push_back(pf[q] * br);

@@ -16,6 +16,9 @@ constexpr int kMaxRowPts = kMaxP * (kMaxP + 1);  // most points of one row in on
 constexpr int kCoefDeg = 3;                      // the coefficient field is a cubic spline
 constexpr int kMaxNel = 1 << 16;
 
+// Rule modes (wq_rules_build flags): the method, and the two comparison rules.
+constexpr int kModeWQ = 0, kModeGL = 1, kModeNC = 2;
+
 // Status bits raised by the kernels.
 constexpr unsigned kBitGeometry = 1u;
 constexpr unsigned kBitNonFinite = 2u;
@@ -59,6 +62,7 @@ struct Lines {
 struct wq_rules {
   wq_mesh mesh;
   int p = 0, dim = 0;
+  int mode = 0;  // 0: weighted Gaussian rules; 1: Gauss-Legendre rows; 2: Newton-Cotes-type rows
   int nel[3] = {1, 1, 1};
   int n[3] = {1, 1, 1};
   int nc[3] = {1, 1, 1};
@@ -86,6 +90,7 @@ namespace wq {
 wq_status solve_rule(int p, int kind, const double *start, double *tau, double *omega);
 wq_status default_rule(int p, int kind, double *tau, double *omega);
 wq_status build_host_tables(wq_rules *R);
+wq_status nc_rule(int p, int kind, double *y, double *v);
 double flop_count(const wq_rules *R, int want_m, int want_k, int64_t row_begin, int64_t row_end,
                   double *coef_flops);
 }  // namespace wq

@@ -12,6 +12,7 @@ import oracle
 from conftest import ROOT, read_golden
 from paper_1710_01048_gb300 import binding as wq
 from paper_1710_01048_gb300 import build as wqbuild
+from paper_1710_01048_gb300 import inputs
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -152,3 +153,67 @@ def test_argument_validation():
     with pytest.raises(wq.WqError):
         R.row(3, 0, 0)
     R.close()
+
+
+def test_band_nnz_rows_matches_mask():
+    # the closed-form CSR row pointer against the band mask's running sum
+    rng = np.random.default_rng(0)
+    for dim, p, nel in [(3, 3, (5, 4, 6)), (3, 2, (1, 1, 1)), (2, 3, (7, 3)), (3, 3, (12, 2, 9)), (2, 2, (1, 5))]:
+        R = wq.Rules(dim, p, nel, device=False)
+        m = inputs.band_mask(nel, p)
+        cs = np.concatenate([[0], np.cumsum(m.sum(1))]).astype(np.int64)
+        rows = m.shape[0]
+        for _ in range(40):
+            rb = int(rng.integers(0, rows + 1))
+            re = int(rng.integers(rb, rows + 1))
+            assert wq.wq_band_nnz_rows(R.handle, rb, re) == cs[re] - cs[rb]
+        assert wq.wq_band_nnz_rows(R.handle, 0, rows) == R.nnz
+        assert wq.wq_band_nnz_rows(R.handle, 3, 2) == -1
+        R.close()
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_comparison_rule_tables_match_oracle(p):
+    # Newton-Cotes-type rows: nodes (r - p + y_k) h, W = h v_k (mass) or v_k
+    # (stiffness), from the oracle's rule; Gauss-Legendre rows: the oracle's
+    # boundary-row form on every row
+    nel = 11
+    h = 1.0 / nel
+    gx, gw = oracle.gauss_legendre(p + 1)
+    for mode in ("nc", "gl"):
+        R = wq.Rules(2, p, (nel, 4), device=False, rule=mode)
+        for kind in (0, 1):
+            y, v, _ = oracle.rule_nc(p, kind)
+            for r in range(nel + p):
+                x, W, e = R.row(0, kind, r)
+                if mode == "nc" and p <= r <= nel - 1:
+                    assert len(x) == 2 * p + 1
+                    assert np.max(np.abs(x - (r - p + y) * h)) < 1e-15
+                    Wo = (h if kind == 0 else 1.0) * v
+                    assert np.max(np.abs(W - Wo)) < 1e-14 * np.max(np.abs(Wo))
+                    assert np.array_equal(e, r - p + np.floor(y).astype(int))
+                else:
+                    elo, ehi = max(0, r - p), min(nel - 1, r)
+                    xs = np.concatenate([(el + 0.5 * (gx + 1.0)) * h for el in range(elo, ehi + 1)])
+                    Wo = np.array([0.5 * h * gw[g % (p + 1)] * oracle.bspline(p, nel, r, xq, kind)
+                                   for g, xq in enumerate(xs)])
+                    assert len(x) == len(xs)
+                    assert np.max(np.abs(x - xs)) < 1e-15
+                    assert np.max(np.abs(W - Wo)) < 1e-13 * max(1.0, np.max(np.abs(Wo)))
+        R.close()
+    with pytest.raises(wq.WqError):
+        wq.wq_rules_build(2, p, (4, 4), wq.WQ_RULES_GAUSS_LEGENDRE | wq.WQ_RULES_NEWTON_COTES)
+    with pytest.raises(wq.WqError):
+        wq.wq_rules_build(2, p, (4, 4), 8)
+
+
+def test_comparison_rule_point_counts():
+    # points per interior row and direction: p+1 (weighted Gaussian), 2p+1
+    # (Newton-Cotes type: knots and midpoints), (p+1)^2 (Gauss-Legendre on the
+    # p+1 elements of the support)
+    for p in (2, 3):
+        for mode, cnt in (("wq", p + 1), ("nc", 2 * p + 1), ("gl", (p + 1) ** 2)):
+            R = wq.Rules(2, p, (20, 20), device=False, rule=mode)
+            for kind in (0, 1):
+                assert all(len(R.row(0, kind, r)[0]) == cnt for r in range(p, 20))
+            R.close()
