@@ -17,12 +17,13 @@
 // direction at a time (x3 then x2), for the two combinations the terms need:
 //   U0: mass kind in x2 and x3           (terms M and K1)
 //   U1: stiffness kind in x2 + in x3     (K2 + K3, summed)
-// one warp per column.  Phase B takes one warp per row: lane l owns the
-// band fibres (j2, j3) = l, l+32, ...; at each x1 point it forms
+// one warp per column.  Phase B spreads (row, band fibre (j2, j3)) items
+// over the CTA's threads, a group of rows at a time; at each x1 point of its
+// row a thread forms
 //   y_M = b1M . U0,  y_K = b1M . U1,  y_S = b1S . U0
 // and accumulates A_M += V1M y_M, A_K += V1M y_K + V1S y_S over the 2P+1
-// entries j1 of the fibre; the row's band is staged in shared memory and
-// written with consecutive lanes on consecutive addresses.  The folded 1D
+// entries j1 of the fibre; the group's bands are staged in shared memory and
+// written with consecutive threads on consecutive addresses.  The folded 1D
 // tables hold W * |J_aa| (mass kind) or W / |J_aa| (stiffness kind), so no
 // other per-point factor remains.  Rows whose x1 rule is the weighted Gaussian
 // one (P+1 points, one per element) take an unrolled path; boundary rows
@@ -125,8 +126,11 @@ struct RowsLayout {
   static constexpr int WX = WZ > WC ? WZ : WC;
   static constexpr int WT = (D == 3) ? NK3 * NL * NB : 0;
   static constexpr int WA = WX + WT;
-  static constexpr int WB = 2 * BAND;
-  static constexpr int WS = pad16<R>(WA > WB ? WA : WB);
+  static constexpr int WS = pad16<R>(WA);  // phase A, per warp
+  // phase B: (row, fibre) items over the CTA, G rows at a time, staged in R
+  static constexpr int G = (NT / NPAIR) < TMAX ? (NT / NPAIR) : TMAX;
+  static constexpr int STAGE = 2 * G * BAND;  // [M | K][G][BAND]
+  static constexpr int SCRATCH = (NW * WS) > STAGE ? (NW * WS) : STAGE;
   // R region
   static constexpr bool INNER_GAUSS = (LM == P + 1);  // interior line: o = q in x2, x3
   // every region is a whole number of 16-byte units, so 4-wide float rows stay aligned
@@ -138,7 +142,7 @@ struct RowsLayout {
   static constexpr int B1 = pad16<R>(2 * MAXPTS1 * 4);
   static constexpr int CB = pad16<R>(NL3 * NL * NL1);    // [l3][l2][l1]
   static constexpr int US = pad16<R>(NU * NL1 * LS);     // [u][l1][j3*NB+j2]
-  static constexpr int R_TOTAL = V23 + V23D + B23 + V1 + V1D + B1 + CB + US + NW * WS;
+  static constexpr int R_TOTAL = V23 + V23D + B23 + V1 + V1D + B1 + CB + US + SCRATCH;
   // int region: E23[2][LM], O23[2][LM], E1[MAXPTS1], OFF1[TMAX+1]
   static constexpr int I_TOTAL = 4 * LM + MAXPTS1 + TMAX + 1;
   static constexpr size_t BYTES = sizeof(R) * (size_t)R_TOTAL + sizeof(int) * (size_t)I_TOTAL;
@@ -173,7 +177,7 @@ __device__ __forceinline__ void rows_block(const RowsArgs &A, const int bid, uns
   R *sB1 = sV1d + L::V1D;                     // [kind][MAXPTS1][4]
   R *sCb = sB1 + L::B1;                       // [l3][l2][l1]
   R *sU = sCb + L::CB;                        // [u][NL1][LS]
-  R *sW = sU + L::US;                         // [warp][WS]
+  R *sW = sU + L::US;                         // phase A: [warp][WS]; phase B: the row stage
   int *sE23 = reinterpret_cast<int *>(smem_raw + sizeof(R) * (size_t)L::R_TOTAL);  // [di][LM]
   int *sO23 = sE23 + 2 * LM;                  // [di][LM]
   int *sE1 = sO23 + 2 * LM;                   // [MAXPTS1]
@@ -420,152 +424,129 @@ __device__ __forceinline__ void rows_block(const RowsArgs &A, const int bid, uns
   }
   __syncthreads();
 
-  // ------------------------------------------------ phase B: one warp per row
+  // ------------------------------------------------ phase B: (row, fibre) items, G rows at a time
+  // Thread t takes fibre t % NPAIR of row t / NPAIR of the group; the group's
+  // bands are staged in shared memory (in R) and copied to the output with
+  // consecutive threads on consecutive addresses, converting to the output
+  // type there.
   const R *U0 = sU;
   const R *U1 = sU + NL1 * LS;
-  O *stM = reinterpret_cast<O *>(sW + warp * L::WS);  // [BAND]
-  O *stK = stM + BAND;
-  constexpr int QUNROLL = sizeof(R) == 4 ? NP : 1;  // keep double-float code compact
-  for (int rl = warp; rl < T; rl += NW) {
-    const int r1 = a + rl;
-    const int q0 = sOff1[rl], q1end = sOff1[rl + 1];
-    const R *bm0 = &sB1[(0 * L::MAXPTS1 + q0) * 4];
-    const R *bs0 = &sB1[(1 * L::MAXPTS1 + q0) * 4];
-    const R *vm0 = &sV1[(0 * L::MAXPTS1 + q0) * NP];
-    const R *vs0 = &sV1[(1 * L::MAXPTS1 + q0) * NP];
-    if (!L::GENERAL && r1 >= P && r1 <= A.N[0] - 1) {
-      // weighted Gaussian rule in x1: point q in element r1-P+q, band offset q;
-      // sliding windows over the coefficient columns (w) and the entries j1 (acc)
-      const int kb = (r1 - P) - l1lo;
-      constexpr int NS = L::NSLOT;
-      int prs[NS];
-      R w0[NS][4], w1[NS][4], aM[NS][NP], aK[NS][NP];
+  R *stM = sW;                  // [G][BAND]
+  R *stK = sW + L::G * BAND;    // [G][BAND]
+  for (int g0 = 0; g0 < T; g0 += L::G) {
+    const int gn = (T - g0) < L::G ? (T - g0) : L::G;
+    if (tid < gn * NPAIR) {
+      const int rg = tid / NPAIR, pr = tid - rg * NPAIR;
+      const int rl = g0 + rg, r1 = a + rl;
+      const int q0 = sOff1[rl], q1end = sOff1[rl + 1];
+      R *oM = stM + rg * BAND + pr * NB;
+      R *oK = stK + rg * BAND + pr * NB;
+      if (!L::GENERAL && r1 >= P && r1 <= A.N[0] - 1) {
+        // weighted Gaussian rule in x1: point q in element r1-P+q, band
+        // offset q; the row's coefficient columns kb .. kb+P+3
+        const int kb = (r1 - P) - l1lo;
+        R w0[NP + 3], w1[NP + 3], aM[NB], aK[NB];
 #pragma unroll
-      for (int s = 0; s < NS; s++) {
-        // a lane past the last fibre repeats it and does not store
-        prs[s] = lane + 32 * s < NPAIR ? lane + 32 * s : NPAIR - 1;
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-          w0[s][i] = U0[(kb + i) * LS + prs[s]];
-          w1[s][i] = DO_K ? U1[(kb + i) * LS + prs[s]] : r_zero<R>();
+        for (int i = 0; i < NP + 3; i++) {
+          w0[i] = U0[(kb + i) * LS + pr];
+          w1[i] = DO_K ? U1[(kb + i) * LS + pr] : r_zero<R>();
         }
 #pragma unroll
-        for (int i = 0; i < NP; i++) { aM[s][i] = r_zero<R>(); aK[s][i] = r_zero<R>(); }
-      }
-#pragma unroll QUNROLL
-      for (int q = 0; q < NP; q++) {
-        R bm[4], vm[NP], bs[4], vs[NP];
-        if constexpr (std::is_same<R, float>::value && NP == 4) {
-          const float4 b4m = reinterpret_cast<const float4 *>(bm0)[q], b4s = reinterpret_cast<const float4 *>(bs0)[q];
-          const float4 v4m = reinterpret_cast<const float4 *>(vm0)[q], v4s = reinterpret_cast<const float4 *>(vs0)[q];
-          bm[0] = b4m.x; bm[1] = b4m.y; bm[2] = b4m.z; bm[3] = b4m.w;
-          bs[0] = b4s.x; bs[1] = b4s.y; bs[2] = b4s.z; bs[3] = b4s.w;
-          vm[0] = v4m.x; vm[1] = v4m.y; vm[2] = v4m.z; vm[3] = v4m.w;
-          vs[0] = v4s.x; vs[1] = v4s.y; vs[2] = v4s.z; vs[3] = v4s.w;
-        } else {
-#pragma unroll
-          for (int i = 0; i < 4; i++) { bm[i] = bm0[q * 4 + i]; bs[i] = bs0[q * 4 + i]; }
-#pragma unroll
-          for (int i = 0; i < NP; i++) { vm[i] = vm0[q * NP + i]; vs[i] = vs0[q * NP + i]; }
+        for (int j = 0; j < NB; j++) {
+          aM[j] = r_zero<R>();
+          aK[j] = r_zero<R>();
         }
+        const R *bm0 = &sB1[(0 * L::MAXPTS1 + q0) * 4];
+        const R *bs0 = &sB1[(1 * L::MAXPTS1 + q0) * 4];
+        const R *vm0 = &sV1[(0 * L::MAXPTS1 + q0) * NP];
+        const R *vs0 = &sV1[(1 * L::MAXPTS1 + q0) * NP];
 #pragma unroll
-        for (int s = 0; s < NS; s++) {
+        for (int q = 0; q < NP; q++) {
+          R bm[4], vm[NP], bs[4], vs[NP];
+          if constexpr (std::is_same<R, float>::value && NP == 4) {
+            const float4 b4m = reinterpret_cast<const float4 *>(bm0)[q], b4s = reinterpret_cast<const float4 *>(bs0)[q];
+            const float4 v4m = reinterpret_cast<const float4 *>(vm0)[q], v4s = reinterpret_cast<const float4 *>(vs0)[q];
+            bm[0] = b4m.x; bm[1] = b4m.y; bm[2] = b4m.z; bm[3] = b4m.w;
+            bs[0] = b4s.x; bs[1] = b4s.y; bs[2] = b4s.z; bs[3] = b4s.w;
+            vm[0] = v4m.x; vm[1] = v4m.y; vm[2] = v4m.z; vm[3] = v4m.w;
+            vs[0] = v4s.x; vs[1] = v4s.y; vs[2] = v4s.z; vs[3] = v4s.w;
+          } else {
+#pragma unroll
+            for (int i = 0; i < 4; i++) { bm[i] = bm0[q * 4 + i]; bs[i] = bs0[q * 4 + i]; }
+#pragma unroll
+            for (int i = 0; i < NP; i++) { vm[i] = vm0[q * NP + i]; vs[i] = vs0[q * NP + i]; }
+          }
           if constexpr (DO_M) {
             R y = r_zero<R>();
 #pragma unroll
-            for (int i = 0; i < 4; i++) y = r_fma(bm[i], w0[s][i], y);
+            for (int i = 0; i < 4; i++) y = r_fma(bm[i], w0[q + i], y);
 #pragma unroll
-            for (int i = 0; i < NP; i++) aM[s][i] = r_fma(vm[i], y, aM[s][i]);
+            for (int i = 0; i < NP; i++) aM[q + i] = r_fma(vm[i], y, aM[q + i]);
           }
           if constexpr (DO_K) {
             R yk = r_zero<R>(), ys = r_zero<R>();
 #pragma unroll
             for (int i = 0; i < 4; i++) {
-              yk = r_fma(bm[i], w1[s][i], yk);
-              ys = r_fma(bs[i], w0[s][i], ys);
+              yk = r_fma(bm[i], w1[q + i], yk);
+              ys = r_fma(bs[i], w0[q + i], ys);
             }
 #pragma unroll
-            for (int i = 0; i < NP; i++) aK[s][i] = r_fma(vs[i], ys, r_fma(vm[i], yk, aK[s][i]));
-          }
-          // entry j1 = q is complete
-          if (lane + 32 * s < NPAIR) {
-            if constexpr (DO_M) stM[prs[s] * NB + q] = r_out(aM[s][0]);
-            if constexpr (DO_K) stK[prs[s] * NB + q] = r_out(aK[s][0]);
-          }
-#pragma unroll
-          for (int i = 0; i < NP - 1; i++) { aM[s][i] = aM[s][i + 1]; aK[s][i] = aK[s][i + 1]; }
-          aM[s][NP - 1] = r_zero<R>();
-          aK[s][NP - 1] = r_zero<R>();
-#pragma unroll
-          for (int i = 0; i < 3; i++) { w0[s][i] = w0[s][i + 1]; w1[s][i] = w1[s][i + 1]; }
-          if (q < P) {
-            w0[s][3] = U0[(kb + q + 4) * LS + prs[s]];
-            if constexpr (DO_K) w1[s][3] = U1[(kb + q + 4) * LS + prs[s]];
+            for (int i = 0; i < NP; i++) aK[q + i] = r_fma(vs[i], ys, r_fma(vm[i], yk, aK[q + i]));
           }
         }
-      }
 #pragma unroll
-      for (int s = 0; s < NS; s++) {
-        if (lane + 32 * s < NPAIR) {
+        for (int j = 0; j < NB; j++) {
+          if constexpr (DO_M) oM[j] = aM[j];
+          if constexpr (DO_K) oK[j] = aK[j];
+        }
+      } else {
+        // Gauss-Legendre on each element of supp B_r1 (or a comparison rule):
+        // any number of points, each with its own band offset
+        R accM[NB], accK[NB];
 #pragma unroll
-          for (int i = 0; i < P; i++) {
-            if constexpr (DO_M) stM[prs[s] * NB + NP + i] = r_out(aM[s][i]);
-            if constexpr (DO_K) stK[prs[s] * NB + NP + i] = r_out(aK[s][i]);
+        for (int j = 0; j < NB; j++) { accM[j] = r_zero<R>(); accK[j] = r_zero<R>(); }
+        for (int q = q0; q < q1end; q++) {
+          const int e = sE1[q];
+          const int k0 = e - l1lo, o = e - r1 + P;
+          const R *bm = &sB1[(0 * L::MAXPTS1 + q) * 4];
+          const R *vm = &sV1[(0 * L::MAXPTS1 + q) * NP], *vmd = &sV1d[(0 * L::MAXPTS1 + q) * NB];
+          if constexpr (DO_M) {
+            R y = r_zero<R>();
+#pragma unroll
+            for (int i = 0; i < 4; i++) y = r_fma(bm[i], U0[(k0 + i) * LS + pr], y);
+            fiber_point<P>(accM, y, vm, vmd, o);
+          }
+          if constexpr (DO_K) {
+            const R *bs = &sB1[(1 * L::MAXPTS1 + q) * 4];
+            R yk = r_zero<R>(), ys = r_zero<R>();
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+              yk = r_fma(bm[i], U1[(k0 + i) * LS + pr], yk);
+              ys = r_fma(bs[i], U0[(k0 + i) * LS + pr], ys);
+            }
+            fiber_point<P>(accK, yk, vm, vmd, o);
+            fiber_point<P>(accK, ys, &sV1[(1 * L::MAXPTS1 + q) * NP], &sV1d[(1 * L::MAXPTS1 + q) * NB], o);
           }
         }
-      }
-    } else {
-      // Gauss-Legendre on each element of supp B_r1: any number of points
 #pragma unroll
-      for (int s = 0; s < L::NSLOT; s++) {
-        const int pr = lane + 32 * s;
-        if (pr < NPAIR) {
-          R accM[NB], accK[NB];
-#pragma unroll
-          for (int j = 0; j < NB; j++) { accM[j] = r_zero<R>(); accK[j] = r_zero<R>(); }
-          for (int q = q0; q < q1end; q++) {
-            const int e = sE1[q];
-            const int k0 = e - l1lo, o = e - r1 + P;
-            const R *bm = &sB1[(0 * L::MAXPTS1 + q) * 4];
-            const R *vm = &sV1[(0 * L::MAXPTS1 + q) * NP], *vmd = &sV1d[(0 * L::MAXPTS1 + q) * NB];
-            if constexpr (DO_M) {
-              R y = r_zero<R>();
-#pragma unroll
-              for (int i = 0; i < 4; i++) y = r_fma(bm[i], U0[(k0 + i) * LS + pr], y);
-              fiber_point<P>(accM, y, vm, vmd, o);
-            }
-            if constexpr (DO_K) {
-              const R *bs = &sB1[(1 * L::MAXPTS1 + q) * 4];
-              R yk = r_zero<R>(), ys = r_zero<R>();
-#pragma unroll
-              for (int i = 0; i < 4; i++) {
-                yk = r_fma(bm[i], U1[(k0 + i) * LS + pr], yk);
-                ys = r_fma(bs[i], U0[(k0 + i) * LS + pr], ys);
-              }
-              fiber_point<P>(accK, yk, vm, vmd, o);
-              fiber_point<P>(accK, ys, &sV1[(1 * L::MAXPTS1 + q) * NP], &sV1d[(1 * L::MAXPTS1 + q) * NB], o);
-            }
-          }
-#pragma unroll
-          for (int j = 0; j < NB; j++) {
-            if constexpr (DO_M) stM[pr * NB + j] = r_out(accM[j]);
-            if constexpr (DO_K) stK[pr * NB + j] = r_out(accK[j]);
-          }
+        for (int j = 0; j < NB; j++) {
+          if constexpr (DO_M) oM[j] = accM[j];
+          if constexpr (DO_K) oK[j] = accK[j];
         }
       }
     }
-    __syncwarp();
-    // the row's band is contiguous in the output: consecutive lanes, consecutive addresses
-    const long long orow = (base + r1 - A.row_begin) * BAND;
+    __syncthreads();
+    // the group's rows are consecutive in the output
+    const long long orow = (base + a + g0 - A.row_begin) * BAND;
     if constexpr (DO_M) {
       O *gM = static_cast<O *>(A.M) + orow;
-      for (int i = lane; i < BAND; i += 32) gM[i] = stM[i];
+      for (int i = tid; i < gn * BAND; i += NT) gM[i] = r_out(stM[i]);
     }
     if constexpr (DO_K) {
       O *gK = static_cast<O *>(A.K) + orow;
-      for (int i = lane; i < BAND; i += 32) gK[i] = stK[i];
+      for (int i = tid; i < gn * BAND; i += NT) gK[i] = r_out(stK[i]);
     }
-    __syncwarp();
+    __syncthreads();
   }
 }
 
