@@ -126,11 +126,11 @@ struct RowsLayout {
   static constexpr int WX = WZ > WC ? WZ : WC;
   static constexpr int WT = (D == 3) ? NK3 * NL * NB : 0;
   static constexpr int WA = WX + WT;
-  static constexpr int WS = pad16<R>(WA);  // phase A, per warp
+  static constexpr int WS = pad16<R>(WA);  // phase A, per half-warp
   // phase B: (row, fibre) items over the CTA, G rows at a time, staged in R
   static constexpr int G = (NT / NPAIR) < TMAX ? (NT / NPAIR) : TMAX;
   static constexpr int STAGE = 2 * G * BAND;  // [M | K][G][BAND]
-  static constexpr int SCRATCH = (NW * WS) > STAGE ? (NW * WS) : STAGE;
+  static constexpr int SCRATCH = (2 * NW * WS) > STAGE ? (2 * NW * WS) : STAGE;  // phase A: per half-warp
   // R region
   static constexpr bool INNER_GAUSS = (LM == P + 1);  // interior line: o = q in x2, x3
   // every region is a whole number of 16-byte units, so 4-wide float rows stay aligned
@@ -149,9 +149,9 @@ struct RowsLayout {
 };
 
 // Resident CTAs per SM the compiler is asked to allow (caps registers at
-// 65536 / (threads * minblocks)): three for float, two for 8-byte types.
+// 65536 / (threads * minblocks)): four for float, two for 8-byte types.
 #ifndef WQ_ROWS_MIN_BLOCKS_F32
-#define WQ_ROWS_MIN_BLOCKS_F32 3
+#define WQ_ROWS_MIN_BLOCKS_F32 4
 #endif
 #ifndef WQ_ROWS_MIN_BLOCKS
 #define WQ_ROWS_MIN_BLOCKS 2
@@ -293,15 +293,20 @@ __device__ __forceinline__ void rows_block(const RowsArgs &A, const int bid, uns
   }
   __syncthreads();
 
-  // ------------------------------------------------ phase A: U, one warp per coefficient column
-  R *wx = sW + warp * L::WS;  // Z, later Cq
-  R *wt = wx + L::WX;         // T3
-  for (int l1 = warp; l1 < nl1; l1 += NW) {
+  // ------------------------------------------------ phase A: U, two coefficient columns per warp
+  // (16 lanes each; a half-warp past the last column idles through the
+  // same loop trip counts, so every __syncwarp is reached by all lanes)
+  const int half = lane >> 4, hl = lane & 15;
+  R *wx = sW + (2 * warp + half) * L::WS;  // Z, later Cq
+  R *wt = wx + L::WX;                      // T3
+  for (int l1b = 2 * warp; l1b < nl1; l1b += 2 * NW) {
+    const int l1 = l1b + half;
+    const bool act = l1 < nl1;
     if constexpr (D == 3) {
       // Z[k3][l2][q3] = sum_i Cb[e3(q3)+i][l2][l1] * b3[k3][q3][i]
-      for (int t = lane; t < L::NK3 * NL * LM; t += 32) {
+      for (int t = hl; t < L::NK3 * NL * LM; t += 16) {
         const int q3 = t % LM, l2 = (t / LM) % NL, k3 = t / (LM * NL);
-        if (q3 < L3 && l2 < nl2) {
+        if (act && q3 < L3 && l2 < nl2) {
           const int e = sE23[LM + q3] - l23lo[1];
           const R *bb = &sB23[((1 * 2 + k3) * LM + q3) * 4];
           R s = r_zero<R>();
@@ -312,9 +317,9 @@ __device__ __forceinline__ void rows_block(const RowsArgs &A, const int bid, uns
       }
       __syncwarp();
       // T3[k3][l2][j3] = sum_q3 Z[k3][l2][q3] * V3[k3][q3][j3 - o3]
-      for (int t = lane; t < L::NK3 * NL; t += 32) {
+      for (int t = hl; t < L::NK3 * NL; t += 16) {
         const int l2 = t % NL, k3 = t / NL;
-        if (l2 < nl2) {
+        if (act && l2 < nl2) {
           R acc[NB];
 #pragma unroll
           for (int j = 0; j < NB; j++) acc[j] = r_zero<R>();
@@ -335,9 +340,9 @@ __device__ __forceinline__ void rows_block(const RowsArgs &A, const int bid, uns
       __syncwarp();
       // Cq[c][q2][j3] = sum_i T3[k3(c)][e2(q2)+i][j3] * b2[k2(c)][q2][i]; c = (kind2, kind3):
       // 0 = (M, M), 1 = (S, M), 2 = (M, S)
-      for (int t = lane; t < L::NCOMBO * LM * NB; t += 32) {
+      for (int t = hl; t < L::NCOMBO * LM * NB; t += 16) {
         const int j3 = t % NB, q2 = (t / NB) % LM, c = t / (NB * LM);
-        if (q2 < L2) {
+        if (act && q2 < L2) {
           const int k2 = (c == 1) ? 1 : 0, k3 = (c == 2) ? 1 : 0;
           const int e = sE23[q2] - l23lo[0];
           const R *bb = &sB23[((0 * 2 + k2) * LM + q2) * 4];
@@ -350,7 +355,8 @@ __device__ __forceinline__ void rows_block(const RowsArgs &A, const int bid, uns
       __syncwarp();
       // U0[l1][j3*NB+j2] = sum_q2 Cq[MM][q2][j3] V2M[q2][j2-o2]
       // U1[l1][j3*NB+j2] = sum_q2 Cq[SM][q2][j3] V2S[q2][..] + Cq[MS][q2][j3] V2M[q2][..]
-      for (int t = lane; t < L::NU * NB; t += 32) {
+      for (int t = hl; t < L::NU * NB; t += 16) {
+        if (!act) continue;
         const int j3 = t % NB, u = t / NB;
         R acc[NB];
 #pragma unroll
@@ -389,9 +395,9 @@ __device__ __forceinline__ void rows_block(const RowsArgs &A, const int bid, uns
       }
     } else {
       // Cq[k2][q2] = sum_i Cb[e2(q2)+i][l1] * b2[k2][q2][i]
-      for (int t = lane; t < L::NCOMBO * LM; t += 32) {
+      for (int t = hl; t < L::NCOMBO * LM; t += 16) {
         const int q2 = t % LM, c = t / LM;
-        if (q2 < L2) {
+        if (act && q2 < L2) {
           const int e = sE23[q2] - l23lo[0];
           const R *bb = &sB23[((0 * 2 + c) * LM + q2) * 4];
           R s = r_zero<R>();
@@ -402,8 +408,8 @@ __device__ __forceinline__ void rows_block(const RowsArgs &A, const int bid, uns
       }
       __syncwarp();
       // U0[l1][j2] = sum_q2 Cq[M][q2] V2M[q2][..];  U1[l1][j2] = sum_q2 Cq[S][q2] V2S[q2][..]
-      if (lane < L::NU) {
-        const int u = lane;
+      if (act && hl < L::NU) {
+        const int u = hl;
         R acc[NB];
 #pragma unroll
         for (int j = 0; j < NB; j++) acc[j] = r_zero<R>();

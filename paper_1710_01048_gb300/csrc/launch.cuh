@@ -10,8 +10,14 @@
 
 namespace wq {
 
-constexpr int kInteriorChunk = 24;
-constexpr int kBoundaryChunk = 16;
+#ifndef WQ_INTERIOR_CHUNK
+#define WQ_INTERIOR_CHUNK 24
+#endif
+#ifndef WQ_BOUNDARY_CHUNK
+#define WQ_BOUNDARY_CHUNK 16
+#endif
+constexpr int kInteriorChunk = WQ_INTERIOR_CHUNK;
+constexpr int kBoundaryChunk = WQ_BOUNDARY_CHUNK;
 constexpr int kGeneralChunk = 8;  // the comparison rules (kernel class 2)
 
 // Upper bound on the x1 points of one chunk's rows that the kernel's shared
