@@ -248,7 +248,9 @@ wq_status wq_batch_launch(wq_batch *batch, void *stream);
 /* Synchronises `stream`, returns and clears the plan's device status (as wq_status_check). */
 wq_status wq_batch_status(wq_batch *batch, void *stream);
 /*
- * Launch configuration: config[0] = chunk length of interior lines (1..24),
+ * Launch configuration: config[0] = chunk length of interior lines (1..24;
+ * cut to the capacity of the degree and arithmetic type, 20 rows for degree 3
+ * in FP64 and double-float),
  * config[1] = chunk length of boundary lines (1..16), config[2] = resident
  * CTAs per SM of the persistent launch (1..config[4]), config[3] = item order
  * (0: patch order, 1: costliest line classes first).  get writes config[0..4],

@@ -4,7 +4,8 @@ Usage: python -m paper_1710_01048_gb300.build [--force] [--verbose]
 
 Each translation unit compiles in parallel with nvcc
 (-gencode arch=compute_103a,code=sm_103a); host code is compiled without FMA
-contraction so the host rule tables are identical on x86_64 and aarch64.
+contraction so the host rule tables are identical on x86_64 and aarch64, and
+device code contracts nothing the source does not write as an FMA.
 Outputs go to paper_1710_01048_gb300/_build/ (git-ignored).
 """
 from __future__ import annotations
@@ -24,8 +25,12 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
-                   "--expt-relaxed-constexpr", "-I", INCLUDE]
+# --fmad=false: device code gets a fused multiply-add only where the source
+# asks for one (fma/fmaf); the double-float arithmetic's error-free
+# transformations need every other product and sum rounded on its own, and
+# every kernel instantiation then computes the same bits.
+CU_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler",
+                   "-ffp-contract=off", "--expt-relaxed-constexpr", "-I", INCLUDE]
 CXX_FLAGS = ["-O2", "-fPIC", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-I", INCLUDE,
              "-I", os.path.join(CUDA_HOME, "include")]
 

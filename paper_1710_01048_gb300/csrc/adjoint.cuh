@@ -39,7 +39,8 @@ struct AdjLayout {
   static constexpr int WT = (D == 3) ? 2 * NL * NB : 0;                    // T3bar
   static constexpr int WZ = (D == 3) ? 2 * NL * LM : 0;                    // Zbar
   static constexpr int WS = pad16<R>((WG > WQ + WT + WZ) ? WG : WQ + WT + WZ);
-  static constexpr int V23 = F::V23, V23D = F::V23D, B23 = F::B23, V1 = F::V1, V1D = F::V1D, B1 = F::B1;
+  static constexpr int V23 = F::V23, V23D = F::V23D, B23 = F::B23, V1 = F::V1, B1 = F::B1;
+  static constexpr int V1D = pad16<R>(2 * MAXPTS1 * NB);  // zero-padded x1 tables [kind][point][j]
   static constexpr int UB = pad16<R>(2 * NL1 * NPAIR);                     // [u][l1][pair]
   static constexpr int R_TOTAL = V23 + V23D + B23 + V1 + V1D + B1 + UB + NW * WS;
   static constexpr int I_TOTAL = 4 * LM + MAXPTS1 + TMAX + 1;

@@ -218,7 +218,8 @@ void fill_tables(const wq_rules *R, wq_precision prec, wq::RowsArgs &ra) {
 
 // Line range and chunking of one line class for rows [rb, re); returns the
 // number of CTAs (0 if the class has no line in the range).
-int chunk_class(const wq_rules *R, int cls, int64_t rb, int64_t re, wq::RowsArgs &ra, wq_status *st) {
+int chunk_class(const wq_rules *R, int cls, int elem_bytes, int64_t rb, int64_t re, wq::RowsArgs &ra,
+                wq_status *st) {
   const int n1 = R->n[0];
   const int first_line = (int)(rb / n1), last_line = (int)((re - 1) / n1);
   const std::vector<int> &lines = cls == 0 ? R->lines.interior : R->lines.boundary;
@@ -226,14 +227,15 @@ int chunk_class(const wq_rules *R, int cls, int64_t rb, int64_t re, wq::RowsArgs
   auto hi = std::upper_bound(lines.begin(), lines.end(), last_line);
   const int nl = (int)(hi - lo);
   if (nl <= 0) return 0;
-  const int tmax = R->mode ? wq::kGeneralChunk : cls == 0 ? wq::kInteriorChunk : wq::kBoundaryChunk;
+  const int tmax = R->mode ? wq::kGeneralChunk : cls == 0 ? wq::interior_chunk(R->p, elem_bytes) : wq::kBoundaryChunk;
   const int bound = R->mode ? wq::chunk_points_bound_general(R->p, tmax) : wq::chunk_points_bound(R->p, tmax);
-  if (R->max_chunk_points[cls] > bound) {
+  const int T = wq::chunk_length(R, tmax);
+  if (wq::max_chunk_points(R, T) > bound) {
     *st = WQ_ERR_UNSUPPORTED;
     return 0;
   }
-  ra.nch = (n1 + tmax - 1) / tmax;
-  ra.T = (n1 + ra.nch - 1) / ra.nch;
+  ra.T = T;
+  ra.nch = (n1 + T - 1) / T;
   ra.lines = (cls == 0 ? R->dev_lines_interior : R->dev_lines_boundary) + (lo - lines.begin());
   return nl * ra.nch;
 }
@@ -274,7 +276,7 @@ wq_status assemble(const wq_rules *R, const double *const *geom, const double *c
   ra.status = R->dev_status;
   for (int cls = 0; cls < 2; cls++) {
     wq_status cst = WQ_OK;
-    const int nblocks = chunk_class(R, cls, rb, re, ra, &cst);
+    const int nblocks = chunk_class(R, cls, prec == WQ_MIXED ? 4 : 8, rb, re, ra, &cst);
     if (cst != WQ_OK) return cst;
     if (nblocks == 0) continue;
     cudaError_t e;
@@ -348,8 +350,6 @@ wq_status wq_rules_build(const wq_mesh *mesh, int flags, wq_rules **out) {
     R->dim = mesh->dim;
     R->mode = rule_bits == WQ_RULES_GAUSS_LEGENDRE ? wq::kModeGL
               : rule_bits == WQ_RULES_NEWTON_COTES   ? wq::kModeNC : wq::kModeWQ;
-    R->chunk_rows[0] = R->mode ? wq::kGeneralChunk : wq::kInteriorChunk;
-    R->chunk_rows[1] = R->mode ? wq::kGeneralChunk : wq::kBoundaryChunk;
     for (int a = 0; a < 3; a++) {
       R->nel[a] = a < mesh->dim ? mesh->nel[a] : 1;
       R->n[a] = a < mesh->dim ? mesh->nel[a] + mesh->degree : 1;
@@ -474,7 +474,7 @@ wq_status wq_assemble_adjoint(const wq_rules *R, const double *const *geom, wq_p
   aa.grad = grad;
   for (int cls = 0; cls < 2; cls++) {
     wq_status cst = WQ_OK;
-    const int nblocks = chunk_class(R, cls, row_begin, row_end, aa.rows, &cst);
+    const int nblocks = chunk_class(R, cls, prec == WQ_MIXED ? 4 : 8, row_begin, row_end, aa.rows, &cst);
     if (cst != WQ_OK) return cst;
     if (nblocks == 0) continue;
     cudaError_t e;

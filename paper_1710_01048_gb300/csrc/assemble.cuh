@@ -95,6 +95,23 @@ __device__ __forceinline__ void fiber_point(R (&acc)[2 * P + 1], R x, const R *_
   else fiber_dense<2 * P + 1>(acc, x, vd);
 }
 
+// acc[o + i] += x * v[i], i = 0..P, for a runtime offset o in [0, P]: the
+// switch form for double (the FP64 pipe is the bound), the dense NB-wide
+// form with the point's P+1 columns selected by comparison otherwise.
+template <int P, typename R>
+__device__ __forceinline__ void fiber_shift(R (&acc)[2 * P + 1], R x, const R *__restrict__ v, int o) {
+  if constexpr (sizeof(R) == 8 && !std::is_same<R, dd>::value) {
+    fiber_add<P>(acc, x, v, o);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 2 * P + 1; j++) {
+      const int i = j - o;
+      const R vv = v[i < 0 ? 0 : (i > P ? P : i)];
+      acc[j] = r_fma(x, (i >= 0 && i <= P) ? vv : r_zero<R>(), acc[j]);
+    }
+  }
+}
+
 // Rounds a region size up to whole 16-byte units of R.
 template <typename R> constexpr int pad16(int n) {
   return (n * (int)sizeof(R) + 15) / 16 * 16 / (int)sizeof(R);
@@ -138,24 +155,30 @@ struct RowsLayout {
   static constexpr int V23D = INNER_GAUSS ? 0 : pad16<R>(2 * 2 * LM * NB);  // zero-padded [..][q][j]
   static constexpr int B23 = pad16<R>(2 * 2 * LM * 4);
   static constexpr int V1 = pad16<R>(2 * MAXPTS1 * NP);  // [kind][point][i]
-  static constexpr int V1D = pad16<R>(2 * MAXPTS1 * NB);  // zero-padded [kind][point][j]
   static constexpr int B1 = pad16<R>(2 * MAXPTS1 * 4);
   static constexpr int CB = pad16<R>(NL3 * NL * NL1);    // [l3][l2][l1]
   static constexpr int US = pad16<R>(NU * NL1 * LS);     // [u][l1][j3*NB+j2]
-  static constexpr int R_TOTAL = V23 + V23D + B23 + V1 + V1D + B1 + CB + US + SCRATCH;
+  static constexpr int R_TOTAL = V23 + V23D + B23 + V1 + B1 + CB + US + SCRATCH;
   // int region: E23[2][LM], O23[2][LM], E1[MAXPTS1], OFF1[TMAX+1]
   static constexpr int I_TOTAL = 4 * LM + MAXPTS1 + TMAX + 1;
   static constexpr size_t BYTES = sizeof(R) * (size_t)R_TOTAL + sizeof(int) * (size_t)I_TOTAL;
 };
 
 // Resident CTAs per SM the compiler is asked to allow (caps registers at
-// 65536 / (threads * minblocks)): four for float, two for 8-byte types.
+// 65536 / (threads * minblocks)): four for float, three for double-float,
+// two for double.
 #ifndef WQ_ROWS_MIN_BLOCKS_F32
 #define WQ_ROWS_MIN_BLOCKS_F32 4
 #endif
 #ifndef WQ_ROWS_MIN_BLOCKS
 #define WQ_ROWS_MIN_BLOCKS 2
 #endif
+#ifndef WQ_ROWS_MIN_BLOCKS_DD
+#define WQ_ROWS_MIN_BLOCKS_DD 3
+#endif
+template <typename R> constexpr int rows_min_blocks() {
+  return sizeof(R) == 4 ? WQ_ROWS_MIN_BLOCKS_F32 : std::is_same<R, dd>::value ? WQ_ROWS_MIN_BLOCKS_DD : WQ_ROWS_MIN_BLOCKS;
+}
 
 // The work of one CTA: chunk `bid` of the launch's line list (line
 // bid / nch, chunk bid % nch), in the dynamic shared memory `smem_raw`
@@ -173,8 +196,7 @@ __device__ __forceinline__ void rows_block(const RowsArgs &A, const int bid, uns
   R *sV23d = sV23 + L::V23;                   // [di][kind][LM][NB] (boundary lines)
   R *sB23 = sV23d + L::V23D;                  // [di][kind][LM][4]
   R *sV1 = sB23 + L::B23;                     // [kind][MAXPTS1][NP]
-  R *sV1d = sV1 + L::V1;                      // [kind][MAXPTS1][NB]
-  R *sB1 = sV1d + L::V1D;                     // [kind][MAXPTS1][4]
+  R *sB1 = sV1 + L::V1;                       // [kind][MAXPTS1][4]
   R *sCb = sB1 + L::B1;                       // [l3][l2][l1]
   R *sU = sCb + L::CB;                        // [u][NL1][LS]
   R *sW = sU + L::US;                         // phase A: [warp][WS]; phase B: the row stage
@@ -239,7 +261,6 @@ __device__ __forceinline__ void rows_block(const RowsArgs &A, const int bid, uns
   const int p1lo = A.off[0][0][a], p1hi = A.off[0][0][b];
   const int np1 = p1hi - p1lo;
   for (int t = tid; t <= T; t += NT) sOff1[t] = A.off[0][0][a + t] - p1lo;
-  __syncthreads();  // sOff1 complete
   for (int t = tid; t < 2 * np1; t += NT) {
     const int kind = t >= np1 ? 1 : 0, q = t - kind * np1;
     const int gq = (kind ? A.off[0][1][a] : p1lo) + q;
@@ -249,18 +270,7 @@ __device__ __forceinline__ void rows_block(const RowsArgs &A, const int bid, uns
     for (int i = 0; i < NP; i++) sV1[(kind * L::MAXPTS1 + q) * NP + i] = Vg[(size_t)gq * NP + i];
 #pragma unroll
     for (int i = 0; i < 4; i++) sB1[(kind * L::MAXPTS1 + q) * 4 + i] = Bg[(size_t)gq * 4 + i];
-    const int e = A.elem[0][0][p1lo + q];
-    if (kind == 0) sE1[q] = e;
-    // the point's row: the last rl with sOff1[rl] <= q
-    int lo_r = 0, hi_r = T - 1;
-    while (lo_r < hi_r) {
-      const int mid = (lo_r + hi_r + 1) >> 1;
-      if (sOff1[mid] <= q) lo_r = mid; else hi_r = mid - 1;
-    }
-    const int o = e - (a + lo_r) + P;
-#pragma unroll
-    for (int j = 0; j < NB; j++)
-      sV1d[(kind * L::MAXPTS1 + q) * NB + j] = (j >= o && j <= o + P) ? Vg[(size_t)gq * NP + (j - o)] : r_zero<R>();
+    if (kind == 0) sE1[q] = A.elem[0][0][p1lo + q];
   }
   const int elo1 = a - P < 0 ? 0 : a - P;
   const int ehi1 = (b - 1) > A.N[0] - 1 ? A.N[0] - 1 : (b - 1);
@@ -515,12 +525,12 @@ __device__ __forceinline__ void rows_block(const RowsArgs &A, const int bid, uns
           const int e = sE1[q];
           const int k0 = e - l1lo, o = e - r1 + P;
           const R *bm = &sB1[(0 * L::MAXPTS1 + q) * 4];
-          const R *vm = &sV1[(0 * L::MAXPTS1 + q) * NP], *vmd = &sV1d[(0 * L::MAXPTS1 + q) * NB];
+          const R *vm = &sV1[(0 * L::MAXPTS1 + q) * NP];
           if constexpr (DO_M) {
             R y = r_zero<R>();
 #pragma unroll
             for (int i = 0; i < 4; i++) y = r_fma(bm[i], U0[(k0 + i) * LS + pr], y);
-            fiber_point<P>(accM, y, vm, vmd, o);
+            fiber_shift<P>(accM, y, vm, o);
           }
           if constexpr (DO_K) {
             const R *bs = &sB1[(1 * L::MAXPTS1 + q) * 4];
@@ -530,8 +540,8 @@ __device__ __forceinline__ void rows_block(const RowsArgs &A, const int bid, uns
               yk = r_fma(bm[i], U1[(k0 + i) * LS + pr], yk);
               ys = r_fma(bs[i], U0[(k0 + i) * LS + pr], ys);
             }
-            fiber_point<P>(accK, yk, vm, vmd, o);
-            fiber_point<P>(accK, ys, &sV1[(1 * L::MAXPTS1 + q) * NP], &sV1d[(1 * L::MAXPTS1 + q) * NB], o);
+            fiber_shift<P>(accK, yk, vm, o);
+            fiber_shift<P>(accK, ys, &sV1[(1 * L::MAXPTS1 + q) * NP], o);
           }
         }
 #pragma unroll
@@ -557,8 +567,7 @@ __device__ __forceinline__ void rows_block(const RowsArgs &A, const int bid, uns
 }
 
 template <int P, int D, int LM, int TMAX, bool DO_M, bool DO_K, typename R>
-__global__ void __launch_bounds__(32 * kRowsWarps, sizeof(R) == 4 ? WQ_ROWS_MIN_BLOCKS_F32 : WQ_ROWS_MIN_BLOCKS)
-    rows_kernel(const RowsArgs A) {
+__global__ void __launch_bounds__(32 * kRowsWarps, rows_min_blocks<R>()) rows_kernel(const RowsArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   rows_block<P, D, LM, TMAX, DO_M, DO_K, R>(A, blockIdx.x, smem_raw);
 }

@@ -61,7 +61,7 @@ struct wq_batch {
   int nseg = 0, nitems = 0;
   unsigned *dev_counter = nullptr, *dev_status = nullptr;
   std::vector<wq::RowsArgs> base_args;  // per patch, without class/chunking
-  int config[4] = {wq::kInteriorChunk, wq::kBoundaryChunk, 1, 1};
+  int config[4] = {wq::kInteriorChunkMax, wq::kBoundaryChunk, 1, 1};
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -78,16 +78,6 @@ wq_status prepare(wq_batch *B) {
   return WQ_OK;
 }
 
-// Most x1 points of one chunk when the lines of n1 rows are cut into chunks of
-// at most t rows (as the launch cuts them).
-int chunk_points(const wq_rules *R, int t) {
-  const std::vector<int> &off = R->host[0][0].off;
-  const int n1 = R->n[0], nch = (n1 + t - 1) / t, tt = (n1 + nch - 1) / nch;
-  int mx = 0;
-  for (int c = 0; c * tt < n1; c++) mx = std::max(mx, off[std::min(n1, (c + 1) * tt)] - off[c * tt]);
-  return mx;
-}
-
 // Builds the segment list for the current configuration and uploads it.
 wq_status build_segments(wq_batch *B) {
   const int tint = B->config[0], tbnd = B->config[1], order = B->config[3];
@@ -97,15 +87,17 @@ wq_status build_segments(wq_batch *B) {
     for (int cls = 0; cls < 2; cls++) {
       const std::vector<int> &lines = cls == 0 ? R->lines.interior : R->lines.boundary;
       if (lines.empty()) continue;
-      const int t = cls == 0 ? tint : tbnd;
-      const int tmax = cls == 0 ? wq::kInteriorChunk : wq::kBoundaryChunk;
-      if (t < 1 || t > tmax) return WQ_ERR_ARG;
-      if (chunk_points(R, t) > wq::chunk_points_bound(R->p, tmax)) return WQ_ERR_UNSUPPORTED;
+      // interior chunks longer than the degree's capacity are cut to it
+      const int tmax = cls == 0 ? wq::interior_chunk(R->p, B->prec == WQ_MIXED ? 4 : 8) : wq::kBoundaryChunk;
+      if (tint < 1 || tint > wq::kInteriorChunkMax || tbnd < 1 || tbnd > wq::kBoundaryChunk) return WQ_ERR_ARG;
+      const int t = cls == 0 ? std::min(tint, tmax) : tbnd;
+      const int T = wq::chunk_length(R, t);
+      if (wq::max_chunk_points(R, T) > wq::chunk_points_bound(R->p, tmax)) return WQ_ERR_UNSUPPORTED;
       wq::BatchSeg S;
       std::memset(&S, 0, sizeof(S));
       S.a = B->base_args[i];
-      S.a.nch = (R->n[0] + t - 1) / t;
-      S.a.T = (R->n[0] + S.a.nch - 1) / S.a.nch;
+      S.a.T = T;
+      S.a.nch = (R->n[0] + T - 1) / T;
       S.a.lines = cls == 0 ? R->dev_lines_interior : R->dev_lines_boundary;
       S.p = R->p;
       S.cls = cls;
@@ -319,7 +311,7 @@ wq_status wq_batch_create(const wq_patch *patches, int npatch, wq_precision prec
     destroy(B);
     return WQ_ERR_CUDA;
   }
-  const int cfg[4] = {wq::kInteriorChunk, wq::kBoundaryChunk, B->max_ctas, 1};
+  const int cfg[4] = {wq::kInteriorChunkMax, wq::kBoundaryChunk, B->max_ctas, 1};
   st = apply_config(B, cfg);
   if (st != WQ_OK) {
     destroy(B);

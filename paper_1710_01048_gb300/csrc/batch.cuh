@@ -20,16 +20,16 @@ struct BatchSeg {
 
 // Dynamic shared memory the batch kernel needs: the largest of the four bodies.
 template <typename R> constexpr size_t batch_smem_bytes() {
-  constexpr size_t a = RowsLayout<2, 3, 3, kInteriorChunk, true, true, R>::BYTES;
+  constexpr size_t a = RowsLayout<2, 3, 3, interior_chunk(2, sizeof(R)), true, true, R>::BYTES;
   constexpr size_t b = RowsLayout<2, 3, 6, kBoundaryChunk, true, true, R>::BYTES;
-  constexpr size_t c = RowsLayout<3, 3, 4, kInteriorChunk, true, true, R>::BYTES;
+  constexpr size_t c = RowsLayout<3, 3, 4, interior_chunk(3, sizeof(R)), true, true, R>::BYTES;
   constexpr size_t d = RowsLayout<3, 3, 12, kBoundaryChunk, true, true, R>::BYTES;
   constexpr size_t ab = a > b ? a : b, cd = c > d ? c : d;
   return ab > cd ? ab : cd;
 }
 
 template <typename R>
-__global__ void __launch_bounds__(32 * kRowsWarps, sizeof(R) == 4 ? WQ_ROWS_MIN_BLOCKS_F32 : WQ_ROWS_MIN_BLOCKS)
+__global__ void __launch_bounds__(32 * kRowsWarps, rows_min_blocks<R>())
     batch_rows_kernel(const BatchSeg *__restrict__ segs, int nseg, int nitems, unsigned *counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ RowsArgs sA;
@@ -59,10 +59,10 @@ __global__ void __launch_bounds__(32 * kRowsWarps, sizeof(R) == 4 ? WQ_ROWS_MIN_
     const int p = S.p, cls = S.cls, bid = item - S.first_item;
     __syncthreads();
     if (p == 2) {
-      if (cls == 0) rows_block<2, 3, 3, kInteriorChunk, true, true, R>(sA, bid, smem_raw);
+      if (cls == 0) rows_block<2, 3, 3, interior_chunk(2, sizeof(R)), true, true, R>(sA, bid, smem_raw);
       else rows_block<2, 3, 6, kBoundaryChunk, true, true, R>(sA, bid, smem_raw);
     } else {
-      if (cls == 0) rows_block<3, 3, 4, kInteriorChunk, true, true, R>(sA, bid, smem_raw);
+      if (cls == 0) rows_block<3, 3, 4, interior_chunk(3, sizeof(R)), true, true, R>(sA, bid, smem_raw);
       else rows_block<3, 3, 12, kBoundaryChunk, true, true, R>(sA, bid, smem_raw);
     }
   }

@@ -1,6 +1,6 @@
 // Dispatch from runtime (dimension, terms, line class) to the row-kernel
 // instantiations.  Interior lines (inner-direction rules with P+1 points)
-// run chunks of up to kInteriorChunk rows; boundary lines (up to P(P+1)
+// run chunks of up to interior_chunk(P, sizeof(R)) rows; boundary lines (up to P(P+1)
 // points per inner direction) chunks of up to kBoundaryChunk rows.  Each CTA
 // has (2P+1) threads per row of its chunk.
 #pragma once
@@ -13,10 +13,20 @@ namespace wq {
 #ifndef WQ_INTERIOR_CHUNK
 #define WQ_INTERIOR_CHUNK 24
 #endif
+#ifndef WQ_INTERIOR_CHUNK_P3_8B
+#define WQ_INTERIOR_CHUNK_P3_8B 20
+#endif
 #ifndef WQ_BOUNDARY_CHUNK
 #define WQ_BOUNDARY_CHUNK 16
 #endif
-constexpr int kInteriorChunk = WQ_INTERIOR_CHUNK;
+// Interior-line chunk length by degree and arithmetic element size: degree 3
+// in double or double-float keeps its shared memory small enough for three
+// resident CTAs per SM.
+constexpr int interior_chunk(int p, int elem_bytes) {
+  return (p == 3 && elem_bytes == 8) ? WQ_INTERIOR_CHUNK_P3_8B : WQ_INTERIOR_CHUNK;
+}
+constexpr int kInteriorChunkMax =
+    WQ_INTERIOR_CHUNK > WQ_INTERIOR_CHUNK_P3_8B ? WQ_INTERIOR_CHUNK : WQ_INTERIOR_CHUNK_P3_8B;
 constexpr int kBoundaryChunk = WQ_BOUNDARY_CHUNK;
 constexpr int kGeneralChunk = 8;  // the comparison rules (kernel class 2)
 
@@ -44,7 +54,7 @@ cudaError_t launch_one(const RowsArgs &a, int nblocks, cudaStream_t s) {
 
 template <int P, int D, bool DO_M, bool DO_K, typename R>
 cudaError_t launch_class(int cls, const RowsArgs &a, int nblocks, cudaStream_t s) {
-  if (cls == 0) return launch_one<P, D, P + 1, kInteriorChunk, DO_M, DO_K, R>(a, nblocks, s);
+  if (cls == 0) return launch_one<P, D, P + 1, interior_chunk(P, sizeof(R)), DO_M, DO_K, R>(a, nblocks, s);
   if (cls == 1) return launch_one<P, D, P *(P + 1), kBoundaryChunk, DO_M, DO_K, R>(a, nblocks, s);
   // class 2, the comparison rules: FP64 only
   if constexpr (std::is_same<R, double>::value)
@@ -67,10 +77,10 @@ cudaError_t launch_rows(int D, bool do_m, bool do_k, int cls, const RowsArgs &a,
 template <int P, typename R>
 cudaError_t launch_adjoint(int D, int cls, const AdjArgs &a, int nblocks, cudaStream_t s) {
   if (D == 2) {
-    if (cls == 0) return launch_adjoint_one<P, 2, P + 1, kInteriorChunk, R>(a, nblocks, s);
+    if (cls == 0) return launch_adjoint_one<P, 2, P + 1, interior_chunk(P, sizeof(R)), R>(a, nblocks, s);
     return launch_adjoint_one<P, 2, P *(P + 1), kBoundaryChunk, R>(a, nblocks, s);
   }
-  if (cls == 0) return launch_adjoint_one<P, 3, P + 1, kInteriorChunk, R>(a, nblocks, s);
+  if (cls == 0) return launch_adjoint_one<P, 3, P + 1, interior_chunk(P, sizeof(R)), R>(a, nblocks, s);
   return launch_adjoint_one<P, 3, P *(P + 1), kBoundaryChunk, R>(a, nblocks, s);
 }
 

@@ -232,10 +232,11 @@ extern "C" wq_status wq_assemble_noalloc(const wq_rules *R, const double *const 
     auto hi = std::upper_bound(lines.begin(), lines.end(), last_line);
     const int nl = (int)(hi - lo);
     if (nl <= 0) continue;
-    const int tmax = cls == 0 ? wq::kInteriorChunk : wq::kBoundaryChunk;
-    if (R->max_chunk_points[cls] > wq::chunk_points_bound(R->p, tmax)) return WQ_ERR_UNSUPPORTED;
-    ra.nch = (n1 + tmax - 1) / tmax;
-    ra.T = (n1 + ra.nch - 1) / ra.nch;
+    const int tmax = cls == 0 ? wq::interior_chunk(R->p, prec == WQ_MIXED ? 4 : 8) : wq::kBoundaryChunk;
+    const int T = wq::chunk_length(R, tmax);
+    if (wq::max_chunk_points(R, T) > wq::chunk_points_bound(R->p, tmax)) return WQ_ERR_UNSUPPORTED;
+    ra.T = T;
+    ra.nch = (n1 + T - 1) / T;
     ra.lines = reinterpret_cast<const int *>(base + (cls == 0 ? L.lines_in : L.lines_bd)) + (lo - lines.begin());
     const bool dm = M != nullptr, dk = K != nullptr;
     cudaError_t e;

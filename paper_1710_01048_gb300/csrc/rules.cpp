@@ -426,16 +426,6 @@ wq_status build_host_tables(wq_rules *R) {
       H.off[n] = (int)H.elem.size();
     }
   }
-  // the most x1 points any chunk of `t` consecutive rows holds (chunks start at
-  // multiples of t, as the assembly launches cut them)
-  for (int cls = 0; cls < 2; cls++) {
-    const int t = R->chunk_rows[cls];
-    const std::vector<int> &off = R->host[0][0].off;
-    const int n1 = R->n[0], nch = (n1 + t - 1) / t, tt = (n1 + nch - 1) / nch;
-    int mx = 0;
-    for (int c = 0; c * tt < n1; c++) mx = std::max(mx, off[std::min(n1, (c + 1) * tt)] - off[c * tt]);
-    R->max_chunk_points[cls] = mx;
-  }
   // lines: D=3 -> (r2, r3), D=2 -> r2; interior when dirs 2..D are interior rows
   R->lines = Lines();
   int nl = R->dim == 3 ? R->n[1] * R->n[2] : R->n[1];
@@ -457,6 +447,23 @@ wq_status build_host_tables(wq_rules *R) {
 // points of direction 1 (the terms with mass kind in direction 1 are summed
 // before it).  Coefficient evaluation: the cubic spline of c on each grid,
 // sum-factorised over the coefficients of each line of rows.
+int chunk_length(const wq_rules *R, int tmax) {
+  const int n1 = R->n[0], nch = (n1 + tmax - 1) / tmax;
+  int npair = 1;
+  for (int a = 1; a < R->dim; a++) npair *= 2 * R->p + 1;
+  const int g = std::max(1, std::min(tmax, 256 / npair));
+  const int t = (n1 + nch - 1) / nch;
+  return std::min(tmax, (t + g - 1) / g * g);
+}
+
+int max_chunk_points(const wq_rules *R, int T) {
+  const std::vector<int> &off = R->host[0][0].off;
+  const int n1 = R->n[0];
+  int mx = 0;
+  for (int c = 0; c * T < n1; c++) mx = std::max(mx, off[std::min(n1, (c + 1) * T)] - off[c * T]);
+  return mx;
+}
+
 double flop_count(const wq_rules *R, int want_m, int want_k, int64_t row_begin, int64_t row_end,
                   double *coef_flops) {
   int p = R->p, D = R->dim, NP = p + 1;

@@ -70,8 +70,6 @@ struct wq_rules {
   double omega[2][wq::kMaxP + 1] = {};
   wq::HostDirKind host[3][2];
   wq::Lines lines;
-  int chunk_rows[2] = {1, 1};        // chunk length limits of the two line classes
-  int max_chunk_points[2] = {0, 0};  // most x1 points in one chunk, per class
   // device side
   bool on_device = false;
   int device = -1;
@@ -91,6 +89,13 @@ wq_status solve_rule(int p, int kind, const double *start, double *tau, double *
 wq_status default_rule(int p, int kind, double *tau, double *omega);
 wq_status build_host_tables(wq_rules *R);
 wq_status nc_rule(int p, int kind, double *y, double *v);
+// Chunk length for lines of n1 rows and a capacity of tmax rows: the even
+// split ceil(n1 / ceil(n1 / tmax)), rounded up to whole groups of rows of the
+// kernel's second phase (floor(256 / (2p+1)^(dim-1)) rows), at most tmax.
+int chunk_length(const wq_rules *R, int tmax);
+// Most x1 points one chunk holds when lines are cut into chunks of T rows
+// (the last one ragged), as the launches cut them.
+int max_chunk_points(const wq_rules *R, int T);
 double flop_count(const wq_rules *R, int want_m, int want_k, int64_t row_begin, int64_t row_end,
                   double *coef_flops);
 }  // namespace wq
