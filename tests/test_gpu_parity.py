@@ -184,3 +184,27 @@ def test_status_geometry_and_nonfinite():
     # the status is cleared by the check
     wq.assemble(R, gd_ok, cd, "fp64")
     R.close()
+
+
+@pytest.mark.parametrize("prec", ["df64", "mixed"])
+def test_128_cubed_sampled(prec):
+    # the 128^3 cubic workload (2.25M rows x 343): sampled rows against the
+    # oracle, and invariants over every row
+    w, g, c = inputs.workload("3d_p3_128")
+    p, nel = w["p"], w["nel"]
+    R = wq.Rules(3, p, nel)
+    gd = [torch.from_numpy(x).cuda() for x in g]
+    cd = torch.from_numpy(c).cuda()
+    M, K = wq.assemble(R, gd, cd, prec)
+    n1 = nel[0] + p
+    n12 = n1 * (nel[1] + p)
+    tol = FP64_TOL if prec == "df64" else MIXED_TOL
+    for rb, re in [(0, 40), (n12 * 70 + n1 * 60, n12 * 70 + n1 * 61), (R.rows - 40, R.rows)]:
+        Mo, Ko, _ = oracle.assemble(3, p, nel, g, c, rb, re)
+        check(M[rb:re].double().cpu().numpy(), Mo, tol, f"M rows {rb}:{re}")
+        check(K[rb:re].double().cpu().numpy(), Ko, tol, f"K rows {rb}:{re}")
+    kabs = K.abs().sum(dim=1, dtype=torch.float64)
+    ks = K.sum(dim=1, dtype=torch.float64).abs()
+    assert (ks <= (1e-12 if prec == "df64" else 1e-5) * kabs).all()
+    del M, K
+    R.close()
