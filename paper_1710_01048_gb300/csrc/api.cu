@@ -158,6 +158,19 @@ wq_status upload(wq_rules *R) {
   R->dev_coefdd = reinterpret_cast<float2 *>(base + coefdd_off);
   R->dev_block = block;
   R->dev_bytes = total;
+  if (R->dim == 3 && R->mode == wq::kModeWQ) {
+    const int nb = 2 * R->p + 1;
+    const size_t ubytes = (size_t)R->n[1] * R->n[2] * 2 * R->nc[0] * nb * nb * sizeof(double);
+    e = cudaMalloc(&R->dev_U, ubytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(block);
+      R->dev_block = nullptr;
+      R->dev_U = nullptr;
+      return e == cudaErrorMemoryAllocation ? WQ_ERR_OOM : WQ_ERR_CUDA;
+    }
+    R->dev_bytes += ubytes;
+  }
   R->device = dev;
   R->on_device = true;
   return WQ_OK;
@@ -240,6 +253,63 @@ int chunk_class(const wq_rules *R, int cls, int elem_bytes, int64_t rb, int64_t 
   return nl * ra.nch;
 }
 
+// The 3D split path: u_kernel for the lines of rows [row_begin, row_end)
+// (their U into R->dev_U), then one row launch over those lines.
+wq_status assemble_split(const wq_rules *R, wq_precision prec, wq::RowsArgs &ra, cudaStream_t s) {
+  const int n1 = R->n[0], n2 = R->n[1];
+  const int first_line = (int)(ra.row_begin / n1), last_line = (int)((ra.row_end - 1) / n1);
+  wq::UArgs ua;
+  std::memset(&ua, 0, sizeof(ua));
+  std::memcpy(ua.off, ra.off, sizeof(ua.off));
+  std::memcpy(ua.elem, ra.elem, sizeof(ua.elem));
+  std::memcpy(ua.V, ra.V, sizeof(ua.V));
+  std::memcpy(ua.beta, ra.beta, sizeof(ua.beta));
+  for (int a = 0; a < 3; a++) {
+    ua.n[a] = ra.n[a];
+    ua.N[a] = ra.N[a];
+    ua.nc[a] = ra.nc[a];
+  }
+  ua.coef = ra.coef;
+  ua.coefR = ra.coefR;
+  ua.U = R->dev_U;
+  ua.line_lo = first_line;
+  ua.line_hi = last_line;
+  ua.r3_lo = first_line / n2;
+  ua.nblk2 = (n2 + wq::kULines - 1) / wq::kULines;
+  ua.nblk1 = (R->nc[0] + wq::kUCols - 1) / wq::kUCols;
+  ua.status = R->dev_status;
+  const int nplanes = last_line / n2 - ua.r3_lo + 1;
+  const int ublocks = nplanes * ua.nblk2 * ua.nblk1;
+  const int T = wq::chunk_length(R, wq::kUGChunk);
+  if (wq::max_chunk_points(R, T) > wq::chunk_points_bound(R->p, wq::kUGChunk)) return WQ_ERR_UNSUPPORTED;
+  ra.lines = nullptr;
+  ra.line0 = first_line;
+  ra.T = T;
+  ra.nch = (n1 + T - 1) / T;
+  ra.Ug = R->dev_U;
+  const int rblocks = (last_line - first_line + 1) * ra.nch;
+  const bool dm = ra.M != nullptr, dk = ra.K != nullptr;
+  cudaError_t e;
+  if (R->p == 2) {
+    e = prec == WQ_FP64   ? wq::launch_u<2, double>(ua, ublocks, s)
+        : prec == WQ_MIXED ? wq::launch_u<2, float>(ua, ublocks, s)
+                           : wq::launch_u<2, wq::dd>(ua, ublocks, s);
+    if (e == cudaSuccess)
+      e = prec == WQ_FP64   ? wq::launch_rows_ug<2, double>(dm, dk, ra, rblocks, s)
+          : prec == WQ_MIXED ? wq::launch_rows_ug<2, float>(dm, dk, ra, rblocks, s)
+                             : wq::launch_rows_ug<2, wq::dd>(dm, dk, ra, rblocks, s);
+  } else {
+    e = prec == WQ_FP64   ? wq::launch_u<3, double>(ua, ublocks, s)
+        : prec == WQ_MIXED ? wq::launch_u<3, float>(ua, ublocks, s)
+                           : wq::launch_u<3, wq::dd>(ua, ublocks, s);
+    if (e == cudaSuccess)
+      e = prec == WQ_FP64   ? wq::launch_rows_ug<3, double>(dm, dk, ra, rblocks, s)
+          : prec == WQ_MIXED ? wq::launch_rows_ug<3, float>(dm, dk, ra, rblocks, s)
+                             : wq::launch_rows_ug<3, wq::dd>(dm, dk, ra, rblocks, s);
+  }
+  return e == cudaSuccess ? WQ_OK : WQ_ERR_CUDA;
+}
+
 wq_status assemble(const wq_rules *R, const double *const *geom, const double *coef, wq_precision prec, void *M,
                    void *K, int64_t rb, int64_t re, void *stream) {
   if (!R || !geom) return WQ_ERR_ARG;
@@ -274,6 +344,7 @@ wq_status assemble(const wq_rules *R, const double *const *geom, const double *c
   ra.row_begin = rb;
   ra.row_end = re;
   ra.status = R->dev_status;
+  if (R->dev_U) return assemble_split(R, prec, ra, s);
   for (int cls = 0; cls < 2; cls++) {
     wq_status cst = WQ_OK;
     const int nblocks = chunk_class(R, cls, prec == WQ_MIXED ? 4 : 8, rb, re, ra, &cst);
@@ -379,6 +450,7 @@ void wq_rules_free(wq_rules *rules) {
     cudaGetDevice(&cur);
     if (cur != rules->device) cudaSetDevice(rules->device);
     cudaFree(rules->dev_block);
+    if (rules->dev_U) cudaFree(rules->dev_U);
     if (cur >= 0 && cur != rules->device) cudaSetDevice(cur);
   }
   delete rules;

@@ -49,8 +49,10 @@ struct RowsArgs {
   const void *coefR;   // the same already in the arithmetic type R (and checked), or null
   void *M, *K;         // band outputs, OutT<R> (double for R = double or dd)
   long long row_begin, row_end;
-  const int *lines;  // line ids of this launch
+  const int *lines;  // line ids of this launch, or null: lines line0, line0+1, ...
+  int line0;
   int nch, T;        // chunks per line and chunk length
+  const void *Ug;    // U of every line, [line][2][nc1][(2P+1)^2] in R (split 3D path)
   unsigned *status;
 };
 
@@ -144,10 +146,9 @@ struct RowsLayout {
   static constexpr int WT = (D == 3) ? NK3 * NL * NB : 0;
   static constexpr int WA = WX + WT;
   static constexpr int WS = pad16<R>(WA);  // phase A, per half-warp
-  // phase B: (row, fibre) items over the CTA, G rows at a time, staged in R
-  static constexpr int G = (NT / NPAIR) < TMAX ? (NT / NPAIR) : TMAX;
-  static constexpr int STAGE = 2 * G * BAND;  // [M | K][G][BAND]
-  static constexpr int SCRATCH = (2 * NW * WS) > STAGE ? (2 * NW * WS) : STAGE;  // phase A: per half-warp
+  // phase B: per-warp stage of 32 items' fibres, one matrix at a time
+  static constexpr int WST = pad16<R>(32 * NB);
+  static constexpr int SCRATCH = (2 * NW * WS) > (NW * WST) ? (2 * NW * WS) : (NW * WST);
   // R region
   static constexpr bool INNER_GAUSS = (LM == P + 1);  // interior line: o = q in x2, x3
   // every region is a whole number of 16-byte units, so 4-wide float rows stay aligned
@@ -180,6 +181,180 @@ template <typename R> constexpr int rows_min_blocks() {
   return sizeof(R) == 4 ? WQ_ROWS_MIN_BLOCKS_F32 : std::is_same<R, dd>::value ? WQ_ROWS_MIN_BLOCKS_DD : WQ_ROWS_MIN_BLOCKS;
 }
 
+// The chunk's x1 tables (rows [a, a+T) hold one contiguous range of points):
+// point offsets per row, folded values and cubic coefficient-spline values of
+// both kinds, elements.  No barrier; the caller synchronises.
+template <int P, int MAXPTS1, typename R>
+__device__ __forceinline__ void load_x1_tables(const RowsArgs &A, const int a, const int T, R *sV1, R *sB1, int *sE1,
+                                               int *sOff1) {
+  constexpr int NP = P + 1, NT = 32 * kRowsWarps;
+  const int tid = threadIdx.x;
+  const int p1lo = A.off[0][0][a], p1hi = A.off[0][0][a + T];
+  const int np1 = p1hi - p1lo;
+  for (int t = tid; t <= T; t += NT) sOff1[t] = A.off[0][0][a + t] - p1lo;
+  for (int t = tid; t < 2 * np1; t += NT) {
+    const int kind = t >= np1 ? 1 : 0, q = t - kind * np1;
+    const int gq = (kind ? A.off[0][1][a] : p1lo) + q;
+    const R *Vg = static_cast<const R *>(A.V[0][kind]);
+    const R *Bg = static_cast<const R *>(A.beta[0][kind]);
+#pragma unroll
+    for (int i = 0; i < NP; i++) sV1[(kind * MAXPTS1 + q) * NP + i] = Vg[(size_t)gq * NP + i];
+#pragma unroll
+    for (int i = 0; i < 4; i++) sB1[(kind * MAXPTS1 + q) * 4 + i] = Bg[(size_t)gq * 4 + i];
+    if (kind == 0) sE1[q] = A.elem[0][0][p1lo + q];
+  }
+}
+
+// Phase B of the row kernel: (row, fibre) items, 32 per warp.  sU holds U0
+// and U1 for the chunk's coefficient columns l1lo .. l1lo+NL1-1 ([u][NL1][NPAIR]);
+// sV1, sB1, sE1, sOff1 the chunk's x1 tables; sW at least NW * 32 * pad16(2P+1)
+// values of per-warp stage.
+template <int P, int D, int MAXPTS1, int NL1, bool GENERAL, bool DO_M, bool DO_K, typename R>
+__device__ __forceinline__ void rows_phase_b(const RowsArgs &A, const R *sU, const R *sV1, const R *sB1,
+                                             const int *sE1, const int *sOff1, R *sW, const int a, const int T,
+                                             const int l1lo, const long long base) {
+  using O = typename OutT<R>::type;
+  constexpr int NP = P + 1, NB = 2 * P + 1, NT = 32 * kRowsWarps;
+  constexpr int NPAIR = (D == 3) ? NB * NB : NB, BAND = NPAIR * NB, LS = NPAIR;
+  constexpr int WST = pad16<R>(32 * NB);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // ------------------------------------------------ phase B: (row, fibre) items, 32 per warp
+  // Item i of the chunk is fibre i % NPAIR of row i / NPAIR; its 2P+1 band
+  // entries sit at offset i * NB of the chunk's output rows, so a warp's 32
+  // consecutive items own one contiguous run of 32 * NB entries per matrix.
+  // The warp stages that run in shared memory and writes it with consecutive
+  // lanes on consecutive addresses, converting to the output type there; no
+  // CTA-wide barrier is needed.
+  const R *U0 = sU;
+  const R *U1 = sU + NL1 * LS;
+  R *wst = sW + warp * WST;  // [32][NB]
+  const int nitems = T * NPAIR;
+  const long long ochunk = (base + a - A.row_begin) * BAND;
+  for (int ib = warp * 32; ib < nitems; ib += NT) {
+    const int item = ib + lane;
+    R oM[NB], oK[NB];
+    if (item < nitems) {
+      const int rl = item / NPAIR, pr = item - rl * NPAIR;
+      const int r1 = a + rl;
+      const int q0 = sOff1[rl], q1end = sOff1[rl + 1];
+      if (!GENERAL && r1 >= P && r1 <= A.N[0] - 1) {
+        // weighted Gaussian rule in x1: point q in element r1-P+q, band
+        // offset q; the row's coefficient columns kb .. kb+P+3
+        const int kb = (r1 - P) - l1lo;
+        R w0[NP + 3], w1[NP + 3], aM[NB], aK[NB];
+#pragma unroll
+        for (int i = 0; i < NP + 3; i++) {
+          w0[i] = U0[(kb + i) * LS + pr];
+          w1[i] = DO_K ? U1[(kb + i) * LS + pr] : r_zero<R>();
+        }
+#pragma unroll
+        for (int j = 0; j < NB; j++) {
+          aM[j] = r_zero<R>();
+          aK[j] = r_zero<R>();
+        }
+        const R *bm0 = &sB1[(0 * MAXPTS1 + q0) * 4];
+        const R *bs0 = &sB1[(1 * MAXPTS1 + q0) * 4];
+        const R *vm0 = &sV1[(0 * MAXPTS1 + q0) * NP];
+        const R *vs0 = &sV1[(1 * MAXPTS1 + q0) * NP];
+#pragma unroll
+        for (int q = 0; q < NP; q++) {
+          R bm[4], vm[NP], bs[4], vs[NP];
+          if constexpr (std::is_same<R, float>::value && NP == 4) {
+            const float4 b4m = reinterpret_cast<const float4 *>(bm0)[q], b4s = reinterpret_cast<const float4 *>(bs0)[q];
+            const float4 v4m = reinterpret_cast<const float4 *>(vm0)[q], v4s = reinterpret_cast<const float4 *>(vs0)[q];
+            bm[0] = b4m.x; bm[1] = b4m.y; bm[2] = b4m.z; bm[3] = b4m.w;
+            bs[0] = b4s.x; bs[1] = b4s.y; bs[2] = b4s.z; bs[3] = b4s.w;
+            vm[0] = v4m.x; vm[1] = v4m.y; vm[2] = v4m.z; vm[3] = v4m.w;
+            vs[0] = v4s.x; vs[1] = v4s.y; vs[2] = v4s.z; vs[3] = v4s.w;
+          } else {
+#pragma unroll
+            for (int i = 0; i < 4; i++) { bm[i] = bm0[q * 4 + i]; bs[i] = bs0[q * 4 + i]; }
+#pragma unroll
+            for (int i = 0; i < NP; i++) { vm[i] = vm0[q * NP + i]; vs[i] = vs0[q * NP + i]; }
+          }
+          if constexpr (DO_M) {
+            R y = r_zero<R>();
+#pragma unroll
+            for (int i = 0; i < 4; i++) y = r_fma(bm[i], w0[q + i], y);
+#pragma unroll
+            for (int i = 0; i < NP; i++) aM[q + i] = r_fma(vm[i], y, aM[q + i]);
+          }
+          if constexpr (DO_K) {
+            R yk = r_zero<R>(), ys = r_zero<R>();
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+              yk = r_fma(bm[i], w1[q + i], yk);
+              ys = r_fma(bs[i], w0[q + i], ys);
+            }
+#pragma unroll
+            for (int i = 0; i < NP; i++) aK[q + i] = r_fma(vs[i], ys, r_fma(vm[i], yk, aK[q + i]));
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < NB; j++) {
+          if constexpr (DO_M) oM[j] = aM[j];
+          if constexpr (DO_K) oK[j] = aK[j];
+        }
+      } else {
+        // Gauss-Legendre on each element of supp B_r1 (or a comparison rule):
+        // any number of points, each with its own band offset
+        R accM[NB], accK[NB];
+#pragma unroll
+        for (int j = 0; j < NB; j++) { accM[j] = r_zero<R>(); accK[j] = r_zero<R>(); }
+        for (int q = q0; q < q1end; q++) {
+          const int e = sE1[q];
+          const int k0 = e - l1lo, o = e - r1 + P;
+          const R *bm = &sB1[(0 * MAXPTS1 + q) * 4];
+          const R *vm = &sV1[(0 * MAXPTS1 + q) * NP];
+          if constexpr (DO_M) {
+            R y = r_zero<R>();
+#pragma unroll
+            for (int i = 0; i < 4; i++) y = r_fma(bm[i], U0[(k0 + i) * LS + pr], y);
+            fiber_shift<P>(accM, y, vm, o);
+          }
+          if constexpr (DO_K) {
+            const R *bs = &sB1[(1 * MAXPTS1 + q) * 4];
+            R yk = r_zero<R>(), ys = r_zero<R>();
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+              yk = r_fma(bm[i], U1[(k0 + i) * LS + pr], yk);
+              ys = r_fma(bs[i], U0[(k0 + i) * LS + pr], ys);
+            }
+            fiber_shift<P>(accK, yk, vm, o);
+            fiber_shift<P>(accK, ys, &sV1[(1 * MAXPTS1 + q) * NP], o);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < NB; j++) {
+          if constexpr (DO_M) oM[j] = accM[j];
+          if constexpr (DO_K) oK[j] = accK[j];
+        }
+      }
+    }
+    const int nent = ((nitems - ib) < 32 ? (nitems - ib) : 32) * NB;
+    if constexpr (DO_M) {
+      if (item < nitems) {
+#pragma unroll
+        for (int j = 0; j < NB; j++) wst[lane * NB + j] = oM[j];
+      }
+      __syncwarp();
+      O *gM = static_cast<O *>(A.M) + ochunk + (long long)ib * NB;
+      for (int i = lane; i < nent; i += 32) gM[i] = r_out(wst[i]);
+      __syncwarp();
+    }
+    if constexpr (DO_K) {
+      if (item < nitems) {
+#pragma unroll
+        for (int j = 0; j < NB; j++) wst[lane * NB + j] = oK[j];
+      }
+      __syncwarp();
+      O *gK = static_cast<O *>(A.K) + ochunk + (long long)ib * NB;
+      for (int i = lane; i < nent; i += 32) gK[i] = r_out(wst[i]);
+      __syncwarp();
+    }
+  }
+}
+
 // The work of one CTA: chunk `bid` of the launch's line list (line
 // bid / nch, chunk bid % nch), in the dynamic shared memory `smem_raw`
 // (RowsLayout::BYTES).  Called by rows_kernel with bid = blockIdx.x and by
@@ -190,7 +365,6 @@ __device__ __forceinline__ void rows_block(const RowsArgs &A, const int bid, uns
   using O = typename OutT<R>::type;
   static_assert(sizeof(O) == sizeof(R), "the band stage shares the R region");
   constexpr int NP = L::NP, NB = L::NB, NT = L::NT, NW = L::NW, LS = L::LS, NL = L::NL, NL1 = L::NL1;
-  constexpr int NPAIR = L::NPAIR, BAND = L::BAND;
 
   R *sV23 = reinterpret_cast<R *>(smem_raw);  // [di][kind][LM][NP]
   R *sV23d = sV23 + L::V23;                   // [di][kind][LM][NB] (boundary lines)
@@ -206,7 +380,7 @@ __device__ __forceinline__ void rows_block(const RowsArgs &A, const int bid, uns
   int *sOff1 = sE1 + L::MAXPTS1;              // [TMAX+1]
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int line = A.lines[bid / A.nch];
+  const int line = A.lines ? A.lines[bid / A.nch] : A.line0 + bid / A.nch;
   const int ch = bid % A.nch;
   const int n1 = A.n[0];
   const int r2 = (D == 3) ? line % A.n[1] : line;
@@ -257,21 +431,7 @@ __device__ __forceinline__ void rows_block(const RowsArgs &A, const int bid, uns
       }
     }
   }
-  // the chunk's x1 tables: rows [a, b) hold one contiguous range of points
-  const int p1lo = A.off[0][0][a], p1hi = A.off[0][0][b];
-  const int np1 = p1hi - p1lo;
-  for (int t = tid; t <= T; t += NT) sOff1[t] = A.off[0][0][a + t] - p1lo;
-  for (int t = tid; t < 2 * np1; t += NT) {
-    const int kind = t >= np1 ? 1 : 0, q = t - kind * np1;
-    const int gq = (kind ? A.off[0][1][a] : p1lo) + q;
-    const R *Vg = static_cast<const R *>(A.V[0][kind]);
-    const R *Bg = static_cast<const R *>(A.beta[0][kind]);
-#pragma unroll
-    for (int i = 0; i < NP; i++) sV1[(kind * L::MAXPTS1 + q) * NP + i] = Vg[(size_t)gq * NP + i];
-#pragma unroll
-    for (int i = 0; i < 4; i++) sB1[(kind * L::MAXPTS1 + q) * 4 + i] = Bg[(size_t)gq * 4 + i];
-    if (kind == 0) sE1[q] = A.elem[0][0][p1lo + q];
-  }
+  load_x1_tables<P, L::MAXPTS1, R>(A, a, T, sV1, sB1, sE1, sOff1);
   const int elo1 = a - P < 0 ? 0 : a - P;
   const int ehi1 = (b - 1) > A.N[0] - 1 ? A.N[0] - 1 : (b - 1);
   const int l1lo = elo1, nl1 = ehi1 - elo1 + 4;
@@ -440,130 +600,7 @@ __device__ __forceinline__ void rows_block(const RowsArgs &A, const int bid, uns
   }
   __syncthreads();
 
-  // ------------------------------------------------ phase B: (row, fibre) items, G rows at a time
-  // Thread t takes fibre t % NPAIR of row t / NPAIR of the group; the group's
-  // bands are staged in shared memory (in R) and copied to the output with
-  // consecutive threads on consecutive addresses, converting to the output
-  // type there.
-  const R *U0 = sU;
-  const R *U1 = sU + NL1 * LS;
-  R *stM = sW;                  // [G][BAND]
-  R *stK = sW + L::G * BAND;    // [G][BAND]
-  for (int g0 = 0; g0 < T; g0 += L::G) {
-    const int gn = (T - g0) < L::G ? (T - g0) : L::G;
-    if (tid < gn * NPAIR) {
-      const int rg = tid / NPAIR, pr = tid - rg * NPAIR;
-      const int rl = g0 + rg, r1 = a + rl;
-      const int q0 = sOff1[rl], q1end = sOff1[rl + 1];
-      R *oM = stM + rg * BAND + pr * NB;
-      R *oK = stK + rg * BAND + pr * NB;
-      if (!L::GENERAL && r1 >= P && r1 <= A.N[0] - 1) {
-        // weighted Gaussian rule in x1: point q in element r1-P+q, band
-        // offset q; the row's coefficient columns kb .. kb+P+3
-        const int kb = (r1 - P) - l1lo;
-        R w0[NP + 3], w1[NP + 3], aM[NB], aK[NB];
-#pragma unroll
-        for (int i = 0; i < NP + 3; i++) {
-          w0[i] = U0[(kb + i) * LS + pr];
-          w1[i] = DO_K ? U1[(kb + i) * LS + pr] : r_zero<R>();
-        }
-#pragma unroll
-        for (int j = 0; j < NB; j++) {
-          aM[j] = r_zero<R>();
-          aK[j] = r_zero<R>();
-        }
-        const R *bm0 = &sB1[(0 * L::MAXPTS1 + q0) * 4];
-        const R *bs0 = &sB1[(1 * L::MAXPTS1 + q0) * 4];
-        const R *vm0 = &sV1[(0 * L::MAXPTS1 + q0) * NP];
-        const R *vs0 = &sV1[(1 * L::MAXPTS1 + q0) * NP];
-#pragma unroll
-        for (int q = 0; q < NP; q++) {
-          R bm[4], vm[NP], bs[4], vs[NP];
-          if constexpr (std::is_same<R, float>::value && NP == 4) {
-            const float4 b4m = reinterpret_cast<const float4 *>(bm0)[q], b4s = reinterpret_cast<const float4 *>(bs0)[q];
-            const float4 v4m = reinterpret_cast<const float4 *>(vm0)[q], v4s = reinterpret_cast<const float4 *>(vs0)[q];
-            bm[0] = b4m.x; bm[1] = b4m.y; bm[2] = b4m.z; bm[3] = b4m.w;
-            bs[0] = b4s.x; bs[1] = b4s.y; bs[2] = b4s.z; bs[3] = b4s.w;
-            vm[0] = v4m.x; vm[1] = v4m.y; vm[2] = v4m.z; vm[3] = v4m.w;
-            vs[0] = v4s.x; vs[1] = v4s.y; vs[2] = v4s.z; vs[3] = v4s.w;
-          } else {
-#pragma unroll
-            for (int i = 0; i < 4; i++) { bm[i] = bm0[q * 4 + i]; bs[i] = bs0[q * 4 + i]; }
-#pragma unroll
-            for (int i = 0; i < NP; i++) { vm[i] = vm0[q * NP + i]; vs[i] = vs0[q * NP + i]; }
-          }
-          if constexpr (DO_M) {
-            R y = r_zero<R>();
-#pragma unroll
-            for (int i = 0; i < 4; i++) y = r_fma(bm[i], w0[q + i], y);
-#pragma unroll
-            for (int i = 0; i < NP; i++) aM[q + i] = r_fma(vm[i], y, aM[q + i]);
-          }
-          if constexpr (DO_K) {
-            R yk = r_zero<R>(), ys = r_zero<R>();
-#pragma unroll
-            for (int i = 0; i < 4; i++) {
-              yk = r_fma(bm[i], w1[q + i], yk);
-              ys = r_fma(bs[i], w0[q + i], ys);
-            }
-#pragma unroll
-            for (int i = 0; i < NP; i++) aK[q + i] = r_fma(vs[i], ys, r_fma(vm[i], yk, aK[q + i]));
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < NB; j++) {
-          if constexpr (DO_M) oM[j] = aM[j];
-          if constexpr (DO_K) oK[j] = aK[j];
-        }
-      } else {
-        // Gauss-Legendre on each element of supp B_r1 (or a comparison rule):
-        // any number of points, each with its own band offset
-        R accM[NB], accK[NB];
-#pragma unroll
-        for (int j = 0; j < NB; j++) { accM[j] = r_zero<R>(); accK[j] = r_zero<R>(); }
-        for (int q = q0; q < q1end; q++) {
-          const int e = sE1[q];
-          const int k0 = e - l1lo, o = e - r1 + P;
-          const R *bm = &sB1[(0 * L::MAXPTS1 + q) * 4];
-          const R *vm = &sV1[(0 * L::MAXPTS1 + q) * NP];
-          if constexpr (DO_M) {
-            R y = r_zero<R>();
-#pragma unroll
-            for (int i = 0; i < 4; i++) y = r_fma(bm[i], U0[(k0 + i) * LS + pr], y);
-            fiber_shift<P>(accM, y, vm, o);
-          }
-          if constexpr (DO_K) {
-            const R *bs = &sB1[(1 * L::MAXPTS1 + q) * 4];
-            R yk = r_zero<R>(), ys = r_zero<R>();
-#pragma unroll
-            for (int i = 0; i < 4; i++) {
-              yk = r_fma(bm[i], U1[(k0 + i) * LS + pr], yk);
-              ys = r_fma(bs[i], U0[(k0 + i) * LS + pr], ys);
-            }
-            fiber_shift<P>(accK, yk, vm, o);
-            fiber_shift<P>(accK, ys, &sV1[(1 * L::MAXPTS1 + q) * NP], o);
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < NB; j++) {
-          if constexpr (DO_M) oM[j] = accM[j];
-          if constexpr (DO_K) oK[j] = accK[j];
-        }
-      }
-    }
-    __syncthreads();
-    // the group's rows are consecutive in the output
-    const long long orow = (base + a + g0 - A.row_begin) * BAND;
-    if constexpr (DO_M) {
-      O *gM = static_cast<O *>(A.M) + orow;
-      for (int i = tid; i < gn * BAND; i += NT) gM[i] = r_out(stM[i]);
-    }
-    if constexpr (DO_K) {
-      O *gK = static_cast<O *>(A.K) + orow;
-      for (int i = tid; i < gn * BAND; i += NT) gK[i] = r_out(stK[i]);
-    }
-    __syncthreads();
-  }
+  rows_phase_b<P, D, L::MAXPTS1, NL1, L::GENERAL, DO_M, DO_K, R>(A, sU, sV1, sB1, sE1, sOff1, sW, a, T, l1lo, base);
 }
 
 template <int P, int D, int LM, int TMAX, bool DO_M, bool DO_K, typename R>

@@ -28,8 +28,13 @@ template <typename R> constexpr size_t batch_smem_bytes() {
   return ab > cd ? ab : cd;
 }
 
+// The batch kernel holds four bodies in one register allocation: it asks for
+// one resident CTA per SM fewer than the single-class kernels so that the
+// union does not spill.
+template <typename R> constexpr int batch_min_blocks() { return sizeof(R) == 4 ? 3 : 2; }
+
 template <typename R>
-__global__ void __launch_bounds__(32 * kRowsWarps, rows_min_blocks<R>())
+__global__ void __launch_bounds__(32 * kRowsWarps, batch_min_blocks<R>())
     batch_rows_kernel(const BatchSeg *__restrict__ segs, int nseg, int nitems, unsigned *counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ RowsArgs sA;

@@ -449,11 +449,7 @@ wq_status build_host_tables(wq_rules *R) {
 // sum-factorised over the coefficients of each line of rows.
 int chunk_length(const wq_rules *R, int tmax) {
   const int n1 = R->n[0], nch = (n1 + tmax - 1) / tmax;
-  int npair = 1;
-  for (int a = 1; a < R->dim; a++) npair *= 2 * R->p + 1;
-  const int g = std::max(1, std::min(tmax, 256 / npair));
-  const int t = (n1 + nch - 1) / nch;
-  return std::min(tmax, (t + g - 1) / g * g);
+  return (n1 + nch - 1) / nch;
 }
 
 int max_chunk_points(const wq_rules *R, int T) {

@@ -1,0 +1,386 @@
+// The 3D assembly split in two kernels.
+//
+// u_kernel computes, for every line (r2, r3) in a range and every coefficient
+// column l1, the two partial contractions of the row kernel's first phase
+// (Eq. Decompo applied to the weighted sums of Eq. GaussQuadSys and
+// Eq. GaussQuadSysStiff, with the coefficient spline c as the integrand's
+// factor):
+//   T3_k3[l1][l2][j3] = sum_q3 (sum_i3 C[l1][l2][e3(q3)+i3] b3_k3[q3][i3]) V3_k3[q3][j3-o3]
+//   U0[l1][j3][j2] = sum_q2 Cq_MM[q2][j3] V2M[q2][j2-o2]
+//   U1[l1][j3][j2] = sum_q2 Cq_SM[q2][j3] V2S[q2][j2-o2] + Cq_MS[q2][j3] V2M[q2][j2-o2]
+//   Cq_c[q2][j3]   = sum_i2 T3_k3(c)[l1][e2(q2)+i2][j3] b2_k2(c)[q2][i2]
+// and stores U in global memory, [line][u][l1][j3*(2P+1)+j2].  T3 depends on
+// r3 only, so a CTA takes a block of kULines lines of one plane (same r3) and
+// kUCols columns and computes T3 once for all of them; each line's x2 stage
+// then reads it from shared memory.  The operation order of every value is
+// the row kernel's, so the split and the fused path give the same bits.
+//
+// rows_ug_kernel is the row kernel without its first phase: it copies the
+// chunk's U columns from global memory and runs phase B.  All lines take the
+// same path (the x2/x3 rule lengths no longer matter), so one launch covers a
+// range of lines.
+#pragma once
+
+#include "assemble.cuh"
+
+namespace wq {
+
+constexpr int kULines = 8, kUCols = 8;
+
+struct UArgs {
+  const int *off[3][2];
+  const int *elem[3][2];
+  const void *V[3][2];
+  const void *beta[3][2];
+  int n[3], N[3], nc[3];
+  const double *coef;  // may be null: c = 1
+  const void *coefR;   // the same in R (checked), or null
+  void *U;             // [line][2][nc1][(2P+1)^2] in R
+  int line_lo, line_hi;  // lines [line_lo, line_hi] are written
+  int r3_lo;             // plane of the launch's first CTA
+  int nblk2, nblk1;      // line blocks per plane, column blocks
+  unsigned *status;
+};
+
+template <int P, typename R> struct ULayout {
+  static constexpr int NP = P + 1, NB = 2 * P + 1;
+  static constexpr int LM = P * (P + 1);          // most points of one row in one direction
+  static constexpr int NL2 = kULines + P + 3;      // x2 coefficient indices of the CTA's lines
+  static constexpr int NL3 = P + 4;                // x3 coefficient indices of one row
+  static constexpr int V3 = pad16<R>(2 * LM * NP);             // [k3][q3][i]
+  static constexpr int B3 = pad16<R>(2 * LM * 4);              // [k3][q3][i]
+  static constexpr int V2 = pad16<R>(kULines * 2 * LM * NP);   // [b][k2][q2][i]
+  static constexpr int B2 = pad16<R>(kULines * 2 * LM * 4);    // [b][k2][q2][i]
+  static constexpr int CB = pad16<R>(kUCols * NL2 * NL3);      // [l1][l2][l3]
+  static constexpr int T3 = pad16<R>(2 * kUCols * NL2 * NB);   // [k3][l1][l2][j3]
+  static constexpr int R_TOTAL = V3 + B3 + V2 + B2 + CB + T3;
+  // int region: e3[LM], o3[LM], L2[kULines], e2[kULines][LM], o2[kULines][LM]
+  static constexpr int I_TOTAL = 2 * LM + kULines + 2 * kULines * LM;
+  static constexpr size_t BYTES = sizeof(R) * (size_t)R_TOTAL + sizeof(int) * (size_t)I_TOTAL;
+};
+
+template <int P, typename R>
+__global__ void __launch_bounds__(256) u_kernel(const UArgs A) {
+  using L = ULayout<P, R>;
+  constexpr int NP = L::NP, NB = L::NB, NPAIR = NB * NB, LM = L::LM, NL2 = L::NL2, NL3 = L::NL3;
+  constexpr int NT = 256;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R *sV3 = reinterpret_cast<R *>(smem_raw);
+  R *sB3 = sV3 + L::V3;
+  R *sV2 = sB3 + L::B3;
+  R *sB2 = sV2 + L::V2;
+  R *sCb = sB2 + L::B2;
+  R *sT3 = sCb + L::CB;
+  int *sE3 = reinterpret_cast<int *>(smem_raw + sizeof(R) * (size_t)L::R_TOTAL);
+  int *sO3 = sE3 + LM;
+  int *sL2 = sO3 + LM;
+  int *sE2 = sL2 + kULines;
+  int *sO2 = sE2 + kULines * LM;
+
+  const int tid = threadIdx.x;
+  const int n2 = A.n[1], nc1 = A.nc[0], nc2 = A.nc[1];
+  int bid = blockIdx.x;
+  const int b1 = bid % A.nblk1;
+  bid /= A.nblk1;
+  const int b2 = bid % A.nblk2;
+  const int r3 = A.r3_lo + bid / A.nblk2;
+  const int r2a = b2 * kULines;
+  const int nlines = (n2 - r2a) < kULines ? (n2 - r2a) : kULines;
+  const int lid0 = r2a + n2 * r3;
+  if (lid0 + nlines - 1 < A.line_lo || lid0 > A.line_hi) return;
+  const int l1a = b1 * kUCols;
+  const int ncols = (nc1 - l1a) < kUCols ? (nc1 - l1a) : kUCols;
+
+  // x3 rule of row r3
+  const int off30 = A.off[2][0][r3], off31 = A.off[2][1][r3];
+  const int L3 = A.off[2][0][r3 + 1] - off30;
+  for (int t = tid; t < 2 * LM; t += NT) {
+    const int kind = t / LM, q = t % LM;
+    if (q < L3) {
+      const int gq = (kind ? off31 : off30) + q;
+      const R *Vg = static_cast<const R *>(A.V[2][kind]);
+      const R *Bg = static_cast<const R *>(A.beta[2][kind]);
+#pragma unroll
+      for (int i = 0; i < NP; i++) sV3[(kind * LM + q) * NP + i] = Vg[(size_t)gq * NP + i];
+#pragma unroll
+      for (int i = 0; i < 4; i++) sB3[(kind * LM + q) * 4 + i] = Bg[(size_t)gq * 4 + i];
+      if (kind == 0) {
+        const int e = A.elem[2][0][gq];
+        sE3[q] = e;
+        sO3[q] = e - r3 + P;
+      }
+    }
+  }
+  // x2 rules of the block's lines
+  for (int t = tid; t < kULines * 2 * LM; t += NT) {
+    const int b = t / (2 * LM), kind = (t / LM) % 2, q = t % LM;
+    if (b < nlines) {
+      const int r2 = r2a + b;
+      const int off0 = A.off[1][0][r2];
+      const int L2b = A.off[1][0][r2 + 1] - off0;
+      if (kind == 0 && q == 0) sL2[b] = L2b;
+      if (q < L2b) {
+        const int gq = (kind ? A.off[1][1][r2] : off0) + q;
+        const R *Vg = static_cast<const R *>(A.V[1][kind]);
+        const R *Bg = static_cast<const R *>(A.beta[1][kind]);
+#pragma unroll
+        for (int i = 0; i < NP; i++) sV2[((b * 2 + kind) * LM + q) * NP + i] = Vg[(size_t)gq * NP + i];
+#pragma unroll
+        for (int i = 0; i < 4; i++) sB2[((b * 2 + kind) * LM + q) * 4 + i] = Bg[(size_t)gq * 4 + i];
+        if (kind == 0) {
+          const int e = A.elem[1][0][gq];
+          sE2[b * LM + q] = e;
+          sO2[b * LM + q] = e - r2 + P;
+        }
+      }
+    }
+  }
+  // the coefficient block: columns l1a.., x2 indices l2lo.., x3 indices l3lo..
+  const int l2lo = (r2a - P) > 0 ? (r2a - P) : 0;
+  const int l2hi = ((r2a + nlines - 1) < (A.N[1] - 1) ? (r2a + nlines - 1) : (A.N[1] - 1)) + 3;
+  const int nl2 = l2hi - l2lo + 1;
+  const int l3lo = (r3 - P) > 0 ? (r3 - P) : 0;
+  const int nl3 = (r3 < A.N[2] - 1 ? r3 : A.N[2] - 1) - l3lo + 4;
+  {
+    unsigned bad = 0;
+    const double *cg = A.coef;
+    const R *cr = static_cast<const R *>(A.coefR);
+    for (int t = tid; t < NL3 * NL2 * kUCols; t += NT) {
+      const int l1 = t % kUCols, l2 = (t / kUCols) % NL2, l3 = t / (kUCols * NL2);
+      if (l1 < ncols && l2 < nl2 && l3 < nl3) {
+        const long long g = (long long)(l1a + l1) + (long long)nc1 * ((long long)(l2lo + l2) + (long long)nc2 * (l3lo + l3));
+        R v;
+        if (cr) {
+          v = cr[g];
+        } else if (cg) {
+          const double x = cg[g];
+          if (!isfinite(x)) bad = 1;
+          v = r_from_double<R>(x);
+        } else {
+          v = r_from_double<R>(1.0);
+        }
+        sCb[(l1 * NL2 + l2) * NL3 + l3] = v;
+      }
+    }
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    if (bad && (tid & 31) == 0) atomicOr(A.status, 2u);
+  }
+  __syncthreads();
+
+  // x3 stage, once for the block: items (k3, l1, l2)
+  const bool in3 = r3 >= P && r3 <= A.N[2] - 1;
+  for (int t = tid; t < 2 * kUCols * NL2; t += NT) {
+    const int l2 = t % NL2, l1 = (t / NL2) % kUCols, k3 = t / (NL2 * kUCols);
+    if (l1 < ncols && l2 < nl2) {
+      const R *cb = &sCb[(l1 * NL2 + l2) * NL3];
+      R acc[NB];
+#pragma unroll
+      for (int j = 0; j < NB; j++) acc[j] = r_zero<R>();
+      if (in3) {
+#pragma unroll
+        for (int q3 = 0; q3 < NP; q3++) {
+          const int e = sE3[q3] - l3lo;
+          const R *bb = &sB3[(k3 * LM + q3) * 4];
+          R z = r_zero<R>();
+#pragma unroll
+          for (int i = 0; i < 4; i++) z = r_fma(cb[e + i], bb[i], z);
+          const R *v = &sV3[(k3 * LM + q3) * NP];
+#pragma unroll
+          for (int i = 0; i < NP; i++) acc[q3 + i] = r_fma(z, v[i], acc[q3 + i]);
+        }
+      } else {
+        for (int q3 = 0; q3 < L3; q3++) {
+          const int e = sE3[q3] - l3lo;
+          const R *bb = &sB3[(k3 * LM + q3) * 4];
+          R z = r_zero<R>();
+#pragma unroll
+          for (int i = 0; i < 4; i++) z = r_fma(cb[e + i], bb[i], z);
+          fiber_shift<P>(acc, z, &sV3[(k3 * LM + q3) * NP], sO3[q3]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NB; j++) sT3[((k3 * kUCols + l1) * NL2 + l2) * NB + j] = acc[j];
+    }
+  }
+  __syncthreads();
+
+  // x2 stage per line: items (line, l1, j3)
+  R *Ug = static_cast<R *>(A.U);
+  for (int t = tid; t < kULines * kUCols * NB; t += NT) {
+    const int j3 = t % NB, l1 = (t / NB) % kUCols, b = t / (NB * kUCols);
+    if (b >= nlines || l1 >= ncols) continue;
+    const int lid = lid0 + b;
+    if (lid < A.line_lo || lid > A.line_hi) continue;
+    const int r2 = r2a + b, L2 = sL2[b];
+    const bool in2 = r2 >= P && r2 <= A.N[1] - 1;
+    const R *t3m = &sT3[((0 * kUCols + l1) * NL2) * NB + j3];  // k3 = 0, index by l2 * NB
+    const R *t3s = &sT3[((1 * kUCols + l1) * NL2) * NB + j3];  // k3 = 1
+    const R *v2 = &sV2[(b * 2) * LM * NP];
+    const R *b2 = &sB2[(b * 2) * LM * 4];
+    R u0[NB], u1[NB];
+#pragma unroll
+    for (int j = 0; j < NB; j++) {
+      u0[j] = r_zero<R>();
+      u1[j] = r_zero<R>();
+    }
+    if (in2 && in3) {
+      // interior line: the row kernel's order, all q2 of (S, M) before (M, S)
+      R c0[NP], c1[NP], c2[NP];
+#pragma unroll
+      for (int q2 = 0; q2 < NP; q2++) {
+        const int e = sE2[b * LM + q2] - l2lo;
+        const R *bm = &b2[(0 * LM + q2) * 4], *bs = &b2[(1 * LM + q2) * 4];
+        R s0 = r_zero<R>(), s1 = r_zero<R>(), s2 = r_zero<R>();
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+          s0 = r_fma(t3m[(e + i) * NB], bm[i], s0);
+          s1 = r_fma(t3m[(e + i) * NB], bs[i], s1);
+          s2 = r_fma(t3s[(e + i) * NB], bm[i], s2);
+        }
+        c0[q2] = s0;
+        c1[q2] = s1;
+        c2[q2] = s2;
+      }
+#pragma unroll
+      for (int q2 = 0; q2 < NP; q2++) {
+        const R *vm = &v2[(0 * LM + q2) * NP];
+#pragma unroll
+        for (int i = 0; i < NP; i++) u0[q2 + i] = r_fma(c0[q2], vm[i], u0[q2 + i]);
+      }
+#pragma unroll
+      for (int q2 = 0; q2 < NP; q2++) {
+        const R *vs = &v2[(1 * LM + q2) * NP];
+#pragma unroll
+        for (int i = 0; i < NP; i++) u1[q2 + i] = r_fma(c1[q2], vs[i], u1[q2 + i]);
+      }
+#pragma unroll
+      for (int q2 = 0; q2 < NP; q2++) {
+        const R *vm = &v2[(0 * LM + q2) * NP];
+#pragma unroll
+        for (int i = 0; i < NP; i++) u1[q2 + i] = r_fma(c2[q2], vm[i], u1[q2 + i]);
+      }
+    } else {
+      // boundary line: per point, (S, M) then (M, S)
+      for (int q2 = 0; q2 < L2; q2++) {
+        const int e = sE2[b * LM + q2] - l2lo, o = sO2[b * LM + q2];
+        const R *bm = &b2[(0 * LM + q2) * 4], *bs = &b2[(1 * LM + q2) * 4];
+        R s0 = r_zero<R>(), s1 = r_zero<R>(), s2 = r_zero<R>();
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+          s0 = r_fma(t3m[(e + i) * NB], bm[i], s0);
+          s1 = r_fma(t3m[(e + i) * NB], bs[i], s1);
+          s2 = r_fma(t3s[(e + i) * NB], bm[i], s2);
+        }
+        fiber_shift<P>(u0, s0, &v2[(0 * LM + q2) * NP], o);
+        fiber_shift<P>(u1, s1, &v2[(1 * LM + q2) * NP], o);
+        fiber_shift<P>(u1, s2, &v2[(0 * LM + q2) * NP], o);
+      }
+    }
+    R *dst0 = Ug + (((size_t)lid * 2 + 0) * nc1 + (l1a + l1)) * NPAIR + j3 * NB;
+    R *dst1 = Ug + (((size_t)lid * 2 + 1) * nc1 + (l1a + l1)) * NPAIR + j3 * NB;
+#pragma unroll
+    for (int j = 0; j < NB; j++) {
+      dst0[j] = u0[j];
+      dst1[j] = u1[j];
+    }
+  }
+}
+
+// Row kernel of the split path: x1 tables and U columns in shared memory, then phase B.
+template <int P, int TMAX, bool DO_M, bool DO_K, typename R> struct RowsLayoutUG {
+  static constexpr int NP = P + 1, NB = 2 * P + 1, NPAIR = NB * NB;
+  static constexpr int NL1 = TMAX + P + 3;
+  static constexpr int NU = DO_K ? 2 : 1;
+  static constexpr int NW = kRowsWarps;
+  static constexpr int MAXPTS1 = TMAX * NP + P * NP * (P - 1);
+  static constexpr int V1 = pad16<R>(2 * MAXPTS1 * NP);
+  static constexpr int B1 = pad16<R>(2 * MAXPTS1 * 4);
+  static constexpr int US = pad16<R>(NU * NL1 * NPAIR);
+  static constexpr int STAGE = NW * pad16<R>(32 * NB);
+  static constexpr int R_TOTAL = V1 + B1 + US + STAGE;
+  static constexpr int I_TOTAL = MAXPTS1 + TMAX + 1;
+  static constexpr size_t BYTES = sizeof(R) * (size_t)R_TOTAL + sizeof(int) * (size_t)I_TOTAL;
+};
+
+template <int P, int TMAX, bool DO_M, bool DO_K, typename R>
+__global__ void __launch_bounds__(32 * kRowsWarps, rows_min_blocks<R>()) rows_ug_kernel(const RowsArgs A) {
+  using L = RowsLayoutUG<P, TMAX, DO_M, DO_K, R>;
+  constexpr int NPAIR = L::NPAIR, NL1 = L::NL1, NT = 32 * kRowsWarps;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R *sV1 = reinterpret_cast<R *>(smem_raw);
+  R *sB1 = sV1 + L::V1;
+  R *sU = sB1 + L::B1;
+  R *sW = sU + L::US;
+  int *sE1 = reinterpret_cast<int *>(smem_raw + sizeof(R) * (size_t)L::R_TOTAL);
+  int *sOff1 = sE1 + L::MAXPTS1;
+
+  const int tid = threadIdx.x;
+  const int line = A.line0 + (int)(blockIdx.x / A.nch);
+  const int ch = blockIdx.x % A.nch;
+  const int n1 = A.n[0];
+  const long long base = (long long)line * n1;
+  long long lo = (long long)ch * A.T, hi = lo + A.T;
+  if (hi > n1) hi = n1;
+  if (lo < A.row_begin - base) lo = A.row_begin - base;
+  if (hi > A.row_end - base) hi = A.row_end - base;
+  if (lo >= hi) return;
+  const int a = (int)lo, b = (int)hi, T = b - a;
+
+  load_x1_tables<P, L::MAXPTS1, R>(A, a, T, sV1, sB1, sE1, sOff1);
+  const int elo1 = a - P < 0 ? 0 : a - P;
+  const int ehi1 = (b - 1) > A.N[0] - 1 ? A.N[0] - 1 : (b - 1);
+  const int l1lo = elo1, nl1 = ehi1 - elo1 + 4;
+  const R *Ug = static_cast<const R *>(A.Ug);
+  const int nc1 = A.nc[0];
+#pragma unroll
+  for (int u = 0; u < L::NU; u++) {
+    const R *src = Ug + (((size_t)line * 2 + u) * nc1 + l1lo) * NPAIR;
+    R *dst = sU + u * NL1 * NPAIR;
+    for (int i = tid; i < nl1 * NPAIR; i += NT) dst[i] = src[i];
+  }
+  __syncthreads();
+  rows_phase_b<P, 3, L::MAXPTS1, NL1, false, DO_M, DO_K, R>(A, sU, sV1, sB1, sE1, sOff1, sW, a, T, l1lo, base);
+}
+
+// Chunk length of the split row kernel (every line, any rule lengths in x2, x3).
+#ifndef WQ_UG_CHUNK
+#define WQ_UG_CHUNK 32
+#endif
+constexpr int kUGChunk = WQ_UG_CHUNK;
+
+template <int P, typename R> cudaError_t launch_u(const UArgs &a, int nblocks, cudaStream_t s) {
+  using L = ULayout<P, R>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(u_kernel<P, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (nblocks <= 0) return cudaSuccess;
+  u_kernel<P, R><<<nblocks, 256, L::BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int P, bool DO_M, bool DO_K, typename R>
+cudaError_t launch_ug_one(const RowsArgs &a, int nblocks, cudaStream_t s) {
+  using L = RowsLayoutUG<P, kUGChunk, DO_M, DO_K, R>;
+  auto kern = rows_ug_kernel<P, kUGChunk, DO_M, DO_K, R>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (nblocks <= 0) return cudaSuccess;
+  kern<<<nblocks, 32 * kRowsWarps, L::BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int P, typename R>
+cudaError_t launch_rows_ug(bool do_m, bool do_k, const RowsArgs &a, int nblocks, cudaStream_t s) {
+  if (do_m && do_k) return launch_ug_one<P, true, true, R>(a, nblocks, s);
+  if (do_m) return launch_ug_one<P, true, false, R>(a, nblocks, s);
+  return launch_ug_one<P, false, true, R>(a, nblocks, s);
+}
+
+}  // namespace wq

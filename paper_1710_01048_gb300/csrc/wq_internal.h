@@ -81,6 +81,8 @@ struct wq_rules {
   unsigned *dev_status = nullptr;
   float *dev_coef32 = nullptr;   // the coefficients rounded to float (mixed mode)
   float2 *dev_coefdd = nullptr;  // the coefficients as double-float pairs (df64 mode)
+  void *dev_U = nullptr;         // 3D: the partial contractions U of every line, [line][2][nc1][(2p+1)^2], 8-byte
+                                 // elements (the split assembly path; its own allocation)
 };
 
 namespace wq {
@@ -90,8 +92,7 @@ wq_status default_rule(int p, int kind, double *tau, double *omega);
 wq_status build_host_tables(wq_rules *R);
 wq_status nc_rule(int p, int kind, double *y, double *v);
 // Chunk length for lines of n1 rows and a capacity of tmax rows: the even
-// split ceil(n1 / ceil(n1 / tmax)), rounded up to whole groups of rows of the
-// kernel's second phase (floor(256 / (2p+1)^(dim-1)) rows), at most tmax.
+// split ceil(n1 / ceil(n1 / tmax)).
 int chunk_length(const wq_rules *R, int tmax);
 // Most x1 points one chunk holds when lines are cut into chunks of T rows
 // (the last one ragged), as the launches cut them.
