@@ -12,7 +12,9 @@
 // and stores U in global memory, [line][u][l1][j3*(2P+1)+j2].  T3 depends on
 // r3 only, so a CTA takes a block of kULines lines of one plane (same r3) and
 // kUCols columns and computes T3 once for all of them; each line's x2 stage
-// then reads it from shared memory.  The operation order of every value is
+// then reads it from shared memory.  Each warp stages its items' U values in
+// shared memory and writes them with consecutive lanes on consecutive
+// addresses.  The operation order of every value is
 // the row kernel's, so the split and the fused path give the same bits.
 //
 // rows_ug_kernel is the row kernel without its first phase: it copies the
@@ -25,7 +27,10 @@
 
 namespace wq {
 
-constexpr int kULines = 8, kUCols = 8;
+#ifndef WQ_UCOLS
+#define WQ_UCOLS 8
+#endif
+constexpr int kULines = 8, kUCols = WQ_UCOLS;
 
 struct UArgs {
   const int *off[3][2];
@@ -53,7 +58,8 @@ template <int P, typename R> struct ULayout {
   static constexpr int B2 = pad16<R>(kULines * 2 * LM * 4);    // [b][k2][q2][i]
   static constexpr int CB = pad16<R>(kUCols * NL2 * NL3);      // [l1][l2][l3]
   static constexpr int T3 = pad16<R>(2 * kUCols * NL2 * NB);   // [k3][l1][l2][j3]
-  static constexpr int R_TOTAL = V3 + B3 + V2 + B2 + CB + T3;
+  static constexpr int WST = pad16<R>(32 * NB);                // per-warp stage
+  static constexpr int R_TOTAL = V3 + B3 + V2 + B2 + CB + T3 + 8 * WST;
   // int region: e3[LM], o3[LM], L2[kULines], e2[kULines][LM], o2[kULines][LM]
   static constexpr int I_TOTAL = 2 * LM + kULines + 2 * kULines * LM;
   static constexpr size_t BYTES = sizeof(R) * (size_t)R_TOTAL + sizeof(int) * (size_t)I_TOTAL;
@@ -71,6 +77,7 @@ __global__ void __launch_bounds__(256) u_kernel(const UArgs A) {
   R *sB2 = sV2 + L::V2;
   R *sCb = sB2 + L::B2;
   R *sT3 = sCb + L::CB;
+  R *sSt = sT3 + L::T3;
   int *sE3 = reinterpret_cast<int *>(smem_raw + sizeof(R) * (size_t)L::R_TOTAL);
   int *sO3 = sE3 + LM;
   int *sL2 = sO3 + LM;
@@ -204,84 +211,103 @@ __global__ void __launch_bounds__(256) u_kernel(const UArgs A) {
   }
   __syncthreads();
 
-  // x2 stage per line: items (line, l1, j3)
+  // x2 stage per line: items (line, l1, j3), 32 per warp
   R *Ug = static_cast<R *>(A.U);
-  for (int t = tid; t < kULines * kUCols * NB; t += NT) {
-    const int j3 = t % NB, l1 = (t / NB) % kUCols, b = t / (NB * kUCols);
-    if (b >= nlines || l1 >= ncols) continue;
+  const int lane = tid & 31, warp = tid >> 5;
+  R *wst = sSt + warp * L::WST;
+  constexpr int NITEM = kULines * kUCols * NB;
+  auto item_ok = [&](int t) {
+    const int l1 = (t / NB) % kUCols, b = t / (NB * kUCols);
     const int lid = lid0 + b;
-    if (lid < A.line_lo || lid > A.line_hi) continue;
-    const int r2 = r2a + b, L2 = sL2[b];
-    const bool in2 = r2 >= P && r2 <= A.N[1] - 1;
-    const R *t3m = &sT3[((0 * kUCols + l1) * NL2) * NB + j3];  // k3 = 0, index by l2 * NB
-    const R *t3s = &sT3[((1 * kUCols + l1) * NL2) * NB + j3];  // k3 = 1
-    const R *v2 = &sV2[(b * 2) * LM * NP];
-    const R *b2 = &sB2[(b * 2) * LM * 4];
+    return b < nlines && l1 < ncols && lid >= A.line_lo && lid <= A.line_hi;
+  };
+  for (int t0 = warp * 32; t0 < NITEM; t0 += NT) {
+    const int t = t0 + lane;
+    const int j3 = t % NB, l1 = (t / NB) % kUCols, b = t / (NB * kUCols);
+    const bool ok = t < NITEM && item_ok(t);
     R u0[NB], u1[NB];
 #pragma unroll
     for (int j = 0; j < NB; j++) {
       u0[j] = r_zero<R>();
       u1[j] = r_zero<R>();
     }
-    if (in2 && in3) {
-      // interior line: the row kernel's order, all q2 of (S, M) before (M, S)
-      R c0[NP], c1[NP], c2[NP];
+    if (ok) {
+      const int r2 = r2a + b, L2 = sL2[b];
+      const bool in2 = r2 >= P && r2 <= A.N[1] - 1;
+      const R *t3m = &sT3[((0 * kUCols + l1) * NL2) * NB + j3];  // k3 = 0, index by l2 * NB
+      const R *t3s = &sT3[((1 * kUCols + l1) * NL2) * NB + j3];  // k3 = 1
+      const R *v2 = &sV2[(b * 2) * LM * NP];
+      const R *b2 = &sB2[(b * 2) * LM * 4];
+      if (in2 && in3) {
+        // interior line: the row kernel's order, all q2 of (S, M) before (M, S)
+        R c0[NP], c1[NP], c2[NP];
 #pragma unroll
-      for (int q2 = 0; q2 < NP; q2++) {
-        const int e = sE2[b * LM + q2] - l2lo;
-        const R *bm = &b2[(0 * LM + q2) * 4], *bs = &b2[(1 * LM + q2) * 4];
-        R s0 = r_zero<R>(), s1 = r_zero<R>(), s2 = r_zero<R>();
+        for (int q2 = 0; q2 < NP; q2++) {
+          const int e = sE2[b * LM + q2] - l2lo;
+          const R *bm = &b2[(0 * LM + q2) * 4], *bs = &b2[(1 * LM + q2) * 4];
+          R s0 = r_zero<R>(), s1 = r_zero<R>(), s2 = r_zero<R>();
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
-          s0 = r_fma(t3m[(e + i) * NB], bm[i], s0);
-          s1 = r_fma(t3m[(e + i) * NB], bs[i], s1);
-          s2 = r_fma(t3s[(e + i) * NB], bm[i], s2);
+          for (int i = 0; i < 4; i++) {
+            s0 = r_fma(t3m[(e + i) * NB], bm[i], s0);
+            s1 = r_fma(t3m[(e + i) * NB], bs[i], s1);
+            s2 = r_fma(t3s[(e + i) * NB], bm[i], s2);
+          }
+          c0[q2] = s0;
+          c1[q2] = s1;
+          c2[q2] = s2;
         }
-        c0[q2] = s0;
-        c1[q2] = s1;
-        c2[q2] = s2;
-      }
 #pragma unroll
-      for (int q2 = 0; q2 < NP; q2++) {
-        const R *vm = &v2[(0 * LM + q2) * NP];
+        for (int q2 = 0; q2 < NP; q2++) {
+          const R *vm = &v2[(0 * LM + q2) * NP];
 #pragma unroll
-        for (int i = 0; i < NP; i++) u0[q2 + i] = r_fma(c0[q2], vm[i], u0[q2 + i]);
-      }
-#pragma unroll
-      for (int q2 = 0; q2 < NP; q2++) {
-        const R *vs = &v2[(1 * LM + q2) * NP];
-#pragma unroll
-        for (int i = 0; i < NP; i++) u1[q2 + i] = r_fma(c1[q2], vs[i], u1[q2 + i]);
-      }
-#pragma unroll
-      for (int q2 = 0; q2 < NP; q2++) {
-        const R *vm = &v2[(0 * LM + q2) * NP];
-#pragma unroll
-        for (int i = 0; i < NP; i++) u1[q2 + i] = r_fma(c2[q2], vm[i], u1[q2 + i]);
-      }
-    } else {
-      // boundary line: per point, (S, M) then (M, S)
-      for (int q2 = 0; q2 < L2; q2++) {
-        const int e = sE2[b * LM + q2] - l2lo, o = sO2[b * LM + q2];
-        const R *bm = &b2[(0 * LM + q2) * 4], *bs = &b2[(1 * LM + q2) * 4];
-        R s0 = r_zero<R>(), s1 = r_zero<R>(), s2 = r_zero<R>();
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-          s0 = r_fma(t3m[(e + i) * NB], bm[i], s0);
-          s1 = r_fma(t3m[(e + i) * NB], bs[i], s1);
-          s2 = r_fma(t3s[(e + i) * NB], bm[i], s2);
+          for (int i = 0; i < NP; i++) u0[q2 + i] = r_fma(c0[q2], vm[i], u0[q2 + i]);
         }
-        fiber_shift<P>(u0, s0, &v2[(0 * LM + q2) * NP], o);
-        fiber_shift<P>(u1, s1, &v2[(1 * LM + q2) * NP], o);
-        fiber_shift<P>(u1, s2, &v2[(0 * LM + q2) * NP], o);
+#pragma unroll
+        for (int q2 = 0; q2 < NP; q2++) {
+          const R *vs = &v2[(1 * LM + q2) * NP];
+#pragma unroll
+          for (int i = 0; i < NP; i++) u1[q2 + i] = r_fma(c1[q2], vs[i], u1[q2 + i]);
+        }
+#pragma unroll
+        for (int q2 = 0; q2 < NP; q2++) {
+          const R *vm = &v2[(0 * LM + q2) * NP];
+#pragma unroll
+          for (int i = 0; i < NP; i++) u1[q2 + i] = r_fma(c2[q2], vm[i], u1[q2 + i]);
+        }
+      } else {
+        // boundary line: per point, (S, M) then (M, S)
+        for (int q2 = 0; q2 < L2; q2++) {
+          const int e = sE2[b * LM + q2] - l2lo, o = sO2[b * LM + q2];
+          const R *bm = &b2[(0 * LM + q2) * 4], *bs = &b2[(1 * LM + q2) * 4];
+          R s0 = r_zero<R>(), s1 = r_zero<R>(), s2 = r_zero<R>();
+#pragma unroll
+          for (int i = 0; i < 4; i++) {
+            s0 = r_fma(t3m[(e + i) * NB], bm[i], s0);
+            s1 = r_fma(t3m[(e + i) * NB], bs[i], s1);
+            s2 = r_fma(t3s[(e + i) * NB], bm[i], s2);
+          }
+          fiber_shift<P>(u0, s0, &v2[(0 * LM + q2) * NP], o);
+          fiber_shift<P>(u1, s1, &v2[(1 * LM + q2) * NP], o);
+          fiber_shift<P>(u1, s2, &v2[(0 * LM + q2) * NP], o);
+        }
       }
     }
-    R *dst0 = Ug + (((size_t)lid * 2 + 0) * nc1 + (l1a + l1)) * NPAIR + j3 * NB;
-    R *dst1 = Ug + (((size_t)lid * 2 + 1) * nc1 + (l1a + l1)) * NPAIR + j3 * NB;
+    // U[line][u][l1][j3*NB+j2]: the warp's items of one line are one contiguous run
 #pragma unroll
-    for (int j = 0; j < NB; j++) {
-      dst0[j] = u0[j];
-      dst1[j] = u1[j];
+    for (int u = 0; u < 2; u++) {
+      if (ok) {
+#pragma unroll
+        for (int j = 0; j < NB; j++) wst[lane * NB + j] = u ? u1[j] : u0[j];
+      }
+      __syncwarp();
+      for (int e = lane; e < 32 * NB; e += 32) {
+        const int il = e / NB, j2 = e - il * NB, tt = t0 + il;
+        if (tt < NITEM && item_ok(tt)) {
+          const int jj3 = tt % NB, ll1 = (tt / NB) % kUCols, bb = tt / (NB * kUCols);
+          Ug[(((size_t)(lid0 + bb) * 2 + u) * nc1 + (l1a + ll1)) * NPAIR + jj3 * NB + j2] = wst[e];
+        }
+      }
+      __syncwarp();
     }
   }
 }
