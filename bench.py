@@ -1,13 +1,15 @@
 """Benchmark: 3D cubic weighted-Gaussian mass+stiffness assembly, nnz/s.
 
-One step = one fused mass+stiffness assembly (coefficient check, geometry
-fold and the row kernels, all rows) of the named synthetic workload through
-the C-ABI.  Default workload: 64^3 elements, C2 cubic (p = 3), separable map
+One step = one mass+stiffness assembly call (coefficient check, geometry
+fold, the partial-contraction kernel and the row kernel, all rows) of the
+named synthetic workload through the C-ABI.  Default workload: 64^3 elements, C2 cubic (p = 3), separable map
 xhat + 0.05 sin(pi xhat) per coordinate, c = exp(0.3 (x+y+z)) with
 lognormal(0.1) noise as a cubic spline on the same mesh, FP64-accurate bands
 (double output, <= 1e-12 relative to the FP64 oracle) computed in
-double-float arithmetic on the FP32 pipe (--prec df64).  The plain FP64 form
-and the FP32 mixed mode are timed beside it ("variants").
+double-float arithmetic on the FP32 pipe (--prec df64).  Timed beside it
+("variants"): the plain FP64 form, the FP32 mixed mode, the comparison rules
+(Gauss-Legendre rows, Newton-Cotes-type rule; FP64) with their quadrature
+point totals, and the 128^3 cubic workload in every precision.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload 3d_p3_64] [--prec df64|fp64|mixed] [--no-cpu-baseline]
@@ -39,6 +41,11 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # 152 SMs x 2 FP64 FMA/clk x 2 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 80.5
 # double-float multiply-add = 12 FP32-pipe instructions (csrc/dd.cuh): FP64-equivalent peak
 DF64_PEAK_TFLOPS = 152 * 128 / 12 * 2 * 2.070e9 / 1e12  # 6.71
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
+# capture of the current kernel (profiles/split_kernels_3d_p3_64_df64.md);
+# absent entries report null
+TRAFFIC = {("3d_p3_64", "df64"): {"bytes": 1.590574e9 + 0.236277e9, "kernel": "rows_ug_kernel<3, 32, M+K, dd>",
+                                  "algorithmic_bytes": 2 * 300763 * 343 * 8}}
 
 
 def measured_peaks():
@@ -198,6 +205,7 @@ def main():
     ap.add_argument("--prec", default="df64", choices=["fp64", "df64", "mixed"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-128", action="store_true", help="skip the 128^3 variant")
     ap.add_argument("--cpu-stride", type=int, default=8)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -270,6 +278,7 @@ def main():
 
     # the other precisions on the same workload, a few steps each
     variants = {}
+    peaks = measured_peaks()
     if not args.no_variants:
         for vp in ("fp64", "df64", "mixed"):
             if vp == args.prec:
@@ -334,6 +343,48 @@ def main():
         del Mv, Kv
         torch.cuda.empty_cache()
 
+        # the 128^3 cubic workload (the precision configuration), every precision
+        if args.workload == "3d_p3_64" and not args.no_128:
+            w2, g2, c2 = inputs.workload("3d_p3_128")
+            R2 = wq.Rules(3, w2["p"], w2["nel"])
+            gd2 = [torch.from_numpy(x).cuda() for x in g2]
+            cd2 = torch.from_numpy(c2).cuda()
+            fl2, _ = R2.flops()
+            big = {"workload": "3d_p3_128", "nel": list(w2["nel"]), "nnz_per_matrix": R2.nnz}
+            for vp in ("df64", "fp64", "mixed"):
+                vdt = torch.float32 if vp == "mixed" else torch.float64
+                Mv = torch.empty((R2.rows, R2.band), dtype=vdt, device="cuda")
+                Kv = torch.empty((R2.rows, R2.band), dtype=vdt, device="cuda")
+                for _ in range(3):
+                    wq.assemble(R2, gd2, cd2, vp, out=(Mv, Kv), stream=stream, check=False)
+                vms = []
+                for _ in range(max(3, min(args.steps, 5))):
+                    v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    v0.record(stream)
+                    wq.assemble(R2, gd2, cd2, vp, out=(Mv, Kv), stream=stream, check=False)
+                    v1.record(stream)
+                    vms.append((v0, v1))
+                torch.cuda.synchronize()
+                vm = float(np.mean([x.elapsed_time(y) for x, y in vms]))
+                ent = {"ms_per_step": vm, "value": world * 2 * R2.nnz / (vm * 1e-3), "unit": "nnz/s"}
+                if vp == "mixed":
+                    bw = 2 * R2.rows * R2.band * 4 / (vm * 1e-3) / 1e9
+                    ent["roofline"] = {"bound": "hbm", "achieved": bw, "peak": peaks.get("hbm_gbs", 6800.0),
+                                       "unit": "GB/s", "frac": bw / peaks.get("hbm_gbs", 6800.0)}
+                else:
+                    pk = FP64_PEAK_TFLOPS if vp == "fp64" else DF64_PEAK_TFLOPS
+                    tf = fl2 / (vm * 1e-3) / 1e12
+                    ent["roofline"] = {"bound": "alu", "achieved": tf, "peak": pk, "unit": "TFLOP/s", "frac": tf / pk}
+                big[vp] = ent
+                del Mv, Kv
+                torch.cuda.empty_cache()
+            st2 = wq.wq_status_check(R2.handle, wq._stream_handle(stream))
+            if st2 != wq.WQ_OK:
+                raise wq.WqError(st2, "128^3 variant")
+            variants["3d_p3_128"] = big
+            R2.close()
+            del gd2, cd2
+
     # end to end through host buffers: pinned inputs H2D, both bands D2H
     gh = [torch.from_numpy(x).pin_memory() for x in g]
     ch = torch.from_numpy(c).pin_memory()
@@ -373,7 +424,6 @@ def main():
     # roofline of the assembly call (fold + the two row launches; the fold is
     # a few microseconds): algorithmic contraction flops / device time
     flops, coef_flops = R.flops()
-    peaks = measured_peaks()
     if args.prec == "fp64":
         achieved = flops / (ms_step * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -383,7 +433,9 @@ def main():
     elif args.prec == "df64":
         achieved = flops / (ms_step * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": DF64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / DF64_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved / DF64_PEAK_TFLOPS,
+                "traffic": TRAFFIC.get((args.workload, "df64"), {}).get("bytes"),
+                "traffic_note": TRAFFIC.get((args.workload, "df64")),
                 "peak_source": "derived: FP32 pipe 152 SMs x 128 lanes x 2.07 GHz / 12 FP32 instructions per "
                                "double-float multiply-add, x 2 flop (FP64-equivalent)",
                 "achieved_incl_coef_eval": (flops + coef_flops) / (ms_step * 1e-3) / 1e12}
