@@ -385,6 +385,37 @@ def main():
             R2.close()
             del gd2, cd2
 
+        # the adjoint (coefficient gradient of sum G*K + H*M) on the 96^3 cubic workload
+        if args.workload == "3d_p3_64" and not args.no_128:
+            w3, g3, c3 = inputs.workload("3d_p3_96")
+            R3 = wq.Rules(3, w3["p"], w3["nel"])
+            gd3 = [torch.from_numpy(x).cuda() for x in g3]
+            gen = torch.Generator(device="cuda").manual_seed(96)
+            adj = {"workload": "3d_p3_96", "ncoef": R3.ncoef}
+            for vp in ("fp64", "df64", "mixed"):
+                vdt = torch.float32 if vp == "mixed" else torch.float64
+                G = torch.randn((R3.rows, R3.band), dtype=vdt, device="cuda", generator=gen)
+                H = torch.randn((R3.rows, R3.band), dtype=vdt, device="cuda", generator=gen)
+                grad = torch.empty(R3.ncoef, dtype=torch.float64, device="cuda")
+                for _ in range(3):
+                    wq.assemble_adjoint(R3, gd3, G, H, vp, out=grad, stream=stream, check=False)
+                vms = []
+                for _ in range(max(3, min(args.steps, 5))):
+                    v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    v0.record(stream)
+                    wq.assemble_adjoint(R3, gd3, G, H, vp, out=grad, stream=stream, check=False)
+                    v1.record(stream)
+                    vms.append((v0, v1))
+                torch.cuda.synchronize()
+                vm = float(np.mean([x.elapsed_time(y) for x, y in vms]))
+                # per step the adjoint reads both weight bands: report band entries per second
+                adj[vp] = {"ms_per_step": vm, "value": 2 * R3.nnz / (vm * 1e-3), "unit": "nnz/s (weights read)",
+                           "weights_gb_s": 2 * R3.rows * R3.band * G.element_size() / (vm * 1e-3) / 1e9}
+                del G, H, grad
+                torch.cuda.empty_cache()
+            variants["adjoint_3d_p3_96"] = adj
+            R3.close()
+
     # end to end through host buffers: pinned inputs H2D, both bands D2H
     gh = [torch.from_numpy(x).pin_memory() for x in g]
     ch = torch.from_numpy(c).pin_memory()
