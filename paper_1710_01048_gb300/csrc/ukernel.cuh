@@ -211,20 +211,20 @@ __global__ void __launch_bounds__(256) u_kernel(const UArgs A) {
   }
   __syncthreads();
 
-  // x2 stage per line: items (line, l1, j3), 32 per warp
+  // x2 stage: warp w takes line w of the block, items (l1, j3) of that line
+  // 32 at a time; item i's NB values of U sit at offset i * NB of the line's
+  // run of the block's columns, so the warp's outputs are one contiguous run
+  static_assert(kULines == kRowsWarps, "one warp per line of the block");
   R *Ug = static_cast<R *>(A.U);
   const int lane = tid & 31, warp = tid >> 5;
   R *wst = sSt + warp * L::WST;
-  constexpr int NITEM = kULines * kUCols * NB;
-  auto item_ok = [&](int t) {
-    const int l1 = (t / NB) % kUCols, b = t / (NB * kUCols);
-    const int lid = lid0 + b;
-    return b < nlines && l1 < ncols && lid >= A.line_lo && lid <= A.line_hi;
-  };
-  for (int t0 = warp * 32; t0 < NITEM; t0 += NT) {
-    const int t = t0 + lane;
-    const int j3 = t % NB, l1 = (t / NB) % kUCols, b = t / (NB * kUCols);
-    const bool ok = t < NITEM && item_ok(t);
+  const int b = warp;
+  const int nitem = ncols * NB;
+  const bool line_ok = b < nlines && lid0 + b >= A.line_lo && lid0 + b <= A.line_hi;
+  for (int i0 = 0; line_ok && i0 < nitem; i0 += 32) {
+    const int t = i0 + lane;
+    const bool ok = t < nitem;
+    const int l1 = t / NB, j3 = t - l1 * NB;
     R u0[NB], u1[NB];
 #pragma unroll
     for (int j = 0; j < NB; j++) {
@@ -292,7 +292,8 @@ __global__ void __launch_bounds__(256) u_kernel(const UArgs A) {
         }
       }
     }
-    // U[line][u][l1][j3*NB+j2]: the warp's items of one line are one contiguous run
+    // U[line][u][l1][j3*NB+j2]: contiguous from column l1a, item i0 onwards
+    const int nent = ((nitem - i0) < 32 ? (nitem - i0) : 32) * NB;
 #pragma unroll
     for (int u = 0; u < 2; u++) {
       if (ok) {
@@ -300,13 +301,8 @@ __global__ void __launch_bounds__(256) u_kernel(const UArgs A) {
         for (int j = 0; j < NB; j++) wst[lane * NB + j] = u ? u1[j] : u0[j];
       }
       __syncwarp();
-      for (int e = lane; e < 32 * NB; e += 32) {
-        const int il = e / NB, j2 = e - il * NB, tt = t0 + il;
-        if (tt < NITEM && item_ok(tt)) {
-          const int jj3 = tt % NB, ll1 = (tt / NB) % kUCols, bb = tt / (NB * kUCols);
-          Ug[(((size_t)(lid0 + bb) * 2 + u) * nc1 + (l1a + ll1)) * NPAIR + jj3 * NB + j2] = wst[e];
-        }
-      }
+      R *dst = Ug + (((size_t)(lid0 + b) * 2 + u) * nc1 + l1a) * NPAIR + (size_t)i0 * NB;
+      for (int e = lane; e < nent; e += 32) dst[e] = wst[e];
       __syncwarp();
     }
   }
