@@ -220,11 +220,12 @@ wq_status wq_assemble_adjoint(const wq_rules *rules, const double *const *geom, 
  * degree, map and coefficient; every row of every patch is assembled as in
  * wq_assemble_mass_stiffness, with the weighted Gaussian rules of Sec. 3).
  * The paper treats one patch; the batch is a throughput form of the same
- * computation.  A plan (wq_batch) holds the patches' work list and folded
- * tables and a CUDA graph of one batched geometry fold and one persistent
- * row launch that takes work items (chunks of lines of rows) from a global
- * counter.  Its results are bit-identical to one wq_assemble_mass_stiffness
- * call per patch with the same precision.
+ * computation.  A plan (wq_batch) holds the patches' work lists, folded
+ * tables and partial-contraction buffers, and a CUDA graph of one batched
+ * geometry fold and two persistent launches (the partial contractions of
+ * every patch, then the rows of every patch) whose CTAs take work items from
+ * global counters.  Its results are bit-identical to one
+ * wq_assemble_mass_stiffness call per patch with the same precision.
  */
 typedef struct wq_batch wq_batch;
 typedef struct {
@@ -248,21 +249,20 @@ wq_status wq_batch_launch(wq_batch *batch, void *stream);
 /* Synchronises `stream`, returns and clears the plan's device status (as wq_status_check). */
 wq_status wq_batch_status(wq_batch *batch, void *stream);
 /*
- * Launch configuration: config[0] = chunk length of interior lines (1..24;
- * cut to the capacity of the degree and arithmetic type, 20 rows for degree 3
- * in FP64 and double-float),
- * config[1] = chunk length of boundary lines (1..16), config[2] = resident
- * CTAs per SM of the persistent launch (1..config[4]), config[3] = item order
- * (0: patch order, 1: costliest line classes first).  get writes config[0..4],
- * config[4] being the most CTAs per SM the kernel can hold; set reads
- * config[0..3], synchronises the device, rebuilds the work list and
- * recaptures the graph.
+ * Launch configuration: config[0] = chunk length of the row launch (1..32
+ * rows of a line), config[1] = resident CTAs per SM of the persistent
+ * partial-contraction launch (1..config[4]), config[2] = resident CTAs per SM
+ * of the persistent row launch (1..config[5]), config[3] = item order (0:
+ * patch order, 1: degree-3 patches first).  get writes config[0..5],
+ * config[4] and config[5] being the most CTAs per SM the two kernels can hold;
+ * set reads config[0..3], synchronises the device, rebuilds the work lists
+ * and recaptures the graph.
  */
 wq_status wq_batch_get_config(const wq_batch *batch, int *config);
 wq_status wq_batch_set_config(wq_batch *batch, const int *config);
 /*
  * Autotuner: times every configuration of a fixed candidate set (chunk
- * lengths 24/16/12/8 and 16/8, the two largest CTA counts, both orders),
+ * lengths 32/24/16, the two largest CTA counts of each kernel, both orders),
  * each `reps` times on `stream` after one warm-up (the plan's outputs are
  * written), keeps the fastest and recaptures the graph.  *best_ms (may be
  * NULL) receives its mean time.  Synchronises the device.

@@ -1,6 +1,7 @@
 // Batched assembly of many independent 3D patches: the plan object
-// (wq_batch), its batched geometry fold, the persistent row launch captured
-// in a CUDA graph, and the autotuner of the launch's tile parameters.
+// (wq_batch), its batched geometry fold, the two persistent launches of the
+// split 3D path captured in a CUDA graph, and the autotuner of their tile
+// parameters.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -42,26 +43,27 @@ __global__ void batch_fold_kernel(const BFold *__restrict__ segs, int nseg, int 
   if ((threadIdx.x & 31) == 0 && bits) atomicOr(status, bits);
 }
 
-// Work of one item (a chunk of a line), relative, for the ordering heuristic:
-// degree-3 boundary lines are the most expensive, degree-2 interior the least.
-int cost_rank(int p, int cls) { return p == 3 ? (cls == 1 ? 0 : 1) : (cls == 1 ? 2 : 3); }
 
 }  // namespace
 
 struct wq_batch {
   int npatch = 0;
   wq_precision prec = WQ_FP64;
-  int device = -1, nsm = 0, max_ctas = 1;
+  int device = -1, nsm = 0, max_ctas = 1, max_uctas = 1;
   std::vector<wq_patch> patches;
-  // device block: fold segments, batch segments, per-patch folded tables, counter, status
+  // device block: fold segments, batch segments, per-patch folded tables and
+  // U buffers, counters, status
   void *dev_block = nullptr;
   BFold *dev_fold = nullptr;
   int nfold = 0, fold_total = 0;
+  wq::BatchUSeg *dev_usegs = nullptr;
   wq::BatchSeg *dev_segs = nullptr;
-  int nseg = 0, nitems = 0;
-  unsigned *dev_counter = nullptr, *dev_status = nullptr;
-  std::vector<wq::RowsArgs> base_args;  // per patch, without class/chunking
-  int config[4] = {wq::kInteriorChunkMax, wq::kBoundaryChunk, 1, 1};
+  int nuseg = 0, nuitems = 0, nseg = 0, nitems = 0;
+  unsigned *dev_counter = nullptr, *dev_status = nullptr;  // counters [2], status
+  std::vector<wq::RowsArgs> base_args;  // per patch, without chunking
+  std::vector<wq::UArgs> base_uargs;    // per patch
+  // chunk length, CTAs per SM of the partial-contraction and of the row kernel, item order
+  int config[4] = {wq::kUGChunk, 1, 1, 1};
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -70,55 +72,60 @@ struct wq_batch {
 namespace {
 
 wq_status prepare(wq_batch *B) {
-  int ctas = 0;
-  cudaError_t e = B->prec == WQ_FP64 ? wq::batch_prepare<double>(&ctas)
-                  : B->prec == WQ_MIXED ? wq::batch_prepare<float>(&ctas) : wq::batch_prepare<wq::dd>(&ctas);
-  if (e != cudaSuccess || ctas < 1) return WQ_ERR_CUDA;
+  int uctas = 0, ctas = 0;
+  cudaError_t e = B->prec == WQ_FP64   ? wq::batch_prepare<double>(&uctas, &ctas)
+                  : B->prec == WQ_MIXED ? wq::batch_prepare<float>(&uctas, &ctas)
+                                        : wq::batch_prepare<wq::dd>(&uctas, &ctas);
+  if (e != cudaSuccess || ctas < 1 || uctas < 1) return WQ_ERR_CUDA;
   B->max_ctas = ctas;
+  B->max_uctas = uctas;
   return WQ_OK;
 }
 
-// Builds the segment list for the current configuration and uploads it.
+// Builds the two segment lists for the current configuration and uploads them.
 wq_status build_segments(wq_batch *B) {
-  const int tint = B->config[0], tbnd = B->config[1], order = B->config[3];
-  std::vector<wq::BatchSeg> segs;
+  const int tchunk = B->config[0], order = B->config[3];
+  if (tchunk < 1 || tchunk > wq::kUGChunk) return WQ_ERR_ARG;
+  std::vector<wq::BatchUSeg> usegs(B->npatch);
+  std::vector<wq::BatchSeg> segs(B->npatch);
   for (int i = 0; i < B->npatch; i++) {
     const wq_rules *R = B->patches[i].rules;
-    for (int cls = 0; cls < 2; cls++) {
-      const std::vector<int> &lines = cls == 0 ? R->lines.interior : R->lines.boundary;
-      if (lines.empty()) continue;
-      // interior chunks longer than the degree's capacity are cut to it
-      const int tmax = cls == 0 ? wq::interior_chunk(R->p, B->prec == WQ_MIXED ? 4 : 8) : wq::kBoundaryChunk;
-      if (tint < 1 || tint > wq::kInteriorChunkMax || tbnd < 1 || tbnd > wq::kBoundaryChunk) return WQ_ERR_ARG;
-      const int t = cls == 0 ? std::min(tint, tmax) : tbnd;
-      const int T = wq::chunk_length(R, t);
-      if (wq::max_chunk_points(R, T) > wq::chunk_points_bound(R->p, tmax)) return WQ_ERR_UNSUPPORTED;
-      wq::BatchSeg S;
-      std::memset(&S, 0, sizeof(S));
-      S.a = B->base_args[i];
-      S.a.T = T;
-      S.a.nch = (R->n[0] + T - 1) / T;
-      S.a.lines = cls == 0 ? R->dev_lines_interior : R->dev_lines_boundary;
-      S.p = R->p;
-      S.cls = cls;
-      S.nitems = (int)lines.size() * S.a.nch;
-      segs.push_back(S);
-    }
+    wq::BatchUSeg &U = usegs[i];
+    std::memset(&U, 0, sizeof(U));
+    U.a = B->base_uargs[i];
+    U.p = R->p;
+    U.nitems = R->n[2] * U.a.nblk2 * U.a.nblk1;
+    const int T = wq::chunk_length(R, tchunk);
+    if (wq::max_chunk_points(R, T) > wq::chunk_points_bound(R->p, wq::kUGChunk)) return WQ_ERR_UNSUPPORTED;
+    wq::BatchSeg &S = segs[i];
+    std::memset(&S, 0, sizeof(S));
+    S.a = B->base_args[i];
+    S.a.T = T;
+    S.a.nch = (R->n[0] + T - 1) / T;
+    S.p = R->p;
+    S.nitems = R->n[1] * R->n[2] * S.a.nch;
   }
-  if (order == 1)
-    std::stable_sort(segs.begin(), segs.end(), [](const wq::BatchSeg &x, const wq::BatchSeg &y) {
-      return cost_rank(x.p, x.cls) < cost_rank(y.p, y.cls);
-    });
-  long long total = 0;
+  if (order == 1) {  // degree 3 first: the costliest items start earliest
+    std::stable_sort(usegs.begin(), usegs.end(), [](const wq::BatchUSeg &x, const wq::BatchUSeg &y) { return x.p > y.p; });
+    std::stable_sort(segs.begin(), segs.end(), [](const wq::BatchSeg &x, const wq::BatchSeg &y) { return x.p > y.p; });
+  }
+  long long utotal = 0, total = 0;
+  for (wq::BatchUSeg &U : usegs) {
+    U.first_item = (int)utotal;
+    utotal += U.nitems;
+  }
   for (wq::BatchSeg &S : segs) {
     S.first_item = (int)total;
     total += S.nitems;
   }
-  if (total > 0x7fffffffLL) return WQ_ERR_UNSUPPORTED;
-  if (cudaDeviceSynchronize() != cudaSuccess) return WQ_ERR_CUDA;  // no launch still reads the old list
-  if (!segs.empty() &&
+  if (total > 0x7fffffffLL || utotal > 0x7fffffffLL) return WQ_ERR_UNSUPPORTED;
+  if (cudaDeviceSynchronize() != cudaSuccess) return WQ_ERR_CUDA;  // no launch still reads the old lists
+  if (cudaMemcpy(B->dev_usegs, usegs.data(), usegs.size() * sizeof(wq::BatchUSeg), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
       cudaMemcpy(B->dev_segs, segs.data(), segs.size() * sizeof(wq::BatchSeg), cudaMemcpyHostToDevice) != cudaSuccess)
     return WQ_ERR_CUDA;
+  B->nuseg = (int)usegs.size();
+  B->nuitems = (int)utotal;
   B->nseg = (int)segs.size();
   B->nitems = (int)total;
   return WQ_OK;
@@ -130,13 +137,15 @@ wq_status enqueue(const wq_batch *B, cudaStream_t s) {
     batch_fold_kernel<<<blocks, 256, 0, s>>>(B->dev_fold, B->nfold, B->fold_total, B->dev_status);
     if (cudaGetLastError() != cudaSuccess) return WQ_ERR_CUDA;
   }
-  if (cudaMemsetAsync(B->dev_counter, 0, sizeof(unsigned), s) != cudaSuccess) return WQ_ERR_CUDA;
-  const int grid = B->nsm * B->config[2];
-  cudaError_t e = B->prec == WQ_FP64
-                      ? wq::launch_batch<double>(B->dev_segs, B->nseg, B->nitems, B->dev_counter, grid, s)
-                  : B->prec == WQ_MIXED
-                      ? wq::launch_batch<float>(B->dev_segs, B->nseg, B->nitems, B->dev_counter, grid, s)
-                      : wq::launch_batch<wq::dd>(B->dev_segs, B->nseg, B->nitems, B->dev_counter, grid, s);
+  if (cudaMemsetAsync(B->dev_counter, 0, 2 * sizeof(unsigned), s) != cudaSuccess) return WQ_ERR_CUDA;
+  const int ugrid = B->nsm * B->config[1], grid = B->nsm * B->config[2];
+  cudaError_t e =
+      B->prec == WQ_FP64   ? wq::launch_batch<double>(B->dev_usegs, B->nuseg, B->nuitems, B->dev_segs, B->nseg,
+                                                      B->nitems, B->dev_counter, ugrid, grid, s)
+      : B->prec == WQ_MIXED ? wq::launch_batch<float>(B->dev_usegs, B->nuseg, B->nuitems, B->dev_segs, B->nseg,
+                                                     B->nitems, B->dev_counter, ugrid, grid, s)
+                            : wq::launch_batch<wq::dd>(B->dev_usegs, B->nuseg, B->nuitems, B->dev_segs, B->nseg,
+                                                       B->nitems, B->dev_counter, ugrid, grid, s);
   return e == cudaSuccess ? WQ_OK : WQ_ERR_CUDA;
 }
 
@@ -147,7 +156,7 @@ void drop_graph(wq_batch *B) {
   B->graph = nullptr;
 }
 
-// Captures fold + counter reset + persistent launch into a CUDA graph.
+// Captures fold + counter reset + the two persistent launches into a CUDA graph.
 wq_status capture(wq_batch *B) {
   drop_graph(B);
   if (cudaStreamBeginCapture(B->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return WQ_ERR_CUDA;
@@ -171,7 +180,8 @@ wq_status apply_config(wq_batch *B, const int *cfg) {
   int old[4];
   std::memcpy(old, B->config, sizeof(old));
   std::memcpy(B->config, cfg, sizeof(old));
-  if (B->config[2] < 1 || B->config[2] > B->max_ctas || (B->config[3] != 0 && B->config[3] != 1)) {
+  if (B->config[1] < 1 || B->config[1] > B->max_uctas || B->config[2] < 1 || B->config[2] > B->max_ctas ||
+      (B->config[3] != 0 && B->config[3] != 1)) {
     std::memcpy(B->config, old, sizeof(old));
     return WQ_ERR_ARG;
   }
@@ -228,11 +238,14 @@ wq_status wq_batch_create(const wq_patch *patches, int npatch, wq_precision prec
   size_t total = 0;
   const size_t fold_off = total;
   total += align_up(sizeof(BFold) * 6 * (size_t)npatch);
+  const size_t useg_off = total;
+  total += align_up(sizeof(wq::BatchUSeg) * (size_t)npatch);
   const size_t seg_off = total;
-  total += align_up(sizeof(wq::BatchSeg) * 2 * (size_t)npatch);
+  total += align_up(sizeof(wq::BatchSeg) * (size_t)npatch);
   const size_t cnt_off = total;
-  total += align_up(2 * sizeof(unsigned));
-  std::vector<size_t> tab_off(6 * (size_t)npatch);
+  total += align_up(3 * sizeof(unsigned));
+  const size_t elem_bytes = prec == WQ_MIXED ? sizeof(float) : sizeof(double);
+  std::vector<size_t> tab_off(6 * (size_t)npatch), u_off(npatch);
   for (int i = 0; i < npatch; i++) {
     const wq_rules *R = patches[i].rules;
     const size_t np = (size_t)R->p + 1;
@@ -242,6 +255,10 @@ wq_status wq_batch_create(const wq_patch *patches, int npatch, wq_precision prec
         const size_t m = (size_t)R->dev[a][k].npts * np;
         total += align_up(m * sizeof(double)) + align_up(m * sizeof(float)) + align_up(m * sizeof(float2));
       }
+    // the patch's own U buffer (patches may share a rules object)
+    const size_t nb = 2 * (size_t)R->p + 1;
+    u_off[i] = total;
+    total += align_up((size_t)R->n[1] * R->n[2] * 2 * R->nc[0] * nb * nb * elem_bytes);
   }
   if (cudaMalloc(&B->dev_block, total) != cudaSuccess) {
     cudaGetLastError();
@@ -250,12 +267,14 @@ wq_status wq_batch_create(const wq_patch *patches, int npatch, wq_precision prec
   }
   char *base = static_cast<char *>(B->dev_block);
   B->dev_fold = reinterpret_cast<BFold *>(base + fold_off);
+  B->dev_usegs = reinterpret_cast<wq::BatchUSeg *>(base + useg_off);
   B->dev_segs = reinterpret_cast<wq::BatchSeg *>(base + seg_off);
   B->dev_counter = reinterpret_cast<unsigned *>(base + cnt_off);
-  B->dev_status = B->dev_counter + 1;
+  B->dev_status = B->dev_counter + 2;
   std::vector<BFold> folds;
   int start = 0;
   B->base_args.resize(npatch);
+  B->base_uargs.resize(npatch);
   for (int i = 0; i < npatch; i++) {
     const wq_patch &P = patches[i];
     const wq_rules *R = P.rules;
@@ -295,23 +314,46 @@ wq_status wq_batch_create(const wq_patch *patches, int npatch, wq_precision prec
       ra.nc[a] = R->nc[a];
     }
     ra.coef = P.coef;
-    ra.coefR = nullptr;  // checked and converted inside the row kernel
+    ra.coefR = nullptr;  // checked and converted inside the partial-contraction kernel
     ra.M = P.M;
     ra.K = P.K;
     ra.row_begin = 0;
     ra.row_end = (long long)R->n[0] * R->n[1] * R->n[2];
+    ra.lines = nullptr;
+    ra.line0 = 0;
+    ra.Ug = base + u_off[i];
     ra.status = B->dev_status;
+    wq::UArgs &ua = B->base_uargs[i];
+    std::memset(&ua, 0, sizeof(ua));
+    std::memcpy(ua.off, ra.off, sizeof(ua.off));
+    std::memcpy(ua.elem, ra.elem, sizeof(ua.elem));
+    std::memcpy(ua.V, ra.V, sizeof(ua.V));
+    std::memcpy(ua.beta, ra.beta, sizeof(ua.beta));
+    for (int a = 0; a < 3; a++) {
+      ua.n[a] = ra.n[a];
+      ua.N[a] = ra.N[a];
+      ua.nc[a] = ra.nc[a];
+    }
+    ua.coef = P.coef;
+    ua.coefR = nullptr;
+    ua.U = base + u_off[i];
+    ua.line_lo = 0;
+    ua.line_hi = R->n[1] * R->n[2] - 1;
+    ua.r3_lo = 0;
+    ua.nblk2 = (R->n[1] + wq::kULines - 1) / wq::kULines;
+    ua.nblk1 = (R->nc[0] + wq::kUCols - 1) / wq::kUCols;
+    ua.status = B->dev_status;
   }
   B->nfold = (int)folds.size();
   B->fold_total = start;
   bool ok = cudaMemcpy(B->dev_fold, folds.data(), folds.size() * sizeof(BFold), cudaMemcpyHostToDevice) == cudaSuccess;
-  ok = ok && cudaMemset(B->dev_counter, 0, 2 * sizeof(unsigned)) == cudaSuccess;
+  ok = ok && cudaMemset(B->dev_counter, 0, 3 * sizeof(unsigned)) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
   if (!ok) {
     destroy(B);
     return WQ_ERR_CUDA;
   }
-  const int cfg[4] = {wq::kInteriorChunkMax, wq::kBoundaryChunk, B->max_ctas, 1};
+  const int cfg[4] = {wq::kUGChunk, B->max_uctas, B->max_ctas, 1};
   st = apply_config(B, cfg);
   if (st != WQ_OK) {
     destroy(B);
@@ -353,7 +395,8 @@ wq_status wq_batch_status(wq_batch *B, void *stream) {
 wq_status wq_batch_get_config(const wq_batch *B, int *config) {
   if (!B || !config) return WQ_ERR_ARG;
   std::memcpy(config, B->config, sizeof(B->config));
-  config[4] = B->max_ctas;
+  config[4] = B->max_uctas;
+  config[5] = B->max_ctas;
   return WQ_OK;
 }
 
@@ -365,10 +408,10 @@ wq_status wq_batch_set_config(wq_batch *B, const int *config) {
 wq_status wq_batch_tune(wq_batch *B, void *stream, int reps, double *best_ms) {
   if (!B || reps < 1) return WQ_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int tints[] = {24, 16, 12, 8};
-  const int tbnds[] = {16, 8};
-  std::vector<int> ctas;
+  const int chunks[] = {32, 24, 16};
+  std::vector<int> ctas, uctas;
   for (int c = B->max_ctas; c >= 1 && (int)ctas.size() < 2; c--) ctas.push_back(c);
+  for (int c = B->max_uctas; c >= 1 && (int)uctas.size() < 2; c--) uctas.push_back(c);
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return WQ_ERR_CUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -380,11 +423,11 @@ wq_status wq_batch_tune(wq_batch *B, void *stream, int reps, double *best_ms) {
   float best_t = -1.0f;
   wq_status st = WQ_OK;
   for (int order = 0; order < 2 && st == WQ_OK; order++)
-    for (int c : ctas)
-      for (int ti : tints)
-        for (int tb : tbnds) {
+    for (int uc : uctas)
+      for (int c : ctas)
+        for (int t : chunks) {
           if (st != WQ_OK) break;
-          const int cfg[4] = {ti, tb, c, order};
+          const int cfg[4] = {t, uc, c, order};
           std::memcpy(B->config, cfg, sizeof(cfg));
           if (build_segments(B) != WQ_OK) continue;  // a chunk length this batch's tables do not fit
           st = enqueue(B, s);  // warm-up

@@ -65,12 +65,13 @@ template <int P, typename R> struct ULayout {
   static constexpr size_t BYTES = sizeof(R) * (size_t)R_TOTAL + sizeof(int) * (size_t)I_TOTAL;
 };
 
+// The work of one u_kernel CTA: block `bid` (plane, line block, column
+// block) in the dynamic shared memory `smem_raw` (ULayout::BYTES).
 template <int P, typename R>
-__global__ void __launch_bounds__(256) u_kernel(const UArgs A) {
+__device__ __forceinline__ void u_block(const UArgs &A, int bid, unsigned char *smem_raw) {
   using L = ULayout<P, R>;
   constexpr int NP = L::NP, NB = L::NB, NPAIR = NB * NB, LM = L::LM, NL2 = L::NL2, NL3 = L::NL3;
   constexpr int NT = 256;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   R *sV3 = reinterpret_cast<R *>(smem_raw);
   R *sB3 = sV3 + L::V3;
   R *sV2 = sB3 + L::B3;
@@ -86,7 +87,6 @@ __global__ void __launch_bounds__(256) u_kernel(const UArgs A) {
 
   const int tid = threadIdx.x;
   const int n2 = A.n[1], nc1 = A.nc[0], nc2 = A.nc[1];
-  int bid = blockIdx.x;
   const int b1 = bid % A.nblk1;
   bid /= A.nblk1;
   const int b2 = bid % A.nblk2;
@@ -308,6 +308,11 @@ __global__ void __launch_bounds__(256) u_kernel(const UArgs A) {
   }
 }
 
+template <int P, typename R> __global__ void __launch_bounds__(256) u_kernel(const UArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  u_block<P, R>(A, blockIdx.x, smem_raw);
+}
+
 // Row kernel of the split path: x1 tables and U columns in shared memory, then phase B.
 template <int P, int TMAX, bool DO_M, bool DO_K, typename R> struct RowsLayoutUG {
   static constexpr int NP = P + 1, NB = 2 * P + 1, NPAIR = NB * NB;
@@ -324,11 +329,11 @@ template <int P, int TMAX, bool DO_M, bool DO_K, typename R> struct RowsLayoutUG
   static constexpr size_t BYTES = sizeof(R) * (size_t)R_TOTAL + sizeof(int) * (size_t)I_TOTAL;
 };
 
+// The work of one rows_ug_kernel CTA: chunk `bid` of lines line0, line0+1, ...
 template <int P, int TMAX, bool DO_M, bool DO_K, typename R>
-__global__ void __launch_bounds__(32 * kRowsWarps, rows_min_blocks<R>()) rows_ug_kernel(const RowsArgs A) {
+__device__ __forceinline__ void rows_ug_block(const RowsArgs &A, int bid, unsigned char *smem_raw) {
   using L = RowsLayoutUG<P, TMAX, DO_M, DO_K, R>;
   constexpr int NPAIR = L::NPAIR, NL1 = L::NL1, NT = 32 * kRowsWarps;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   R *sV1 = reinterpret_cast<R *>(smem_raw);
   R *sB1 = sV1 + L::V1;
   R *sU = sB1 + L::B1;
@@ -337,8 +342,8 @@ __global__ void __launch_bounds__(32 * kRowsWarps, rows_min_blocks<R>()) rows_ug
   int *sOff1 = sE1 + L::MAXPTS1;
 
   const int tid = threadIdx.x;
-  const int line = A.line0 + (int)(blockIdx.x / A.nch);
-  const int ch = blockIdx.x % A.nch;
+  const int line = A.line0 + bid / A.nch;
+  const int ch = bid % A.nch;
   const int n1 = A.n[0];
   const long long base = (long long)line * n1;
   long long lo = (long long)ch * A.T, hi = lo + A.T;
@@ -362,6 +367,12 @@ __global__ void __launch_bounds__(32 * kRowsWarps, rows_min_blocks<R>()) rows_ug
   }
   __syncthreads();
   rows_phase_b<P, 3, L::MAXPTS1, NL1, false, DO_M, DO_K, R>(A, sU, sV1, sB1, sE1, sOff1, sW, a, T, l1lo, base);
+}
+
+template <int P, int TMAX, bool DO_M, bool DO_K, typename R>
+__global__ void __launch_bounds__(32 * kRowsWarps, rows_min_blocks<R>()) rows_ug_kernel(const RowsArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  rows_ug_block<P, TMAX, DO_M, DO_K, R>(A, blockIdx.x, smem_raw);
 }
 
 // Chunk length of the split row kernel (every line, any rule lengths in x2, x3).

@@ -1,5 +1,6 @@
-"""Batched assembly (wq_batch_*): one persistent launch for many patches,
-replayed from a CUDA graph, with an autotuned launch configuration.
+"""Batched assembly (wq_batch_*): two persistent launches (partial
+contractions, rows) for many patches, replayed from a CUDA graph, with an
+autotuned launch configuration.
 
 Every patch's bands must be bit-identical to a single-patch
 wq_assemble_mass_stiffness call in the same precision (the batch runs the
@@ -64,22 +65,21 @@ def test_batch_equals_single_patch_calls(prec):
 def test_batch_configurations_and_tuner():
     patches, _ = make_patches(SMALL, "fp64", seed=3)
     B = wq.Batch(patches, "fp64")
-    mx = B.config["max_ctas_per_sm"]
-    assert mx >= 1
-    for cfg in [(24, 16, mx, 1), (8, 8, 1, 0), (13, 5, mx, 0), (1, 1, 1, 1)]:
+    mu, mx = B.config["max_u_ctas_per_sm"], B.config["max_ctas_per_sm"]
+    assert mu >= 1 and mx >= 1
+    for cfg in [(32, mu, mx, 1), (8, 1, 1, 0), (13, mu, mx, 0), (1, 1, 1, 1)]:
         for _, _, _, M, K in patches:
             M.fill_(float("nan"))
             K.fill_(float("nan"))
         B.set_config(*cfg)
         c = B.config
-        assert (c["chunk_interior"], c["chunk_boundary"], c["ctas_per_sm"], c["order"]) == cfg
+        assert (c["chunk"], c["u_ctas_per_sm"], c["ctas_per_sm"], c["order"]) == cfg
         B.launch()
         B.check()
         assert_matches_single(patches, "fp64")
-    with pytest.raises(wq.WqError):
-        B.set_config(25, 16, 1, 0)  # longer than the compiled chunk capacity
-    with pytest.raises(wq.WqError):
-        B.set_config(24, 16, mx + 1, 0)
+    for bad in [(33, mu, mx, 0), (32, mu + 1, mx, 0), (32, mu, mx + 1, 0), (32, mu, mx, 2)]:
+        with pytest.raises(wq.WqError):
+            B.set_config(*bad)
     ms = B.tune(reps=1)
     assert ms > 0
     for _, _, _, M, K in patches:
