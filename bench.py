@@ -9,7 +9,8 @@ lognormal(0.1) noise as a cubic spline on the same mesh, FP64-accurate bands
 double-float arithmetic on the FP32 pipe (--prec df64).  Timed beside it
 ("variants"): the plain FP64 form, the FP32 mixed mode, the comparison rules
 (Gauss-Legendre rows, Newton-Cotes-type rule; FP64) with their quadrature
-point totals, and the 128^3 cubic workload in every precision.
+point totals, the 128^3 cubic workload in every precision, the adjoint on
+the 96^3 cubic workload and the 256-patch batch.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload 3d_p3_64] [--prec df64|fp64|mixed] [--no-cpu-baseline]
@@ -205,7 +206,8 @@ def main():
     ap.add_argument("--prec", default="df64", choices=["fp64", "df64", "mixed"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-128", action="store_true", help="skip the 128^3 variant")
+    ap.add_argument("--no-128", action="store_true", help="skip the 128^3 and adjoint variants")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 256-patch batch variant")
     ap.add_argument("--cpu-stride", type=int, default=8)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -415,6 +417,56 @@ def main():
                 torch.cuda.empty_cache()
             variants["adjoint_3d_p3_96"] = adj
             R3.close()
+
+        # the batch of 256 independent patches (8..48 elements per direction, p in {2, 3}):
+        # one graph of two persistent launches, tuned, against one call per patch
+        if not args.no_batch:
+            specs = inputs.batch_patches(256, seed=0)
+            rules_cache, base = {}, []
+            for sp in specs:
+                key = (sp["p"], sp["nel"])
+                if key not in rules_cache:
+                    rules_cache[key] = wq.Rules(3, sp["p"], sp["nel"])
+                base.append((rules_cache[key], [torch.from_numpy(x).cuda() for x in sp["geom"]],
+                             torch.from_numpy(sp["coef"]).cuda()))
+            bnnz = 2 * sum(Rb.nnz for Rb, _, _ in base)
+            bat = {"workload": "batch_256", "patches": 256, "nnz_per_step": bnnz}
+            for vp in ("fp64", "df64", "mixed"):
+                vdt = torch.float32 if vp == "mixed" else torch.float64
+                pts = [(Rb, gb, cb, torch.empty((Rb.rows, Rb.band), dtype=vdt, device="cuda"),
+                        torch.empty((Rb.rows, Rb.band), dtype=vdt, device="cuda")) for Rb, gb, cb in base]
+                Bp = wq.Batch(pts, vp)
+                Bp.tune(reps=1, stream=stream)
+
+                def timed(fn, n):
+                    fn()
+                    v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    v0.record(stream)
+                    for _ in range(n):
+                        fn()
+                    v1.record(stream)
+                    torch.cuda.synchronize()
+                    return v0.elapsed_time(v1) / n
+
+                tb = timed(lambda: Bp.launch(stream), 5)
+                stb = Bp.status(stream)
+                if stb != wq.WQ_OK:
+                    raise wq.WqError(stb, "batch")
+
+                def seq():
+                    for Rb, gb, cb, Mb, Kb in pts:
+                        wq.assemble(Rb, gb, cb, vp, out=(Mb, Kb), stream=stream, check=False)
+
+                ts = timed(seq, 2)
+                bat[vp] = {"ms_per_step": tb, "value": bnnz / (tb * 1e-3), "unit": "nnz/s",
+                           "ms_one_call_per_patch": ts, "config": Bp.config}
+                Bp.close()
+                del pts
+                torch.cuda.empty_cache()
+            variants["batch_256"] = bat
+            for Rb in rules_cache.values():
+                Rb.close()
+            del base
 
     # end to end through host buffers: pinned inputs H2D, both bands D2H
     gh = [torch.from_numpy(x).pin_memory() for x in g]
