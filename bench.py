@@ -478,12 +478,12 @@ def main():
     e2e_steps = max(3, min(args.steps, 10))
 
     def e2e_step():
+        # inputs to the device, then the assembly with its band copies to the
+        # host overlapped range by range (binding.assemble_to_host)
         for dst, src in zip(gd, gh):
             dst.copy_(src, non_blocking=True)
         cd.copy_(ch, non_blocking=True)
-        step()
-        Mh.copy_(M, non_blocking=True)
-        Kh.copy_(K, non_blocking=True)
+        wq.assemble_to_host(R, gd, cd, args.prec, Mh, Kh, M, K, nchunks=8, stream=stream)
 
     e2e_step()
     barrier()

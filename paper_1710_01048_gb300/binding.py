@@ -486,3 +486,51 @@ def band_to_csr(rules, band, prec="fp64", row_begin=0, row_end=None, stream=None
                                  ctypes.c_void_p(rowptr.data_ptr()), ctypes.c_void_p(col.data_ptr()),
                                  ctypes.c_void_p(val.data_ptr()), _stream_handle(stream)), "wq_band_to_csr")
     return rowptr, col[:nnz], val[:nnz]
+
+
+def assemble_to_host(rules, geom, coef, prec, M_host, K_host, M_dev, K_dev, nchunks=8, stream=None):
+    """Assembles M and K into pinned host tensors M_host, K_host (rows x band),
+    overlapping the device-to-host copies with the assembly: the rows are cut
+    into nchunks ranges; range k is assembled on `stream` into M_dev, K_dev
+    (full-size device tensors) while range k-1 is copied to the host on a
+    second stream.  Returns after enqueueing; `stream` waits for the copies."""
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    copy = _copy_stream(stream.device)
+    rows = rules.rows
+    bounds = [rows * k // nchunks for k in range(nchunks + 1)]
+    gp = [g.data_ptr() for g in geom]
+    cp = ctypes.c_void_p(coef.data_ptr()) if coef is not None else None
+    p = PRECISIONS[prec]
+    s = ctypes.c_void_p(stream.cuda_stream)
+    esz = M_dev.element_size()
+    for k in range(nchunks):
+        rb, re = bounds[k], bounds[k + 1]
+        if rb == re:
+            continue
+        st = wq_assemble_mass_stiffness(rules.handle, gp, cp, p, ctypes.c_void_p(M_dev.data_ptr() + rb * rules.band * esz),
+                                        ctypes.c_void_p(K_dev.data_ptr() + rb * rules.band * esz), rb, re, s)
+        _check(st, "wq_assemble_mass_stiffness")
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        copy.wait_event(ev)
+        with torch.cuda.stream(copy):
+            M_host[rb:re].copy_(M_dev[rb:re], non_blocking=True)
+            K_host[rb:re].copy_(K_dev[rb:re], non_blocking=True)
+    done = torch.cuda.Event()
+    done.record(copy)
+    stream.wait_event(done)
+
+
+_COPY_STREAMS = {}
+
+
+def _copy_stream(device):
+    import torch
+
+    key = str(device)
+    if key not in _COPY_STREAMS:
+        _COPY_STREAMS[key] = torch.cuda.Stream(device=device)
+    return _COPY_STREAMS[key]

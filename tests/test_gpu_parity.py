@@ -208,3 +208,26 @@ def test_128_cubed_sampled(prec):
     assert (ks <= (1e-12 if prec == "df64" else 1e-5) * kabs).all()
     del M, K
     R.close()
+
+
+@pytest.mark.parametrize("prec", ["df64", "mixed"])
+def test_assemble_to_host_overlapped(prec):
+    # bands assembled range by range with their host copies overlapped equal
+    # the one-call device result
+    p, nel = 3, (21, 10, 9)
+    g, c = inputs.make(3, p, nel, 0.05, "exp", 0.1, seed=8)
+    R = wq.Rules(3, p, nel)
+    gd = [torch.from_numpy(x).cuda() for x in g]
+    cd = torch.from_numpy(c).cuda()
+    M, K = wq.assemble(R, gd, cd, prec)
+    dt = M.dtype
+    Mh = torch.empty((R.rows, R.band), dtype=dt).pin_memory()
+    Kh = torch.empty((R.rows, R.band), dtype=dt).pin_memory()
+    Md, Kd = torch.empty_like(M), torch.empty_like(K)
+    for nch in (1, 5, 8):
+        Mh.zero_()
+        Kh.zero_()
+        wq.assemble_to_host(R, gd, cd, prec, Mh, Kh, Md, Kd, nchunks=nch)
+        torch.cuda.synchronize()
+        assert torch.equal(Mh, M.cpu()) and torch.equal(Kh, K.cpu())
+    R.close()
