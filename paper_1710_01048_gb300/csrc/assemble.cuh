@@ -266,6 +266,20 @@ __device__ __forceinline__ void rows_phase_b(const RowsArgs &A, const R *sU, con
             bs[0] = b4s.x; bs[1] = b4s.y; bs[2] = b4s.z; bs[3] = b4s.w;
             vm[0] = v4m.x; vm[1] = v4m.y; vm[2] = v4m.z; vm[3] = v4m.w;
             vs[0] = v4s.x; vs[1] = v4s.y; vs[2] = v4s.z; vs[3] = v4s.w;
+          } else if constexpr (std::is_same<R, dd>::value && NP == 4) {
+            // two double-float values per 16-byte load (rows of 4 values are 32-byte aligned)
+            const float4 *b4m = reinterpret_cast<const float4 *>(bm0) + 2 * q;
+            const float4 *b4s = reinterpret_cast<const float4 *>(bs0) + 2 * q;
+            const float4 *v4m = reinterpret_cast<const float4 *>(vm0) + 2 * q;
+            const float4 *v4s = reinterpret_cast<const float4 *>(vs0) + 2 * q;
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+              const float4 x = b4m[h], y = b4s[h], z = v4m[h], w = v4s[h];
+              bm[2 * h] = dd{x.x, x.y}; bm[2 * h + 1] = dd{x.z, x.w};
+              bs[2 * h] = dd{y.x, y.y}; bs[2 * h + 1] = dd{y.z, y.w};
+              vm[2 * h] = dd{z.x, z.y}; vm[2 * h + 1] = dd{z.z, z.w};
+              vs[2 * h] = dd{w.x, w.y}; vs[2 * h + 1] = dd{w.z, w.w};
+            }
           } else {
 #pragma unroll
             for (int i = 0; i < 4; i++) { bm[i] = bm0[q * 4 + i]; bs[i] = bs0[q * 4 + i]; }
