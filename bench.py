@@ -497,9 +497,9 @@ def main():
 
     # max over ranks
     if dist is not None:
-        tt = torch.tensor([ms_step, e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_step, e2e_ms = tt.tolist()
+        from paper_1710_01048_gb300 import shard
+
+        ms_step, e2e_ms = shard.max_over_ranks([ms_step, e2e_ms], dist, device="cuda")
 
     value = world * nnz_step / (ms_step * 1e-3)
     e2e_value = world * nnz_step / (e2e_ms * 1e-3)

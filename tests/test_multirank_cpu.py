@@ -1,0 +1,81 @@
+"""The N > 1 host path on CPU: two gloo ranks shard the rows of a mesh at
+x3-plane boundaries, count their shards' non-zeros and flops with the host
+library, and reduce them; the shards must cover every row exactly once and
+the reduced counts must equal the whole mesh's."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+from paper_1710_01048_gb300 import shard
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, dim, p, nel, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_1710_01048_gb300 import binding as wq
+
+        R = wq.Rules(dim, p, nel, device=False)
+        n = [v + p for v in nel]
+        rb, re = shard.shard_rows(n, rank, world)
+        nnz = wq.wq_band_nnz_rows(R.handle, rb, re)
+        flops = R.flops(row_begin=rb, row_end=re)[0] if re > rb else 0.0
+        tot_nnz, tot_flops, nrows = shard.sum_over_ranks([nnz, flops, re - rb], dist)
+        mx = shard.max_over_ranks([float(rank), -float(rank)], dist)
+        ranges = [None] * world
+        dist.all_gather_object(ranges, (rb, re))
+        if rank == 0:
+            q.put(dict(tot_nnz=tot_nnz, tot_flops=tot_flops, nrows=nrows, mx=mx, ranges=ranges,
+                       nnz_all=wq.wq_band_nnz_rows(R.handle, 0, R.rows), flops_all=R.flops()[0], rows=R.rows))
+        R.close()
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("dim,p,nel", [(3, 3, (6, 5, 7)), (3, 2, (4, 3, 1)), (2, 3, (9, 4))])
+def test_two_rank_row_shards(dim, p, nel):
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, dim, p, nel, q)) for r in range(world)]
+    for pr in procs:
+        pr.start()
+    res = q.get(timeout=120)
+    for pr in procs:
+        pr.join(timeout=120)
+        assert pr.exitcode == 0
+    # the shards tile the rows in order, cut at plane boundaries
+    n = [v + p for v in nel]
+    per_plane = 1
+    for v in n[:-1]:
+        per_plane *= v
+    ranges = res["ranges"]
+    assert ranges[0][0] == 0 and ranges[-1][1] == res["rows"]
+    for (a0, a1), (b0, b1) in zip(ranges, ranges[1:]):
+        assert a1 == b0
+    for a0, a1 in ranges:
+        assert a0 % per_plane == 0 and a1 % per_plane == 0
+    assert res["nrows"] == res["rows"]
+    assert res["tot_nnz"] == res["nnz_all"]
+    assert abs(res["tot_flops"] - res["flops_all"]) <= 1e-9 * res["flops_all"]
+    assert res["mx"] == [1.0, 0.0]
+
+
+def test_plane_ranges_more_ranks_than_planes():
+    ranges = shard.plane_row_ranges((4, 4, 3), 5)
+    assert sum(b - a for a, b in ranges) == 48
+    assert all(a % 16 == 0 and b % 16 == 0 for a, b in ranges)
+    assert sum(1 for a, b in ranges if a == b) == 2
