@@ -54,6 +54,7 @@ struct RowsArgs {
   int nch, T;        // chunks per line and chunk length
   const void *Ug;    // U of every line, [line][2][nc1][(2P+1)^2] in R (split 3D path)
   unsigned *status;
+  float zero;  // 0.0f, read at run time by the packed double-float path (dd2_fma)
 };
 
 // acc[o + i] += x * v[i], i = 0..P, with a compile-time register index in
@@ -241,6 +242,50 @@ __device__ __forceinline__ void rows_phase_b(const RowsArgs &A, const R *sU, con
         // weighted Gaussian rule in x1: point q in element r1-P+q, band
         // offset q; the row's coefficient columns kb .. kb+P+3
         const int kb = (r1 - P) - l1lo;
+        if constexpr (std::is_same<R, dd>::value && DO_M && DO_K && NP == 4) {
+          // double-float with M and K side by side in packed pairs: the terms
+          // sharing an operand (b1M with U0 and U1; V1M with y_M and y_K) run as
+          // one packed multiply-add, the rest (y_S, V1S y_S) as before
+          const unsigned long long z = f2_pack(A.zero, A.zero);
+          dd2 w01[NP + 3], aMK[NB];
+#pragma unroll
+          for (int i = 0; i < NP + 3; i++) w01[i] = dd2_pack(U0[(kb + i) * LS + pr], U1[(kb + i) * LS + pr]);
+#pragma unroll
+          for (int j = 0; j < NB; j++) aMK[j] = dd2{z, z};
+          const float4 *b4m = reinterpret_cast<const float4 *>(&sB1[(0 * MAXPTS1 + q0) * 4]);
+          const float4 *b4s = reinterpret_cast<const float4 *>(&sB1[(1 * MAXPTS1 + q0) * 4]);
+          const float4 *v4m = reinterpret_cast<const float4 *>(&sV1[(0 * MAXPTS1 + q0) * NP]);
+          const float4 *v4s = reinterpret_cast<const float4 *>(&sV1[(1 * MAXPTS1 + q0) * NP]);
+#pragma unroll
+          for (int q = 0; q < NP; q++) {
+            dd bm[4], bs[4], vm[4], vs[4];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+              const float4 x = b4m[2 * q + h], y = b4s[2 * q + h], z = v4m[2 * q + h], w = v4s[2 * q + h];
+              bm[2 * h] = dd{x.x, x.y}; bm[2 * h + 1] = dd{x.z, x.w};
+              bs[2 * h] = dd{y.x, y.y}; bs[2 * h + 1] = dd{y.z, y.w};
+              vm[2 * h] = dd{z.x, z.y}; vm[2 * h + 1] = dd{z.z, z.w};
+              vs[2 * h] = dd{w.x, w.y}; vs[2 * h + 1] = dd{w.z, w.w};
+            }
+            dd2 yMK{z, z};
+            dd ys = r_zero<dd>();
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+              yMK = dd2_fma(dd2_pack(bm[i], bm[i]), w01[q + i], yMK, z);
+              ys = dd_fma(bs[i], dd2_first(w01[q + i]), ys);
+            }
+#pragma unroll
+            for (int i = 0; i < NP; i++) {
+              const dd2 t = dd2_fma(dd2_pack(vm[i], vm[i]), yMK, aMK[q + i], z);
+              aMK[q + i] = dd2_with_second(t, dd_fma(vs[i], ys, dd2_second(t)));
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < NB; j++) {
+            oM[j] = dd2_first(aMK[j]);
+            oK[j] = dd2_second(aMK[j]);
+          }
+        } else {
         R w0[NP + 3], w1[NP + 3], aM[NB], aK[NB];
 #pragma unroll
         for (int i = 0; i < NP + 3; i++) {
@@ -308,6 +353,7 @@ __device__ __forceinline__ void rows_phase_b(const RowsArgs &A, const R *sU, con
         for (int j = 0; j < NB; j++) {
           if constexpr (DO_M) oM[j] = aM[j];
           if constexpr (DO_K) oK[j] = aK[j];
+        }
         }
       } else {
         // Gauss-Legendre on each element of supp B_r1 (or a comparison rule):

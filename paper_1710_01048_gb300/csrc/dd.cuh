@@ -78,6 +78,80 @@ __device__ __forceinline__ double dd_to_double(dd a) {
   return float_to_double_bits(a.hi) + float_to_double_bits(a.lo);
 }
 
+// ---------------------------------------------------------------- packed pairs
+// Two double-float values side by side for the packed FP32 instructions of
+// sm_100 and later (add/sub/fma .f32x2: one instruction issues two lanes
+// of FP32 work, halving the issue slots of the arithmetic): hi = (x.hi, y.hi)
+// and lo = (x.lo, y.lo) as 64-bit register pairs.  dd2_fma performs dd_fma's
+// operations lane by lane, so each lane's result has dd_fma's bits.
+struct dd2 {
+  unsigned long long hi, lo;
+};
+
+__device__ __forceinline__ unsigned long long f2_pack(float x, float y) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long r, float &x, float &y) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+__device__ __forceinline__ dd2 dd2_pack(dd x, dd y) { return dd2{f2_pack(x.hi, y.hi), f2_pack(x.lo, y.lo)}; }
+__device__ __forceinline__ dd dd2_first(dd2 a) {
+  float h0, h1, l0, l1;
+  f2_unpack(a.hi, h0, h1);
+  f2_unpack(a.lo, l0, l1);
+  return dd{h0, l0};
+}
+__device__ __forceinline__ dd dd2_second(dd2 a) {
+  float h0, h1, l0, l1;
+  f2_unpack(a.hi, h0, h1);
+  f2_unpack(a.lo, l0, l1);
+  return dd{h1, l1};
+}
+__device__ __forceinline__ dd2 dd2_with_second(dd2 a, dd y) {
+  float h0, h1, l0, l1;
+  f2_unpack(a.hi, h0, h1);
+  f2_unpack(a.lo, l0, l1);
+  return dd2{f2_pack(h0, y.hi), f2_pack(l0, y.lo)};
+}
+
+// lane-wise a*b + c with dd_fma's operations and bits.  z must be a pair of
+// zeros that the compiler cannot see as constants (a value read at run time).
+// The leading product is formed as fma(a.hi, b.hi, z) rather than by a packed
+// multiply: with a packed multiply (or a literal zero, which lets the compiler
+// turn the FMA back into one) the generated code did not keep the product's
+// rounding separate from the following add and subtract, and every lane came
+// out wrong at single precision; with no packed multiply in the sequence each
+// lane has dd_fma's bits (checked over 2^17 random lanes).
+__device__ __forceinline__ dd2 dd2_fma(dd2 a, dd2 b, dd2 c, unsigned long long z) {
+  const unsigned long long ph = f2_fma(a.hi, b.hi, z);
+  unsigned long long pl = f2_fma(a.hi, b.hi, f2_sub(z, ph));
+  pl = f2_fma(a.hi, b.lo, pl);
+  pl = f2_fma(a.lo, b.hi, pl);
+  const unsigned long long sh = f2_add(ph, c.hi);
+  const unsigned long long t = f2_sub(sh, ph);
+  const unsigned long long sl = f2_add(f2_sub(ph, f2_sub(sh, t)), f2_sub(c.hi, t));
+  return dd2{sh, f2_add(sl, f2_add(pl, c.lo))};
+}
+
 // ---------------------------------------------------------------- generic helpers
 // The row kernels are written once over an arithmetic type R (double, float
 // or dd) through these helpers; OutT<R> is the band's storage type.
