@@ -59,14 +59,14 @@ struct RowsArgs {
 
 // acc[o + i] += x * v[i], i = 0..P, with a compile-time register index in
 // each case.
-template <int P, int O, typename R>
-__device__ __forceinline__ void fiber_at(R (&acc)[2 * P + 1], R x, const R *__restrict__ v) {
+template <int P, int O, typename R, typename VT>
+__device__ __forceinline__ void fiber_at(R (&acc)[2 * P + 1], R x, VT v) {
 #pragma unroll
   for (int i = 0; i <= P; i++) acc[O + i] = r_fma(x, v[i], acc[O + i]);
 }
 
-template <int P, typename R>
-__device__ __forceinline__ void fiber_add(R (&acc)[2 * P + 1], R x, const R *__restrict__ v, int o) {
+template <int P, typename R, typename VT>
+__device__ __forceinline__ void fiber_add(R (&acc)[2 * P + 1], R x, VT v, int o) {
   switch (o) {
     case 0: fiber_at<P, 0>(acc, x, v); break;
     case 1: fiber_at<P, 1>(acc, x, v); break;
@@ -101,8 +101,8 @@ __device__ __forceinline__ void fiber_point(R (&acc)[2 * P + 1], R x, const R *_
 // acc[o + i] += x * v[i], i = 0..P, for a runtime offset o in [0, P]: the
 // switch form for double (the FP64 pipe is the bound), the dense NB-wide
 // form with the point's P+1 columns selected by comparison otherwise.
-template <int P, typename R>
-__device__ __forceinline__ void fiber_shift(R (&acc)[2 * P + 1], R x, const R *__restrict__ v, int o) {
+template <int P, typename R, typename VT>
+__device__ __forceinline__ void fiber_shift(R (&acc)[2 * P + 1], R x, VT v, int o) {
   if constexpr (sizeof(R) == 8 && !std::is_same<R, dd>::value) {
     fiber_add<P>(acc, x, v, o);
   } else {
@@ -182,6 +182,24 @@ template <typename R> constexpr int rows_min_blocks() {
   return sizeof(R) == 4 ? WQ_ROWS_MIN_BLOCKS_F32 : std::is_same<R, dd>::value ? WQ_ROWS_MIN_BLOCKS_DD : WQ_ROWS_MIN_BLOCKS;
 }
 
+// Position of entry i of kind k (0: mass factors, 1: stiffness factors) of
+// point q in an x1 table with W entries per point.  For double the two kinds
+// are interleaved entry by entry, so that an (M, S) pair is one 16-byte load
+// (the FP64 row kernel measured 3 % faster so); float and double-float keep
+// one block per kind, whose runs of four entries their 16-byte loads take.
+template <typename R, int MAXPTS1, int W> __device__ __forceinline__ int x1_idx(int q, int i, int k) {
+  if constexpr (std::is_same<R, double>::value) return 2 * (q * W + i) + k;
+  else return (k * MAXPTS1 + q) * W + i;
+}
+
+// Entries 0.. of one kind of one point of an x1 table, indexable like a pointer.
+template <typename R, int MAXPTS1, int W> struct X1Row {
+  static constexpr int S = std::is_same<R, double>::value ? 2 : 1;  // entry stride
+  const R *v;
+  __device__ __forceinline__ X1Row(const R *t, int q, int k) : v(t + x1_idx<R, MAXPTS1, W>(q, 0, k)) {}
+  __device__ __forceinline__ R operator[](int i) const { return v[i * S]; }
+};
+
 // The chunk's x1 tables (rows [a, a+T) hold one contiguous range of points):
 // point offsets per row, folded values and cubic coefficient-spline values of
 // both kinds, elements.  No barrier; the caller synchronises.
@@ -199,9 +217,9 @@ __device__ __forceinline__ void load_x1_tables(const RowsArgs &A, const int a, c
     const R *Vg = static_cast<const R *>(A.V[0][kind]);
     const R *Bg = static_cast<const R *>(A.beta[0][kind]);
 #pragma unroll
-    for (int i = 0; i < NP; i++) sV1[(kind * MAXPTS1 + q) * NP + i] = Vg[(size_t)gq * NP + i];
+    for (int i = 0; i < NP; i++) sV1[x1_idx<R, MAXPTS1, NP>(q, i, kind)] = Vg[(size_t)gq * NP + i];
 #pragma unroll
-    for (int i = 0; i < 4; i++) sB1[(kind * MAXPTS1 + q) * 4 + i] = Bg[(size_t)gq * 4 + i];
+    for (int i = 0; i < 4; i++) sB1[x1_idx<R, MAXPTS1, 4>(q, i, kind)] = Bg[(size_t)gq * 4 + i];
     if (kind == 0) sE1[q] = A.elem[0][0][p1lo + q];
   }
 }
@@ -327,9 +345,15 @@ __device__ __forceinline__ void rows_phase_b(const RowsArgs &A, const R *sU, con
             }
           } else {
 #pragma unroll
-            for (int i = 0; i < 4; i++) { bm[i] = bm0[q * 4 + i]; bs[i] = bs0[q * 4 + i]; }
+            for (int i = 0; i < 4; i++) {
+              bm[i] = sB1[x1_idx<R, MAXPTS1, 4>(q0 + q, i, 0)];
+              bs[i] = sB1[x1_idx<R, MAXPTS1, 4>(q0 + q, i, 1)];
+            }
 #pragma unroll
-            for (int i = 0; i < NP; i++) { vm[i] = vm0[q * NP + i]; vs[i] = vs0[q * NP + i]; }
+            for (int i = 0; i < NP; i++) {
+              vm[i] = sV1[x1_idx<R, MAXPTS1, NP>(q0 + q, i, 0)];
+              vs[i] = sV1[x1_idx<R, MAXPTS1, NP>(q0 + q, i, 1)];
+            }
           }
           if constexpr (DO_M) {
             R y = r_zero<R>();
@@ -364,8 +388,8 @@ __device__ __forceinline__ void rows_phase_b(const RowsArgs &A, const R *sU, con
         for (int q = q0; q < q1end; q++) {
           const int e = sE1[q];
           const int k0 = e - l1lo, o = e - r1 + P;
-          const R *bm = &sB1[(0 * MAXPTS1 + q) * 4];
-          const R *vm = &sV1[(0 * MAXPTS1 + q) * NP];
+          const X1Row<R, MAXPTS1, 4> bm{sB1, q, 0};
+          const X1Row<R, MAXPTS1, NP> vm{sV1, q, 0};
           if constexpr (DO_M) {
             R y = r_zero<R>();
 #pragma unroll
@@ -373,7 +397,7 @@ __device__ __forceinline__ void rows_phase_b(const RowsArgs &A, const R *sU, con
             fiber_shift<P>(accM, y, vm, o);
           }
           if constexpr (DO_K) {
-            const R *bs = &sB1[(1 * MAXPTS1 + q) * 4];
+            const X1Row<R, MAXPTS1, 4> bs{sB1, q, 1};
             R yk = r_zero<R>(), ys = r_zero<R>();
 #pragma unroll
             for (int i = 0; i < 4; i++) {
@@ -381,7 +405,7 @@ __device__ __forceinline__ void rows_phase_b(const RowsArgs &A, const R *sU, con
               ys = r_fma(bs[i], U0[(k0 + i) * LS + pr], ys);
             }
             fiber_shift<P>(accK, yk, vm, o);
-            fiber_shift<P>(accK, ys, &sV1[(1 * MAXPTS1 + q) * NP], o);
+            fiber_shift<P>(accK, ys, X1Row<R, MAXPTS1, NP>{sV1, q, 1}, o);
           }
         }
 #pragma unroll
@@ -429,8 +453,8 @@ __device__ __forceinline__ void rows_block(const RowsArgs &A, const int bid, uns
   R *sV23 = reinterpret_cast<R *>(smem_raw);  // [di][kind][LM][NP]
   R *sV23d = sV23 + L::V23;                   // [di][kind][LM][NB] (boundary lines)
   R *sB23 = sV23d + L::V23D;                  // [di][kind][LM][4]
-  R *sV1 = sB23 + L::B23;                     // [kind][MAXPTS1][NP]
-  R *sB1 = sV1 + L::V1;                       // [kind][MAXPTS1][4]
+  R *sV1 = sB23 + L::B23;                     // 2 x MAXPTS1 x NP (x1_idx)
+  R *sB1 = sV1 + L::V1;                       // 2 x MAXPTS1 x 4 (x1_idx)
   R *sCb = sB1 + L::B1;                       // [l3][l2][l1]
   R *sU = sCb + L::CB;                        // [u][NL1][LS]
   R *sW = sU + L::US;                         // phase A: [warp][WS]; phase B: the row stage
