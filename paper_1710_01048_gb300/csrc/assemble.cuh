@@ -115,6 +115,20 @@ __device__ __forceinline__ void fiber_shift(R (&acc)[2 * P + 1], R x, VT v, int 
   }
 }
 
+// Double-float mass and stiffness updates of one point at band offset O,
+// packed: (aM, aK)[O+i] += (y, yk) vm[i], then aK[O+i] += ys vs[i], with
+// yy = (y, yk) and aMK[j] = (aM[j], aK[j]); the operand order of every
+// multiply-add is fiber_shift's, so the bits are those of the unpacked path.
+template <int P, int O, typename VT>
+__device__ __forceinline__ void fiber_mk_at(dd2 (&aMK)[2 * P + 1], dd2 yy, dd ys, VT vm, VT vs, unsigned long long z) {
+#pragma unroll
+  for (int i = 0; i <= P; i++) {
+    const dd v = vm[i];
+    const dd2 t = dd2_fma(yy, dd2_pack(v, v), aMK[O + i], z);
+    aMK[O + i] = dd2_with_second(t, dd_fma(ys, vs[i], dd2_second(t)));
+  }
+}
+
 // Rounds a region size up to whole 16-byte units of R.
 template <typename R> constexpr int pad16(int n) {
   return (n * (int)sizeof(R) + 15) / 16 * 16 / (int)sizeof(R);
@@ -381,37 +395,75 @@ __device__ __forceinline__ void rows_phase_b(const RowsArgs &A, const R *sU, con
         }
       } else {
         // Gauss-Legendre on each element of supp B_r1 (or a comparison rule):
-        // any number of points, each with its own band offset
-        R accM[NB], accK[NB];
+        // any number of points, each with its own band offset o
+        if constexpr (std::is_same<R, dd>::value && DO_M && DO_K) {
+          // double-float: the interior path's packed (M, K) pairs, P+1
+          // updates per point through a switch on o (uniform across a warp's
+          // items of one row; 5 % faster at 64^3 than the dense form)
+          const unsigned long long z = f2_pack(A.zero, A.zero);
+          dd2 aMK[NB];
 #pragma unroll
-        for (int j = 0; j < NB; j++) { accM[j] = r_zero<R>(); accK[j] = r_zero<R>(); }
-        for (int q = q0; q < q1end; q++) {
-          const int e = sE1[q];
-          const int k0 = e - l1lo, o = e - r1 + P;
-          const X1Row<R, MAXPTS1, 4> bm{sB1, q, 0};
-          const X1Row<R, MAXPTS1, NP> vm{sV1, q, 0};
-          if constexpr (DO_M) {
-            R y = r_zero<R>();
-#pragma unroll
-            for (int i = 0; i < 4; i++) y = r_fma(bm[i], U0[(k0 + i) * LS + pr], y);
-            fiber_shift<P>(accM, y, vm, o);
-          }
-          if constexpr (DO_K) {
-            const X1Row<R, MAXPTS1, 4> bs{sB1, q, 1};
-            R yk = r_zero<R>(), ys = r_zero<R>();
+          for (int j = 0; j < NB; j++) aMK[j] = dd2{z, z};
+          for (int q = q0; q < q1end; q++) {
+            const int e = sE1[q];
+            const int k0 = e - l1lo, o = e - r1 + P;
+            const X1Row<R, MAXPTS1, 4> bm{sB1, q, 0}, bs{sB1, q, 1};
+            const X1Row<R, MAXPTS1, NP> vm{sV1, q, 0}, vs{sV1, q, 1};
+            dd2 yy{z, z};
+            dd ys = r_zero<dd>();
 #pragma unroll
             for (int i = 0; i < 4; i++) {
-              yk = r_fma(bm[i], U1[(k0 + i) * LS + pr], yk);
-              ys = r_fma(bs[i], U0[(k0 + i) * LS + pr], ys);
+              const dd w0 = U0[(k0 + i) * LS + pr], w1 = U1[(k0 + i) * LS + pr];
+              const dd b = bm[i];
+              yy = dd2_fma(dd2_pack(b, b), dd2_pack(w0, w1), yy, z);
+              ys = dd_fma(bs[i], w0, ys);
             }
-            fiber_shift<P>(accK, yk, vm, o);
-            fiber_shift<P>(accK, ys, X1Row<R, MAXPTS1, NP>{sV1, q, 1}, o);
+            switch (o) {
+              case 0: fiber_mk_at<P, 0>(aMK, yy, ys, vm, vs, z); break;
+              case 1: fiber_mk_at<P, 1>(aMK, yy, ys, vm, vs, z); break;
+              case 2: fiber_mk_at<P, 2>(aMK, yy, ys, vm, vs, z); break;
+              default:
+                if constexpr (P >= 3) fiber_mk_at<P, (P >= 3 ? 3 : 0)>(aMK, yy, ys, vm, vs, z);
+                break;
+            }
           }
-        }
 #pragma unroll
-        for (int j = 0; j < NB; j++) {
-          if constexpr (DO_M) oM[j] = accM[j];
-          if constexpr (DO_K) oK[j] = accK[j];
+          for (int j = 0; j < NB; j++) {
+            oM[j] = dd2_first(aMK[j]);
+            oK[j] = dd2_second(aMK[j]);
+          }
+        } else {
+          R accM[NB], accK[NB];
+#pragma unroll
+          for (int j = 0; j < NB; j++) { accM[j] = r_zero<R>(); accK[j] = r_zero<R>(); }
+          for (int q = q0; q < q1end; q++) {
+            const int e = sE1[q];
+            const int k0 = e - l1lo, o = e - r1 + P;
+            const X1Row<R, MAXPTS1, 4> bm{sB1, q, 0};
+            const X1Row<R, MAXPTS1, NP> vm{sV1, q, 0};
+            if constexpr (DO_M) {
+              R y = r_zero<R>();
+#pragma unroll
+              for (int i = 0; i < 4; i++) y = r_fma(bm[i], U0[(k0 + i) * LS + pr], y);
+              fiber_shift<P>(accM, y, vm, o);
+            }
+            if constexpr (DO_K) {
+              const X1Row<R, MAXPTS1, 4> bs{sB1, q, 1};
+              R yk = r_zero<R>(), ys = r_zero<R>();
+#pragma unroll
+              for (int i = 0; i < 4; i++) {
+                yk = r_fma(bm[i], U1[(k0 + i) * LS + pr], yk);
+                ys = r_fma(bs[i], U0[(k0 + i) * LS + pr], ys);
+              }
+              fiber_shift<P>(accK, yk, vm, o);
+              fiber_shift<P>(accK, ys, X1Row<R, MAXPTS1, NP>{sV1, q, 1}, o);
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < NB; j++) {
+            if constexpr (DO_M) oM[j] = accM[j];
+            if constexpr (DO_K) oK[j] = accK[j];
+          }
         }
       }
     }
