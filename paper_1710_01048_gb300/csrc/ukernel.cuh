@@ -45,6 +45,7 @@ struct UArgs {
   int r3_lo;             // plane of the launch's first CTA
   int nblk2, nblk1;      // line blocks per plane, column blocks
   unsigned *status;
+  float zero;  // 0.0f, read at run time by the packed double-float path (dd2_fma)
 };
 
 template <int P, typename R> struct ULayout {
@@ -238,7 +239,53 @@ __device__ __forceinline__ void u_block(const UArgs &A, int bid, unsigned char *
       const R *t3s = &sT3[((1 * kUCols + l1) * NL2) * NB + j3];  // k3 = 1
       const R *v2 = &sV2[(b * 2) * LM * NP];
       const R *b2 = &sB2[(b * 2) * LM * 4];
-      if (in2 && in3) {
+      if (std::is_same<R, dd>::value && in2 && in3) {
+        // interior line in double-float: the same order, with the updates
+        // that share a table entry as packed pairs (s0, s2) and (u0, u1)
+        if constexpr (std::is_same<R, dd>::value) {
+          const unsigned long long z = f2_pack(A.zero, A.zero);
+          dd2 c02[NP];
+          dd c1[NP];
+#pragma unroll
+          for (int q2 = 0; q2 < NP; q2++) {
+            const int e = sE2[b * LM + q2] - l2lo;
+            const R *bm = &b2[(0 * LM + q2) * 4], *bs = &b2[(1 * LM + q2) * 4];
+            dd2 s02{z, z};
+            dd s1 = r_zero<dd>();
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+              const dd tm = t3m[(e + i) * NB], ts = t3s[(e + i) * NB], bb = bm[i];
+              s02 = dd2_fma(dd2_pack(tm, ts), dd2_pack(bb, bb), s02, z);
+              s1 = dd_fma(tm, bs[i], s1);
+            }
+            c02[q2] = s02;
+            c1[q2] = s1;
+          }
+#pragma unroll
+          for (int q2 = 0; q2 < NP; q2++) {
+            const R *vs = &v2[(1 * LM + q2) * NP];
+#pragma unroll
+            for (int i = 0; i < NP; i++) u1[q2 + i] = dd_fma(c1[q2], vs[i], u1[q2 + i]);
+          }
+          dd2 u01[NB];
+#pragma unroll
+          for (int j = 0; j < NB; j++) u01[j] = dd2{f2_pack(A.zero, u1[j].hi), f2_pack(A.zero, u1[j].lo)};
+#pragma unroll
+          for (int q2 = 0; q2 < NP; q2++) {
+            const R *vm = &v2[(0 * LM + q2) * NP];
+#pragma unroll
+            for (int i = 0; i < NP; i++) {
+              const dd v = vm[i];
+              u01[q2 + i] = dd2_fma(c02[q2], dd2_pack(v, v), u01[q2 + i], z);
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < NB; j++) {
+            u0[j] = dd2_first(u01[j]);
+            u1[j] = dd2_second(u01[j]);
+          }
+        }
+      } else if (in2 && in3) {
         // interior line: the row kernel's order, all q2 of (S, M) before (M, S)
         R c0[NP], c1[NP], c2[NP];
 #pragma unroll
@@ -308,7 +355,11 @@ __device__ __forceinline__ void u_block(const UArgs &A, int bid, unsigned char *
   }
 }
 
-template <int P, typename R> __global__ void __launch_bounds__(256) u_kernel(const UArgs A) {
+// Four resident CTAs per SM (the shared-memory limit as well).
+#ifndef WQ_U_MIN_BLOCKS
+#define WQ_U_MIN_BLOCKS 4
+#endif
+template <int P, typename R> __global__ void __launch_bounds__(256, WQ_U_MIN_BLOCKS) u_kernel(const UArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   u_block<P, R>(A, blockIdx.x, smem_raw);
 }
