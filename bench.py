@@ -45,7 +45,7 @@ DF64_PEAK_TFLOPS = 152 * 128 / 12 * 2 * 2.070e9 / 1e12  # 6.71
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
 # capture of the current kernel (profiles/split_kernels_3d_p3_64_df64.md);
 # absent entries report null
-TRAFFIC = {("3d_p3_64", "df64"): {"bytes": None, "kernel": "rows_ug_kernel<3, 32, M+K, dd>",
+TRAFFIC = {("3d_p3_64", "df64"): {"bytes": 1.590632e9 + 0.236710e9, "kernel": "rows_ug_kernel<3, 32, M+K, dd>",
                                   "algorithmic_bytes": 2 * 300763 * 343 * 8}}
 
 
