@@ -193,6 +193,44 @@ wq_status wq_assemble_mass_stiffness(const wq_rules *rules, const double *const 
                                      void *stream);
 
 /*
+ * Matrix-free apply: y_M = M x and y_K = K x for rows [row_begin, row_end)
+ * of the matrices of wq_assemble_mass_stiffness (Eq. Mass, Eq. Stiffness
+ * with the weighted Gaussian rules; K x is the operator of Eq. LinSys), with
+ * every band entry formed as in the assembly and multiplied into x at once:
+ * the band is never stored.
+ *   geom, coef  as for wq_assemble_mass_stiffness;
+ *   x           device, one value per row of the whole mesh (wq_rows), in
+ *               row order, double for WQ_FP64 and WQ_DF64, float for
+ *               WQ_MIXED;
+ *   yM, yK      device, row_end - row_begin values of the same type, row
+ *               row_begin first; either (not both) may be NULL.
+ * y_r is the sum over the row's band of entry times x at the entry's column,
+ * in the precision of `prec` (double-float products and sums for WQ_DF64).
+ * 3D rules objects built for the weighted Gaussian rules on the device
+ * (WQ_RULES_DEVICE, no comparison-rule flag) only: others give
+ * WQ_ERR_UNSUPPORTED.  x must not overlap yM or yK.
+ */
+wq_status wq_apply_mass_stiffness(const wq_rules *rules, const double *const *geom, const double *coef,
+                                  wq_precision prec, const void *x, void *yM, void *yK, int64_t row_begin,
+                                  int64_t row_end, void *stream);
+
+/*
+ * Load vector (Eq. Load): b_r = integral of f B_r |det J| for rows
+ * [row_begin, row_end), each row integrated by its own weighted Gaussian
+ * mass rule.  Since the basis is a partition of unity, this is M(f) 1, the
+ * mass matrix with coefficient f applied to the vector of ones, and is
+ * computed that way by the apply kernels.
+ *   geom   as for wq_assemble_mass_stiffness;
+ *   f      device, prod(nel_a + 3) doubles, x fastest: degree-3 spline of
+ *          the source f; NULL means f = 1;
+ *   b      device, row_end - row_begin values, double for WQ_FP64 and
+ *          WQ_DF64, float for WQ_MIXED.
+ * Same rules-object requirements as wq_apply_mass_stiffness.
+ */
+wq_status wq_assemble_load(const wq_rules *rules, const double *const *geom, const double *f, wq_precision prec,
+                           void *b, int64_t row_begin, int64_t row_end, void *stream);
+
+/*
  * Adjoint of the assembly with respect to the coefficient spline: every band
  * entry of M and K (Eq. Mass, Eq. Stiffness with the weighted Gaussian rules)
  * is linear in the coefficients C of c, so for band weights G, H the

@@ -29,7 +29,8 @@ EXPORTS = ["wq_status_string", "wq_version", "wq_rule_1d", "wq_rule_1d_from", "w
            "wq_rules_row", "wq_rows", "wq_band_width", "wq_band_nnz", "wq_coef_count", "wq_flop_count",
            "wq_assemble_mass", "wq_assemble_stiffness", "wq_assemble_mass_stiffness", "wq_status_check",
            "wq_assemble_noalloc", "wq_assemble_adjoint", "wq_batch_create", "wq_batch_launch", "wq_batch_status",
-           "wq_batch_get_config", "wq_batch_set_config", "wq_batch_tune", "wq_batch_free", "wq_assemble_batch", "wq_band_nnz_rows", "wq_band_to_csr"]
+           "wq_batch_get_config", "wq_batch_set_config", "wq_batch_tune", "wq_batch_free", "wq_assemble_batch", "wq_band_nnz_rows", "wq_band_to_csr",
+           "wq_apply_mass_stiffness", "wq_assemble_load"]
 
 
 class WqError(RuntimeError):
@@ -84,6 +85,9 @@ def _lib():
     lib.wq_assemble_stiffness.argtypes = [c_void_p, PP, c_void_p, c_int, c_void_p, i64, i64, c_void_p]
     lib.wq_assemble_mass_stiffness.argtypes = [c_void_p, PP, c_void_p, c_int, c_void_p, c_void_p, i64, i64,
                                                c_void_p]
+    lib.wq_apply_mass_stiffness.argtypes = [c_void_p, PP, c_void_p, c_int, c_void_p, c_void_p, c_void_p, i64, i64,
+                                            c_void_p]
+    lib.wq_assemble_load.argtypes = [c_void_p, PP, c_void_p, c_int, c_void_p, i64, i64, c_void_p]
     lib.wq_status_check.argtypes = [c_void_p, c_void_p]
     lib.wq_assemble_noalloc.argtypes = [c_void_p, PP, c_void_p, c_int, c_void_p, c_void_p, i64, i64, c_void_p, c_int]
     lib.wq_assemble_adjoint.argtypes = [c_void_p, PP, c_int, c_void_p, c_void_p, c_void_p, i64, i64, c_void_p]
@@ -215,6 +219,17 @@ def wq_assemble_mass_stiffness(handle, geom_ptrs, coef_ptr, prec, M_ptr, K_ptr, 
     return _lib().wq_assemble_mass_stiffness(handle, g, coef_ptr, prec, M_ptr, K_ptr, row_begin, row_end, stream)
 
 
+def wq_apply_mass_stiffness(handle, geom_ptrs, coef_ptr, prec, x_ptr, yM_ptr, yK_ptr, row_begin, row_end, stream):
+    g, keep = _geom_array(geom_ptrs)
+    return _lib().wq_apply_mass_stiffness(handle, g, coef_ptr, prec, x_ptr, yM_ptr, yK_ptr, row_begin, row_end,
+                                          stream)
+
+
+def wq_assemble_load(handle, geom_ptrs, f_ptr, prec, b_ptr, row_begin, row_end, stream):
+    g, keep = _geom_array(geom_ptrs)
+    return _lib().wq_assemble_load(handle, g, f_ptr, prec, b_ptr, row_begin, row_end, stream)
+
+
 def wq_status_check(handle, stream):
     return _lib().wq_status_check(handle, stream)
 
@@ -326,6 +341,62 @@ def assemble(rules, geom, coef=None, prec="fp64", mass=True, stiffness=True, row
     if check:
         _check(wq_status_check(rules.handle, s), "wq_status_check")
     return M, K
+
+
+def apply(rules, geom, x, coef=None, prec="fp64", mass=True, stiffness=True, row_begin=0, row_end=None, out=None,
+          stream=None, check=True):
+    """Matrix-free y_M = M x and y_K = K x for rows [row_begin, row_end)
+    (the band is never stored).  x: CUDA tensor of rules.rows values, float64
+    for 'fp64'/'df64', float32 for 'mixed'.  Returns (yM, yK), None for a
+    matrix not asked for; `out` = (yM, yK) tensors to write instead."""
+    import torch
+
+    if row_end is None:
+        row_end = rules.rows
+    p = PRECISIONS[prec]
+    dt = torch.float32 if p == WQ_MIXED else torch.float64
+    assert x.is_cuda and x.dtype == dt and x.is_contiguous() and x.numel() == rules.rows
+    if coef is not None:
+        assert coef.is_cuda and coef.dtype == torch.float64 and coef.is_contiguous() and coef.numel() == rules.ncoef
+    n = row_end - row_begin
+    if out is None:
+        yM = torch.empty(n, dtype=dt, device=x.device) if mass else None
+        yK = torch.empty(n, dtype=dt, device=x.device) if stiffness else None
+    else:
+        yM, yK = out
+    s = _stream_handle(stream)
+    gp = [g.data_ptr() for g in geom]
+    cp = ctypes.c_void_p(coef.data_ptr()) if coef is not None else None
+    st = wq_apply_mass_stiffness(rules.handle, gp, cp, p, ctypes.c_void_p(x.data_ptr()),
+                                 ctypes.c_void_p(yM.data_ptr()) if yM is not None else None,
+                                 ctypes.c_void_p(yK.data_ptr()) if yK is not None else None, row_begin, row_end, s)
+    _check(st, "wq_apply_mass_stiffness")
+    if check:
+        _check(wq_status_check(rules.handle, s), "wq_status_check")
+    return yM, yK
+
+
+def assemble_load(rules, geom, f=None, prec="fp64", row_begin=0, row_end=None, out=None, stream=None, check=True):
+    """Load vector b_r = integral of f B_r |det J| (Eq. Load) for rows
+    [row_begin, row_end) with the weighted Gaussian mass rules; f: CUDA
+    float64 tensor of rules.ncoef spline coefficients, or None for f = 1."""
+    import torch
+
+    if row_end is None:
+        row_end = rules.rows
+    p = PRECISIONS[prec]
+    dt = torch.float32 if p == WQ_MIXED else torch.float64
+    if f is not None:
+        assert f.is_cuda and f.dtype == torch.float64 and f.is_contiguous() and f.numel() == rules.ncoef
+    b = torch.empty(row_end - row_begin, dtype=dt, device=geom[0].device) if out is None else out
+    s = _stream_handle(stream)
+    gp = [g.data_ptr() for g in geom]
+    fp = ctypes.c_void_p(f.data_ptr()) if f is not None else None
+    _check(wq_assemble_load(rules.handle, gp, fp, p, ctypes.c_void_p(b.data_ptr()), row_begin, row_end, s),
+           "wq_assemble_load")
+    if check:
+        _check(wq_status_check(rules.handle, s), "wq_status_check")
+    return b
 
 
 def assemble_adjoint(rules, geom, G=None, H=None, prec="fp64", row_begin=0, row_end=None, out=None, stream=None,

@@ -255,7 +255,10 @@ int chunk_class(const wq_rules *R, int cls, int elem_bytes, int64_t rb, int64_t 
 
 // The 3D split path: u_kernel for the lines of rows [row_begin, row_end)
 // (their U into R->dev_U), then one row launch over those lines.
-wq_status assemble_split(const wq_rules *R, wq_precision prec, wq::RowsArgs &ra, cudaStream_t s) {
+// The split 3D path: u_kernel, then the row kernel (apply: the apply kernel,
+// y into ra.M / ra.K).
+wq_status assemble_split(const wq_rules *R, wq_precision prec, wq::RowsArgs &ra, cudaStream_t s,
+                         bool apply = false) {
   const int n1 = R->n[0], n2 = R->n[1];
   const int first_line = (int)(ra.row_begin / n1), last_line = (int)((ra.row_end - 1) / n1);
   wq::UArgs ua;
@@ -280,8 +283,9 @@ wq_status assemble_split(const wq_rules *R, wq_precision prec, wq::RowsArgs &ra,
   ua.status = R->dev_status;
   const int nplanes = last_line / n2 - ua.r3_lo + 1;
   const int ublocks = nplanes * ua.nblk2 * ua.nblk1;
-  const int T = wq::chunk_length(R, wq::kUGChunk);
-  if (wq::max_chunk_points(R, T) > wq::chunk_points_bound(R->p, wq::kUGChunk)) return WQ_ERR_UNSUPPORTED;
+  const int tmax = apply ? wq::kApplyChunk : wq::kUGChunk;
+  const int T = wq::chunk_length(R, tmax);
+  if (wq::max_chunk_points(R, T) > wq::chunk_points_bound(R->p, tmax)) return WQ_ERR_UNSUPPORTED;
   ra.lines = nullptr;
   ra.line0 = first_line;
   ra.T = T;
@@ -294,7 +298,11 @@ wq_status assemble_split(const wq_rules *R, wq_precision prec, wq::RowsArgs &ra,
     e = prec == WQ_FP64   ? wq::launch_u<2, double>(ua, ublocks, s)
         : prec == WQ_MIXED ? wq::launch_u<2, float>(ua, ublocks, s)
                            : wq::launch_u<2, wq::dd>(ua, ublocks, s);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && apply)
+      e = prec == WQ_FP64   ? wq::launch_apply_ug<2, double>(dk, ra, rblocks, s)
+          : prec == WQ_MIXED ? wq::launch_apply_ug<2, float>(dk, ra, rblocks, s)
+                             : wq::launch_apply_ug<2, wq::dd>(dk, ra, rblocks, s);
+    else if (e == cudaSuccess)
       e = prec == WQ_FP64   ? wq::launch_rows_ug<2, double>(dm, dk, ra, rblocks, s)
           : prec == WQ_MIXED ? wq::launch_rows_ug<2, float>(dm, dk, ra, rblocks, s)
                              : wq::launch_rows_ug<2, wq::dd>(dm, dk, ra, rblocks, s);
@@ -302,7 +310,11 @@ wq_status assemble_split(const wq_rules *R, wq_precision prec, wq::RowsArgs &ra,
     e = prec == WQ_FP64   ? wq::launch_u<3, double>(ua, ublocks, s)
         : prec == WQ_MIXED ? wq::launch_u<3, float>(ua, ublocks, s)
                            : wq::launch_u<3, wq::dd>(ua, ublocks, s);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && apply)
+      e = prec == WQ_FP64   ? wq::launch_apply_ug<3, double>(dk, ra, rblocks, s)
+          : prec == WQ_MIXED ? wq::launch_apply_ug<3, float>(dk, ra, rblocks, s)
+                             : wq::launch_apply_ug<3, wq::dd>(dk, ra, rblocks, s);
+    else if (e == cudaSuccess)
       e = prec == WQ_FP64   ? wq::launch_rows_ug<3, double>(dm, dk, ra, rblocks, s)
           : prec == WQ_MIXED ? wq::launch_rows_ug<3, float>(dm, dk, ra, rblocks, s)
                              : wq::launch_rows_ug<3, wq::dd>(dm, dk, ra, rblocks, s);
@@ -310,25 +322,27 @@ wq_status assemble_split(const wq_rules *R, wq_precision prec, wq::RowsArgs &ra,
   return e == cudaSuccess ? WQ_OK : WQ_ERR_CUDA;
 }
 
-wq_status assemble(const wq_rules *R, const double *const *geom, const double *coef, wq_precision prec, void *M,
-                   void *K, int64_t rb, int64_t re, void *stream) {
+// Argument checks shared by assembly and apply (rows [rb, re) non-empty or
+// empty; outputs checked by the caller).
+wq_status check_call(const wq_rules *R, const double *const *geom, wq_precision prec, int64_t rb, int64_t re) {
   if (!R || !geom) return WQ_ERR_ARG;
   if (!R->on_device) return WQ_ERR_ARG;
   if (prec != WQ_FP64 && prec != WQ_MIXED && prec != WQ_DF64) return WQ_ERR_ARG;
   if (R->mode != wq::kModeWQ && prec != WQ_FP64) return WQ_ERR_UNSUPPORTED;
   int64_t rows = (int64_t)R->n[0] * R->n[1] * R->n[2];
   if (rb < 0 || re > rows || rb > re) return WQ_ERR_ARG;
-  if (rb != re && !M && !K) return WQ_ERR_ARG;
   for (int a = 0; a < R->dim; a++)
     if (!geom[a]) return WQ_ERR_ARG;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != R->device) return WQ_ERR_ARG;
-  if (rb == re) return WQ_OK;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return WQ_OK;
+}
+
+// Fold, coefficient preparation and the row-kernel arguments for rows [rb, re).
+wq_status prepare_rows(const wq_rules *R, const double *const *geom, const double *coef, wq_precision prec,
+                       int64_t rb, int64_t re, cudaStream_t s, wq::RowsArgs &ra) {
   wq_status st = launch_fold(R, geom, s);
   if (st != WQ_OK) return st;
-
-  wq::RowsArgs ra;
   fill_tables(R, prec, ra);
   ra.coef = coef;
   if (coef) {
@@ -339,11 +353,24 @@ wq_status assemble(const wq_rules *R, const double *const *geom, const double *c
     ra.coefR = prec == WQ_FP64 ? (const void *)coef
                : prec == WQ_MIXED ? (const void *)R->dev_coef32 : (const void *)R->dev_coefdd;
   }
-  ra.M = M;
-  ra.K = K;
   ra.row_begin = rb;
   ra.row_end = re;
   ra.status = R->dev_status;
+  return WQ_OK;
+}
+
+wq_status assemble(const wq_rules *R, const double *const *geom, const double *coef, wq_precision prec, void *M,
+                   void *K, int64_t rb, int64_t re, void *stream) {
+  wq_status st = check_call(R, geom, prec, rb, re);
+  if (st != WQ_OK) return st;
+  if (rb != re && !M && !K) return WQ_ERR_ARG;
+  if (rb == re) return WQ_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  wq::RowsArgs ra;
+  st = prepare_rows(R, geom, coef, prec, rb, re, s, ra);
+  if (st != WQ_OK) return st;
+  ra.M = M;
+  ra.K = K;
   if (R->dev_U) return assemble_split(R, prec, ra, s);
   for (int cls = 0; cls < 2; cls++) {
     wq_status cst = WQ_OK;
@@ -364,6 +391,24 @@ wq_status assemble(const wq_rules *R, const double *const *geom, const double *c
     if (e != cudaSuccess) return WQ_ERR_CUDA;
   }
   return WQ_OK;
+}
+
+// y_M = M x, y_K = K x (x NULL: x = 1) through the split path's apply kernels.
+wq_status apply(const wq_rules *R, const double *const *geom, const double *coef, wq_precision prec,
+                const void *x, void *yM, void *yK, int64_t rb, int64_t re, void *stream) {
+  wq_status st = check_call(R, geom, prec, rb, re);
+  if (st != WQ_OK) return st;
+  if (R->dim != 3 || !R->dev_U) return WQ_ERR_UNSUPPORTED;
+  if (rb != re && !yM && !yK) return WQ_ERR_ARG;
+  if (rb == re) return WQ_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  wq::RowsArgs ra;
+  st = prepare_rows(R, geom, coef, prec, rb, re, s, ra);
+  if (st != WQ_OK) return st;
+  ra.M = yM;
+  ra.K = yK;
+  ra.x = x;
+  return assemble_split(R, prec, ra, s, true);
 }
 
 }  // namespace
@@ -515,6 +560,19 @@ wq_status wq_assemble_mass_stiffness(const wq_rules *rules, const double *const 
                                      void *stream) {
   if (row_begin != row_end && (!M || !K)) return WQ_ERR_ARG;
   return assemble(rules, geom, coef, prec, M, K, row_begin, row_end, stream);
+}
+
+wq_status wq_apply_mass_stiffness(const wq_rules *rules, const double *const *geom, const double *coef,
+                                  wq_precision prec, const void *x, void *yM, void *yK, int64_t row_begin,
+                                  int64_t row_end, void *stream) {
+  if (row_begin != row_end && !x) return WQ_ERR_ARG;
+  return apply(rules, geom, coef, prec, x, yM, yK, row_begin, row_end, stream);
+}
+
+wq_status wq_assemble_load(const wq_rules *rules, const double *const *geom, const double *f, wq_precision prec,
+                           void *b, int64_t row_begin, int64_t row_end, void *stream) {
+  if (row_begin != row_end && !b) return WQ_ERR_ARG;
+  return apply(rules, geom, f, prec, nullptr, b, nullptr, row_begin, row_end, stream);
 }
 
 wq_status wq_assemble_adjoint(const wq_rules *R, const double *const *geom, wq_precision prec, const void *G,

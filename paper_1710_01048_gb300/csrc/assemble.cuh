@@ -55,6 +55,10 @@ struct RowsArgs {
   const void *Ug;    // U of every line, [line][2][nc1][(2P+1)^2] in R (split 3D path)
   unsigned *status;
   float zero;  // 0.0f, read at run time by the packed double-float path (dd2_fma)
+  // matrix-free apply (rows_phase_b with APPLY): M and K above then receive
+  // y = M x and y = K x, one OutT<R> value per row of [row_begin, row_end);
+  // x holds one OutT<R> value per row of the whole mesh, or is null for x = 1
+  const void *x;
 };
 
 // acc[o + i] += x * v[i], i = 0..P, with a compile-time register index in
@@ -242,10 +246,14 @@ __device__ __forceinline__ void load_x1_tables(const RowsArgs &A, const int a, c
 // and U1 for the chunk's coefficient columns l1lo .. l1lo+NL1-1 ([u][NL1][NPAIR]);
 // sV1, sB1, sE1, sOff1 the chunk's x1 tables; sW at least NW * 32 * pad16(2P+1)
 // values of per-warp stage.
-template <int P, int D, int MAXPTS1, int NL1, bool GENERAL, bool DO_M, bool DO_K, typename R>
+// APPLY: instead of the band, y = M x and y = K x for the chunk's rows.  sX
+// holds x at the chunk's columns, [fibre][NL1 + P - 3] from column a - P (zero
+// outside the mesh); sW then holds 2 * T * NPAIR per-fibre partial sums, and
+// the call ends with a CTA-wide barrier.
+template <int P, int D, int MAXPTS1, int NL1, bool GENERAL, bool DO_M, bool DO_K, typename R, bool APPLY = false>
 __device__ __forceinline__ void rows_phase_b(const RowsArgs &A, const R *sU, const R *sV1, const R *sB1,
                                              const int *sE1, const int *sOff1, R *sW, const int a, const int T,
-                                             const int l1lo, const long long base) {
+                                             const int l1lo, const long long base, const R *sX = nullptr) {
   using O = typename OutT<R>::type;
   constexpr int NP = P + 1, NB = 2 * P + 1, NT = 32 * kRowsWarps;
   constexpr int NPAIR = (D == 3) ? NB * NB : NB, BAND = NPAIR * NB, LS = NPAIR;
@@ -467,6 +475,24 @@ __device__ __forceinline__ void rows_phase_b(const RowsArgs &A, const R *sU, con
         }
       }
     }
+    if constexpr (APPLY) {
+      // this fibre's share of y: its NB entries times x at their columns
+      // (r1 - P + j of the row's x1 index), kept per fibre for the row sums
+      if (item < nitems) {
+        constexpr int XL = NL1 + P - 3;
+        const int rl = item / NPAIR, pr = item - rl * NPAIR;
+        const R *xr = sX + pr * XL + rl;
+        R pm = r_zero<R>(), pk = r_zero<R>();
+#pragma unroll
+        for (int j = 0; j < NB; j++) {
+          if constexpr (DO_M) pm = r_fma(oM[j], xr[j], pm);
+          if constexpr (DO_K) pk = r_fma(oK[j], xr[j], pk);
+        }
+        sW[2 * item] = pm;
+        sW[2 * item + 1] = pk;
+      }
+      continue;
+    }
     const int nent = ((nitems - ib) < 32 ? (nitems - ib) : 32) * NB;
     if constexpr (DO_M) {
       if (item < nitems) {
@@ -487,6 +513,28 @@ __device__ __forceinline__ void rows_phase_b(const RowsArgs &A, const R *sU, con
       O *gK = static_cast<O *>(A.K) + ochunk + (long long)ib * NB;
       for (int i = lane; i < nent; i += 32) gK[i] = r_out(wst[i]);
       __syncwarp();
+    }
+  }
+  if constexpr (APPLY) {
+    // y of each row: the sum of its NPAIR fibre partials, formed by one warp
+    // in a fixed order (lane-strided sums, then a butterfly)
+    __syncthreads();
+    for (int rl = warp; rl < T; rl += kRowsWarps) {
+      R sm = r_zero<R>(), sk = r_zero<R>();
+      for (int pr = lane; pr < NPAIR; pr += 32) {
+        sm = r_add(sm, sW[2 * (rl * NPAIR + pr)]);
+        sk = r_add(sk, sW[2 * (rl * NPAIR + pr) + 1]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sm = r_add(sm, r_shfl_xor(sm, o));
+        sk = r_add(sk, r_shfl_xor(sk, o));
+      }
+      if (lane == 0) {
+        const long long yi = base + a + rl - A.row_begin;
+        if (DO_M && A.M) static_cast<O *>(A.M)[yi] = r_out(sm);
+        if (DO_K && A.K) static_cast<O *>(A.K)[yi] = r_out(sk);
+      }
     }
   }
 }

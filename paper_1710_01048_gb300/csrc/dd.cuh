@@ -172,6 +172,17 @@ __device__ __forceinline__ double r_add(double a, double b) { return a + b; }
 __device__ __forceinline__ float r_add(float a, float b) { return a + b; }
 __device__ __forceinline__ dd r_add(dd a, dd b) { return dd_add(a, b); }
 
+__device__ __forceinline__ double r_shfl_xor(double a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+__device__ __forceinline__ float r_shfl_xor(float a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+__device__ __forceinline__ dd r_shfl_xor(dd a, int o) {
+  return dd{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+
+// A band-typed value (OutT) in the arithmetic type.
+__device__ __forceinline__ double r_from_out(double a, double) { return a; }
+__device__ __forceinline__ float r_from_out(float a, float) { return a; }
+__device__ __forceinline__ dd r_from_out(double a, dd) { return dd_from_double(a); }
+
 __device__ __forceinline__ double r_out(double a) { return a; }
 __device__ __forceinline__ float r_out(float a) { return a; }
 __device__ __forceinline__ double r_out(dd a) { return dd_to_double(a); }

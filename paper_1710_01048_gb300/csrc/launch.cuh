@@ -87,16 +87,22 @@ cudaError_t launch_adjoint(int D, int cls, const AdjArgs &a, int nblocks, cudaSt
 
 extern template cudaError_t launch_u<2, double>(const UArgs &, int, cudaStream_t);
 extern template cudaError_t launch_rows_ug<2, double>(bool, bool, const RowsArgs &, int, cudaStream_t);
+extern template cudaError_t launch_apply_ug<2, double>(bool, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_u<2, float>(const UArgs &, int, cudaStream_t);
 extern template cudaError_t launch_rows_ug<2, float>(bool, bool, const RowsArgs &, int, cudaStream_t);
+extern template cudaError_t launch_apply_ug<2, float>(bool, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_u<2, dd>(const UArgs &, int, cudaStream_t);
 extern template cudaError_t launch_rows_ug<2, dd>(bool, bool, const RowsArgs &, int, cudaStream_t);
+extern template cudaError_t launch_apply_ug<2, dd>(bool, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_u<3, double>(const UArgs &, int, cudaStream_t);
 extern template cudaError_t launch_rows_ug<3, double>(bool, bool, const RowsArgs &, int, cudaStream_t);
+extern template cudaError_t launch_apply_ug<3, double>(bool, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_u<3, float>(const UArgs &, int, cudaStream_t);
 extern template cudaError_t launch_rows_ug<3, float>(bool, bool, const RowsArgs &, int, cudaStream_t);
+extern template cudaError_t launch_apply_ug<3, float>(bool, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_u<3, dd>(const UArgs &, int, cudaStream_t);
 extern template cudaError_t launch_rows_ug<3, dd>(bool, bool, const RowsArgs &, int, cudaStream_t);
+extern template cudaError_t launch_apply_ug<3, dd>(bool, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_rows<2, double>(int, bool, bool, int, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_rows<3, double>(int, bool, bool, int, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_rows<2, float>(int, bool, bool, int, const RowsArgs &, int, cudaStream_t);

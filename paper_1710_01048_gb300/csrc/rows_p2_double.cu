@@ -1,4 +1,4 @@
-// Instantiation of the row, split-path and adjoint kernels for degree 2, arithmetic type double.
+// Instantiation of the row, split-path, apply and adjoint kernels for degree 2, arithmetic type double.
 #include "launch.cuh"
 
 namespace wq {
@@ -6,4 +6,5 @@ template cudaError_t launch_rows<2, double>(int, bool, bool, int, const RowsArgs
 template cudaError_t launch_adjoint<2, double>(int, int, const AdjArgs &, int, cudaStream_t);
 template cudaError_t launch_u<2, double>(const UArgs &, int, cudaStream_t);
 template cudaError_t launch_rows_ug<2, double>(bool, bool, const RowsArgs &, int, cudaStream_t);
+template cudaError_t launch_apply_ug<2, double>(bool, const RowsArgs &, int, cudaStream_t);
 }

@@ -467,4 +467,114 @@ cudaError_t launch_rows_ug(bool do_m, bool do_k, const RowsArgs &a, int nblocks,
   return launch_ug_one<P, false, true, R>(a, nblocks, s);
 }
 
+// ---------------------------------------------------------------- matrix-free apply
+// The split row kernel with y = M x, y = K x in place of the band: per chunk
+// of up to kApplyChunk rows of one line, the x1 tables, the U columns and x
+// at the chunk's columns in shared memory, then phase B in APPLY mode (the
+// band entries of a fibre meet x in registers; per-row sums by one warp).
+#ifndef WQ_APPLY_CHUNK
+#define WQ_APPLY_CHUNK 16
+#endif
+constexpr int kApplyChunk = WQ_APPLY_CHUNK;
+
+template <int P, bool DO_M, bool DO_K, typename R> struct ApplyLayoutUG {
+  static constexpr int TMAX = kApplyChunk;
+  static constexpr int NP = P + 1, NB = 2 * P + 1, NPAIR = NB * NB;
+  static constexpr int NL1 = TMAX + P + 3;
+  static constexpr int XL = TMAX + 2 * P;  // x columns a - P .. a + TMAX - 1 + P
+  static constexpr int NU = DO_K ? 2 : 1;
+  static constexpr int MAXPTS1 = TMAX * NP + P * NP * (P - 1);
+  static constexpr int V1 = pad16<R>(2 * MAXPTS1 * NP);
+  static constexpr int B1 = pad16<R>(2 * MAXPTS1 * 4);
+  static constexpr int US = pad16<R>(NU * NL1 * NPAIR);
+  static constexpr int XS = pad16<R>(NPAIR * XL);
+  static constexpr int PART = pad16<R>(2 * TMAX * NPAIR);  // per-fibre partial sums (M, K)
+  static constexpr int R_TOTAL = V1 + B1 + US + XS + PART;
+  static constexpr int I_TOTAL = MAXPTS1 + TMAX + 1;
+  static constexpr size_t BYTES = sizeof(R) * (size_t)R_TOTAL + sizeof(int) * (size_t)I_TOTAL;
+};
+
+template <int P, bool DO_M, bool DO_K, typename R>
+__device__ __forceinline__ void apply_ug_block(const RowsArgs &A, int bid, unsigned char *smem_raw) {
+  using L = ApplyLayoutUG<P, DO_M, DO_K, R>;
+  using O = typename OutT<R>::type;
+  constexpr int NB = L::NB, NPAIR = L::NPAIR, NL1 = L::NL1, XL = L::XL, NT = 32 * kRowsWarps;
+  static_assert(NL1 + P - 3 == XL, "x row length seen by phase B");
+  R *sV1 = reinterpret_cast<R *>(smem_raw);
+  R *sB1 = sV1 + L::V1;
+  R *sU = sB1 + L::B1;
+  R *sX = sU + L::US;
+  R *sP = sX + L::XS;
+  int *sE1 = reinterpret_cast<int *>(smem_raw + sizeof(R) * (size_t)L::R_TOTAL);
+  int *sOff1 = sE1 + L::MAXPTS1;
+
+  const int tid = threadIdx.x;
+  const int line = A.line0 + bid / A.nch;
+  const int ch = bid % A.nch;
+  const int n1 = A.n[0], n2 = A.n[1], n3 = A.n[2];
+  const long long base = (long long)line * n1;
+  long long lo = (long long)ch * A.T, hi = lo + A.T;
+  if (hi > n1) hi = n1;
+  if (lo < A.row_begin - base) lo = A.row_begin - base;
+  if (hi > A.row_end - base) hi = A.row_end - base;
+  if (lo >= hi) return;  // uniform across the CTA: no thread reaches the barriers below
+  const int a = (int)lo, b = (int)hi, T = b - a;
+
+  load_x1_tables<P, L::MAXPTS1, R>(A, a, T, sV1, sB1, sE1, sOff1);
+  const int elo1 = a - P < 0 ? 0 : a - P;
+  const int ehi1 = (b - 1) > A.N[0] - 1 ? A.N[0] - 1 : (b - 1);
+  const int l1lo = elo1, nl1 = ehi1 - elo1 + 4;
+  const R *Ug = static_cast<const R *>(A.Ug);
+  const int nc1 = A.nc[0];
+#pragma unroll
+  for (int u = 0; u < L::NU; u++) {
+    const R *src = Ug + (((size_t)line * 2 + u) * nc1 + l1lo) * NPAIR;
+    R *dst = sU + u * NL1 * NPAIR;
+    for (int i = tid; i < nl1 * NPAIR; i += NT) dst[i] = src[i];
+  }
+  // x at the columns of the chunk's band: fibre (j3, j2) of line (r2, r3)
+  // reads row (r2 - P + j2, r3 - P + j3) of x, columns a - P .. b - 1 + P
+  const O *xg = static_cast<const O *>(A.x);
+  const int r2 = line % n2, r3 = line / n2;
+  for (int t = tid; t < NPAIR * XL; t += NT) {
+    const int pr = t / XL, c = t - pr * XL;
+    const int c1 = a - P + c, c2 = r2 - P + pr % NB, c3 = r3 - P + pr / NB;
+    R v = r_zero<R>();
+    if (c < T + 2 * P && c1 >= 0 && c1 < n1 && c2 >= 0 && c2 < n2 && c3 >= 0 && c3 < n3)
+      v = xg ? r_from_out(xg[c1 + (long long)n1 * (c2 + (long long)n2 * c3)], R()) : r_from_double<R>(1.0);
+    sX[t] = v;
+  }
+  __syncthreads();
+  rows_phase_b<P, 3, L::MAXPTS1, NL1, false, DO_M, DO_K, R, true>(A, sU, sV1, sB1, sE1, sOff1, sP, a, T, l1lo,
+                                                                    base, sX);
+}
+
+template <int P, bool DO_M, bool DO_K, typename R>
+__global__ void __launch_bounds__(32 * kRowsWarps, rows_min_blocks<R>()) apply_ug_kernel(const RowsArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  apply_ug_block<P, DO_M, DO_K, R>(A, blockIdx.x, smem_raw);
+}
+
+template <int P, bool DO_M, bool DO_K, typename R>
+cudaError_t launch_apply_one(const RowsArgs &a, int nblocks, cudaStream_t s) {
+  using L = ApplyLayoutUG<P, DO_M, DO_K, R>;
+  auto kern = apply_ug_kernel<P, DO_M, DO_K, R>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (nblocks <= 0) return cudaSuccess;
+  kern<<<nblocks, 32 * kRowsWarps, L::BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+// y = M x and y = K x (do_k), or y = M x only (the load vector's form).
+template <int P, typename R>
+cudaError_t launch_apply_ug(bool do_k, const RowsArgs &a, int nblocks, cudaStream_t s) {
+  if (do_k) return launch_apply_one<P, true, true, R>(a, nblocks, s);
+  return launch_apply_one<P, true, false, R>(a, nblocks, s);
+}
+
 }  // namespace wq
