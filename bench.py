@@ -447,6 +447,53 @@ def main():
             variants["adjoint_3d_p3_96"] = adj
             R3.close()
 
+        # matrix-free apply y = M x, y = K x (the band never stored) and the
+        # load vector, on the same workload as the headline
+        if args.workload == "3d_p3_64":
+            gen = torch.Generator(device="cuda").manual_seed(64)
+            app = {"workload": args.workload, "nnz_per_step": nnz_step}
+            for vp in ("df64", "fp64", "mixed"):
+                vdt = torch.float32 if vp == "mixed" else torch.float64
+                xv = torch.randn(rows, dtype=torch.float64, device="cuda", generator=gen).to(vdt)
+                yM = torch.empty(rows, dtype=vdt, device="cuda")
+                yK = torch.empty(rows, dtype=vdt, device="cuda")
+                for _ in range(3):
+                    wq.apply(R, gd, xv, cd, vp, out=(yM, yK), stream=stream, check=False)
+                vms = []
+                for _ in range(max(3, min(args.steps, 10))):
+                    flush.fill_(1)
+                    v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    v0.record(stream)
+                    wq.apply(R, gd, xv, cd, vp, out=(yM, yK), stream=stream, check=False)
+                    v1.record(stream)
+                    vms.append((v0, v1))
+                torch.cuda.synchronize()
+                vm = float(np.mean([x.elapsed_time(y) for x, y in vms]))
+                # the contractions plus one multiply-add per band entry and matrix
+                fl_apply = R.flops()[0] + 2 * 2 * R.nnz
+                pk = {"fp64": FP64_PEAK_TFLOPS, "df64": DF64_PEAK_TFLOPS, "mixed": FP32_PEAK_TFLOPS}[vp]
+                tf = fl_apply / (vm * 1e-3) / 1e12
+                app[vp] = {"ms_per_step": vm, "value": world * nnz_step / (vm * 1e-3), "unit": "nnz/s (applied)",
+                           "roofline": {"bound": "alu", "achieved": tf, "peak": pk, "unit": "TFLOP/s",
+                                        "frac": tf / pk}}
+                if vp == "df64":
+                    bl = torch.empty(rows, dtype=vdt, device="cuda")
+                    for _ in range(3):
+                        wq.assemble_load(R, gd, cd, vp, out=bl, stream=stream, check=False)
+                    v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    v0.record(stream)
+                    for _ in range(5):
+                        wq.assemble_load(R, gd, cd, vp, out=bl, stream=stream, check=False)
+                    v1.record(stream)
+                    torch.cuda.synchronize()
+                    app["load_vector_df64_ms"] = v0.elapsed_time(v1) / 5
+                    del bl
+                del xv, yM, yK
+            sta = wq.wq_status_check(R.handle, wq._stream_handle(stream))
+            if sta != wq.WQ_OK:
+                raise wq.WqError(sta, "apply variant")
+            variants["apply_3d_p3_64"] = app
+
         # the batch of 256 independent patches (8..48 elements per direction, p in {2, 3}):
         # one graph of two persistent launches, tuned, against one call per patch
         if not args.no_batch:
