@@ -58,7 +58,11 @@ template <int P, typename R> struct ULayout {
   static constexpr int V2 = pad16<R>(kULines * 2 * LM * NP);   // [b][k2][q2][i]
   static constexpr int B2 = pad16<R>(kULines * 2 * LM * 4);    // [b][k2][q2][i]
   static constexpr int CB = pad16<R>(kUCols * NL2 * NL3);      // [l1][l2][l3]
-  static constexpr int T3 = pad16<R>(2 * kUCols * NL2 * NB);   // [k3][l1][l2][j3]
+  // T3 [k3][l1] blocks of NL2 * NB values, padded to a stride = NB (mod 32):
+  // the x2 stage's 32 lanes read runs of NB values from consecutive l1
+  // blocks, which then fall in disjoint shared-memory banks
+  static constexpr int T3S = NL2 * NB + ((NB - NL2 * NB) % 32 + 32) % 32;
+  static constexpr int T3 = pad16<R>(2 * kUCols * T3S);          // [k3][l1][l2][j3]
   static constexpr int WST = pad16<R>(32 * NB);                // per-warp stage
   static constexpr int R_TOTAL = V3 + B3 + V2 + B2 + CB + T3 + 8 * WST;
   // int region: e3[LM], o3[LM], L2[kULines], e2[kULines][LM], o2[kULines][LM]
@@ -207,7 +211,7 @@ __device__ __forceinline__ void u_block(const UArgs &A, int bid, unsigned char *
         }
       }
 #pragma unroll
-      for (int j = 0; j < NB; j++) sT3[((k3 * kUCols + l1) * NL2 + l2) * NB + j] = acc[j];
+      for (int j = 0; j < NB; j++) sT3[(k3 * kUCols + l1) * L::T3S + l2 * NB + j] = acc[j];
     }
   }
   __syncthreads();
@@ -235,8 +239,8 @@ __device__ __forceinline__ void u_block(const UArgs &A, int bid, unsigned char *
     if (ok) {
       const int r2 = r2a + b, L2 = sL2[b];
       const bool in2 = r2 >= P && r2 <= A.N[1] - 1;
-      const R *t3m = &sT3[((0 * kUCols + l1) * NL2) * NB + j3];  // k3 = 0, index by l2 * NB
-      const R *t3s = &sT3[((1 * kUCols + l1) * NL2) * NB + j3];  // k3 = 1
+      const R *t3m = &sT3[(0 * kUCols + l1) * L::T3S + j3];  // k3 = 0, index by l2 * NB
+      const R *t3s = &sT3[(1 * kUCols + l1) * L::T3S + j3];  // k3 = 1
       const R *v2 = &sV2[(b * 2) * LM * NP];
       const R *b2 = &sB2[(b * 2) * LM * 4];
       if (std::is_same<R, dd>::value && in2 && in3) {
