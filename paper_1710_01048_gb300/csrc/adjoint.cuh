@@ -9,9 +9,9 @@
 //        yM[q] = sum_j1 H[j1] V1M[q][j1],  yK[q] = sum_j1 G[j1] V1M[q][j1],
 //        yS[q] = sum_j1 G[j1] V1S[q][j1]
 //      accumulated into Ubar0[l1] += b1M[q][l1] yM[q] + b1S[q][l1] yS[q] and
-//      Ubar1[l1] += b1M[q][l1] yK[q].  Rows at least 7 apart touch disjoint
-//      coefficient columns, so the rows are taken in 7 phases and every
-//      shared-memory update is exclusive.
+//      Ubar1[l1] += b1M[q][l1] yK[q]: each thread takes one fibre of four
+//      consecutive rows and keeps its columns in registers, and the threads'
+//      windows are added to Ubar in three ordered rounds.
 //   2. x2 then x3 stages transposed, one warp per coefficient column, giving
 //      the chunk's block of dJ/dC, added to the gradient in global memory.
 #pragma once
@@ -33,16 +33,14 @@ struct AdjLayout {
   static constexpr int NPAIR = F::NPAIR, BAND = F::BAND, NSLOT = F::NSLOT;
   static constexpr int NL1 = F::NL1, NL = P + 4, NW = F::NW, NT = F::NT, MAXPTS1 = F::MAXPTS1;
   static constexpr int NPHASE = P + 4;  // rows this far apart touch disjoint columns
-  // per-warp scratch: a row slice of G and H (phase 1) or the column work (phase 2)
-  static constexpr int WG = 2 * 32 * NB;                                   // [H|G][32 fibres][NB]
+  // per-warp scratch of phase 2 (the column work)
   static constexpr int WQ = (D == 3) ? 3 * LM * NB : 2 * LM;               // Cqbar
   static constexpr int WT = (D == 3) ? 2 * NL * NB : 0;                    // T3bar
   static constexpr int WZ = (D == 3) ? 2 * NL * LM : 0;                    // Zbar
-  static constexpr int WS = pad16<R>((WG > WQ + WT + WZ) ? WG : WQ + WT + WZ);
+  static constexpr int WS = pad16<R>(WQ + WT + WZ);
   static constexpr int V23 = F::V23, V23D = F::V23D, B23 = F::B23, V1 = F::V1, B1 = F::B1;
-  static constexpr int V1D = pad16<R>(2 * MAXPTS1 * NB);  // zero-padded x1 tables [kind][point][j]
   static constexpr int UB = pad16<R>(2 * NL1 * NPAIR);                     // [u][l1][pair]
-  static constexpr int R_TOTAL = V23 + V23D + B23 + V1 + V1D + B1 + UB + NW * WS;
+  static constexpr int R_TOTAL = V23 + V23D + B23 + V1 + B1 + UB + NW * WS;
   static constexpr int I_TOTAL = 4 * LM + MAXPTS1 + TMAX + 1;
   static constexpr size_t BYTES = sizeof(R) * (size_t)R_TOTAL + sizeof(int) * (size_t)I_TOTAL;
 };
@@ -52,6 +50,58 @@ template <> __device__ __forceinline__ dd r_from_out<dd>(double v) { return dd_f
 __device__ __forceinline__ double r_to_double(double a) { return a; }
 __device__ __forceinline__ double r_to_double(float a) { return (double)a; }
 __device__ __forceinline__ double r_to_double(dd a) { return dd_to_double(a); }
+
+// One x1 point of the transposed x1 stage at band offset O for window row K
+// (the point's columns are window columns K + O .. K + O + 3).
+template <int P, int O, int K, int WN, typename R>
+__device__ __forceinline__ void adj_x1_point(R (&w0)[WN], R (&w1)[WN], const R (&hv)[2 * P + 1],
+                                             const R (&gv)[2 * P + 1], const R *vm, const R *vs, const R *bm,
+                                             const R *bs) {
+  R yM = r_zero<R>(), yK = r_zero<R>(), yS = r_zero<R>();
+#pragma unroll
+  for (int i = 0; i <= P; i++) {
+    yM = r_fma(hv[O + i], vm[i], yM);
+    yK = r_fma(gv[O + i], vm[i], yK);
+    yS = r_fma(gv[O + i], vs[i], yS);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    w0[K + O + i] = r_fma(bs[i], yS, r_fma(bm[i], yM, w0[K + O + i]));
+    w1[K + O + i] = r_fma(bm[i], yK, w1[K + O + i]);
+  }
+}
+
+// Row K of a segment starting at chunk row rl (x1 index a + rl + K): the
+// fibre's H and G entries (grow: the fibre's first entry in row rl; a null
+// weight is zero), then the row's points through a switch on the band offset.
+template <int P, int K, int WN, int MAXPTS1, int BAND, typename R, typename O>
+__device__ __forceinline__ void adj_x1_row(R (&w0)[WN], R (&w1)[WN], const int rl, const int T, const int a,
+                                           const O *Hg, const O *Gg, const long long grow, const int *sOff1,
+                                           const int *sE1, const R *sV1, const R *sB1) {
+  constexpr int NP = P + 1, NB = 2 * P + 1;
+  if (rl + K >= T) return;
+  const long long g = grow + (long long)K * BAND;
+  R hv[NB], gv[NB];
+#pragma unroll
+  for (int j = 0; j < NB; j++) {
+    hv[j] = Hg ? r_from_out<R>(Hg[g + j]) : r_zero<R>();
+    gv[j] = Gg ? r_from_out<R>(Gg[g + j]) : r_zero<R>();
+  }
+  const int q0 = sOff1[rl + K], q1e = sOff1[rl + K + 1];
+  for (int q = q0; q < q1e; q++) {
+    const int o = sE1[q] - (a + rl + K) + P;
+    const R *vm = &sV1[(0 * MAXPTS1 + q) * NP], *vs = &sV1[(1 * MAXPTS1 + q) * NP];
+    const R *bm = &sB1[(0 * MAXPTS1 + q) * 4], *bs = &sB1[(1 * MAXPTS1 + q) * 4];
+    switch (o) {
+      case 0: adj_x1_point<P, 0, K, WN>(w0, w1, hv, gv, vm, vs, bm, bs); break;
+      case 1: adj_x1_point<P, 1, K, WN>(w0, w1, hv, gv, vm, vs, bm, bs); break;
+      case 2: adj_x1_point<P, 2, K, WN>(w0, w1, hv, gv, vm, vs, bm, bs); break;
+      default:
+        if constexpr (P >= 3) adj_x1_point<P, (P >= 3 ? 3 : 0), K, WN>(w0, w1, hv, gv, vm, vs, bm, bs);
+        break;
+    }
+  }
+}
 
 template <int P, int D, int LM, int TMAX, typename R>
 __global__ void __launch_bounds__(32 * kRowsWarps, sizeof(R) == 4 ? 2 : 1) adjoint_kernel(const AdjArgs AA) {
@@ -68,8 +118,7 @@ __global__ void __launch_bounds__(32 * kRowsWarps, sizeof(R) == 4 ? 2 : 1) adjoi
   R *sV23d = sV23 + L::V23;
   R *sB23 = sV23d + L::V23D;
   R *sV1 = sB23 + L::B23;
-  R *sV1d = sV1 + L::V1;
-  R *sB1 = sV1d + L::V1D;
+  R *sB1 = sV1 + L::V1;
   R *sUb = sB1 + L::B1;  // [u][NL1][NPAIR]
   R *sW = sUb + L::UB;
   int *sE23 = reinterpret_cast<int *>(smem_raw + sizeof(R) * (size_t)L::R_TOTAL);
@@ -146,68 +195,61 @@ __global__ void __launch_bounds__(32 * kRowsWarps, sizeof(R) == 4 ? 2 : 1) adjoi
     for (int i = 0; i < NP; i++) sV1[(kind * L::MAXPTS1 + q) * NP + i] = Vg[(size_t)gq * NP + i];
 #pragma unroll
     for (int i = 0; i < 4; i++) sB1[(kind * L::MAXPTS1 + q) * 4 + i] = Bg[(size_t)gq * 4 + i];
-    const int e = A.elem[0][0][p1lo + q];
-    if (kind == 0) sE1[q] = e;
-    int lo_r = 0, hi_r = T - 1;
-    while (lo_r < hi_r) {
-      const int mid = (lo_r + hi_r + 1) >> 1;
-      if (sOff1[mid] <= q) lo_r = mid; else hi_r = mid - 1;
-    }
-    const int o = e - (a + lo_r) + P;
-#pragma unroll
-    for (int j = 0; j < NB; j++)
-      sV1d[(kind * L::MAXPTS1 + q) * NB + j] = (j >= o && j <= o + P) ? Vg[(size_t)gq * NP + (j - o)] : r_zero<R>();
+    if (kind == 0) sE1[q] = A.elem[0][0][p1lo + q];
   }
   const int L2 = L23[0], L3 = L23[1];
   const int nl2 = nl23[0], nl3 = (D == 3) ? nl23[1] : 1;
   __syncthreads();
 
-  // ------------------------------------------------ 1. x1 stage transposed, rows in phases
-  R *ws = sW + warp * L::WS;  // [0: H | 1: G][32][NB]
+  // ------------------------------------------------ 1. x1 stage transposed, register windows
+  // Thread (segment s, fibre pr) takes rows s*RS .. s*RS+RS-1 of the chunk for
+  // band fibre pr: per row and x1 point q (element e, band offset o = e - r1 + P)
+  //   yM = sum_i H[o+i] V1M[q][i], yK = sum_i G[o+i] V1M[q][i], yS = sum_i G[o+i] V1S[q][i]
+  // and Ubar0[e+i] += b1M[q][i] yM + b1S[q][i] yS, Ubar1[e+i] += b1M[q][i] yK,
+  // kept in a register window over the columns its rows touch.  The windows
+  // are then added to Ubar in three ordered rounds (segments s, s+3, ... touch
+  // disjoint columns), so the result does not depend on thread timing.
   R *Ub0 = sUb, *Ub1 = sUb + NL1 * NPAIR;
-  const O *Hg = static_cast<const O *>(AA.H);
-  const O *Gg = static_cast<const O *>(AA.G);
-  for (int ph = 0; ph < L::NPHASE; ph++) {
-    const int nrows_ph = (T - ph + L::NPHASE - 1) / L::NPHASE;  // rows ph, ph+NPHASE, ...
-    for (int item = warp; item < nrows_ph * L::NSLOT; item += NW) {
-      const int rl = ph + (item / L::NSLOT) * L::NPHASE, s = item % L::NSLOT;
-      const int r1 = a + rl;
-      const int f0 = 32 * s, nf = (NPAIR - f0) < 32 ? (NPAIR - f0) : 32;
-      // this slot's fibres of the row: NB consecutive entries each, one contiguous run
-      const long long grow = (base + r1 - A.row_begin) * BAND + (long long)f0 * NB;
-      for (int i = lane; i < nf * NB; i += 32) {
-        ws[i] = hasH ? r_from_out<R>(Hg[grow + i]) : r_zero<R>();
-        ws[32 * NB + i] = hasG ? r_from_out<R>(Gg[grow + i]) : r_zero<R>();
+  {
+    constexpr int RS = 4, WN = RS + P + 3;
+    const O *Hg = hasH ? static_cast<const O *>(AA.H) : nullptr;
+    const O *Gg = hasG ? static_cast<const O *>(AA.G) : nullptr;
+    const int nseg = (T + RS - 1) / RS, nitems = nseg * NPAIR;
+    for (int it0 = 0; it0 < nitems; it0 += NT) {  // uniform trip count: every thread meets the barriers
+      const int it = it0 + tid;
+      const bool act = it < nitems;
+      const int sg = it / NPAIR, pr = it - sg * NPAIR;
+      R w0[WN], w1[WN];
+#pragma unroll
+      for (int c = 0; c < WN; c++) {
+        w0[c] = r_zero<R>();
+        w1[c] = r_zero<R>();
       }
-      __syncwarp();
-      if (lane < nf) {
-        const int pr = f0 + lane;
-        const R *hv = &ws[lane * NB];
-        const R *gv = &ws[32 * NB + lane * NB];
-        const int q0 = sOff1[rl], q1e = sOff1[rl + 1];
-        for (int q = q0; q < q1e; q++) {
-          const int e = sE1[q], k0 = e - l1lo;
-          const R *vm = &sV1d[(0 * L::MAXPTS1 + q) * NB], *vs = &sV1d[(1 * L::MAXPTS1 + q) * NB];
-          R yM = r_zero<R>(), yK = r_zero<R>(), yS = r_zero<R>();
+      if (act) {
+        const long long grow = (base + a + sg * RS - A.row_begin) * BAND + (long long)pr * NB;
+        const int rl = sg * RS;
+        static_assert(RS == 4, "four rows per segment");
+        adj_x1_row<P, 0, WN, L::MAXPTS1, BAND>(w0, w1, rl, T, a, Hg, Gg, grow, sOff1, sE1, sV1, sB1);
+        adj_x1_row<P, 1, WN, L::MAXPTS1, BAND>(w0, w1, rl, T, a, Hg, Gg, grow, sOff1, sE1, sV1, sB1);
+        adj_x1_row<P, 2, WN, L::MAXPTS1, BAND>(w0, w1, rl, T, a, Hg, Gg, grow, sOff1, sE1, sV1, sB1);
+        adj_x1_row<P, 3, WN, L::MAXPTS1, BAND>(w0, w1, rl, T, a, Hg, Gg, grow, sOff1, sE1, sV1, sB1);
+      }
+      // window column c is coefficient column a + sg*RS - P + c
+      const int cbase = a + sg * RS - P - l1lo;
+      for (int round = 0; round < 3; round++) {
+        if (act && sg % 3 == round) {
 #pragma unroll
-          for (int j = 0; j < NB; j++) {
-            yM = r_fma(hv[j], vm[j], yM);
-            yK = r_fma(gv[j], vm[j], yK);
-            yS = r_fma(gv[j], vs[j], yS);
-          }
-          const R *bm = &sB1[(0 * L::MAXPTS1 + q) * 4], *bs = &sB1[(1 * L::MAXPTS1 + q) * 4];
-#pragma unroll
-          for (int i = 0; i < 4; i++) {
-            R *u0 = &Ub0[(k0 + i) * NPAIR + pr];
-            *u0 = r_fma(bs[i], yS, r_fma(bm[i], yM, *u0));
-            R *u1 = &Ub1[(k0 + i) * NPAIR + pr];
-            *u1 = r_fma(bm[i], yK, *u1);
+          for (int c = 0; c < WN; c++) {
+            const int col = cbase + c;
+            if (col >= 0 && col < nl1) {
+              Ub0[col * NPAIR + pr] = r_add(Ub0[col * NPAIR + pr], w0[c]);
+              Ub1[col * NPAIR + pr] = r_add(Ub1[col * NPAIR + pr], w1[c]);
+            }
           }
         }
+        __syncthreads();
       }
-      __syncwarp();
     }
-    __syncthreads();
   }
 
   // ------------------------------------------------ 2. x2, x3 stages transposed, warp per column
