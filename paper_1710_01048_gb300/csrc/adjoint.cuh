@@ -103,8 +103,23 @@ __device__ __forceinline__ void adj_x1_row(R (&w0)[WN], R (&w1)[WN], const int r
   }
 }
 
+// Resident CTAs per SM the register allocation is sized for (measured at
+// 96^3: four for float, three for double, two for double-float, whose
+// register windows spill at three).
+#ifndef WQ_ADJ_MIN_BLOCKS_F32
+#define WQ_ADJ_MIN_BLOCKS_F32 4
+#endif
+#ifndef WQ_ADJ_MIN_BLOCKS_F64
+#define WQ_ADJ_MIN_BLOCKS_F64 3
+#endif
+#ifndef WQ_ADJ_MIN_BLOCKS_DD
+#define WQ_ADJ_MIN_BLOCKS_DD 2
+#endif
+template <typename R> constexpr int adj_min_blocks() {
+  return sizeof(R) == 4 ? WQ_ADJ_MIN_BLOCKS_F32 : std::is_same<R, dd>::value ? WQ_ADJ_MIN_BLOCKS_DD : WQ_ADJ_MIN_BLOCKS_F64;
+}
 template <int P, int D, int LM, int TMAX, typename R>
-__global__ void __launch_bounds__(32 * kRowsWarps, sizeof(R) == 4 ? 2 : 1) adjoint_kernel(const AdjArgs AA) {
+__global__ void __launch_bounds__(32 * kRowsWarps, adj_min_blocks<R>()) adjoint_kernel(const AdjArgs AA) {
   using L = AdjLayout<P, D, LM, TMAX, R>;
   using O = typename OutT<R>::type;
   const RowsArgs &A = AA.rows;
