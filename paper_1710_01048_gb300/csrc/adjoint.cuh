@@ -30,9 +30,8 @@ template <int P, int D, int LM, int TMAX, typename R>
 struct AdjLayout {
   using F = RowsLayout<P, D, LM, TMAX, true, true, R>;
   static constexpr int NP = P + 1, NB = 2 * P + 1;
-  static constexpr int NPAIR = F::NPAIR, BAND = F::BAND, NSLOT = F::NSLOT;
+  static constexpr int NPAIR = F::NPAIR, BAND = F::BAND;
   static constexpr int NL1 = F::NL1, NL = P + 4, NW = F::NW, NT = F::NT, MAXPTS1 = F::MAXPTS1;
-  static constexpr int NPHASE = P + 4;  // rows this far apart touch disjoint columns
   // per-warp scratch of phase 2 (the column work)
   static constexpr int WQ = (D == 3) ? 3 * LM * NB : 2 * LM;               // Cqbar
   static constexpr int WT = (D == 3) ? 2 * NL * NB : 0;                    // T3bar
@@ -45,8 +44,6 @@ struct AdjLayout {
   static constexpr size_t BYTES = sizeof(R) * (size_t)R_TOTAL + sizeof(int) * (size_t)I_TOTAL;
 };
 
-template <typename R> __device__ __forceinline__ R r_from_out(typename OutT<R>::type v) { return (R)v; }
-template <> __device__ __forceinline__ dd r_from_out<dd>(double v) { return dd_from_double(v); }
 __device__ __forceinline__ double r_to_double(double a) { return a; }
 __device__ __forceinline__ double r_to_double(float a) { return (double)a; }
 __device__ __forceinline__ double r_to_double(dd a) { return dd_to_double(a); }

@@ -178,10 +178,9 @@ __device__ __forceinline__ dd r_shfl_xor(dd a, int o) {
   return dd{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
 }
 
-// A band-typed value (OutT) in the arithmetic type.
-__device__ __forceinline__ double r_from_out(double a, double) { return a; }
-__device__ __forceinline__ float r_from_out(float a, float) { return a; }
-__device__ __forceinline__ dd r_from_out(double a, dd) { return dd_from_double(a); }
+// A band-typed value (OutT<R>) in the arithmetic type R.
+template <typename R> __device__ __forceinline__ R r_from_out(typename OutT<R>::type v) { return (R)v; }
+template <> __device__ __forceinline__ dd r_from_out<dd>(double v) { return dd_from_double(v); }
 
 __device__ __forceinline__ double r_out(double a) { return a; }
 __device__ __forceinline__ float r_out(float a) { return a; }

@@ -545,7 +545,7 @@ __device__ __forceinline__ void apply_ug_block(const RowsArgs &A, int bid, unsig
     const int c1 = a - P + c, c2 = r2 - P + pr % NB, c3 = r3 - P + pr / NB;
     R v = r_zero<R>();
     if (c < T + 2 * P && c1 >= 0 && c1 < n1 && c2 >= 0 && c2 < n2 && c3 >= 0 && c3 < n3)
-      v = xg ? r_from_out(xg[c1 + (long long)n1 * (c2 + (long long)n2 * c3)], R()) : r_from_double<R>(1.0);
+      v = xg ? r_from_out<R>(xg[c1 + (long long)n1 * (c2 + (long long)n2 * c3)]) : r_from_double<R>(1.0);
     sX[t] = v;
   }
   __syncthreads();
