@@ -206,9 +206,9 @@ wq_status wq_assemble_mass_stiffness(const wq_rules *rules, const double *const 
  *               row_begin first; either (not both) may be NULL.
  * y_r is the sum over the row's band of entry times x at the entry's column,
  * in the precision of `prec` (double-float products and sums for WQ_DF64).
- * 3D rules objects built for the weighted Gaussian rules on the device
- * (WQ_RULES_DEVICE, no comparison-rule flag) only: others give
- * WQ_ERR_UNSUPPORTED.  x must not overlap yM or yK.
+ * Rules objects built for the weighted Gaussian rules on the device
+ * (WQ_RULES_DEVICE, no comparison-rule flag), 2D or 3D; comparison-rule
+ * objects give WQ_ERR_UNSUPPORTED.  x must not overlap yM or yK.
  */
 wq_status wq_apply_mass_stiffness(const wq_rules *rules, const double *const *geom, const double *coef,
                                   wq_precision prec, const void *x, void *yM, void *yK, int64_t row_begin,

@@ -254,9 +254,8 @@ int chunk_class(const wq_rules *R, int cls, int elem_bytes, int64_t rb, int64_t 
 }
 
 // The 3D split path: u_kernel for the lines of rows [row_begin, row_end)
-// (their U into R->dev_U), then one row launch over those lines.
-// The split 3D path: u_kernel, then the row kernel (apply: the apply kernel,
-// y into ra.M / ra.K).
+// (their U into R->dev_U), then one launch of the row kernel over those
+// lines (apply: of the apply kernel, y into ra.M / ra.K).
 wq_status assemble_split(const wq_rules *R, wq_precision prec, wq::RowsArgs &ra, cudaStream_t s,
                          bool apply = false) {
   const int n1 = R->n[0], n2 = R->n[1];
@@ -398,7 +397,7 @@ wq_status apply(const wq_rules *R, const double *const *geom, const double *coef
                 const void *x, void *yM, void *yK, int64_t rb, int64_t re, void *stream) {
   wq_status st = check_call(R, geom, prec, rb, re);
   if (st != WQ_OK) return st;
-  if (R->dim != 3 || !R->dev_U) return WQ_ERR_UNSUPPORTED;
+  if (R->mode != wq::kModeWQ || (R->dim == 3 && !R->dev_U)) return WQ_ERR_UNSUPPORTED;
   if (rb != re && !yM && !yK) return WQ_ERR_ARG;
   if (rb == re) return WQ_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -408,7 +407,26 @@ wq_status apply(const wq_rules *R, const double *const *geom, const double *coef
   ra.M = yM;
   ra.K = yK;
   ra.x = x;
-  return assemble_split(R, prec, ra, s, true);
+  if (R->dim == 3) return assemble_split(R, prec, ra, s, true);
+  // 2D: the fused row kernel in apply mode, per line class
+  const bool dk = yK != nullptr;
+  for (int cls = 0; cls < 2; cls++) {
+    wq_status cst = WQ_OK;
+    const int nblocks = chunk_class(R, cls, prec == WQ_MIXED ? 4 : 8, rb, re, ra, &cst);
+    if (cst != WQ_OK) return cst;
+    if (nblocks == 0) continue;
+    cudaError_t e;
+    if (R->p == 2)
+      e = prec == WQ_FP64   ? wq::launch_apply_2d<2, double>(cls, dk, ra, nblocks, s)
+          : prec == WQ_MIXED ? wq::launch_apply_2d<2, float>(cls, dk, ra, nblocks, s)
+                             : wq::launch_apply_2d<2, wq::dd>(cls, dk, ra, nblocks, s);
+    else
+      e = prec == WQ_FP64   ? wq::launch_apply_2d<3, double>(cls, dk, ra, nblocks, s)
+          : prec == WQ_MIXED ? wq::launch_apply_2d<3, float>(cls, dk, ra, nblocks, s)
+                             : wq::launch_apply_2d<3, wq::dd>(cls, dk, ra, nblocks, s);
+    if (e != cudaSuccess) return WQ_ERR_CUDA;
+  }
+  return WQ_OK;
 }
 
 }  // namespace

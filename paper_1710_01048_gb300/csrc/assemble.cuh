@@ -138,7 +138,7 @@ template <typename R> constexpr int pad16(int n) {
   return (n * (int)sizeof(R) + 15) / 16 * 16 / (int)sizeof(R);
 }
 
-template <int P, int D, int LM, int TMAX, bool DO_M, bool DO_K, typename R>
+template <int P, int D, int LM, int TMAX, bool DO_M, bool DO_K, typename R, bool APPLY = false>
 struct RowsLayout {
   static constexpr int NP = P + 1;             // points of a weighted Gaussian rule
   static constexpr int NB = 2 * P + 1;         // band width per direction
@@ -167,7 +167,11 @@ struct RowsLayout {
   static constexpr int WS = pad16<R>(WA);  // phase A, per half-warp
   // phase B: per-warp stage of 32 items' fibres, one matrix at a time
   static constexpr int WST = pad16<R>(32 * NB);
-  static constexpr int SCRATCH = (2 * NW * WS) > (NW * WST) ? (2 * NW * WS) : (NW * WST);
+  static constexpr int SCRATCH0 = (2 * NW * WS) > (NW * WST) ? (2 * NW * WS) : (NW * WST);
+  // apply: phase B's per-fibre partial sums share the scratch; x gets its own region
+  static constexpr int PART = pad16<R>(2 * TMAX * NPAIR);
+  static constexpr int SCRATCH = (APPLY && PART > SCRATCH0) ? PART : SCRATCH0;
+  static constexpr int XS = APPLY ? pad16<R>(NPAIR * (TMAX + 2 * P)) : 0;
   // R region
   static constexpr bool INNER_GAUSS = (LM == P + 1);  // interior line: o = q in x2, x3
   // every region is a whole number of 16-byte units, so 4-wide float rows stay aligned
@@ -178,7 +182,7 @@ struct RowsLayout {
   static constexpr int B1 = pad16<R>(2 * MAXPTS1 * 4);
   static constexpr int CB = pad16<R>(NL3 * NL * NL1);    // [l3][l2][l1]
   static constexpr int US = pad16<R>(NU * NL1 * LS);     // [u][l1][j3*NB+j2]
-  static constexpr int R_TOTAL = V23 + V23D + B23 + V1 + B1 + CB + US + SCRATCH;
+  static constexpr int R_TOTAL = V23 + V23D + B23 + V1 + B1 + CB + US + SCRATCH + XS;
   // int region: E23[2][LM], O23[2][LM], E1[MAXPTS1], OFF1[TMAX+1]
   static constexpr int I_TOTAL = 4 * LM + MAXPTS1 + TMAX + 1;
   static constexpr size_t BYTES = sizeof(R) * (size_t)R_TOTAL + sizeof(int) * (size_t)I_TOTAL;
@@ -539,13 +543,34 @@ __device__ __forceinline__ void rows_phase_b(const RowsArgs &A, const R *sU, con
   }
 }
 
+// x at the band columns of rows a .. a+T-1 of a line (apply): sX[pr][c] =
+// x at column (a - P + c) in x1 and, across the line, at the fibre pr's offset
+// rows (r2 - P + j2 and, in 3D, r3 - P + j3; pr = j3 (2P+1) + j2); zero
+// outside the mesh; x null means x = 1.  XL = T_max + 2P columns per fibre.
+template <int P, int D, int XL, typename R>
+__device__ __forceinline__ void stage_x(const RowsArgs &A, const int line, const int a, const int T, R *sX) {
+  using O = typename OutT<R>::type;
+  constexpr int NB = 2 * P + 1, NPAIR = (D == 3) ? NB * NB : NB, NT = 32 * kRowsWarps;
+  const O *xg = static_cast<const O *>(A.x);
+  const int n1 = A.n[0], n2 = A.n[1], n3 = (D == 3) ? A.n[2] : 1;
+  const int r2 = (D == 3) ? line % n2 : line, r3 = (D == 3) ? line / n2 : 0;
+  for (int t = threadIdx.x; t < NPAIR * XL; t += NT) {
+    const int pr = t / XL, c = t - pr * XL;
+    const int c1 = a - P + c, c2 = r2 - P + pr % NB, c3 = (D == 3) ? r3 - P + pr / NB : 0;
+    R v = r_zero<R>();
+    if (c < T + 2 * P && c1 >= 0 && c1 < n1 && c2 >= 0 && c2 < n2 && c3 >= 0 && c3 < n3)
+      v = xg ? r_from_out<R>(xg[c1 + (long long)n1 * (c2 + (long long)n2 * c3)]) : r_from_double<R>(1.0);
+    sX[t] = v;
+  }
+}
+
 // The work of one CTA: chunk `bid` of the launch's line list (line
 // bid / nch, chunk bid % nch), in the dynamic shared memory `smem_raw`
 // (RowsLayout::BYTES).  Called by rows_kernel with bid = blockIdx.x and by
 // the persistent batch kernel once per work item.
-template <int P, int D, int LM, int TMAX, bool DO_M, bool DO_K, typename R>
+template <int P, int D, int LM, int TMAX, bool DO_M, bool DO_K, typename R, bool APPLY = false>
 __device__ __forceinline__ void rows_block(const RowsArgs &A, const int bid, unsigned char *smem_raw) {
-  using L = RowsLayout<P, D, LM, TMAX, DO_M, DO_K, R>;
+  using L = RowsLayout<P, D, LM, TMAX, DO_M, DO_K, R, APPLY>;
   using O = typename OutT<R>::type;
   static_assert(sizeof(O) == sizeof(R), "the band stage shares the R region");
   constexpr int NP = L::NP, NB = L::NB, NT = L::NT, NW = L::NW, LS = L::LS, NL = L::NL, NL1 = L::NL1;
@@ -558,6 +583,7 @@ __device__ __forceinline__ void rows_block(const RowsArgs &A, const int bid, uns
   R *sCb = sB1 + L::B1;                       // [l3][l2][l1]
   R *sU = sCb + L::CB;                        // [u][NL1][LS]
   R *sW = sU + L::US;                         // phase A: [warp][WS]; phase B: the row stage
+  R *sX = sW + L::SCRATCH;                    // apply: x at the chunk's band columns
   int *sE23 = reinterpret_cast<int *>(smem_raw + sizeof(R) * (size_t)L::R_TOTAL);  // [di][LM]
   int *sO23 = sE23 + 2 * LM;                  // [di][LM]
   int *sE1 = sO23 + 2 * LM;                   // [MAXPTS1]
@@ -782,15 +808,17 @@ __device__ __forceinline__ void rows_block(const RowsArgs &A, const int bid, uns
     }
     __syncwarp();
   }
+  if constexpr (APPLY) stage_x<P, D, TMAX + 2 * P>(A, line, a, T, sX);
   __syncthreads();
 
-  rows_phase_b<P, D, L::MAXPTS1, NL1, L::GENERAL, DO_M, DO_K, R>(A, sU, sV1, sB1, sE1, sOff1, sW, a, T, l1lo, base);
+  rows_phase_b<P, D, L::MAXPTS1, NL1, L::GENERAL, DO_M, DO_K, R, APPLY>(A, sU, sV1, sB1, sE1, sOff1, sW, a, T, l1lo,
+                                                                        base, sX);
 }
 
-template <int P, int D, int LM, int TMAX, bool DO_M, bool DO_K, typename R>
+template <int P, int D, int LM, int TMAX, bool DO_M, bool DO_K, typename R, bool APPLY = false>
 __global__ void __launch_bounds__(32 * kRowsWarps, rows_min_blocks<R>()) rows_kernel(const RowsArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  rows_block<P, D, LM, TMAX, DO_M, DO_K, R>(A, blockIdx.x, smem_raw);
+  rows_block<P, D, LM, TMAX, DO_M, DO_K, R, APPLY>(A, blockIdx.x, smem_raw);
 }
 
 }  // namespace wq

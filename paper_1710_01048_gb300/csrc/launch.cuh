@@ -75,6 +75,33 @@ cudaError_t launch_rows(int D, bool do_m, bool do_k, int cls, const RowsArgs &a,
   return launch_class<P, 3, false, true, R>(cls, a, nblocks, s);
 }
 
+// Matrix-free apply on 2D meshes: the fused row kernel in APPLY mode (M and,
+// if do_k, K), per line class.
+template <int P, int LM, int TMAX, bool DO_K, typename R>
+cudaError_t launch_apply_fused_one(const RowsArgs &a, int nblocks, cudaStream_t s) {
+  using L = RowsLayout<P, 2, LM, TMAX, true, DO_K, R, true>;
+  auto kern = rows_kernel<P, 2, LM, TMAX, true, DO_K, R, true>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (nblocks <= 0) return cudaSuccess;
+  kern<<<nblocks, L::NT, L::BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int P, typename R>
+cudaError_t launch_apply_2d(int cls, bool do_k, const RowsArgs &a, int nblocks, cudaStream_t s) {
+  constexpr int TI = interior_chunk(P, sizeof(R));
+  if (cls == 0)
+    return do_k ? launch_apply_fused_one<P, P + 1, TI, true, R>(a, nblocks, s)
+                : launch_apply_fused_one<P, P + 1, TI, false, R>(a, nblocks, s);
+  return do_k ? launch_apply_fused_one<P, P *(P + 1), kBoundaryChunk, true, R>(a, nblocks, s)
+              : launch_apply_fused_one<P, P *(P + 1), kBoundaryChunk, false, R>(a, nblocks, s);
+}
+
 template <int P, typename R>
 cudaError_t launch_adjoint(int D, int cls, const AdjArgs &a, int nblocks, cudaStream_t s) {
   if (D == 2) {
@@ -88,21 +115,27 @@ cudaError_t launch_adjoint(int D, int cls, const AdjArgs &a, int nblocks, cudaSt
 extern template cudaError_t launch_u<2, double>(const UArgs &, int, cudaStream_t);
 extern template cudaError_t launch_rows_ug<2, double>(bool, bool, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_apply_ug<2, double>(bool, const RowsArgs &, int, cudaStream_t);
+extern template cudaError_t launch_apply_2d<2, double>(int, bool, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_u<2, float>(const UArgs &, int, cudaStream_t);
 extern template cudaError_t launch_rows_ug<2, float>(bool, bool, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_apply_ug<2, float>(bool, const RowsArgs &, int, cudaStream_t);
+extern template cudaError_t launch_apply_2d<2, float>(int, bool, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_u<2, dd>(const UArgs &, int, cudaStream_t);
 extern template cudaError_t launch_rows_ug<2, dd>(bool, bool, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_apply_ug<2, dd>(bool, const RowsArgs &, int, cudaStream_t);
+extern template cudaError_t launch_apply_2d<2, dd>(int, bool, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_u<3, double>(const UArgs &, int, cudaStream_t);
 extern template cudaError_t launch_rows_ug<3, double>(bool, bool, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_apply_ug<3, double>(bool, const RowsArgs &, int, cudaStream_t);
+extern template cudaError_t launch_apply_2d<3, double>(int, bool, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_u<3, float>(const UArgs &, int, cudaStream_t);
 extern template cudaError_t launch_rows_ug<3, float>(bool, bool, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_apply_ug<3, float>(bool, const RowsArgs &, int, cudaStream_t);
+extern template cudaError_t launch_apply_2d<3, float>(int, bool, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_u<3, dd>(const UArgs &, int, cudaStream_t);
 extern template cudaError_t launch_rows_ug<3, dd>(bool, bool, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_apply_ug<3, dd>(bool, const RowsArgs &, int, cudaStream_t);
+extern template cudaError_t launch_apply_2d<3, dd>(int, bool, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_rows<2, double>(int, bool, bool, int, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_rows<3, double>(int, bool, bool, int, const RowsArgs &, int, cudaStream_t);
 extern template cudaError_t launch_rows<2, float>(int, bool, bool, int, const RowsArgs &, int, cudaStream_t);

@@ -7,4 +7,5 @@ template cudaError_t launch_adjoint<2, dd>(int, int, const AdjArgs &, int, cudaS
 template cudaError_t launch_u<2, dd>(const UArgs &, int, cudaStream_t);
 template cudaError_t launch_rows_ug<2, dd>(bool, bool, const RowsArgs &, int, cudaStream_t);
 template cudaError_t launch_apply_ug<2, dd>(bool, const RowsArgs &, int, cudaStream_t);
+template cudaError_t launch_apply_2d<2, dd>(int, bool, const RowsArgs &, int, cudaStream_t);
 }

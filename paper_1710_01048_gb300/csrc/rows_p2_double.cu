@@ -7,4 +7,5 @@ template cudaError_t launch_adjoint<2, double>(int, int, const AdjArgs &, int, c
 template cudaError_t launch_u<2, double>(const UArgs &, int, cudaStream_t);
 template cudaError_t launch_rows_ug<2, double>(bool, bool, const RowsArgs &, int, cudaStream_t);
 template cudaError_t launch_apply_ug<2, double>(bool, const RowsArgs &, int, cudaStream_t);
+template cudaError_t launch_apply_2d<2, double>(int, bool, const RowsArgs &, int, cudaStream_t);
 }

@@ -7,4 +7,5 @@ template cudaError_t launch_adjoint<2, float>(int, int, const AdjArgs &, int, cu
 template cudaError_t launch_u<2, float>(const UArgs &, int, cudaStream_t);
 template cudaError_t launch_rows_ug<2, float>(bool, bool, const RowsArgs &, int, cudaStream_t);
 template cudaError_t launch_apply_ug<2, float>(bool, const RowsArgs &, int, cudaStream_t);
+template cudaError_t launch_apply_2d<2, float>(int, bool, const RowsArgs &, int, cudaStream_t);
 }

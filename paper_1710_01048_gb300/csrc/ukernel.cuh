@@ -501,8 +501,7 @@ template <int P, bool DO_M, bool DO_K, typename R> struct ApplyLayoutUG {
 template <int P, bool DO_M, bool DO_K, typename R>
 __device__ __forceinline__ void apply_ug_block(const RowsArgs &A, int bid, unsigned char *smem_raw) {
   using L = ApplyLayoutUG<P, DO_M, DO_K, R>;
-  using O = typename OutT<R>::type;
-  constexpr int NB = L::NB, NPAIR = L::NPAIR, NL1 = L::NL1, XL = L::XL, NT = 32 * kRowsWarps;
+  constexpr int NPAIR = L::NPAIR, NL1 = L::NL1, XL = L::XL, NT = 32 * kRowsWarps;
   static_assert(NL1 + P - 3 == XL, "x row length seen by phase B");
   R *sV1 = reinterpret_cast<R *>(smem_raw);
   R *sB1 = sV1 + L::V1;
@@ -515,7 +514,7 @@ __device__ __forceinline__ void apply_ug_block(const RowsArgs &A, int bid, unsig
   const int tid = threadIdx.x;
   const int line = A.line0 + bid / A.nch;
   const int ch = bid % A.nch;
-  const int n1 = A.n[0], n2 = A.n[1], n3 = A.n[2];
+  const int n1 = A.n[0];
   const long long base = (long long)line * n1;
   long long lo = (long long)ch * A.T, hi = lo + A.T;
   if (hi > n1) hi = n1;
@@ -536,18 +535,7 @@ __device__ __forceinline__ void apply_ug_block(const RowsArgs &A, int bid, unsig
     R *dst = sU + u * NL1 * NPAIR;
     for (int i = tid; i < nl1 * NPAIR; i += NT) dst[i] = src[i];
   }
-  // x at the columns of the chunk's band: fibre (j3, j2) of line (r2, r3)
-  // reads row (r2 - P + j2, r3 - P + j3) of x, columns a - P .. b - 1 + P
-  const O *xg = static_cast<const O *>(A.x);
-  const int r2 = line % n2, r3 = line / n2;
-  for (int t = tid; t < NPAIR * XL; t += NT) {
-    const int pr = t / XL, c = t - pr * XL;
-    const int c1 = a - P + c, c2 = r2 - P + pr % NB, c3 = r3 - P + pr / NB;
-    R v = r_zero<R>();
-    if (c < T + 2 * P && c1 >= 0 && c1 < n1 && c2 >= 0 && c2 < n2 && c3 >= 0 && c3 < n3)
-      v = xg ? r_from_out<R>(xg[c1 + (long long)n1 * (c2 + (long long)n2 * c3)]) : r_from_double<R>(1.0);
-    sX[t] = v;
-  }
+  stage_x<P, 3, XL>(A, line, a, T, sX);
   __syncthreads();
   rows_phase_b<P, 3, L::MAXPTS1, NL1, false, DO_M, DO_K, R, true>(A, sU, sV1, sB1, sE1, sOff1, sP, a, T, l1lo,
                                                                     base, sX);

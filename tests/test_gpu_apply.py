@@ -4,8 +4,9 @@
 Parity: y = M x and y = K x against the band matvec of the oracle's bands
 (tests/bandops.py, pinned in test_oracle_apply.py), per row relative to
 sum |B| |x| over the row: <= 1e-12 for fp64 and df64, <= 1e-5 for mixed.
-Sizes span several apply chunks per line (16 rows) with ragged tails,
-interior and boundary lines, and tiny all-boundary meshes.  The load vector
+Sizes span several apply chunks per line (16 rows in 3D, the assembly's
+chunks in 2D) with ragged tails, interior and boundary lines, and tiny
+all-boundary meshes, in 3D (split kernels) and 2D (fused kernel).  The load vector
 for f = 1 on the identity map is pinned to its closed form directly.  At the
 benchmark size (64^3 cubic) the apply is compared with the band of the
 assembly on the GPU (itself parity-tested against the oracle) and K 1 = 0 is
@@ -51,6 +52,42 @@ def test_apply_matches_oracle_band_matvec(p, nel, prec):
     for y, B in ((yM, M), (yK, K)):
         e = row_errors(y.cpu().numpy(), band_matvec(B, cols, x), band_abs_matvec(B, cols, x))
         assert e.max() <= TOL[prec], f"{nel} {prec}: {e.max():.3e}"
+    R.close()
+
+
+MESHES_2D = [(3, (32, 32)), (2, (40, 9)), (3, (1, 1)), (2, (3, 50)), (3, (57, 2))]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64", "mixed"])
+@pytest.mark.parametrize("p,nel", MESHES_2D)
+def test_apply_2d_matches_oracle_band_matvec(p, nel, prec):
+    g, c = inputs.make(2, p, nel, 0.05, "exp", 0.1, seed=13)
+    R = wq.Rules(2, p, nel)
+    gd = [torch.from_numpy(v).cuda() for v in g]
+    cd = torch.from_numpy(c).cuda()
+    dt = torch.float32 if prec == "mixed" else torch.float64
+    x = np.random.default_rng(14).standard_normal(R.rows)
+    if prec == "mixed":
+        x = x.astype(np.float32).astype(np.float64)
+    yM, yK = wq.apply(R, gd, torch.from_numpy(x).to(dt).cuda(), cd, prec)
+    M, K, _ = oracle.assemble(2, p, nel, g, c)
+    cols = band_columns(2, p, nel)
+    for y, B in ((yM, M), (yK, K)):
+        e = row_errors(y.cpu().numpy(), band_matvec(B, cols, x), band_abs_matvec(B, cols, x))
+        assert e.max() <= TOL[prec], f"{nel} {prec}: {e.max():.3e}"
+    # row ranges and the load vector (f = 1 on the identity map: the basis integrals)
+    rb, re = 7, R.rows - 5
+    a, b = wq.apply(R, gd, torch.from_numpy(x).to(dt).cuda(), cd, prec, row_begin=rb, row_end=re)
+    assert torch.equal(a, yM[rb:re]) and torch.equal(b, yK[rb:re])
+    gi = [torch.from_numpy(v).cuda() for v in inputs.geometry(p, nel)]
+    bl = wq.assemble_load(R, gi, None, prec).cpu().numpy().astype(np.float64)
+    ints = []
+    for ne in nel:
+        t = np.concatenate([np.zeros(p), np.linspace(0.0, 1.0, ne + 1), np.ones(p)])
+        ints.append(np.array([(t[r + p + 1] - t[r]) / (p + 1) for r in range(ne + p)]))
+    expect = np.multiply.outer(ints[1], ints[0]).reshape(-1)
+    tol = {"fp64": 1e-14, "df64": 1e-13, "mixed": 1e-6}[prec]
+    assert np.max(np.abs(bl - expect)) <= tol * np.max(expect)
     R.close()
 
 
@@ -159,13 +196,7 @@ def test_apply_arguments():
     st = wq.wq_assemble_load(R.handle, gp, None, wq.WQ_FP64, None, 0, R.rows, ctypes.c_void_p(s))
     assert st == wq.WQ_ERR_ARG  # no output
     R.close()
-    # 2D, and the comparison rules: not supported by the apply kernels
-    R2 = wq.Rules(2, 3, (6, 5))
-    g2 = [torch.from_numpy(v).cuda() for v in inputs.geometry(3, (6, 5))]
-    with pytest.raises(wq.WqError) as ei:
-        wq.assemble_load(R2, g2)
-    assert ei.value.status == wq.WQ_ERR_UNSUPPORTED
-    R2.close()
+    # the comparison rules: not supported by the apply kernels
     Rg = wq.Rules(3, 2, (3, 3, 3), rule="gl")
     g3 = [torch.from_numpy(v).cuda() for v in inputs.geometry(2, (3, 3, 3))]
     with pytest.raises(wq.WqError) as ei:
