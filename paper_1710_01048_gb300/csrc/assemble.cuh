@@ -487,10 +487,20 @@ __device__ __forceinline__ void rows_phase_b(const RowsArgs &A, const R *sU, con
         const int rl = item / NPAIR, pr = item - rl * NPAIR;
         const R *xr = sX + pr * XL + rl;
         R pm = r_zero<R>(), pk = r_zero<R>();
+        if constexpr (std::is_same<R, dd>::value && DO_M && DO_K) {
+          // both sums as one packed pair, each lane dd_fma's bits
+          const unsigned long long z = f2_pack(A.zero, A.zero);
+          dd2 pmk{z, z};
 #pragma unroll
-        for (int j = 0; j < NB; j++) {
-          if constexpr (DO_M) pm = r_fma(oM[j], xr[j], pm);
-          if constexpr (DO_K) pk = r_fma(oK[j], xr[j], pk);
+          for (int j = 0; j < NB; j++) pmk = dd2_fma(dd2_pack(oM[j], oK[j]), dd2_pack(xr[j], xr[j]), pmk, z);
+          pm = dd2_first(pmk);
+          pk = dd2_second(pmk);
+        } else {
+#pragma unroll
+          for (int j = 0; j < NB; j++) {
+            if constexpr (DO_M) pm = r_fma(oM[j], xr[j], pm);
+            if constexpr (DO_K) pk = r_fma(oK[j], xr[j], pk);
+          }
         }
         sW[2 * item] = pm;
         sW[2 * item + 1] = pk;

@@ -477,7 +477,7 @@ cudaError_t launch_rows_ug(bool do_m, bool do_k, const RowsArgs &a, int nblocks,
 // at the chunk's columns in shared memory, then phase B in APPLY mode (the
 // band entries of a fibre meet x in registers; per-row sums by one warp).
 #ifndef WQ_APPLY_CHUNK
-#define WQ_APPLY_CHUNK 16
+#define WQ_APPLY_CHUNK 24
 #endif
 constexpr int kApplyChunk = WQ_APPLY_CHUNK;
 

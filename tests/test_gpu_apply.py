@@ -4,7 +4,7 @@
 Parity: y = M x and y = K x against the band matvec of the oracle's bands
 (tests/bandops.py, pinned in test_oracle_apply.py), per row relative to
 sum |B| |x| over the row: <= 1e-12 for fp64 and df64, <= 1e-5 for mixed.
-Sizes span several apply chunks per line (16 rows in 3D, the assembly's
+Sizes span several apply chunks per line (24 rows in 3D, the assembly's
 chunks in 2D) with ragged tails, interior and boundary lines, and tiny
 all-boundary meshes, in 3D (split kernels) and 2D (fused kernel).  The load vector
 for f = 1 on the identity map is pinned to its closed form directly.  At the
