@@ -144,10 +144,11 @@ void wq_rules_free(wq_rules *rules);
 
 /*
  * Host view of one row's 1D rule: direction dir (0-based, < dim), kind,
- * row index in [0, nel_dir + p).  *npts receives the point count; x, w
- * (each >= degree*(degree+1) doubles) receive the points and combined
- * weights W; elem (>= degree*(degree+1) ints) the element of each point.
- * Any output pointer may be NULL.
+ * row index in [0, nel_dir + p).  *npts receives the point count (at most
+ * degree*(degree+1) for the weighted rules, (degree+1)^2 with
+ * WQ_RULES_GAUSS_LEGENDRE); x, w receive the points and combined weights W,
+ * elem the element of each point, each with room for *npts values (call
+ * with NULL arrays first to learn it).  Any output pointer may be NULL.
  */
 wq_status wq_rules_row(const wq_rules *rules, int dir, int kind, int row, int *npts, double *x, double *w,
                        int *elem);
