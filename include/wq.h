@@ -136,6 +136,9 @@ wq_status wq_rule_1d_from(int degree, int kind, const double *start, double *tau
  * and fills the device copy (current device) used by the assembly calls;
  * WQ_RULES_HOST_ONLY builds host tables only (no CUDA call is made).
  * *out receives a new object to be released with wq_rules_free.
+ * WQ_ERR_OOM if the device allocation fails (also forced, before any CUDA
+ * call, when the environment variable WQ_FAULT_DEVICE_ALLOC is set: a hook
+ * for testing callers' error paths); nothing is leaked on any error.
  */
 wq_status wq_rules_build(const wq_mesh *mesh, int flags, wq_rules **out);
 

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -70,6 +71,8 @@ __global__ void coef_prepare_kernel(const double *__restrict__ c, size_t n, int 
 }
 
 wq_status upload(wq_rules *R) {
+  // fault injection for callers' error paths: the device allocation fails
+  if (std::getenv("WQ_FAULT_DEVICE_ALLOC")) return WQ_ERR_OOM;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return WQ_ERR_CUDA;
   int np = R->p + 1;

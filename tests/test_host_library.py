@@ -155,6 +155,27 @@ def test_argument_validation():
     R.close()
 
 
+def test_injected_device_allocation_failure(monkeypatch):
+    # the allocation-failure hook fails the device upload before any CUDA call
+    monkeypatch.setenv("WQ_FAULT_DEVICE_ALLOC", "1")
+    with pytest.raises(wq.WqError) as ei:
+        wq.Rules(3, 3, (4, 4, 4), device=True)
+    assert ei.value.status == wq.WQ_ERR_OOM
+    # host tables are unaffected
+    R = wq.Rules(3, 3, (4, 4, 4), device=False)
+    assert R.rows == 7 ** 3
+    R.close()
+
+
+def test_apply_and_load_reject_host_only_rules():
+    R = wq.Rules(3, 2, (3, 3, 3), device=False)
+    st = wq.wq_apply_mass_stiffness(R.handle, [1, 1, 1], None, wq.WQ_FP64, 1, 1, 1, 0, 1, None)
+    assert st == wq.WQ_ERR_ARG
+    st = wq.wq_assemble_load(R.handle, [1, 1, 1], None, wq.WQ_FP64, 1, 0, 1, None)
+    assert st == wq.WQ_ERR_ARG
+    R.close()
+
+
 def test_band_nnz_rows_matches_mask():
     # the closed-form CSR row pointer against the band mask's running sum
     rng = np.random.default_rng(0)
