@@ -363,6 +363,7 @@ wq_status prepare_rows(const wq_rules *R, const double *const *geom, const doubl
 
 wq_status assemble(const wq_rules *R, const double *const *geom, const double *coef, wq_precision prec, void *M,
                    void *K, int64_t rb, int64_t re, void *stream) {
+  wq::TraceRange trace("wq_assemble");
   wq_status st = check_call(R, geom, prec, rb, re);
   if (st != WQ_OK) return st;
   if (rb != re && !M && !K) return WQ_ERR_ARG;
@@ -398,6 +399,7 @@ wq_status assemble(const wq_rules *R, const double *const *geom, const double *c
 // y_M = M x, y_K = K x (x NULL: x = 1) through the split path's apply kernels.
 wq_status apply(const wq_rules *R, const double *const *geom, const double *coef, wq_precision prec,
                 const void *x, void *yM, void *yK, int64_t rb, int64_t re, void *stream) {
+  wq::TraceRange trace("wq_apply");
   wq_status st = check_call(R, geom, prec, rb, re);
   if (st != WQ_OK) return st;
   if (R->mode != wq::kModeWQ || (R->dim == 3 && !R->dev_U)) return WQ_ERR_UNSUPPORTED;
@@ -466,6 +468,7 @@ wq_status wq_rule_1d_from(int degree, int kind, const double *start, double *tau
 }
 
 wq_status wq_rules_build(const wq_mesh *mesh, int flags, wq_rules **out) {
+  wq::TraceRange trace("wq_rules_build");
   if (!mesh || !out) return WQ_ERR_ARG;
   *out = nullptr;
   if (mesh->dim < 2 || mesh->dim > 3 || mesh->degree < 2 || mesh->degree > wq::kMaxP) return WQ_ERR_UNSUPPORTED;
@@ -598,6 +601,7 @@ wq_status wq_assemble_load(const wq_rules *rules, const double *const *geom, con
 
 wq_status wq_assemble_adjoint(const wq_rules *R, const double *const *geom, wq_precision prec, const void *G,
                               const void *H, double *grad, int64_t row_begin, int64_t row_end, void *stream) {
+  wq::TraceRange trace("wq_assemble_adjoint");
   if (!R || !geom || !grad) return WQ_ERR_ARG;
   if (!R->on_device) return WQ_ERR_ARG;
   if (R->mode != wq::kModeWQ) return WQ_ERR_UNSUPPORTED;

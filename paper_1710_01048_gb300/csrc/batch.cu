@@ -375,6 +375,7 @@ void wq_batch_free(wq_batch *batch) {
 }
 
 wq_status wq_batch_launch(wq_batch *B, void *stream) {
+  wq::TraceRange trace("wq_batch_launch");
   if (!B || !B->exec) return WQ_ERR_ARG;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != B->device) return WQ_ERR_ARG;

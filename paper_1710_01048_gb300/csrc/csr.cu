@@ -137,6 +137,7 @@ int64_t wq_band_nnz_rows(const wq_rules *R, int64_t row_begin, int64_t row_end) 
 
 wq_status wq_band_to_csr(const wq_rules *R, wq_precision prec, const void *band, int64_t row_begin, int64_t row_end,
                          int64_t *rowptr, int32_t *col, void *val, void *stream) {
+  wq::TraceRange trace("wq_band_to_csr");
   if (!R || !R->on_device) return WQ_ERR_ARG;
   if (prec != WQ_FP64 && prec != WQ_MIXED && prec != WQ_DF64) return WQ_ERR_ARG;
   const int64_t rows = (int64_t)R->n[0] * R->n[1] * R->n[2];

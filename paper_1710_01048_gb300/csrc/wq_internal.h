@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <vector>
@@ -9,6 +10,15 @@
 #include "../../include/wq.h"
 
 namespace wq {
+
+// A named NVTX range around one entry point's host work and launches (for
+// profilers that filter by range; a no-op when no tool is attached).
+struct TraceRange {
+  explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange &) = delete;
+  TraceRange &operator=(const TraceRange &) = delete;
+};
 
 constexpr int kMaxP = 3;
 constexpr int kMaxDim = 3;
