@@ -79,3 +79,62 @@ def test_plane_ranges_more_ranks_than_planes():
     assert sum(b - a for a, b in ranges) == 48
     assert all(a % 16 == 0 and b % 16 == 0 for a, b in ranges)
     assert sum(1 for a, b in ranges if a == b) == 2
+
+
+def _adjoint_rank_main(rank, world, port, p, nel, q):
+    # each rank: the oracle's gradient of its own rows' weights (the partial
+    # gradient a sharded adjoint computes), then the halo reduction
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import numpy as np
+
+        import oracle
+        from paper_1710_01048_gb300 import inputs
+
+        g, c = inputs.make(3, p, nel, 0.05, "exp", 0.1, seed=41)
+        rows = int(np.prod([v + p for v in nel]))
+        band = (2 * p + 1) ** 3
+        rng = np.random.default_rng(42)
+        G = rng.standard_normal((rows, band))
+        H = rng.standard_normal((rows, band))
+        rb, re = shard.shard_rows([v + p for v in nel], rank, world)
+        mask = np.zeros((rows, 1))
+        mask[rb:re] = 1.0
+        part = torch.from_numpy(oracle.gradient(3, p, nel, g, G * mask, H * mask))
+        lo, hi = shard.halo_reduce_gradient(part, nel, p, rank, world, dist)
+        layer = (nel[0] + 3) * (nel[1] + 3)
+        owned = part[lo * layer:hi * layer].numpy().copy()
+        pieces = [None] * world
+        dist.all_gather_object(pieces, (lo, hi, owned))
+        if rank == 0:
+            full = oracle.gradient(3, p, nel, g, G, H)
+            q.put(dict(pieces=pieces, full=full, layer=layer, ncl=nel[2] + 3))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,p,nel", [(2, 3, (4, 3, 6)), (3, 2, (3, 4, 5)), (3, 3, (3, 2, 2))])
+def test_sharded_adjoint_halo_reduction(world, p, nel):
+    # the owned coefficient layers of the halo-reduced partial gradients tile
+    # the layers and equal the gradient of the whole mesh
+    import numpy as np
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_adjoint_rank_main, args=(r, world, port, p, nel, q)) for r in range(world)]
+    for pr in procs:
+        pr.start()
+    res = q.get(timeout=300)
+    for pr in procs:
+        pr.join(timeout=300)
+        assert pr.exitcode == 0
+    layer, full = res["layer"], res["full"]
+    covered = []
+    for lo, hi, owned in res["pieces"]:
+        covered.extend(range(lo, hi))
+        ref = full[lo * layer:hi * layer]
+        assert np.max(np.abs(owned - ref)) <= 1e-12 * np.max(np.abs(full))
+    assert sorted(covered) == list(range(res["ncl"]))
