@@ -2,25 +2,28 @@
 
 One step = one mass+stiffness assembly call (coefficient check, geometry
 fold, the partial-contraction kernel and the row kernel, all rows) of the
-named synthetic workload through the C-ABI.  Default workload: 64^3 elements, C2 cubic (p = 3), separable map
-xhat + 0.05 sin(pi xhat) per coordinate, c = exp(0.3 (x+y+z)) with
-lognormal(0.1) noise as a cubic spline on the same mesh, FP64-accurate bands
-(double output, <= 1e-12 relative to the FP64 oracle) computed in
-double-float arithmetic on the FP32 pipe (--prec df64).  Timed beside it
-("variants"): the plain FP64 form, the FP32 mixed mode, the comparison rules
-(Gauss-Legendre rows, Newton-Cotes-type rule; FP64) with their quadrature
-point totals, the 128^3 cubic workload in every precision, the adjoint on
-the 96^3 cubic workload and the 256-patch batch.
+named synthetic workload through the C-ABI.  Default workload: 128^3
+elements, C2 cubic (p = 3), separable map xhat + 0.05 sin(pi xhat) per
+coordinate, c = exp(0.3 (x+y+z)) with lognormal(0.1) noise as a cubic spline
+on the same mesh, FP64 arithmetic and FP64 bands (--prec fp64).  Beside it
+("variants"): the same workload in double-float (FP64-accurate on the FP32
+pipe) and FP32 (mixed) arithmetic, each with its error against the oracle;
+the 64^3 cubic and quadratic workloads and the 2D 32^2 cubic one in every
+precision; the comparison rules (Gauss-Legendre rows, Newton-Cotes-type
+rule; FP64) with their quadrature point totals; the adjoint on the 96^3
+cubic workload; the matrix-free apply; the 256-patch batch.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload 3d_p3_64] [--prec df64|fp64|mixed] [--no-cpu-baseline]
+                    [--workload 3d_p3_128] [--prec fp64|df64|mixed] [--no-cpu-baseline]
 
 Prints one JSON line.  value = assembled non-zeros (M and K) per second over
 all ranks, device time (CUDA events around each step on the launching
 stream, L2 flushed before each step by writing a 256 MiB buffer); e2e = the
-same through host buffers (pinned H2D of geometry and coefficients, D2H of
-both bands, inside the timed region).  Under torchrun every rank assembles
-its own copy of the workload (weak scaling, no data-path collective).
+same through host buffers (wq_assemble_mass_stiffness_host: pinned H2D of
+geometry and coefficients, D2H of both bands, inside the timed region).
+Under torchrun the mesh grows along x3 with the rank count (128 x 128 x
+128 N elements) and each rank assembles its own slab of x3 planes (weak
+scaling, no data-path collective).
 """
 from __future__ import annotations
 
@@ -37,16 +40,21 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "3D cubic WQ mass+stiffness assembled nnz/s"
-# peaks
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz = 1.259
+DTYPE = {"fp64": "f64", "df64": "f32x2", "mixed": "f32"}
+# peaks of the ALU-bound forms (none is in MEASURED_PEAKS.json, which holds
+# the HBM copy rate and dense bf16 tensor rates):
+# FP64: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz = 1.259 TFLOP/s (the
+# nominal FP64 rate of the part, 1.25 TFLOP/s)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 80.5
 # double-float multiply-add = 12 FP32-pipe instructions (csrc/dd.cuh): FP64-equivalent peak
 DF64_PEAK_TFLOPS = 152 * 128 / 12 * 2 * 2.070e9 / 1e12  # 6.71
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
-# capture of the current kernel (profiles/split_kernels_3d_p3_64_df64.md);
-# absent entries report null
-TRAFFIC = {("3d_p3_64", "df64"): {"bytes": 1.590632e9 + 0.236710e9, "kernel": "rows_ug_kernel<3, 32, M+K, dd>",
-                                  "algorithmic_bytes": 2 * 300763 * 343 * 8}}
+# capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum);
+# entries without a capture of the current kernel are absent and report null.
+# "scale": the captured case's rows, when the capture was made on a smaller
+# mesh of the same kernel and its traffic is scaled to the workload's rows.
+TRAFFIC = {}
 
 
 def measured_peaks():
@@ -115,45 +123,67 @@ def band_nnz_rows(nel, p, rows_idx):
     """Number of in-range band entries of the given rows (one matrix)."""
     import numpy as np
 
+    dim = len(nel)
     n = [v + p for v in nel]
-    r1 = rows_idx % n[0]
-    r2 = (rows_idx // n[0]) % n[1]
-    r3 = rows_idx // (n[0] * n[1])
     cnt = np.ones_like(rows_idx)
-    for r, m in ((r1, n[0]), (r2, n[1]), (r3, n[2])):
-        cnt = cnt * (np.minimum(m - 1, r + p) - np.maximum(0, r - p) + 1)
+    rest = rows_idx
+    for a in range(dim):
+        r = rest % n[a]
+        rest = rest // n[a]
+        cnt = cnt * (np.minimum(n[a] - 1, r + p) - np.maximum(0, r - p) + 1)
     return int(cnt.sum())
 
 
 def cpu_sample_rows(nel, p, stride):
-    """Every `stride`-th x3-slab of rows (interior and boundary rows alike)."""
+    """Every `stride`-th slab of rows along the last direction (interior and
+    boundary rows alike)."""
     n = [v + p for v in nel]
-    slab = n[0] * n[1]
-    return [(s * slab, (s + 1) * slab) for s in range(0, n[2], stride)]
+    slab = 1
+    for v in n[:-1]:
+        slab *= v
+    return [(s * slab, (s + 1) * slab) for s in range(0, n[-1], stride)]
 
 
-def run_cpu_baseline(w, g, c, stride, max_slabs=None):
-    """Times the FP64 oracle on a sample of slabs with all host cores."""
+def run_oracle_sample(w, g, c, stride):
+    """The FP64 oracle on a sample of slabs with all host cores: (seconds,
+    in-range non-zeros of M and K, the sample's rows, [(rb, re, M, K)])."""
     import numpy as np
 
     import oracle
 
-    nel, p = w["nel"], w["p"]
+    nel, p, dim = w["nel"], w["p"], w["dim"]
     ranges = cpu_sample_rows(nel, p, stride)
-    if max_slabs:
-        ranges = ranges[:max_slabs]
     nnz = 0
-    t0 = time.perf_counter()
     outs = []
+    t0 = time.perf_counter()
     for rb, re in ranges:
-        M, K, _ = oracle.assemble(3, p, nel, g, c, rb, re)
+        M, K, _ = oracle.assemble(dim, p, nel, g, c, rb, re)
         outs.append((rb, re, M, K))
-        nnz += 2 * band_nnz_rows(nel, p, np.arange(rb, re))
     dt = time.perf_counter() - t0
+    for rb, re in ranges:
+        nnz += 2 * band_nnz_rows(nel, p, np.arange(rb, re))
     rows = sum(re - rb for rb, re in ranges)
-    return {"value": nnz / dt, "unit": "nnz/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{len(ranges)} x3-slabs (every {stride}th, {rows} rows of {int(np.prod([v + p for v in nel]))}), "
-                      f"{dt:.1f} s wall"}, outs
+    return dt, nnz, rows, outs
+
+
+def errors_vs_oracle(bands, outs):
+    """Per-matrix relative max-entry and Frobenius errors of device bands on
+    the oracle's sampled rows (bands: (M, K) torch tensors of all rows)."""
+    import numpy as np
+
+    res = {}
+    for name, A, k in (("M", bands[0], 2), ("K", bands[1], 3)):
+        dmax = omax = dsq = osq = 0.0
+        for o in outs:
+            rb, re, O = o[0], o[1], o[k]
+            d = A[rb:re].double().cpu().numpy() - O
+            dmax = max(dmax, float(np.max(np.abs(d))))
+            omax = max(omax, float(np.max(np.abs(O))))
+            dsq += float(np.sum(d * d))
+            osq += float(np.sum(O * O))
+        res[name] = {"rel_max": dmax / omax, "rel_fro": (dsq / osq) ** 0.5}
+    res["max"] = max(res["M"]["rel_max"], res["K"]["rel_max"], res["M"]["rel_fro"], res["K"]["rel_fro"])
+    return res
 
 
 def reference_arm(args):
@@ -166,31 +196,32 @@ def reference_arm(args):
     if rank != 0:
         return 0
     w, g, c = inputs.workload(args.workload)
-    nel, p = w["nel"], w["p"]
-    n = [v + p for v in nel]
-    slab = n[0] * n[1]
-    # each step: one x3-slab of rows (a bounded sample of the workload)
+    nel, p, dim = w["nel"], w["p"], w["dim"]
+    ranges = cpu_sample_rows(nel, p, 1)
+    # each step: one slab of rows along the last direction (a bounded sample of the workload)
     import oracle
 
     oracle.build()
     for i in range(args.warmup):
-        oracle.assemble(3, p, nel, g, c, slab * (i % n[2]), slab * (i % n[2] + 1))
+        rb, re = ranges[i % len(ranges)]
+        oracle.assemble(dim, p, nel, g, c, rb, re)
     t = []
     nnz = 0
     for i in range(args.steps):
-        s = (n[2] // 2 + i) % n[2]
+        rb, re = ranges[(len(ranges) // 2 + i) % len(ranges)]
         t0 = time.perf_counter()
-        oracle.assemble(3, p, nel, g, c, slab * s, slab * (s + 1))
+        oracle.assemble(dim, p, nel, g, c, rb, re)
         t.append(time.perf_counter() - t0)
-        nnz += 2 * band_nnz_rows(nel, p, np.arange(slab * s, slab * (s + 1)))
+        nnz += 2 * band_nnz_rows(nel, p, np.arange(rb, re))
     total = sum(t)
     value = nnz / total
+    slab = ranges[0][1] - ranges[0][0]
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": args.workload, "nel": list(nel), "degree": p, "precision": "fp64"},
            "cpu_baseline": {"value": value, "unit": "nnz/s", "cores": os.cpu_count(), "kind": "oracle",
-                            "sample": f"one x3-slab ({slab} rows) per step"},
+                            "sample": f"one slab of {slab} rows along the last direction per step"},
            "e2e": {"value": value, "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return 0
@@ -202,13 +233,13 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="3d_p3_64")
-    ap.add_argument("--prec", default="df64", choices=["fp64", "df64", "mixed"])
+    ap.add_argument("--workload", default="3d_p3_128")
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "df64", "mixed"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-128", action="store_true", help="skip the 128^3 and adjoint variants")
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-patch batch variant")
-    ap.add_argument("--cpu-stride", type=int, default=8)
+    ap.add_argument("--cpu-stride", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -219,7 +250,7 @@ def main():
     import torch
 
     from paper_1710_01048_gb300 import binding as wq
-    from paper_1710_01048_gb300 import inputs
+    from paper_1710_01048_gb300 import inputs, shard
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -236,21 +267,45 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    w, g, c = inputs.workload(args.workload)
-    dim, p, nel = w["dim"], w["p"], w["nel"]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+
+    def timed(fn, n, do_flush=True):
+        """Mean device time (ms) of n calls of fn, CUDA events on the stream."""
+        evs = []
+        for _ in range(n):
+            if do_flush:
+                flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in evs]
+
+    # ------------------------------------------------------------ the workload (this rank's slab)
+    w = dict(inputs.WORKLOADS[args.workload])
+    dim, p = w["dim"], w["p"]
+    nel = list(w["nel"])
+    nel[-1] *= world  # weak scaling: the mesh grows along the last direction
+    nel = tuple(nel)
+    g, c = inputs.make(dim, p, nel, w["amp"], w["coef"], w["sigma"], w["seed"])
     R = wq.Rules(dim, p, nel)
-    rows, band = R.rows, R.band
-    nnz_step = 2 * R.nnz  # M and K
+    rb, re = shard.shard_rows([v + p for v in nel], rank, world)
+    rows, band = re - rb, R.band
+    nnz_rank = wq.wq_band_nnz_rows(R.handle, rb, re)
+    nnz_step = 2 * nnz_rank  # M and K
     gd = [torch.from_numpy(x).cuda() for x in g]
     cd = torch.from_numpy(c).cuda()
     dt = torch.float32 if args.prec == "mixed" else torch.float64
     M = torch.empty((rows, band), dtype=dt, device="cuda")
     K = torch.empty((rows, band), dtype=dt, device="cuda")
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    stream = torch.cuda.current_stream()
 
     def step():
-        wq.assemble(R, gd, cd, args.prec, out=(M, K), stream=stream, check=False)
+        wq.assemble(R, gd, cd, args.prec, out=(M, K), row_begin=rb, row_end=re, stream=stream, check=False)
 
     for _ in range(args.warmup):
         step()
@@ -262,354 +317,334 @@ def main():
     sampler.start()
     time.sleep(0.3)
     barrier()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for e0, e1 in evs:
-        flush.fill_(1)
-        e0.record(stream)
-        step()
-        e1.record(stream)
+    ms = timed(step, args.steps)
     barrier()
     clocks = sampler.stop()
-    ms = [e0.elapsed_time(e1) for e0, e1 in evs]
     ms_step = float(np.mean(ms))
     st = wq.wq_status_check(R.handle, wq._stream_handle(stream))
     if st != wq.WQ_OK:
         raise wq.WqError(st, "timed steps")
-    # coefficient check/convert + fold + interior-line rows + boundary-line rows per step
+    # coefficient check/convert + fold + partial contractions + rows per step
     gpu_launches = 4 * args.steps
 
-    # end to end through host buffers: pinned inputs H2D, both bands D2H
-    # (measured before the variants, whose large allocations would otherwise
-    # precede it)
-    gh = [torch.from_numpy(x).pin_memory() for x in g]
-    ch = torch.from_numpy(c).pin_memory()
-    Mh = torch.empty((rows, band), dtype=dt).pin_memory()
-    Kh = torch.empty((rows, band), dtype=dt).pin_memory()
-    h2d = sum(x.numel() * 8 for x in gh) + ch.numel() * 8
-    d2h = 2 * rows * band * M.element_size()
-    e2e_steps = max(3, min(args.steps, 10))
+    # the oracle's sampled rows (rank 0 at N = 1): CPU baseline and the
+    # accuracy of every precision on those rows
+    sample = None
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        secs, snnz, srows, outs = run_oracle_sample(w, g, c, args.cpu_stride)
+        sample = outs
+        cpu = {"value": snnz / secs, "unit": "nnz/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{len(outs)} slabs of rows along x3 (every {args.cpu_stride}th; {srows} of {R.rows} "
+                         f"rows, {snnz} non-zeros of M and K), {secs:.1f} s wall; the rate is the sample's"}
+    accuracy = errors_vs_oracle((M, K), sample) if sample else None
 
-    def e2e_step():
-        # inputs to the device, then the assembly with its band copies to the
-        # host overlapped range by range (binding.assemble_to_host)
-        for dst, src in zip(gd, gh):
-            dst.copy_(src, non_blocking=True)
-        cd.copy_(ch, non_blocking=True)
-        wq.assemble_to_host(R, gd, cd, args.prec, Mh, Kh, M, K, nchunks=8, stream=stream)
+    # ------------------------------------------------------------ end to end through host buffers
+    e2e = None
+    if not args.no_e2e:
+        gh = [torch.from_numpy(x).pin_memory() for x in g]
+        ch = torch.from_numpy(c).pin_memory()
+        Mh = torch.empty((rows, band), dtype=dt, pin_memory=True)
+        Kh = torch.empty((rows, band), dtype=dt, pin_memory=True)
+        gdd = [torch.empty_like(x) for x in gd]
+        cdd = torch.empty_like(cd)
+        h2d = sum(x.numel() * 8 for x in gh) + ch.numel() * 8
+        d2h = 2 * rows * band * M.element_size()
+        e2e_steps = max(3, min(args.steps, 10))
 
-    e2e_step()
-    barrier()
-    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0e.record(stream)
-    for _ in range(e2e_steps):
+        def e2e_step():
+            wq.assemble_to_host(R, gh, ch, args.prec, Mh, Kh, gdd, cdd, M, K, nchunks=8, stream=stream,
+                                row_begin=rb, row_end=re)
+
         e2e_step()
-    t1e.record(stream)
-    barrier()
-    e2e_ms = t0e.elapsed_time(t1e) / e2e_steps
-
-    # the other precisions on the same workload, a few steps each
-    variants = {}
-    peaks = measured_peaks()
-    if not args.no_variants:
-        for vp in ("fp64", "df64", "mixed"):
-            if vp == args.prec:
-                continue
-            vdt = torch.float32 if vp == "mixed" else torch.float64
-            Mv = torch.empty((rows, band), dtype=vdt, device="cuda")
-            Kv = torch.empty((rows, band), dtype=vdt, device="cuda")
-            for _ in range(3):
-                wq.assemble(R, gd, cd, vp, out=(Mv, Kv), stream=stream, check=False)
-            vms = []
-            for _ in range(max(3, min(args.steps, 10))):
-                flush.fill_(1)
-                v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                v0.record(stream)
-                wq.assemble(R, gd, cd, vp, out=(Mv, Kv), stream=stream, check=False)
-                v1.record(stream)
-                vms.append((v0, v1))
-            torch.cuda.synchronize()
-            vm = float(np.mean([x.elapsed_time(y) for x, y in vms]))
-            ev = {"ms_per_step": vm, "value": world * nnz_step / (vm * 1e-3), "unit": "nnz/s",
-                  "dtype": {"fp64": "f64", "df64": "f32x2", "mixed": "f32"}[vp]}
-            if vp == "mixed":
-                # accuracy of the FP32 bands against this run's FP64-accurate bands
-                ev["max_rel_err_vs_fp64_bands"] = max(
-                    float(((Mv.double() - M.double()).abs().max() / M.double().abs().max()).item()),
-                    float(((Kv.double() - K.double()).abs().max() / K.double().abs().max()).item()))
-            variants[vp] = ev
-            del Mv, Kv
-        torch.cuda.empty_cache()
-
-        # the comparison rules (FP64, same kernel's general-points class):
-        # Gauss-Legendre on every element of each row's support, and the
-        # Newton-Cotes-type weighted rules; with the quadrature-point counts
-        Mv = torch.empty((rows, band), dtype=torch.float64, device="cuda")
-        Kv = torch.empty((rows, band), dtype=torch.float64, device="cuda")
-        points = {}
-        for mode in ("wq", "nc", "gl"):
-            Rm = R if mode == "wq" else wq.Rules(dim, p, nel, rule=mode)
-            total = 1
-            for a in range(dim):
-                total *= sum(len(Rm.row(a, 0, r)[0]) for r in range(nel[a] + p))
-            points[mode] = {"points_per_interior_row_and_direction": len(Rm.row(0, 0, p)[0]),
-                            "rule_points_total": total}
-            if mode == "wq":
-                continue
-            for _ in range(3):
-                wq.assemble(Rm, gd, cd, "fp64", out=(Mv, Kv), stream=stream, check=False)
-            vms = []
-            for _ in range(max(3, min(args.steps, 5))):
-                flush.fill_(1)
-                v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                v0.record(stream)
-                wq.assemble(Rm, gd, cd, "fp64", out=(Mv, Kv), stream=stream, check=False)
-                v1.record(stream)
-                vms.append((v0, v1))
-            torch.cuda.synchronize()
-            vm = float(np.mean([x.elapsed_time(y) for x, y in vms]))
-            variants["fp64_" + mode + "_rule"] = {"ms_per_step": vm, "value": world * nnz_step / (vm * 1e-3),
-                                                  "unit": "nnz/s", "dtype": "f64", **points[mode]}
-            Rm.close()
-        variants["rule_points"] = points
-        del Mv, Kv
-        torch.cuda.empty_cache()
-
-        # the 128^3 cubic workload (the precision configuration), every precision
-        if args.workload == "3d_p3_64" and not args.no_128:
-            w2, g2, c2 = inputs.workload("3d_p3_128")
-            R2 = wq.Rules(3, w2["p"], w2["nel"])
-            gd2 = [torch.from_numpy(x).cuda() for x in g2]
-            cd2 = torch.from_numpy(c2).cuda()
-            fl2, _ = R2.flops()
-            big = {"workload": "3d_p3_128", "nel": list(w2["nel"]), "nnz_per_matrix": R2.nnz}
-            for vp in ("df64", "fp64", "mixed"):
-                vdt = torch.float32 if vp == "mixed" else torch.float64
-                Mv = torch.empty((R2.rows, R2.band), dtype=vdt, device="cuda")
-                Kv = torch.empty((R2.rows, R2.band), dtype=vdt, device="cuda")
-                for _ in range(3):
-                    wq.assemble(R2, gd2, cd2, vp, out=(Mv, Kv), stream=stream, check=False)
-                vms = []
-                for _ in range(max(3, min(args.steps, 5))):
-                    v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    v0.record(stream)
-                    wq.assemble(R2, gd2, cd2, vp, out=(Mv, Kv), stream=stream, check=False)
-                    v1.record(stream)
-                    vms.append((v0, v1))
-                torch.cuda.synchronize()
-                vm = float(np.mean([x.elapsed_time(y) for x, y in vms]))
-                ent = {"ms_per_step": vm, "value": world * 2 * R2.nnz / (vm * 1e-3), "unit": "nnz/s"}
-                if vp == "mixed":
-                    bw = 2 * R2.rows * R2.band * 4 / (vm * 1e-3) / 1e9
-                    ent["roofline"] = {"bound": "hbm", "achieved": bw, "peak": peaks.get("hbm_gbs", 6800.0),
-                                       "unit": "GB/s", "frac": bw / peaks.get("hbm_gbs", 6800.0)}
-                else:
-                    pk = FP64_PEAK_TFLOPS if vp == "fp64" else DF64_PEAK_TFLOPS
-                    tf = fl2 / (vm * 1e-3) / 1e12
-                    ent["roofline"] = {"bound": "alu", "achieved": tf, "peak": pk, "unit": "TFLOP/s", "frac": tf / pk}
-                big[vp] = ent
-                del Mv, Kv
-                torch.cuda.empty_cache()
-            st2 = wq.wq_status_check(R2.handle, wq._stream_handle(stream))
-            if st2 != wq.WQ_OK:
-                raise wq.WqError(st2, "128^3 variant")
-            variants["3d_p3_128"] = big
-            R2.close()
-            del gd2, cd2
-
-        # the adjoint (coefficient gradient of sum G*K + H*M) on the 96^3 cubic workload
-        if args.workload == "3d_p3_64" and not args.no_128:
-            w3, g3, c3 = inputs.workload("3d_p3_96")
-            R3 = wq.Rules(3, w3["p"], w3["nel"])
-            gd3 = [torch.from_numpy(x).cuda() for x in g3]
-            gen = torch.Generator(device="cuda").manual_seed(96)
-            adj = {"workload": "3d_p3_96", "ncoef": R3.ncoef}
-            for vp in ("fp64", "df64", "mixed"):
-                vdt = torch.float32 if vp == "mixed" else torch.float64
-                G = torch.randn((R3.rows, R3.band), dtype=vdt, device="cuda", generator=gen)
-                H = torch.randn((R3.rows, R3.band), dtype=vdt, device="cuda", generator=gen)
-                grad = torch.empty(R3.ncoef, dtype=torch.float64, device="cuda")
-                for _ in range(3):
-                    wq.assemble_adjoint(R3, gd3, G, H, vp, out=grad, stream=stream, check=False)
-                vms = []
-                for _ in range(max(3, min(args.steps, 5))):
-                    v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    v0.record(stream)
-                    wq.assemble_adjoint(R3, gd3, G, H, vp, out=grad, stream=stream, check=False)
-                    v1.record(stream)
-                    vms.append((v0, v1))
-                torch.cuda.synchronize()
-                vm = float(np.mean([x.elapsed_time(y) for x, y in vms]))
-                # per step the adjoint reads both weight bands: report band entries per second
-                adj[vp] = {"ms_per_step": vm, "value": 2 * R3.nnz / (vm * 1e-3), "unit": "nnz/s (weights read)",
-                           "weights_gb_s": 2 * R3.rows * R3.band * G.element_size() / (vm * 1e-3) / 1e9}
-                del G, H, grad
-                torch.cuda.empty_cache()
-            variants["adjoint_3d_p3_96"] = adj
-            R3.close()
-
-        # matrix-free apply y = M x, y = K x (the band never stored) and the
-        # load vector, on the same workload as the headline
-        if args.workload == "3d_p3_64":
-            gen = torch.Generator(device="cuda").manual_seed(64)
-            app = {"workload": args.workload, "nnz_per_step": nnz_step}
-            for vp in ("df64", "fp64", "mixed"):
-                vdt = torch.float32 if vp == "mixed" else torch.float64
-                xv = torch.randn(rows, dtype=torch.float64, device="cuda", generator=gen).to(vdt)
-                yM = torch.empty(rows, dtype=vdt, device="cuda")
-                yK = torch.empty(rows, dtype=vdt, device="cuda")
-                for _ in range(3):
-                    wq.apply(R, gd, xv, cd, vp, out=(yM, yK), stream=stream, check=False)
-                vms = []
-                for _ in range(max(3, min(args.steps, 10))):
-                    flush.fill_(1)
-                    v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    v0.record(stream)
-                    wq.apply(R, gd, xv, cd, vp, out=(yM, yK), stream=stream, check=False)
-                    v1.record(stream)
-                    vms.append((v0, v1))
-                torch.cuda.synchronize()
-                vm = float(np.mean([x.elapsed_time(y) for x, y in vms]))
-                # the contractions plus one multiply-add per band entry and matrix
-                fl_apply = R.flops()[0] + 2 * 2 * R.nnz
-                pk = {"fp64": FP64_PEAK_TFLOPS, "df64": DF64_PEAK_TFLOPS, "mixed": FP32_PEAK_TFLOPS}[vp]
-                tf = fl_apply / (vm * 1e-3) / 1e12
-                app[vp] = {"ms_per_step": vm, "value": world * nnz_step / (vm * 1e-3), "unit": "nnz/s (applied)",
-                           "roofline": {"bound": "alu", "achieved": tf, "peak": pk, "unit": "TFLOP/s",
-                                        "frac": tf / pk}}
-                if vp == "df64":
-                    bl = torch.empty(rows, dtype=vdt, device="cuda")
-                    for _ in range(3):
-                        wq.assemble_load(R, gd, cd, vp, out=bl, stream=stream, check=False)
-                    v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    v0.record(stream)
-                    for _ in range(5):
-                        wq.assemble_load(R, gd, cd, vp, out=bl, stream=stream, check=False)
-                    v1.record(stream)
-                    torch.cuda.synchronize()
-                    app["load_vector_df64_ms"] = v0.elapsed_time(v1) / 5
-                    del bl
-                del xv, yM, yK
-            sta = wq.wq_status_check(R.handle, wq._stream_handle(stream))
-            if sta != wq.WQ_OK:
-                raise wq.WqError(sta, "apply variant")
-            variants["apply_3d_p3_64"] = app
-
-        # the batch of 256 independent patches (8..48 elements per direction, p in {2, 3}):
-        # one graph of two persistent launches, tuned, against one call per patch
-        if not args.no_batch:
-            specs = inputs.batch_patches(256, seed=0)
-            rules_cache, base = {}, []
-            for sp in specs:
-                key = (sp["p"], sp["nel"])
-                if key not in rules_cache:
-                    rules_cache[key] = wq.Rules(3, sp["p"], sp["nel"])
-                base.append((rules_cache[key], [torch.from_numpy(x).cuda() for x in sp["geom"]],
-                             torch.from_numpy(sp["coef"]).cuda()))
-            bnnz = 2 * sum(Rb.nnz for Rb, _, _ in base)
-            bat = {"workload": "batch_256", "patches": 256, "nnz_per_step": bnnz}
-            for vp in ("fp64", "df64", "mixed"):
-                vdt = torch.float32 if vp == "mixed" else torch.float64
-                pts = [(Rb, gb, cb, torch.empty((Rb.rows, Rb.band), dtype=vdt, device="cuda"),
-                        torch.empty((Rb.rows, Rb.band), dtype=vdt, device="cuda")) for Rb, gb, cb in base]
-                Bp = wq.Batch(pts, vp)
-                Bp.tune(reps=1, stream=stream)
-
-                def timed(fn, n):
-                    fn()
-                    v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    v0.record(stream)
-                    for _ in range(n):
-                        fn()
-                    v1.record(stream)
-                    torch.cuda.synchronize()
-                    return v0.elapsed_time(v1) / n
-
-                tb = timed(lambda: Bp.launch(stream), 5)
-                stb = Bp.status(stream)
-                if stb != wq.WQ_OK:
-                    raise wq.WqError(stb, "batch")
-
-                def seq():
-                    for Rb, gb, cb, Mb, Kb in pts:
-                        wq.assemble(Rb, gb, cb, vp, out=(Mb, Kb), stream=stream, check=False)
-
-                ts = timed(seq, 2)
-                bat[vp] = {"ms_per_step": tb, "value": bnnz / (tb * 1e-3), "unit": "nnz/s",
-                           "ms_one_call_per_patch": ts, "config": Bp.config}
-                Bp.close()
-                del pts
-                torch.cuda.empty_cache()
-            variants["batch_256"] = bat
-            for Rb in rules_cache.values():
-                Rb.close()
-            del base
-
+        barrier()
+        e2e_ms = float(np.mean(timed(e2e_step, e2e_steps, do_flush=False)))
+        barrier()
+        if not torch.equal(Mh[: min(rows, 64)], M[: min(rows, 64)].cpu()):
+            raise RuntimeError("end-to-end bands differ from the device bands")
+        e2e = {"ms_per_step": e2e_ms, "h2d": h2d, "d2h": d2h}
+        del Mh, Kh, gh, ch, gdd, cdd
 
     # max over ranks
     if dist is not None:
-        from paper_1710_01048_gb300 import shard
+        ms_step, e2e_ms_max = shard.max_over_ranks([ms_step, e2e["ms_per_step"] if e2e else 0.0], dist,
+                                                   device="cuda")
+        if e2e:
+            e2e["ms_per_step"] = e2e_ms_max
+        nnz_all = shard.sum_over_ranks([nnz_step], dist, device="cuda")[0]
+    else:
+        nnz_all = nnz_step
+    value = nnz_all / (ms_step * 1e-3)
 
-        ms_step, e2e_ms = shard.max_over_ranks([ms_step, e2e_ms], dist, device="cuda")
-
-    value = world * nnz_step / (ms_step * 1e-3)
-    e2e_value = world * nnz_step / (e2e_ms * 1e-3)
-
-    # roofline of the assembly call (fold + the two row launches; the fold is
-    # a few microseconds): algorithmic contraction flops / device time
-    flops, coef_flops = R.flops()
-    if args.prec == "fp64":
+    # roofline of the assembly call (coefficient prepare + fold + the two
+    # kernels): the step's algorithmic contraction flops / the step's device time
+    flops, coef_flops = R.flops(row_begin=rb, row_end=re)
+    bytes_step = 2 * rows * band * M.element_size()
+    if args.prec in ("fp64", "df64"):
+        pk = FP64_PEAK_TFLOPS if args.prec == "fp64" else DF64_PEAK_TFLOPS
         achieved = flops / (ms_step * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (not in MEASURED_PEAKS.json)",
-                "achieved_incl_coef_eval": (flops + coef_flops) / (ms_step * 1e-3) / 1e12}
-    elif args.prec == "df64":
-        achieved = flops / (ms_step * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": DF64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / DF64_PEAK_TFLOPS,
-                "traffic": TRAFFIC.get((args.workload, "df64"), {}).get("bytes"),
-                "traffic_note": TRAFFIC.get((args.workload, "df64")),
-                "peak_source": "derived: FP32 pipe 152 SMs x 128 lanes x 2.07 GHz / 12 FP32 instructions per "
-                               "double-float multiply-add, x 2 flop (FP64-equivalent)",
+        roof = {"bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
+                "peak_source": ("derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal FP64 1.25 TFLOP/s; "
+                                "not in MEASURED_PEAKS.json)" if args.prec == "fp64" else
+                                "derived: FP32 pipe 152 SMs x 128 lanes x 2.07 GHz / 12 FP32 instructions per "
+                                "double-float multiply-add, x 2 flop (FP64-equivalent)"),
+                "flops_per_step": flops, "band_bytes_per_step": bytes_step,
+                "band_gb_s": bytes_step / (ms_step * 1e-3) / 1e9,
                 "achieved_incl_coef_eval": (flops + coef_flops) / (ms_step * 1e-3) / 1e12}
     else:
-        bytes_step = 2 * rows * band * 4
-        hbm = peaks.get("hbm_gbs", 6800.0)
         achieved = bytes_step / (ms_step * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
                 else "fallback 6.8 TB/s",
                 "fp32_tflops": (flops + coef_flops) / (ms_step * 1e-3) / 1e12, "fp32_peak_tflops": FP32_PEAK_TFLOPS}
+    tr = TRAFFIC.get((args.workload, args.prec))
+    if tr and world == 1:
+        roof["traffic"] = tr["bytes"] * (R.rows / tr["scale_rows"] if tr.get("scale_rows") else 1.0)
+        roof["traffic_note"] = tr["note"]
+    else:
+        roof["traffic"] = None
+
+    # ------------------------------------------------------------ variants (rank 0 at N = 1)
+    variants = {}
+    if not args.no_variants and world == 1:
+        variants = run_variants(args, wq, inputs, R, w, g, gd, cd, (M, K), sample, timed, stream, peaks)
 
     out = {"metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": {"fp64": "f64", "df64": "f32x2", "mixed": "f32"}[args.prec],
-           "data": "synthetic",
-           "config": {"workload": args.workload, "nel": list(nel), "degree": p, "rows": rows, "band": band,
-                      "nnz_per_matrix": R.nnz, "precision": args.prec,
+           "vs_baseline": None, "dtype": DTYPE[args.prec], "data": "synthetic",
+           "config": {"workload": args.workload, "nel": list(nel), "degree": p, "rows": int(R.rows),
+                      "rows_per_rank": int(rows), "band": int(band), "nnz_per_matrix": int(R.nnz),
+                      "precision": args.prec,
                       "l2": "256 MiB buffer written before each timed step; each step also writes "
-                            f"{2 * rows * band * M.element_size() / 1e9:.2f} GB of band output"},
-           "roofline": roof,
-           "e2e": {"value": e2e_value, "unit": "nnz/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-           "clocks": clocks, "gpu_launches": gpu_launches, "ms_per_step_min": float(np.min(ms)),
-           "variants": variants}
-
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu, outs = run_cpu_baseline(w, g, c, args.cpu_stride, max_slabs=None)
+                            f"{bytes_step / 1e9:.2f} GB of band output per rank"},
+           "roofline": roof, "clocks": clocks, "gpu_launches": gpu_launches,
+           "ms_per_step_min": float(np.min(ms)), "ms_per_step_max": float(np.max(ms))}
+    if e2e:
+        out["e2e"] = {"value": nnz_all / (e2e["ms_per_step"] * 1e-3), "unit": "nnz/s",
+                      "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
+                      "ms_per_step": e2e["ms_per_step"],
+                      "path": "wq_assemble_mass_stiffness_host (pinned host buffers, 8 overlapped row ranges)"}
+    if cpu:
         out["cpu_baseline"] = cpu
-        # accuracy of this run's bands on the sampled rows against the oracle
-        emax = 0.0
-        for rb, re, Mo, Ko in outs:
-            for A, O in ((M[rb:re], Mo), (K[rb:re], Ko)):
-                d = A.double().cpu().numpy() - O
-                emax = max(emax, float(np.max(np.abs(d)) / np.max(np.abs(O))))
-        out["max_rel_err_vs_oracle"] = emax
+    if accuracy:
+        out["max_rel_err_vs_oracle"] = accuracy["max"]
+        out["error_vs_oracle"] = {k: accuracy[k] for k in ("M", "K")}
+    out["variants"] = variants
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     R.close()
     return 0
+
+
+def run_variants(args, wq, inputs, R, w, g, gd, cd, bands, sample, timed, stream, peaks):
+    """The other precisions of the headline workload (with their errors on the
+    oracle's sampled rows), the other workloads of the same method, the
+    comparison rules, the adjoint, the matrix-free apply and the batch."""
+    import numpy as np
+    import torch
+
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    variants = {}
+    reps = max(3, min(args.steps, 10))
+
+    def assemble_timed(Rv, gdv, cdv, prec, out, n):
+        fn = lambda: wq.assemble(Rv, gdv, cdv, prec, out=out, stream=stream, check=False)  # noqa: E731
+        for _ in range(3):
+            fn()
+        ms = float(np.mean(timed(fn, n)))
+        st = wq.wq_status_check(Rv.handle, wq._stream_handle(stream))
+        if st != wq.WQ_OK:
+            raise wq.WqError(st, "variant")
+        return ms
+
+    def roofline(Rv, prec, ms, nbytes):
+        fl, _ = Rv.flops()
+        if prec == "mixed":
+            bw = nbytes / (ms * 1e-3) / 1e9
+            return {"bound": "hbm", "achieved": bw, "peak": hbm, "unit": "GB/s", "frac": bw / hbm,
+                    "fp32_tflops": fl / (ms * 1e-3) / 1e12}
+        pk = FP64_PEAK_TFLOPS if prec == "fp64" else DF64_PEAK_TFLOPS
+        tf = fl / (ms * 1e-3) / 1e12
+        return {"bound": "alu", "achieved": tf, "peak": pk, "unit": "TFLOP/s", "frac": tf / pk}
+
+    # the other precisions of the headline workload, errors on the oracle's rows
+    for vp in ("fp64", "df64", "mixed"):
+        if vp == args.prec:
+            continue
+        vdt = torch.float32 if vp == "mixed" else torch.float64
+        if vdt == bands[0].dtype:
+            Mv, Kv = bands  # the headline's errors are already taken: reuse its buffers
+        else:
+            Mv = torch.empty((R.rows, R.band), dtype=vdt, device="cuda")
+            Kv = torch.empty((R.rows, R.band), dtype=vdt, device="cuda")
+        vm = assemble_timed(R, gd, cd, vp, (Mv, Kv), reps)
+        ev = {"ms_per_step": vm, "value": 2 * R.nnz / (vm * 1e-3), "unit": "nnz/s", "dtype": DTYPE[vp],
+              "roofline": roofline(R, vp, vm, 2 * R.rows * R.band * Mv.element_size())}
+        if sample:
+            ev["error_vs_oracle"] = errors_vs_oracle((Mv, Kv), sample)
+        variants[vp] = ev
+        del Mv, Kv
+    torch.cuda.empty_cache()
+
+    # the other workloads: 64^3 cubic and quadratic, 2D 32^2 cubic (c as
+    # named, and c = 1), every precision, errors on oracle rows
+    others = [("3d_p3_64", 16), ("3d_p2_64", 16), ("2d_p3_32", 1), ("2d_p3_32_c1", 1)]
+    for name, stride in others:
+        if name == args.workload:
+            continue
+        wv, gv, cv = inputs.workload(name)
+        Rv = wq.Rules(wv["dim"], wv["p"], wv["nel"])
+        gdv = [torch.from_numpy(x).cuda() for x in gv]
+        cdv = torch.from_numpy(cv).cuda()
+        _, _, _, outs = run_oracle_sample(wv, gv, cv, stride)
+        ent = {"workload": name, "nel": list(wv["nel"]), "degree": wv["p"], "rows": int(Rv.rows),
+               "nnz_per_matrix": int(Rv.nnz),
+               "oracle_rows": int(sum(o[1] - o[0] for o in outs))}
+        for vp in ("fp64", "df64", "mixed"):
+            vdt = torch.float32 if vp == "mixed" else torch.float64
+            Mv = torch.empty((Rv.rows, Rv.band), dtype=vdt, device="cuda")
+            Kv = torch.empty((Rv.rows, Rv.band), dtype=vdt, device="cuda")
+            vm = assemble_timed(Rv, gdv, cdv, vp, (Mv, Kv), reps)
+            ent[vp] = {"ms_per_step": vm, "value": 2 * Rv.nnz / (vm * 1e-3), "unit": "nnz/s",
+                       "roofline": roofline(Rv, vp, vm, 2 * Rv.rows * Rv.band * Mv.element_size()),
+                       "error_vs_oracle": errors_vs_oracle((Mv, Kv), outs)}
+            del Mv, Kv
+        variants[name] = ent
+        Rv.close()
+    torch.cuda.empty_cache()
+
+    # the comparison rules (FP64, same kernel's general-points class) on the
+    # 64^3 cubic workload: Gauss-Legendre on every element of each row's
+    # support, and the Newton-Cotes-type weighted rules; with the
+    # quadrature-point counts
+    wc, gc, cc = inputs.workload("3d_p3_64")
+    gdc = [torch.from_numpy(x).cuda() for x in gc]
+    cdc = torch.from_numpy(cc).cuda()
+    points = {}
+    Mv = Kv = None
+    for mode in ("wq", "nc", "gl"):
+        Rm = wq.Rules(3, wc["p"], wc["nel"], rule=mode)
+        total = 1
+        for a in range(3):
+            total *= sum(len(Rm.row(a, 0, r)[0]) for r in range(wc["nel"][a] + wc["p"]))
+        points[mode] = {"points_per_interior_row_and_direction": len(Rm.row(0, 0, wc["p"])[0]),
+                        "rule_points_total": total}
+        if Mv is None:
+            Mv = torch.empty((Rm.rows, Rm.band), dtype=torch.float64, device="cuda")
+            Kv = torch.empty((Rm.rows, Rm.band), dtype=torch.float64, device="cuda")
+        vm = assemble_timed(Rm, gdc, cdc, "fp64", (Mv, Kv), max(3, min(args.steps, 5)))
+        variants["3d_p3_64_fp64_" + mode + "_rule"] = {"ms_per_step": vm, "value": 2 * Rm.nnz / (vm * 1e-3),
+                                                        "unit": "nnz/s", "dtype": "f64", **points[mode]}
+        Rm.close()
+    variants["rule_points_3d_p3_64"] = points
+    del Mv, Kv
+    torch.cuda.empty_cache()
+
+    # the adjoint (coefficient gradient of sum G*K + H*M) on the 96^3 cubic workload
+    w3, g3, c3 = inputs.workload("3d_p3_96")
+    R3 = wq.Rules(3, w3["p"], w3["nel"])
+    gd3 = [torch.from_numpy(x).cuda() for x in g3]
+    gen = torch.Generator(device="cuda").manual_seed(96)
+    adj = {"workload": "3d_p3_96", "ncoef": R3.ncoef}
+    for vp in ("fp64", "df64", "mixed"):
+        vdt = torch.float32 if vp == "mixed" else torch.float64
+        G = torch.randn((R3.rows, R3.band), dtype=vdt, device="cuda", generator=gen)
+        H = torch.randn((R3.rows, R3.band), dtype=vdt, device="cuda", generator=gen)
+        grad = torch.empty(R3.ncoef, dtype=torch.float64, device="cuda")
+        fn = lambda: wq.assemble_adjoint(R3, gd3, G, H, vp, out=grad, stream=stream, check=False)  # noqa: E731
+        for _ in range(3):
+            fn()
+        vm = float(np.mean(timed(fn, max(3, min(args.steps, 5)))))
+        fl, _ = R3.flops()
+        # per step the adjoint reads both weight bands: report band entries per second
+        adj[vp] = {"ms_per_step": vm, "value": 2 * R3.nnz / (vm * 1e-3), "unit": "nnz/s (weights read)",
+                   "weights_gb_s": 2 * R3.rows * R3.band * G.element_size() / (vm * 1e-3) / 1e9,
+                   "forward_flops_per_ms": fl / vm}
+        del G, H, grad
+        torch.cuda.empty_cache()
+    st = wq.wq_status_check(R3.handle, wq._stream_handle(stream))
+    if st != wq.WQ_OK:
+        raise wq.WqError(st, "adjoint variant")
+    variants["adjoint_3d_p3_96"] = adj
+    R3.close()
+
+    # matrix-free apply y = M x, y = K x (the band never stored) and the load
+    # vector, on the 64^3 cubic workload
+    Ra = wq.Rules(3, wc["p"], wc["nel"])
+    gen = torch.Generator(device="cuda").manual_seed(64)
+    app = {"workload": "3d_p3_64", "nnz_per_step": 2 * Ra.nnz}
+    for vp in ("df64", "fp64", "mixed"):
+        vdt = torch.float32 if vp == "mixed" else torch.float64
+        xv = torch.randn(Ra.rows, dtype=torch.float64, device="cuda", generator=gen).to(vdt)
+        yM = torch.empty(Ra.rows, dtype=vdt, device="cuda")
+        yK = torch.empty(Ra.rows, dtype=vdt, device="cuda")
+        fn = lambda: wq.apply(Ra, gdc, xv, cdc, vp, out=(yM, yK), stream=stream, check=False)  # noqa: E731
+        for _ in range(3):
+            fn()
+        vm = float(np.mean(timed(fn, reps)))
+        # the contractions plus one multiply-add per band entry and matrix
+        fl_apply = Ra.flops()[0] + 2 * 2 * Ra.nnz
+        pk = {"fp64": FP64_PEAK_TFLOPS, "df64": DF64_PEAK_TFLOPS, "mixed": FP32_PEAK_TFLOPS}[vp]
+        tf = fl_apply / (vm * 1e-3) / 1e12
+        app[vp] = {"ms_per_step": vm, "value": 2 * Ra.nnz / (vm * 1e-3), "unit": "nnz/s (applied)",
+                   "roofline": {"bound": "alu", "achieved": tf, "peak": pk, "unit": "TFLOP/s", "frac": tf / pk}}
+        if vp == "df64":
+            bl = torch.empty(Ra.rows, dtype=vdt, device="cuda")
+            fl_ = lambda: wq.assemble_load(Ra, gdc, cdc, vp, out=bl, stream=stream, check=False)  # noqa: E731
+            for _ in range(3):
+                fl_()
+            app["load_vector_df64_ms"] = float(np.mean(timed(fl_, 5)))
+            del bl
+        del xv, yM, yK
+    sta = wq.wq_status_check(Ra.handle, wq._stream_handle(stream))
+    if sta != wq.WQ_OK:
+        raise wq.WqError(sta, "apply variant")
+    variants["apply_3d_p3_64"] = app
+    Ra.close()
+
+    # the batch of 256 independent patches (8..48 elements per direction, p in {2, 3}):
+    # one graph of two persistent launches, tuned, against one call per patch
+    if not args.no_batch:
+        specs = inputs.batch_patches(256, seed=0)
+        rules_cache, base = {}, []
+        for sp in specs:
+            key = (sp["p"], sp["nel"])
+            if key not in rules_cache:
+                rules_cache[key] = wq.Rules(3, sp["p"], sp["nel"])
+            base.append((rules_cache[key], [torch.from_numpy(x).cuda() for x in sp["geom"]],
+                         torch.from_numpy(sp["coef"]).cuda()))
+        bnnz = 2 * sum(Rb.nnz for Rb, _, _ in base)
+        bat = {"workload": "batch_256", "patches": 256, "nnz_per_step": bnnz}
+        for vp in ("fp64", "df64", "mixed"):
+            vdt = torch.float32 if vp == "mixed" else torch.float64
+            pts = [(Rb, gb, cb, torch.empty((Rb.rows, Rb.band), dtype=vdt, device="cuda"),
+                    torch.empty((Rb.rows, Rb.band), dtype=vdt, device="cuda")) for Rb, gb, cb in base]
+            Bp = wq.Batch(pts, vp)
+            Bp.tune(reps=1, stream=stream)
+            Bp.launch(stream)
+            tb = float(np.mean(timed(lambda: Bp.launch(stream), 5)))
+            stb = Bp.status(stream)
+            if stb != wq.WQ_OK:
+                raise wq.WqError(stb, "batch")
+
+            def seq():
+                for Rb, gb, cb, Mb, Kb in pts:
+                    wq.assemble(Rb, gb, cb, vp, out=(Mb, Kb), stream=stream, check=False)
+
+            seq()
+            ts = float(np.mean(timed(seq, 2)))
+            bat[vp] = {"ms_per_step": tb, "value": bnnz / (tb * 1e-3), "unit": "nnz/s",
+                       "ms_one_call_per_patch": ts, "config": Bp.config}
+            Bp.close()
+            del pts
+            torch.cuda.empty_cache()
+        variants["batch_256"] = bat
+        for Rb in rules_cache.values():
+            Rb.close()
+        del base
+    return variants
 
 
 if __name__ == "__main__":

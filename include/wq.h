@@ -197,6 +197,41 @@ wq_status wq_assemble_mass_stiffness(const wq_rules *rules, const double *const 
                                      void *stream);
 
 /*
+ * The same assembly end to end between host buffers (Eq. Mass, Eq.
+ * Stiffness; the computation of wq_assemble_mass_stiffness): the host
+ * inputs are copied to caller-owned device buffers on `stream`, rows
+ * [row_begin, row_end) are assembled in `nchunks` consecutive ranges into
+ * caller-owned device bands, and each range's bands are copied to the host
+ * on `copy_stream` while the next range is being assembled on `stream`.
+ *   geom_host[a], coef_host  host inputs as for wq_assemble_mass_stiffness
+ *                            (coef_host NULL: c = 1);
+ *   geom_dev[a], coef_dev    device buffers of the same sizes, overwritten
+ *                            (coef_dev unused, may be NULL, when coef_host
+ *                            is NULL);
+ *   M_dev, K_dev             device bands of (row_end - row_begin) rows
+ *                            (double for WQ_FP64 and WQ_DF64, float for
+ *                            WQ_MIXED), overwritten: the staging area;
+ *   M_host, K_host           host bands of the same shape and type,
+ *                            overwritten, row row_begin first;
+ *   nchunks                  1 .. 1024 row ranges;
+ *   stream, copy_stream      two different CUDA streams of the current device.
+ * The call returns once everything is enqueued; `stream` then waits for the
+ * last copy, so a synchronisation of `stream` makes M_host and K_host valid.
+ * The host buffers must stay alive, and unread, until then; page-locked host
+ * memory (cudaHostAlloc, cudaHostRegister) lets the copies overlap the
+ * assembly, pageable memory makes them synchronous.  Two CUDA events are
+ * created and released per call; no device memory is allocated.  Device-
+ * detected problems are reported by wq_status_check, argument errors as for
+ * wq_assemble_mass_stiffness (WQ_ERR_ARG also for nchunks out of range or
+ * equal streams).
+ */
+wq_status wq_assemble_mass_stiffness_host(const wq_rules *rules, const double *const *geom_host,
+                                          const double *coef_host, wq_precision prec, void *M_host, void *K_host,
+                                          double *const *geom_dev, double *coef_dev, void *M_dev, void *K_dev,
+                                          int64_t row_begin, int64_t row_end, int nchunks, void *stream,
+                                          void *copy_stream);
+
+/*
  * Matrix-free apply: y_M = M x and y_K = K x for rows [row_begin, row_end)
  * of the matrices of wq_assemble_mass_stiffness (Eq. Mass, Eq. Stiffness
  * with the weighted Gaussian rules; K x is the operator of Eq. LinSys), with

@@ -30,7 +30,7 @@ EXPORTS = ["wq_status_string", "wq_version", "wq_rule_1d", "wq_rule_1d_from", "w
            "wq_assemble_mass", "wq_assemble_stiffness", "wq_assemble_mass_stiffness", "wq_status_check",
            "wq_assemble_noalloc", "wq_assemble_adjoint", "wq_batch_create", "wq_batch_launch", "wq_batch_status",
            "wq_batch_get_config", "wq_batch_set_config", "wq_batch_tune", "wq_batch_free", "wq_assemble_batch", "wq_band_nnz_rows", "wq_band_to_csr",
-           "wq_apply_mass_stiffness", "wq_assemble_load"]
+           "wq_apply_mass_stiffness", "wq_assemble_load", "wq_assemble_mass_stiffness_host"]
 
 
 class WqError(RuntimeError):
@@ -88,6 +88,8 @@ def _lib():
     lib.wq_apply_mass_stiffness.argtypes = [c_void_p, PP, c_void_p, c_int, c_void_p, c_void_p, c_void_p, i64, i64,
                                             c_void_p]
     lib.wq_assemble_load.argtypes = [c_void_p, PP, c_void_p, c_int, c_void_p, i64, i64, c_void_p]
+    lib.wq_assemble_mass_stiffness_host.argtypes = [c_void_p, PP, c_void_p, c_int, c_void_p, c_void_p, PP, c_void_p,
+                                                    c_void_p, c_void_p, i64, i64, c_int, c_void_p, c_void_p]
     lib.wq_status_check.argtypes = [c_void_p, c_void_p]
     lib.wq_assemble_noalloc.argtypes = [c_void_p, PP, c_void_p, c_int, c_void_p, c_void_p, i64, i64, c_void_p, c_int]
     lib.wq_assemble_adjoint.argtypes = [c_void_p, PP, c_int, c_void_p, c_void_p, c_void_p, i64, i64, c_void_p]
@@ -559,40 +561,43 @@ def band_to_csr(rules, band, prec="fp64", row_begin=0, row_end=None, stream=None
     return rowptr, col[:nnz], val[:nnz]
 
 
-def assemble_to_host(rules, geom, coef, prec, M_host, K_host, M_dev, K_dev, nchunks=8, stream=None):
-    """Assembles M and K into pinned host tensors M_host, K_host (rows x band),
-    overlapping the device-to-host copies with the assembly: the rows are cut
-    into nchunks ranges; range k is assembled on `stream` into M_dev, K_dev
-    (full-size device tensors) while range k-1 is copied to the host on a
-    second stream.  Returns after enqueueing; `stream` waits for the copies."""
+def wq_assemble_mass_stiffness_host(handle, geom_host_ptrs, coef_host_ptr, prec, M_host_ptr, K_host_ptr,
+                                    geom_dev_ptrs, coef_dev_ptr, M_dev_ptr, K_dev_ptr, row_begin, row_end, nchunks,
+                                    stream, copy_stream):
+    gh, keep_h = _geom_array(geom_host_ptrs)
+    gd, keep_d = _geom_array(geom_dev_ptrs)
+    return _lib().wq_assemble_mass_stiffness_host(handle, gh, coef_host_ptr, prec, M_host_ptr, K_host_ptr, gd,
+                                                  coef_dev_ptr, M_dev_ptr, K_dev_ptr, row_begin, row_end,
+                                                  int(nchunks), stream, copy_stream)
+
+
+def assemble_to_host(rules, geom_host, coef_host, prec, M_host, K_host, geom_dev, coef_dev, M_dev, K_dev, nchunks=8,
+                     stream=None, row_begin=0, row_end=None):
+    """wq_assemble_mass_stiffness_host: inputs from host tensors (geom_host,
+    coef_host; pinned for overlap) to the device buffers geom_dev, coef_dev,
+    the rows assembled in nchunks ranges into M_dev, K_dev, each range copied
+    into the host tensors M_host, K_host on a second stream while the next is
+    assembled.  Rows [row_begin, row_end) (default all); the band tensors
+    hold those rows.  Returns after enqueueing; `stream` waits for the copies."""
     import torch
 
+    if row_end is None:
+        row_end = rules.rows
     if stream is None:
         stream = torch.cuda.current_stream()
     copy = _copy_stream(stream.device)
-    rows = rules.rows
-    bounds = [rows * k // nchunks for k in range(nchunks + 1)]
-    gp = [g.data_ptr() for g in geom]
-    cp = ctypes.c_void_p(coef.data_ptr()) if coef is not None else None
-    p = PRECISIONS[prec]
-    s = ctypes.c_void_p(stream.cuda_stream)
-    esz = M_dev.element_size()
-    for k in range(nchunks):
-        rb, re = bounds[k], bounds[k + 1]
-        if rb == re:
-            continue
-        st = wq_assemble_mass_stiffness(rules.handle, gp, cp, p, ctypes.c_void_p(M_dev.data_ptr() + rb * rules.band * esz),
-                                        ctypes.c_void_p(K_dev.data_ptr() + rb * rules.band * esz), rb, re, s)
-        _check(st, "wq_assemble_mass_stiffness")
-        ev = torch.cuda.Event()
-        ev.record(stream)
-        copy.wait_event(ev)
-        with torch.cuda.stream(copy):
-            M_host[rb:re].copy_(M_dev[rb:re], non_blocking=True)
-            K_host[rb:re].copy_(K_dev[rb:re], non_blocking=True)
-    done = torch.cuda.Event()
-    done.record(copy)
-    stream.wait_event(done)
+    for X in list(geom_host) + list(geom_dev) + [M_host, K_host, M_dev, K_dev]:
+        assert X.is_contiguous()
+    if coef_host is not None:
+        assert coef_host.is_contiguous() and coef_dev is not None and coef_dev.is_contiguous()
+    st = wq_assemble_mass_stiffness_host(
+        rules.handle, [g.data_ptr() for g in geom_host],
+        ctypes.c_void_p(coef_host.data_ptr()) if coef_host is not None else None, PRECISIONS[prec],
+        ctypes.c_void_p(M_host.data_ptr()), ctypes.c_void_p(K_host.data_ptr()), [g.data_ptr() for g in geom_dev],
+        ctypes.c_void_p(coef_dev.data_ptr()) if coef_host is not None else None, ctypes.c_void_p(M_dev.data_ptr()),
+        ctypes.c_void_p(K_dev.data_ptr()), row_begin, row_end, nchunks, ctypes.c_void_p(stream.cuda_stream),
+        ctypes.c_void_p(copy.cuda_stream))
+    _check(st, "wq_assemble_mass_stiffness_host")
 
 
 _COPY_STREAMS = {}

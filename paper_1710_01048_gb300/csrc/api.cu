@@ -586,6 +586,64 @@ wq_status wq_assemble_mass_stiffness(const wq_rules *rules, const double *const 
   return assemble(rules, geom, coef, prec, M, K, row_begin, row_end, stream);
 }
 
+wq_status wq_assemble_mass_stiffness_host(const wq_rules *R, const double *const *geom_host,
+                                          const double *coef_host, wq_precision prec, void *M_host, void *K_host,
+                                          double *const *geom_dev, double *coef_dev, void *M_dev, void *K_dev,
+                                          int64_t row_begin, int64_t row_end, int nchunks, void *stream,
+                                          void *copy_stream) {
+  wq::TraceRange trace("wq_assemble_mass_stiffness_host");
+  if (!R || !geom_host || !geom_dev) return WQ_ERR_ARG;
+  if (nchunks < 1 || nchunks > 1024) return WQ_ERR_ARG;
+  if (stream == copy_stream) return WQ_ERR_ARG;
+  if (coef_host && !coef_dev) return WQ_ERR_ARG;
+  for (int a = 0; a < R->dim; a++)
+    if (!geom_host[a] || !geom_dev[a]) return WQ_ERR_ARG;
+  wq_status st = check_call(R, geom_dev, prec, row_begin, row_end);
+  if (st != WQ_OK) return st;
+  if (row_begin == row_end) return WQ_OK;
+  if (!M_host || !K_host || !M_dev || !K_dev) return WQ_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream), cs = static_cast<cudaStream_t>(copy_stream);
+  // inputs: host -> device on the compute stream
+  for (int a = 0; a < R->dim; a++)
+    if (cudaMemcpyAsync(geom_dev[a], geom_host[a], (size_t)R->n[a] * sizeof(double), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+      return WQ_ERR_CUDA;
+  const size_t ncoef = (size_t)R->nc[0] * R->nc[1] * R->nc[2];
+  if (coef_host &&
+      cudaMemcpyAsync(coef_dev, coef_host, ncoef * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return WQ_ERR_CUDA;
+  const double *coef = coef_host ? coef_dev : nullptr;
+  // one event marks each range's assembly (re-recorded per range: a wait
+  // binds to the record made before it), one the end of the copies
+  cudaEvent_t ready = nullptr, done = nullptr;
+  if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess) return WQ_ERR_CUDA;
+  if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) {
+    cudaEventDestroy(ready);
+    return WQ_ERR_CUDA;
+  }
+  const int64_t band = wq_band_width(R), rows = row_end - row_begin;
+  const size_t esz = prec == WQ_MIXED ? sizeof(float) : sizeof(double);
+  for (int k = 0; k < nchunks && st == WQ_OK; k++) {
+    const int64_t rb = row_begin + rows * k / nchunks, re = row_begin + rows * (k + 1) / nchunks;
+    if (rb == re) continue;
+    const size_t off = (size_t)(rb - row_begin) * band * esz, bytes = (size_t)(re - rb) * band * esz;
+    char *md = static_cast<char *>(M_dev) + off, *kd = static_cast<char *>(K_dev) + off;
+    st = assemble(R, geom_dev, coef, prec, md, kd, rb, re, stream);
+    if (st != WQ_OK) break;
+    if (cudaEventRecord(ready, s) != cudaSuccess || cudaStreamWaitEvent(cs, ready, 0) != cudaSuccess ||
+        cudaMemcpyAsync(static_cast<char *>(M_host) + off, md, bytes, cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+        cudaMemcpyAsync(static_cast<char *>(K_host) + off, kd, bytes, cudaMemcpyDeviceToHost, cs) != cudaSuccess)
+      st = WQ_ERR_CUDA;
+  }
+  if (st == WQ_OK &&
+      (cudaEventRecord(done, cs) != cudaSuccess || cudaStreamWaitEvent(s, done, 0) != cudaSuccess))
+    st = WQ_ERR_CUDA;
+  // destruction is deferred by the runtime until the recorded work completes
+  cudaEventDestroy(ready);
+  cudaEventDestroy(done);
+  return st;
+}
+
 wq_status wq_apply_mass_stiffness(const wq_rules *rules, const double *const *geom, const double *coef,
                                   wq_precision prec, const void *x, void *yM, void *yK, int64_t row_begin,
                                   int64_t row_end, void *stream) {

@@ -20,6 +20,6 @@ def test_reference_arm_prints_one_contract_line():
         assert k in d, k
     assert d["impl"] == "reference" and d["steps"] == 3 and d["warmup"] == 3
     assert d["value"] > 0 and d["higher_is_better"] is True and d["unit"] == "nnz/s"
-    assert d["config"]["workload"] == "3d_p3_64"
+    assert d["config"]["workload"] == "3d_p3_128"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0

@@ -186,7 +186,7 @@ def test_status_geometry_and_nonfinite():
     R.close()
 
 
-@pytest.mark.parametrize("prec", ["df64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "df64", "mixed"])
 def test_128_cubed_sampled(prec):
     # the 128^3 cubic workload (2.25M rows x 343): sampled rows against the
     # oracle, and invariants over every row
@@ -198,36 +198,75 @@ def test_128_cubed_sampled(prec):
     M, K = wq.assemble(R, gd, cd, prec)
     n1 = nel[0] + p
     n12 = n1 * (nel[1] + p)
-    tol = FP64_TOL if prec == "df64" else MIXED_TOL
-    for rb, re in [(0, 40), (n12 * 70 + n1 * 60, n12 * 70 + n1 * 61), (R.rows - 40, R.rows)]:
+    tol = MIXED_TOL if prec == "mixed" else FP64_TOL
+    # first rows, one interior line, a line of the boundary plane r2 = 1,
+    # rows at the x1 end of an interior line, the last rows, and a seeded
+    # sample of single rows anywhere in the mesh
+    rng = np.random.default_rng(128)
+    ranges = [(0, 40), (n12 * 70 + n1 * 60, n12 * 70 + n1 * 61), (n12 * 33 + n1 * 1, n12 * 33 + n1 * 2),
+              (n12 * 99 + n1 * 77 + n1 - 9, n12 * 99 + n1 * 78 + 4), (R.rows - 40, R.rows)]
+    ranges += [(int(r), int(r) + 1) for r in rng.integers(0, R.rows, size=24)]
+    for rb, re in ranges:
         Mo, Ko, _ = oracle.assemble(3, p, nel, g, c, rb, re)
         check(M[rb:re].double().cpu().numpy(), Mo, tol, f"M rows {rb}:{re}")
         check(K[rb:re].double().cpu().numpy(), Ko, tol, f"K rows {rb}:{re}")
     kabs = K.abs().sum(dim=1, dtype=torch.float64)
     ks = K.sum(dim=1, dtype=torch.float64).abs()
-    assert (ks <= (1e-12 if prec == "df64" else 1e-5) * kabs).all()
+    assert (ks <= (1e-5 if prec == "mixed" else 1e-12) * kabs).all()
     del M, K
     R.close()
 
 
-@pytest.mark.parametrize("prec", ["df64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "df64", "mixed"])
 def test_assemble_to_host_overlapped(prec):
-    # bands assembled range by range with their host copies overlapped equal
-    # the one-call device result
+    # wq_assemble_mass_stiffness_host: host inputs, bands assembled range by
+    # range with their host copies overlapped, equal the one-call device
+    # result bit for bit (and c = 1 through a NULL coefficient)
     p, nel = 3, (21, 10, 9)
     g, c = inputs.make(3, p, nel, 0.05, "exp", 0.1, seed=8)
     R = wq.Rules(3, p, nel)
     gd = [torch.from_numpy(x).cuda() for x in g]
     cd = torch.from_numpy(c).cuda()
-    M, K = wq.assemble(R, gd, cd, prec)
-    dt = M.dtype
-    Mh = torch.empty((R.rows, R.band), dtype=dt).pin_memory()
-    Kh = torch.empty((R.rows, R.band), dtype=dt).pin_memory()
-    Md, Kd = torch.empty_like(M), torch.empty_like(K)
-    for nch in (1, 5, 8):
-        Mh.zero_()
-        Kh.zero_()
-        wq.assemble_to_host(R, gd, cd, prec, Mh, Kh, Md, Kd, nchunks=nch)
-        torch.cuda.synchronize()
-        assert torch.equal(Mh, M.cpu()) and torch.equal(Kh, K.cpu())
+    gh = [torch.from_numpy(x).pin_memory() for x in g]
+    ch = torch.from_numpy(c).pin_memory()
+    for coef_dev, coef_host in ((cd, ch), (None, None)):
+        M, K = wq.assemble(R, gd, coef_dev, prec)
+        dt = M.dtype
+        Mh = torch.empty((R.rows, R.band), dtype=dt).pin_memory()
+        Kh = torch.empty((R.rows, R.band), dtype=dt).pin_memory()
+        Md, Kd = torch.empty_like(M), torch.empty_like(K)
+        gdd = [torch.empty_like(x) for x in gd]
+        cdd = torch.empty_like(cd)
+        for nch in (1, 5, 8):
+            Mh.zero_()
+            Kh.zero_()
+            wq.assemble_to_host(R, gh, coef_host, prec, Mh, Kh, gdd, cdd, Md, Kd, nchunks=nch)
+            torch.cuda.synchronize()
+            assert torch.equal(Mh, M.cpu()) and torch.equal(Kh, K.cpu())
+    assert wq.wq_status_check(R.handle, wq._stream_handle(None)) == wq.WQ_OK
+    R.close()
+
+
+def test_assemble_to_host_arguments():
+    # argument errors are reported before anything is enqueued
+    import ctypes
+
+    p, nel = 2, (4, 3, 5)
+    g, c = inputs.make(3, p, nel, 0.0, "one")
+    R = wq.Rules(3, p, nel)
+    gh = [torch.from_numpy(x) for x in g]
+    gd = [x.cuda() for x in gh]
+    M = torch.empty((R.rows, R.band), dtype=torch.float64, device="cuda")
+    Mh = torch.empty((R.rows, R.band), dtype=torch.float64)
+    s = torch.cuda.current_stream()
+    hp, dp = [x.data_ptr() for x in gh], [x.data_ptr() for x in gd]
+    mp, mhp = ctypes.c_void_p(M.data_ptr()), ctypes.c_void_p(Mh.data_ptr())
+    ss = ctypes.c_void_p(s.cuda_stream)
+    other = ctypes.c_void_p(torch.cuda.Stream().cuda_stream)
+    call = wq.wq_assemble_mass_stiffness_host
+    assert call(R.handle, hp, None, wq.WQ_FP64, mhp, mhp, dp, None, mp, mp, 0, R.rows, 0, ss, other) == wq.WQ_ERR_ARG
+    assert call(R.handle, hp, None, wq.WQ_FP64, mhp, mhp, dp, None, mp, mp, 0, R.rows, 2, ss, ss) == wq.WQ_ERR_ARG
+    assert call(R.handle, hp, None, wq.WQ_FP64, mhp, mhp, dp, None, mp, mp, 0, R.rows + 1, 2, ss, other) == \
+        wq.WQ_ERR_ARG
+    assert call(R.handle, hp, None, wq.WQ_FP64, None, None, dp, None, None, None, 3, 3, 2, ss, other) == wq.WQ_OK
     R.close()
