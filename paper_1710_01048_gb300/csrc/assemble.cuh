@@ -61,6 +61,53 @@ struct RowsArgs {
   const void *x;
 };
 
+// Asynchronous global -> shared copies of one 4- or 8-byte element
+// (cp.async): complete in the issuing thread after cp_async_wait_all(),
+// visible to the CTA after a barrier.
+template <typename T> __device__ __forceinline__ void cp_async_el(T *sdst, const T *gsrc) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(sdst)),
+                 "l"(gsrc)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(sdst)),
+                 "l"(gsrc)
+                 : "memory");
+}
+// n consecutive elements, strided over the threads tid, tid + nt, ...
+template <typename T> __device__ __forceinline__ void cp_async_n(T *sdst, const T *gsrc, int n, int tid, int nt) {
+  for (int i = tid; i < n; i += nt) cp_async_el(sdst + i, gsrc + i);
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Bulk asynchronous shared -> global copy (cp.async.bulk, bulk-group
+// completion): both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_store_s2g(void *gdst, const void *ssrc, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(gdst),
+               "r"((unsigned)__cvta_generic_to_shared(ssrc)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+// Waits until the committed bulk copies of this thread have read their source.
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+// Makes this thread's shared-memory writes visible to the bulk copies.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// Writes n floats of a stage to g: the 16-byte-aligned middle by one bulk
+// copy (thread `issuer`), the at most three entries on either side by plain
+// stores (threads helper0 ..); s is positioned so that s[i] and g[i] agree
+// modulo 16 bytes.  The caller fences, synchronises and commits.
+__device__ __forceinline__ void stage_out(float *g, const float *s, int n, int tid, int issuer, int helper0) {
+  const int head = min((int)((4 - (((uintptr_t)g >> 2) & 3)) & 3), n);
+  const int mid = (n - head) / 4 * 4;
+  const int tail = n - head - mid;
+  if (tid == issuer && mid > 0) bulk_store_s2g(g + head, s + head, (unsigned)mid * 4u);
+  const int h = tid - helper0;
+  if (h >= 0 && h < head) g[h] = s[h];
+  if (h >= head && h < head + tail) g[mid + h] = s[mid + h];  // entries head + mid .. n - 1
+}
+
 // acc[o + i] += x * v[i], i = 0..P, with a compile-time register index in
 // each case.
 template <int P, int O, typename R, typename VT>
@@ -103,11 +150,14 @@ __device__ __forceinline__ void fiber_point(R (&acc)[2 * P + 1], R x, const R *_
 }
 
 // acc[o + i] += x * v[i], i = 0..P, for a runtime offset o in [0, P]: the
-// switch form for double (the FP64 pipe is the bound), the dense NB-wide
-// form with the point's P+1 columns selected by comparison otherwise.
+// switch form for double and float (every call site has o uniform across a
+// warp, or nearly so), the dense NB-wide form with the point's P+1 columns
+// selected by comparison for double-float.  The two forms give the same
+// values: the dense form's extra terms add x * 0 to entries that start at +0
+// and never become -0.
 template <int P, typename R, typename VT>
 __device__ __forceinline__ void fiber_shift(R (&acc)[2 * P + 1], R x, VT v, int o) {
-  if constexpr (sizeof(R) == 8 && !std::is_same<R, dd>::value) {
+  if constexpr (!std::is_same<R, dd>::value) {
     fiber_add<P>(acc, x, v, o);
   } else {
 #pragma unroll
@@ -138,6 +188,19 @@ template <typename R> constexpr int pad16(int n) {
   return (n * (int)sizeof(R) + 15) / 16 * 16 / (int)sizeof(R);
 }
 
+// Per-warp band stage of phase B, in values of R: for float one buffer per
+// matrix, each one run of kBulkSub x 32 items plus three entries of alignment slack, written
+// to global memory by bulk copies; otherwise one buffer for both matrices in
+// turn, written by the warp's lanes.
+template <typename R, int NB, bool APPLY> constexpr bool bulk_stage() {
+  return std::is_same<R, float>::value && !APPLY;
+}
+constexpr int kBulkSub = 2;  // 32-item sub-runs per bulk run
+template <typename R, int NB> constexpr int stage_run() { return pad16<R>(32 * kBulkSub * NB + 3); }
+template <typename R, int NB, bool APPLY> constexpr int stage_per_warp() {
+  return bulk_stage<R, NB, APPLY>() ? 2 * stage_run<R, NB>() : pad16<R>(32 * NB);
+}
+
 template <int P, int D, int LM, int TMAX, bool DO_M, bool DO_K, typename R, bool APPLY = false>
 struct RowsLayout {
   static constexpr int NP = P + 1;             // points of a weighted Gaussian rule
@@ -166,7 +229,7 @@ struct RowsLayout {
   static constexpr int WA = WX + WT;
   static constexpr int WS = pad16<R>(WA);  // phase A, per half-warp
   // phase B: per-warp stage of 32 items' fibres, one matrix at a time
-  static constexpr int WST = pad16<R>(32 * NB);
+  static constexpr int WST = stage_per_warp<R, NB, APPLY>();
   static constexpr int SCRATCH0 = (2 * NW * WS) > (NW * WST) ? (2 * NW * WS) : (NW * WST);
   // apply: phase B's per-fibre partial sums share the scratch; x gets its own region
   static constexpr int PART = pad16<R>(2 * TMAX * NPAIR);
@@ -224,7 +287,8 @@ template <typename R, int MAXPTS1, int W> struct X1Row {
 
 // The chunk's x1 tables (rows [a, a+T) hold one contiguous range of points):
 // point offsets per row, folded values and cubic coefficient-spline values of
-// both kinds, elements.  No barrier; the caller synchronises.
+// both kinds, elements, by asynchronous copies: the caller waits for them
+// (cp_async_wait_all) and synchronises.
 template <int P, int MAXPTS1, typename R>
 __device__ __forceinline__ void load_x1_tables(const RowsArgs &A, const int a, const int T, R *sV1, R *sB1, int *sE1,
                                                int *sOff1) {
@@ -239,10 +303,60 @@ __device__ __forceinline__ void load_x1_tables(const RowsArgs &A, const int a, c
     const R *Vg = static_cast<const R *>(A.V[0][kind]);
     const R *Bg = static_cast<const R *>(A.beta[0][kind]);
 #pragma unroll
-    for (int i = 0; i < NP; i++) sV1[x1_idx<R, MAXPTS1, NP>(q, i, kind)] = Vg[(size_t)gq * NP + i];
+    for (int i = 0; i < NP; i++) cp_async_el(&sV1[x1_idx<R, MAXPTS1, NP>(q, i, kind)], &Vg[(size_t)gq * NP + i]);
 #pragma unroll
-    for (int i = 0; i < 4; i++) sB1[x1_idx<R, MAXPTS1, 4>(q, i, kind)] = Bg[(size_t)gq * 4 + i];
-    if (kind == 0) sE1[q] = A.elem[0][0][p1lo + q];
+    for (int i = 0; i < 4; i++) cp_async_el(&sB1[x1_idx<R, MAXPTS1, 4>(q, i, kind)], &Bg[(size_t)gq * 4 + i]);
+    if (kind == 0) cp_async_el(&sE1[q], &A.elem[0][0][p1lo + q]);
+  }
+}
+
+// The P+1 Gauss-Legendre points q .. q+P of one element, at band offset O,
+// of a boundary x1 row: per point y_M = b1M . u0, y_K = b1M . u1,
+// y_S = b1S . u0 and the updates of fiber_shift, in the same order.
+template <int P, int O, int MAXPTS1, bool DO_M, bool DO_K, typename R>
+__device__ __forceinline__ void gl_element(R (&accM)[2 * P + 1], R (&accK)[2 * P + 1], const R (&u0)[4],
+                                           const R (&u1)[4], const R *sB1, const R *sV1, const int q) {
+  constexpr int NP = P + 1;
+#pragma unroll
+  for (int qq = 0; qq < NP; qq++) {
+    R bm[4], bs[4], vm[NP], vs[NP];
+    if constexpr (std::is_same<R, float>::value && NP == 4) {
+      const float4 b4m = reinterpret_cast<const float4 *>(&sB1[(0 * MAXPTS1 + q + qq) * 4])[0];
+      const float4 b4s = reinterpret_cast<const float4 *>(&sB1[(1 * MAXPTS1 + q + qq) * 4])[0];
+      const float4 v4m = reinterpret_cast<const float4 *>(&sV1[(0 * MAXPTS1 + q + qq) * NP])[0];
+      const float4 v4s = reinterpret_cast<const float4 *>(&sV1[(1 * MAXPTS1 + q + qq) * NP])[0];
+      bm[0] = b4m.x; bm[1] = b4m.y; bm[2] = b4m.z; bm[3] = b4m.w;
+      bs[0] = b4s.x; bs[1] = b4s.y; bs[2] = b4s.z; bs[3] = b4s.w;
+      vm[0] = v4m.x; vm[1] = v4m.y; vm[2] = v4m.z; vm[3] = v4m.w;
+      vs[0] = v4s.x; vs[1] = v4s.y; vs[2] = v4s.z; vs[3] = v4s.w;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        bm[i] = sB1[x1_idx<R, MAXPTS1, 4>(q + qq, i, 0)];
+        bs[i] = sB1[x1_idx<R, MAXPTS1, 4>(q + qq, i, 1)];
+      }
+#pragma unroll
+      for (int i = 0; i < NP; i++) {
+        vm[i] = sV1[x1_idx<R, MAXPTS1, NP>(q + qq, i, 0)];
+        vs[i] = sV1[x1_idx<R, MAXPTS1, NP>(q + qq, i, 1)];
+      }
+    }
+    if constexpr (DO_M) {
+      R y = r_zero<R>();
+#pragma unroll
+      for (int i = 0; i < 4; i++) y = r_fma(bm[i], u0[i], y);
+      fiber_at<P, O>(accM, y, vm);
+    }
+    if constexpr (DO_K) {
+      R yk = r_zero<R>(), ys = r_zero<R>();
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        yk = r_fma(bm[i], u1[i], yk);
+        ys = r_fma(bs[i], u0[i], ys);
+      }
+      fiber_at<P, O>(accK, yk, vm);
+      fiber_at<P, O>(accK, ys, vs);
+    }
   }
 }
 
@@ -261,21 +375,29 @@ __device__ __forceinline__ void rows_phase_b(const RowsArgs &A, const R *sU, con
   using O = typename OutT<R>::type;
   constexpr int NP = P + 1, NB = 2 * P + 1, NT = 32 * kRowsWarps;
   constexpr int NPAIR = (D == 3) ? NB * NB : NB, BAND = NPAIR * NB, LS = NPAIR;
-  constexpr int WST = pad16<R>(32 * NB);
+  constexpr bool BULK = bulk_stage<R, NB, APPLY>();
+  constexpr int WST = stage_per_warp<R, NB, APPLY>(), WSTB = stage_run<R, NB>();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // ------------------------------------------------ phase B: (row, fibre) items, 32 per warp
   // Item i of the chunk is fibre i % NPAIR of row i / NPAIR; its 2P+1 band
   // entries sit at offset i * NB of the chunk's output rows, so a warp's 32
   // consecutive items own one contiguous run of 32 * NB entries per matrix.
-  // The warp stages that run in shared memory and writes it with consecutive
-  // lanes on consecutive addresses, converting to the output type there; no
-  // CTA-wide barrier is needed.
+  // The warp stages that run in shared memory; in float (BULK) one lane
+  // writes its 16-byte-aligned middle with a bulk asynchronous copy per
+  // matrix and lanes store the ends, otherwise the warp's lanes write it
+  // with consecutive lanes on consecutive addresses, converting to the
+  // output type there.  No CTA-wide barrier is needed.
   const R *U0 = sU;
   const R *U1 = sU + NL1 * LS;
   R *wst = sW + warp * WST;  // [32][NB]
   const int nitems = T * NPAIR;
   const long long ochunk = (base + a - A.row_begin) * BAND;
-  for (int ib = warp * 32; ib < nitems; ib += NT) {
+  // in float a warp's consecutive iterations take consecutive 32-item
+  // sub-runs (kBulkSub per run, written out together)
+  constexpr int SUB = BULK ? kBulkSub : 1;
+  for (int it = 0;; it++) {
+    const int ib = warp * 32 * SUB + (it / SUB) * NT * SUB + (it % SUB) * 32;
+    if (ib >= nitems) break;
     const int item = ib + lane;
     R oM[NB], oK[NB];
     if (item < nitems) {
@@ -444,6 +566,37 @@ __device__ __forceinline__ void rows_phase_b(const RowsArgs &A, const R *sU, con
             oM[j] = dd2_first(aMK[j]);
             oK[j] = dd2_second(aMK[j]);
           }
+        } else if constexpr (!GENERAL) {
+          // Gauss-Legendre rows: P+1 points in each element of the support,
+          // in element order; per element its four coefficient columns are
+          // loaded once and its band offset selects compile-time indices
+          // (the per-point order of the general form below is kept)
+          R accM[NB], accK[NB];
+#pragma unroll
+          for (int j = 0; j < NB; j++) { accM[j] = r_zero<R>(); accK[j] = r_zero<R>(); }
+          for (int q = q0; q < q1end; q += NP) {
+            const int e = sE1[q];
+            const int k0 = e - l1lo, o = e - r1 + P;
+            R u0[4], u1[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+              u0[i] = U0[(k0 + i) * LS + pr];
+              u1[i] = DO_K ? U1[(k0 + i) * LS + pr] : r_zero<R>();
+            }
+            switch (o) {
+              case 0: gl_element<P, 0, MAXPTS1, DO_M, DO_K>(accM, accK, u0, u1, sB1, sV1, q); break;
+              case 1: gl_element<P, 1, MAXPTS1, DO_M, DO_K>(accM, accK, u0, u1, sB1, sV1, q); break;
+              case 2: gl_element<P, 2, MAXPTS1, DO_M, DO_K>(accM, accK, u0, u1, sB1, sV1, q); break;
+              default:
+                if constexpr (P >= 3) gl_element<P, (P >= 3 ? 3 : 0), MAXPTS1, DO_M, DO_K>(accM, accK, u0, u1, sB1, sV1, q);
+                break;
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < NB; j++) {
+            if constexpr (DO_M) oM[j] = accM[j];
+            if constexpr (DO_K) oK[j] = accK[j];
+          }
         } else {
           R accM[NB], accK[NB];
 #pragma unroll
@@ -508,26 +661,58 @@ __device__ __forceinline__ void rows_phase_b(const RowsArgs &A, const R *sU, con
       continue;
     }
     const int nent = ((nitems - ib) < 32 ? (nitems - ib) : 32) * NB;
-    if constexpr (DO_M) {
+    if constexpr (BULK) {
+      const int h = it % SUB, ib0 = ib - h * 32;  // sub-run h of the run starting at item ib0
+      float *gM = DO_M ? static_cast<float *>(A.M) + ochunk + (long long)ib0 * NB : nullptr;
+      float *gK = DO_K ? static_cast<float *>(A.K) + ochunk + (long long)ib0 * NB : nullptr;
+      float *sM = wst + (DO_M ? (int)(((uintptr_t)gM >> 2) & 3) : 0);
+      float *sK = wst + WSTB + (DO_K ? (int)(((uintptr_t)gK >> 2) & 3) : 0);
+      if (h == 0) {
+        if (lane == 0) bulk_wait_read();  // the previous run's copies have read the stage
+        __syncwarp();
+      }
       if (item < nitems) {
 #pragma unroll
-        for (int j = 0; j < NB; j++) wst[lane * NB + j] = oM[j];
+        for (int j = 0; j < NB; j++) {
+          if constexpr (DO_M) sM[(h * 32 + lane) * NB + j] = oM[j];
+          if constexpr (DO_K) sK[(h * 32 + lane) * NB + j] = oK[j];
+        }
       }
-      __syncwarp();
-      O *gM = static_cast<O *>(A.M) + ochunk + (long long)ib * NB;
-      for (int i = lane; i < nent; i += 32) gM[i] = r_out(wst[i]);
-      __syncwarp();
-    }
-    if constexpr (DO_K) {
-      if (item < nitems) {
+      if (h == SUB - 1 || ib + 32 >= nitems) {
+        const int nent = ((nitems - ib0) < 32 * SUB ? (nitems - ib0) : 32 * SUB) * NB;
+        fence_proxy_async();
+        __syncwarp();
+        if constexpr (DO_M) stage_out(gM, sM, nent, lane, 0, 1);
+        if constexpr (DO_K) stage_out(gK, sK, nent, lane, 0, 8);
+        if (lane == 0) bulk_commit();
+      }
+    } else {
+      if constexpr (DO_M) {
+        if (item < nitems) {
 #pragma unroll
-        for (int j = 0; j < NB; j++) wst[lane * NB + j] = oK[j];
+          for (int j = 0; j < NB; j++) wst[lane * NB + j] = oM[j];
+        }
+        __syncwarp();
+        O *gM = static_cast<O *>(A.M) + ochunk + (long long)ib * NB;
+        for (int i = lane; i < nent; i += 32) gM[i] = r_out(wst[i]);
+        __syncwarp();
       }
-      __syncwarp();
-      O *gK = static_cast<O *>(A.K) + ochunk + (long long)ib * NB;
-      for (int i = lane; i < nent; i += 32) gK[i] = r_out(wst[i]);
-      __syncwarp();
+      if constexpr (DO_K) {
+        if (item < nitems) {
+#pragma unroll
+          for (int j = 0; j < NB; j++) wst[lane * NB + j] = oK[j];
+        }
+        __syncwarp();
+        O *gK = static_cast<O *>(A.K) + ochunk + (long long)ib * NB;
+        for (int i = lane; i < nent; i += 32) gK[i] = r_out(wst[i]);
+        __syncwarp();
+      }
     }
+  }
+  // the stage is read before the caller may reuse the shared memory
+  if constexpr (BULK) {
+    if (lane == 0) bulk_wait_read();
+    __syncwarp();
   }
   if constexpr (APPLY) {
     // y of each row: the sum of its NPAIR fibre partials, formed by one warp
@@ -681,6 +866,7 @@ __device__ __forceinline__ void rows_block(const RowsArgs &A, const int bid, uns
     bad = __reduce_or_sync(0xffffffffu, bad);
     if (bad && lane == 0) atomicOr(A.status, 2u);
   }
+  cp_async_wait_all();  // the x1 tables
   __syncthreads();
 
   // ------------------------------------------------ phase A: U, two coefficient columns per warp

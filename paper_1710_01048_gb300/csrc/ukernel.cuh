@@ -32,6 +32,23 @@ namespace wq {
 #endif
 constexpr int kULines = 8, kUCols = WQ_UCOLS;
 
+// A table row of N values from shared memory into registers: as 16-byte
+// loads where the row is four floats (rows start on 16-byte boundaries),
+// else value by value.
+template <int N, typename R> __device__ __forceinline__ void load_row(R (&d)[N], const R *s) {
+  if constexpr (std::is_same<R, float>::value && N == 4) {
+    const float4 x = *reinterpret_cast<const float4 *>(s);
+    d[0] = x.x;
+    d[1] = x.y;
+    d[2] = x.z;
+    d[3] = x.w;
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; i++) d[i] = s[i];
+  }
+}
+template <typename R> __device__ __forceinline__ void load_row4(R (&d)[4], const R *s) { load_row<4>(d, s); }
+
 struct UArgs {
   const int *off[3][2];
   const int *elem[3][2];
@@ -63,7 +80,11 @@ template <int P, typename R> struct ULayout {
   // blocks, which then fall in disjoint shared-memory banks
   static constexpr int T3S = NL2 * NB + ((NB - NL2 * NB) % 32 + 32) % 32;
   static constexpr int T3 = pad16<R>(2 * kUCols * T3S);          // [k3][l1][l2][j3]
-  static constexpr int WST = pad16<R>(32 * NB);                // per-warp stage
+  // per-warp stage: float, one buffer per u written by bulk copies (a run of
+  // 32 items plus alignment slack); otherwise one buffer for both in turn
+  static constexpr bool BULK = std::is_same<R, float>::value;
+  static constexpr int WSTB = pad16<R>(32 * NB + 3);
+  static constexpr int WST = BULK ? 2 * WSTB : pad16<R>(32 * NB);
   static constexpr int R_TOTAL = V3 + B3 + V2 + B2 + CB + T3 + 8 * WST;
   // int region: e3[LM], o3[LM], L2[kULines], e2[kULines][LM], o2[kULines][LM]
   static constexpr int I_TOTAL = 2 * LM + kULines + 2 * kULines * LM;
@@ -106,23 +127,15 @@ __device__ __forceinline__ void u_block(const UArgs &A, int bid, unsigned char *
   // x3 rule of row r3
   const int off30 = A.off[2][0][r3], off31 = A.off[2][1][r3];
   const int L3 = A.off[2][0][r3 + 1] - off30;
-  for (int t = tid; t < 2 * LM; t += NT) {
-    const int kind = t / LM, q = t % LM;
-    if (q < L3) {
-      const int gq = (kind ? off31 : off30) + q;
-      const R *Vg = static_cast<const R *>(A.V[2][kind]);
-      const R *Bg = static_cast<const R *>(A.beta[2][kind]);
+  // (tables and the coefficient block by asynchronous copies, all in flight
+  // together; the offsets o = e - r + P are formed where they are used)
 #pragma unroll
-      for (int i = 0; i < NP; i++) sV3[(kind * LM + q) * NP + i] = Vg[(size_t)gq * NP + i];
-#pragma unroll
-      for (int i = 0; i < 4; i++) sB3[(kind * LM + q) * 4 + i] = Bg[(size_t)gq * 4 + i];
-      if (kind == 0) {
-        const int e = A.elem[2][0][gq];
-        sE3[q] = e;
-        sO3[q] = e - r3 + P;
-      }
-    }
+  for (int kind = 0; kind < 2; kind++) {
+    const int o = kind ? off31 : off30;
+    cp_async_n(&sV3[kind * LM * NP], static_cast<const R *>(A.V[2][kind]) + (size_t)o * NP, L3 * NP, tid, NT);
+    cp_async_n(&sB3[kind * LM * 4], static_cast<const R *>(A.beta[2][kind]) + (size_t)o * 4, L3 * 4, tid, NT);
   }
+  cp_async_n(sE3, A.elem[2][0] + off30, L3, tid, NT);
   // x2 rules of the block's lines
   for (int t = tid; t < kULines * 2 * LM; t += NT) {
     const int b = t / (2 * LM), kind = (t / LM) % 2, q = t % LM;
@@ -136,14 +149,10 @@ __device__ __forceinline__ void u_block(const UArgs &A, int bid, unsigned char *
         const R *Vg = static_cast<const R *>(A.V[1][kind]);
         const R *Bg = static_cast<const R *>(A.beta[1][kind]);
 #pragma unroll
-        for (int i = 0; i < NP; i++) sV2[((b * 2 + kind) * LM + q) * NP + i] = Vg[(size_t)gq * NP + i];
+        for (int i = 0; i < NP; i++) cp_async_el(&sV2[((b * 2 + kind) * LM + q) * NP + i], &Vg[(size_t)gq * NP + i]);
 #pragma unroll
-        for (int i = 0; i < 4; i++) sB2[((b * 2 + kind) * LM + q) * 4 + i] = Bg[(size_t)gq * 4 + i];
-        if (kind == 0) {
-          const int e = A.elem[1][0][gq];
-          sE2[b * LM + q] = e;
-          sO2[b * LM + q] = e - r2 + P;
-        }
+        for (int i = 0; i < 4; i++) cp_async_el(&sB2[((b * 2 + kind) * LM + q) * 4 + i], &Bg[(size_t)gq * 4 + i]);
+        if (kind == 0) cp_async_el(&sE2[b * LM + q], &A.elem[1][0][gq]);
       }
     }
   }
@@ -161,22 +170,22 @@ __device__ __forceinline__ void u_block(const UArgs &A, int bid, unsigned char *
       const int l1 = t % kUCols, l2 = (t / kUCols) % NL2, l3 = t / (kUCols * NL2);
       if (l1 < ncols && l2 < nl2 && l3 < nl3) {
         const long long g = (long long)(l1a + l1) + (long long)nc1 * ((long long)(l2lo + l2) + (long long)nc2 * (l3lo + l3));
-        R v;
+        R *dst = &sCb[(l1 * NL2 + l2) * NL3 + l3];
         if (cr) {
-          v = cr[g];
+          cp_async_el(dst, &cr[g]);
         } else if (cg) {
           const double x = cg[g];
           if (!isfinite(x)) bad = 1;
-          v = r_from_double<R>(x);
+          *dst = r_from_double<R>(x);
         } else {
-          v = r_from_double<R>(1.0);
+          *dst = r_from_double<R>(1.0);
         }
-        sCb[(l1 * NL2 + l2) * NL3 + l3] = v;
       }
     }
     bad = __reduce_or_sync(0xffffffffu, bad);
     if (bad && (tid & 31) == 0) atomicOr(A.status, 2u);
   }
+  cp_async_wait_all();
   __syncthreads();
 
   // x3 stage, once for the block: items (k3, l1, l2)
@@ -189,14 +198,19 @@ __device__ __forceinline__ void u_block(const UArgs &A, int bid, unsigned char *
 #pragma unroll
       for (int j = 0; j < NB; j++) acc[j] = r_zero<R>();
       if (in3) {
+        // interior plane: point q3 in element e0 + q3
+        const int e0 = sE3[0] - l3lo;
+        R c[NP + 3];
+#pragma unroll
+        for (int i = 0; i < NP + 3; i++) c[i] = cb[e0 + i];
 #pragma unroll
         for (int q3 = 0; q3 < NP; q3++) {
-          const int e = sE3[q3] - l3lo;
-          const R *bb = &sB3[(k3 * LM + q3) * 4];
+          R bb[4], v[NP];
+          load_row4(bb, &sB3[(k3 * LM + q3) * 4]);
+          load_row<NP>(v, &sV3[(k3 * LM + q3) * NP]);
           R z = r_zero<R>();
 #pragma unroll
-          for (int i = 0; i < 4; i++) z = r_fma(cb[e + i], bb[i], z);
-          const R *v = &sV3[(k3 * LM + q3) * NP];
+          for (int i = 0; i < 4; i++) z = r_fma(c[q3 + i], bb[i], z);
 #pragma unroll
           for (int i = 0; i < NP; i++) acc[q3 + i] = r_fma(z, v[i], acc[q3 + i]);
         }
@@ -207,7 +221,7 @@ __device__ __forceinline__ void u_block(const UArgs &A, int bid, unsigned char *
           R z = r_zero<R>();
 #pragma unroll
           for (int i = 0; i < 4; i++) z = r_fma(cb[e + i], bb[i], z);
-          fiber_shift<P>(acc, z, &sV3[(k3 * LM + q3) * NP], sO3[q3]);
+          fiber_shift<P>(acc, z, &sV3[(k3 * LM + q3) * NP], sE3[q3] - r3 + P);
         }
       }
 #pragma unroll
@@ -290,45 +304,55 @@ __device__ __forceinline__ void u_block(const UArgs &A, int bid, unsigned char *
           }
         }
       } else if (in2 && in3) {
-        // interior line: the row kernel's order, all q2 of (S, M) before (M, S)
+        // interior line: the row kernel's order, all q2 of (S, M) before (M, S);
+        // point q2 lies in element e0 + q2, so the item's T3 values are read
+        // once, and the line's tables row by row (16-byte loads in float)
+        const int e0 = sE2[b * LM] - l2lo;
+        R tm[NP + 3], ts[NP + 3];
+#pragma unroll
+        for (int i = 0; i < NP + 3; i++) {
+          tm[i] = t3m[(e0 + i) * NB];
+          ts[i] = t3s[(e0 + i) * NB];
+        }
         R c0[NP], c1[NP], c2[NP];
 #pragma unroll
         for (int q2 = 0; q2 < NP; q2++) {
-          const int e = sE2[b * LM + q2] - l2lo;
-          const R *bm = &b2[(0 * LM + q2) * 4], *bs = &b2[(1 * LM + q2) * 4];
+          R bm[4], bs[4];
+          load_row4(bm, &b2[(0 * LM + q2) * 4]);
+          load_row4(bs, &b2[(1 * LM + q2) * 4]);
           R s0 = r_zero<R>(), s1 = r_zero<R>(), s2 = r_zero<R>();
 #pragma unroll
           for (int i = 0; i < 4; i++) {
-            s0 = r_fma(t3m[(e + i) * NB], bm[i], s0);
-            s1 = r_fma(t3m[(e + i) * NB], bs[i], s1);
-            s2 = r_fma(t3s[(e + i) * NB], bm[i], s2);
+            s0 = r_fma(tm[q2 + i], bm[i], s0);
+            s1 = r_fma(tm[q2 + i], bs[i], s1);
+            s2 = r_fma(ts[q2 + i], bm[i], s2);
           }
           c0[q2] = s0;
           c1[q2] = s1;
           c2[q2] = s2;
         }
+        R vm[NP][NP], vs[NP][NP];
 #pragma unroll
         for (int q2 = 0; q2 < NP; q2++) {
-          const R *vm = &v2[(0 * LM + q2) * NP];
-#pragma unroll
-          for (int i = 0; i < NP; i++) u0[q2 + i] = r_fma(c0[q2], vm[i], u0[q2 + i]);
+          load_row<NP>(vm[q2], &v2[(0 * LM + q2) * NP]);
+          load_row<NP>(vs[q2], &v2[(1 * LM + q2) * NP]);
         }
 #pragma unroll
-        for (int q2 = 0; q2 < NP; q2++) {
-          const R *vs = &v2[(1 * LM + q2) * NP];
+        for (int q2 = 0; q2 < NP; q2++)
 #pragma unroll
-          for (int i = 0; i < NP; i++) u1[q2 + i] = r_fma(c1[q2], vs[i], u1[q2 + i]);
-        }
+          for (int i = 0; i < NP; i++) u0[q2 + i] = r_fma(c0[q2], vm[q2][i], u0[q2 + i]);
 #pragma unroll
-        for (int q2 = 0; q2 < NP; q2++) {
-          const R *vm = &v2[(0 * LM + q2) * NP];
+        for (int q2 = 0; q2 < NP; q2++)
 #pragma unroll
-          for (int i = 0; i < NP; i++) u1[q2 + i] = r_fma(c2[q2], vm[i], u1[q2 + i]);
-        }
+          for (int i = 0; i < NP; i++) u1[q2 + i] = r_fma(c1[q2], vs[q2][i], u1[q2 + i]);
+#pragma unroll
+        for (int q2 = 0; q2 < NP; q2++)
+#pragma unroll
+          for (int i = 0; i < NP; i++) u1[q2 + i] = r_fma(c2[q2], vm[q2][i], u1[q2 + i]);
       } else {
         // boundary line: per point, (S, M) then (M, S)
         for (int q2 = 0; q2 < L2; q2++) {
-          const int e = sE2[b * LM + q2] - l2lo, o = sO2[b * LM + q2];
+          const int e = sE2[b * LM + q2] - l2lo, o = sE2[b * LM + q2] - r2 + P;
           const R *bm = &b2[(0 * LM + q2) * 4], *bs = &b2[(1 * LM + q2) * 4];
           R s0 = r_zero<R>(), s1 = r_zero<R>(), s2 = r_zero<R>();
 #pragma unroll
@@ -345,17 +369,43 @@ __device__ __forceinline__ void u_block(const UArgs &A, int bid, unsigned char *
     }
     // U[line][u][l1][j3*NB+j2]: contiguous from column l1a, item i0 onwards
     const int nent = ((nitem - i0) < 32 ? (nitem - i0) : 32) * NB;
+    if constexpr (L::BULK) {
+      // both runs staged, written by bulk copies (lane 0) and plain stores of
+      // their unaligned ends; the previous runs' copies have read the stage
+      if (lane == 0) bulk_wait_read();
+      __syncwarp();
+      float *dst[2], *st[2];
 #pragma unroll
-    for (int u = 0; u < 2; u++) {
-      if (ok) {
+      for (int u = 0; u < 2; u++) {
+        dst[u] = Ug + (((size_t)(lid0 + b) * 2 + u) * nc1 + l1a) * NPAIR + (size_t)i0 * NB;
+        st[u] = wst + u * L::WSTB + (int)(((uintptr_t)dst[u] >> 2) & 3);
+        if (ok) {
 #pragma unroll
-        for (int j = 0; j < NB; j++) wst[lane * NB + j] = u ? u1[j] : u0[j];
+          for (int j = 0; j < NB; j++) st[u][lane * NB + j] = u ? u1[j] : u0[j];
+        }
       }
+      fence_proxy_async();
       __syncwarp();
-      R *dst = Ug + (((size_t)(lid0 + b) * 2 + u) * nc1 + l1a) * NPAIR + (size_t)i0 * NB;
-      for (int e = lane; e < nent; e += 32) dst[e] = wst[e];
-      __syncwarp();
+      stage_out(dst[0], st[0], nent, lane, 0, 1);
+      stage_out(dst[1], st[1], nent, lane, 0, 8);
+      if (lane == 0) bulk_commit();
+    } else {
+#pragma unroll
+      for (int u = 0; u < 2; u++) {
+        if (ok) {
+#pragma unroll
+          for (int j = 0; j < NB; j++) wst[lane * NB + j] = u ? u1[j] : u0[j];
+        }
+        __syncwarp();
+        R *dst = Ug + (((size_t)(lid0 + b) * 2 + u) * nc1 + l1a) * NPAIR + (size_t)i0 * NB;
+        for (int e = lane; e < nent; e += 32) dst[e] = wst[e];
+        __syncwarp();
+      }
     }
+  }
+  if constexpr (L::BULK) {
+    if (lane == 0) bulk_wait_read();  // the stage is read before the CTA's shared memory is released
+    __syncwarp();
   }
 }
 
@@ -378,7 +428,7 @@ template <int P, int TMAX, bool DO_M, bool DO_K, typename R> struct RowsLayoutUG
   static constexpr int V1 = pad16<R>(2 * MAXPTS1 * NP);
   static constexpr int B1 = pad16<R>(2 * MAXPTS1 * 4);
   static constexpr int US = pad16<R>(NU * NL1 * NPAIR);
-  static constexpr int STAGE = NW * pad16<R>(32 * NB);
+  static constexpr int STAGE = NW * stage_per_warp<R, NB, false>();
   static constexpr int R_TOTAL = V1 + B1 + US + STAGE;
   static constexpr int I_TOTAL = MAXPTS1 + TMAX + 1;
   static constexpr size_t BYTES = sizeof(R) * (size_t)R_TOTAL + sizeof(int) * (size_t)I_TOTAL;
@@ -415,11 +465,9 @@ __device__ __forceinline__ void rows_ug_block(const RowsArgs &A, int bid, unsign
   const R *Ug = static_cast<const R *>(A.Ug);
   const int nc1 = A.nc[0];
 #pragma unroll
-  for (int u = 0; u < L::NU; u++) {
-    const R *src = Ug + (((size_t)line * 2 + u) * nc1 + l1lo) * NPAIR;
-    R *dst = sU + u * NL1 * NPAIR;
-    for (int i = tid; i < nl1 * NPAIR; i += NT) dst[i] = src[i];
-  }
+  for (int u = 0; u < L::NU; u++)
+    cp_async_n(sU + u * NL1 * NPAIR, Ug + (((size_t)line * 2 + u) * nc1 + l1lo) * NPAIR, nl1 * NPAIR, tid, NT);
+  cp_async_wait_all();
   __syncthreads();
   rows_phase_b<P, 3, L::MAXPTS1, NL1, false, DO_M, DO_K, R>(A, sU, sV1, sB1, sE1, sOff1, sW, a, T, l1lo, base);
 }
@@ -530,12 +578,10 @@ __device__ __forceinline__ void apply_ug_block(const RowsArgs &A, int bid, unsig
   const R *Ug = static_cast<const R *>(A.Ug);
   const int nc1 = A.nc[0];
 #pragma unroll
-  for (int u = 0; u < L::NU; u++) {
-    const R *src = Ug + (((size_t)line * 2 + u) * nc1 + l1lo) * NPAIR;
-    R *dst = sU + u * NL1 * NPAIR;
-    for (int i = tid; i < nl1 * NPAIR; i += NT) dst[i] = src[i];
-  }
+  for (int u = 0; u < L::NU; u++)
+    cp_async_n(sU + u * NL1 * NPAIR, Ug + (((size_t)line * 2 + u) * nc1 + l1lo) * NPAIR, nl1 * NPAIR, tid, NT);
   stage_x<P, 3, XL>(A, line, a, T, sX);
+  cp_async_wait_all();
   __syncthreads();
   rows_phase_b<P, 3, L::MAXPTS1, NL1, false, DO_M, DO_K, R, true>(A, sU, sV1, sB1, sE1, sOff1, sP, a, T, l1lo,
                                                                     base, sX);

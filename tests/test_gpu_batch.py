@@ -152,3 +152,16 @@ def test_batch_256_patches(prec):
     B.check()
     assert_matches_single(patches, prec)
     B.close()
+
+
+def test_batch_equals_fused_mixed_on_long_lines():
+    # the mixed-mode single calls run the fused kernel (several 32-row chunks
+    # per line, edge rows apart); the batch runs the split kernels; both form
+    # every value with the same operations in the same order
+    specs = [(3, (70, 5, 4)), (2, (66, 3, 4)), (3, (97, 2, 3)), (2, (33, 4, 2))]
+    patches, _ = make_patches(specs, "mixed", seed=9)
+    B = wq.Batch(patches, "mixed")
+    B.launch()
+    B.check()
+    assert_matches_single(patches, "mixed")
+    B.close()
