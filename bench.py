@@ -327,18 +327,6 @@ def main():
     # coefficient check/convert + fold + partial contractions + rows per step
     gpu_launches = 4 * args.steps
 
-    # the oracle's sampled rows (rank 0 at N = 1): CPU baseline and the
-    # accuracy of every precision on those rows
-    sample = None
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        secs, snnz, srows, outs = run_oracle_sample(w, g, c, args.cpu_stride)
-        sample = outs
-        cpu = {"value": snnz / secs, "unit": "nnz/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{len(outs)} slabs of rows along x3 (every {args.cpu_stride}th; {srows} of {R.rows} "
-                         f"rows, {snnz} non-zeros of M and K), {secs:.1f} s wall; the rate is the sample's"}
-    accuracy = errors_vs_oracle((M, K), sample) if sample else None
-
     # ------------------------------------------------------------ end to end through host buffers
     e2e = None
     if not args.no_e2e:
@@ -364,6 +352,18 @@ def main():
             raise RuntimeError("end-to-end bands differ from the device bands")
         e2e = {"ms_per_step": e2e_ms, "h2d": h2d, "d2h": d2h}
         del Mh, Kh, gh, ch, gdd, cdd
+
+    # the oracle's sampled rows (rank 0 at N = 1): CPU baseline and the
+    # accuracy of every precision on those rows
+    sample = None
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        secs, snnz, srows, outs = run_oracle_sample(w, g, c, args.cpu_stride)
+        sample = outs
+        cpu = {"value": snnz / secs, "unit": "nnz/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{len(outs)} slabs of rows along x3 (every {args.cpu_stride}th; {srows} of {R.rows} "
+                         f"rows, {snnz} non-zeros of M and K), {secs:.1f} s wall; the rate is the sample's"}
+    accuracy = errors_vs_oracle((M, K), sample) if sample else None
 
     # max over ranks
     if dist is not None:
@@ -558,10 +558,16 @@ def run_variants(args, wq, inputs, R, w, g, gd, cd, bands, sample, timed, stream
             fn()
         vm = float(np.mean(timed(fn, max(3, min(args.steps, 5)))))
         fl, _ = R3.flops()
-        # per step the adjoint reads both weight bands: report band entries per second
+        # per step the adjoint reads both weight bands (band entries per
+        # second); its transposed stages do the forward contraction's
+        # multiply-adds, counted as its algorithmic flops
+        pk = {"fp64": FP64_PEAK_TFLOPS, "df64": DF64_PEAK_TFLOPS, "mixed": FP32_PEAK_TFLOPS}[vp]
+        tf = fl / (vm * 1e-3) / 1e12
         adj[vp] = {"ms_per_step": vm, "value": 2 * R3.nnz / (vm * 1e-3), "unit": "nnz/s (weights read)",
                    "weights_gb_s": 2 * R3.rows * R3.band * G.element_size() / (vm * 1e-3) / 1e9,
-                   "forward_flops_per_ms": fl / vm}
+                   "roofline": {"bound": "alu", "achieved": tf, "peak": pk, "unit": "TFLOP/s", "frac": tf / pk,
+                                "flops_per_gradient": fl,
+                                "weight_bytes_per_gradient": 2 * R3.rows * R3.band * G.element_size()}}
         del G, H, grad
         torch.cuda.empty_cache()
     st = wq.wq_status_check(R3.handle, wq._stream_handle(stream))

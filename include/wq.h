@@ -282,10 +282,15 @@ wq_status wq_assemble_load(const wq_rules *rules, const double *const *geom, con
  *   G, H       device band arrays laid out like K and M of those rows (double
  *              for WQ_FP64 and WQ_DF64, float for WQ_MIXED); either may be
  *              NULL (a zero weight);
- *   grad       device, prod(nel_a + 3) doubles, x fastest; overwritten (it is
- *              cleared on `stream`, then accumulated with atomic adds, so the
- *              summation order, and the last bits of the result, may change
- *              from call to call).
+ *   grad       device, prod(nel_a + 3) doubles, x fastest; overwritten.
+ * Each chunk of rows writes its block of the gradient to its own slot of a
+ * scratch array; a second kernel then sums, for every coefficient, the blocks
+ * of the chunks that touch it in a fixed order, so repeated calls on the same
+ * inputs return the same bits.  The scratch (FP64, about 50 values per row
+ * of a 3D cubic mesh) belongs to the rules object: the first call that needs
+ * it allocates it, a later call with more rows or other chunking may replace
+ * it (synchronising `stream` first), and wq_rules_free releases it; the call
+ * returns WQ_ERR_OOM if that allocation fails.
  * The same row-range, device and stream rules as the forward calls apply;
  * an empty range, or G and H both NULL, gives grad = 0.
  */

@@ -13,7 +13,11 @@
 //      consecutive rows and keeps its columns in registers, and the threads'
 //      windows are added to Ubar in three ordered rounds.
 //   2. x2 then x3 stages transposed, one warp per coefficient column, giving
-//      the chunk's block of dJ/dC, added to the gradient in global memory.
+//      the chunk's block of dJ/dC, stored in the chunk's own slot of a
+//      scratch array ([l3][l2][l1] from the block's first coefficient).
+// adjoint_gather_kernel then forms each coefficient's gradient as the sum of
+// the blocks of the chunks that touch it, in a fixed order (x3 row, x2 row,
+// chunk), so the result does not depend on the order in which CTAs ran.
 #pragma once
 
 #include "assemble.cuh"
@@ -23,7 +27,22 @@ namespace wq {
 struct AdjArgs {
   RowsArgs rows;         // tables, sizes, row range, line list, chunking (M, K, coef unused)
   const void *G, *H;     // band weights, OutT<R>, rows [row_begin, row_end); either may be null
-  double *grad;          // prod(nel_a + 3) coefficients, accumulated into
+  double *partial;       // chunk blocks: slot (line * nch_max + chunk) of blk values
+  int nch_max, nl1max;   // slots per line; the l1 extent of a block
+  long long blk;         // values per slot: NL * NL * nl1max (3D), NL * nl1max (2D)
+};
+
+// The chunks of a line: its class's chunk length T (rows per chunk), clipped
+// to the call's rows, as the adjoint (and forward) kernels cut them.
+struct GatherArgs {
+  const double *partial;
+  double *grad;  // prod(nc_a) coefficients, overwritten
+  int dim, p;
+  int n[3], N[3], nc[3];
+  long long row_begin, row_end;
+  int T_int, T_bnd;  // chunk lengths of interior and boundary lines
+  int nch_max, nl1max;
+  long long blk;
 };
 
 template <int P, int D, int LM, int TMAX, typename R>
@@ -265,6 +284,8 @@ __global__ void __launch_bounds__(32 * kRowsWarps, adj_min_blocks<R>()) adjoint_
   }
 
   // ------------------------------------------------ 2. x2, x3 stages transposed, warp per column
+  // this chunk's slot of the block scratch
+  const long long chunk_slot = ((long long)line * AA.nch_max + ch) * AA.blk;
   R *wq = sW + warp * L::WS;  // Cqbar
   R *wt = wq + L::WQ;         // T3bar
   R *wz = wt + L::WT;         // Zbar
@@ -351,9 +372,7 @@ __global__ void __launch_bounds__(32 * kRowsWarps, adj_min_blocks<R>()) adjoint_
         const int t = lane + 32 * s2;
         const int l3 = t % NL, l2 = t / NL;
         if (t < NL * NL && l2 < nl2 && l3 < nl3) {
-          const long long g = (long long)(l1lo + l1) +
-                              (long long)A.nc[0] * ((long long)(l23lo[0] + l2) + (long long)A.nc[1] * (l23lo[1] + l3));
-          atomicAdd(&AA.grad[g], r_to_double(cb[s2]));
+          AA.partial[chunk_slot + ((long long)l3 * NL + l2) * AA.nl1max + l1] = r_to_double(cb[s2]);
         }
       }
     } else {
@@ -386,8 +405,7 @@ __global__ void __launch_bounds__(32 * kRowsWarps, adj_min_blocks<R>()) adjoint_
             s = r_fma(wq[1 * LM + q2], sB23[(1 * LM + q2) * 4 + i], s);
           }
         }
-        const long long g = (long long)(l1lo + l1) + (long long)A.nc[0] * (long long)(l23lo[0] + l2);
-        atomicAdd(&AA.grad[g], r_to_double(s));
+        AA.partial[chunk_slot + (long long)l2 * AA.nl1max + l1] = r_to_double(s);
       }
       (void)cb;
     }

@@ -70,6 +70,63 @@ __global__ void coef_prepare_kernel(const double *__restrict__ c, size_t n, int 
   if (bad && (threadIdx.x & 31) == 0) atomicOr(status, wq::kBitNonFinite);
 }
 
+// dJ/dC of every coefficient: the sum, over the lines (x3 row ascending,
+// then x2 row) and chunks (ascending) whose coefficient block contains it,
+// of that block's entry.  One thread per coefficient.
+__global__ void adjoint_gather_kernel(const wq::GatherArgs G) {
+  const long long ncoef = (long long)G.nc[0] * G.nc[1] * G.nc[2];
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= ncoef) return;
+  const int P = G.p, NL = P + 4;
+  const int c1 = (int)(g % G.nc[0]);
+  const int c2 = (int)((g / G.nc[0]) % G.nc[1]);
+  const int c3 = G.dim == 3 ? (int)(g / ((long long)G.nc[0] * G.nc[1])) : 0;
+  const int n1 = G.n[0], N1 = G.N[0];
+  double s = 0.0;
+  const int r3lo = G.dim == 3 ? (c3 - 3 > 0 ? c3 - 3 : 0) : 0;
+  const int r3hi = G.dim == 3 ? (c3 + P < G.n[2] - 1 ? c3 + P : G.n[2] - 1) : 0;
+  for (int r3 = r3lo; r3 <= r3hi; r3++) {
+    int e3lo = 0;
+    bool in3 = true;
+    if (G.dim == 3) {
+      e3lo = r3 - P > 0 ? r3 - P : 0;
+      const int e3hi = r3 < G.N[2] - 1 ? r3 : G.N[2] - 1;
+      if (c3 < e3lo || c3 > e3hi + 3) continue;
+      in3 = r3 >= P && r3 <= G.N[2] - 1;
+    }
+    const int r2lo = c2 - 3 > 0 ? c2 - 3 : 0, r2hi = c2 + P < G.n[1] - 1 ? c2 + P : G.n[1] - 1;
+    for (int r2 = r2lo; r2 <= r2hi; r2++) {
+      const int e2lo = r2 - P > 0 ? r2 - P : 0;
+      const int e2hi = r2 < G.N[1] - 1 ? r2 : G.N[1] - 1;
+      if (c2 < e2lo || c2 > e2hi + 3) continue;
+      const bool in2 = r2 >= P && r2 <= G.N[1] - 1;
+      const int T = (in2 && in3) ? G.T_int : G.T_bnd;
+      const int nch = (n1 + T - 1) / T;
+      const long long line = (long long)r2 + (long long)G.n[1] * r3;
+      const long long base = line * n1;
+      int chlo = (c1 - 2) / T - 1, chhi = (c1 + P) / T;
+      if (chlo < 0) chlo = 0;
+      if (chhi > nch - 1) chhi = nch - 1;
+      for (int ch = chlo; ch <= chhi; ch++) {
+        long long lo = (long long)ch * T, hi = lo + T;
+        if (hi > n1) hi = n1;
+        if (lo < G.row_begin - base) lo = G.row_begin - base;
+        if (hi > G.row_end - base) hi = G.row_end - base;
+        if (lo >= hi) continue;
+        const int a = (int)lo, b = (int)hi;
+        const int l1lo = a - P > 0 ? a - P : 0;
+        const int e1hi = (b - 1) < N1 - 1 ? (b - 1) : N1 - 1;
+        if (c1 < l1lo || c1 > e1hi + 3) continue;
+        const long long slot = (line * G.nch_max + ch) * G.blk;
+        const long long ent = G.dim == 3 ? ((long long)(c3 - e3lo) * NL + (c2 - e2lo)) * G.nl1max + (c1 - l1lo)
+                                         : (long long)(c2 - e2lo) * G.nl1max + (c1 - l1lo);
+        s += G.partial[slot + ent];
+      }
+    }
+  }
+  G.grad[g] = s;
+}
+
 wq_status upload(wq_rules *R) {
   // fault injection for callers' error paths: the device allocation fails
   if (std::getenv("WQ_FAULT_DEVICE_ALLOC")) return WQ_ERR_OOM;
@@ -520,6 +577,7 @@ void wq_rules_free(wq_rules *rules) {
     if (cur != rules->device) cudaSetDevice(rules->device);
     cudaFree(rules->dev_block);
     if (rules->dev_U) cudaFree(rules->dev_U);
+    if (rules->dev_adj) cudaFree(rules->dev_adj);
     if (cur >= 0 && cur != rules->device) cudaSetDevice(cur);
   }
   delete rules;
@@ -672,8 +730,32 @@ wq_status wq_assemble_adjoint(const wq_rules *R, const double *const *geom, wq_p
   if (cudaGetDevice(&dev) != cudaSuccess || dev != R->device) return WQ_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t ncoef = (size_t)R->nc[0] * R->nc[1] * R->nc[2];
-  if (cudaMemsetAsync(grad, 0, ncoef * sizeof(double), s) != cudaSuccess) return WQ_ERR_CUDA;
-  if (row_begin == row_end || (!G && !H)) return WQ_OK;
+  if (row_begin == row_end || (!G && !H))
+    return cudaMemsetAsync(grad, 0, ncoef * sizeof(double), s) == cudaSuccess ? WQ_OK : WQ_ERR_CUDA;
+  // the chunking of both line classes, and the block scratch it needs
+  const int eb = prec == WQ_MIXED ? 4 : 8, n1 = R->n[0], p = R->p;
+  const int T_int = wq::chunk_length(R, wq::interior_chunk(p, eb));
+  const int T_bnd = wq::chunk_length(R, wq::kBoundaryChunk);
+  const int nch_max = std::max((n1 + T_int - 1) / T_int, (n1 + T_bnd - 1) / T_bnd);
+  const int nl1max = std::max(T_int, T_bnd) + p + 3, NL = p + 4;
+  const long long blk = (long long)(R->dim == 3 ? NL * NL : NL) * nl1max;
+  const size_t nlines = (size_t)R->n[1] * R->n[2];
+  const size_t need = nlines * nch_max * (size_t)blk * sizeof(double);
+  if (need > R->dev_adj_bytes) {
+    // grown, never shrunk; the previous contents are not needed
+    if (R->dev_adj && cudaStreamSynchronize(s) != cudaSuccess) return WQ_ERR_CUDA;
+    if (R->dev_adj) cudaFree(R->dev_adj);
+    R->dev_adj = nullptr;
+    R->dev_adj_bytes = 0;
+    void *p_adj = nullptr;
+    const cudaError_t e = cudaMalloc(&p_adj, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? WQ_ERR_OOM : WQ_ERR_CUDA;
+    }
+    R->dev_adj = static_cast<double *>(p_adj);
+    R->dev_adj_bytes = need;
+  }
   wq_status st = launch_fold(R, geom, s);
   if (st != WQ_OK) return st;
   wq::AdjArgs aa;
@@ -684,10 +766,13 @@ wq_status wq_assemble_adjoint(const wq_rules *R, const double *const *geom, wq_p
   aa.rows.status = R->dev_status;
   aa.G = G;
   aa.H = H;
-  aa.grad = grad;
+  aa.partial = R->dev_adj;
+  aa.nch_max = nch_max;
+  aa.nl1max = nl1max;
+  aa.blk = blk;
   for (int cls = 0; cls < 2; cls++) {
     wq_status cst = WQ_OK;
-    const int nblocks = chunk_class(R, cls, prec == WQ_MIXED ? 4 : 8, row_begin, row_end, aa.rows, &cst);
+    const int nblocks = chunk_class(R, cls, eb, row_begin, row_end, aa.rows, &cst);
     if (cst != WQ_OK) return cst;
     if (nblocks == 0) continue;
     cudaError_t e;
@@ -701,7 +786,26 @@ wq_status wq_assemble_adjoint(const wq_rules *R, const double *const *geom, wq_p
                              : wq::launch_adjoint<3, wq::dd>(R->dim, cls, aa, nblocks, s);
     if (e != cudaSuccess) return WQ_ERR_CUDA;
   }
-  return WQ_OK;
+  wq::GatherArgs ga;
+  std::memset(&ga, 0, sizeof(ga));
+  ga.partial = R->dev_adj;
+  ga.grad = grad;
+  ga.dim = R->dim;
+  ga.p = p;
+  for (int a = 0; a < 3; a++) {
+    ga.n[a] = R->n[a];
+    ga.N[a] = R->nel[a];
+    ga.nc[a] = R->nc[a];
+  }
+  ga.row_begin = row_begin;
+  ga.row_end = row_end;
+  ga.T_int = T_int;
+  ga.T_bnd = T_bnd;
+  ga.nch_max = nch_max;
+  ga.nl1max = nl1max;
+  ga.blk = blk;
+  adjoint_gather_kernel<<<(unsigned)((ncoef + 255) / 256), 256, 0, s>>>(ga);
+  return check_launch(cudaGetLastError());
 }
 
 wq_status wq_status_check(const wq_rules *R, void *stream) {

@@ -12,9 +12,9 @@
 
 namespace wq {
 
-// Writes point q's p+1 folded values in FP64, FP32 and double-float form and
-// returns the status bits it raises (geometry where J_aa <= 0, non-finite
-// where J_aa is NaN or Inf).
+// Writes point q's p+1 folded values in FP64, FP32 and (unless vdd is null)
+// double-float form and returns the status bits it raises (geometry where
+// J_aa <= 0, non-finite where J_aa is NaN or Inf).
 __device__ __forceinline__ unsigned fold_point(int q, int np, int kind, const int *elem, const double *w,
                                                const double *t0, const double *t1, const double *g, double *v64,
                                                float *v32, float2 *vdd) {
@@ -31,7 +31,7 @@ __device__ __forceinline__ unsigned fold_point(int q, int np, int kind, const in
     const float vh = (float)v;
     v64[(size_t)q * np + i] = v;
     v32[(size_t)q * np + i] = vh;
-    vdd[(size_t)q * np + i] = make_float2(vh, (float)(v - (double)vh));
+    if (vdd) vdd[(size_t)q * np + i] = make_float2(vh, (float)(v - (double)vh));
   }
   return bits;
 }

@@ -14,6 +14,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "fold.cuh"
 #include "launch.cuh"
 #include "wq_internal.h"
 
@@ -102,8 +103,10 @@ struct NaFoldArgs {
 };
 
 // The geometry-factor fold (mass kind: W |J_aa| B; stiffness kind:
-// W / |J_aa| B') into the scratch, plus the float copy of the coefficient
-// spline values the mixed mode reads.
+// W / |J_aa| B') into the scratch through wq::fold_point (FP64 and float
+// tables, the arithmetic of the ordinary fold), plus the float copy of the
+// cubic B-spline values at the points (beta) that the mixed mode reads; the
+// coefficients themselves are converted by the row kernel.
 __global__ void fold_noalloc_kernel(const NaFoldArgs A) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   unsigned bits = 0;
@@ -111,19 +114,8 @@ __global__ void fold_noalloc_kernel(const NaFoldArgs A) {
     int s = 0;
     while (s + 1 < A.nseg && t >= A.seg[s + 1].start) s++;
     const NaSeg &S = A.seg[s];
-    const int q = t - S.start, np = A.np;
-    const int e = S.elem[q];
-    double J = 0.0;
-    for (int i = 0; i < np; i++) J = fma(S.g[e + i], S.t1[(size_t)q * np + i], J);
-    if (!(J > 0.0)) bits |= isfinite(J) ? wq::kBitGeometry : wq::kBitNonFinite;
-    const double aj = fabs(J);
-    const double f = S.kind == WQ_KIND_MASS ? S.w[q] * aj : S.w[q] / aj;
-    const double *T = S.kind == WQ_KIND_MASS ? S.t0 : S.t1;
-    for (int i = 0; i < np; i++) {
-      const double v = f * T[(size_t)q * np + i];
-      S.v64[(size_t)q * np + i] = v;
-      S.v32[(size_t)q * np + i] = (float)v;
-    }
+    const int q = t - S.start;
+    bits = wq::fold_point(q, A.np, S.kind, S.elem, S.w, S.t0, S.t1, S.g, S.v64, S.v32, nullptr);
     for (int i = 0; i < 4; i++) S.beta32[(size_t)q * 4 + i] = (float)S.beta[(size_t)q * 4 + i];
   }
   bits = __reduce_or_sync(0xffffffffu, bits);

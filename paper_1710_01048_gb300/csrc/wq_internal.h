@@ -93,6 +93,10 @@ struct wq_rules {
   float2 *dev_coefdd = nullptr;  // the coefficients as double-float pairs (df64 mode)
   void *dev_U = nullptr;         // 3D: the partial contractions U of every line, [line][2][nc1][(2p+1)^2], 8-byte
                                  // elements (the split assembly path; its own allocation)
+  // the adjoint's per-chunk coefficient blocks (FP64), allocated by the first
+  // wq_assemble_adjoint call that needs them and grown when a call needs more
+  mutable double *dev_adj = nullptr;
+  mutable size_t dev_adj_bytes = 0;
 };
 
 namespace wq {

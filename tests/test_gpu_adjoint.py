@@ -196,3 +196,31 @@ def test_finite_differences_96():
     g64 = wq.assemble_adjoint(R, gd, G, H, "df64")
     assert (g64 - grad).abs().max().item() <= FP64_TOL * grad.abs().max().item()
     R.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64", "mixed"])
+def test_gradient_is_bitwise_repeatable(prec):
+    # the chunk blocks are summed in a fixed order: calls on the same inputs
+    # give the same bits, over the whole mesh and over a row range whose
+    # first and last lines are cut
+    p, nel = 3, (23, 9, 8)
+    g, _ = inputs.make(3, p, nel, 0.05, "one")
+    R = wq.Rules(3, p, nel)
+    dt = torch.float32 if prec == "mixed" else torch.float64
+    gd = [torch.from_numpy(x).cuda() for x in g]
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    G = torch.randn((R.rows, R.band), dtype=dt, device="cuda", generator=gen)
+    H = torch.randn((R.rows, R.band), dtype=dt, device="cuda", generator=gen)
+    for rb, re in ((0, R.rows), (37, R.rows - 101)):
+        first = wq.assemble_adjoint(R, gd, G[rb:re].contiguous(), H[rb:re].contiguous(), prec, rb, re)
+        for _ in range(3):
+            again = wq.assemble_adjoint(R, gd, G[rb:re].contiguous(), H[rb:re].contiguous(), prec, rb, re)
+            assert torch.equal(first, again)
+    # the row-range gradients add up to the whole mesh's (up to rounding)
+    full = wq.assemble_adjoint(R, gd, G, H, prec)
+    cut = R.rows // 3
+    a = wq.assemble_adjoint(R, gd, G[:cut].contiguous(), H[:cut].contiguous(), prec, 0, cut)
+    b = wq.assemble_adjoint(R, gd, G[cut:].contiguous(), H[cut:].contiguous(), prec, cut, R.rows)
+    tol = MIXED_TOL if prec == "mixed" else FP64_TOL
+    assert rel_max((a + b).cpu().numpy(), full.cpu().numpy()) <= tol
+    R.close()

@@ -151,13 +151,28 @@ def test_batch_256_patches(prec):
     B.launch()
     B.check()
     assert_matches_single(patches, prec)
+    # a seeded sample of the patches against the oracle: three x3 slabs of
+    # rows each (first, middle, last), every row of the slab
+    tol = 1e-6 if prec == "mixed" else 1e-12
+    rng = np.random.default_rng(256)
+    for k in rng.choice(len(specs), size=6, replace=False):
+        s = specs[int(k)]
+        R, _, _, M, K = patches[int(k)]
+        n = [v + s["p"] for v in s["nel"]]
+        slab = n[0] * n[1]
+        for z in (0, n[2] // 2, n[2] - 1):
+            rb, re = z * slab, (z + 1) * slab
+            Mo, Ko, _ = oracle.assemble(3, s["p"], s["nel"], s["geom"], s["coef"], rb, re)
+            for A, O in ((M, Mo), (K, Ko)):
+                d = A[rb:re].double().cpu().numpy() - O
+                assert np.max(np.abs(d)) <= tol * np.max(np.abs(O)), (k, z)
+                assert np.linalg.norm(d) <= tol * np.linalg.norm(O), (k, z)
     B.close()
 
 
-def test_batch_equals_fused_mixed_on_long_lines():
-    # the mixed-mode single calls run the fused kernel (several 32-row chunks
-    # per line, edge rows apart); the batch runs the split kernels; both form
-    # every value with the same operations in the same order
+def test_batch_equals_single_calls_mixed_on_long_lines():
+    # lines of several row chunks, in FP32: the persistent batch launches and
+    # the per-mesh launches run the same block code, so the bits agree
     specs = [(3, (70, 5, 4)), (2, (66, 3, 4)), (3, (97, 2, 3)), (2, (33, 4, 2))]
     patches, _ = make_patches(specs, "mixed", seed=9)
     B = wq.Batch(patches, "mixed")

@@ -270,3 +270,24 @@ def test_assemble_to_host_arguments():
         wq.WQ_ERR_ARG
     assert call(R.handle, hp, None, wq.WQ_FP64, None, None, dp, None, None, None, 3, 3, 2, ss, other) == wq.WQ_OK
     R.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64", "mixed"])
+def test_plane_shards_equal_whole_mesh(prec):
+    # the row slabs that ranks take (cut at x3 planes) assembled one by one
+    # reproduce the whole mesh's bands bit for bit
+    from paper_1710_01048_gb300 import shard
+
+    p, nel = 3, (9, 7, 8)
+    g, c = inputs.make(3, p, nel, 0.05, "exp", 0.1, seed=31)
+    R = wq.Rules(3, p, nel)
+    gd = [torch.from_numpy(x).cuda() for x in g]
+    cd = torch.from_numpy(c).cuda()
+    M, K = wq.assemble(R, gd, cd, prec)
+    n = [v + p for v in nel]
+    for world in (2, 3, 5):
+        for rank in range(world):
+            rb, re = shard.shard_rows(n, rank, world)
+            Ms, Ks = wq.assemble(R, gd, cd, prec, row_begin=rb, row_end=re)
+            assert torch.equal(Ms, M[rb:re]) and torch.equal(Ks, K[rb:re]), (world, rank)
+    R.close()

@@ -138,3 +138,52 @@ def test_sharded_adjoint_halo_reduction(world, p, nel):
         ref = full[lo * layer:hi * layer]
         assert np.max(np.abs(owned - ref)) <= 1e-12 * np.max(np.abs(full))
     assert sorted(covered) == list(range(res["ncl"]))
+
+
+def _assembly_rank_main(rank, world, port, dim, p, nel, q):
+    # each rank assembles its own row slab (the oracle stands in for the
+    # device call on a CPU-only host); rank 0 gathers the slabs
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        from paper_1710_01048_gb300 import inputs
+
+        g, c = inputs.make(dim, p, nel, 0.05, "exp", 0.1, seed=43)
+        n = [v + p for v in nel]
+        rb, re = shard.shard_rows(n, rank, world)
+        M, K, _ = oracle.assemble(dim, p, nel, g, c, rb, re)
+        pieces = [None] * world
+        dist.all_gather_object(pieces, (rb, re, M, K))
+        if rank == 0:
+            Mf, Kf, _ = oracle.assemble(dim, p, nel, g, c)
+            q.put(dict(pieces=pieces, Mf=Mf, Kf=Kf))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,dim,p,nel", [(2, 3, 3, (5, 4, 6)), (3, 3, 2, (4, 3, 5)), (2, 2, 3, (7, 6))])
+def test_rank_slabs_reassemble_the_mesh(world, dim, p, nel):
+    # the ranks' slabs, each assembled over its own row range, tile the rows
+    # and equal the whole mesh's bands row for row (every row has its own
+    # rule and points, so a slab needs nothing from another rank)
+    import numpy as np
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_assembly_rank_main, args=(r, world, port, dim, p, nel, q)) for r in range(world)]
+    for pr in procs:
+        pr.start()
+    res = q.get(timeout=300)
+    for pr in procs:
+        pr.join(timeout=300)
+        assert pr.exitcode == 0
+    rows = res["Mf"].shape[0]
+    nxt = 0
+    for rb, re, M, K in res["pieces"]:
+        assert rb == nxt
+        nxt = re
+        assert np.array_equal(M, res["Mf"][rb:re]) and np.array_equal(K, res["Kf"][rb:re])
+    assert nxt == rows
