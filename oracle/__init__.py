@@ -69,6 +69,8 @@ def _load():
     lib.wqo_row_points.argtypes = [I, I, I, I, PD, PD]
     lib.wqo_rule_nc.argtypes = [I, I, PD, PD, PD]
     lib.wqo_assemble_rule.argtypes = [I, I, I, PI, PD, PD, PD, PD, LL, LL, PD, PD, I]
+    lib.wqo_boundary_rule.argtypes = [I, I, I, PD, PD, PI, PD]
+    lib.wqo_row_points_mode.argtypes = [I, I, I, I, I, PD, PD]
     _lib = lib
     return lib
 
@@ -160,12 +162,31 @@ def rule_nc(p: int, kind: int):
     return y, v, res.value
 
 
+def boundary_rule(p: int, kind: int, r: int):
+    """The weighted Gaussian rule of low-side boundary row r < p (the Remark
+    closing Sec. 3, read as in wq_oracle.c): nodes t and weights Wl in units
+    of h (x = t h, W = Wl h^(1 - kind)), and the largest relative
+    residual of its conditions; None where no such rule is defined."""
+    t = np.zeros(p + 1)
+    W = np.zeros(p + 1)
+    n = ctypes.c_int(0)
+    res = ctypes.c_double(0.0)
+    st = _load().wqo_boundary_rule(p, kind, r, _pd(t), _pd(W), ctypes.byref(n), ctypes.byref(res))
+    if st == 2:
+        return None
+    if st:
+        raise RuntimeError(f"oracle boundary rule p={p} kind={kind} row={r} not found")
+    return t[:n.value].copy(), W[:n.value].copy(), res.value
+
+
 def assemble_rule(mode, dim, p, nel, geom, coef=None, row_begin=0, row_end=None, mass=True, stiffness=True,
                   threads=0):
-    """assemble() with the comparison rules: mode 'gl' = (p+1)-point
+    """assemble() with another rule set: mode 'gl' = (p+1)-point
     Gauss-Legendre on every element of supp B_r for every row, 'nc' = the
-    Newton-Cotes-type weighted rules on interior rows.  Returns (M, K)."""
-    code = {"gl": 1, "nc": 2}[mode]
+    Newton-Cotes-type weighted rules on interior rows (the comparison
+    rules), 'wqb' = the weighted Gaussian rules with the boundary rows on
+    their own weighted rules (boundary_rule).  Returns (M, K)."""
+    code = {"gl": 1, "nc": 2, "wqb": 3}[mode]
     nel = [int(v) for v in nel]
     n = [nel[a] + p for a in range(dim)]
     nrows = int(np.prod(n))
@@ -183,12 +204,16 @@ def assemble_rule(mode, dim, p, nel, geom, coef=None, row_begin=0, row_end=None,
     return M, K
 
 
-def row_points(p: int, nel: int, kind: int, r: int):
+def row_points(p: int, nel: int, kind: int, r: int, mode: str = "wq"):
     """Rule points and combined weights W = h*omega*B_r^(nu)(x) of row r of
-    one direction (GL on boundary rows)."""
+    one direction (mode 'wq': GL on boundary rows; 'wqb': boundary rows on
+    their weighted rules where defined)."""
     x = np.zeros(16)
     W = np.zeros(16)
-    L = _load().wqo_row_points(p, nel, kind, r, _pd(x), _pd(W))
+    if mode == "wq":
+        L = _load().wqo_row_points(p, nel, kind, r, _pd(x), _pd(W))
+    else:
+        L = _load().wqo_row_points_mode({"wq": 0, "gl": 1, "nc": 2, "wqb": 3}[mode], p, nel, kind, r, _pd(x), _pd(W))
     if L < 0:
         raise ValueError("bad row")
     return x[:L].copy(), W[:L].copy()

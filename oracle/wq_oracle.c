@@ -401,17 +401,32 @@ static int dir_init(dir1d *D, int p, int N) {
  * (the method), Gauss-Legendre on every element of supp B_r for every row
  * (the element-wise Gauss point set), or the Newton-Cotes-type weighted
  * rules (wqo_rule_nc).  Rows touching the boundary use Gauss-Legendre in
- * all three. */
-enum { RULE_WQ = 0, RULE_GL = 1, RULE_NC = 2 };
+ * these three.  RULE_WQB is the method with weighted Gaussian rules for the
+ * boundary rows too (wqo_boundary_rule), where such a rule is defined. */
+enum { RULE_WQ = 0, RULE_GL = 1, RULE_NC = 2, RULE_WQB = 3 };
 
 typedef struct {
   int mode;
   double tau[2][2 * MAXP + 1], om[2][2 * MAXP + 1];  /* WQ: nodes and weights; NC: nodes and folded weights */
+  /* RULE_WQB: the low-side boundary rules of rows r < p, in units of h:
+   * nodes t_k = x_k / h, weights Wl_k = W_k / h^(1 - nu) (W = omega B_r^(nu)
+   * with omega ~ h and B_r' ~ 1/h); nb = 0: none */
+  int nb[2][MAXP];
+  double bt[2][MAXP][MAXP + 1], bw[2][MAXP][MAXP + 1];
 } rule_set;
+
+int wqo_boundary_rule(int p, int nu, int r, double *t, double *Wl, int *npts, double *max_resid);
 
 static int rule_set_init(rule_set *S, int p, int mode) {
   double res;
   S->mode = mode;
+  memset(S->nb, 0, sizeof(S->nb));
+  if (mode == RULE_WQB)
+    for (int nu = 0; nu < 2; nu++)
+      for (int r = 0; r < p; r++) {
+        int st = wqo_boundary_rule(p, nu, r, S->bt[nu][r], S->bw[nu][r], &S->nb[nu][r], &res);
+        if (st == 1) return 3; /* a rule that should exist was not found */
+      }
   for (int nu = 0; nu < 2; nu++) {
     if (mode == RULE_NC) {
       if (wqo_rule_nc(p, nu, S->tau[nu], S->om[nu], &res)) return 3;
@@ -447,6 +462,20 @@ static int row_rule(const dir1d *D, const rule_set *S, int nu, int r, double *x,
     }
     return p + 1;
   }
+  if (S->mode == RULE_WQB && D->N >= 2 * p + 1) {
+    /* low-side row r < p, or the mirror image x -> 1 - x of low-side row
+     * n-1-r (B_{n-1-j}(1-x) = B_j(x), so derivatives change sign) */
+    int low = r < p, rm = low ? r : D->n - 1 - r;
+    if (rm < p && S->nb[nu][rm] > 0) {
+      double scale = nu ? 1.0 : h;
+      double sgn = (low || !nu) ? 1.0 : -1.0;
+      for (int k = 0; k < S->nb[nu][rm]; k++) {
+        x[k] = low ? S->bt[nu][rm][k] * h : 1.0 - S->bt[nu][rm][k] * h;
+        W[k] = sgn * S->bw[nu][rm][k] * scale;
+      }
+      return S->nb[nu][rm];
+    }
+  }
   double gx[MAXP + 1], gw[MAXP + 1];
   gauss_legendre(p + 1, gx, gw);
   int L = 0;
@@ -468,6 +497,187 @@ static int element_of(const dir1d *D, double x) {
   if (e < 0) e = 0;
   if (e > D->N - 1) e = D->N - 1;
   return e;
+}
+
+/* ------------------------------------------------------------------ */
+/* Weighted Gaussian rules for the boundary rows                        */
+/* ------------------------------------------------------------------ */
+
+/* The Remark closing Sec. 3 leaves the boundary rows to systems "modified
+ * accordingly".  Reading taken here (open uniform knots, a mesh of at least
+ * 2p+1 elements, so the low-side rows do not see the other boundary): the
+ * rule of row r < p and kind nu is exact for the products B_r^(nu) B_s^(nu)
+ * with every interacting s = 0 .. r+p, and has n = ceil(rank/2) nodes, rank
+ * being the dimension of the span of the B_s^(nu) on supp B_r (m = r+p+1 for
+ * the mass kind; m-1 for the stiffness kind, whose derivatives sum to zero,
+ * so the condition of s = r+p is dropped).  When rank is odd one more
+ * condition fixes the free parameter: exactness for B_r^(nu) times the
+ * monomial (x/h)^(p-nu+1), the next degree above the span on one element
+ * (for a one-element support this makes the rule the classical Gauss rule
+ * of the weight B_r^(nu)).  The rows that have such a rule with every node
+ * strictly inside supp B_r: every mass row, the stiffness rows 0 and 1 for
+ * p = 2, and the stiffness rows 0 and 2 for p = 3 (for p = 3, row 1 the
+ * system has no real solution inside the support; that row keeps
+ * Gauss-Legendre).  Unknowns are the nodes x_k and the combined weights
+ * W_k = omega_k B_r^(nu)(x_k); moments by Gauss-Legendre on each element of
+ * the support (exact for these piecewise polynomials); solved by damped
+ * Gauss-Newton (Levenberg-Marquardt) with a central-difference Jacobian from
+ * a fixed list of starts, keeping the nodes inside the support. */
+static int brule_defined(int p, int nu, int r) {
+  if (r < 0 || r >= p) return 0;
+  if (nu == 0) return 1;
+  return p == 2 ? 1 : (r != 1);
+}
+
+typedef struct {
+  dir1d D;
+  int p, nu, r, nf, n, extra;
+  double mu[2 * MAXP + 2];
+} brule_sys;
+
+static double brule_f(const brule_sys *B, int j, double x) {
+  if (B->extra && j == B->nf - 1) return pow(x / B->D.h, (double)(B->p - B->nu + 1));
+  return bspl(B->D.t, B->D.nt, j, B->p, B->nu, x); /* s = j */
+}
+
+static void brule_residual(const brule_sys *B, const double *u, double *F) {
+  for (int j = 0; j < B->nf; j++) {
+    double s = -B->mu[j];
+    for (int k = 0; k < B->n; k++) s += u[B->n + k] * brule_f(B, j, u[k]);
+    F[j] = s;
+  }
+}
+
+int wqo_boundary_rule(int p, int nu, int r, double *t, double *Wl, int *npts, double *max_resid) {
+  *npts = 0;
+  *max_resid = 0.0;
+  if (p < 2 || p > MAXP || nu < 0 || nu > 1 || r < 0 || r >= p) return 2;
+  if (!brule_defined(p, nu, r)) return 2;
+  brule_sys B;
+  if (dir_init(&B.D, p, 2 * p + 1)) return 2;
+  B.p = p; B.nu = nu; B.r = r;
+  int m = r + p + 1;
+  int rank = nu ? m - 1 : m;
+  B.n = (rank + 1) / 2;
+  B.extra = rank % 2;
+  B.nf = rank + B.extra;
+  double h = B.D.h, a = 0.0, b = (double)(r + 1) * h;
+  /* moments: 8-point Gauss-Legendre on each element of [a, b] */
+  double gx[8], gw[8];
+  gauss_legendre(8, gx, gw);
+  for (int j = 0; j < B.nf; j++) {
+    double s = 0.0;
+    for (int e = 0; e <= r; e++)
+      for (int g = 0; g < 8; g++) {
+        double x = ((double)e + 0.5 * (gx[g] + 1.0)) * h;
+        s += 0.5 * h * gw[g] * bspl(B.D.t, B.D.nt, r, p, nu, x) * brule_f(&B, j, x);
+      }
+    B.mu[j] = s;
+  }
+  double mumax = 1.0;
+  for (int j = 0; j < B.nf; j++) if (fabs(B.mu[j]) > mumax) mumax = fabs(B.mu[j]);
+  const int n = B.n, nn = 2 * B.n;
+  double lg[MAXP + 1], lw[MAXP + 1];
+  gauss_legendre(n, lg, lw);
+  for (int start = 0; start < 4; start++) {
+    double u[2 * MAXP + 2], F[2 * MAXP + 2];
+    for (int k = 0; k < n; k++) {
+      double f = (double)(k + 1) / (double)(n + 1);
+      if (start == 0) f = 0.5 * (lg[k] + 1.0);
+      if (start == 2) f = ((k + 0.5) / n) * ((k + 0.5) / n);
+      if (start == 3) f = 1.0 - (1.0 - (k + 0.5) / n) * (1.0 - (k + 0.5) / n);
+      u[k] = a + f * (b - a);
+    }
+    /* weights for the start nodes: least squares on the conditions */
+    {
+      double A[2 * MAXP + 2][MAXP + 1], N[(MAXP + 1) * (MAXP + 1)], rhs[MAXP + 1];
+      for (int j = 0; j < B.nf; j++)
+        for (int k = 0; k < n; k++) A[j][k] = brule_f(&B, j, u[k]);
+      for (int k = 0; k < n; k++) {
+        rhs[k] = 0.0;
+        for (int j = 0; j < B.nf; j++) rhs[k] += A[j][k] * B.mu[j];
+        for (int l = 0; l < n; l++) {
+          double s = 0.0;
+          for (int j = 0; j < B.nf; j++) s += A[j][k] * A[j][l];
+          N[k * n + l] = s;
+        }
+      }
+      if (solve_dense(n, N, rhs)) continue;
+      for (int k = 0; k < n; k++) u[n + k] = rhs[k];
+    }
+    brule_residual(&B, u, F);
+    double lam = 1e-3;
+    for (int it = 0; it < 300; it++) {
+      double fn = 0.0, fmax = 0.0;
+      for (int j = 0; j < B.nf; j++) { fn += F[j] * F[j]; if (fabs(F[j]) > fmax) fmax = fabs(F[j]); }
+      if (fmax <= 1e-15 * mumax) break;
+      double J[2 * MAXP + 2][2 * MAXP + 2];
+      for (int c = 0; c < nn; c++) {
+        double up[2 * MAXP + 2], um[2 * MAXP + 2], Fp[2 * MAXP + 2], Fm[2 * MAXP + 2];
+        double dstep = c < n ? 1e-7 * h : 1e-7 * (fabs(u[c]) > 1.0 ? fabs(u[c]) : 1.0);
+        memcpy(up, u, sizeof(double) * nn);
+        memcpy(um, u, sizeof(double) * nn);
+        up[c] += dstep;
+        um[c] -= dstep;
+        brule_residual(&B, up, Fp);
+        brule_residual(&B, um, Fm);
+        for (int j = 0; j < B.nf; j++) J[j][c] = (Fp[j] - Fm[j]) / (2.0 * dstep);
+      }
+      int moved = 0;
+      while (lam <= 1e12) {
+        double A[(2 * MAXP + 2) * (2 * MAXP + 2)], g[2 * MAXP + 2];
+        for (int c = 0; c < nn; c++) {
+          g[c] = 0.0;
+          for (int j = 0; j < B.nf; j++) g[c] -= J[j][c] * F[j];
+          for (int d = 0; d < nn; d++) {
+            double s = 0.0;
+            for (int j = 0; j < B.nf; j++) s += J[j][c] * J[j][d];
+            A[c * nn + d] = s;
+          }
+        }
+        for (int c = 0; c < nn; c++) A[c * nn + c] *= 1.0 + lam;
+        if (solve_dense(nn, A, g)) { lam *= 10.0; continue; }
+        double v[2 * MAXP + 2], Fv[2 * MAXP + 2];
+        int inside = 1;
+        for (int c = 0; c < nn; c++) v[c] = u[c] + g[c];
+        for (int k = 0; k < n; k++) if (!(v[k] > a && v[k] < b)) inside = 0;
+        if (inside) {
+          brule_residual(&B, v, Fv);
+          double fv = 0.0;
+          for (int j = 0; j < B.nf; j++) fv += Fv[j] * Fv[j];
+          if (fv < fn) {
+            memcpy(u, v, sizeof(double) * nn);
+            memcpy(F, Fv, sizeof(double) * B.nf);
+            lam = lam / 10.0 > 1e-12 ? lam / 10.0 : 1e-12;
+            moved = 1;
+            break;
+          }
+        }
+        lam *= 10.0;
+      }
+      if (!moved) break;
+    }
+    double fmax = 0.0;
+    for (int j = 0; j < B.nf; j++) if (fabs(F[j]) > fmax) fmax = fabs(F[j]);
+    if (fmax <= 1e-14 * mumax) {
+      /* ascending nodes, in units of h */
+      for (int k = 0; k < n; k++)
+        for (int l = k + 1; l < n; l++)
+          if (u[l] < u[k]) {
+            double tx = u[k]; u[k] = u[l]; u[l] = tx;
+            double tw = u[n + k]; u[n + k] = u[n + l]; u[n + l] = tw;
+          }
+      double wscale = nu ? 1.0 : 1.0 / h; /* W = Wl h^(1-nu) */
+      for (int k = 0; k < n; k++) {
+        t[k] = u[k] / h;
+        Wl[k] = u[n + k] * wscale;
+      }
+      *npts = n;
+      *max_resid = fmax / mumax;
+      return 0;
+    }
+  }
+  return 1;
 }
 
 /* ------------------------------------------------------------------ */
@@ -690,11 +900,13 @@ int wqo_assemble(int dim, int p, const int *nel, const double *g1, const double 
 
 /* The same assembly with the comparison rules: mode 1 = Gauss-Legendre on
  * every element of supp B_r for every row, mode 2 = Newton-Cotes-type
- * weighted rules on the interior rows. */
+ * weighted rules on the interior rows; or mode 3, the weighted Gaussian
+ * rules with boundary rows on their own weighted rules (wqo_boundary_rule,
+ * Gauss-Legendre where none is defined or the mesh is below 2p+1 elements). */
 int wqo_assemble_rule(int mode, int dim, int p, const int *nel, const double *g1, const double *g2,
                       const double *g3, const double *coef, long long row_begin, long long row_end, double *M,
                       double *K, int nthreads) {
-  if (mode != RULE_GL && mode != RULE_NC) return 2;
+  if (mode != RULE_GL && mode != RULE_NC && mode != RULE_WQB) return 2;
   return assemble_mode(mode, dim, p, nel, g1, g2, g3, coef, row_begin, row_end, M, K, NULL, nthreads);
 }
 
@@ -911,6 +1123,17 @@ int wqo_row_points(int p, int N, int nu, int r, double *x, double *W) {
   if (dir_init(&D, p, N)) return -1;
   rule_set RS;
   if (rule_set_init(&RS, p, RULE_WQ)) return -1;
+  if (r < 0 || r >= D.n) return -1;
+  return row_rule(&D, &RS, nu, r, x, W);
+}
+
+/* The same in a given rule mode (RULE_WQ .. RULE_WQB). */
+int wqo_row_points_mode(int mode, int p, int N, int nu, int r, double *x, double *W) {
+  dir1d D;
+  if (mode < RULE_WQ || mode > RULE_WQB) return -1;
+  if (dir_init(&D, p, N)) return -1;
+  rule_set RS;
+  if (rule_set_init(&RS, p, mode)) return -1;
   if (r < 0 || r >= D.n) return -1;
   return row_rule(&D, &RS, nu, r, x, W);
 }
