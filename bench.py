@@ -517,14 +517,15 @@ def run_variants(args, wq, inputs, R, w, g, gd, cd, bands, sample, timed, stream
 
     # the comparison rules (FP64, same kernel's general-points class) on the
     # 64^3 cubic workload: Gauss-Legendre on every element of each row's
-    # support, and the Newton-Cotes-type weighted rules; with the
-    # quadrature-point counts
+    # support, and the Newton-Cotes-type weighted rules; and the weighted
+    # Gaussian rules with the boundary rows on their own weighted rules
+    # ('wqb', the default kernels); with the quadrature-point counts
     wc, gc, cc = inputs.workload("3d_p3_64")
     gdc = [torch.from_numpy(x).cuda() for x in gc]
     cdc = torch.from_numpy(cc).cuda()
     points = {}
     Mv = Kv = None
-    for mode in ("wq", "nc", "gl"):
+    for mode in ("wq", "wqb", "nc", "gl"):
         Rm = wq.Rules(3, wc["p"], wc["nel"], rule=mode)
         total = 1
         for a in range(3):

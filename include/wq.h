@@ -85,7 +85,19 @@ enum {
    * with the Newton-Cotes-type weighted rules of Sec. 1 / Sec. 4 (nodes at
    * the knots and element midpoints of the support, 2p+1 per direction). */
   WQ_RULES_GAUSS_LEGENDRE = 2,
-  WQ_RULES_NEWTON_COTES = 4
+  WQ_RULES_NEWTON_COTES = 4,
+  /* The weighted Gaussian rules for the boundary rows too (the Remark
+   * closing Sec. 3: the systems "modified accordingly"): row r < p (and its
+   * mirror image n-1-r) of each kind gets ceil(rank/2) nodes exact for the
+   * products B_r^(nu) B_s^(nu) over every interacting s (rank r+p+1 for the
+   * mass kind, r+p for the stiffness kind), with one more condition, on
+   * B_r^(nu) (x/h)^(p-nu+1), when the rank is odd; defined for every mass
+   * row and every stiffness row but p = 3 row 1, which keeps Gauss-Legendre,
+   * as do all rows of directions with fewer than 2p+1 elements.  Assembly
+   * calls only (mass, stiffness, both, host-buffer form): the apply, load,
+   * adjoint, batch and no-alloc calls return WQ_ERR_UNSUPPORTED for it.  Not
+   * combinable with the comparison rules. */
+  WQ_RULES_BOUNDARY_WEIGHTED = 8
 };
 
 typedef struct wq_mesh {

@@ -22,7 +22,8 @@ WQ_FP64, WQ_MIXED, WQ_DF64 = 0, 1, 2
 PRECISIONS = {"fp64": WQ_FP64, "mixed": WQ_MIXED, "df64": WQ_DF64}
 WQ_KIND_MASS, WQ_KIND_STIFFNESS = 0, 1
 WQ_RULES_HOST_ONLY, WQ_RULES_DEVICE, WQ_RULES_GAUSS_LEGENDRE, WQ_RULES_NEWTON_COTES = 0, 1, 2, 4
-RULE_FLAGS = {"wq": 0, "gl": WQ_RULES_GAUSS_LEGENDRE, "nc": WQ_RULES_NEWTON_COTES}
+WQ_RULES_BOUNDARY_WEIGHTED = 8
+RULE_FLAGS = {"wq": 0, "gl": WQ_RULES_GAUSS_LEGENDRE, "nc": WQ_RULES_NEWTON_COTES, "wqb": WQ_RULES_BOUNDARY_WEIGHTED}
 
 # every function declared in include/wq.h
 EXPORTS = ["wq_status_string", "wq_version", "wq_rule_1d", "wq_rule_1d_from", "wq_rules_build", "wq_rules_free",
@@ -253,9 +254,11 @@ class Rules:
     """Owns a wq_rules handle (host tables, and device tables when device=True)."""
 
     def __init__(self, dim, degree, nel, device=True, rule="wq"):
-        """rule: 'wq' (the weighted Gaussian rules), or the comparison rules
-        'gl' (Gauss-Legendre on every element of each row's support) and 'nc'
-        (Newton-Cotes-type weighted rules on the interior rows)."""
+        """rule: 'wq' (the weighted Gaussian rules, Gauss-Legendre on the
+        boundary rows), 'wqb' (weighted Gaussian rules for the boundary rows
+        too, where defined), or the comparison rules 'gl' (Gauss-Legendre on
+        every element of each row's support) and 'nc' (Newton-Cotes-type
+        weighted rules on the interior rows)."""
         self.dim, self.degree, self.nel = int(dim), int(degree), tuple(int(v) for v in nel)
         self.rule = rule
         flags = (WQ_RULES_DEVICE if device else WQ_RULES_HOST_ONLY) | RULE_FLAGS[rule]

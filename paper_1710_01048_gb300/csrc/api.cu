@@ -287,6 +287,9 @@ void fill_tables(const wq_rules *R, wq_precision prec, wq::RowsArgs &ra) {
     ra.N[a] = R->nel[a];
     ra.nc[a] = R->nc[a];
   }
+  // boundary x1 rows: Gauss-Legendre, P+1 points per element in element
+  // order, unless the boundary rows have their own weighted rules
+  ra.bnd_grouped = (R->mode == wq::kModeWQ && !R->bnd_weighted) ? 1 : 0;
 }
 
 // Line range and chunking of one line class for rows [rb, re); returns the
@@ -459,7 +462,7 @@ wq_status apply(const wq_rules *R, const double *const *geom, const double *coef
   wq::TraceRange trace("wq_apply");
   wq_status st = check_call(R, geom, prec, rb, re);
   if (st != WQ_OK) return st;
-  if (R->mode != wq::kModeWQ || (R->dim == 3 && !R->dev_U)) return WQ_ERR_UNSUPPORTED;
+  if (R->mode != wq::kModeWQ || R->bnd_weighted || (R->dim == 3 && !R->dev_U)) return WQ_ERR_UNSUPPORTED;
   if (rb != re && !yM && !yK) return WQ_ERR_ARG;
   if (rb == re) return WQ_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -530,8 +533,10 @@ wq_status wq_rules_build(const wq_mesh *mesh, int flags, wq_rules **out) {
   *out = nullptr;
   if (mesh->dim < 2 || mesh->dim > 3 || mesh->degree < 2 || mesh->degree > wq::kMaxP) return WQ_ERR_UNSUPPORTED;
   const int rule_bits = flags & (WQ_RULES_GAUSS_LEGENDRE | WQ_RULES_NEWTON_COTES);
-  if ((flags & ~(WQ_RULES_DEVICE | WQ_RULES_GAUSS_LEGENDRE | WQ_RULES_NEWTON_COTES)) != 0) return WQ_ERR_ARG;
+  if ((flags & ~(WQ_RULES_DEVICE | WQ_RULES_GAUSS_LEGENDRE | WQ_RULES_NEWTON_COTES | WQ_RULES_BOUNDARY_WEIGHTED)) != 0)
+    return WQ_ERR_ARG;
   if (rule_bits == (WQ_RULES_GAUSS_LEGENDRE | WQ_RULES_NEWTON_COTES)) return WQ_ERR_ARG;
+  if (rule_bits && (flags & WQ_RULES_BOUNDARY_WEIGHTED)) return WQ_ERR_ARG;
   for (int a = 0; a < mesh->dim; a++) {
     if (mesh->nel[a] < 1) return WQ_ERR_ARG;
     if (mesh->nel[a] > wq::kMaxNel) return WQ_ERR_UNSUPPORTED;
@@ -547,6 +552,7 @@ wq_status wq_rules_build(const wq_mesh *mesh, int flags, wq_rules **out) {
     R->dim = mesh->dim;
     R->mode = rule_bits == WQ_RULES_GAUSS_LEGENDRE ? wq::kModeGL
               : rule_bits == WQ_RULES_NEWTON_COTES   ? wq::kModeNC : wq::kModeWQ;
+    R->bnd_weighted = (flags & WQ_RULES_BOUNDARY_WEIGHTED) != 0;
     for (int a = 0; a < 3; a++) {
       R->nel[a] = a < mesh->dim ? mesh->nel[a] : 1;
       R->n[a] = a < mesh->dim ? mesh->nel[a] + mesh->degree : 1;
@@ -720,7 +726,7 @@ wq_status wq_assemble_adjoint(const wq_rules *R, const double *const *geom, wq_p
   wq::TraceRange trace("wq_assemble_adjoint");
   if (!R || !geom || !grad) return WQ_ERR_ARG;
   if (!R->on_device) return WQ_ERR_ARG;
-  if (R->mode != wq::kModeWQ) return WQ_ERR_UNSUPPORTED;
+  if (R->mode != wq::kModeWQ || R->bnd_weighted) return WQ_ERR_UNSUPPORTED;
   if (prec != WQ_FP64 && prec != WQ_MIXED && prec != WQ_DF64) return WQ_ERR_ARG;
   const int64_t rows = (int64_t)R->n[0] * R->n[1] * R->n[2];
   if (row_begin < 0 || row_end > rows || row_begin > row_end) return WQ_ERR_ARG;

@@ -59,6 +59,10 @@ struct RowsArgs {
   // y = M x and y = K x, one OutT<R> value per row of [row_begin, row_end);
   // x holds one OutT<R> value per row of the whole mesh, or is null for x = 1
   const void *x;
+  // 1: every boundary x1 row holds P+1 points per element of its support in
+  // element order (Gauss-Legendre), processed element by element; 0: the
+  // general per-point form
+  int bnd_grouped;
 };
 
 // Asynchronous global -> shared copies of one 4- or 8-byte element
@@ -566,7 +570,7 @@ __device__ __forceinline__ void rows_phase_b(const RowsArgs &A, const R *sU, con
             oM[j] = dd2_first(aMK[j]);
             oK[j] = dd2_second(aMK[j]);
           }
-        } else if constexpr (!GENERAL) {
+        } else if (!GENERAL && A.bnd_grouped) {
           // Gauss-Legendre rows: P+1 points in each element of the support,
           // in element order; per element its four coefficient columns are
           // loaded once and its band offset selects compile-time indices

@@ -217,6 +217,7 @@ wq_status wq_batch_create(const wq_patch *patches, int npatch, wq_precision prec
     const wq_patch &P = patches[i];
     const wq_rules *R = P.rules;
     if (!R || !R->on_device || R->device != dev || R->dim != 3 || R->mode != wq::kModeWQ) return WQ_ERR_ARG;
+    if (R->bnd_weighted) return WQ_ERR_UNSUPPORTED;
     if (!P.M || !P.K || !P.geom[0] || !P.geom[1] || !P.geom[2]) return WQ_ERR_ARG;
   }
   wq_batch *B = new (std::nothrow) wq_batch();
@@ -281,6 +282,7 @@ wq_status wq_batch_create(const wq_patch *patches, int npatch, wq_precision prec
     const size_t np = (size_t)R->p + 1;
     wq::RowsArgs &ra = B->base_args[i];
     std::memset(&ra, 0, sizeof(ra));
+    ra.bnd_grouped = 1;  // Gauss-Legendre boundary rows
     for (int a = 0; a < 3; a++) {
       for (int k = 0; k < 2; k++) {
         const wq::DevDirKind &Dk = R->dev[a][k];

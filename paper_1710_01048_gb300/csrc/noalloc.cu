@@ -129,7 +129,7 @@ extern "C" wq_status wq_assemble_noalloc(const wq_rules *R, const double *const 
                                          void *stream, int check_status) {
   if (!R || !geom) return WQ_ERR_ARG;
   if (prec != WQ_FP64 && prec != WQ_MIXED) return WQ_ERR_ARG;
-  if (R->mode != wq::kModeWQ) return WQ_ERR_UNSUPPORTED;
+  if (R->mode != wq::kModeWQ || R->bnd_weighted) return WQ_ERR_UNSUPPORTED;
   const int64_t rows = (int64_t)R->n[0] * R->n[1] * R->n[2];
   if (row_begin < 0 || row_end > rows || row_begin > row_end) return WQ_ERR_ARG;
   if (row_begin == row_end) return WQ_OK;
@@ -213,6 +213,7 @@ extern "C" wq_status wq_assemble_noalloc(const wq_rules *R, const double *const 
   ra.coef = coef;
   ra.M = M;
   ra.K = K;
+  ra.bnd_grouped = 1;  // Gauss-Legendre boundary rows
   ra.row_begin = row_begin;
   ra.row_end = row_end;
   ra.status = status;

@@ -13,6 +13,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <utility>
+#include <vector>
 
 #include "wq_internal.h"
 
@@ -302,6 +304,217 @@ void basis(const std::vector<double> &t, int q, int e, double x, double *val, do
   }
 }
 
+// ------------------------------------------------------------------ boundary rows
+// Weighted Gaussian rules for the rows whose weight function touches the
+// boundary (the Remark closing Sec. 3 leaves them to the systems "modified
+// accordingly").  Row r < p of kind nu: ceil(rank/2) nodes exact for the
+// products B_r^(nu) B_s^(nu), s = 0 .. r+p (rank r+p+1 for the mass kind;
+// r+p for the stiffness kind, whose derivatives sum to zero, so s = r+p is
+// dropped), and, when the rank is odd, for B_r^(nu) (x/h)^(p-nu+1).  Defined
+// for every mass row, the stiffness rows of p = 2 and rows 0 and 2 of p = 3
+// stiffness (row 1 has no such rule inside its support).  The rule is found
+// by variable projection: for given nodes the combined weights W_k solve the
+// linear least-squares problem of the conditions, and the nodes follow
+// damped Gauss-Newton steps on the remaining residual (central-difference
+// Jacobian), from a fixed list of starting nodes, on a reference mesh of
+// 2p+1 elements; results in units of h (t = x/h, Wl = W / h^(1-nu)).
+
+bool boundary_rule_defined(int p, int kind, int r) {
+  if (r < 0 || r >= p) return false;
+  return kind == WQ_KIND_MASS || p == 2 || r != 1;
+}
+
+struct BoundarySystem {
+  int p, kind, r, nf, n;
+  bool extra;
+  double h, a, b;
+  std::vector<double> t;  // degree-p knots of the reference mesh
+  double mu[2 * kMaxP + 2];
+  // condition function j at x: B_j^(kind)(x) (j < rank), else (x/h)^(p-kind+1)
+  double f(int j, double x) const {
+    if (extra && j == nf - 1) return std::pow(x / h, (double)(p - kind + 1));
+    const int N = (int)std::lround(1.0 / h);
+    int e = (int)std::floor(x / h);
+    e = std::max(0, std::min(N - 1, e));
+    const int i = j - e;
+    if (i < 0 || i > p) return 0.0;
+    double v[8], dv[8];
+    basis(t, p, e, x, v, dv);
+    return kind == WQ_KIND_MASS ? v[i] : dv[i];
+  }
+};
+
+// Weights minimising |A(x) W - mu| for nodes x (normal equations), and the
+// residual A W - mu; false if the normal matrix is singular.
+bool project_weights(const BoundarySystem &S, const double *x, double *W, double *res) {
+  const int n = S.n, nf = S.nf;
+  double A[2 * kMaxP + 2][kMaxP + 1];
+  for (int j = 0; j < nf; j++)
+    for (int k = 0; k < n; k++) A[j][k] = S.f(j, x[k]);
+  double G[kMaxP + 1][kMaxP + 2];
+  for (int k = 0; k < n; k++) {
+    for (int l = 0; l < n; l++) {
+      double acc = 0.0;
+      for (int j = 0; j < nf; j++) acc += A[j][k] * A[j][l];
+      G[k][l] = acc;
+    }
+    double acc = 0.0;
+    for (int j = 0; j < nf; j++) acc += A[j][k] * S.mu[j];
+    G[k][n] = acc;
+  }
+  for (int c = 0; c < n; c++) {
+    int piv = c;
+    for (int r = c + 1; r < n; r++)
+      if (std::fabs(G[r][c]) > std::fabs(G[piv][c])) piv = r;
+    if (!(std::fabs(G[piv][c]) > 0.0)) return false;
+    for (int k = 0; k <= n; k++) std::swap(G[c][k], G[piv][k]);
+    for (int r = 0; r < n; r++) {
+      if (r == c) continue;
+      const double m = G[r][c] / G[c][c];
+      for (int k = c; k <= n; k++) G[r][k] -= m * G[c][k];
+    }
+  }
+  for (int k = 0; k < n; k++) W[k] = G[k][n] / G[k][k];
+  for (int j = 0; j < nf; j++) {
+    double acc = -S.mu[j];
+    for (int k = 0; k < n; k++) acc += A[j][k] * W[k];
+    res[j] = acc;
+  }
+  return true;
+}
+
+double sumsq(const double *v, int n) {
+  double s = 0.0;
+  for (int i = 0; i < n; i++) s += v[i] * v[i];
+  return s;
+}
+
+wq_status boundary_rule_impl(int p, int kind, int r, double *tl, double *wl, int *npts) {
+  *npts = 0;
+  if (!boundary_rule_defined(p, kind, r)) return WQ_ERR_UNSUPPORTED;
+  BoundarySystem S;
+  const int Nref = 2 * p + 1;
+  S.p = p;
+  S.kind = kind;
+  S.r = r;
+  S.h = 1.0 / (double)Nref;
+  S.t = knots(p, Nref);
+  const int m = r + p + 1, rank = kind == WQ_KIND_MASS ? m : m - 1;
+  S.n = (rank + 1) / 2;
+  S.extra = (rank % 2) == 1;
+  S.nf = rank + (S.extra ? 1 : 0);
+  S.a = 0.0;
+  S.b = (double)(r + 1) * S.h;
+  // moments: 4-point Gauss-Legendre on each element of the support (exact
+  // for the products, of degree <= 2p+1)
+  double gx[4], gw[4];
+  gauss_legendre(4, gx, gw);
+  for (int j = 0; j < S.nf; j++) {
+    double acc = 0.0;
+    for (int e = 0; e <= r; e++)
+      for (int g = 0; g < 4; g++) {
+        const double x = ((double)e + 0.5 * (gx[g] + 1.0)) * S.h;
+        double v[8], dv[8];
+        basis(S.t, p, e, x, v, dv);
+        const double wr = kind == WQ_KIND_MASS ? v[r - e] : dv[r - e];
+        acc += 0.5 * S.h * gw[g] * wr * S.f(j, x);
+      }
+    S.mu[j] = acc;
+  }
+  double scale = 1.0;
+  for (int j = 0; j < S.nf; j++) scale = std::max(scale, std::fabs(S.mu[j]));
+  const int n = S.n, nf = S.nf;
+  for (int start = 0; start < 4; start++) {
+    double x[kMaxP + 1], W[kMaxP + 1], res[2 * kMaxP + 2];
+    for (int k = 0; k < n; k++) {
+      const double u = (k + 0.5) / (double)n;
+      const double f = start == 0 ? (k + 1.0) / (n + 1.0) : start == 1 ? u * u : start == 2 ? 1.0 - (1.0 - u) * (1.0 - u) : u;
+      x[k] = S.a + f * (S.b - S.a);
+    }
+    if (!project_weights(S, x, W, res)) continue;
+    double lam = 1e-3;
+    for (int it = 0; it < 400 && std::sqrt(sumsq(res, nf)) > 1e-16 * scale; it++) {
+      // Jacobian of the projected residual with respect to the nodes
+      double J[2 * kMaxP + 2][kMaxP + 1];
+      for (int k = 0; k < n; k++) {
+        double xp[kMaxP + 1], xm[kMaxP + 1], Wt[kMaxP + 1], rp[2 * kMaxP + 2], rm[2 * kMaxP + 2];
+        std::copy(x, x + n, xp);
+        std::copy(x, x + n, xm);
+        const double d = 1e-7 * S.h;
+        xp[k] += d;
+        xm[k] -= d;
+        if (!project_weights(S, xp, Wt, rp) || !project_weights(S, xm, Wt, rm)) return WQ_ERR_NO_CONVERGENCE;
+        for (int j = 0; j < nf; j++) J[j][k] = (rp[j] - rm[j]) / (2.0 * d);
+      }
+      bool moved = false;
+      while (lam < 1e14 && !moved) {
+        double G[kMaxP + 1][kMaxP + 2];
+        for (int k = 0; k < n; k++) {
+          for (int l = 0; l < n; l++) {
+            double acc = 0.0;
+            for (int j = 0; j < nf; j++) acc += J[j][k] * J[j][l];
+            G[k][l] = acc * (k == l ? 1.0 + lam : 1.0);
+          }
+          double acc = 0.0;
+          for (int j = 0; j < nf; j++) acc -= J[j][k] * res[j];
+          G[k][n] = acc;
+        }
+        bool ok = true;
+        for (int c = 0; c < n && ok; c++) {
+          int piv = c;
+          for (int r2 = c + 1; r2 < n; r2++)
+            if (std::fabs(G[r2][c]) > std::fabs(G[piv][c])) piv = r2;
+          if (!(std::fabs(G[piv][c]) > 0.0)) ok = false;
+          else {
+            for (int k = 0; k <= n; k++) std::swap(G[c][k], G[piv][k]);
+            for (int r2 = 0; r2 < n; r2++) {
+              if (r2 == c) continue;
+              const double mm = G[r2][c] / G[c][c];
+              for (int k = c; k <= n; k++) G[r2][k] -= mm * G[c][k];
+            }
+          }
+        }
+        if (ok) {
+          double xn[kMaxP + 1], Wn[kMaxP + 1], rn[2 * kMaxP + 2];
+          bool inside = true;
+          for (int k = 0; k < n; k++) {
+            xn[k] = x[k] + G[k][n] / G[k][k];
+            if (!(xn[k] > S.a && xn[k] < S.b)) inside = false;
+          }
+          if (inside && project_weights(S, xn, Wn, rn) && sumsq(rn, nf) < sumsq(res, nf)) {
+            std::copy(xn, xn + n, x);
+            std::copy(Wn, Wn + n, W);
+            std::copy(rn, rn + nf, res);
+            lam = std::max(lam * 0.1, 1e-12);
+            moved = true;
+            break;
+          }
+        }
+        lam *= 10.0;
+      }
+      if (!moved) break;
+    }
+    double worst = 0.0;
+    for (int j = 0; j < nf; j++) worst = std::max(worst, std::fabs(res[j]));
+    if (worst <= 1e-14 * scale) {
+      // ascending nodes in units of h
+      for (int k = 0; k < n; k++)
+        for (int l = k + 1; l < n; l++)
+          if (x[l] < x[k]) {
+            std::swap(x[k], x[l]);
+            std::swap(W[k], W[l]);
+          }
+      for (int k = 0; k < n; k++) {
+        tl[k] = x[k] / S.h;
+        wl[k] = kind == WQ_KIND_MASS ? W[k] / S.h : W[k];
+      }
+      *npts = n;
+      return WQ_OK;
+    }
+  }
+  return WQ_ERR_NO_CONVERGENCE;
+}
+
 }  // namespace
 
 // Newton-Cotes-type weighted rule on the cardinal support [0, p+1] (the
@@ -354,8 +567,22 @@ wq_status nc_rule(int p, int kind, double *y, double *v) {
   return WQ_OK;
 }
 
+wq_status boundary_rule(int p, int kind, int r, double *t, double *Wl, int *npts) {
+  return boundary_rule_impl(p, kind, r, t, Wl, npts);
+}
+
 wq_status build_host_tables(wq_rules *R) {
   int p = R->p;
+  // boundary weighted rules of the low-side rows, both kinds (units of h)
+  double bt[2][kMaxP][kMaxP + 1] = {}, bw[2][kMaxP][kMaxP + 1] = {};
+  int bn[2][kMaxP] = {};
+  if (R->bnd_weighted)
+    for (int kind = 0; kind < 2; kind++)
+      for (int r = 0; r < p; r++) {
+        if (!boundary_rule_defined(p, kind, r)) continue;
+        wq_status st = boundary_rule_impl(p, kind, r, bt[kind][r], bw[kind][r], &bn[kind][r]);
+        if (st != WQ_OK) return st;
+      }
   for (int kind = 0; kind < 2; kind++) {
     wq_status st = default_rule(p, kind, R->tau[kind], R->omega[kind]);
     if (st != WQ_OK) return st;
@@ -382,7 +609,54 @@ wq_status build_host_tables(wq_rules *R) {
         std::vector<int> pe;
         std::vector<double> px, pf;
         bool folded = false;  // pf already holds the combined weight W
-        if (R->mode == kModeWQ && r >= p && r <= N - 1) {
+        const bool bnd_row = r < p || r > N - 1;
+        if (R->bnd_weighted && bnd_row && N >= 2 * p + 1) {
+          // both kinds' points (weighted rule, or Gauss-Legendre where none
+          // is defined) with combined weights, then per element the larger
+          // of the two counts, the shorter list padded with zero weights at
+          // the element's midpoint
+          folded = true;
+          const int low = r < p, rm = low ? r : n - 1 - r;
+          const int elo = std::max(0, r - p), ehi = std::min(N - 1, r);
+          std::vector<int> ke[2];
+          std::vector<double> kx[2], kw[2];
+          for (int k = 0; k < 2; k++) {
+            if (bn[k][rm] > 0) {
+              for (int q = 0; q < bn[k][rm]; q++) {
+                const double x = low ? bt[k][rm][q] * h : 1.0 - bt[k][rm][q] * h;
+                const double sgn = (low || k == WQ_KIND_MASS) ? 1.0 : -1.0;
+                ke[k].push_back(std::max(0, std::min(N - 1, (int)std::floor(x / h))));
+                kx[k].push_back(x);
+                kw[k].push_back(sgn * bw[k][rm][q] * (k == WQ_KIND_MASS ? h : 1.0));
+              }
+            } else {
+              for (int e = elo; e <= ehi; e++)
+                for (int g = 0; g <= p; g++) {
+                  const double x = ((double)e + 0.5 * (gx[g] + 1.0)) * h;
+                  double v[8], dv[8];
+                  basis(tp, p, e, x, v, dv);
+                  ke[k].push_back(e);
+                  kx[k].push_back(x);
+                  kw[k].push_back(0.5 * h * gw[g] * (k == WQ_KIND_MASS ? v[r - e] : dv[r - e]));
+                }
+            }
+          }
+          for (int e = elo; e <= ehi; e++) {
+            int cnt[2] = {0, 0};
+            for (int k = 0; k < 2; k++)
+              for (size_t q = 0; q < ke[k].size(); q++) cnt[k] += ke[k][q] == e;
+            std::vector<std::pair<double, double>> own;  // (x, W) of this kind in element e
+            for (size_t q = 0; q < ke[kind].size(); q++)
+              if (ke[kind][q] == e) own.push_back({kx[kind][q], kw[kind][q]});
+            std::sort(own.begin(), own.end());
+            while ((int)own.size() < std::max(cnt[0], cnt[1])) own.push_back({((double)e + 0.5) * h, 0.0});
+            for (const auto &pt : own) {
+              pe.push_back(e);
+              px.push_back(pt.first);
+              pf.push_back(pt.second);
+            }
+          }
+        } else if (R->mode == kModeWQ && r >= p && r <= N - 1) {
           for (int k = 0; k <= p; k++) {
             pe.push_back(r - p + k);
             px.push_back(((double)(r - p) + R->tau[kind][k]) * h);

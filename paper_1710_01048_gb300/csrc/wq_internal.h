@@ -73,6 +73,10 @@ struct wq_rules {
   wq_mesh mesh;
   int p = 0, dim = 0;
   int mode = 0;  // 0: weighted Gaussian rules; 1: Gauss-Legendre rows; 2: Newton-Cotes-type rows
+  // mode 0 with weighted Gaussian rules for the boundary rows as well
+  // (WQ_RULES_BOUNDARY_WEIGHTED): their points are padded per element so that
+  // both kinds have the same elements point by point
+  bool bnd_weighted = false;
   int nel[3] = {1, 1, 1};
   int n[3] = {1, 1, 1};
   int nc[3] = {1, 1, 1};
@@ -111,6 +115,10 @@ int chunk_length(const wq_rules *R, int tmax);
 // Most x1 points one chunk holds when lines are cut into chunks of T rows
 // (the last one ragged), as the launches cut them.
 int max_chunk_points(const wq_rules *R, int T);
+// Boundary row r < p of kind: the weighted Gaussian rule in units of h (x =
+// t h from the low end, W = Wl h^(1-kind)); WQ_ERR_UNSUPPORTED where none is
+// defined (Gauss-Legendre is used there).
+wq_status boundary_rule(int p, int kind, int r, double *t, double *Wl, int *npts);
 double flop_count(const wq_rules *R, int want_m, int want_k, int64_t row_begin, int64_t row_end,
                   double *coef_flops);
 }  // namespace wq

@@ -2,6 +2,7 @@
 symbol of include/wq.h; the host rule solver reproduces the paper's rules;
 the per-row tables agree with the oracle's; bookkeeping and argument
 checks."""
+import ctypes
 import os
 import re
 
@@ -225,7 +226,7 @@ def test_comparison_rule_tables_match_oracle(p):
     with pytest.raises(wq.WqError):
         wq.wq_rules_build(2, p, (4, 4), wq.WQ_RULES_GAUSS_LEGENDRE | wq.WQ_RULES_NEWTON_COTES)
     with pytest.raises(wq.WqError):
-        wq.wq_rules_build(2, p, (4, 4), 8)
+        wq.wq_rules_build(2, p, (4, 4), 16)
 
 
 def test_comparison_rule_point_counts():
@@ -238,3 +239,55 @@ def test_comparison_rule_point_counts():
             for kind in (0, 1):
                 assert all(len(R.row(0, kind, r)[0]) == cnt for r in range(p, 20))
             R.close()
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_boundary_weighted_rules_match_the_oracle(p):
+    # WQ_RULES_BOUNDARY_WEIGHTED: the boundary rows' points (padding of zero
+    # weight dropped) are the oracle's weighted rules, to the solves'
+    # accuracy; interior rows are unchanged; the two kinds' points lie in the
+    # same elements one by one (the kernels take both from one list)
+    import oracle
+
+    for N in (2 * p + 1, 13):
+        n = N + p
+        R = wq.Rules(2, p, (N, N), device=False, rule="wqb")
+        Rw = wq.Rules(2, p, (N, N), device=False)
+        for r in range(n):
+            xs = []
+            for kind in (0, 1):
+                x, W, e = R.row(0, kind, r)
+                xs.append(e)
+                # padding points carry W = 0 in boundary rows (an interior
+                # p = 2 stiffness rule has a genuine zero weight at its centre)
+                keep = (W != 0.0) if (r < p or r > N - 1) else np.ones(len(W), bool)
+                xo, Wo = oracle.row_points(p, N, kind, r, "wqb")
+                o = np.argsort(x[keep])
+                oo = np.argsort(xo)
+                assert len(xo) == keep.sum(), (N, r, kind)
+                assert np.max(np.abs(x[keep][o] - xo[oo])) <= 1e-12
+                assert np.max(np.abs(W[keep][o] - Wo[oo])) <= 1e-12 * max(1.0, np.max(np.abs(Wo)))
+                if p <= r <= N - 1:
+                    xw, Ww, _ = Rw.row(0, kind, r)
+                    assert np.array_equal(x, xw) and np.array_equal(W, Ww)
+            assert np.array_equal(xs[0], xs[1])
+        R.close()
+        Rw.close()
+
+
+def test_boundary_weighted_rules_fewer_points_and_flags():
+    # p = 3: boundary rows 0 and 2 drop from 4 and 12 points to 2 and 3; the
+    # flag does not combine with the comparison rules
+    R = wq.Rules(3, 3, (9, 8, 7), device=False, rule="wqb")
+    Rg = wq.Rules(3, 3, (9, 8, 7), device=False)
+    counts = [len(R.row(0, 0, r)[0]) for r in range(3)]
+    assert counts == [2, 8, 3]
+    assert [len(Rg.row(0, 0, r)[0]) for r in range(3)] == [4, 8, 12]
+    assert R.flops()[0] < Rg.flops()[0]
+    R.close()
+    Rg.close()
+    m = wq.wq_mesh(3, 3, (ctypes.c_int * 3)(5, 5, 5))
+    h = ctypes.c_void_p()
+    for bad in (wq.WQ_RULES_BOUNDARY_WEIGHTED | wq.WQ_RULES_GAUSS_LEGENDRE,
+                wq.WQ_RULES_BOUNDARY_WEIGHTED | wq.WQ_RULES_NEWTON_COTES):
+        assert wq.library().wq_rules_build(ctypes.byref(m), bad, ctypes.byref(h)) == wq.WQ_ERR_ARG
