@@ -54,7 +54,22 @@ DF64_PEAK_TFLOPS = 152 * 128 / 12 * 2 * 2.070e9 / 1e12  # 6.71
 # entries without a capture of the current kernel are absent and report null.
 # "scale": the captured case's rows, when the capture was made on a smaller
 # mesh of the same kernel and its traffic is scaled to the workload's rows.
-TRAFFIC = {}
+_CAP64 = ("ncu --set full --clock-control none -k regex:rows_ug_kernel, python bench.py --workload 3d_p3_64 "
+          "--steps 1 --warmup 3 --no-cpu-baseline --no-variants --no-e2e --prec {}; 64^3 launch scaled by rows")
+TRAFFIC = {
+    ("3d_p3_128", "fp64"): {"bytes": 236.140544e6 + 1.589815e9, "scale_rows": 300763,
+                            "note": "rows_ug_kernel<3,32,M+K,double>: " + _CAP64.format("fp64")},
+    ("3d_p3_128", "df64"): {"bytes": 236.021504e6 + 1.590448e9, "scale_rows": 300763,
+                            "note": "rows_ug_kernel<3,32,M+K,dd>: " + _CAP64.format("df64")},
+    ("3d_p3_128", "mixed"): {"bytes": 118.000640e6 + 767.056128e6, "scale_rows": 300763,
+                             "note": "rows_ug_kernel<3,32,M+K,float>: " + _CAP64.format("mixed")},
+    ("3d_p3_64", "fp64"): {"bytes": 236.140544e6 + 1.589815e9,
+                           "note": "rows_ug_kernel<3,32,M+K,double>: " + _CAP64.format("fp64").split(";")[0]},
+    ("3d_p3_64", "df64"): {"bytes": 236.021504e6 + 1.590448e9,
+                           "note": "rows_ug_kernel<3,32,M+K,dd>: " + _CAP64.format("df64").split(";")[0]},
+    ("3d_p3_64", "mixed"): {"bytes": 118.000640e6 + 767.056128e6,
+                            "note": "rows_ug_kernel<3,32,M+K,float>: " + _CAP64.format("mixed").split(";")[0]},
+}
 
 
 def measured_peaks():
@@ -401,6 +416,9 @@ def main():
     if tr and world == 1:
         roof["traffic"] = tr["bytes"] * (R.rows / tr["scale_rows"] if tr.get("scale_rows") else 1.0)
         roof["traffic_note"] = tr["note"]
+        # the dominant kernel's algorithmic bytes: the band written plus the
+        # partial contractions U it reads
+        roof["traffic_over_band_bytes"] = roof["traffic"] / bytes_step
     else:
         roof["traffic"] = None
 
