@@ -360,6 +360,17 @@ wq_status wq_batch_set_config(wq_batch *batch, const int *config);
  * each `reps` times on `stream` after one warm-up (the plan's outputs are
  * written), keeps the fastest and recaptures the graph.  *best_ms (may be
  * NULL) receives its mean time.  Synchronises the device.
+ * Persisted cache: when the environment variable WQ_AUTOTUNE_CACHE names a
+ * file, the call first looks up the plan's key there -- the GPU (name,
+ * compute capability, SM count), the precision, the kernels' occupancy
+ * limits, the degree mix, the row count and a hash of the patches' degrees,
+ * element counts and coefficient presence -- and, on a hit whose
+ * configuration the plan accepts, applies it and returns its stored time
+ * without timing anything.  On a miss it times as above and adds or
+ * replaces the entry (the file is a JSON object, one entry per line:
+ *   "<key>": {"config": [chunk, u_ctas, ctas, order], "ms": t}
+ * rewritten through a temporary file and a rename; a failed write is not
+ * an error).
  */
 wq_status wq_batch_tune(wq_batch *batch, void *stream, int reps, double *best_ms);
 /* Synchronises the plan's device and frees the plan. */

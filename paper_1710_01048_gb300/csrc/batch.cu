@@ -5,8 +5,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "batch.cuh"
@@ -192,6 +196,38 @@ wq_status apply_config(wq_batch *B, const int *cfg) {
     return st;
   }
   return capture(B);
+}
+
+// The autotuner cache's key: the GPU (name, compute capability, SMs), the
+// precision, the occupancy limits of this build's two kernels, the degree mix
+// and a hash (64-bit FNV-1a) of the patches' shapes in plan order; empty on
+// a CUDA error.
+std::string cache_key(const wq_batch *B) {
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, B->device) != cudaSuccess) return std::string();
+  int np2 = 0, np3 = 0;
+  long long rows = 0;
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&h](long long v) {
+    for (int i = 0; i < 8; i++) {
+      h ^= (uint64_t)((v >> (8 * i)) & 0xff);
+      h *= 1099511628211ull;
+    }
+  };
+  for (const wq_patch &P : B->patches) {
+    const wq_rules *R = P.rules;
+    (R->p == 2 ? np2 : np3)++;
+    rows += (long long)R->n[0] * R->n[1] * R->n[2];
+    mix(R->p);
+    for (int a = 0; a < 3; a++) mix(R->nel[a]);
+    mix(P.coef != nullptr);
+  }
+  char buf[384];
+  std::snprintf(buf, sizeof(buf), "v1|%s|cc%d.%d|sm%d|%s|occ%d,%d|p2x%d,p3x%d|rows%lld|shape%016llx", prop.name,
+                prop.major, prop.minor, prop.multiProcessorCount,
+                B->prec == WQ_FP64 ? "fp64" : B->prec == WQ_MIXED ? "mixed" : "df64", B->max_uctas, B->max_ctas, np2,
+                np3, rows, (unsigned long long)h);
+  return wq::tune_cache_clean_key(buf);
 }
 
 void destroy(wq_batch *B) {
@@ -410,6 +446,19 @@ wq_status wq_batch_set_config(wq_batch *B, const int *config) {
 
 wq_status wq_batch_tune(wq_batch *B, void *stream, int reps, double *best_ms) {
   if (!B || reps < 1) return WQ_ERR_ARG;
+  const char *cache = std::getenv("WQ_AUTOTUNE_CACHE");
+  std::string key;
+  if (cache && *cache) {
+    key = cache_key(B);
+    int cfg[4];
+    double ms = 0.0;
+    // a cached configuration the plan cannot take (another build's CTA
+    // limits, a chunk its tables do not fit) is timed again
+    if (!key.empty() && wq::tune_cache_lookup(cache, key, cfg, &ms) && apply_config(B, cfg) == WQ_OK) {
+      if (best_ms) *best_ms = ms;
+      return WQ_OK;
+    }
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int chunks[] = {32, 24, 16};
   std::vector<int> ctas, uctas;
@@ -453,7 +502,9 @@ wq_status wq_batch_tune(wq_batch *B, void *stream, int reps, double *best_ms) {
   cudaEventDestroy(e1);
   if (st != WQ_OK) return st;
   if (best_ms) *best_ms = best_t;
-  return apply_config(B, best);
+  st = apply_config(B, best);
+  if (st == WQ_OK && !key.empty()) wq::tune_cache_store(cache, key, best, best_t);  // best effort
+  return st;
 }
 
 wq_status wq_assemble_batch(const wq_patch *patches, int npatch, wq_precision prec, void *stream) {

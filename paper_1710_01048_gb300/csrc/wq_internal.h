@@ -5,6 +5,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
+#include <string>
 #include <vector>
 
 #include "../../include/wq.h"
@@ -119,6 +120,10 @@ int max_chunk_points(const wq_rules *R, int T);
 // t h from the low end, W = Wl h^(1-kind)); WQ_ERR_UNSUPPORTED where none is
 // defined (Gauss-Legendre is used there).
 wq_status boundary_rule(int p, int kind, int r, double *t, double *Wl, int *npts);
+// tune_cache.cpp: the batch autotuner's cache file (one JSON entry per line)
+std::string tune_cache_clean_key(const std::string &raw);
+bool tune_cache_lookup(const char *path, const std::string &key, int cfg[4], double *ms);
+bool tune_cache_store(const char *path, const std::string &key, const int cfg[4], double ms);
 double flop_count(const wq_rules *R, int want_m, int want_k, int64_t row_begin, int64_t row_end,
                   double *coef_flops);
 }  // namespace wq

@@ -6,6 +6,8 @@ Every patch's bands must be bit-identical to a single-patch
 wq_assemble_mass_stiffness call in the same precision (the batch runs the
 same per-chunk arithmetic), whatever the chunk lengths, CTA count or item
 order; a few patches are also compared with the oracle."""
+import json
+
 import numpy as np
 import pytest
 
@@ -62,7 +64,8 @@ def test_batch_equals_single_patch_calls(prec):
     B.close()
 
 
-def test_batch_configurations_and_tuner():
+def test_batch_configurations_and_tuner(monkeypatch):
+    monkeypatch.delenv("WQ_AUTOTUNE_CACHE", raising=False)
     patches, _ = make_patches(SMALL, "fp64", seed=3)
     B = wq.Batch(patches, "fp64")
     mu, mx = B.config["max_u_ctas_per_sm"], B.config["max_ctas_per_sm"]
@@ -89,6 +92,59 @@ def test_batch_configurations_and_tuner():
     B.check()
     assert_matches_single(patches, "fp64")
     B.close()
+
+
+def _cfg(B):
+    c = B.config
+    return [c["chunk"], c["u_ctas_per_sm"], c["ctas_per_sm"], c["order"]]
+
+
+def test_tuner_cache(tmp_path, monkeypatch):
+    path = tmp_path / "tune.json"
+    monkeypatch.setenv("WQ_AUTOTUNE_CACHE", str(path))
+    patches, _ = make_patches(SMALL[:5], "mixed", seed=7)
+    B = wq.Batch(patches, "mixed")
+    ms = B.tune(reps=1)
+    assert ms > 0
+    d = json.loads(path.read_text())
+    assert len(d) == 1
+    key, ent = next(iter(d.items()))
+    assert ent["config"] == _cfg(B) and abs(ent["ms"] - ms) <= 1e-5 * ms
+    assert "|mixed|" in key and f"|sm{torch.cuda.get_device_properties(0).multi_processor_count}|" in key
+    B.close()
+    # plant another valid configuration and a time no run takes: a new plan of
+    # the same patches comes back with both, so its tune() timed nothing
+    planted = [16, 1, 1, 1 - ent["config"][3]]
+    path.write_text('{\n  "%s": {"config": [%d, %d, %d, %d], "ms": 1234.5}\n}\n' % (key, *planted))
+    for _, _, _, M, K in patches:
+        M.fill_(float("nan"))
+        K.fill_(float("nan"))
+    B2 = wq.Batch(patches, "mixed")
+    assert B2.tune(reps=1) == 1234.5
+    assert _cfg(B2) == planted
+    B2.launch()
+    B2.check()
+    assert_matches_single(patches, "mixed")
+    B2.close()
+    # another precision or another patch set is another key: timed, and added
+    # beside the planted entry
+    B3 = wq.Batch(patches, "fp64")
+    ms3 = B3.tune(reps=1)
+    assert 0 < ms3 < 1234.5
+    B4 = wq.Batch(patches[:3], "mixed")
+    B4.tune(reps=1)
+    d = json.loads(path.read_text())
+    assert len(d) == 3 and d[key] == {"config": planted, "ms": 1234.5}
+    B3.close()
+    B4.close()
+    # a cached configuration the plan rejects is timed again and replaced
+    path.write_text('{\n  "%s": {"config": [32, 999, 1, 0], "ms": 1234.5}\n}\n' % key)
+    B5 = wq.Batch(patches, "mixed")
+    ms5 = B5.tune(reps=1)
+    assert ms5 < 1234.5
+    d = json.loads(path.read_text())
+    assert d[key]["config"] == _cfg(B5) and d[key]["config"][1] != 999
+    B5.close()
 
 
 def test_graph_replay_reads_new_inputs_and_one_shot():
