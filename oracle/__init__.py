@@ -71,6 +71,10 @@ def _load():
     lib.wqo_assemble_rule.argtypes = [I, I, I, PI, PD, PD, PD, PD, LL, LL, PD, PD, I]
     lib.wqo_boundary_rule.argtypes = [I, I, I, PD, PD, PI, PD]
     lib.wqo_row_points_mode.argtypes = [I, I, I, I, I, PD, PD]
+    lib.wqo_cross_rule.argtypes = [I, PD, PD, PD, PD]
+    lib.wqo_row_points_cross.argtypes = [I, I, I, I, PD, PD]
+    lib.wqo_assemble_general.argtypes = [I, I, PI, PD, PD, LL, LL, PD, PD, I]
+    lib.wqo_assemble_gl_net.argtypes = [I, I, PI, PD, PD, I, LL, LL, PD, PD, I]
     _lib = lib
     return lib
 
@@ -290,3 +294,83 @@ def gradient(dim, p, nel, geom, G=None, H=None):
     if st:
         raise RuntimeError(f"oracle gradient failed (status {st})")
     return grad
+
+
+# ------------------------------------------------------------------ maps with a full control net
+def cross_rule(p: int):
+    """The mixed-derivative rules of the non-separable stiffness terms (read
+    as in wq_oracle.c, wqo_cross_rule): nodes y on the cardinal support
+    [0, p+1] shared by kind 2 (weights w for the weight N', tests N) and
+    kind 3 (weights v for the weight N, tests N').  Returns (y, w, v,
+    max_residual)."""
+    y = np.zeros(p + 1)
+    w = np.zeros(p + 1)
+    v = np.zeros(p + 1)
+    res = ctypes.c_double(0.0)
+    st = _load().wqo_cross_rule(p, _pd(y), _pd(w), _pd(v), ctypes.byref(res))
+    if st:
+        raise RuntimeError(f"oracle cross rule p={p} failed (status {st})")
+    return y, w, v, res.value
+
+
+def row_points_cross(p: int, nel: int, kind: int, r: int):
+    """Points and weights of row r of one direction for kind 2 (weight B_r',
+    tests B_s) or kind 3 (weight B_r, tests B_s')."""
+    x = np.zeros(16)
+    W = np.zeros(16)
+    L = _load().wqo_row_points_cross(p, nel, kind, r, _pd(x), _pd(W))
+    if L < 0:
+        raise ValueError("bad row or kind")
+    return x[:L].copy(), W[:L].copy()
+
+
+def _net_args(dim, p, nel, net):
+    n = [int(nel[a]) + p for a in range(dim)]
+    net = _f64(net)
+    if net.size != dim * int(np.prod(n)):
+        raise ValueError("net must hold dim * prod(nel + p) values")
+    return net
+
+
+def assemble_general(dim, p, nel, net, coef=None, row_begin=0, row_end=None, mass=True, stiffness=True, threads=0):
+    """Rows [row_begin, row_end) of M and K (full metric) for the map given by
+    its full control net (component a of control point (i1, i2, i3) at
+    net[a * prod(n) + i1 + n1 * (i2 + n2 * i3)]), with the weighted rules of
+    Sec. 3 for the mass and (B', B') terms and the mixed rules (cross_rule)
+    for the off-diagonal metric terms.  Returns (M, K)."""
+    nel = [int(v) for v in nel]
+    n = [nel[a] + p for a in range(dim)]
+    nrows = int(np.prod(n))
+    if row_end is None:
+        row_end = nrows
+    band = (2 * p + 1) ** dim
+    M = np.zeros((row_end - row_begin, band)) if mass else None
+    K = np.zeros((row_end - row_begin, band)) if stiffness else None
+    g = _net_args(dim, p, nel, net)
+    nel_c = (ctypes.c_int * 3)(*(nel + [1] * (3 - dim)))
+    st = _load().wqo_assemble_general(dim, p, nel_c, _pd(g), _pd(_f64(coef)), row_begin, row_end, _pd(M), _pd(K),
+                                      int(threads))
+    if st:
+        raise RuntimeError(f"oracle assemble_general failed (status {st})")
+    return M, K
+
+
+def assemble_gl_net(dim, p, nel, net, coef=None, ng=None, row_begin=0, row_end=None, threads=0):
+    """assemble_gl for the map given by its full control net."""
+    nel = [int(v) for v in nel]
+    if ng is None:
+        ng = p + 3
+    n = [nel[a] + p for a in range(dim)]
+    nrows = int(np.prod(n))
+    if row_end is None:
+        row_end = nrows
+    band = (2 * p + 1) ** dim
+    M = np.zeros((row_end - row_begin, band))
+    K = np.zeros((row_end - row_begin, band))
+    g = _net_args(dim, p, nel, net)
+    nel_c = (ctypes.c_int * 3)(*(nel + [1] * (3 - dim)))
+    st = _load().wqo_assemble_gl_net(dim, p, nel_c, _pd(g), _pd(_f64(coef)), ng, row_begin, row_end, _pd(M), _pd(K),
+                                     int(threads))
+    if st:
+        raise RuntimeError(f"oracle GL assemble (net) failed (status {st})")
+    return M, K

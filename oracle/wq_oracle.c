@@ -25,8 +25,11 @@
  *     nested loops over rows x rule points x band columns.
  *
  * Only the diagonal metric terms have a weighted rule in the paper (Sec. 3.2);
- * the oracle reports the largest off-diagonal metric entry relative to the
- * diagonal ones so tests can confirm the map is separable.
+ * wqo_assemble reports the largest off-diagonal metric entry relative to the
+ * diagonal ones so tests can confirm the map is separable.  For a map given
+ * by its full control net, wqo_assemble_general adds the off-diagonal terms,
+ * integrated with mixed-derivative rules (wqo_cross_rule) whose construction
+ * the paper leaves open; the reading taken is stated there.
  *
  * Band layout of a row r = r1 + n1*(r2 + n2*r3): entry
  *   (d3+p)*(2p+1)^2 + (d2+p)*(2p+1) + (d1+p),  column s_a = r_a + d_a,
@@ -681,6 +684,152 @@ int wqo_boundary_rule(int p, int nu, int r, double *t, double *Wl, int *npts, do
 }
 
 /* ------------------------------------------------------------------ */
+/* Mixed-derivative rules for non-separable maps                        */
+/* ------------------------------------------------------------------ */
+
+/* A map whose Jacobian is not diagonal adds to Eq. Stiffness the terms
+ * dB_r/dxhat_a C_ab dB_s/dxhat_b with a != b.  Their direction-a factor
+ * pairs the weight B_r' with the test functions B_s ("kind 2") and their
+ * direction-b factor the weight B_r with the test functions B_s' ("kind 3");
+ * Sec. 3.2 gives rules for the (B', B') pair only.  Reading taken here (the
+ * paper is silent on these pairs): one node set per interior row serves both
+ * mixed kinds, on the cardinal support [0, p+1],
+ *   kind 2: sum_k w_k N(y_k - d)  = int N'(y) N(y - d) dy,
+ *   kind 3: sum_k v_k N'(y_k - d) = int N(y) N'(y - d) dy,   d = -p..p,
+ * with nodes symmetric about (p+1)/2, w antisymmetric (as the weight N' is)
+ * and v symmetric.  Under these symmetries the conditions of d and -d
+ * coincide and d = 0 holds identically, so each kind keeps the p conditions
+ * d = 1..p.  p = 3: two node pairs, unknowns (y1, y2, w1, w2, v1, v2), six
+ * conditions; p = 2: one pair and the centre node (where the antisymmetric
+ * kind has weight 0), unknowns (y1, w1, v1, vc), four conditions.  One node
+ * per element, as the rules of Sec. 3.  Solved by Newton's method with a
+ * central-difference Jacobian, started from the element midpoints. */
+
+/* int_0^{p+1} N^(nuw)(y) N^(nut)(y - d) dy, element by element with a
+ * Gauss-Legendre rule exact for the piecewise polynomial integrand. */
+static double mixed_moment(int p, int nuw, int nut, int d) {
+  double gx[8], gw[8];
+  int ng = p + 2;
+  gauss_legendre(ng, gx, gw);
+  double s = 0.0;
+  for (int u = 0; u <= p; u++)
+    for (int g = 0; g < ng; g++) {
+      double y = (double)u + 0.5 * (gx[g] + 1.0);
+      s += 0.5 * gw[g] * cardinal(p, nuw, y) * cardinal(p, nut, y - (double)d);
+    }
+  return s;
+}
+
+static void expand_cross(int p, const double *u, double *y, double *w, double *v) {
+  if (p == 2) {
+    y[0] = u[0]; y[1] = 1.5; y[2] = 3.0 - u[0];
+    w[0] = u[1]; w[1] = 0.0; w[2] = -u[1];
+    v[0] = u[2]; v[1] = u[3]; v[2] = u[2];
+  } else {
+    y[0] = u[0]; y[1] = u[1]; y[2] = 4.0 - u[1]; y[3] = 4.0 - u[0];
+    w[0] = u[2]; w[1] = u[3]; w[2] = -u[3]; w[3] = -u[2];
+    v[0] = u[4]; v[1] = u[5]; v[2] = u[5]; v[3] = u[4];
+  }
+}
+
+/* Residual of condition d of kind 2 or 3 (see above). */
+static double cross_residual(int p, int kind, const double *y, const double *w, const double *v, int d) {
+  double s = 0.0;
+  for (int k = 0; k <= p; k++)
+    s += kind == 2 ? w[k] * cardinal(p, 0, y[k] - (double)d) : v[k] * cardinal(p, 1, y[k] - (double)d);
+  return s - (kind == 2 ? mixed_moment(p, 1, 0, d) : mixed_moment(p, 0, 1, d));
+}
+
+static void cross_system(int p, const double *u, double *F) {
+  double y[MAXP + 1], w[MAXP + 1], v[MAXP + 1];
+  expand_cross(p, u, y, w, v);
+  for (int d = 1; d <= p; d++) {
+    F[d - 1] = cross_residual(p, 2, y, w, v, d);
+    F[p + d - 1] = cross_residual(p, 3, y, w, v, d);
+  }
+}
+
+/* The mixed rules (y, w, v), p + 1 nodes each.  Returns 0 when Newton
+ * converged and both kinds meet all 2p+1 conditions to 1e-14 with node k in
+ * element k; *max_resid receives the largest residual. */
+int wqo_cross_rule(int p, double *y, double *w, double *v, double *max_resid) {
+  if (p < 2 || p > MAXP) return 2;
+  int n = 2 * p;
+  double u[6];
+  if (p == 2) { u[0] = 0.5; u[1] = 1.0; u[2] = 0.25; u[3] = 0.5; }
+  else { u[0] = 0.5; u[1] = 1.5; u[2] = 1.0; u[3] = 1.0; u[4] = 0.25; u[5] = 0.25; }
+  for (int it = 0; it < 100; it++) {
+    double F[6], A[36], step[6];
+    cross_system(p, u, F);
+    double fmax = 0.0;
+    for (int e = 0; e < n; e++) if (fabs(F[e]) > fmax) fmax = fabs(F[e]);
+    if (!(fmax < 1e3)) return 3;
+    for (int j = 0; j < n; j++) {
+      double hj = 1e-6 * (fabs(u[j]) > 1.0 ? fabs(u[j]) : 1.0);
+      double up[6], um[6], Fp[6], Fm[6];
+      memcpy(up, u, sizeof(up));
+      memcpy(um, u, sizeof(um));
+      up[j] += hj;
+      um[j] -= hj;
+      cross_system(p, up, Fp);
+      cross_system(p, um, Fm);
+      for (int e = 0; e < n; e++) A[e * n + j] = (Fp[e] - Fm[e]) / (2.0 * hj);
+    }
+    for (int e = 0; e < n; e++) step[e] = -F[e];
+    if (solve_dense(n, A, step)) return 3;
+    double smax = 0.0;
+    for (int j = 0; j < n; j++) {
+      u[j] += step[j];
+      if (fabs(step[j]) > smax) smax = fabs(step[j]);
+    }
+    if (smax < 1e-16 && it > 3) break;
+  }
+  expand_cross(p, u, y, w, v);
+  double mr = 0.0;
+  for (int kind = 2; kind <= 3; kind++)
+    for (int d = -p; d <= p; d++) {
+      double r = fabs(cross_residual(p, kind, y, w, v, d));
+      if (!(r <= mr)) mr = r;
+    }
+  if (max_resid) *max_resid = mr;
+  int bad = !(mr <= 1e-14);
+  for (int k = 0; k <= p; k++)
+    if (!(y[k] > (double)k && y[k] < (double)(k + 1))) bad = 1;
+  return bad ? 3 : 0;
+}
+
+/* Points and weights of row r in one direction for kind 2 (weight B_r', test
+ * functions B_s) or kind 3 (weight B_r, test functions B_s').  Interior rows
+ * (p <= r <= N-1): the mixed rule mapped to supp B_r, x_k = (r - p + y_k) h,
+ * W_k = w_k (kind 2: int B_r' B_s dx = int N' N dy) or W_k = h v_k (kind 3:
+ * B_s' = N'/h).  Other rows: (p+1)-point Gauss-Legendre on each element of
+ * supp B_r with the weight function folded in, as for the other kinds. */
+static int cross_row_rule(const dir1d *D, const double *cy, const double *cw, const double *cv, int kind, int r,
+                          double *x, double *W) {
+  int p = D->p;
+  double h = D->h;
+  if (r >= p && r <= D->N - 1) {
+    for (int k = 0; k <= p; k++) {
+      x[k] = ((double)(r - p) + cy[k]) * h;
+      W[k] = kind == 2 ? cw[k] : h * cv[k];
+    }
+    return p + 1;
+  }
+  double gx[MAXP + 1], gw[MAXP + 1];
+  gauss_legendre(p + 1, gx, gw);
+  int L = 0;
+  int elo = r - p < 0 ? 0 : r - p;
+  int ehi = r > D->N - 1 ? D->N - 1 : r;
+  for (int e = elo; e <= ehi; e++)
+    for (int g = 0; g <= p; g++) {
+      x[L] = ((double)e + 0.5 * (gx[g] + 1.0)) * h;
+      W[L] = 0.5 * h * gw[g] * bspl(D->t, D->nt, r, p, kind == 2 ? 1 : 0, x[L]);
+      L++;
+    }
+  return L;
+}
+
+/* ------------------------------------------------------------------ */
 /* Geometry and coefficient at a parameter point                       */
 /* ------------------------------------------------------------------ */
 
@@ -688,6 +837,10 @@ typedef struct {
   int dim, p;
   dir1d dir[3];
   const double *g[3];  /* 1D control values; control point i = (g1[i1], g2[i2], g3[i3]) */
+  /* or, when not NULL, the full control net (Eq. Gmap1): component a of
+   * control point (i1, i2, i3) at net[a * nctrl + i1 + n1 * (i2 + n2 * i3)] */
+  const double *net;
+  long long nctrl;
   const double *coef;  /* degree-3 coefficient spline, x fastest, or NULL for c = 1 */
 } problem;
 
@@ -735,10 +888,11 @@ static void jacobian_at(const problem *P, const double *x, double J[3][3]) {
       for (int i1 = 0; i1 < cnt[0]; i1++) {
         int idx[3] = {lo[0] + i1, lo[1] + i2, lo[2] + i3};
         int ii[3] = {i1, i2, i3};
+        long long lin = idx[0] + (long long)P->dir[0].n * (idx[1] + (long long)P->dir[1].n * idx[2]);
         for (int b = 0; b < dim; b++) {
           double db = 1.0;
           for (int c = 0; c < dim; c++) db *= (c == b) ? dB[c][ii[c]] : B[c][ii[c]];
-          for (int a = 0; a < dim; a++) J[a][b] += P->g[a][idx[a]] * db;
+          for (int a = 0; a < dim; a++) J[a][b] += (P->net ? P->net[a * P->nctrl + lin] : P->g[a][idx[a]]) * db;
         }
       }
 }
@@ -803,7 +957,21 @@ static int setup_problem(problem *P, int dim, int p, const int *nel, const doubl
     P->g[a] = a < dim ? gs[a] : NULL;
     if (a < dim && !gs[a]) return 2;
   }
+  P->net = NULL;
+  P->nctrl = 1;
+  for (int a = 0; a < dim; a++) P->nctrl *= P->dir[a].n;
   P->coef = coef;
+  return 0;
+}
+
+/* The same for a full control net (dim components of prod n_a values). */
+static int setup_problem_net(problem *P, int dim, int p, const int *nel, const double *net, const double *coef) {
+  if (!net) return 2;
+  const double *gs[3] = {net, net, net}; /* placeholders, unused with a net */
+  int st = setup_problem(P, dim, p, nel, gs[0], gs[1], gs[2], coef);
+  if (st) return st;
+  for (int a = 0; a < 3; a++) P->g[a] = NULL;
+  P->net = net;
   return 0;
 }
 
@@ -919,12 +1087,31 @@ int wqo_assemble_rule(int mode, int dim, int p, const int *nel, const double *g1
  * the full metric) by ng-point Gauss-Legendre on every element of supp B_r:
  * the classical element-wise assembly, exact when the integrand is a
  * piecewise polynomial of degree <= 2 ng - 1 per direction. */
+static int assemble_gl_problem(problem *PP, int ng, long long row_begin, long long row_end, double *M, double *K,
+                               int nthreads);
+
 int wqo_assemble_gl(int dim, int p, const int *nel, const double *g1, const double *g2, const double *g3,
                     const double *coef, int ng, long long row_begin, long long row_end, double *M, double *K,
                     int nthreads) {
   problem P;
   int st = setup_problem(&P, dim, p, nel, g1, g2, g3, coef);
   if (st) return st;
+  return assemble_gl_problem(&P, ng, row_begin, row_end, M, K, nthreads);
+}
+
+/* The same with the map given by its full control net (layout of problem.net). */
+int wqo_assemble_gl_net(int dim, int p, const int *nel, const double *net, const double *coef, int ng,
+                        long long row_begin, long long row_end, double *M, double *K, int nthreads) {
+  problem P;
+  int st = setup_problem_net(&P, dim, p, nel, net, coef);
+  if (st) return st;
+  return assemble_gl_problem(&P, ng, row_begin, row_end, M, K, nthreads);
+}
+
+static int assemble_gl_problem(problem *PP, int ng, long long row_begin, long long row_end, double *M, double *K,
+                               int nthreads) {
+  const problem P = *PP;
+  const int dim = P.dim, p = P.p;
   if (ng < 1 || ng > 16) return 2;
   double gx[16], gw[16];
   gauss_legendre(ng, gx, gw);
@@ -1026,6 +1213,137 @@ int wqo_assemble_gl(int dim, int p, const int *nel, const double *g1, const doub
               }
   }
   return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Weighted-quadrature assembly for a non-separable map                 */
+/* ------------------------------------------------------------------ */
+
+/* |det J| and the metric G = J^-1 J^-T at x (full Jacobian, Eq. Gmap2). */
+static double metric_at(const problem *P, const double *x, double G[3][3]) {
+  double J[3][3], I[3][3];
+  jacobian_at(P, x, J);
+  double det = det3(J);
+  inv3(J, det, I);
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; b < 3; b++) {
+      G[a][b] = 0.0;
+      for (int m = 0; m < 3; m++) G[a][b] += I[a][m] * I[b][m];
+    }
+  return fabs(det);
+}
+
+/* Rows [row_begin, row_end) of M (Eq. Mass) and K (Eq. Stiffness with the
+ * full metric) for the map given by its full control net, each row with its
+ * own rules: M = the mass term; K = sum over a, b of the terms
+ *   int dB_r/dxhat_a  c |det J| (J^-1 J^-T)_ab  dB_s/dxhat_b,
+ * each integrated by the tensor product of one 1D rule per direction d:
+ *   d = a = b: the stiffness rule (kind 1, Eq. GaussQuadSysStiff);
+ *   d = a != b: the mixed rule of kind 2 (weight B_r', tests B_s);
+ *   d = b != a: the mixed rule of kind 3 (weight B_r, tests B_s');
+ *   otherwise: the mass rule (kind 0, Eq. GaussQuadSys);
+ * the factor c |det J| (J^-1 J^-T)_ab (c |det J| for M) evaluated at every
+ * point of that tensor grid.  Boundary rows use Gauss-Legendre in every kind
+ * (Remark closing Sec. 3).  net: dim components of prod(nel_a + p) values
+ * (layout of problem.net); coef as in wqo_assemble.  For a separable net the
+ * off-diagonal metric is exactly zero and this equals wqo_assemble.
+ * Returns 0, 2 for bad arguments, 3 if a rule fails its check. */
+int wqo_assemble_general(int dim, int p, const int *nel, const double *net, const double *coef,
+                         long long row_begin, long long row_end, double *M, double *K, int nthreads) {
+  problem P;
+  int st = setup_problem_net(&P, dim, p, nel, net, coef);
+  if (st) return st;
+  rule_set RS;
+  if (rule_set_init(&RS, p, RULE_WQ)) return 3;
+  double cy[MAXP + 1], cw[MAXP + 1], cv[MAXP + 1], cres;
+  if (wqo_cross_rule(p, cy, cw, cv, &cres)) return 3;
+  int nb = 2 * p + 1;
+  int band = 1;
+  long long nrows = 1;
+  int n[3] = {1, 1, 1};
+  for (int a = 0; a < dim; a++) { band *= nb; n[a] = P.dir[a].n; nrows *= n[a]; }
+  if (row_begin < 0 || row_end > nrows || row_begin > row_end) return 2;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel for schedule(dynamic, 4)
+  for (long long r = row_begin; r < row_end; r++) {
+    int ri[3] = {(int)(r % n[0]), (int)((r / n[0]) % n[1]), (int)(r / ((long long)n[0] * n[1]))};
+    /* each direction's points and weights for the four kinds, and the band
+     * columns' test values there: B_s for kinds 0 and 2, B_s' for 1 and 3 */
+    double x[3][4][MAXL], W[3][4][MAXL], bv[3][4][MAXL][2 * MAXP + 1];
+    int L[3][4];
+    for (int a = 0; a < 3; a++)
+      for (int kind = 0; kind < 4; kind++) {
+        if (a >= dim) {
+          L[a][kind] = 1; x[a][kind][0] = 0.0; W[a][kind][0] = 1.0;
+          for (int d = 0; d < nb; d++) bv[a][kind][0][d] = (d == p) ? 1.0 : 0.0;
+          continue;
+        }
+        const dir1d *D = &P.dir[a];
+        L[a][kind] = kind < 2 ? row_rule(D, &RS, kind, ri[a], x[a][kind], W[a][kind])
+                              : cross_row_rule(D, cy, cw, cv, kind, ri[a], x[a][kind], W[a][kind]);
+        int nut = (kind == 1 || kind == 3);
+        for (int k = 0; k < L[a][kind]; k++)
+          for (int d = -p; d <= p; d++) {
+            int s = ri[a] + d;
+            bv[a][kind][k][d + p] = (s >= 0 && s < D->n) ? bspl(D->t, D->nt, s, p, nut, x[a][kind][k]) : 0.0;
+          }
+      }
+    double *Mr = M ? M + (r - row_begin) * band : NULL;
+    double *Kr = K ? K + (r - row_begin) * band : NULL;
+    if (Mr) memset(Mr, 0, sizeof(double) * band);
+    if (Kr) memset(Kr, 0, sizeof(double) * band);
+    int dlo[3], dhi[3];
+    for (int a = 0; a < 3; a++) { dlo[a] = a < dim ? -p : 0; dhi[a] = a < dim ? p : 0; }
+    /* term -1: mass; term (a, b) = a * dim + b: stiffness */
+    for (int term = -1; term < dim * dim; term++) {
+      if (term < 0 && !Mr) continue;
+      if (term >= 0 && !Kr) continue;
+      int ta = term < 0 ? -1 : term / dim, tb = term < 0 ? -1 : term % dim;
+      int kind[3];
+      for (int d = 0; d < 3; d++) {
+        if (term < 0 || d >= dim) kind[d] = 0;
+        else if (d == ta && d == tb) kind[d] = 1;
+        else if (d == ta) kind[d] = 2;
+        else if (d == tb) kind[d] = 3;
+        else kind[d] = 0;
+      }
+      double *out = term < 0 ? Mr : Kr;
+      for (int k3 = 0; k3 < L[2][kind[2]]; k3++)
+        for (int k2 = 0; k2 < L[1][kind[1]]; k2++)
+          for (int k1 = 0; k1 < L[0][kind[0]]; k1++) {
+            double xp[3] = {x[0][kind[0]][k1], x[1][kind[1]][k2], x[2][kind[2]][k3]};
+            double wprod = W[0][kind[0]][k1] * W[1][kind[1]][k2] * W[2][kind[2]][k3];
+            double G[3][3];
+            double adet = metric_at(&P, xp, G);
+            double C = coef_at(&P, xp) * adet * (term < 0 ? 1.0 : G[ta][tb]);
+            double wc = wprod * C;
+            for (int d3 = dlo[2]; d3 <= dhi[2]; d3++)
+              for (int d2 = dlo[1]; d2 <= dhi[1]; d2++)
+                for (int d1 = dlo[0]; d1 <= dhi[0]; d1++) {
+                  double v = wc * bv[0][kind[0]][k1][d1 + p] * bv[1][kind[1]][k2][d2 + p] *
+                             bv[2][kind[2]][k3][d3 + p];
+                  int bi = 0, mul = 1;
+                  int dd[3] = {d1, d2, d3};
+                  for (int a = 0; a < dim; a++) { bi += (dd[a] + p) * mul; mul *= nb; }
+                  out[bi] += v;
+                }
+          }
+    }
+  }
+  return 0;
+}
+
+/* Points and weights of row r in one direction for kind 2 or 3 (for pins). */
+int wqo_row_points_cross(int p, int N, int kind, int r, double *x, double *W) {
+  dir1d D;
+  if (kind != 2 && kind != 3) return -1;
+  if (dir_init(&D, p, N)) return -1;
+  double cy[MAXP + 1], cw[MAXP + 1], cv[MAXP + 1], res;
+  if (wqo_cross_rule(p, cy, cw, cv, &res)) return -1;
+  if (r < 0 || r >= D.n) return -1;
+  return cross_row_rule(&D, cy, cw, cv, kind, r, x, W);
 }
 
 /* ------------------------------------------------------------------ */

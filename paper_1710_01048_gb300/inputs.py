@@ -14,6 +14,13 @@ that both the CUDA path and the CPU oracle consume:
   with numpy's default_rng(seed) in x-fastest order.
 * ``workload(name)``: the named synthetic workloads (sizes, geometry
   amplitude, coefficient recipe) used by the tests and the benchmark.
+* ``full_net(p, nel, kind, amp)``: the full control net of a non-separable
+  map (component a of control point i at net[a * prod(n) + i1 + n1 * (i2 +
+  n2 * i3)]), the control points being the images of the Greville points
+  under an affine map with shear ('affine', reproduced exactly) or under the
+  warp xi_a + amp * (sin(pi xi_a) + sin(pi xi_b) sin(pi xi_c)), (b, c) the
+  other directions ('warp'); ``net_from_separable`` writes a separable map's
+  1D arrays as such a net.
 """
 from __future__ import annotations
 
@@ -120,6 +127,21 @@ WORKLOADS = {
     "3d_p3_12": dict(dim=3, p=3, nel=(12, 12, 12), amp=0.05, coef="exp", sigma=0.1, seed=0),
 }
 
+# Non-separable maps (full control nets): the warp of full_net with amp 0.05,
+# the same coefficient recipe
+NET_WORKLOADS = {
+    "3d_p3_64_warp": dict(dim=3, p=3, nel=(64, 64, 64), net="warp", amp=0.05, coef="exp", sigma=0.1, seed=0),
+    "3d_p3_128_warp": dict(dim=3, p=3, nel=(128, 128, 128), net="warp", amp=0.05, coef="exp", sigma=0.1, seed=0),
+    "2d_p3_32_warp": dict(dim=2, p=3, nel=(32, 32), net="warp", amp=0.05, coef="sincos", sigma=0.0, seed=0),
+}
+
+
+def make_net(dim, p, nel, net="warp", amp=0.05, coef="one", sigma=0.0, seed=0):
+    """(net, coef) arrays for a non-separable workload description."""
+    nel = tuple(int(v) for v in nel)
+    _, c = make(dim, p, nel, 0.0, coef, sigma, seed)
+    return full_net(p, nel, net, amp), c
+
 
 def make(dim, p, nel, amp=0.0, coef="one", sigma=0.0, seed=0):
     """(geom, coef) arrays for a workload description."""
@@ -134,6 +156,48 @@ def make(dim, p, nel, amp=0.0, coef="one", sigma=0.0, seed=0):
     else:
         raise ValueError(coef)
     return g, c
+
+
+# a fixed sheared affine map (det > 0) and its translation, per dimension
+AFFINE = {2: (np.array([[1.0, 0.35], [-0.2, 0.9]]), np.array([0.1, -0.2])),
+          3: (np.array([[1.0, 0.3, -0.2], [0.1, 0.9, 0.25], [-0.15, 0.2, 1.1]]), np.array([0.1, -0.2, 0.3]))}
+
+
+def _greville_grid(p, nel):
+    dim = len(nel)
+    xs = [greville(p, int(nel[a])) for a in range(dim)]
+    return np.meshgrid(*xs, indexing="ij")  # [a][i1, i2, i3]
+
+
+def _flatten_net(comps):
+    """Component arrays indexed [i1, i2, i3] -> flat net, x fastest per component."""
+    return np.ascontiguousarray(np.concatenate([c.transpose().reshape(-1) for c in comps]))
+
+
+def full_net(p, nel, kind="warp", amp=0.05):
+    dim = len(nel)
+    xi = _greville_grid(p, nel)
+    if kind == "affine":
+        A, b = AFFINE[dim]
+        comps = [sum(A[a, c] * xi[c] for c in range(dim)) + b[a] for a in range(dim)]
+    elif kind == "warp":
+        comps = []
+        for a in range(dim):
+            others = [c for c in range(dim) if c != a]
+            cross = np.ones_like(xi[0])
+            for c in others:
+                cross = cross * np.sin(np.pi * xi[c])
+            comps.append(xi[a] + amp * (np.sin(np.pi * xi[a]) + cross))
+    else:
+        raise ValueError(kind)
+    return _flatten_net(comps)
+
+
+def net_from_separable(p, nel, geom):
+    """The full net of the separable map with 1D control arrays geom."""
+    dim = len(nel)
+    grids = np.meshgrid(*[np.asarray(geom[a], dtype=np.float64) for a in range(dim)], indexing="ij")
+    return _flatten_net(grids)
 
 
 def workload(name):
