@@ -22,7 +22,9 @@
  * x_a = sum_i g_{a,i} B_i(xhat_a), and a coefficient field c multiplying the
  * integrands (c = 1 in Eq. Mass / Eq. Stiffness), given as a degree-3 spline
  * on the same mesh.  Only the diagonal metric terms have a weighted rule in
- * the paper (Sec. 3.2), which is why maps must be separable.
+ * the paper (Sec. 3.2), which is why these calls take separable maps; maps
+ * given by a full control net go through wq_assemble_general, which adds
+ * mixed-derivative rules for the off-diagonal terms.
  *
  * Band layout (output): rows r = r1 + n1*(r2 + n2*r3) with n_a = nel_a + p,
  * each row holding (2p+1)^d entries; entry index
@@ -75,7 +77,12 @@ typedef enum wq_precision {
                    float's exponent range (|values| in 1e-30 .. 1e30) */
 } wq_precision;
 
-enum { WQ_KIND_MASS = 0, WQ_KIND_STIFFNESS = 1 };
+/* Kinds of 1D rules.  MASS and STIFFNESS are the rules of Sec. 3.1 and 3.2
+ * (weight B_r with tests B_s; weight B_r' with tests B_s').  The two mixed
+ * kinds integrate the off-diagonal metric terms of a non-separable map
+ * (wq_assemble_general): MIXED_DW the weight B_r' with the tests B_s,
+ * MIXED_WD the weight B_r with the tests B_s'. */
+enum { WQ_KIND_MASS = 0, WQ_KIND_STIFFNESS = 1, WQ_KIND_MIXED_DW = 2, WQ_KIND_MIXED_WD = 3 };
 enum {
   WQ_RULES_HOST_ONLY = 0,
   WQ_RULES_DEVICE = 1,
@@ -139,6 +146,23 @@ wq_status wq_rule_1d(int degree, int kind, double *tau, double *omega);
 wq_status wq_rule_1d_from(int degree, int kind, const double *start, double *tau, double *omega);
 
 /*
+ * The mixed-derivative rules for the off-diagonal metric terms of a
+ * non-separable map (Eq. Stiffness with a full Jacobian; the paper gives
+ * rules for the diagonal pairs only, Sec. 3.2).  One node set on the
+ * cardinal support [0, p+1] serves both mixed kinds: writes degree+1 nodes
+ * y[k] (one per unit element, ascending, symmetric about (p+1)/2) and the
+ * weights w[k] (antisymmetric) and v[k] (symmetric) such that, for
+ * d = -p..p,
+ *   sum_k w_k N(y_k - d)  = int N'(y) N(y - d) dy   (weight N', tests N),
+ *   sum_k v_k N'(y_k - d) = int N(y) N'(y - d) dy   (weight N, tests N').
+ * By the symmetries each kind has p independent conditions; p = 3 takes two
+ * node pairs (six unknowns), p = 2 one pair and the centre node (four).
+ * Host arrays of length degree+1; WQ_ERR_NO_CONVERGENCE if the Newton solve
+ * or the exactness check fails.
+ */
+wq_status wq_rule_1d_mixed(int degree, double *y, double *w, double *v);
+
+/*
  * Builds the per-direction row tables of a mesh: for every row of every
  * direction and both kinds, the rule points (interior rows: the weighted
  * Gaussian rule mapped to supp B_r; boundary rows: (p+1)-point
@@ -158,8 +182,12 @@ wq_status wq_rules_build(const wq_mesh *mesh, int flags, wq_rules **out);
 void wq_rules_free(wq_rules *rules);
 
 /*
- * Host view of one row's 1D rule: direction dir (0-based, < dim), kind,
- * row index in [0, nel_dir + p).  *npts receives the point count (at most
+ * Host view of one row's 1D rule: direction dir (0-based, < dim), kind
+ * (WQ_KIND_*; the mixed kinds exist for rules objects of the weighted
+ * Gaussian rules without other flags, else WQ_ERR_UNSUPPORTED; their
+ * interior rows use wq_rule_1d_mixed mapped to supp B_r, W = w_k for
+ * MIXED_DW and W = h v_k for MIXED_WD, their boundary rows Gauss-Legendre
+ * with B_r' or B_r folded in), row index in [0, nel_dir + p).  *npts receives the point count (at most
  * degree*(degree+1) for the weighted rules, (degree+1)^2 with
  * WQ_RULES_GAUSS_LEGENDRE); x, w receive the points and combined weights W,
  * elem the element of each point, each with room for *npts values (call
@@ -242,6 +270,37 @@ wq_status wq_assemble_mass_stiffness_host(const wq_rules *rules, const double *c
                                           double *const *geom_dev, double *coef_dev, void *M_dev, void *K_dev,
                                           int64_t row_begin, int64_t row_end, int nchunks, void *stream,
                                           void *copy_stream);
+
+/*
+ * Assembly for a map given by its full control net (Eq. Gmap1): rows
+ * [row_begin, row_end) of M (Eq. Mass) and K (Eq. Stiffness with the full
+ * metric C = c |det J| J^-1 J^-T), in the band layout above.
+ *   net   device, dim * prod(n_a) doubles (n_a = nel_a + p): component a of
+ *         control point (i1, i2, i3) at net[a*prod(n) + i1 + n1*(i2 + n2*i3)];
+ *   coef  device coefficient spline as for wq_assemble_mass_stiffness, or NULL;
+ *   M, K  device bands (double) of row_end - row_begin rows; either (not
+ *         both) may be NULL.
+ * M uses the mass rule in every direction with the factor c |det J| at each
+ * point; K is the sum over a, b of the terms dB_r/dxhat_a C_ab dB_s/dxhat_b,
+ * each with the tensor product of the stiffness rule where d = a = b, the
+ * mixed rule WQ_KIND_MIXED_DW where d = a != b, WQ_KIND_MIXED_WD where
+ * d = b != a and the mass rule in the other directions; the factors are
+ * evaluated at every point from the full Jacobian.  Boundary rows use
+ * Gauss-Legendre in every kind.  Exact (up to rounding) for affine maps with
+ * c = 1; for a separable net the result equals wq_assemble_mass_stiffness
+ * up to rounding.  prec must be WQ_FP64 (else WQ_ERR_UNSUPPORTED); the
+ * rules object must be built with WQ_RULES_DEVICE and no other flag (else
+ * WQ_ERR_UNSUPPORTED).  A Jacobian determinant <= 0 or a non-finite value
+ * is reported by wq_status_check (WQ_ERR_GEOMETRY, WQ_ERR_NONFINITE; the
+ * bands are written with |det J|).  The metric factors of a slab of rows
+ * are kept in a scratch array of the rules object (at most 1 GiB, or one
+ * x3 plane's points if more; the environment variable WQ_GENERAL_SLAB_BYTES
+ * lowers that bound), allocated by the first call that needs it and
+ * grown by later calls (synchronising `stream` first); WQ_ERR_OOM if that
+ * allocation fails.
+ */
+wq_status wq_assemble_general(const wq_rules *rules, const double *net, const double *coef, wq_precision prec,
+                              void *M, void *K, int64_t row_begin, int64_t row_end, void *stream);
 
 /*
  * Matrix-free apply: y_M = M x and y_K = K x for rows [row_begin, row_end)

@@ -20,7 +20,7 @@ WQ_OK, WQ_ERR_ARG, WQ_ERR_UNSUPPORTED, WQ_ERR_NO_CONVERGENCE = 0, 1, 2, 3
 WQ_ERR_GEOMETRY, WQ_ERR_NONFINITE, WQ_ERR_CUDA, WQ_ERR_OOM, WQ_ERR_TIMEOUT = 4, 5, 6, 7, 8
 WQ_FP64, WQ_MIXED, WQ_DF64 = 0, 1, 2
 PRECISIONS = {"fp64": WQ_FP64, "mixed": WQ_MIXED, "df64": WQ_DF64}
-WQ_KIND_MASS, WQ_KIND_STIFFNESS = 0, 1
+WQ_KIND_MASS, WQ_KIND_STIFFNESS, WQ_KIND_MIXED_DW, WQ_KIND_MIXED_WD = 0, 1, 2, 3
 WQ_RULES_HOST_ONLY, WQ_RULES_DEVICE, WQ_RULES_GAUSS_LEGENDRE, WQ_RULES_NEWTON_COTES = 0, 1, 2, 4
 WQ_RULES_BOUNDARY_WEIGHTED = 8
 RULE_FLAGS = {"wq": 0, "gl": WQ_RULES_GAUSS_LEGENDRE, "nc": WQ_RULES_NEWTON_COTES, "wqb": WQ_RULES_BOUNDARY_WEIGHTED}
@@ -31,7 +31,8 @@ EXPORTS = ["wq_status_string", "wq_version", "wq_rule_1d", "wq_rule_1d_from", "w
            "wq_assemble_mass", "wq_assemble_stiffness", "wq_assemble_mass_stiffness", "wq_status_check",
            "wq_assemble_noalloc", "wq_assemble_adjoint", "wq_batch_create", "wq_batch_launch", "wq_batch_status",
            "wq_batch_get_config", "wq_batch_set_config", "wq_batch_tune", "wq_batch_free", "wq_assemble_batch", "wq_band_nnz_rows", "wq_band_to_csr",
-           "wq_apply_mass_stiffness", "wq_assemble_load", "wq_assemble_mass_stiffness_host"]
+           "wq_apply_mass_stiffness", "wq_assemble_load", "wq_assemble_mass_stiffness_host", "wq_rule_1d_mixed",
+           "wq_assemble_general"]
 
 
 class WqError(RuntimeError):
@@ -92,6 +93,8 @@ def _lib():
     lib.wq_assemble_mass_stiffness_host.argtypes = [c_void_p, PP, c_void_p, c_int, c_void_p, c_void_p, PP, c_void_p,
                                                     c_void_p, c_void_p, i64, i64, c_int, c_void_p, c_void_p]
     lib.wq_status_check.argtypes = [c_void_p, c_void_p]
+    lib.wq_rule_1d_mixed.argtypes = [c_int, PD, PD, PD]
+    lib.wq_assemble_general.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, i64, i64, c_void_p]
     lib.wq_assemble_noalloc.argtypes = [c_void_p, PP, c_void_p, c_int, c_void_p, c_void_p, i64, i64, c_void_p, c_int]
     lib.wq_assemble_adjoint.argtypes = [c_void_p, PP, c_int, c_void_p, c_void_p, c_void_p, i64, i64, c_void_p]
     PPatch = ctypes.POINTER(wq_patch)
@@ -144,6 +147,15 @@ def wq_rule_1d(degree, kind):
     om = np.zeros(degree + 1)
     _check(_lib().wq_rule_1d(degree, kind, _pd(tau), _pd(om)), "wq_rule_1d")
     return tau, om
+
+
+def wq_rule_1d_mixed(degree):
+    """(y, w, v) of the mixed-derivative rules (numpy arrays)."""
+    y = np.zeros(degree + 1)
+    w = np.zeros(degree + 1)
+    v = np.zeros(degree + 1)
+    _check(_lib().wq_rule_1d_mixed(degree, _pd(y), _pd(w), _pd(v)), "wq_rule_1d_mixed")
+    return y, w, v
 
 
 def wq_rule_1d_from(degree, kind, start):
@@ -343,6 +355,37 @@ def assemble(rules, geom, coef=None, prec="fp64", mass=True, stiffness=True, row
     else:
         st = wq_assemble_stiffness(rules.handle, gp, cp, p, ctypes.c_void_p(K.data_ptr()), row_begin, row_end, s)
     _check(st, "wq_assemble")
+    if check:
+        _check(wq_status_check(rules.handle, s), "wq_status_check")
+    return M, K
+
+
+def assemble_general(rules, net, coef=None, prec="fp64", mass=True, stiffness=True, row_begin=0, row_end=None,
+                     out=None, stream=None, check=True):
+    """Rows [row_begin, row_end) of M and/or K for the map given by its full
+    control net (wq_assemble_general).  net: float64 CUDA tensor of
+    dim * prod(nel + p) values (component-major, x fastest); coef as for
+    assemble().  Returns (M, K), None for a matrix not asked for."""
+    import torch
+
+    if row_end is None:
+        row_end = rules.rows
+    p = PRECISIONS[prec]
+    assert net.is_cuda and net.dtype == torch.float64 and net.is_contiguous()
+    if coef is not None:
+        assert coef.is_cuda and coef.dtype == torch.float64 and coef.is_contiguous() and coef.numel() == rules.ncoef
+    nrows = row_end - row_begin
+    if out is None:
+        M = torch.empty((nrows, rules.band), dtype=torch.float64, device=net.device) if mass else None
+        K = torch.empty((nrows, rules.band), dtype=torch.float64, device=net.device) if stiffness else None
+    else:
+        M, K = out
+    s = _stream_handle(stream)
+    st = _lib().wq_assemble_general(rules.handle, ctypes.c_void_p(net.data_ptr()),
+                                    ctypes.c_void_p(coef.data_ptr()) if coef is not None else None, p,
+                                    ctypes.c_void_p(M.data_ptr()) if M is not None else None,
+                                    ctypes.c_void_p(K.data_ptr()) if K is not None else None, row_begin, row_end, s)
+    _check(st, "wq_assemble_general")
     if check:
         _check(wq_status_check(rules.handle, s), "wq_status_check")
     return M, K

@@ -218,6 +218,55 @@ wq_status upload(wq_rules *R) {
   R->dev_coefdd = reinterpret_cast<float2 *>(base + coefdd_off);
   R->dev_block = block;
   R->dev_bytes = total;
+  // the mixed-derivative kinds' tables (maps given by a full control net)
+  if (!R->hostx[0].elem.empty()) {
+    size_t xo[3][6], xt = 0;
+    for (int a = 0; a < R->dim; a++) {
+      const wq::HostCross &X = R->hostx[a];
+      const size_t npts = X.elem.size();
+      const size_t sz[6] = {npts * sizeof(int), npts * sizeof(double), npts * sizeof(double),
+                            npts * np * sizeof(double), npts * np * sizeof(double), npts * 4 * sizeof(double)};
+      for (int i = 0; i < 6; i++) {
+        xo[a][i] = xt;
+        xt += align_up(sz[i]);
+      }
+    }
+    void *xb = nullptr;
+    e = cudaMalloc(&xb, xt);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(block);
+      R->dev_block = nullptr;
+      return e == cudaErrorMemoryAllocation ? WQ_ERR_OOM : WQ_ERR_CUDA;
+    }
+    char *xbase = static_cast<char *>(xb);
+    bool xok = true;
+    for (int a = 0; a < R->dim; a++) {
+      const wq::HostCross &X = R->hostx[a];
+      const size_t npts = X.elem.size();
+      const void *src[6] = {X.elem.data(), X.w2.data(), X.w3.data(), X.t0.data(), X.t1.data(), X.beta.data()};
+      const size_t sz[6] = {npts * sizeof(int), npts * sizeof(double), npts * sizeof(double),
+                            npts * np * sizeof(double), npts * np * sizeof(double), npts * 4 * sizeof(double)};
+      for (int i = 0; i < 6; i++)
+        xok = xok && (sz[i] == 0 || cudaMemcpy(xbase + xo[a][i], src[i], sz[i], cudaMemcpyHostToDevice) == cudaSuccess);
+      wq::DevCross &D = R->devx[a];
+      D.elem = reinterpret_cast<const int *>(xbase + xo[a][0]);
+      D.w2 = reinterpret_cast<const double *>(xbase + xo[a][1]);
+      D.w3 = reinterpret_cast<const double *>(xbase + xo[a][2]);
+      D.t0 = reinterpret_cast<const double *>(xbase + xo[a][3]);
+      D.t1 = reinterpret_cast<const double *>(xbase + xo[a][4]);
+      D.beta = reinterpret_cast<const double *>(xbase + xo[a][5]);
+      D.npts = (int)npts;
+    }
+    if (!xok) {
+      cudaFree(xb);
+      cudaFree(block);
+      R->dev_block = nullptr;
+      return WQ_ERR_CUDA;
+    }
+    R->dev_cross = xb;
+    R->dev_bytes += xt;
+  }
   if (R->dim == 3 && R->mode == wq::kModeWQ) {
     const int nb = 2 * R->p + 1;
     const size_t ubytes = (size_t)R->n[1] * R->n[2] * 2 * R->nc[0] * nb * nb * sizeof(double);
@@ -225,7 +274,9 @@ wq_status upload(wq_rules *R) {
     if (e != cudaSuccess) {
       cudaGetLastError();
       cudaFree(block);
+      if (R->dev_cross) cudaFree(R->dev_cross);
       R->dev_block = nullptr;
+      R->dev_cross = nullptr;
       R->dev_U = nullptr;
       return e == cudaErrorMemoryAllocation ? WQ_ERR_OOM : WQ_ERR_CUDA;
     }
@@ -522,6 +573,12 @@ wq_status wq_rule_1d(int degree, int kind, double *tau, double *omega) {
   return wq::default_rule(degree, kind, tau, omega);
 }
 
+wq_status wq_rule_1d_mixed(int degree, double *y, double *w, double *v) {
+  if (!y || !w || !v) return WQ_ERR_ARG;
+  if (degree < 2 || degree > wq::kMaxP) return WQ_ERR_UNSUPPORTED;
+  return wq::mixed_rule(degree, y, w, v);
+}
+
 wq_status wq_rule_1d_from(int degree, int kind, const double *start, double *tau, double *omega) {
   if (!start || !tau || !omega) return WQ_ERR_ARG;
   return wq::solve_rule(degree, kind, start, tau, omega);
@@ -584,13 +641,27 @@ void wq_rules_free(wq_rules *rules) {
     cudaFree(rules->dev_block);
     if (rules->dev_U) cudaFree(rules->dev_U);
     if (rules->dev_adj) cudaFree(rules->dev_adj);
+    if (rules->dev_cross) cudaFree(rules->dev_cross);
+    if (rules->dev_gm) cudaFree(rules->dev_gm);
     if (cur >= 0 && cur != rules->device) cudaSetDevice(cur);
   }
   delete rules;
 }
 
 wq_status wq_rules_row(const wq_rules *R, int dir, int kind, int row, int *npts, double *x, double *w, int *elem) {
-  if (!R || dir < 0 || dir >= R->dim || (kind != 0 && kind != 1) || row < 0 || row >= R->n[dir]) return WQ_ERR_ARG;
+  if (!R || dir < 0 || dir >= R->dim || kind < 0 || kind > 3 || row < 0 || row >= R->n[dir]) return WQ_ERR_ARG;
+  if (kind >= 2) {
+    const wq::HostCross &X = R->hostx[dir];
+    if (X.elem.empty()) return WQ_ERR_UNSUPPORTED;
+    int o0 = X.off[row], o1 = X.off[row + 1];
+    if (npts) *npts = o1 - o0;
+    for (int q = o0; q < o1; q++) {
+      if (x) x[q - o0] = X.x[q];
+      if (w) w[q - o0] = kind == 2 ? X.w2[q] : X.w3[q];
+      if (elem) elem[q - o0] = X.elem[q];
+    }
+    return WQ_OK;
+  }
   const HostDirKind &H = R->host[dir][kind];
   int o0 = H.off[row], o1 = H.off[row + 1];
   if (npts) *npts = o1 - o0;

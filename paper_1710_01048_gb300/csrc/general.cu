@@ -1,0 +1,657 @@
+// Assembly for maps given by a full control net (Eq. Gmap1): the metric
+// C = c |det J| J^-1 J^-T (Eq. Stiffness) is no longer diagonal, nor a
+// product of 1D factors, so it is evaluated point by point.
+//
+// K_rs = sum over a, b of int dB_r/dxhat_a C_ab dB_s/dxhat_b, each term with
+// the tensor product of one 1D rule per direction d: the stiffness rule
+// where d = a = b (Eq. GaussQuadSysStiff), the mixed rule of kind 2 (weight
+// B_r', tests B_s) where d = a != b, that of kind 3 (weight B_r, tests B_s')
+// where d = b != a, the mass rule (Eq. GaussQuadSys) elsewhere; M with the
+// mass rule in every direction and the factor c |det J|.  Kinds 2 and 3
+// share their points, so the terms live on seven point grids (five in 2D):
+//   g0 (m,m,m): c|det J|   g1 (s,m,m): C11   g2 (m,s,m): C22   g3 (m,m,s): C33
+//   g4 (x,x,m): C12        g5 (x,m,x): C13   g6 (m,x,x): C23
+// (m, s, x: the mass, stiffness and mixed point sets of a direction).  Every
+// point of a grid belongs to exactly one row (each row has its own points),
+// so no work is shared between rows except the map's partial contractions.
+//
+// gm_metric3_kernel evaluates the factors of one slab of x3 planes into a
+// scratch array: a CTA takes one x3 point q3, one x2 row r2 and a chunk of
+// x1 points of one (x2, x3) point-kind pair, contracts the control net over
+// x3 (H, shared by the row's x2 points) and x2 (E), then forms the Jacobian,
+// the coefficient and the metric entry at every point of the chunk.
+// gm_rows_kernel assembles one row per warp from its points' factors by sum
+// factorisation, x3 first: per term X = F A3, Y += X A2 over the terms of
+// equal direction-1 kind, band += Y A1 (Eq. Decompo).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "wq_internal.h"
+
+namespace wq {
+namespace {
+
+constexpr int kGmChunk = 128;                   // x1 points per metric item
+constexpr int kGmCols = kGmChunk + 2 * kMaxP + 4;  // x1 control / coefficient columns of one chunk
+constexpr int kGmWarps = 4;                     // rows (warps) per CTA of the row kernel
+constexpr int kGmGrids = 7;
+
+struct GmTab {  // one direction, one point set (m, s, x): what the metric reads
+  const int *elem;
+  const double *t0, *t1, *beta;
+};
+
+struct GmArgs {
+  int dim;
+  int n[3], N[3], nc[3], np[3];
+  const int *off[3];        // row offsets into the point lists (equal for every kind)
+  GmTab tab[3][3];          // [direction][point set m, s, x]
+  const double *W[3][4];    // [direction][weight-test kind 0..3]: combined weights
+  const double *T[3][4];    // the test values there (p+1 per point)
+  const double *net;        // dim components of ntot control values
+  long long ntot;
+  const double *coef;       // may be null: c = 1
+  double *F;                // kGmGrids factor arrays of fstride values
+  long long fstride;
+  int slab_lo, slab_n;      // 3D: x3 points [slab_lo, slab_lo + slab_n); 2D: x2 points
+  long long row_begin, row_end, out_row0;
+  double *M, *K;
+  unsigned *status;
+};
+
+// Point-set pairs (x2, x3) of the metric groups and, per group, the x1 point
+// sets and the grid each feeds.  Component codes: 0 = c|det J|, else 1 + 3a + b.
+struct GmGroup {
+  int k2, k3, ng;
+  int k1[2], grid[2], comp[2];
+};
+__constant__ GmGroup c_groups3[6] = {
+    {0, 0, 2, {0, 1}, {0, 1}, {0, 1 + 0}},  // (m,m): g0 mass, g1 C11
+    {1, 0, 1, {0, 0}, {2, 2}, {1 + 4, 0}},  // (s,m): g2 C22
+    {0, 1, 1, {0, 0}, {3, 3}, {1 + 8, 0}},  // (m,s): g3 C33
+    {2, 0, 1, {2, 0}, {4, 4}, {1 + 1, 0}},  // (x,m): g4 C12
+    {0, 2, 1, {2, 0}, {5, 5}, {1 + 2, 0}},  // (m,x): g5 C13
+    {2, 2, 1, {0, 0}, {6, 6}, {1 + 5, 0}},  // (x,x): g6 C23
+};
+__constant__ GmGroup c_groups2[3] = {
+    {0, 0, 2, {0, 1}, {0, 1}, {0, 1 + 0}},  // (m): g0 mass, g1 C11
+    {1, 0, 1, {0, 0}, {2, 2}, {1 + 4, 0}},  // (s): g2 C22
+    {2, 0, 1, {2, 0}, {4, 4}, {1 + 1, 0}},  // (x): g4 C12
+};
+
+// Terms of K (and M): grid and weight-test kind per direction; grouped by the
+// direction-1 kind so that each group shares the last contraction.
+struct GmTerm {
+  int grid, k[3];
+};
+__constant__ GmTerm c_terms3[10] = {
+    {0, {0, 0, 0}},                                 // M
+    {2, {0, 1, 0}}, {3, {0, 0, 1}}, {6, {0, 2, 3}}, {6, {0, 3, 2}},  // direction-1 kind 0: K22 K33 K23 K32
+    {1, {1, 0, 0}},                                 // kind 1: K11
+    {4, {2, 3, 0}}, {5, {2, 0, 3}},                 // kind 2: K12 K13
+    {4, {3, 2, 0}}, {5, {3, 0, 2}},                 // kind 3: K21 K31
+};
+__constant__ int c_group_start3[6] = {0, 1, 5, 6, 8, 10};
+__constant__ GmTerm c_terms2[5] = {
+    {0, {0, 0, 0}},  // M
+    {2, {0, 1, 0}},  // K22
+    {1, {1, 0, 0}},  // K11
+    {4, {2, 3, 0}},  // K12
+    {4, {3, 2, 0}},  // K21
+};
+__constant__ int c_group_start2[6] = {0, 1, 2, 3, 4, 5};
+
+// The metric entry `comp` at one point from the Jacobian columns j0..j2 (3D).
+__device__ __forceinline__ double metric3(int comp, const double *j0, const double *j1, const double *j2, double c,
+                                          unsigned &bits) {
+  const double a0[3] = {j1[1] * j2[2] - j1[2] * j2[1], j1[2] * j2[0] - j1[0] * j2[2], j1[0] * j2[1] - j1[1] * j2[0]};
+  const double det = j0[0] * a0[0] + j0[1] * a0[1] + j0[2] * a0[2];
+  if (!(det > 0.0)) bits |= isfinite(det) ? kBitGeometry : kBitNonFinite;
+  const double adet = fabs(det);
+  if (comp == 0) return c * adet;
+  const int a = (comp - 1) / 3, b = (comp - 1) % 3;
+  // rows of det * J^-1: a0 = j1 x j2, a1 = j2 x j0, a2 = j0 x j1
+  double ra[3], rb[3];
+  const double *u = a == 0 ? j1 : (a == 1 ? j2 : j0), *v = a == 0 ? j2 : (a == 1 ? j0 : j1);
+  ra[0] = u[1] * v[2] - u[2] * v[1];
+  ra[1] = u[2] * v[0] - u[0] * v[2];
+  ra[2] = u[0] * v[1] - u[1] * v[0];
+  u = b == 0 ? j1 : (b == 1 ? j2 : j0);
+  v = b == 0 ? j2 : (b == 1 ? j0 : j1);
+  rb[0] = u[1] * v[2] - u[2] * v[1];
+  rb[1] = u[2] * v[0] - u[0] * v[2];
+  rb[2] = u[0] * v[1] - u[1] * v[0];
+  return c * (ra[0] * rb[0] + ra[1] * rb[1] + ra[2] * rb[2]) / adet;
+}
+
+// 2D: J = [j0 j1] (columns), det J^-1 rows r0 = (j1.y, -j1.x), r1 = (-j0.y, j0.x).
+__device__ __forceinline__ double metric2(int comp, const double *j0, const double *j1, double c, unsigned &bits) {
+  const double det = j0[0] * j1[1] - j1[0] * j0[1];
+  if (!(det > 0.0)) bits |= isfinite(det) ? kBitGeometry : kBitNonFinite;
+  const double adet = fabs(det);
+  if (comp == 0) return c * adet;
+  const int a = (comp - 1) / 3, b = (comp - 1) % 3;
+  const double ra[2] = {a == 0 ? j1[1] : -j0[1], a == 0 ? -j1[0] : j0[0]};
+  const double rb[2] = {b == 0 ? j1[1] : -j0[1], b == 0 ? -j1[0] : j0[0]};
+  return c * (ra[0] * rb[0] + ra[1] * rb[1]) / adet;
+}
+
+// Smallest of vlo and largest of vhi over the CTA (every thread takes part).
+__device__ __forceinline__ void block_minmax(int vlo, int vhi, int &vmin, int &vmax, int *sred) {
+  int lo = __reduce_min_sync(0xffffffffu, vlo), hi = __reduce_max_sync(0xffffffffu, vhi);
+  if (threadIdx.x == 0) {
+    sred[0] = 0x7fffffff;
+    sred[1] = -1;
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&sred[0], lo);
+    atomicMax(&sred[1], hi);
+  }
+  __syncthreads();
+  vmin = sred[0];
+  vmax = sred[1];
+}
+
+// Shared memory of the 3D metric kernel (doubles): H of the two x3 patterns
+// [2][3][2P+1][kGmCols], the coefficient's Hc [P+4][kGmCols], E [10][kGmCols].
+template <int P> constexpr int metric3_smem_doubles() {
+  return 2 * 3 * (2 * P + 1) * kGmCols + (P + 4) * kGmCols + 10 * kGmCols;
+}
+
+template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3_kernel(const GmArgs A) {
+  constexpr int NP = P + 1, NI2 = 2 * P + 1, NL2 = P + 4, NT = kGmChunk;
+  extern __shared__ double sm[];
+  double *sHv = sm;                      // [a][i2][col]
+  double *sHd = sHv + 3 * NI2 * kGmCols;  // [a][i2][col]
+  double *sHc = sHd + 3 * NI2 * kGmCols;  // [l2][col]
+  double *sE = sHc + NL2 * kGmCols;       // [vv0..2, dv0..2, vd0..2, c][col]
+  __shared__ int sred[2];
+  const int tid = threadIdx.x;
+  const int np1 = A.np[0], np2 = A.np[1];
+  const int nch1 = (np1 + NT - 1) / NT;
+  long long item = blockIdx.x;
+  const int c1 = (int)(item % nch1);
+  item /= nch1;
+  const int r2 = (int)(item % A.n[1]);
+  item /= A.n[1];
+  const int q3l = (int)(item % A.slab_n);
+  const GmGroup grp = c_groups3[(int)(item / A.slab_n)];
+  const int q3 = A.slab_lo + q3l;
+
+  // the x3 point: element and basis values
+  const GmTab &T3 = A.tab[2][grp.k3];
+  const int e3 = T3.elem[q3];
+  double b3v[NP], b3d[NP], c3[4];
+#pragma unroll
+  for (int i = 0; i < NP; i++) {
+    b3v[i] = T3.t0[(size_t)q3 * NP + i];
+    b3d[i] = T3.t1[(size_t)q3 * NP + i];
+  }
+#pragma unroll
+  for (int l = 0; l < 4; l++) c3[l] = T3.beta[(size_t)q3 * 4 + l];
+
+  // the chunk's x1 points and the columns they touch (all point sets share elements)
+  const int qa = c1 * NT, qb = min(np1, qa + NT);
+  const int *elem1 = A.tab[0][0].elem;
+  const int myq = qa + tid;
+  int emin, emax;
+  block_minmax(myq < qb ? elem1[myq] : 0x7fffffff, myq < qb ? elem1[myq] : -1, emin, emax, sred);
+  const int ni1 = emax + P - emin + 1, nl1 = emax + 3 - emin + 1;
+  // the x2 row's elements and the control / coefficient rows they touch
+  const int e2lo = max(0, r2 - P), e2hi = min(A.N[1] - 1, r2);
+  const int ni2 = e2hi + P - e2lo + 1, nl2 = e2hi + 3 - e2lo + 1;
+  const int n1 = A.n[0], n2 = A.n[1], nc1 = A.nc[0], nc2 = A.nc[1];
+
+  // H: contraction of the net over the x3 point's p+1 control layers
+  for (int t = tid; t < ni2 * ni1; t += NT) {
+    const int i2 = e2lo + t / ni1, col = t % ni1, i1 = emin + col;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      const double *g = A.net + a * A.ntot + i1 + (long long)n1 * i2;
+      double hv = 0.0, hd = 0.0;
+#pragma unroll
+      for (int i = 0; i < NP; i++) {
+        const double x = g[(long long)n1 * n2 * (e3 + i)];
+        hv = fma(x, b3v[i], hv);
+        hd = fma(x, b3d[i], hd);
+      }
+      sHv[(a * NI2 + (i2 - e2lo)) * kGmCols + col] = hv;
+      sHd[(a * NI2 + (i2 - e2lo)) * kGmCols + col] = hd;
+    }
+  }
+  if (A.coef)
+    for (int t = tid; t < nl2 * nl1; t += NT) {
+      const int l2 = e2lo + t / nl1, col = t % nl1, l1 = emin + col;
+      const double *g = A.coef + l1 + (long long)nc1 * l2;
+      double hc = 0.0;
+#pragma unroll
+      for (int l = 0; l < 4; l++) hc = fma(g[(long long)nc1 * nc2 * (e3 + l)], c3[l], hc);
+      sHc[(l2 - e2lo) * kGmCols + col] = hc;
+    }
+  __syncthreads();
+
+  unsigned bits = 0;
+  const GmTab &T2 = A.tab[1][grp.k2];
+  const int q2a = A.off[1][r2], q2b = A.off[1][r2 + 1];
+  for (int q2 = q2a; q2 < q2b; q2++) {
+    const int e2 = T2.elem[q2];
+    double b2v[NP], b2d[NP], c2[4];
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+      b2v[i] = T2.t0[(size_t)q2 * NP + i];
+      b2d[i] = T2.t1[(size_t)q2 * NP + i];
+    }
+#pragma unroll
+    for (int l = 0; l < 4; l++) c2[l] = T2.beta[(size_t)q2 * 4 + l];
+    // E: the x2 contraction at this x2 point
+    for (int col = tid; col < ni1; col += NT) {
+#pragma unroll
+      for (int a = 0; a < 3; a++) {
+        double vv = 0.0, dv = 0.0, vd = 0.0;
+#pragma unroll
+        for (int i = 0; i < NP; i++) {
+          const int row = (a * NI2 + (e2 - e2lo + i)) * kGmCols + col;
+          vv = fma(sHv[row], b2v[i], vv);
+          dv = fma(sHv[row], b2d[i], dv);
+          vd = fma(sHd[row], b2v[i], vd);
+        }
+        sE[a * kGmCols + col] = vv;
+        sE[(3 + a) * kGmCols + col] = dv;
+        sE[(6 + a) * kGmCols + col] = vd;
+      }
+    }
+    if (A.coef)
+      for (int col = tid; col < nl1; col += NT) {
+        double ec = 0.0;
+#pragma unroll
+        for (int l = 0; l < 4; l++) ec = fma(sHc[(e2 - e2lo + l) * kGmCols + col], c2[l], ec);
+        sE[9 * kGmCols + col] = ec;
+      }
+    __syncthreads();
+    if (myq < qb) {
+      const int e1 = elem1[myq], o = e1 - emin;
+      for (int gi = 0; gi < grp.ng; gi++) {
+        const GmTab &T1 = A.tab[0][grp.k1[gi]];
+        double j0[3], j1[3], j2[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+          double d1 = 0.0, d2 = 0.0, d3 = 0.0;
+#pragma unroll
+          for (int i = 0; i < NP; i++) {
+            const double bv = T1.t0[(size_t)myq * NP + i], bd = T1.t1[(size_t)myq * NP + i];
+            d1 = fma(sE[a * kGmCols + o + i], bd, d1);
+            d2 = fma(sE[(3 + a) * kGmCols + o + i], bv, d2);
+            d3 = fma(sE[(6 + a) * kGmCols + o + i], bv, d3);
+          }
+          j0[a] = d1;
+          j1[a] = d2;
+          j2[a] = d3;
+        }
+        double c = 1.0;
+        if (A.coef) {
+          c = 0.0;
+#pragma unroll
+          for (int l = 0; l < 4; l++) c = fma(sE[9 * kGmCols + o + l], T1.beta[(size_t)myq * 4 + l], c);
+          if (!isfinite(c)) bits |= kBitNonFinite;
+        }
+        const double f = metric3(grp.comp[gi], j0, j1, j2, c, bits);
+        A.F[grp.grid[gi] * A.fstride + myq + (long long)np1 * (q2 + (long long)np2 * q3l)] = f;
+      }
+    }
+    __syncthreads();
+  }
+  bits = __reduce_or_sync(0xffffffffu, bits);
+  if ((tid & 31) == 0 && bits) atomicOr(A.status, bits);
+}
+
+// 2D: a CTA takes one x2 point (of the group's x2 set) and a chunk of x1
+// points; E is the net's contraction over that point's p+1 control rows.
+template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric2_kernel(const GmArgs A) {
+  constexpr int NP = P + 1, NT = kGmChunk;
+  __shared__ double sE[5 * kGmCols];  // [v0, v1, d0, d1, c][col]
+  __shared__ int sred[2];
+  const int tid = threadIdx.x;
+  const int np1 = A.np[0];
+  const int nch1 = (np1 + NT - 1) / NT;
+  long long item = blockIdx.x;
+  const int c1 = (int)(item % nch1);
+  item /= nch1;
+  const int q2l = (int)(item % A.slab_n);
+  const GmGroup grp = c_groups2[(int)(item / A.slab_n)];
+  const int q2 = A.slab_lo + q2l;
+  const GmTab &T2 = A.tab[1][grp.k2];
+  const int e2 = T2.elem[q2];
+  double b2v[NP], b2d[NP], c2[4];
+#pragma unroll
+  for (int i = 0; i < NP; i++) {
+    b2v[i] = T2.t0[(size_t)q2 * NP + i];
+    b2d[i] = T2.t1[(size_t)q2 * NP + i];
+  }
+#pragma unroll
+  for (int l = 0; l < 4; l++) c2[l] = T2.beta[(size_t)q2 * 4 + l];
+  const int qa = c1 * NT, qb = min(np1, qa + NT);
+  const int *elem1 = A.tab[0][0].elem;
+  const int myq = qa + tid;
+  int emin, emax;
+  block_minmax(myq < qb ? elem1[myq] : 0x7fffffff, myq < qb ? elem1[myq] : -1, emin, emax, sred);
+  const int ni1 = emax + P - emin + 1, nl1 = emax + 3 - emin + 1;
+  const int n1 = A.n[0], nc1 = A.nc[0];
+  for (int col = tid; col < ni1; col += NT) {
+#pragma unroll
+    for (int a = 0; a < 2; a++) {
+      const double *g = A.net + a * A.ntot + emin + col;
+      double v = 0.0, d = 0.0;
+#pragma unroll
+      for (int i = 0; i < NP; i++) {
+        const double x = g[(long long)n1 * (e2 + i)];
+        v = fma(x, b2v[i], v);
+        d = fma(x, b2d[i], d);
+      }
+      sE[a * kGmCols + col] = v;
+      sE[(2 + a) * kGmCols + col] = d;
+    }
+  }
+  if (A.coef)
+    for (int col = tid; col < nl1; col += NT) {
+      const double *g = A.coef + emin + col;
+      double ec = 0.0;
+#pragma unroll
+      for (int l = 0; l < 4; l++) ec = fma(g[(long long)nc1 * (e2 + l)], c2[l], ec);
+      sE[4 * kGmCols + col] = ec;
+    }
+  __syncthreads();
+  unsigned bits = 0;
+  if (myq < qb) {
+    const int o = elem1[myq] - emin;
+    for (int gi = 0; gi < grp.ng; gi++) {
+      const GmTab &T1 = A.tab[0][grp.k1[gi]];
+      double j0[2], j1[2];
+#pragma unroll
+      for (int a = 0; a < 2; a++) {
+        double d1 = 0.0, d2 = 0.0;
+#pragma unroll
+        for (int i = 0; i < NP; i++) {
+          d1 = fma(sE[a * kGmCols + o + i], T1.t1[(size_t)myq * NP + i], d1);
+          d2 = fma(sE[(2 + a) * kGmCols + o + i], T1.t0[(size_t)myq * NP + i], d2);
+        }
+        j0[a] = d1;
+        j1[a] = d2;
+      }
+      double c = 1.0;
+      if (A.coef) {
+        c = 0.0;
+#pragma unroll
+        for (int l = 0; l < 4; l++) c = fma(sE[4 * kGmCols + o + l], T1.beta[(size_t)myq * 4 + l], c);
+        if (!isfinite(c)) bits |= kBitNonFinite;
+      }
+      A.F[grp.grid[gi] * A.fstride + myq + (long long)np1 * q2l] = metric2(grp.comp[gi], j0, j1, c, bits);
+    }
+  }
+  bits = __reduce_or_sync(0xffffffffu, bits);
+  if ((tid & 31) == 0 && bits) atomicOr(A.status, bits);
+}
+
+// Per-warp shared memory of the row kernel (doubles): the weight-test tables
+// [DIM][4][LM][NB], X [LM][LM][NB] (3D), Y [LM][NB^(DIM-1)].
+template <int P, int DIM> constexpr int rows_warp_doubles() {
+  constexpr int NB = 2 * P + 1, LM = P * (P + 1);
+  return DIM * 4 * LM * NB + (DIM == 3 ? LM * LM * NB : 0) + LM * (DIM == 3 ? NB * NB : NB);
+}
+
+template <int P, int DIM> __global__ void __launch_bounds__(32 * kGmWarps) gm_rows_kernel(const GmArgs A) {
+  constexpr int NB = 2 * P + 1, NP = P + 1, LM = P * (P + 1);
+  constexpr int NY = DIM == 3 ? NB * NB : NB;  // columns of Y (s2, s3)
+  constexpr int NBAND = NY * NB;
+  constexpr int NOUT = (NBAND + 31) / 32;
+  extern __shared__ double sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double *sA = sm + warp * rows_warp_doubles<P, DIM>();  // [d][k][q][j]
+  double *sX = sA + DIM * 4 * LM * NB;
+  double *sY = sX + (DIM == 3 ? LM * LM * NB : 0);
+  const long long row = A.row_begin + (long long)blockIdx.x * kGmWarps + warp;
+  if (row >= A.row_end) return;
+  int r[3] = {(int)(row % A.n[0]), (int)((row / A.n[0]) % A.n[1]), 0};
+  if (DIM == 3) r[2] = (int)(row / ((long long)A.n[0] * A.n[1]));
+  int off[3], L[3];
+#pragma unroll
+  for (int d = 0; d < DIM; d++) {
+    off[d] = A.off[d][r[d]];
+    L[d] = A.off[d][r[d] + 1] - off[d];
+  }
+  // weight-test tables: A_d^k[q][j] = W(q) T(q, i), j = elem(q) - r + P + i
+  for (int d = 0; d < DIM; d++) {
+    const int *elem = A.tab[d][0].elem;
+    for (int t = lane; t < 4 * L[d] * NB; t += 32) {
+      const int k = t / (L[d] * NB), q = (t / NB) % L[d], j = t % NB;
+      const int i = j - (elem[off[d] + q] - r[d] + P);
+      double v = 0.0;
+      if (i >= 0 && i < NP) v = A.W[d][k][off[d] + q] * A.T[d][k][(size_t)(off[d] + q) * NP + i];
+      sA[((d * 4 + k) * LM + q) * NB + j] = v;
+    }
+  }
+  __syncwarp();
+  double outK[NOUT];
+#pragma unroll
+  for (int o = 0; o < NOUT; o++) outK[o] = 0.0;
+  const GmTerm *terms = DIM == 3 ? c_terms3 : c_terms2;
+  const int *gstart = DIM == 3 ? c_group_start3 : c_group_start2;
+  const long long ob = (row - A.out_row0) * NBAND;
+  for (int grp = 0; grp < 5; grp++) {
+    if (grp == 0 ? !A.M : !A.K) continue;
+    for (int t = lane; t < L[0] * NY; t += 32) sY[t] = 0.0;
+    __syncwarp();
+    int k1 = 0;
+    for (int ti = gstart[grp]; ti < gstart[grp + 1]; ti++) {
+      const GmTerm tm = terms[ti];
+      k1 = tm.k[0];
+      const double *F = A.F + tm.grid * A.fstride;
+      const double *A2 = sA + ((1 * 4 + tm.k[1]) * LM) * NB;
+      if (DIM == 3) {
+        const double *A3 = sA + ((2 * 4 + tm.k[2]) * LM) * NB;
+        // X[q1][q2][s3] = sum_q3 F[q1, q2, q3] A3[q3][s3]
+        for (int t = lane; t < L[0] * L[1] * NB; t += 32) {
+          const int q1 = t % L[0], q2 = (t / L[0]) % L[1], s3 = t / (L[0] * L[1]);
+          const double *f = F + off[0] + q1 + (long long)A.np[0] * (off[1] + q2 + (long long)A.np[1] *
+                                                                             (off[2] - A.slab_lo));
+          double x = 0.0;
+          for (int q3 = 0; q3 < L[2]; q3++)
+            x = fma(f[(long long)A.np[0] * A.np[1] * q3], A3[q3 * NB + s3], x);
+          sX[t] = x;
+        }
+        __syncwarp();
+        // Y[q1][s2][s3] += sum_q2 X[q1][q2][s3] A2[q2][s2]
+        for (int t = lane; t < L[0] * NB * NB; t += 32) {
+          const int q1 = t % L[0], s2 = (t / L[0]) % NB, s3 = t / (L[0] * NB);
+          double y = sY[t];
+          for (int q2 = 0; q2 < L[1]; q2++) y = fma(sX[q1 + L[0] * (q2 + L[1] * s3)], A2[q2 * NB + s2], y);
+          sY[t] = y;
+        }
+        __syncwarp();
+      } else {
+        // Y[q1][s2] += sum_q2 F[q1, q2] A2[q2][s2]
+        for (int t = lane; t < L[0] * NB; t += 32) {
+          const int q1 = t % L[0], s2 = t / L[0];
+          const double *f = F + off[0] + q1 + (long long)A.np[0] * (off[1] - A.slab_lo);
+          double y = sY[t];
+          for (int q2 = 0; q2 < L[1]; q2++) y = fma(f[(long long)A.np[0] * q2], A2[q2 * NB + s2], y);
+          sY[t] = y;
+        }
+        __syncwarp();
+      }
+    }
+    // band[s1 + NB * s23] += sum_q1 Y[q1][s23] A1[q1][s1]
+    const double *A1 = sA + ((0 * 4 + k1) * LM) * NB;
+#pragma unroll
+    for (int o = 0; o < NOUT; o++) {
+      const int e = lane + 32 * o;
+      if (e < NBAND) {
+        const int s1 = e % NB, s23 = e / NB;
+        double v = 0.0;
+        for (int q1 = 0; q1 < L[0]; q1++) v = fma(sY[q1 + L[0] * s23], A1[q1 * NB + s1], v);
+        if (grp == 0)
+          A.M[ob + e] = v;
+        else
+          outK[o] += v;
+      }
+    }
+    __syncwarp();
+  }
+  if (A.K) {
+#pragma unroll
+    for (int o = 0; o < NOUT; o++) {
+      const int e = lane + 32 * o;
+      if (e < NBAND) A.K[ob + e] = outK[o];
+    }
+  }
+}
+
+template <int P, int DIM> wq_status launch_slab(const GmArgs &a, long long nitems, long long nrows, cudaStream_t s) {
+  if (nitems > 0) {
+    if (DIM == 3) {
+      const size_t smem = sizeof(double) * (size_t)metric3_smem_doubles<P>();
+      gm_metric3_kernel<P><<<(unsigned)nitems, kGmChunk, smem, s>>>(a);
+    } else {
+      gm_metric2_kernel<P><<<(unsigned)nitems, kGmChunk, 0, s>>>(a);
+    }
+    if (cudaGetLastError() != cudaSuccess) return WQ_ERR_CUDA;
+  }
+  if (nrows > 0) {
+    const size_t smem = sizeof(double) * (size_t)rows_warp_doubles<P, DIM>() * kGmWarps;
+    gm_rows_kernel<P, DIM><<<(unsigned)((nrows + kGmWarps - 1) / kGmWarps), 32 * kGmWarps, smem, s>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return WQ_ERR_CUDA;
+  }
+  return WQ_OK;
+}
+
+template <int P, int DIM> cudaError_t set_smem_limits() {
+  cudaError_t e = cudaSuccess;
+  if (DIM == 3)
+    e = cudaFuncSetAttribute(gm_metric3_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * metric3_smem_doubles<P>()));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gm_rows_kernel<P, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * rows_warp_doubles<P, DIM>() * kGmWarps));
+  return e;
+}
+
+// Scratch budget of one slab's factor arrays.
+constexpr size_t kGmScratchBytes = size_t(1) << 30;
+
+}  // namespace
+}  // namespace wq
+
+extern "C" wq_status wq_assemble_general(const wq_rules *R, const double *net, const double *coef,
+                                         wq_precision prec, void *M, void *K, int64_t row_begin, int64_t row_end,
+                                         void *stream) {
+  using namespace wq;
+  TraceRange trace("wq_assemble_general");
+  if (!R || !R->on_device) return WQ_ERR_ARG;
+  const long long nrows = (long long)R->n[0] * R->n[1] * R->n[2];
+  if (row_begin < 0 || row_end > nrows || row_begin > row_end) return WQ_ERR_ARG;
+  if (row_begin == row_end) return WQ_OK;
+  if (!net || (!M && !K)) return WQ_ERR_ARG;
+  if (prec != WQ_FP64) return WQ_ERR_UNSUPPORTED;
+  if (R->mode != kModeWQ || R->bnd_weighted || !R->dev_cross) return WQ_ERR_UNSUPPORTED;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != R->device) return WQ_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int dim = R->dim, p = R->p;
+
+  GmArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.dim = dim;
+  a.ntot = 1;
+  for (int d = 0; d < 3; d++) {
+    a.n[d] = R->n[d];
+    a.N[d] = R->nel[d];
+    a.nc[d] = R->nc[d];
+    a.np[d] = d < dim ? R->dev[d][0].npts : 1;
+    if (d < dim) a.ntot *= R->n[d];
+  }
+  for (int d = 0; d < dim; d++) {
+    const DevDirKind &Dm = R->dev[d][0], &Ds = R->dev[d][1];
+    const DevCross &Dx = R->devx[d];
+    a.off[d] = Dm.off;
+    a.tab[d][0] = GmTab{Dm.elem, Dm.t0, Dm.t1, Dm.beta};
+    a.tab[d][1] = GmTab{Ds.elem, Ds.t0, Ds.t1, Ds.beta};
+    a.tab[d][2] = GmTab{Dx.elem, Dx.t0, Dx.t1, Dx.beta};
+    a.W[d][0] = Dm.w;
+    a.T[d][0] = Dm.t0;
+    a.W[d][1] = Ds.w;
+    a.T[d][1] = Ds.t1;
+    a.W[d][2] = Dx.w2;
+    a.T[d][2] = Dx.t0;
+    a.W[d][3] = Dx.w3;
+    a.T[d][3] = Dx.t1;
+  }
+  a.net = net;
+  a.coef = coef;
+  a.M = static_cast<double *>(M);
+  a.K = static_cast<double *>(K);
+  a.out_row0 = row_begin;
+  a.status = R->dev_status;
+
+  // slabs of whole x3 planes (3D) or x2 lines (2D), their points' factors at most kGmScratchBytes
+  const int sd = dim - 1;                      // slab direction
+  const long long plane = dim == 3 ? (long long)R->n[0] * R->n[1] : R->n[0];
+  const int pl0 = (int)(row_begin / plane), pl1 = (int)((row_end - 1) / plane);
+  const std::vector<int> &offs = R->host[sd][0].off;
+  const long long per_point = (long long)kGmGrids * a.np[0] * (dim == 3 ? a.np[1] : 1) * (long long)sizeof(double);
+  int most = 0;
+  for (int r = pl0; r <= pl1; r++) most = std::max(most, offs[r + 1] - offs[r]);
+  // (WQ_GENERAL_SLAB_BYTES lowers the bound, down to one plane per slab: a
+  // hook for testing the slab loop on small meshes)
+  long long budget = (long long)kGmScratchBytes;
+  if (const char *env = std::getenv("WQ_GENERAL_SLAB_BYTES")) {
+    const long long v = std::atoll(env);
+    if (v > 0 && v < budget) budget = v;
+  }
+  budget = std::max(budget, per_point * most);
+  // grow the scratch to the largest slab of this call
+  std::vector<std::pair<int, int>> slabs;
+  long long need = 0;
+  for (int r = pl0; r <= pl1;) {
+    int e = r;
+    while (e + 1 <= pl1 && per_point * (offs[e + 2] - offs[r]) <= budget) e++;
+    slabs.push_back({r, e});
+    need = std::max(need, per_point * (long long)(offs[e + 1] - offs[r]));
+    r = e + 1;
+  }
+  if ((size_t)need > R->dev_gm_bytes) {
+    if (R->dev_gm) {
+      if (cudaStreamSynchronize(s) != cudaSuccess) return WQ_ERR_CUDA;
+      cudaFree(R->dev_gm);
+      R->dev_gm = nullptr;
+      R->dev_gm_bytes = 0;
+    }
+    if (cudaMalloc(&R->dev_gm, (size_t)need) != cudaSuccess) {
+      cudaGetLastError();
+      return WQ_ERR_OOM;
+    }
+    R->dev_gm_bytes = (size_t)need;
+  }
+  a.F = static_cast<double *>(R->dev_gm);
+  cudaError_t e = p == 2 ? (dim == 3 ? set_smem_limits<2, 3>() : set_smem_limits<2, 2>())
+                         : (dim == 3 ? set_smem_limits<3, 3>() : set_smem_limits<3, 2>());
+  if (e != cudaSuccess) return WQ_ERR_CUDA;
+  for (const auto &sl : slabs) {
+    a.slab_lo = offs[sl.first];
+    a.slab_n = offs[sl.second + 1] - offs[sl.first];
+    a.fstride = (long long)a.np[0] * (dim == 3 ? a.np[1] : 1) * a.slab_n;
+    a.row_begin = std::max((long long)row_begin, sl.first * plane);
+    a.row_end = std::min((long long)row_end, (sl.second + 1) * plane);
+    const long long nch1 = (a.np[0] + kGmChunk - 1) / kGmChunk;
+    const long long nitems = dim == 3 ? 6LL * a.slab_n * R->n[1] * nch1 : 3LL * a.slab_n * nch1;
+    if (nitems > 0x7fffffffLL) return WQ_ERR_UNSUPPORTED;
+    const long long nr = a.row_end - a.row_begin;
+    wq_status st = p == 2 ? (dim == 3 ? launch_slab<2, 3>(a, nitems, nr, s) : launch_slab<2, 2>(a, nitems, nr, s))
+                          : (dim == 3 ? launch_slab<3, 3>(a, nitems, nr, s) : launch_slab<3, 2>(a, nitems, nr, s));
+    if (st != WQ_OK) return st;
+  }
+  return WQ_OK;
+}

@@ -567,6 +567,141 @@ wq_status nc_rule(int p, int kind, double *y, double *v) {
   return WQ_OK;
 }
 
+// ------------------------------------------------------------------ mixed-derivative rules
+// A non-separable map adds to Eq. Stiffness the terms dB_r/dxhat_a C_ab
+// dB_s/dxhat_b, a != b.  In direction a they pair the weight B_r' with the
+// tests B_s (kind 2), in direction b the weight B_r with the tests B_s'
+// (kind 3); Sec. 3.2 covers the (B', B') pair only.  One node set per
+// interior row serves both kinds: on the cardinal support [0, p+1], nodes y
+// symmetric about the centre, kind 2 weights w antisymmetric, kind 3 weights
+// v symmetric, so that each kind keeps the p conditions d = 1..p
+//   sum_k w_k N(y_k - d) = int N' N(. - d) =  N'_{2p+1}(p+1+d),
+//   sum_k v_k N'(y_k - d) = int N N'(. - d) = -N'_{2p+1}(p+1+d)
+// (derivatives of the convolution identity int N N(. - d) = N_{2p+1}(p+1+d)).
+// p = 3: two node pairs, six unknowns; p = 2: one pair and the centre node
+// (antisymmetric weight 0 there), four unknowns.  Newton's method with the
+// analytic Jacobian from the element midpoints; the result must meet all
+// 2p+1 conditions of both kinds and keep one node per element.
+namespace {
+
+struct MixedParam {
+  int nu;
+  double Ay[4][6], by[4], Aw[4][6], Av[4][6];
+};
+
+MixedParam mixed_param(int p) {
+  MixedParam P;
+  std::memset(&P, 0, sizeof(P));
+  if (p == 2) {  // u = (y1, w1, v1, vc)
+    P.nu = 4;
+    P.Ay[0][0] = 1; P.by[1] = 1.5; P.Ay[2][0] = -1; P.by[2] = 3;
+    P.Aw[0][1] = 1; P.Aw[2][1] = -1;
+    P.Av[0][2] = 1; P.Av[1][3] = 1; P.Av[2][2] = 1;
+  } else {  // u = (y1, y2, w1, w2, v1, v2)
+    P.nu = 6;
+    P.Ay[0][0] = 1; P.Ay[1][1] = 1; P.Ay[2][1] = -1; P.by[2] = 4; P.Ay[3][0] = -1; P.by[3] = 4;
+    P.Aw[0][2] = 1; P.Aw[1][3] = 1; P.Aw[2][3] = -1; P.Aw[3][2] = -1;
+    P.Av[0][4] = 1; P.Av[1][5] = 1; P.Av[2][5] = 1; P.Av[3][4] = 1;
+  }
+  return P;
+}
+
+void mixed_expand(const MixedParam &P, int L, const double *u, double *y, double *w, double *v) {
+  for (int k = 0; k < L; k++) {
+    y[k] = P.by[k];
+    w[k] = 0.0;
+    v[k] = 0.0;
+    for (int j = 0; j < P.nu; j++) {
+      y[k] += P.Ay[k][j] * u[j];
+      w[k] += P.Aw[k][j] * u[j];
+      v[k] += P.Av[k][j] * u[j];
+    }
+  }
+}
+
+// int N'(y) N(y - d) dy = N'_{2p+1}(p+1+d) (kind 2; kind 3 is its negative).
+double mixed_moment(int p, int d) {
+  if (d < -p || d > p) return 0.0;
+  const int n = 2 * p + 1;
+  return (double)cardinal_at_integer_num(n, 1, p + 1 + d) / (double)factorial(n - 1);
+}
+
+double mixed_residual(int p, int kind, const double *y, const double *w, const double *v, int d) {
+  double s = 0.0;
+  for (int k = 0; k <= p; k++)
+    s += kind == 2 ? w[k] * cardinal(p, 0, y[k] - d) : v[k] * cardinal(p, 1, y[k] - d);
+  return s - (kind == 2 ? mixed_moment(p, d) : -mixed_moment(p, d));
+}
+
+bool solve_n(int n, double A[6][6], double *b) {
+  for (int c = 0; c < n; c++) {
+    int piv = c;
+    for (int r = c + 1; r < n; r++)
+      if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+    if (A[piv][c] == 0.0) return false;
+    if (piv != c) {
+      for (int k = 0; k < n; k++) std::swap(A[c][k], A[piv][k]);
+      std::swap(b[c], b[piv]);
+    }
+    for (int r = c + 1; r < n; r++) {
+      const double f = A[r][c] / A[c][c];
+      for (int k = c; k < n; k++) A[r][k] -= f * A[c][k];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int r = n - 1; r >= 0; r--) {
+    double t = b[r];
+    for (int k = r + 1; k < n; k++) t -= A[r][k] * b[k];
+    b[r] = t / A[r][r];
+  }
+  return true;
+}
+
+}  // namespace
+
+wq_status mixed_rule(int p, double *y, double *w, double *v) {
+  if (p < 2 || p > kMaxP) return WQ_ERR_UNSUPPORTED;
+  const int L = p + 1;
+  const MixedParam P = mixed_param(p);
+  double u[6];
+  if (p == 2) { u[0] = 0.5; u[1] = 1.0; u[2] = 0.25; u[3] = 0.5; }
+  else { u[0] = 0.5; u[1] = 1.5; u[2] = 1.0; u[3] = 1.0; u[4] = 0.25; u[5] = 0.25; }
+  for (int it = 0; it < 100; it++) {
+    double yy[4], ww[4], vv[4];
+    mixed_expand(P, L, u, yy, ww, vv);
+    double F[6], Jm[6][6];
+    for (int e = 0; e < 2 * p; e++) {
+      const int kind = e < p ? 2 : 3, d = e % p + 1;
+      F[e] = -mixed_residual(p, kind, yy, ww, vv, d);
+      for (int j = 0; j < P.nu; j++) {
+        double t = 0.0;
+        for (int k = 0; k < L; k++) {
+          if (kind == 2)
+            t += ww[k] * cardinal(p, 1, yy[k] - d) * P.Ay[k][j] + cardinal(p, 0, yy[k] - d) * P.Aw[k][j];
+          else
+            t += vv[k] * cardinal(p, 2, yy[k] - d) * P.Ay[k][j] + cardinal(p, 1, yy[k] - d) * P.Av[k][j];
+        }
+        Jm[e][j] = t;
+      }
+    }
+    if (!solve_n(P.nu, Jm, F)) return WQ_ERR_NO_CONVERGENCE;
+    double smax = 0.0;
+    for (int j = 0; j < P.nu; j++) {
+      u[j] += F[j];
+      smax = std::max(smax, std::fabs(F[j]));
+      if (!std::isfinite(u[j]) || std::fabs(u[j]) > 1e6) return WQ_ERR_NO_CONVERGENCE;
+    }
+    if (smax < 1e-16 && it >= 3) break;
+  }
+  mixed_expand(P, L, u, y, w, v);
+  for (int k = 0; k < L; k++)
+    if (!(y[k] > (double)k && y[k] < (double)(k + 1))) return WQ_ERR_NO_CONVERGENCE;
+  for (int kind = 2; kind <= 3; kind++)
+    for (int d = -p; d <= p; d++)
+      if (!(std::fabs(mixed_residual(p, kind, y, w, v, d)) <= 1e-14)) return WQ_ERR_NO_CONVERGENCE;
+  return WQ_OK;
+}
+
 wq_status boundary_rule(int p, int kind, int r, double *t, double *Wl, int *npts) {
   return boundary_rule_impl(p, kind, r, t, Wl, npts);
 }
@@ -698,6 +833,63 @@ wq_status build_host_tables(wq_rules *R) {
         }
       }
       H.off[n] = (int)H.elem.size();
+    }
+  }
+  // mixed-derivative kinds (maps given by a full control net): the mixed
+  // rules on interior rows, Gauss-Legendre with B_r' (kind 2) or B_r (kind
+  // 3) folded in on boundary rows; same point counts and elements per row as
+  // the mass kind
+  for (int a = 0; a < 3; a++) R->hostx[a] = HostCross();
+  if (R->mode == kModeWQ && !R->bnd_weighted) {
+    double my[kMaxP + 1], mw[kMaxP + 1], mv[kMaxP + 1];
+    wq_status st = mixed_rule(p, my, mw, mv);
+    if (st != WQ_OK) return st;
+    for (int a = 0; a < R->dim; a++) {
+      const int N = R->nel[a], n = R->n[a];
+      const double h = 1.0 / (double)N;
+      std::vector<double> tp = knots(p, N), tc = knots(kCoefDeg, N);
+      HostCross &X = R->hostx[a];
+      X.off.assign(n + 1, 0);
+      for (int r = 0; r < n; r++) {
+        X.off[r] = (int)X.elem.size();
+        std::vector<int> pe;
+        std::vector<double> px, pw2, pw3;
+        if (r >= p && r <= N - 1) {
+          for (int k = 0; k <= p; k++) {
+            pe.push_back(r - p + k);
+            px.push_back(((double)(r - p) + my[k]) * h);
+            pw2.push_back(mw[k]);      // int B_r' B_s dx = int N' N dy
+            pw3.push_back(h * mv[k]);  // B_s' = N' / h
+          }
+        } else {
+          const int elo = std::max(0, r - p), ehi = std::min(N - 1, r);
+          for (int e = elo; e <= ehi; e++)
+            for (int g = 0; g <= p; g++) {
+              const double x = ((double)e + 0.5 * (gx[g] + 1.0)) * h;
+              double v[8], dv[8];
+              basis(tp, p, e, x, v, dv);
+              pe.push_back(e);
+              px.push_back(x);
+              pw2.push_back(0.5 * h * gw[g] * dv[r - e]);
+              pw3.push_back(0.5 * h * gw[g] * v[r - e]);
+            }
+        }
+        for (size_t q = 0; q < pe.size(); q++) {
+          double v[8], dv[8], cv[8], cd[8];
+          basis(tp, p, pe[q], px[q], v, dv);
+          basis(tc, kCoefDeg, pe[q], px[q], cv, cd);
+          X.elem.push_back(pe[q]);
+          X.x.push_back(px[q]);
+          X.w2.push_back(pw2[q]);
+          X.w3.push_back(pw3[q]);
+          for (int i = 0; i <= p; i++) {
+            X.t0.push_back(v[i]);
+            X.t1.push_back(dv[i]);
+          }
+          for (int i = 0; i <= kCoefDeg; i++) X.beta.push_back(cv[i]);
+        }
+      }
+      X.off[n] = (int)X.elem.size();
     }
   }
   // lines: D=3 -> (r2, r3), D=2 -> r2; interior when dirs 2..D are interior rows

@@ -48,6 +48,23 @@ struct HostDirKind {
   std::vector<double> beta;  // npts*4: B3_{elem+i}(x)
 };
 
+// One direction of the mixed-derivative kinds (kind 2: weight B_r', tests
+// B_s; kind 3: weight B_r, tests B_s'), which share their points; offsets,
+// point counts and elements per row equal the mass kind's.
+struct HostCross {
+  std::vector<int> off, elem;
+  std::vector<double> x;
+  std::vector<double> w2, w3;  // combined weights of kinds 2 and 3
+  std::vector<double> t0, t1;  // npts*(p+1): B_{elem+i}(x), B'_{elem+i}(x)
+  std::vector<double> beta;    // npts*4: B3_{elem+i}(x)
+};
+
+struct DevCross {
+  const int *elem;
+  const double *w2, *w3, *t0, *t1, *beta;
+  int npts;
+};
+
 // Device view of one direction and kind (all arrays in device memory).
 struct DevDirKind {
   const int *off;
@@ -84,6 +101,7 @@ struct wq_rules {
   double tau[2][wq::kMaxP + 1] = {};
   double omega[2][wq::kMaxP + 1] = {};
   wq::HostDirKind host[3][2];
+  wq::HostCross hostx[3];  // mode 0 without boundary weighted rules only
   wq::Lines lines;
   // device side
   bool on_device = false;
@@ -98,6 +116,12 @@ struct wq_rules {
   float2 *dev_coefdd = nullptr;  // the coefficients as double-float pairs (df64 mode)
   void *dev_U = nullptr;         // 3D: the partial contractions U of every line, [line][2][nc1][(2p+1)^2], 8-byte
                                  // elements (the split assembly path; its own allocation)
+  wq::DevCross devx[3] = {};      // device copy of hostx (its own allocation, dev_cross)
+  void *dev_cross = nullptr;
+  // scratch of the non-separable assembly (the metric factors of a slab of
+  // rows), allocated by the first call that needs it, grown when needed
+  mutable void *dev_gm = nullptr;
+  mutable size_t dev_gm_bytes = 0;
   // the adjoint's per-chunk coefficient blocks (FP64), allocated by the first
   // wq_assemble_adjoint call that needs them and grown when a call needs more
   mutable double *dev_adj = nullptr;
@@ -120,6 +144,9 @@ int max_chunk_points(const wq_rules *R, int T);
 // t h from the low end, W = Wl h^(1-kind)); WQ_ERR_UNSUPPORTED where none is
 // defined (Gauss-Legendre is used there).
 wq_status boundary_rule(int p, int kind, int r, double *t, double *Wl, int *npts);
+// The mixed-derivative rules on the cardinal support: nodes y, kind 2
+// weights w (weight N', tests N), kind 3 weights v (weight N, tests N').
+wq_status mixed_rule(int p, double *y, double *w, double *v);
 // tune_cache.cpp: the batch autotuner's cache file (one JSON entry per line)
 std::string tune_cache_clean_key(const std::string &raw);
 bool tune_cache_lookup(const char *path, const std::string &key, int cfg[4], double *ms);

@@ -291,3 +291,40 @@ def test_boundary_weighted_rules_fewer_points_and_flags():
     for bad in (wq.WQ_RULES_BOUNDARY_WEIGHTED | wq.WQ_RULES_GAUSS_LEGENDRE,
                 wq.WQ_RULES_BOUNDARY_WEIGHTED | wq.WQ_RULES_NEWTON_COTES):
         assert wq.library().wq_rules_build(ctypes.byref(m), bad, ctypes.byref(h)) == wq.WQ_ERR_ARG
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_mixed_rules_match_the_oracle(p):
+    y, w, v = wq.wq_rule_1d_mixed(p)
+    yo, wo, vo, _ = oracle.cross_rule(p)
+    assert np.max(np.abs(y - yo)) <= 1e-15
+    assert np.max(np.abs(w - wo)) <= 2e-15 and np.max(np.abs(v - vo)) <= 2e-15
+
+
+@pytest.mark.parametrize("p", [2, 3])
+@pytest.mark.parametrize("nel", [1, 2, 3, 5, 11])
+def test_mixed_row_tables_match_oracle(p, nel):
+    R = wq.Rules(2, p, (nel, 4), device=False)
+    for kind in (wq.WQ_KIND_MIXED_DW, wq.WQ_KIND_MIXED_WD):
+        for r in range(nel + p):
+            x, W, e = R.row(0, kind, r)
+            xo, Wo = oracle.row_points_cross(p, nel, kind, r)
+            xm, _, em = R.row(0, 0, r)
+            assert len(x) == len(xo) == len(xm)
+            assert np.all(e == em)  # same elements point by point as the mass kind
+            assert np.max(np.abs(x - xo)) < 1e-15
+            assert np.max(np.abs(W - Wo)) < 1e-14 * max(1.0, np.max(np.abs(Wo)))
+    R.close()
+
+
+def test_mixed_kinds_only_with_the_plain_rules():
+    for rule in ("gl", "nc", "wqb"):
+        R = wq.Rules(3, 3, (9, 8, 7), device=False, rule=rule)
+        with pytest.raises(wq.WqError) as ei:
+            R.row(0, wq.WQ_KIND_MIXED_DW, 3)
+        assert ei.value.status == wq.WQ_ERR_UNSUPPORTED
+        R.close()
+    R = wq.Rules(3, 3, (9, 8, 7), device=False)
+    with pytest.raises(wq.WqError):
+        R.row(0, 4, 3)
+    R.close()
