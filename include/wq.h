@@ -278,8 +278,8 @@ wq_status wq_assemble_mass_stiffness_host(const wq_rules *rules, const double *c
  *   net   device, dim * prod(n_a) doubles (n_a = nel_a + p): component a of
  *         control point (i1, i2, i3) at net[a*prod(n) + i1 + n1*(i2 + n2*i3)];
  *   coef  device coefficient spline as for wq_assemble_mass_stiffness, or NULL;
- *   M, K  device bands (double) of row_end - row_begin rows; either (not
- *         both) may be NULL.
+ *   M, K  device bands of row_end - row_begin rows (double for WQ_FP64,
+ *         float for WQ_MIXED); either (not both) may be NULL.
  * M uses the mass rule in every direction with the factor c |det J| at each
  * point; K is the sum over a, b of the terms dB_r/dxhat_a C_ab dB_s/dxhat_b,
  * each with the tensor product of the stiffness rule where d = a = b, the
@@ -288,14 +288,19 @@ wq_status wq_assemble_mass_stiffness_host(const wq_rules *rules, const double *c
  * evaluated at every point from the full Jacobian.  Boundary rows use
  * Gauss-Legendre in every kind.  Exact (up to rounding) for affine maps with
  * c = 1; for a separable net the result equals wq_assemble_mass_stiffness
- * up to rounding.  prec must be WQ_FP64 (else WQ_ERR_UNSUPPORTED); the
- * rules object must be built with WQ_RULES_DEVICE and no other flag (else
- * WQ_ERR_UNSUPPORTED).  A Jacobian determinant <= 0 or a non-finite value
+ * up to rounding.  prec: WQ_FP64 (everything in FP64), or WQ_MIXED: the
+ * Jacobian in FP32 from the net's scaled differences p (P_i - P_{i-1}) /
+ * (t_{i+p} - t_i), formed in FP64 (each column of J is then a sum of the
+ * degree p-1 derivative spline's terms, free of the cancellation of
+ * sum_i P_i B_i'), and the metric and contractions in FP32, ~1e-7 relative;
+ * WQ_DF64 gives WQ_ERR_UNSUPPORTED.  The rules object must be built with
+ * WQ_RULES_DEVICE and no other flag (else WQ_ERR_UNSUPPORTED).  A Jacobian determinant <= 0 or a non-finite value
  * is reported by wq_status_check (WQ_ERR_GEOMETRY, WQ_ERR_NONFINITE; the
  * bands are written with |det J|).  The metric factors of a slab of rows
- * are kept in a scratch array of the rules object (at most 1 GiB, or one
- * x3 plane's points if more; the environment variable WQ_GENERAL_SLAB_BYTES
- * lowers that bound), allocated by the first call that needs it and
+ * (and, for WQ_MIXED, the difference nets, dim^2 floats per control
+ * point) are kept in a scratch array of the rules object (the factors at
+ * most 1 GiB, or one x3 plane's points if more; the environment variable
+ * WQ_GENERAL_SLAB_BYTES lowers that bound), allocated by the first call that needs it and
  * grown by later calls (synchronising `stream` first); WQ_ERR_OOM if that
  * allocation fails.
  */

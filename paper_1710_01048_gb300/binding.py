@@ -365,7 +365,8 @@ def assemble_general(rules, net, coef=None, prec="fp64", mass=True, stiffness=Tr
     """Rows [row_begin, row_end) of M and/or K for the map given by its full
     control net (wq_assemble_general).  net: float64 CUDA tensor of
     dim * prod(nel + p) values (component-major, x fastest); coef as for
-    assemble().  Returns (M, K), None for a matrix not asked for."""
+    assemble(); prec 'fp64' (float64 bands) or 'mixed' (FP32, float32
+    bands).  Returns (M, K), None for a matrix not asked for."""
     import torch
 
     if row_end is None:
@@ -375,9 +376,10 @@ def assemble_general(rules, net, coef=None, prec="fp64", mass=True, stiffness=Tr
     if coef is not None:
         assert coef.is_cuda and coef.dtype == torch.float64 and coef.is_contiguous() and coef.numel() == rules.ncoef
     nrows = row_end - row_begin
+    dt = torch.float32 if p == WQ_MIXED else torch.float64
     if out is None:
-        M = torch.empty((nrows, rules.band), dtype=torch.float64, device=net.device) if mass else None
-        K = torch.empty((nrows, rules.band), dtype=torch.float64, device=net.device) if stiffness else None
+        M = torch.empty((nrows, rules.band), dtype=dt, device=net.device) if mass else None
+        K = torch.empty((nrows, rules.band), dtype=dt, device=net.device) if stiffness else None
     else:
         M, K = out
     s = _stream_handle(stream)

@@ -134,17 +134,17 @@ wq_status upload(wq_rules *R) {
   if (cudaGetDevice(&dev) != cudaSuccess) return WQ_ERR_CUDA;
   int np = R->p + 1;
   size_t total = 0;
-  // sizes per (dir, kind): off, elem, w, t0, t1, beta, v64, v32, beta32, vdd, betadd
-  size_t off_sz[3][2][11];
+  // sizes per (dir, kind): off, elem, w, t0, t1, beta, v64, v32, beta32, vdd, betadd, tl
+  size_t off_sz[3][2][12];
   for (int a = 0; a < R->dim; a++)
     for (int k = 0; k < 2; k++) {
       const HostDirKind &H = R->host[a][k];
       size_t npts = H.elem.size();
-      size_t s[11] = {H.off.size() * sizeof(int), npts * sizeof(int), npts * sizeof(double),
+      size_t s[12] = {H.off.size() * sizeof(int), npts * sizeof(int), npts * sizeof(double),
                       npts * np * sizeof(double), npts * np * sizeof(double), npts * 4 * sizeof(double),
                       npts * np * sizeof(double), npts * np * sizeof(float), npts * 4 * sizeof(float),
-                      npts * np * sizeof(float2), npts * 4 * sizeof(float2)};
-      for (int i = 0; i < 11; i++) {
+                      npts * np * sizeof(float2), npts * 4 * sizeof(float2), npts * (np - 1) * sizeof(double)};
+      for (int i = 0; i < 12; i++) {
         off_sz[a][k][i] = total;
         total += align_up(s[i]);
       }
@@ -190,6 +190,7 @@ wq_status upload(wq_rules *R) {
       ok = ok && put(off_sz[a][k][5], H.beta.data(), npts * 4 * sizeof(double));
       ok = ok && put(off_sz[a][k][8], b32.data(), npts * 4 * sizeof(float));
       ok = ok && put(off_sz[a][k][10], bdd.data(), npts * 4 * sizeof(float2));
+      ok = ok && put(off_sz[a][k][11], H.tl.data(), npts * (np - 1) * sizeof(double));
       wq::DevDirKind &Dk = R->dev[a][k];
       Dk.off = reinterpret_cast<const int *>(base + off_sz[a][k][0]);
       Dk.elem = reinterpret_cast<const int *>(base + off_sz[a][k][1]);
@@ -202,6 +203,7 @@ wq_status upload(wq_rules *R) {
       Dk.beta32 = reinterpret_cast<float *>(base + off_sz[a][k][8]);
       Dk.vdd = reinterpret_cast<float2 *>(base + off_sz[a][k][9]);
       Dk.betadd = reinterpret_cast<float2 *>(base + off_sz[a][k][10]);
+      Dk.tl = reinterpret_cast<const double *>(base + off_sz[a][k][11]);
       Dk.npts = (int)npts;
     }
   ok = ok && put(lines_int, R->lines.interior.data(), R->lines.interior.size() * sizeof(int));
@@ -220,13 +222,14 @@ wq_status upload(wq_rules *R) {
   R->dev_bytes = total;
   // the mixed-derivative kinds' tables (maps given by a full control net)
   if (!R->hostx[0].elem.empty()) {
-    size_t xo[3][6], xt = 0;
+    size_t xo[3][7], xt = 0;
     for (int a = 0; a < R->dim; a++) {
       const wq::HostCross &X = R->hostx[a];
       const size_t npts = X.elem.size();
-      const size_t sz[6] = {npts * sizeof(int), npts * sizeof(double), npts * sizeof(double),
-                            npts * np * sizeof(double), npts * np * sizeof(double), npts * 4 * sizeof(double)};
-      for (int i = 0; i < 6; i++) {
+      const size_t sz[7] = {npts * sizeof(int), npts * sizeof(double), npts * sizeof(double),
+                            npts * np * sizeof(double), npts * np * sizeof(double), npts * 4 * sizeof(double),
+                            npts * (np - 1) * sizeof(double)};
+      for (int i = 0; i < 7; i++) {
         xo[a][i] = xt;
         xt += align_up(sz[i]);
       }
@@ -244,10 +247,12 @@ wq_status upload(wq_rules *R) {
     for (int a = 0; a < R->dim; a++) {
       const wq::HostCross &X = R->hostx[a];
       const size_t npts = X.elem.size();
-      const void *src[6] = {X.elem.data(), X.w2.data(), X.w3.data(), X.t0.data(), X.t1.data(), X.beta.data()};
-      const size_t sz[6] = {npts * sizeof(int), npts * sizeof(double), npts * sizeof(double),
-                            npts * np * sizeof(double), npts * np * sizeof(double), npts * 4 * sizeof(double)};
-      for (int i = 0; i < 6; i++)
+      const void *src[7] = {X.elem.data(), X.w2.data(), X.w3.data(), X.t0.data(), X.t1.data(), X.beta.data(),
+                            X.tl.data()};
+      const size_t sz[7] = {npts * sizeof(int), npts * sizeof(double), npts * sizeof(double),
+                            npts * np * sizeof(double), npts * np * sizeof(double), npts * 4 * sizeof(double),
+                            npts * (np - 1) * sizeof(double)};
+      for (int i = 0; i < 7; i++)
         xok = xok && (sz[i] == 0 || cudaMemcpy(xbase + xo[a][i], src[i], sz[i], cudaMemcpyHostToDevice) == cudaSuccess);
       wq::DevCross &D = R->devx[a];
       D.elem = reinterpret_cast<const int *>(xbase + xo[a][0]);
@@ -256,6 +261,7 @@ wq_status upload(wq_rules *R) {
       D.t0 = reinterpret_cast<const double *>(xbase + xo[a][3]);
       D.t1 = reinterpret_cast<const double *>(xbase + xo[a][4]);
       D.beta = reinterpret_cast<const double *>(xbase + xo[a][5]);
+      D.tl = reinterpret_cast<const double *>(xbase + xo[a][6]);
       D.npts = (int)npts;
     }
     if (!xok) {

@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <type_traits>
 #include <cstring>
 #include <vector>
 
@@ -42,7 +43,7 @@ constexpr int kGmGrids = 7;
 
 struct GmTab {  // one direction, one point set (m, s, x): what the metric reads
   const int *elem;
-  const double *t0, *t1, *beta;
+  const double *t0, *t1, *beta, *tl;
 };
 
 struct GmArgs {
@@ -55,11 +56,13 @@ struct GmArgs {
   const double *net;        // dim components of ntot control values
   long long ntot;
   const double *coef;       // may be null: c = 1
-  double *F;                // kGmGrids factor arrays of fstride values
+  void *F;                  // kGmGrids factor arrays of fstride values (double or float)
+  const float *D;           // FP32 path: scaled differences of the net, [b][a][ntot]
   long long fstride;
   int slab_lo, slab_n;      // 3D: x3 points [slab_lo, slab_lo + slab_n); 2D: x2 points
+  int ib_lo, ib_n;          // the slab's interior x3 planes (2D: x2 lines) [ib_lo, ib_lo + ib_n)
   long long row_begin, row_end, out_row0;
-  double *M, *K;
+  void *M, *K;              // bands, double or float
   unsigned *status;
 };
 
@@ -105,39 +108,52 @@ __constant__ GmTerm c_terms2[5] = {
 };
 __constant__ int c_group_start2[6] = {0, 1, 2, 3, 4, 5};
 
-// The metric entry `comp` at one point from the Jacobian columns j0..j2 (3D).
-__device__ __forceinline__ double metric3(int comp, const double *j0, const double *j1, const double *j2, double c,
+struct V3 {
+  double x, y, z;
+};
+__device__ __forceinline__ V3 cross3(const V3 &u, const V3 &v) {
+  return V3{fma(u.y, v.z, -u.z * v.y), fma(u.z, v.x, -u.x * v.z), fma(u.x, v.y, -u.y * v.x)};
+}
+__device__ __forceinline__ double dot3(const V3 &u, const V3 &v) { return fma(u.x, v.x, fma(u.y, v.y, u.z * v.z)); }
+
+// The metric entry `comp` at one point from the Jacobian columns j0..j2
+// (3D): the rows of det * J^-1 are j1 x j2, j2 x j0, j0 x j1, so
+// c |det J| (J^-1 J^-T)_ab = c (row_a . row_b) / |det J|.  comp is uniform
+// over the CTA (one group per CTA).
+__device__ __forceinline__ double metric3(int comp, const V3 &j0, const V3 &j1, const V3 &j2, double c,
                                           unsigned &bits) {
-  const double a0[3] = {j1[1] * j2[2] - j1[2] * j2[1], j1[2] * j2[0] - j1[0] * j2[2], j1[0] * j2[1] - j1[1] * j2[0]};
-  const double det = j0[0] * a0[0] + j0[1] * a0[1] + j0[2] * a0[2];
+  const V3 a0 = cross3(j1, j2);
+  const double det = dot3(j0, a0);
   if (!(det > 0.0)) bits |= isfinite(det) ? kBitGeometry : kBitNonFinite;
   const double adet = fabs(det);
   if (comp == 0) return c * adet;
   const int a = (comp - 1) / 3, b = (comp - 1) % 3;
-  // rows of det * J^-1: a0 = j1 x j2, a1 = j2 x j0, a2 = j0 x j1
-  double ra[3], rb[3];
-  const double *u = a == 0 ? j1 : (a == 1 ? j2 : j0), *v = a == 0 ? j2 : (a == 1 ? j0 : j1);
-  ra[0] = u[1] * v[2] - u[2] * v[1];
-  ra[1] = u[2] * v[0] - u[0] * v[2];
-  ra[2] = u[0] * v[1] - u[1] * v[0];
-  u = b == 0 ? j1 : (b == 1 ? j2 : j0);
-  v = b == 0 ? j2 : (b == 1 ? j0 : j1);
-  rb[0] = u[1] * v[2] - u[2] * v[1];
-  rb[1] = u[2] * v[0] - u[0] * v[2];
-  rb[2] = u[0] * v[1] - u[1] * v[0];
-  return c * (ra[0] * rb[0] + ra[1] * rb[1] + ra[2] * rb[2]) / adet;
+  V3 ra, rb;
+  if (a == 0)
+    ra = a0;
+  else if (a == 1)
+    ra = cross3(j2, j0);
+  else
+    ra = cross3(j0, j1);
+  if (b == a)
+    rb = ra;
+  else if (b == 1)
+    rb = cross3(j2, j0);
+  else
+    rb = cross3(j0, j1);
+  return c * dot3(ra, rb) / adet;
 }
 
 // 2D: J = [j0 j1] (columns), det J^-1 rows r0 = (j1.y, -j1.x), r1 = (-j0.y, j0.x).
 __device__ __forceinline__ double metric2(int comp, const double *j0, const double *j1, double c, unsigned &bits) {
-  const double det = j0[0] * j1[1] - j1[0] * j0[1];
+  const double det = fma(j0[0], j1[1], -j1[0] * j0[1]);
   if (!(det > 0.0)) bits |= isfinite(det) ? kBitGeometry : kBitNonFinite;
   const double adet = fabs(det);
   if (comp == 0) return c * adet;
   const int a = (comp - 1) / 3, b = (comp - 1) % 3;
   const double ra[2] = {a == 0 ? j1[1] : -j0[1], a == 0 ? -j1[0] : j0[0]};
   const double rb[2] = {b == 0 ? j1[1] : -j0[1], b == 0 ? -j1[0] : j0[0]};
-  return c * (ra[0] * rb[0] + ra[1] * rb[1]) / adet;
+  return c * fma(ra[0], rb[0], ra[1] * rb[1]) / adet;
 }
 
 // Smallest of vlo and largest of vhi over the CTA (every thread takes part).
@@ -180,7 +196,7 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3_kernel(c
   const int r2 = (int)(item % A.n[1]);
   item /= A.n[1];
   const int q3l = (int)(item % A.slab_n);
-  const GmGroup grp = c_groups3[(int)(item / A.slab_n)];
+  const GmGroup &grp = c_groups3[(int)(item / A.slab_n)];  // read in place (no local copy)
   const int q3 = A.slab_lo + q3l;
 
   // the x3 point: element and basis values
@@ -248,10 +264,12 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3_kernel(c
     }
 #pragma unroll
     for (int l = 0; l < 4; l++) c2[l] = T2.beta[(size_t)q2 * 4 + l];
-    // E: the x2 contraction at this x2 point
-    for (int col = tid; col < ni1; col += NT) {
-#pragma unroll
-      for (int a = 0; a < 3; a++) {
+    // E: the x2 contraction at this x2 point, one (component, column) per
+    // thread, then the coefficient's columns
+    const int nE = 3 * ni1 + (A.coef ? nl1 : 0);
+    for (int t = tid; t < nE; t += NT) {
+      if (t < 3 * ni1) {
+        const int a = t / ni1, col = t - a * ni1;
         double vv = 0.0, dv = 0.0, vd = 0.0;
 #pragma unroll
         for (int i = 0; i < NP; i++) {
@@ -263,35 +281,40 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3_kernel(c
         sE[a * kGmCols + col] = vv;
         sE[(3 + a) * kGmCols + col] = dv;
         sE[(6 + a) * kGmCols + col] = vd;
-      }
-    }
-    if (A.coef)
-      for (int col = tid; col < nl1; col += NT) {
+      } else {
+        const int col = t - 3 * ni1;
         double ec = 0.0;
 #pragma unroll
         for (int l = 0; l < 4; l++) ec = fma(sHc[(e2 - e2lo + l) * kGmCols + col], c2[l], ec);
         sE[9 * kGmCols + col] = ec;
       }
+    }
     __syncthreads();
     if (myq < qb) {
       const int e1 = elem1[myq], o = e1 - emin;
       for (int gi = 0; gi < grp.ng; gi++) {
         const GmTab &T1 = A.tab[0][grp.k1[gi]];
-        double j0[3], j1[3], j2[3];
+        double bv[NP], bd[NP];
+#pragma unroll
+        for (int i = 0; i < NP; i++) {
+          bv[i] = T1.t0[(size_t)myq * NP + i];
+          bd[i] = T1.t1[(size_t)myq * NP + i];
+        }
+        double jc[3][3];  // jc[b][a] = d x_a / d xhat_b
 #pragma unroll
         for (int a = 0; a < 3; a++) {
           double d1 = 0.0, d2 = 0.0, d3 = 0.0;
 #pragma unroll
           for (int i = 0; i < NP; i++) {
-            const double bv = T1.t0[(size_t)myq * NP + i], bd = T1.t1[(size_t)myq * NP + i];
-            d1 = fma(sE[a * kGmCols + o + i], bd, d1);
-            d2 = fma(sE[(3 + a) * kGmCols + o + i], bv, d2);
-            d3 = fma(sE[(6 + a) * kGmCols + o + i], bv, d3);
+            d1 = fma(sE[a * kGmCols + o + i], bd[i], d1);
+            d2 = fma(sE[(3 + a) * kGmCols + o + i], bv[i], d2);
+            d3 = fma(sE[(6 + a) * kGmCols + o + i], bv[i], d3);
           }
-          j0[a] = d1;
-          j1[a] = d2;
-          j2[a] = d3;
+          jc[0][a] = d1;
+          jc[1][a] = d2;
+          jc[2][a] = d3;
         }
+        const V3 j0{jc[0][0], jc[0][1], jc[0][2]}, j1{jc[1][0], jc[1][1], jc[1][2]}, j2{jc[2][0], jc[2][1], jc[2][2]};
         double c = 1.0;
         if (A.coef) {
           c = 0.0;
@@ -300,7 +323,7 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3_kernel(c
           if (!isfinite(c)) bits |= kBitNonFinite;
         }
         const double f = metric3(grp.comp[gi], j0, j1, j2, c, bits);
-        A.F[grp.grid[gi] * A.fstride + myq + (long long)np1 * (q2 + (long long)np2 * q3l)] = f;
+        static_cast<double *>(A.F)[grp.grid[gi] * A.fstride + myq + (long long)np1 * (q2 + (long long)np2 * q3l)] = f;
       }
     }
     __syncthreads();
@@ -322,7 +345,7 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric2_kernel(c
   const int c1 = (int)(item % nch1);
   item /= nch1;
   const int q2l = (int)(item % A.slab_n);
-  const GmGroup grp = c_groups2[(int)(item / A.slab_n)];
+  const GmGroup &grp = c_groups2[(int)(item / A.slab_n)];
   const int q2 = A.slab_lo + q2l;
   const GmTab &T2 = A.tab[1][grp.k2];
   const int e2 = T2.elem[q2];
@@ -389,112 +412,461 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric2_kernel(c
         for (int l = 0; l < 4; l++) c = fma(sE[4 * kGmCols + o + l], T1.beta[(size_t)myq * 4 + l], c);
         if (!isfinite(c)) bits |= kBitNonFinite;
       }
-      A.F[grp.grid[gi] * A.fstride + myq + (long long)np1 * q2l] = metric2(grp.comp[gi], j0, j1, c, bits);
+      static_cast<double *>(A.F)[grp.grid[gi] * A.fstride + myq + (long long)np1 * q2l] =
+          metric2(grp.comp[gi], j0, j1, c, bits);
     }
   }
   bits = __reduce_or_sync(0xffffffffu, bits);
   if ((tid & 31) == 0 && bits) atomicOr(A.status, bits);
 }
 
-// Per-warp shared memory of the row kernel (doubles): the weight-test tables
-// [DIM][4][LM][NB], X [LM][LM][NB] (3D), Y [LM][NB^(DIM-1)].
-template <int P, int DIM> constexpr int rows_warp_doubles() {
-  constexpr int NB = 2 * P + 1, LM = P * (P + 1);
+// ------------------------------------------------------------------ FP32 metric
+// The FP32 form (WQ_MIXED) takes the Jacobian from the scaled differences of
+// the net, D_b[i] = p (P_i - P_{i-e_b}) / (t_{i_b+p} - t_{i_b}) (formed in
+// FP64, rounded once), and the degree p-1 basis of direction b: each column
+// of J is then a sum of terms of one sign pattern without the cancellation
+// of sum_i P_i B_i'(x) (whose terms are ~1/h larger than the result), so
+// FP32 arithmetic keeps ~1e-7 relative accuracy at any mesh size.
+
+__global__ void gm_diff_kernel(const double *__restrict__ net, float *__restrict__ D, int dim, int p, int n0, int n1,
+                               int N0, int N1, int N2, long long ntot) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < ntot;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i[3] = {(int)(idx % n0), (int)((idx / n0) % n1), (int)(idx / ((long long)n0 * n1))};
+    const int Nn[3] = {N0, N1, N2};
+    const long long stride[3] = {1, n0, (long long)n0 * n1};
+    for (int b = 0; b < dim; b++) {
+      const int ib = i[b];
+      const double sc = ib >= 1 ? (double)p * Nn[b] / (double)(min(ib, Nn[b]) - max(ib - p, 0)) : 0.0;
+      for (int a = 0; a < dim; a++)
+        D[(b * dim + a) * ntot + idx] =
+            ib >= 1 ? (float)((net[a * ntot + idx] - net[a * ntot + idx - stride[b]]) * sc) : 0.0f;
+    }
+  }
+}
+
+struct F3 {
+  float x, y, z;
+};
+__device__ __forceinline__ F3 cross3f(const F3 &u, const F3 &v) {
+  return F3{fmaf(u.y, v.z, -u.z * v.y), fmaf(u.z, v.x, -u.x * v.z), fmaf(u.x, v.y, -u.y * v.x)};
+}
+__device__ __forceinline__ float dot3f(const F3 &u, const F3 &v) { return fmaf(u.x, v.x, fmaf(u.y, v.y, u.z * v.z)); }
+
+__device__ __forceinline__ float metric3f(int comp, const F3 &j0, const F3 &j1, const F3 &j2, float c,
+                                          unsigned &bits) {
+  const F3 a0 = cross3f(j1, j2);
+  const float det = dot3f(j0, a0);
+  if (!(det > 0.0f)) bits |= isfinite(det) ? kBitGeometry : kBitNonFinite;
+  const float adet = fabsf(det);
+  if (comp == 0) return c * adet;
+  const int a = (comp - 1) / 3, b = (comp - 1) % 3;
+  F3 ra, rb;
+  if (a == 0)
+    ra = a0;
+  else if (a == 1)
+    ra = cross3f(j2, j0);
+  else
+    ra = cross3f(j0, j1);
+  if (b == a)
+    rb = ra;
+  else if (b == 1)
+    rb = cross3f(j2, j0);
+  else
+    rb = cross3f(j0, j1);
+  return c * dot3f(ra, rb) / adet;
+}
+
+// Shared memory of the 3D FP32 metric kernel (floats): H of the three
+// Jacobian columns [3][3][2P+1][kGmCols], Hc [P+4][kGmCols], E [10][kGmCols].
+template <int P> constexpr int metric3f_smem_floats() {
+  return 9 * (2 * P + 1) * kGmCols + (P + 4) * kGmCols + 10 * kGmCols;
+}
+
+// As gm_metric3_kernel, in FP32 from the difference nets: column b of J
+// contracts D_b with the degree p-1 basis in direction b and the degree-p
+// basis in the others (H: over x3, E: over x2, then x1 at each point).
+template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3f_kernel(const GmArgs A) {
+  constexpr int NP = P + 1, NI2 = 2 * P + 1, NL2 = P + 4, NT = kGmChunk;
+  extern __shared__ float smf[];
+  float *sH = smf;                      // [column b][a][i2][col]
+  float *sHc = sH + 9 * NI2 * kGmCols;  // [l2][col]
+  float *sE = sHc + NL2 * kGmCols;      // [E0 a, E1 a, E2 a, c][col]
+  __shared__ int sred[2];
+  const int tid = threadIdx.x;
+  const int np1 = A.np[0], np2 = A.np[1];
+  const int nch1 = (np1 + NT - 1) / NT;
+  long long item = blockIdx.x;
+  const int c1 = (int)(item % nch1);
+  item /= nch1;
+  const int r2 = (int)(item % A.n[1]);
+  item /= A.n[1];
+  const int q3l = (int)(item % A.slab_n);
+  const GmGroup &grp = c_groups3[(int)(item / A.slab_n)];
+  const int q3 = A.slab_lo + q3l;
+  const GmTab &T3 = A.tab[2][grp.k3];
+  const int e3 = T3.elem[q3];
+  float b3v[NP], b3l[P], c3[4];
+#pragma unroll
+  for (int i = 0; i < NP; i++) b3v[i] = (float)T3.t0[(size_t)q3 * NP + i];
+#pragma unroll
+  for (int j = 0; j < P; j++) b3l[j] = (float)T3.tl[(size_t)q3 * P + j];
+#pragma unroll
+  for (int l = 0; l < 4; l++) c3[l] = (float)T3.beta[(size_t)q3 * 4 + l];
+  const int qa = c1 * NT, qb = min(np1, qa + NT);
+  const int *elem1 = A.tab[0][0].elem;
+  const int myq = qa + tid;
+  int emin, emax;
+  block_minmax(myq < qb ? elem1[myq] : 0x7fffffff, myq < qb ? elem1[myq] : -1, emin, emax, sred);
+  const int ni1 = emax + P - emin + 1, nl1 = emax + 3 - emin + 1;
+  const int e2lo = max(0, r2 - P), e2hi = min(A.N[1] - 1, r2);
+  const int ni2 = e2hi + P - e2lo + 1, nl2 = e2hi + 3 - e2lo + 1;
+  const int n1 = A.n[0], n2 = A.n[1], nc1 = A.nc[0], nc2 = A.nc[1];
+  const long long nt = A.ntot, s3 = (long long)n1 * n2;
+  for (int t = tid; t < ni2 * ni1; t += NT) {
+    const int i2 = e2lo + t / ni1, col = t % ni1;
+    const long long base = emin + col + (long long)n1 * i2;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      const float *d0 = A.D + (0 * 3 + a) * nt + base, *d1 = A.D + (1 * 3 + a) * nt + base,
+                  *d2 = A.D + (2 * 3 + a) * nt + base;
+      float h0 = 0.0f, h1 = 0.0f, h2 = 0.0f;
+#pragma unroll
+      for (int i = 0; i < NP; i++) {
+        h0 = fmaf(d0[s3 * (e3 + i)], b3v[i], h0);
+        h1 = fmaf(d1[s3 * (e3 + i)], b3v[i], h1);
+      }
+#pragma unroll
+      for (int j = 0; j < P; j++) h2 = fmaf(d2[s3 * (e3 + 1 + j)], b3l[j], h2);
+      const int row = (a * NI2 + (i2 - e2lo)) * kGmCols + col;
+      sH[row] = h0;
+      sH[3 * NI2 * kGmCols + row] = h1;
+      sH[6 * NI2 * kGmCols + row] = h2;
+    }
+  }
+  if (A.coef)
+    for (int t = tid; t < nl2 * nl1; t += NT) {
+      const int l2 = e2lo + t / nl1, col = t % nl1, l1 = emin + col;
+      const double *g = A.coef + l1 + (long long)nc1 * l2;
+      float hc = 0.0f;
+#pragma unroll
+      for (int l = 0; l < 4; l++) hc = fmaf((float)g[(long long)nc1 * nc2 * (e3 + l)], c3[l], hc);
+      sHc[(l2 - e2lo) * kGmCols + col] = hc;
+    }
+  __syncthreads();
+  unsigned bits = 0;
+  const GmTab &T2 = A.tab[1][grp.k2];
+  const int q2a = A.off[1][r2], q2b = A.off[1][r2 + 1];
+  for (int q2 = q2a; q2 < q2b; q2++) {
+    const int e2 = T2.elem[q2];
+    float b2v[NP], b2l[P], c2[4];
+#pragma unroll
+    for (int i = 0; i < NP; i++) b2v[i] = (float)T2.t0[(size_t)q2 * NP + i];
+#pragma unroll
+    for (int j = 0; j < P; j++) b2l[j] = (float)T2.tl[(size_t)q2 * P + j];
+#pragma unroll
+    for (int l = 0; l < 4; l++) c2[l] = (float)T2.beta[(size_t)q2 * 4 + l];
+    const int nE = 3 * ni1 + (A.coef ? nl1 : 0);
+    for (int t = tid; t < nE; t += NT) {
+      if (t < 3 * ni1) {
+        const int a = t / ni1, col = t - a * ni1;
+        float v0 = 0.0f, v1 = 0.0f, v2 = 0.0f;
+#pragma unroll
+        for (int i = 0; i < NP; i++) {
+          const int row = (a * NI2 + (e2 - e2lo + i)) * kGmCols + col;
+          v0 = fmaf(sH[row], b2v[i], v0);
+          v2 = fmaf(sH[6 * NI2 * kGmCols + row], b2v[i], v2);
+        }
+#pragma unroll
+        for (int j = 0; j < P; j++)
+          v1 = fmaf(sH[3 * NI2 * kGmCols + (a * NI2 + (e2 - e2lo + 1 + j)) * kGmCols + col], b2l[j], v1);
+        sE[a * kGmCols + col] = v0;
+        sE[(3 + a) * kGmCols + col] = v1;
+        sE[(6 + a) * kGmCols + col] = v2;
+      } else {
+        const int col = t - 3 * ni1;
+        float ec = 0.0f;
+#pragma unroll
+        for (int l = 0; l < 4; l++) ec = fmaf(sHc[(e2 - e2lo + l) * kGmCols + col], c2[l], ec);
+        sE[9 * kGmCols + col] = ec;
+      }
+    }
+    __syncthreads();
+    if (myq < qb) {
+      const int o = elem1[myq] - emin;
+      for (int gi = 0; gi < grp.ng; gi++) {
+        const GmTab &T1 = A.tab[0][grp.k1[gi]];
+        float bv[NP], bl[P];
+#pragma unroll
+        for (int i = 0; i < NP; i++) bv[i] = (float)T1.t0[(size_t)myq * NP + i];
+#pragma unroll
+        for (int j = 0; j < P; j++) bl[j] = (float)T1.tl[(size_t)myq * P + j];
+        float jc[3][3];  // jc[b][a] = d x_a / d xhat_b
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+          float d1 = 0.0f, d2 = 0.0f, d3 = 0.0f;
+#pragma unroll
+          for (int j = 0; j < P; j++) d1 = fmaf(sE[a * kGmCols + o + 1 + j], bl[j], d1);
+#pragma unroll
+          for (int i = 0; i < NP; i++) {
+            d2 = fmaf(sE[(3 + a) * kGmCols + o + i], bv[i], d2);
+            d3 = fmaf(sE[(6 + a) * kGmCols + o + i], bv[i], d3);
+          }
+          jc[0][a] = d1;
+          jc[1][a] = d2;
+          jc[2][a] = d3;
+        }
+        const F3 j0{jc[0][0], jc[0][1], jc[0][2]}, j1{jc[1][0], jc[1][1], jc[1][2]}, j2{jc[2][0], jc[2][1], jc[2][2]};
+        float c = 1.0f;
+        if (A.coef) {
+          c = 0.0f;
+#pragma unroll
+          for (int l = 0; l < 4; l++) c = fmaf(sE[9 * kGmCols + o + l], (float)T1.beta[(size_t)myq * 4 + l], c);
+          if (!isfinite(c)) bits |= kBitNonFinite;
+        }
+        const float f = metric3f(grp.comp[gi], j0, j1, j2, c, bits);
+        static_cast<float *>(A.F)[grp.grid[gi] * A.fstride + myq + (long long)np1 * (q2 + (long long)np2 * q3l)] = f;
+      }
+    }
+    __syncthreads();
+  }
+  bits = __reduce_or_sync(0xffffffffu, bits);
+  if ((tid & 31) == 0 && bits) atomicOr(A.status, bits);
+}
+
+// 2D FP32: E0 = D0 contracted with the x2 point's degree-p basis, E1 = D1
+// with its degree p-1 basis; J's columns at each x1 point.
+template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric2f_kernel(const GmArgs A) {
+  constexpr int NP = P + 1, NT = kGmChunk;
+  __shared__ float sE[5 * kGmCols];  // [E0 a0, a1, E1 a0, a1, c][col]
+  __shared__ int sred[2];
+  const int tid = threadIdx.x;
+  const int np1 = A.np[0];
+  const int nch1 = (np1 + NT - 1) / NT;
+  long long item = blockIdx.x;
+  const int c1 = (int)(item % nch1);
+  item /= nch1;
+  const int q2l = (int)(item % A.slab_n);
+  const GmGroup &grp = c_groups2[(int)(item / A.slab_n)];
+  const int q2 = A.slab_lo + q2l;
+  const GmTab &T2 = A.tab[1][grp.k2];
+  const int e2 = T2.elem[q2];
+  float b2v[NP], b2l[P], c2[4];
+#pragma unroll
+  for (int i = 0; i < NP; i++) b2v[i] = (float)T2.t0[(size_t)q2 * NP + i];
+#pragma unroll
+  for (int j = 0; j < P; j++) b2l[j] = (float)T2.tl[(size_t)q2 * P + j];
+#pragma unroll
+  for (int l = 0; l < 4; l++) c2[l] = (float)T2.beta[(size_t)q2 * 4 + l];
+  const int qa = c1 * NT, qb = min(np1, qa + NT);
+  const int *elem1 = A.tab[0][0].elem;
+  const int myq = qa + tid;
+  int emin, emax;
+  block_minmax(myq < qb ? elem1[myq] : 0x7fffffff, myq < qb ? elem1[myq] : -1, emin, emax, sred);
+  const int ni1 = emax + P - emin + 1, nl1 = emax + 3 - emin + 1;
+  const int n1 = A.n[0], nc1 = A.nc[0];
+  const long long nt = A.ntot;
+  for (int t = tid; t < 2 * ni1; t += NT) {
+    const int a = t / ni1, col = t - a * ni1;
+    const float *d0 = A.D + (0 * 2 + a) * nt + emin + col, *d1 = A.D + (1 * 2 + a) * nt + emin + col;
+    float v0 = 0.0f, v1 = 0.0f;
+#pragma unroll
+    for (int i = 0; i < NP; i++) v0 = fmaf(d0[(long long)n1 * (e2 + i)], b2v[i], v0);
+#pragma unroll
+    for (int j = 0; j < P; j++) v1 = fmaf(d1[(long long)n1 * (e2 + 1 + j)], b2l[j], v1);
+    sE[a * kGmCols + col] = v0;
+    sE[(2 + a) * kGmCols + col] = v1;
+  }
+  if (A.coef)
+    for (int col = tid; col < nl1; col += NT) {
+      const double *g = A.coef + emin + col;
+      float ec = 0.0f;
+#pragma unroll
+      for (int l = 0; l < 4; l++) ec = fmaf((float)g[(long long)nc1 * (e2 + l)], c2[l], ec);
+      sE[4 * kGmCols + col] = ec;
+    }
+  __syncthreads();
+  unsigned bits = 0;
+  if (myq < qb) {
+    const int o = elem1[myq] - emin;
+    for (int gi = 0; gi < grp.ng; gi++) {
+      const GmTab &T1 = A.tab[0][grp.k1[gi]];
+      float j0[2], j1[2];
+#pragma unroll
+      for (int a = 0; a < 2; a++) {
+        float d1 = 0.0f, d2 = 0.0f;
+#pragma unroll
+        for (int j = 0; j < P; j++) d1 = fmaf(sE[a * kGmCols + o + 1 + j], (float)T1.tl[(size_t)myq * P + j], d1);
+#pragma unroll
+        for (int i = 0; i < NP; i++) d2 = fmaf(sE[(2 + a) * kGmCols + o + i], (float)T1.t0[(size_t)myq * NP + i], d2);
+        j0[a] = d1;
+        j1[a] = d2;
+      }
+      float c = 1.0f;
+      if (A.coef) {
+        c = 0.0f;
+#pragma unroll
+        for (int l = 0; l < 4; l++) c = fmaf(sE[4 * kGmCols + o + l], (float)T1.beta[(size_t)myq * 4 + l], c);
+        if (!isfinite(c)) bits |= kBitNonFinite;
+      }
+      const float det = fmaf(j0[0], j1[1], -j1[0] * j0[1]);
+      if (!(det > 0.0f)) bits |= isfinite(det) ? kBitGeometry : kBitNonFinite;
+      const float adet = fabsf(det);
+      const int comp = grp.comp[gi];
+      float f;
+      if (comp == 0) {
+        f = c * adet;
+      } else {
+        const int a = (comp - 1) / 3, b = (comp - 1) % 3;
+        const float ra0 = a == 0 ? j1[1] : -j0[1], ra1 = a == 0 ? -j1[0] : j0[0];
+        const float rb0 = b == 0 ? j1[1] : -j0[1], rb1 = b == 0 ? -j1[0] : j0[0];
+        f = c * fmaf(ra0, rb0, ra1 * rb1) / adet;
+      }
+      static_cast<float *>(A.F)[grp.grid[gi] * A.fstride + myq + (long long)np1 * q2l] = f;
+    }
+  }
+  bits = __reduce_or_sync(0xffffffffu, bits);
+  if ((tid & 31) == 0 && bits) atomicOr(A.status, bits);
+}
+
+// Per-warp shared memory of the row kernel (elements of R): the weight-test tables
+// [DIM][4][LM][NB], X [LM][LM][NB] (3D), Y [LM][NB^(DIM-1)]; LM = the most
+// points of a row in one direction (LC when the row class fixes it).
+template <int P, int DIM, int LC> constexpr int rows_warp_elems() {
+  constexpr int NB = 2 * P + 1, LM = LC ? LC : P * (P + 1);
   return DIM * 4 * LM * NB + (DIM == 3 ? LM * LM * NB : 0) + LM * (DIM == 3 ? NB * NB : NB);
 }
 
-template <int P, int DIM> __global__ void __launch_bounds__(32 * kGmWarps) gm_rows_kernel(const GmArgs A) {
-  constexpr int NB = 2 * P + 1, NP = P + 1, LM = P * (P + 1);
+// One row per warp.  LC = P+1: the interior rows (every direction on its
+// weighted rule, p+1 points), taken from the interior box of the slab with
+// compile-time loop bounds; LC = 0: the other rows of the range (at least
+// one direction on Gauss-Legendre), the interior ones skipped.
+template <int P, int DIM, int LC, int WARPS, typename R>
+__global__ void __launch_bounds__(32 * WARPS) gm_rows_kernel(const GmArgs A) {
+  constexpr int NB = 2 * P + 1, NP = P + 1, LM = LC ? LC : P * (P + 1);
   constexpr int NY = DIM == 3 ? NB * NB : NB;  // columns of Y (s2, s3)
   constexpr int NBAND = NY * NB;
   constexpr int NOUT = (NBAND + 31) / 32;
-  extern __shared__ double sm[];
+  constexpr int UR = LC ? 64 : 1;  // unroll the row loops only where their bounds are compile-time
+  extern __shared__ __align__(16) unsigned char smrows[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double *sA = sm + warp * rows_warp_doubles<P, DIM>();  // [d][k][q][j]
-  double *sX = sA + DIM * 4 * LM * NB;
-  double *sY = sX + (DIM == 3 ? LM * LM * NB : 0);
-  const long long row = A.row_begin + (long long)blockIdx.x * kGmWarps + warp;
-  if (row >= A.row_end) return;
-  int r[3] = {(int)(row % A.n[0]), (int)((row / A.n[0]) % A.n[1]), 0};
-  if (DIM == 3) r[2] = (int)(row / ((long long)A.n[0] * A.n[1]));
+  R *sA = reinterpret_cast<R *>(smrows) + warp * rows_warp_elems<P, DIM, LC>();  // [d][k][q][j]
+  R *sX = sA + DIM * 4 * LM * NB;
+  R *sY = sX + (DIM == 3 ? LM * LM * NB : 0);
+  const long long idx = (long long)blockIdx.x * WARPS + warp;
+  int r[3] = {0, 0, 0};
+  long long row;
+  if (LC) {
+    const int b1 = A.N[0] - P, b2 = DIM == 3 ? A.N[1] - P : A.ib_n;
+    if (idx >= (long long)b1 * b2 * (DIM == 3 ? A.ib_n : 1)) return;
+    r[0] = P + (int)(idx % b1);
+    if (DIM == 3) {
+      r[1] = P + (int)((idx / b1) % b2);
+      r[2] = A.ib_lo + (int)(idx / ((long long)b1 * b2));
+    } else {
+      r[1] = A.ib_lo + (int)(idx / b1);
+    }
+    row = r[0] + (long long)A.n[0] * (r[1] + (long long)A.n[1] * r[2]);
+    if (row < A.row_begin || row >= A.row_end) return;
+  } else {
+    row = A.row_begin + idx;
+    if (row >= A.row_end) return;
+    r[0] = (int)(row % A.n[0]);
+    r[1] = (int)((row / A.n[0]) % A.n[1]);
+    if (DIM == 3) r[2] = (int)(row / ((long long)A.n[0] * A.n[1]));
+    bool interior = true;
+#pragma unroll
+    for (int d = 0; d < DIM; d++) interior = interior && r[d] >= P && r[d] <= A.N[d] - 1;
+    if (interior) return;
+  }
   int off[3], L[3];
 #pragma unroll
   for (int d = 0; d < DIM; d++) {
     off[d] = A.off[d][r[d]];
-    L[d] = A.off[d][r[d] + 1] - off[d];
+    L[d] = LC ? LC : A.off[d][r[d] + 1] - off[d];
   }
   // weight-test tables: A_d^k[q][j] = W(q) T(q, i), j = elem(q) - r + P + i
+#pragma unroll
   for (int d = 0; d < DIM; d++) {
     const int *elem = A.tab[d][0].elem;
+#pragma unroll UR
     for (int t = lane; t < 4 * L[d] * NB; t += 32) {
       const int k = t / (L[d] * NB), q = (t / NB) % L[d], j = t % NB;
       const int i = j - (elem[off[d] + q] - r[d] + P);
-      double v = 0.0;
-      if (i >= 0 && i < NP) v = A.W[d][k][off[d] + q] * A.T[d][k][(size_t)(off[d] + q) * NP + i];
+      R v = 0;
+      if (i >= 0 && i < NP) v = (R)(A.W[d][k][off[d] + q] * A.T[d][k][(size_t)(off[d] + q) * NP + i]);
       sA[((d * 4 + k) * LM + q) * NB + j] = v;
     }
   }
   __syncwarp();
-  double outK[NOUT];
+  R outK[NOUT];
 #pragma unroll
-  for (int o = 0; o < NOUT; o++) outK[o] = 0.0;
+  for (int o = 0; o < NOUT; o++) outK[o] = 0;
   const GmTerm *terms = DIM == 3 ? c_terms3 : c_terms2;
   const int *gstart = DIM == 3 ? c_group_start3 : c_group_start2;
   const long long ob = (row - A.out_row0) * NBAND;
+  const long long s2 = A.np[0], s3 = (long long)A.np[0] * A.np[1];
   for (int grp = 0; grp < 5; grp++) {
     if (grp == 0 ? !A.M : !A.K) continue;
-    for (int t = lane; t < L[0] * NY; t += 32) sY[t] = 0.0;
+#pragma unroll UR
+    for (int t = lane; t < L[0] * NY; t += 32) sY[t] = 0;
     __syncwarp();
     int k1 = 0;
     for (int ti = gstart[grp]; ti < gstart[grp + 1]; ti++) {
-      const GmTerm tm = terms[ti];
+      const GmTerm &tm = terms[ti];
       k1 = tm.k[0];
-      const double *F = A.F + tm.grid * A.fstride;
-      const double *A2 = sA + ((1 * 4 + tm.k[1]) * LM) * NB;
+      const R *F = static_cast<const R *>(A.F) + tm.grid * A.fstride;
+      const R *A2 = sA + ((1 * 4 + tm.k[1]) * LM) * NB;
       if (DIM == 3) {
-        const double *A3 = sA + ((2 * 4 + tm.k[2]) * LM) * NB;
+        const R *A3 = sA + ((2 * 4 + tm.k[2]) * LM) * NB;
+        const R *F0 = F + off[0] + s2 * off[1] + s3 * (off[2] - A.slab_lo);
         // X[q1][q2][s3] = sum_q3 F[q1, q2, q3] A3[q3][s3]
+#pragma unroll UR
         for (int t = lane; t < L[0] * L[1] * NB; t += 32) {
-          const int q1 = t % L[0], q2 = (t / L[0]) % L[1], s3 = t / (L[0] * L[1]);
-          const double *f = F + off[0] + q1 + (long long)A.np[0] * (off[1] + q2 + (long long)A.np[1] *
-                                                                             (off[2] - A.slab_lo));
-          double x = 0.0;
-          for (int q3 = 0; q3 < L[2]; q3++)
-            x = fma(f[(long long)A.np[0] * A.np[1] * q3], A3[q3 * NB + s3], x);
+          const int q1 = t % L[0], q2 = (t / L[0]) % L[1], c3 = t / (L[0] * L[1]);
+          const R *f = F0 + q1 + s2 * q2;
+          R x = 0;
+#pragma unroll UR
+          for (int q3 = 0; q3 < L[2]; q3++) x = fma(f[s3 * q3], A3[q3 * NB + c3], x);
           sX[t] = x;
         }
         __syncwarp();
         // Y[q1][s2][s3] += sum_q2 X[q1][q2][s3] A2[q2][s2]
+#pragma unroll UR
         for (int t = lane; t < L[0] * NB * NB; t += 32) {
-          const int q1 = t % L[0], s2 = (t / L[0]) % NB, s3 = t / (L[0] * NB);
-          double y = sY[t];
-          for (int q2 = 0; q2 < L[1]; q2++) y = fma(sX[q1 + L[0] * (q2 + L[1] * s3)], A2[q2 * NB + s2], y);
+          const int q1 = t % L[0], c2 = (t / L[0]) % NB, c3 = t / (L[0] * NB);
+          R y = sY[t];
+#pragma unroll UR
+          for (int q2 = 0; q2 < L[1]; q2++) y = fma(sX[q1 + L[0] * (q2 + L[1] * c3)], A2[q2 * NB + c2], y);
           sY[t] = y;
         }
         __syncwarp();
       } else {
+        const R *F0 = F + off[0] + s2 * (off[1] - A.slab_lo);
         // Y[q1][s2] += sum_q2 F[q1, q2] A2[q2][s2]
+#pragma unroll UR
         for (int t = lane; t < L[0] * NB; t += 32) {
-          const int q1 = t % L[0], s2 = t / L[0];
-          const double *f = F + off[0] + q1 + (long long)A.np[0] * (off[1] - A.slab_lo);
-          double y = sY[t];
-          for (int q2 = 0; q2 < L[1]; q2++) y = fma(f[(long long)A.np[0] * q2], A2[q2 * NB + s2], y);
+          const int q1 = t % L[0], c2 = t / L[0];
+          R y = sY[t];
+#pragma unroll UR
+          for (int q2 = 0; q2 < L[1]; q2++) y = fma(F0[q1 + s2 * q2], A2[q2 * NB + c2], y);
           sY[t] = y;
         }
         __syncwarp();
       }
     }
     // band[s1 + NB * s23] += sum_q1 Y[q1][s23] A1[q1][s1]
-    const double *A1 = sA + ((0 * 4 + k1) * LM) * NB;
+    const R *A1 = sA + ((0 * 4 + k1) * LM) * NB;
 #pragma unroll
     for (int o = 0; o < NOUT; o++) {
       const int e = lane + 32 * o;
       if (e < NBAND) {
         const int s1 = e % NB, s23 = e / NB;
-        double v = 0.0;
+        R v = 0;
+#pragma unroll UR
         for (int q1 = 0; q1 < L[0]; q1++) v = fma(sY[q1 + L[0] * s23], A1[q1 * NB + s1], v);
         if (grp == 0)
-          A.M[ob + e] = v;
+          static_cast<R *>(A.M)[ob + e] = v;
         else
           outK[o] += v;
       }
@@ -505,38 +877,75 @@ template <int P, int DIM> __global__ void __launch_bounds__(32 * kGmWarps) gm_ro
 #pragma unroll
     for (int o = 0; o < NOUT; o++) {
       const int e = lane + 32 * o;
-      if (e < NBAND) A.K[ob + e] = outK[o];
+      if (e < NBAND) static_cast<R *>(A.K)[ob + e] = outK[o];
     }
   }
 }
 
-template <int P, int DIM> wq_status launch_slab(const GmArgs &a, long long nitems, long long nrows, cudaStream_t s) {
+constexpr int kGmWarpsInt = 8;  // rows (warps) per CTA of the interior-row kernel
+
+template <int P, int DIM, typename R>
+wq_status launch_slab(const GmArgs &a, long long nitems, long long nrows, long long nint, cudaStream_t s) {
+  constexpr bool F32 = std::is_same<R, float>::value;
   if (nitems > 0) {
     if (DIM == 3) {
-      const size_t smem = sizeof(double) * (size_t)metric3_smem_doubles<P>();
-      gm_metric3_kernel<P><<<(unsigned)nitems, kGmChunk, smem, s>>>(a);
+      if (F32)
+        gm_metric3f_kernel<P><<<(unsigned)nitems, kGmChunk, sizeof(float) * (size_t)metric3f_smem_floats<P>(), s>>>(a);
+      else
+        gm_metric3_kernel<P><<<(unsigned)nitems, kGmChunk, sizeof(double) * (size_t)metric3_smem_doubles<P>(), s>>>(a);
     } else {
-      gm_metric2_kernel<P><<<(unsigned)nitems, kGmChunk, 0, s>>>(a);
+      if (F32)
+        gm_metric2f_kernel<P><<<(unsigned)nitems, kGmChunk, 0, s>>>(a);
+      else
+        gm_metric2_kernel<P><<<(unsigned)nitems, kGmChunk, 0, s>>>(a);
     }
     if (cudaGetLastError() != cudaSuccess) return WQ_ERR_CUDA;
   }
+  if (nint > 0) {
+    const size_t smem = sizeof(R) * (size_t)rows_warp_elems<P, DIM, P + 1>() * kGmWarpsInt;
+    gm_rows_kernel<P, DIM, P + 1, kGmWarpsInt, R>
+        <<<(unsigned)((nint + kGmWarpsInt - 1) / kGmWarpsInt), 32 * kGmWarpsInt, smem, s>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return WQ_ERR_CUDA;
+  }
   if (nrows > 0) {
-    const size_t smem = sizeof(double) * (size_t)rows_warp_doubles<P, DIM>() * kGmWarps;
-    gm_rows_kernel<P, DIM><<<(unsigned)((nrows + kGmWarps - 1) / kGmWarps), 32 * kGmWarps, smem, s>>>(a);
+    const size_t smem = sizeof(R) * (size_t)rows_warp_elems<P, DIM, 0>() * kGmWarps;
+    gm_rows_kernel<P, DIM, 0, kGmWarps, R>
+        <<<(unsigned)((nrows + kGmWarps - 1) / kGmWarps), 32 * kGmWarps, smem, s>>>(a);
     if (cudaGetLastError() != cudaSuccess) return WQ_ERR_CUDA;
   }
   return WQ_OK;
 }
 
-template <int P, int DIM> cudaError_t set_smem_limits() {
+template <int P, int DIM, typename R> cudaError_t set_smem_limits() {
   cudaError_t e = cudaSuccess;
   if (DIM == 3)
-    e = cudaFuncSetAttribute(gm_metric3_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(double) * metric3_smem_doubles<P>()));
+    e = std::is_same<R, float>::value
+            ? cudaFuncSetAttribute(gm_metric3f_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(sizeof(float) * metric3f_smem_floats<P>()))
+            : cudaFuncSetAttribute(gm_metric3_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(sizeof(double) * metric3_smem_doubles<P>()));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(gm_rows_kernel<P, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(double) * rows_warp_doubles<P, DIM>() * kGmWarps));
+    e = cudaFuncSetAttribute(gm_rows_kernel<P, DIM, 0, kGmWarps, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(R) * rows_warp_elems<P, DIM, 0>() * kGmWarps));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gm_rows_kernel<P, DIM, P + 1, kGmWarpsInt, R>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(R) * rows_warp_elems<P, DIM, P + 1>() * kGmWarpsInt));
   return e;
+}
+
+template <typename R> cudaError_t set_limits(int p, int dim) {
+  return p == 2 ? (dim == 3 ? set_smem_limits<2, 3, R>() : set_smem_limits<2, 2, R>())
+                : (dim == 3 ? set_smem_limits<3, 3, R>() : set_smem_limits<3, 2, R>());
+}
+
+template <typename R>
+wq_status launch_any(int p, int dim, const GmArgs &a, long long nitems, long long nrows, long long nint,
+                     cudaStream_t s) {
+  return p == 2 ? (dim == 3 ? launch_slab<2, 3, R>(a, nitems, nrows, nint, s)
+                            : launch_slab<2, 2, R>(a, nitems, nrows, nint, s))
+                : (dim == 3 ? launch_slab<3, 3, R>(a, nitems, nrows, nint, s)
+                            : launch_slab<3, 2, R>(a, nitems, nrows, nint, s));
 }
 
 // Scratch budget of one slab's factor arrays.
@@ -555,7 +964,9 @@ extern "C" wq_status wq_assemble_general(const wq_rules *R, const double *net, c
   if (row_begin < 0 || row_end > nrows || row_begin > row_end) return WQ_ERR_ARG;
   if (row_begin == row_end) return WQ_OK;
   if (!net || (!M && !K)) return WQ_ERR_ARG;
-  if (prec != WQ_FP64) return WQ_ERR_UNSUPPORTED;
+  if (prec != WQ_FP64 && prec != WQ_MIXED) return WQ_ERR_UNSUPPORTED;
+  const bool f32 = prec == WQ_MIXED;
+  const size_t elt = f32 ? sizeof(float) : sizeof(double);
   if (R->mode != kModeWQ || R->bnd_weighted || !R->dev_cross) return WQ_ERR_UNSUPPORTED;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != R->device) return WQ_ERR_ARG;
@@ -577,9 +988,9 @@ extern "C" wq_status wq_assemble_general(const wq_rules *R, const double *net, c
     const DevDirKind &Dm = R->dev[d][0], &Ds = R->dev[d][1];
     const DevCross &Dx = R->devx[d];
     a.off[d] = Dm.off;
-    a.tab[d][0] = GmTab{Dm.elem, Dm.t0, Dm.t1, Dm.beta};
-    a.tab[d][1] = GmTab{Ds.elem, Ds.t0, Ds.t1, Ds.beta};
-    a.tab[d][2] = GmTab{Dx.elem, Dx.t0, Dx.t1, Dx.beta};
+    a.tab[d][0] = GmTab{Dm.elem, Dm.t0, Dm.t1, Dm.beta, Dm.tl};
+    a.tab[d][1] = GmTab{Ds.elem, Ds.t0, Ds.t1, Ds.beta, Ds.tl};
+    a.tab[d][2] = GmTab{Dx.elem, Dx.t0, Dx.t1, Dx.beta, Dx.tl};
     a.W[d][0] = Dm.w;
     a.T[d][0] = Dm.t0;
     a.W[d][1] = Ds.w;
@@ -591,8 +1002,8 @@ extern "C" wq_status wq_assemble_general(const wq_rules *R, const double *net, c
   }
   a.net = net;
   a.coef = coef;
-  a.M = static_cast<double *>(M);
-  a.K = static_cast<double *>(K);
+  a.M = M;
+  a.K = K;
   a.out_row0 = row_begin;
   a.status = R->dev_status;
 
@@ -601,7 +1012,9 @@ extern "C" wq_status wq_assemble_general(const wq_rules *R, const double *net, c
   const long long plane = dim == 3 ? (long long)R->n[0] * R->n[1] : R->n[0];
   const int pl0 = (int)(row_begin / plane), pl1 = (int)((row_end - 1) / plane);
   const std::vector<int> &offs = R->host[sd][0].off;
-  const long long per_point = (long long)kGmGrids * a.np[0] * (dim == 3 ? a.np[1] : 1) * (long long)sizeof(double);
+  const long long per_point = (long long)kGmGrids * a.np[0] * (dim == 3 ? a.np[1] : 1) * (long long)elt;
+  // FP32: the scaled difference nets ([b][a], dim^2 arrays of the net's size) precede the factors
+  const long long dbytes = f32 ? (long long)((dim * dim * a.ntot * sizeof(float) + 255) / 256 * 256) : 0;
   int most = 0;
   for (int r = pl0; r <= pl1; r++) most = std::max(most, offs[r + 1] - offs[r]);
   // (WQ_GENERAL_SLAB_BYTES lowers the bound, down to one plane per slab: a
@@ -622,6 +1035,7 @@ extern "C" wq_status wq_assemble_general(const wq_rules *R, const double *net, c
     need = std::max(need, per_point * (long long)(offs[e + 1] - offs[r]));
     r = e + 1;
   }
+  need += dbytes;
   if ((size_t)need > R->dev_gm_bytes) {
     if (R->dev_gm) {
       if (cudaStreamSynchronize(s) != cudaSuccess) return WQ_ERR_CUDA;
@@ -635,10 +1049,16 @@ extern "C" wq_status wq_assemble_general(const wq_rules *R, const double *net, c
     }
     R->dev_gm_bytes = (size_t)need;
   }
-  a.F = static_cast<double *>(R->dev_gm);
-  cudaError_t e = p == 2 ? (dim == 3 ? set_smem_limits<2, 3>() : set_smem_limits<2, 2>())
-                         : (dim == 3 ? set_smem_limits<3, 3>() : set_smem_limits<3, 2>());
+  a.F = static_cast<char *>(R->dev_gm) + dbytes;
+  a.D = f32 ? static_cast<const float *>(R->dev_gm) : nullptr;
+  cudaError_t e = f32 ? set_limits<float>(p, dim) : set_limits<double>(p, dim);
   if (e != cudaSuccess) return WQ_ERR_CUDA;
+  if (f32) {
+    const long long blocks = std::min<long long>((a.ntot + 255) / 256, 8192);
+    gm_diff_kernel<<<(unsigned)blocks, 256, 0, s>>>(net, static_cast<float *>(R->dev_gm), dim, p, a.n[0], a.n[1],
+                                                    a.N[0], a.N[1], a.N[2], a.ntot);
+    if (cudaGetLastError() != cudaSuccess) return WQ_ERR_CUDA;
+  }
   for (const auto &sl : slabs) {
     a.slab_lo = offs[sl.first];
     a.slab_n = offs[sl.second + 1] - offs[sl.first];
@@ -649,8 +1069,13 @@ extern "C" wq_status wq_assemble_general(const wq_rules *R, const double *net, c
     const long long nitems = dim == 3 ? 6LL * a.slab_n * R->n[1] * nch1 : 3LL * a.slab_n * nch1;
     if (nitems > 0x7fffffffLL) return WQ_ERR_UNSUPPORTED;
     const long long nr = a.row_end - a.row_begin;
-    wq_status st = p == 2 ? (dim == 3 ? launch_slab<2, 3>(a, nitems, nr, s) : launch_slab<2, 2>(a, nitems, nr, s))
-                          : (dim == 3 ? launch_slab<3, 3>(a, nitems, nr, s) : launch_slab<3, 2>(a, nitems, nr, s));
+    // interior planes of the slab: rows p .. nel-1 of the slab direction
+    a.ib_lo = std::max(sl.first, p);
+    a.ib_n = std::max(0, std::min(sl.second, R->nel[sd] - 1) - a.ib_lo + 1);
+    long long nint = (long long)std::max(0, R->nel[0] - p) * a.ib_n;
+    if (dim == 3) nint *= std::max(0, R->nel[1] - p);
+    wq_status st = f32 ? launch_any<float>(p, dim, a, nitems, nr, nint, s)
+                       : launch_any<double>(p, dim, a, nitems, nr, nint, s);
     if (st != WQ_OK) return st;
   }
   return WQ_OK;

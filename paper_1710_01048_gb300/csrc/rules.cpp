@@ -274,7 +274,7 @@ std::vector<double> knots(int q, int N) {
 
 // Values and first derivatives of the q+1 degree-q B-splines B_e..B_{e+q}
 // acting on element e, at x, by the triangular (de Boor) recurrence.
-void basis(const std::vector<double> &t, int q, int e, double x, double *val, double *der) {
+void basis(const std::vector<double> &t, int q, int e, double x, double *val, double *der, double *low = nullptr) {
   int i = e + q;
   double left[8], right[8], Nt[8][8];
   Nt[0][0] = 1.0;
@@ -302,6 +302,9 @@ void basis(const std::vector<double> &t, int q, int e, double x, double *val, do
     }
     der[j] = (double)q * (a - b);
   }
+  // degree q-1 on the same knots: B_{e+1+j, q-1}(x), j = 0..q-1
+  if (low)
+    for (int j = 0; j < q; j++) low[j] = Nt[q - 1][j];
 }
 
 // ------------------------------------------------------------------ boundary rows
@@ -817,8 +820,9 @@ wq_status build_host_tables(wq_rules *R) {
         for (size_t q = 0; q < pe.size(); q++) {
           int e = pe[q];
           double x = px[q];
-          double v[8], dv[8], cv[8], cd[8];
-          basis(tp, p, e, x, v, dv);
+          double v[8], dv[8], cv[8], cd[8], lo[8];
+          basis(tp, p, e, x, v, dv, lo);
+          for (int i = 0; i < p; i++) H.tl.push_back(lo[i]);
           basis(tc, kCoefDeg, e, x, cv, cd);
           int j = r - e;  // B_r among B_e..B_{e+p}
           double br = folded ? 1.0 : (kind == WQ_KIND_MASS ? v[j] : dv[j]);
@@ -875,8 +879,9 @@ wq_status build_host_tables(wq_rules *R) {
             }
         }
         for (size_t q = 0; q < pe.size(); q++) {
-          double v[8], dv[8], cv[8], cd[8];
-          basis(tp, p, pe[q], px[q], v, dv);
+          double v[8], dv[8], cv[8], cd[8], lo[8];
+          basis(tp, p, pe[q], px[q], v, dv, lo);
+          for (int i = 0; i < p; i++) X.tl.push_back(lo[i]);
           basis(tc, kCoefDeg, pe[q], px[q], cv, cd);
           X.elem.push_back(pe[q]);
           X.x.push_back(px[q]);

@@ -46,6 +46,7 @@ struct HostDirKind {
   std::vector<double> t0;    // npts*(p+1): B_{elem+i}(x)
   std::vector<double> t1;    // npts*(p+1): B'_{elem+i}(x)
   std::vector<double> beta;  // npts*4: B3_{elem+i}(x)
+  std::vector<double> tl;    // npts*p: B_{elem+1+j, p-1}(x), degree p-1 on the same knots
 };
 
 // One direction of the mixed-derivative kinds (kind 2: weight B_r', tests
@@ -57,11 +58,12 @@ struct HostCross {
   std::vector<double> w2, w3;  // combined weights of kinds 2 and 3
   std::vector<double> t0, t1;  // npts*(p+1): B_{elem+i}(x), B'_{elem+i}(x)
   std::vector<double> beta;    // npts*4: B3_{elem+i}(x)
+  std::vector<double> tl;      // npts*p: B_{elem+1+j, p-1}(x)
 };
 
 struct DevCross {
   const int *elem;
-  const double *w2, *w3, *t0, *t1, *beta;
+  const double *w2, *w3, *t0, *t1, *beta, *tl;
   int npts;
 };
 
@@ -78,6 +80,7 @@ struct DevDirKind {
   float *beta32;
   float2 *vdd;     // the folded tables as double-float pairs (hi, lo)
   float2 *betadd;  // the cubic values as double-float pairs
+  const double *tl;  // npts*p: degree p-1 values (non-separable maps, FP32 Jacobian)
   int npts;
 };
 

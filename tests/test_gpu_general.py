@@ -19,6 +19,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-12
+TOL32 = 1e-6
 
 
 def check(A, O, tol, what):
@@ -42,6 +43,38 @@ def test_general_parity_warped(dim, p, nel):
     Mo, Ko = oracle.assemble_general(dim, p, nel, net, c)
     check(M, Mo, TOL, "M")
     check(K, Ko, TOL, "K")
+    R.close()
+
+
+@pytest.mark.parametrize("dim,p,nel", [(3, 3, (19, 9, 7)), (3, 2, (11, 5, 6)), (3, 3, (2, 3, 1)), (3, 2, (1, 1, 1)),
+                                       (3, 3, (140, 4, 3)), (2, 3, (33, 12)), (2, 2, (9, 4)), (2, 3, (1, 2)),
+                                       (2, 2, (131, 5))])
+def test_general_parity_warped_fp32(dim, p, nel):
+    net, c = inputs.make_net(dim, p, nel, "warp", 0.05, "exp", 0.1, seed=61)
+    R = wq.Rules(dim, p, nel)
+    M, K = wq.assemble_general(R, dev(net), dev(c), prec="mixed")
+    assert M.dtype == torch.float32 and K.dtype == torch.float32
+    Mo, Ko = oracle.assemble_general(dim, p, nel, net, c)
+    check(M, Mo, TOL32, "M")
+    check(K, Ko, TOL32, "K")
+    # the slab loop and row ranges give the same bits in FP32 too
+    Mr, Kr = wq.assemble_general(R, dev(net), dev(c), prec="mixed", row_begin=R.rows // 3, row_end=R.rows - 1)
+    assert torch.equal(Mr, M[R.rows // 3:R.rows - 1]) and torch.equal(Kr, K[R.rows // 3:R.rows - 1])
+    R.close()
+
+
+def test_general_fp32_accuracy_at_64_cubed_sampled():
+    dim, p, nel = 3, 3, (64, 64, 64)
+    net, c = inputs.make_net(dim, p, nel, "warp", 0.05, "exp", 0.1, seed=0)
+    R = wq.Rules(dim, p, nel)
+    M, K = wq.assemble_general(R, dev(net), dev(c), prec="mixed")
+    rng = np.random.default_rng(8)
+    rows = sorted(set(rng.integers(0, R.rows, size=24).tolist()) | {0, R.rows - 1, R.rows // 2})
+    Mh, Kh = M.double().cpu().numpy(), K.double().cpu().numpy()
+    for r in rows:
+        Mo, Ko = oracle.assemble_general(dim, p, nel, net, c, row_begin=r, row_end=r + 1)
+        for A, O in ((Mh[r], Mo[0]), (Kh[r], Ko[0])):
+            assert np.max(np.abs(A - O)) <= TOL32 * np.max(np.abs(O)), r
     R.close()
 
 
@@ -118,6 +151,9 @@ def test_status_and_refusals():
     with pytest.raises(wq.WqError) as ei:
         wq.assemble_general(R, dev(flipped))
     assert ei.value.status == wq.WQ_ERR_GEOMETRY
+    with pytest.raises(wq.WqError) as ei:
+        wq.assemble_general(R, dev(flipped), prec="mixed")
+    assert ei.value.status == wq.WQ_ERR_GEOMETRY
     M, K = wq.assemble_general(R, dev(flipped), check=False)
     assert wq.wq_status_check(R.handle, wq._stream_handle(None)) == wq.WQ_ERR_GEOMETRY
     Mo, Ko = wq.assemble_general(R, dev(net))
@@ -131,7 +167,7 @@ def test_status_and_refusals():
     out = torch.empty((R.rows, R.band), dtype=torch.float64, device="cuda")
     lib = wq.library()
     nd = dev(net)
-    for prec in (wq.WQ_MIXED, wq.WQ_DF64):
+    for prec in (wq.WQ_DF64,):
         assert lib.wq_assemble_general(R.handle, ctypes.c_void_p(nd.data_ptr()), None, prec,
                                        ctypes.c_void_p(out.data_ptr()), None, 0, R.rows, s) == wq.WQ_ERR_UNSUPPORTED
     assert lib.wq_assemble_general(R.handle, None, None, wq.WQ_FP64, ctypes.c_void_p(out.data_ptr()), None, 0,
