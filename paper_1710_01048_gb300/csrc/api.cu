@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "fold.cuh"
 #include "launch.cuh"
@@ -272,6 +273,69 @@ wq_status upload(wq_rules *R) {
     }
     R->dev_cross = xb;
     R->dev_bytes += xt;
+    // derived tables of the non-separable path, staged on the host and copied at once
+    std::vector<char> stage;
+    auto push = [&stage](const void *src, size_t bytes) -> size_t {
+      const size_t off = stage.size();
+      stage.resize(align_up(off + bytes));
+      if (bytes) std::memcpy(stage.data() + off, src, bytes);
+      return off;
+    };
+    size_t go[3][3][3], gw64[3][4], gw32[3][4];
+    for (int a = 0; a < R->dim; a++) {
+      const wq::HostDirKind *Hk[2] = {&R->host[a][0], &R->host[a][1]};
+      const wq::HostCross &X = R->hostx[a];
+      const std::vector<double> *t0s[3] = {&Hk[0]->t0, &Hk[1]->t0, &X.t0};
+      const std::vector<double> *tls[3] = {&Hk[0]->tl, &Hk[1]->tl, &X.tl};
+      const std::vector<double> *bes[3] = {&Hk[0]->beta, &Hk[1]->beta, &X.beta};
+      for (int k = 0; k < 3; k++) {
+        const std::vector<double> *src[3] = {t0s[k], tls[k], bes[k]};
+        for (int t = 0; t < 3; t++) {
+          std::vector<float> f(src[t]->begin(), src[t]->end());
+          go[a][k][t] = push(f.data(), f.size() * sizeof(float));
+        }
+      }
+      const std::vector<double> *ws[4] = {&Hk[0]->w, &Hk[1]->w, &X.w2, &X.w3};
+      const std::vector<double> *ts[4] = {&Hk[0]->t0, &Hk[1]->t1, &X.t0, &X.t1};
+      for (int k = 0; k < 4; k++) {
+        const size_t npts = ws[k]->size();
+        std::vector<double> w64(npts * np);
+        std::vector<float> w32(npts * np);
+        for (size_t q = 0; q < npts; q++)
+          for (int i = 0; i < np; i++) {
+            w64[q * np + i] = (*ws[k])[q] * (*ts[k])[q * np + i];
+            w32[q * np + i] = (float)w64[q * np + i];
+          }
+        gw64[a][k] = push(w64.data(), w64.size() * sizeof(double));
+        gw32[a][k] = push(w32.data(), w32.size() * sizeof(float));
+      }
+    }
+    void *gb = nullptr;
+    e = cudaMalloc(&gb, stage.size());
+    if (e != cudaSuccess || cudaMemcpy(gb, stage.data(), stage.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      if (gb) cudaFree(gb);
+      cudaFree(xb);
+      cudaFree(block);
+      R->dev_block = nullptr;
+      R->dev_cross = nullptr;
+      return e == cudaErrorMemoryAllocation ? WQ_ERR_OOM : WQ_ERR_CUDA;
+    }
+    const char *gbase = static_cast<const char *>(gb);
+    for (int a = 0; a < R->dim; a++) {
+      wq::GmDevTab &G = R->gmt[a];
+      for (int k = 0; k < 3; k++) {
+        G.t0f[k] = reinterpret_cast<const float *>(gbase + go[a][k][0]);
+        G.tlf[k] = reinterpret_cast<const float *>(gbase + go[a][k][1]);
+        G.betaf[k] = reinterpret_cast<const float *>(gbase + go[a][k][2]);
+      }
+      for (int k = 0; k < 4; k++) {
+        G.wt64[k] = reinterpret_cast<const double *>(gbase + gw64[a][k]);
+        G.wt32[k] = reinterpret_cast<const float *>(gbase + gw32[a][k]);
+      }
+    }
+    R->dev_gmtab = gb;
+    R->dev_bytes += stage.size();
   }
   if (R->dim == 3 && R->mode == wq::kModeWQ) {
     const int nb = 2 * R->p + 1;
@@ -281,8 +345,10 @@ wq_status upload(wq_rules *R) {
       cudaGetLastError();
       cudaFree(block);
       if (R->dev_cross) cudaFree(R->dev_cross);
+      if (R->dev_gmtab) cudaFree(R->dev_gmtab);
       R->dev_block = nullptr;
       R->dev_cross = nullptr;
+      R->dev_gmtab = nullptr;
       R->dev_U = nullptr;
       return e == cudaErrorMemoryAllocation ? WQ_ERR_OOM : WQ_ERR_CUDA;
     }
@@ -648,6 +714,7 @@ void wq_rules_free(wq_rules *rules) {
     if (rules->dev_U) cudaFree(rules->dev_U);
     if (rules->dev_adj) cudaFree(rules->dev_adj);
     if (rules->dev_cross) cudaFree(rules->dev_cross);
+    if (rules->dev_gmtab) cudaFree(rules->dev_gmtab);
     if (rules->dev_gm) cudaFree(rules->dev_gm);
     if (cur >= 0 && cur != rules->device) cudaSetDevice(cur);
   }

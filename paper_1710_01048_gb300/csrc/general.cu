@@ -44,6 +44,7 @@ constexpr int kGmGrids = 7;
 struct GmTab {  // one direction, one point set (m, s, x): what the metric reads
   const int *elem;
   const double *t0, *t1, *beta, *tl;
+  const float *t0f, *tlf, *betaf;  // the same in FP32 (the FP32 Jacobian)
 };
 
 struct GmArgs {
@@ -51,13 +52,16 @@ struct GmArgs {
   int n[3], N[3], nc[3], np[3];
   const int *off[3];        // row offsets into the point lists (equal for every kind)
   GmTab tab[3][3];          // [direction][point set m, s, x]
-  const double *W[3][4];    // [direction][weight-test kind 0..3]: combined weights
-  const double *T[3][4];    // the test values there (p+1 per point)
+  // [direction][weight-test kind 0..3]: W(q) T(q, i), the combined weight
+  // times each of the point's p+1 test values (FP64 and FP32)
+  const double *WT64[3][4];
+  const float *WT32[3][4];
   const double *net;        // dim components of ntot control values
   long long ntot;
   const double *coef;       // may be null: c = 1
   void *F;                  // kGmGrids factor arrays of fstride values (double or float)
   const float *D;           // FP32 path: scaled differences of the net, [b][a][ntot]
+  const float *coef32;      // FP32 path: the coefficients in FP32 (null: c = 1)
   long long fstride;
   int slab_lo, slab_n;      // 3D: x3 points [slab_lo, slab_lo + slab_n); 2D: x2 points
   int ib_lo, ib_n;          // the slab's interior x3 planes (2D: x2 lines) [ib_lo, ib_lo + ib_n)
@@ -429,7 +433,18 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric2_kernel(c
 // FP32 arithmetic keeps ~1e-7 relative accuracy at any mesh size.
 
 __global__ void gm_diff_kernel(const double *__restrict__ net, float *__restrict__ D, int dim, int p, int n0, int n1,
-                               int N0, int N1, int N2, long long ntot) {
+                               int N0, int N1, int N2, long long ntot, const double *__restrict__ coef,
+                               float *__restrict__ coef32, long long ncoef, unsigned *status) {
+  unsigned bad = 0;
+  if (coef)
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncoef;
+         i += (long long)gridDim.x * blockDim.x) {
+      const float v = (float)coef[i];
+      if (!isfinite(v)) bad = 1;
+      coef32[i] = v;
+    }
+  bad = __reduce_or_sync(0xffffffffu, bad);
+  if (bad && (threadIdx.x & 31) == 0) atomicOr(status, kBitNonFinite);
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < ntot;
        idx += (long long)gridDim.x * blockDim.x) {
     const int i[3] = {(int)(idx % n0), (int)((idx / n0) % n1), (int)(idx / ((long long)n0 * n1))};
@@ -508,11 +523,11 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3f_kernel(
   const int e3 = T3.elem[q3];
   float b3v[NP], b3l[P], c3[4];
 #pragma unroll
-  for (int i = 0; i < NP; i++) b3v[i] = (float)T3.t0[(size_t)q3 * NP + i];
+  for (int i = 0; i < NP; i++) b3v[i] = T3.t0f[(size_t)q3 * NP + i];
 #pragma unroll
-  for (int j = 0; j < P; j++) b3l[j] = (float)T3.tl[(size_t)q3 * P + j];
+  for (int j = 0; j < P; j++) b3l[j] = T3.tlf[(size_t)q3 * P + j];
 #pragma unroll
-  for (int l = 0; l < 4; l++) c3[l] = (float)T3.beta[(size_t)q3 * 4 + l];
+  for (int l = 0; l < 4; l++) c3[l] = T3.betaf[(size_t)q3 * 4 + l];
   const int qa = c1 * NT, qb = min(np1, qa + NT);
   const int *elem1 = A.tab[0][0].elem;
   const int myq = qa + tid;
@@ -544,13 +559,13 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3f_kernel(
       sH[6 * NI2 * kGmCols + row] = h2;
     }
   }
-  if (A.coef)
+  if (A.coef32)
     for (int t = tid; t < nl2 * nl1; t += NT) {
       const int l2 = e2lo + t / nl1, col = t % nl1, l1 = emin + col;
-      const double *g = A.coef + l1 + (long long)nc1 * l2;
+      const float *g = A.coef32 + l1 + (long long)nc1 * l2;
       float hc = 0.0f;
 #pragma unroll
-      for (int l = 0; l < 4; l++) hc = fmaf((float)g[(long long)nc1 * nc2 * (e3 + l)], c3[l], hc);
+      for (int l = 0; l < 4; l++) hc = fmaf(g[(long long)nc1 * nc2 * (e3 + l)], c3[l], hc);
       sHc[(l2 - e2lo) * kGmCols + col] = hc;
     }
   __syncthreads();
@@ -561,12 +576,12 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3f_kernel(
     const int e2 = T2.elem[q2];
     float b2v[NP], b2l[P], c2[4];
 #pragma unroll
-    for (int i = 0; i < NP; i++) b2v[i] = (float)T2.t0[(size_t)q2 * NP + i];
+    for (int i = 0; i < NP; i++) b2v[i] = T2.t0f[(size_t)q2 * NP + i];
 #pragma unroll
-    for (int j = 0; j < P; j++) b2l[j] = (float)T2.tl[(size_t)q2 * P + j];
+    for (int j = 0; j < P; j++) b2l[j] = T2.tlf[(size_t)q2 * P + j];
 #pragma unroll
-    for (int l = 0; l < 4; l++) c2[l] = (float)T2.beta[(size_t)q2 * 4 + l];
-    const int nE = 3 * ni1 + (A.coef ? nl1 : 0);
+    for (int l = 0; l < 4; l++) c2[l] = T2.betaf[(size_t)q2 * 4 + l];
+    const int nE = 3 * ni1 + (A.coef32 ? nl1 : 0);
     for (int t = tid; t < nE; t += NT) {
       if (t < 3 * ni1) {
         const int a = t / ni1, col = t - a * ni1;
@@ -598,9 +613,9 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3f_kernel(
         const GmTab &T1 = A.tab[0][grp.k1[gi]];
         float bv[NP], bl[P];
 #pragma unroll
-        for (int i = 0; i < NP; i++) bv[i] = (float)T1.t0[(size_t)myq * NP + i];
+        for (int i = 0; i < NP; i++) bv[i] = T1.t0f[(size_t)myq * NP + i];
 #pragma unroll
-        for (int j = 0; j < P; j++) bl[j] = (float)T1.tl[(size_t)myq * P + j];
+        for (int j = 0; j < P; j++) bl[j] = T1.tlf[(size_t)myq * P + j];
         float jc[3][3];  // jc[b][a] = d x_a / d xhat_b
 #pragma unroll
         for (int a = 0; a < 3; a++) {
@@ -618,10 +633,10 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3f_kernel(
         }
         const F3 j0{jc[0][0], jc[0][1], jc[0][2]}, j1{jc[1][0], jc[1][1], jc[1][2]}, j2{jc[2][0], jc[2][1], jc[2][2]};
         float c = 1.0f;
-        if (A.coef) {
+        if (A.coef32) {
           c = 0.0f;
 #pragma unroll
-          for (int l = 0; l < 4; l++) c = fmaf(sE[9 * kGmCols + o + l], (float)T1.beta[(size_t)myq * 4 + l], c);
+          for (int l = 0; l < 4; l++) c = fmaf(sE[9 * kGmCols + o + l], T1.betaf[(size_t)myq * 4 + l], c);
           if (!isfinite(c)) bits |= kBitNonFinite;
         }
         const float f = metric3f(grp.comp[gi], j0, j1, j2, c, bits);
@@ -653,11 +668,11 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric2f_kernel(
   const int e2 = T2.elem[q2];
   float b2v[NP], b2l[P], c2[4];
 #pragma unroll
-  for (int i = 0; i < NP; i++) b2v[i] = (float)T2.t0[(size_t)q2 * NP + i];
+  for (int i = 0; i < NP; i++) b2v[i] = T2.t0f[(size_t)q2 * NP + i];
 #pragma unroll
-  for (int j = 0; j < P; j++) b2l[j] = (float)T2.tl[(size_t)q2 * P + j];
+  for (int j = 0; j < P; j++) b2l[j] = T2.tlf[(size_t)q2 * P + j];
 #pragma unroll
-  for (int l = 0; l < 4; l++) c2[l] = (float)T2.beta[(size_t)q2 * 4 + l];
+  for (int l = 0; l < 4; l++) c2[l] = T2.betaf[(size_t)q2 * 4 + l];
   const int qa = c1 * NT, qb = min(np1, qa + NT);
   const int *elem1 = A.tab[0][0].elem;
   const int myq = qa + tid;
@@ -677,12 +692,12 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric2f_kernel(
     sE[a * kGmCols + col] = v0;
     sE[(2 + a) * kGmCols + col] = v1;
   }
-  if (A.coef)
+  if (A.coef32)
     for (int col = tid; col < nl1; col += NT) {
-      const double *g = A.coef + emin + col;
+      const float *g = A.coef32 + emin + col;
       float ec = 0.0f;
 #pragma unroll
-      for (int l = 0; l < 4; l++) ec = fmaf((float)g[(long long)nc1 * (e2 + l)], c2[l], ec);
+      for (int l = 0; l < 4; l++) ec = fmaf(g[(long long)nc1 * (e2 + l)], c2[l], ec);
       sE[4 * kGmCols + col] = ec;
     }
   __syncthreads();
@@ -696,17 +711,17 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric2f_kernel(
       for (int a = 0; a < 2; a++) {
         float d1 = 0.0f, d2 = 0.0f;
 #pragma unroll
-        for (int j = 0; j < P; j++) d1 = fmaf(sE[a * kGmCols + o + 1 + j], (float)T1.tl[(size_t)myq * P + j], d1);
+        for (int j = 0; j < P; j++) d1 = fmaf(sE[a * kGmCols + o + 1 + j], T1.tlf[(size_t)myq * P + j], d1);
 #pragma unroll
-        for (int i = 0; i < NP; i++) d2 = fmaf(sE[(2 + a) * kGmCols + o + i], (float)T1.t0[(size_t)myq * NP + i], d2);
+        for (int i = 0; i < NP; i++) d2 = fmaf(sE[(2 + a) * kGmCols + o + i], T1.t0f[(size_t)myq * NP + i], d2);
         j0[a] = d1;
         j1[a] = d2;
       }
       float c = 1.0f;
-      if (A.coef) {
+      if (A.coef32) {
         c = 0.0f;
 #pragma unroll
-        for (int l = 0; l < 4; l++) c = fmaf(sE[4 * kGmCols + o + l], (float)T1.beta[(size_t)myq * 4 + l], c);
+        for (int l = 0; l < 4; l++) c = fmaf(sE[4 * kGmCols + o + l], T1.betaf[(size_t)myq * 4 + l], c);
         if (!isfinite(c)) bits |= kBitNonFinite;
       }
       const float det = fmaf(j0[0], j1[1], -j1[0] * j0[1]);
@@ -729,30 +744,40 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric2f_kernel(
   if ((tid & 31) == 0 && bits) atomicOr(A.status, bits);
 }
 
-// Per-warp shared memory of the row kernel (elements of R): the weight-test tables
-// [DIM][4][LM][NB], X [LM][LM][NB] (3D), Y [LM][NB^(DIM-1)]; LM = the most
+// Per-warp shared memory of the row kernel (elements of R): the weight-test
+// tables [DIM][4][LM][NBP] (rows padded to NBP), X [LM][LM][NB] (3D),
+// Y [LM][NB^(DIM-1)] and the band row being written [NB^DIM]; LM = the most
 // points of a row in one direction (LC when the row class fixes it).
+template <int P> constexpr int nb_pad() { return ((2 * P + 1) + 3) / 4 * 4; }
 template <int P, int DIM, int LC> constexpr int rows_warp_elems() {
-  constexpr int NB = 2 * P + 1, LM = LC ? LC : P * (P + 1);
-  return DIM * 4 * LM * NB + (DIM == 3 ? LM * LM * NB : 0) + LM * (DIM == 3 ? NB * NB : NB);
+  constexpr int NB = 2 * P + 1, LM = LC ? LC : P * (P + 1), NY = DIM == 3 ? NB * NB : NB;
+  return DIM * 4 * LM * nb_pad<P>() + (DIM == 3 ? LM * LM * NB : 0) + LM * NY + NY * NB;
 }
 
 // One row per warp.  LC = P+1: the interior rows (every direction on its
 // weighted rule, p+1 points), taken from the interior box of the slab with
 // compile-time loop bounds; LC = 0: the other rows of the range (at least
-// one direction on Gauss-Legendre), the interior ones skipped.
+// one direction on Gauss-Legendre), the interior ones skipped.  Each lane
+// owns a run of outputs of every contraction (a row of NB columns, or half
+// of one), so the weight-test row of the contracted point is read once for
+// them all: X[q1][q2][.] = sum_q3 F[q1,q2,q3] A3[q3][.], then Y[q1][.][s3] +=
+// sum_q2 X[q1][q2][s3] A2[q2][.] over the terms of one direction-1 kind,
+// then band[.][s23] += sum_q1 Y[q1][s23] A1[q1][.]; the band row is staged
+// in shared memory and written with consecutive lanes on consecutive entries.
 template <int P, int DIM, int LC, int WARPS, typename R>
 __global__ void __launch_bounds__(32 * WARPS) gm_rows_kernel(const GmArgs A) {
-  constexpr int NB = 2 * P + 1, NP = P + 1, LM = LC ? LC : P * (P + 1);
+  constexpr int NB = 2 * P + 1, NP = P + 1, NBP = nb_pad<P>(), LM = LC ? LC : P * (P + 1);
   constexpr int NY = DIM == 3 ? NB * NB : NB;  // columns of Y (s2, s3)
   constexpr int NBAND = NY * NB;
-  constexpr int NOUT = (NBAND + 31) / 32;
-  constexpr int UR = LC ? 64 : 1;  // unroll the row loops only where their bounds are compile-time
+  constexpr int NK = (NY + 31) / 32;  // band columns s23 per lane
+  constexpr int H1 = (NB + 1) / 2;    // the first half of the x3 columns
+  constexpr int UR = LC ? 64 : 1;     // unroll the row loops only where their bounds are compile-time
   extern __shared__ __align__(16) unsigned char smrows[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  R *sA = reinterpret_cast<R *>(smrows) + warp * rows_warp_elems<P, DIM, LC>();  // [d][k][q][j]
-  R *sX = sA + DIM * 4 * LM * NB;
+  R *sA = reinterpret_cast<R *>(smrows) + warp * rows_warp_elems<P, DIM, LC>();  // [d][k][q][NBP]
+  R *sX = sA + DIM * 4 * LM * NBP;
   R *sY = sX + (DIM == 3 ? LM * LM * NB : 0);
+  R *sO = sY + LM * NY;
   const long long idx = (long long)blockIdx.x * WARPS + warp;
   int r[3] = {0, 0, 0};
   long long row;
@@ -785,23 +810,36 @@ __global__ void __launch_bounds__(32 * WARPS) gm_rows_kernel(const GmArgs A) {
     off[d] = A.off[d][r[d]];
     L[d] = LC ? LC : A.off[d][r[d] + 1] - off[d];
   }
-  // weight-test tables: A_d^k[q][j] = W(q) T(q, i), j = elem(q) - r + P + i
+  // weight-test tables: A_d^k[q][j] = W(q) T(q, j - o), o = elem(q) - r + P
 #pragma unroll
   for (int d = 0; d < DIM; d++) {
     const int *elem = A.tab[d][0].elem;
 #pragma unroll UR
-    for (int t = lane; t < 4 * L[d] * NB; t += 32) {
-      const int k = t / (L[d] * NB), q = (t / NB) % L[d], j = t % NB;
-      const int i = j - (elem[off[d] + q] - r[d] + P);
-      R v = 0;
-      if (i >= 0 && i < NP) v = (R)(A.W[d][k][off[d] + q] * A.T[d][k][(size_t)(off[d] + q) * NP + i]);
-      sA[((d * 4 + k) * LM + q) * NB + j] = v;
+    for (int t = lane; t < 4 * L[d]; t += 32) {
+      const int k = t / L[d], q = t - k * L[d];
+      const int o = elem[off[d] + q] - r[d] + P;
+      const R *wt = (std::is_same<R, float>::value ? (const R *)A.WT32[d][k] : (const R *)A.WT64[d][k]) +
+                    (size_t)(off[d] + q) * NP;
+      R v[NP];
+#pragma unroll
+      for (int i = 0; i < NP; i++) v[i] = wt[i];
+      R *rowp = sA + ((d * 4 + k) * LM + q) * NBP;
+#pragma unroll
+      for (int j = 0; j < NBP; j++) {
+        R x = 0;
+#pragma unroll
+        for (int i = 0; i < NP; i++)
+          if (j == o + i) x = v[i];
+        rowp[j] = x;
+      }
     }
   }
   __syncwarp();
-  R outK[NOUT];
+  R outK[NK][NB];
 #pragma unroll
-  for (int o = 0; o < NOUT; o++) outK[o] = 0;
+  for (int c = 0; c < NK; c++)
+#pragma unroll
+    for (int s = 0; s < NB; s++) outK[c][s] = 0;
   const GmTerm *terms = DIM == 3 ? c_terms3 : c_terms2;
   const int *gstart = DIM == 3 ? c_group_start3 : c_group_start2;
   const long long ob = (row - A.out_row0) * NBAND;
@@ -816,69 +854,116 @@ __global__ void __launch_bounds__(32 * WARPS) gm_rows_kernel(const GmArgs A) {
       const GmTerm &tm = terms[ti];
       k1 = tm.k[0];
       const R *F = static_cast<const R *>(A.F) + tm.grid * A.fstride;
-      const R *A2 = sA + ((1 * 4 + tm.k[1]) * LM) * NB;
+      const R *A2 = sA + ((1 * 4 + tm.k[1]) * LM) * NBP;
       if (DIM == 3) {
-        const R *A3 = sA + ((2 * 4 + tm.k[2]) * LM) * NB;
+        const R *A3 = sA + ((2 * 4 + tm.k[2]) * LM) * NBP;
         const R *F0 = F + off[0] + s2 * off[1] + s3 * (off[2] - A.slab_lo);
-        // X[q1][q2][s3] = sum_q3 F[q1, q2, q3] A3[q3][s3]
+        // X: items (q1, q2, half of the x3 columns)
 #pragma unroll UR
-        for (int t = lane; t < L[0] * L[1] * NB; t += 32) {
-          const int q1 = t % L[0], q2 = (t / L[0]) % L[1], c3 = t / (L[0] * L[1]);
+        for (int it = lane; it < 2 * L[0] * L[1]; it += 32) {
+          const int pr = it >> 1, c0 = (it & 1) * H1;
+          const int q1 = pr % L[0], q2 = pr / L[0];
           const R *f = F0 + q1 + s2 * q2;
-          R x = 0;
+          R acc[H1];
+#pragma unroll
+          for (int h = 0; h < H1; h++) acc[h] = 0;
 #pragma unroll UR
-          for (int q3 = 0; q3 < L[2]; q3++) x = fma(f[s3 * q3], A3[q3 * NB + c3], x);
-          sX[t] = x;
+          for (int q3 = 0; q3 < L[2]; q3++) {
+            const R fv = f[s3 * q3];
+            const R *a = A3 + q3 * NBP + c0;
+#pragma unroll
+            for (int h = 0; h < H1; h++) acc[h] = fma(fv, a[h], acc[h]);
+          }
+          R *x = sX + pr * NB + c0;
+#pragma unroll
+          for (int h = 0; h < H1; h++)
+            if (c0 + h < NB) x[h] = acc[h];
         }
         __syncwarp();
-        // Y[q1][s2][s3] += sum_q2 X[q1][q2][s3] A2[q2][s2]
+        // Y: items (q1, s3), all x2 columns
 #pragma unroll UR
-        for (int t = lane; t < L[0] * NB * NB; t += 32) {
-          const int q1 = t % L[0], c2 = (t / L[0]) % NB, c3 = t / (L[0] * NB);
-          R y = sY[t];
+        for (int it = lane; it < L[0] * NB; it += 32) {
+          const int q1 = it % L[0], c3 = it / L[0];
+          R acc[NB];
+#pragma unroll
+          for (int c = 0; c < NB; c++) acc[c] = 0;
 #pragma unroll UR
-          for (int q2 = 0; q2 < L[1]; q2++) y = fma(sX[q1 + L[0] * (q2 + L[1] * c3)], A2[q2 * NB + c2], y);
-          sY[t] = y;
+          for (int q2 = 0; q2 < L[1]; q2++) {
+            const R xv = sX[(q1 + L[0] * q2) * NB + c3];
+            const R *a = A2 + q2 * NBP;
+#pragma unroll
+            for (int c = 0; c < NB; c++) acc[c] = fma(xv, a[c], acc[c]);
+          }
+          R *y = sY + q1 * NY + NB * c3;
+#pragma unroll
+          for (int c = 0; c < NB; c++) y[c] += acc[c];
         }
         __syncwarp();
       } else {
         const R *F0 = F + off[0] + s2 * (off[1] - A.slab_lo);
-        // Y[q1][s2] += sum_q2 F[q1, q2] A2[q2][s2]
+        // Y: items q1, all x2 columns
 #pragma unroll UR
-        for (int t = lane; t < L[0] * NB; t += 32) {
-          const int q1 = t % L[0], c2 = t / L[0];
-          R y = sY[t];
+        for (int it = lane; it < L[0]; it += 32) {
+          R acc[NB];
+#pragma unroll
+          for (int c = 0; c < NB; c++) acc[c] = 0;
 #pragma unroll UR
-          for (int q2 = 0; q2 < L[1]; q2++) y = fma(F0[q1 + s2 * q2], A2[q2 * NB + c2], y);
-          sY[t] = y;
+          for (int q2 = 0; q2 < L[1]; q2++) {
+            const R fv = F0[it + s2 * q2];
+            const R *a = A2 + q2 * NBP;
+#pragma unroll
+            for (int c = 0; c < NB; c++) acc[c] = fma(fv, a[c], acc[c]);
+          }
+          R *y = sY + it * NY;
+#pragma unroll
+          for (int c = 0; c < NB; c++) y[c] += acc[c];
         }
         __syncwarp();
       }
     }
-    // band[s1 + NB * s23] += sum_q1 Y[q1][s23] A1[q1][s1]
-    const R *A1 = sA + ((0 * 4 + k1) * LM) * NB;
+    // band: items s23, all x1 columns
+    const R *A1 = sA + ((0 * 4 + k1) * LM) * NBP;
 #pragma unroll
-    for (int o = 0; o < NOUT; o++) {
-      const int e = lane + 32 * o;
-      if (e < NBAND) {
-        const int s1 = e % NB, s23 = e / NB;
-        R v = 0;
+    for (int c = 0; c < NK; c++) {
+      const int s23 = lane + 32 * c;
+      if (s23 < NY) {
+        R acc[NB];
+#pragma unroll
+        for (int s = 0; s < NB; s++) acc[s] = 0;
 #pragma unroll UR
-        for (int q1 = 0; q1 < L[0]; q1++) v = fma(sY[q1 + L[0] * s23], A1[q1 * NB + s1], v);
-        if (grp == 0)
-          static_cast<R *>(A.M)[ob + e] = v;
-        else
-          outK[o] += v;
+        for (int q1 = 0; q1 < L[0]; q1++) {
+          const R yv = sY[q1 * NY + s23];
+          const R *a = A1 + q1 * NBP;
+#pragma unroll
+          for (int s = 0; s < NB; s++) acc[s] = fma(yv, a[s], acc[s]);
+        }
+        if (grp == 0) {
+#pragma unroll
+          for (int s = 0; s < NB; s++) sO[s23 * NB + s] = acc[s];
+        } else {
+#pragma unroll
+          for (int s = 0; s < NB; s++) outK[c][s] += acc[s];
+        }
       }
     }
     __syncwarp();
+    if (grp == 0) {
+      R *M = static_cast<R *>(A.M) + ob;
+      for (int e = lane; e < NBAND; e += 32) M[e] = sO[e];
+      __syncwarp();
+    }
   }
   if (A.K) {
 #pragma unroll
-    for (int o = 0; o < NOUT; o++) {
-      const int e = lane + 32 * o;
-      if (e < NBAND) static_cast<R *>(A.K)[ob + e] = outK[o];
+    for (int c = 0; c < NK; c++) {
+      const int s23 = lane + 32 * c;
+      if (s23 < NY)
+#pragma unroll
+        for (int s = 0; s < NB; s++) sO[s23 * NB + s] = outK[c][s];
     }
+    __syncwarp();
+    R *K = static_cast<R *>(A.K) + ob;
+    for (int e = lane; e < NBAND; e += 32) K[e] = sO[e];
   }
 }
 
@@ -988,17 +1073,19 @@ extern "C" wq_status wq_assemble_general(const wq_rules *R, const double *net, c
     const DevDirKind &Dm = R->dev[d][0], &Ds = R->dev[d][1];
     const DevCross &Dx = R->devx[d];
     a.off[d] = Dm.off;
-    a.tab[d][0] = GmTab{Dm.elem, Dm.t0, Dm.t1, Dm.beta, Dm.tl};
-    a.tab[d][1] = GmTab{Ds.elem, Ds.t0, Ds.t1, Ds.beta, Ds.tl};
-    a.tab[d][2] = GmTab{Dx.elem, Dx.t0, Dx.t1, Dx.beta, Dx.tl};
-    a.W[d][0] = Dm.w;
-    a.T[d][0] = Dm.t0;
-    a.W[d][1] = Ds.w;
-    a.T[d][1] = Ds.t1;
-    a.W[d][2] = Dx.w2;
-    a.T[d][2] = Dx.t0;
-    a.W[d][3] = Dx.w3;
-    a.T[d][3] = Dx.t1;
+    a.tab[d][0] = GmTab{Dm.elem, Dm.t0, Dm.t1, Dm.beta, Dm.tl, nullptr, nullptr, nullptr};
+    a.tab[d][1] = GmTab{Ds.elem, Ds.t0, Ds.t1, Ds.beta, Ds.tl, nullptr, nullptr, nullptr};
+    a.tab[d][2] = GmTab{Dx.elem, Dx.t0, Dx.t1, Dx.beta, Dx.tl, nullptr, nullptr, nullptr};
+    const GmDevTab &G = R->gmt[d];
+    for (int k = 0; k < 3; k++) {
+      a.tab[d][k].t0f = G.t0f[k];
+      a.tab[d][k].tlf = G.tlf[k];
+      a.tab[d][k].betaf = G.betaf[k];
+    }
+    for (int k = 0; k < 4; k++) {
+      a.WT64[d][k] = G.wt64[k];
+      a.WT32[d][k] = G.wt32[k];
+    }
   }
   a.net = net;
   a.coef = coef;
@@ -1014,7 +1101,9 @@ extern "C" wq_status wq_assemble_general(const wq_rules *R, const double *net, c
   const std::vector<int> &offs = R->host[sd][0].off;
   const long long per_point = (long long)kGmGrids * a.np[0] * (dim == 3 ? a.np[1] : 1) * (long long)elt;
   // FP32: the scaled difference nets ([b][a], dim^2 arrays of the net's size) precede the factors
-  const long long dbytes = f32 ? (long long)((dim * dim * a.ntot * sizeof(float) + 255) / 256 * 256) : 0;
+  const long long ncoef = (long long)R->nc[0] * R->nc[1] * R->nc[2];
+  const long long dnet = f32 ? (long long)((dim * dim * a.ntot * sizeof(float) + 255) / 256 * 256) : 0;
+  const long long dbytes = f32 ? dnet + (long long)((ncoef * sizeof(float) + 255) / 256 * 256) : 0;
   int most = 0;
   for (int r = pl0; r <= pl1; r++) most = std::max(most, offs[r + 1] - offs[r]);
   // (WQ_GENERAL_SLAB_BYTES lowers the bound, down to one plane per slab: a
@@ -1051,12 +1140,15 @@ extern "C" wq_status wq_assemble_general(const wq_rules *R, const double *net, c
   }
   a.F = static_cast<char *>(R->dev_gm) + dbytes;
   a.D = f32 ? static_cast<const float *>(R->dev_gm) : nullptr;
+  float *coef32 = f32 ? reinterpret_cast<float *>(static_cast<char *>(R->dev_gm) + dnet) : nullptr;
+  a.coef32 = f32 && coef ? coef32 : nullptr;
   cudaError_t e = f32 ? set_limits<float>(p, dim) : set_limits<double>(p, dim);
   if (e != cudaSuccess) return WQ_ERR_CUDA;
   if (f32) {
-    const long long blocks = std::min<long long>((a.ntot + 255) / 256, 8192);
+    const long long blocks = std::min<long long>((std::max(a.ntot, ncoef) + 255) / 256, 8192);
     gm_diff_kernel<<<(unsigned)blocks, 256, 0, s>>>(net, static_cast<float *>(R->dev_gm), dim, p, a.n[0], a.n[1],
-                                                    a.N[0], a.N[1], a.N[2], a.ntot);
+                                                    a.N[0], a.N[1], a.N[2], a.ntot, coef, coef32, ncoef,
+                                                    R->dev_status);
     if (cudaGetLastError() != cudaSuccess) return WQ_ERR_CUDA;
   }
   for (const auto &sl : slabs) {

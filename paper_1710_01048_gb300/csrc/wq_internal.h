@@ -67,6 +67,17 @@ struct DevCross {
   int npts;
 };
 
+// Derived tables of one direction for maps given by a full control net:
+// per point set (m, s, x) the degree-p values, degree p-1 values and cubic
+// values in FP32 (the FP32 Jacobian reads no double), and per weight-test
+// kind 0..3 the products W(q) T(q, i) of each point's weight and its p+1
+// test values, in FP64 and FP32.
+struct GmDevTab {
+  const float *t0f[3], *tlf[3], *betaf[3];
+  const double *wt64[4];
+  const float *wt32[4];
+};
+
 // Device view of one direction and kind (all arrays in device memory).
 struct DevDirKind {
   const int *off;
@@ -121,6 +132,8 @@ struct wq_rules {
                                  // elements (the split assembly path; its own allocation)
   wq::DevCross devx[3] = {};      // device copy of hostx (its own allocation, dev_cross)
   void *dev_cross = nullptr;
+  wq::GmDevTab gmt[3] = {};       // derived tables of the non-separable path (allocation dev_gmtab)
+  void *dev_gmtab = nullptr;
   // scratch of the non-separable assembly (the metric factors of a slab of
   // rows), allocated by the first call that needs it, grown when needed
   mutable void *dev_gm = nullptr;
