@@ -456,6 +456,48 @@ def main():
     return 0
 
 
+def general_counts(Rg, dim, p, nel, has_coef):
+    """Algorithmic work of one assembly for a map given by a full control net
+    (wq_assemble_general): (flops of the row contractions, flops of the
+    per-point metric, factor points, HBM bytes of FP32 data flow).
+
+    Rows: per row and term, the sum-factorised contractions over the band's
+    non-zero structure, each 1D weight-test row touching p+1 band columns:
+    3D 2 L1 L2 L3 (p+1) + 2 L1 L2 (2p+1)(p+1) per term (10 terms) and
+    2 L1 (2p+1)^2 (p+1) per direction-1 group (5 groups); 2D 2 L1 L2 (p+1)
+    per term (5) and 2 L1 (2p+1)(p+1) per group (5).  Summed over rows these
+    factor into the per-direction point counts.  Metric: per point of each
+    grid the Jacobian (p+1 multiply-adds per entry), the coefficient (4
+    multiply-adds) and the
+    metric entry (determinant 15 flops, an off-diagonal or stiffness entry 31
+    in 3D; 5 and 13 in 2D); the partial contractions of the net that feed the
+    Jacobian are not counted."""
+    import numpy as np
+    NP, NB = p + 1, 2 * p + 1
+    n = [nel[a] + p for a in range(dim)]
+    np_ = [sum(len(Rg.row(a, 0, r)[0]) for r in range(n[a])) for a in range(dim)]
+    if dim == 3:
+        rows_fl = 10 * (2 * NP * np_[0] * np_[1] * np_[2] + 2 * NB * NP * np_[0] * np_[1] * n[2]) \
+            + 5 * 2 * NB * NB * NP * np_[0] * n[1] * n[2]
+        pts = np_[0] * np_[1] * np_[2]
+        per_pt_j = 2 * (3 * NP + 3 * NP + 3 * NP)
+        met = pts * (7 * per_pt_j + (7 * 8 if has_coef else 0) + 15 + 6 * 31)
+        grids = 7
+    else:
+        rows_fl = 5 * 2 * NP * np_[0] * np_[1] + 5 * 2 * NB * NP * np_[0] * n[1]
+        pts = np_[0] * np_[1]
+        per_pt_j = 2 * (2 * NP + 2 * NP)
+        met = pts * (4 * per_pt_j + (4 * 8 if has_coef else 0) + 5 + 3 * 13)
+        grids = 4
+    ntot = int(np.prod(n))
+    ncoef = int(np.prod([nel[a] + 3 for a in range(dim)]))
+    rows = int(np.prod(n))
+    nband = NB ** dim
+    bytes32 = (8 * dim * ntot + 2 * 4 * dim * dim * ntot + (12 * ncoef if has_coef else 0)
+               + 2 * 4 * grids * pts + 2 * 4 * rows * nband)
+    return float(rows_fl), float(met), int(grids * pts), float(bytes32)
+
+
 def run_variants(args, wq, inputs, R, w, g, gd, cd, bands, sample, timed, stream, peaks):
     """The other precisions of the headline workload (with their errors on the
     oracle's sampled rows), the other workloads of the same method, the
@@ -628,6 +670,48 @@ def run_variants(args, wq, inputs, R, w, g, gd, cd, bands, sample, timed, stream
         raise wq.WqError(sta, "apply variant")
     variants["apply_3d_p3_64"] = app
     Ra.close()
+
+    # maps given by a full control net (the off-diagonal metric terms with the
+    # mixed-derivative rules): the warped 64^3 cubic workload, FP64 and FP32
+    # (parity with the oracle is tested, not timed here)
+    gen_out = {}
+    for gname in ("3d_p3_64_warp",):
+        wn = inputs.NET_WORKLOADS[gname]
+        netn, cnn = inputs.make_net(wn["dim"], wn["p"], wn["nel"], wn["net"], wn["amp"], wn["coef"], wn["sigma"],
+                                    wn["seed"])
+        Rg = wq.Rules(wn["dim"], wn["p"], wn["nel"])
+        ndg, cdg = torch.from_numpy(netn).cuda(), torch.from_numpy(cnn).cuda()
+        rows_fl, met_fl, npts, b32 = general_counts(Rg, wn["dim"], wn["p"], wn["nel"], True)
+        ent = {"workload": gname, "nel": list(wn["nel"]), "degree": wn["p"], "rows": int(Rg.rows),
+               "nnz_per_matrix": int(Rg.nnz), "metric_points": npts, "flops_rows": rows_fl, "flops_metric": met_fl,
+               "fp32_algorithmic_bytes": b32}
+        for vp in ("fp64", "mixed"):
+            vdt = torch.float32 if vp == "mixed" else torch.float64
+            Mv = torch.empty((Rg.rows, Rg.band), dtype=vdt, device="cuda")
+            Kv = torch.empty((Rg.rows, Rg.band), dtype=vdt, device="cuda")
+            fn = lambda: wq.assemble_general(Rg, ndg, cdg, vp, out=(Mv, Kv), stream=stream,  # noqa: E731
+                                             check=False)
+            for _ in range(3):
+                fn()
+            vm = float(np.mean(timed(fn, max(3, min(args.steps, 5)))))
+            stg = wq.wq_status_check(Rg.handle, wq._stream_handle(stream))
+            if stg != wq.WQ_OK:
+                raise wq.WqError(stg, "general variant")
+            tf = (rows_fl + met_fl) / (vm * 1e-3) / 1e12
+            if vp == "fp64":
+                roof = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": tf / FP64_PEAK_TFLOPS}
+            else:
+                bw = b32 / (vm * 1e-3) / 1e9
+                roof = {"bound": "hbm", "achieved": bw, "peak": hbm, "unit": "GB/s", "frac": bw / hbm,
+                        "fp32_tflops": tf, "fp32_frac": tf / FP32_PEAK_TFLOPS}
+            ent[vp] = {"ms_per_step": vm, "value": 2 * Rg.nnz / (vm * 1e-3), "unit": "nnz/s", "dtype": DTYPE[vp],
+                       "roofline": roof}
+            del Mv, Kv
+            torch.cuda.empty_cache()
+        gen_out[gname] = ent
+        Rg.close()
+    variants["general_map"] = gen_out
 
     # the batch of 256 independent patches (8..48 elements per direction, p in {2, 3}):
     # one graph of two persistent launches, tuned, against one call per patch

@@ -40,6 +40,7 @@ constexpr int kGmChunk = 128;                   // x1 points per metric item
 constexpr int kGmCols = kGmChunk + 2 * kMaxP + 4;  // x1 control / coefficient columns of one chunk
 constexpr int kGmWarps = 4;                     // rows (warps) per CTA of the row kernel
 constexpr int kGmGrids = 7;
+constexpr int kGmRows64 = 2, kGmRows32 = 4;  // x2 rows per 3D metric item (FP64, FP32)
 
 struct GmTab {  // one direction, one point set (m, s, x): what the metric reads
   const int *elem;
@@ -178,13 +179,13 @@ __device__ __forceinline__ void block_minmax(int vlo, int vhi, int &vmin, int &v
 }
 
 // Shared memory of the 3D metric kernel (doubles): H of the two x3 patterns
-// [2][3][2P+1][kGmCols], the coefficient's Hc [P+4][kGmCols], E [10][kGmCols].
+// [2][3][R2B+2P][kGmCols], the coefficient's Hc [R2B+P+3][kGmCols], E [10][kGmCols].
 template <int P> constexpr int metric3_smem_doubles() {
-  return 2 * 3 * (2 * P + 1) * kGmCols + (P + 4) * kGmCols + 10 * kGmCols;
+  return 2 * 3 * (kGmRows64 + 2 * P) * kGmCols + (kGmRows64 + P + 3) * kGmCols + 10 * kGmCols;
 }
 
 template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3_kernel(const GmArgs A) {
-  constexpr int NP = P + 1, NI2 = 2 * P + 1, NL2 = P + 4, NT = kGmChunk;
+  constexpr int NP = P + 1, R2B = kGmRows64, NI2 = R2B + 2 * P, NL2 = R2B + P + 3, NT = kGmChunk;
   extern __shared__ double sm[];
   double *sHv = sm;                      // [a][i2][col]
   double *sHd = sHv + 3 * NI2 * kGmCols;  // [a][i2][col]
@@ -197,8 +198,9 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3_kernel(c
   long long item = blockIdx.x;
   const int c1 = (int)(item % nch1);
   item /= nch1;
-  const int r2 = (int)(item % A.n[1]);
-  item /= A.n[1];
+  const int nb2 = (A.n[1] + R2B - 1) / R2B;
+  const int r2a = (int)(item % nb2) * R2B, r2b = min(A.n[1], r2a + R2B) - 1;
+  item /= nb2;
   const int q3l = (int)(item % A.slab_n);
   const GmGroup &grp = c_groups3[(int)(item / A.slab_n)];  // read in place (no local copy)
   const int q3 = A.slab_lo + q3l;
@@ -222,8 +224,8 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3_kernel(c
   int emin, emax;
   block_minmax(myq < qb ? elem1[myq] : 0x7fffffff, myq < qb ? elem1[myq] : -1, emin, emax, sred);
   const int ni1 = emax + P - emin + 1, nl1 = emax + 3 - emin + 1;
-  // the x2 row's elements and the control / coefficient rows they touch
-  const int e2lo = max(0, r2 - P), e2hi = min(A.N[1] - 1, r2);
+  // the x2 rows' elements and the control / coefficient rows they touch
+  const int e2lo = max(0, r2a - P), e2hi = min(A.N[1] - 1, r2b);
   const int ni2 = e2hi + P - e2lo + 1, nl2 = e2hi + 3 - e2lo + 1;
   const int n1 = A.n[0], n2 = A.n[1], nc1 = A.nc[0], nc2 = A.nc[1];
 
@@ -257,7 +259,7 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3_kernel(c
 
   unsigned bits = 0;
   const GmTab &T2 = A.tab[1][grp.k2];
-  const int q2a = A.off[1][r2], q2b = A.off[1][r2 + 1];
+  const int q2a = A.off[1][r2a], q2b = A.off[1][r2b + 1];
   for (int q2 = q2a; q2 < q2b; q2++) {
     const int e2 = T2.elem[q2];
     double b2v[NP], b2d[NP], c2[4];
@@ -495,14 +497,14 @@ __device__ __forceinline__ float metric3f(int comp, const F3 &j0, const F3 &j1, 
 // Shared memory of the 3D FP32 metric kernel (floats): H of the three
 // Jacobian columns [3][3][2P+1][kGmCols], Hc [P+4][kGmCols], E [10][kGmCols].
 template <int P> constexpr int metric3f_smem_floats() {
-  return 9 * (2 * P + 1) * kGmCols + (P + 4) * kGmCols + 10 * kGmCols;
+  return 9 * (kGmRows32 + 2 * P) * kGmCols + (kGmRows32 + P + 3) * kGmCols + 10 * kGmCols;
 }
 
 // As gm_metric3_kernel, in FP32 from the difference nets: column b of J
 // contracts D_b with the degree p-1 basis in direction b and the degree-p
 // basis in the others (H: over x3, E: over x2, then x1 at each point).
 template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3f_kernel(const GmArgs A) {
-  constexpr int NP = P + 1, NI2 = 2 * P + 1, NL2 = P + 4, NT = kGmChunk;
+  constexpr int NP = P + 1, R2B = kGmRows32, NI2 = R2B + 2 * P, NL2 = R2B + P + 3, NT = kGmChunk;
   extern __shared__ float smf[];
   float *sH = smf;                      // [column b][a][i2][col]
   float *sHc = sH + 9 * NI2 * kGmCols;  // [l2][col]
@@ -514,8 +516,9 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3f_kernel(
   long long item = blockIdx.x;
   const int c1 = (int)(item % nch1);
   item /= nch1;
-  const int r2 = (int)(item % A.n[1]);
-  item /= A.n[1];
+  const int nb2 = (A.n[1] + R2B - 1) / R2B;
+  const int r2a = (int)(item % nb2) * R2B, r2b = min(A.n[1], r2a + R2B) - 1;
+  item /= nb2;
   const int q3l = (int)(item % A.slab_n);
   const GmGroup &grp = c_groups3[(int)(item / A.slab_n)];
   const int q3 = A.slab_lo + q3l;
@@ -534,7 +537,7 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3f_kernel(
   int emin, emax;
   block_minmax(myq < qb ? elem1[myq] : 0x7fffffff, myq < qb ? elem1[myq] : -1, emin, emax, sred);
   const int ni1 = emax + P - emin + 1, nl1 = emax + 3 - emin + 1;
-  const int e2lo = max(0, r2 - P), e2hi = min(A.N[1] - 1, r2);
+  const int e2lo = max(0, r2a - P), e2hi = min(A.N[1] - 1, r2b);
   const int ni2 = e2hi + P - e2lo + 1, nl2 = e2hi + 3 - e2lo + 1;
   const int n1 = A.n[0], n2 = A.n[1], nc1 = A.nc[0], nc2 = A.nc[1];
   const long long nt = A.ntot, s3 = (long long)n1 * n2;
@@ -571,7 +574,22 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3f_kernel(
   __syncthreads();
   unsigned bits = 0;
   const GmTab &T2 = A.tab[1][grp.k2];
-  const int q2a = A.off[1][r2], q2b = A.off[1][r2 + 1];
+  const int q2a = A.off[1][r2a], q2b = A.off[1][r2b + 1];
+  // this thread's x1 point: its basis values for each x1 point set of the group
+  float pv[2][NP], pl[2][P], pc[2][4];
+  const int ng = grp.ng;
+  if (myq < qb)
+#pragma unroll
+    for (int gi = 0; gi < 2; gi++) {
+      if (gi >= ng) break;
+      const GmTab &T1 = A.tab[0][grp.k1[gi]];
+#pragma unroll
+      for (int i = 0; i < NP; i++) pv[gi][i] = T1.t0f[(size_t)myq * NP + i];
+#pragma unroll
+      for (int j = 0; j < P; j++) pl[gi][j] = T1.tlf[(size_t)myq * P + j];
+#pragma unroll
+      for (int l = 0; l < 4; l++) pc[gi][l] = T1.betaf[(size_t)myq * 4 + l];
+    }
   for (int q2 = q2a; q2 < q2b; q2++) {
     const int e2 = T2.elem[q2];
     float b2v[NP], b2l[P], c2[4];
@@ -609,13 +627,10 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3f_kernel(
     __syncthreads();
     if (myq < qb) {
       const int o = elem1[myq] - emin;
-      for (int gi = 0; gi < grp.ng; gi++) {
-        const GmTab &T1 = A.tab[0][grp.k1[gi]];
-        float bv[NP], bl[P];
 #pragma unroll
-        for (int i = 0; i < NP; i++) bv[i] = T1.t0f[(size_t)myq * NP + i];
-#pragma unroll
-        for (int j = 0; j < P; j++) bl[j] = T1.tlf[(size_t)myq * P + j];
+      for (int gi = 0; gi < 2; gi++) {
+        if (gi >= ng) break;
+        const float *bv = pv[gi], *bl = pl[gi];
         float jc[3][3];  // jc[b][a] = d x_a / d xhat_b
 #pragma unroll
         for (int a = 0; a < 3; a++) {
@@ -636,7 +651,7 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3f_kernel(
         if (A.coef32) {
           c = 0.0f;
 #pragma unroll
-          for (int l = 0; l < 4; l++) c = fmaf(sE[9 * kGmCols + o + l], T1.betaf[(size_t)myq * 4 + l], c);
+          for (int l = 0; l < 4; l++) c = fmaf(sE[9 * kGmCols + o + l], pc[gi][l], c);
           if (!isfinite(c)) bits |= kBitNonFinite;
         }
         const float f = metric3f(grp.comp[gi], j0, j1, j2, c, bits);
@@ -1158,7 +1173,8 @@ extern "C" wq_status wq_assemble_general(const wq_rules *R, const double *net, c
     a.row_begin = std::max((long long)row_begin, sl.first * plane);
     a.row_end = std::min((long long)row_end, (sl.second + 1) * plane);
     const long long nch1 = (a.np[0] + kGmChunk - 1) / kGmChunk;
-    const long long nitems = dim == 3 ? 6LL * a.slab_n * R->n[1] * nch1 : 3LL * a.slab_n * nch1;
+    const int r2b = f32 ? kGmRows32 : kGmRows64;
+    const long long nitems = dim == 3 ? 6LL * a.slab_n * ((R->n[1] + r2b - 1) / r2b) * nch1 : 3LL * a.slab_n * nch1;
     if (nitems > 0x7fffffffLL) return WQ_ERR_UNSUPPORTED;
     const long long nr = a.row_end - a.row_begin;
     // interior planes of the slab: rows p .. nel-1 of the slab direction
