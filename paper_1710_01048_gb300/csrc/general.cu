@@ -66,6 +66,7 @@ struct GmArgs {
   long long fstride;
   int slab_lo, slab_n;      // 3D: x3 points [slab_lo, slab_lo + slab_n); 2D: x2 points
   int ib_lo, ib_n;          // the slab's interior x3 planes (2D: x2 lines) [ib_lo, ib_lo + ib_n)
+  int bp_lo, bp_hi;         // the slab's planes (2D: lines) [bp_lo, bp_hi]
   long long row_begin, row_end, out_row0;
   void *M, *K;              // bands, double or float
   unsigned *status;
@@ -809,15 +810,59 @@ __global__ void __launch_bounds__(32 * WARPS) gm_rows_kernel(const GmArgs A) {
     row = r[0] + (long long)A.n[0] * (r[1] + (long long)A.n[1] * r[2]);
     if (row < A.row_begin || row >= A.row_end) return;
   } else {
-    row = A.row_begin + idx;
-    if (row >= A.row_end) return;
-    r[0] = (int)(row % A.n[0]);
-    r[1] = (int)((row / A.n[0]) % A.n[1]);
-    if (DIM == 3) r[2] = (int)(row / ((long long)A.n[0] * A.n[1]));
-    bool interior = true;
-#pragma unroll
-    for (int d = 0; d < DIM; d++) interior = interior && r[d] >= P && r[d] <= A.N[d] - 1;
-    if (interior) return;
+    // the slab's other rows, enumerated without gaps: the planes (2D:
+    // lines) of the slab direction outside the interior range in full, and
+    // in the interior ones the rows with an earlier direction outside its
+    // interior range (lines with r2 outside it first, then r1 outside it)
+    constexpr int SD = DIM - 1;
+    const int n1 = A.n[0], b1 = max(0, A.N[0] - P);
+    const long long full = DIM == 3 ? (long long)n1 * A.n[1] : n1;
+    const int b2 = DIM == 3 ? max(0, A.N[1] - P) : 0;
+    const long long part = DIM == 3 ? (long long)(A.n[1] - b2) * n1 + (long long)b2 * (n1 - b1) : n1 - b1;
+    const int pl0 = A.bp_lo, pl1 = A.bp_hi, Ns = A.N[SD];
+    const int nA = max(0, min(pl1, P - 1) - pl0 + 1);
+    const int bLo = max(pl0, P), bHi = min(pl1, Ns - 1), nB = max(0, bHi - bLo + 1);
+    const int cLo = max(pl0, max(P, Ns));
+    long long j = idx;
+    int plane;
+    bool whole;
+    if (j < nA * full) {
+      plane = pl0 + (int)(j / full);
+      j %= full;
+      whole = true;
+    } else if ((j -= nA * full) < nB * part) {
+      plane = bLo + (int)(j / part);
+      j %= part;
+      whole = false;
+    } else {
+      j -= nB * part;
+      plane = cLo + (int)(j / full);
+      if (plane > pl1) return;
+      j %= full;
+      whole = true;
+    }
+    r[SD] = plane;
+    if (whole) {
+      r[0] = (int)(j % n1);
+      if (DIM == 3) r[1] = (int)(j / n1);
+    } else if (DIM == 3) {
+      const long long lines_out = (long long)(A.n[1] - b2) * n1;
+      if (j < lines_out) {
+        const int m = (int)(j / n1);
+        r[1] = m < P ? m : m + b2;
+        r[0] = (int)(j % n1);
+      } else {
+        j -= lines_out;
+        r[1] = P + (int)(j / (n1 - b1));
+        const int k = (int)(j % (n1 - b1));
+        r[0] = k < P ? k : k + b1;
+      }
+    } else {
+      const int k = (int)j;
+      r[0] = k < P ? k : k + b1;
+    }
+    row = r[0] + (long long)n1 * (r[1] + (long long)A.n[1] * r[2]);
+    if (row < A.row_begin || row >= A.row_end) return;
   }
   int off[3], L[3];
 #pragma unroll
@@ -1176,8 +1221,21 @@ extern "C" wq_status wq_assemble_general(const wq_rules *R, const double *net, c
     const int r2b = f32 ? kGmRows32 : kGmRows64;
     const long long nitems = dim == 3 ? 6LL * a.slab_n * ((R->n[1] + r2b - 1) / r2b) * nch1 : 3LL * a.slab_n * nch1;
     if (nitems > 0x7fffffffLL) return WQ_ERR_UNSUPPORTED;
-    const long long nr = a.row_end - a.row_begin;
-    // interior planes of the slab: rows p .. nel-1 of the slab direction
+    long long nr = 0;
+    // interior planes of the slab: rows p .. nel-1 of the slab direction;
+    // the other rows of the slab's planes, counted as the boundary kernel
+    // enumerates them
+    a.bp_lo = sl.first;
+    a.bp_hi = sl.second;
+    {
+      const long long n1 = R->n[0], b1 = std::max(0, R->nel[0] - p);
+      const long long full = dim == 3 ? n1 * R->n[1] : n1;
+      const long long b2 = dim == 3 ? std::max(0, R->nel[1] - p) : 0;
+      const long long part = dim == 3 ? (R->n[1] - b2) * n1 + b2 * (n1 - b1) : n1 - b1;
+      long long nb = 0;
+      for (int r = sl.first; r <= sl.second; r++) nb += (r >= p && r <= R->nel[sd] - 1) ? part : full;
+      nr = nb;
+    }
     a.ib_lo = std::max(sl.first, p);
     a.ib_n = std::max(0, std::min(sl.second, R->nel[sd] - 1) - a.ib_lo + 1);
     long long nint = (long long)std::max(0, R->nel[0] - p) * a.ib_n;
