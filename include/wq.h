@@ -466,8 +466,11 @@ wq_status wq_band_to_csr(const wq_rules *rules, wq_precision prec, const void *b
 /*
  * Synchronises `stream`, then returns and clears the device-detected status
  * of the assembly calls made with `rules` since the previous check:
- * WQ_ERR_GEOMETRY if some J_aa <= 0, WQ_ERR_NONFINITE if some input was NaN
- * or Inf, WQ_ERR_CUDA if a kernel failed, else WQ_OK.
+ * WQ_ERR_GEOMETRY if some J_aa <= 0 (or det J <= 0 for wq_assemble_general),
+ * WQ_ERR_NONFINITE if some input was NaN or Inf, WQ_ERR_UNSUPPORTED if a
+ * kernel met a size it cannot hold (it then writes nothing; not expected for
+ * any mesh the rules object accepts), WQ_ERR_CUDA if a kernel failed, else
+ * WQ_OK.
  */
 wq_status wq_status_check(const wq_rules *rules, void *stream);
 

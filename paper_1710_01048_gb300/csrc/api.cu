@@ -965,6 +965,7 @@ wq_status wq_status_check(const wq_rules *R, void *stream) {
   unsigned bits = 0;
   if (cudaMemcpy(&bits, R->dev_status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return WQ_ERR_CUDA;
   if (cudaMemset(R->dev_status, 0, sizeof(unsigned)) != cudaSuccess) return WQ_ERR_CUDA;
+  if (bits & wq::kBitInternal) return WQ_ERR_UNSUPPORTED;
   if (bits & wq::kBitNonFinite) return WQ_ERR_NONFINITE;
   if (bits & wq::kBitGeometry) return WQ_ERR_GEOMETRY;
   return WQ_OK;

@@ -37,7 +37,12 @@ namespace wq {
 namespace {
 
 constexpr int kGmChunk = 128;                   // x1 points per metric item
-constexpr int kGmCols = kGmChunk + 2 * kMaxP + 4;  // x1 control / coefficient columns of one chunk
+// x1 control / coefficient columns one chunk of kGmChunk points can touch:
+// every row has at least p+1 points (its weighted rule, or p+1 Gauss-Legendre
+// points per element), so a chunk spans at most ceil((kGmChunk-1)/(p+1)) + 1
+// rows r_a..r_b, whose points lie in elements r_a-p .. r_b; their control
+// columns are r_a-p .. r_b+p and coefficient columns r_a-p .. r_b+3
+template <int P> constexpr int gm_cols() { return kGmChunk / (P + 1) + 2 * P + 5; }
 constexpr int kGmWarps = 4;                     // rows (warps) per CTA of the row kernel
 constexpr int kGmGrids = 7;
 constexpr int kGmRows64 = 2, kGmRows32 = 4;  // x2 rows per 3D metric item (FP64, FP32)
@@ -182,10 +187,12 @@ __device__ __forceinline__ void block_minmax(int vlo, int vhi, int &vmin, int &v
 // Shared memory of the 3D metric kernel (doubles): H of the two x3 patterns
 // [2][3][R2B+2P][kGmCols], the coefficient's Hc [R2B+P+3][kGmCols], E [10][kGmCols].
 template <int P> constexpr int metric3_smem_doubles() {
+  constexpr int kGmCols = gm_cols<P>();
   return 2 * 3 * (kGmRows64 + 2 * P) * kGmCols + (kGmRows64 + P + 3) * kGmCols + 10 * kGmCols;
 }
 
 template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3_kernel(const GmArgs A) {
+  constexpr int kGmCols = gm_cols<P>();
   constexpr int NP = P + 1, R2B = kGmRows64, NI2 = R2B + 2 * P, NL2 = R2B + P + 3, NT = kGmChunk;
   extern __shared__ double sm[];
   double *sHv = sm;                      // [a][i2][col]
@@ -225,6 +232,10 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3_kernel(c
   int emin, emax;
   block_minmax(myq < qb ? elem1[myq] : 0x7fffffff, myq < qb ? elem1[myq] : -1, emin, emax, sred);
   const int ni1 = emax + P - emin + 1, nl1 = emax + 3 - emin + 1;
+  if (ni1 > kGmCols || nl1 > kGmCols) {  // cannot happen (see gm_cols); reported, nothing written
+    if (tid == 0) atomicOr(A.status, kBitInternal);
+    return;
+  }
   // the x2 rows' elements and the control / coefficient rows they touch
   const int e2lo = max(0, r2a - P), e2hi = min(A.N[1] - 1, r2b);
   const int ni2 = e2hi + P - e2lo + 1, nl2 = e2hi + 3 - e2lo + 1;
@@ -342,6 +353,7 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3_kernel(c
 // 2D: a CTA takes one x2 point (of the group's x2 set) and a chunk of x1
 // points; E is the net's contraction over that point's p+1 control rows.
 template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric2_kernel(const GmArgs A) {
+  constexpr int kGmCols = gm_cols<P>();
   constexpr int NP = P + 1, NT = kGmChunk;
   __shared__ double sE[5 * kGmCols];  // [v0, v1, d0, d1, c][col]
   __shared__ int sred[2];
@@ -370,6 +382,10 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric2_kernel(c
   int emin, emax;
   block_minmax(myq < qb ? elem1[myq] : 0x7fffffff, myq < qb ? elem1[myq] : -1, emin, emax, sred);
   const int ni1 = emax + P - emin + 1, nl1 = emax + 3 - emin + 1;
+  if (ni1 > kGmCols || nl1 > kGmCols) {  // cannot happen (see gm_cols); reported, nothing written
+    if (tid == 0) atomicOr(A.status, kBitInternal);
+    return;
+  }
   const int n1 = A.n[0], nc1 = A.nc[0];
   for (int col = tid; col < ni1; col += NT) {
 #pragma unroll
@@ -498,13 +514,15 @@ __device__ __forceinline__ float metric3f(int comp, const F3 &j0, const F3 &j1, 
 // Shared memory of the 3D FP32 metric kernel (floats): H of the three
 // Jacobian columns [3][3][2P+1][kGmCols], Hc [P+4][kGmCols], E [10][kGmCols].
 template <int P> constexpr int metric3f_smem_floats() {
+  constexpr int kGmCols = gm_cols<P>();
   return 9 * (kGmRows32 + 2 * P) * kGmCols + (kGmRows32 + P + 3) * kGmCols + 10 * kGmCols;
 }
 
 // As gm_metric3_kernel, in FP32 from the difference nets: column b of J
 // contracts D_b with the degree p-1 basis in direction b and the degree-p
 // basis in the others (H: over x3, E: over x2, then x1 at each point).
-template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3f_kernel(const GmArgs A) {
+template <int P> __global__ void __launch_bounds__(kGmChunk, 5) gm_metric3f_kernel(const GmArgs A) {
+  constexpr int kGmCols = gm_cols<P>();
   constexpr int NP = P + 1, R2B = kGmRows32, NI2 = R2B + 2 * P, NL2 = R2B + P + 3, NT = kGmChunk;
   extern __shared__ float smf[];
   float *sH = smf;                      // [column b][a][i2][col]
@@ -538,6 +556,10 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3f_kernel(
   int emin, emax;
   block_minmax(myq < qb ? elem1[myq] : 0x7fffffff, myq < qb ? elem1[myq] : -1, emin, emax, sred);
   const int ni1 = emax + P - emin + 1, nl1 = emax + 3 - emin + 1;
+  if (ni1 > kGmCols || nl1 > kGmCols) {  // cannot happen (see gm_cols); reported, nothing written
+    if (tid == 0) atomicOr(A.status, kBitInternal);
+    return;
+  }
   const int e2lo = max(0, r2a - P), e2hi = min(A.N[1] - 1, r2b);
   const int ni2 = e2hi + P - e2lo + 1, nl2 = e2hi + 3 - e2lo + 1;
   const int n1 = A.n[0], n2 = A.n[1], nc1 = A.nc[0], nc2 = A.nc[1];
@@ -668,6 +690,7 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3f_kernel(
 // 2D FP32: E0 = D0 contracted with the x2 point's degree-p basis, E1 = D1
 // with its degree p-1 basis; J's columns at each x1 point.
 template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric2f_kernel(const GmArgs A) {
+  constexpr int kGmCols = gm_cols<P>();
   constexpr int NP = P + 1, NT = kGmChunk;
   __shared__ float sE[5 * kGmCols];  // [E0 a0, a1, E1 a0, a1, c][col]
   __shared__ int sred[2];
@@ -695,6 +718,10 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric2f_kernel(
   int emin, emax;
   block_minmax(myq < qb ? elem1[myq] : 0x7fffffff, myq < qb ? elem1[myq] : -1, emin, emax, sred);
   const int ni1 = emax + P - emin + 1, nl1 = emax + 3 - emin + 1;
+  if (ni1 > kGmCols || nl1 > kGmCols) {  // cannot happen (see gm_cols); reported, nothing written
+    if (tid == 0) atomicOr(A.status, kBitInternal);
+    return;
+  }
   const int n1 = A.n[0], nc1 = A.nc[0];
   const long long nt = A.ntot;
   for (int t = tid; t < 2 * ni1; t += NT) {
