@@ -63,7 +63,9 @@ typedef enum wq_status {
   WQ_ERR_NONFINITE = 5,      /* NaN or Inf in the geometry or coefficients */
   WQ_ERR_CUDA = 6,           /* a CUDA runtime call failed */
   WQ_ERR_OOM = 7,            /* device allocation failed */
-  WQ_ERR_TIMEOUT = 8         /* reserved: a bounded device wait expired */
+  WQ_ERR_TIMEOUT = 8,        /* reserved: a bounded device wait expired */
+  WQ_ERR_CHECK = 9           /* a device-side range check failed: only libraries built with
+                                -DWQ_CHECKED=1 run these checks; the access was skipped */
 } wq_status;
 
 typedef enum wq_precision {
@@ -469,8 +471,8 @@ wq_status wq_band_to_csr(const wq_rules *rules, wq_precision prec, const void *b
  * WQ_ERR_GEOMETRY if some J_aa <= 0 (or det J <= 0 for wq_assemble_general),
  * WQ_ERR_NONFINITE if some input was NaN or Inf, WQ_ERR_UNSUPPORTED if a
  * kernel met a size it cannot hold (it then writes nothing; not expected for
- * any mesh the rules object accepts), WQ_ERR_CUDA if a kernel failed, else
- * WQ_OK.
+ * any mesh the rules object accepts), WQ_ERR_CHECK if a range check of a
+ * checked build failed, WQ_ERR_CUDA if a kernel failed, else WQ_OK.
  */
 wq_status wq_status_check(const wq_rules *rules, void *stream);
 

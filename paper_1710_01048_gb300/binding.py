@@ -14,10 +14,12 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libwq.so")
+# the in-tree build; WQ_LIBRARY may name another build of the same sources
+# (e.g. the checked build, compiled with -DWQ_CHECKED=1)
+LIB_PATH = os.environ.get("WQ_LIBRARY") or os.path.join(_HERE, "_build", "libwq.so")
 
 WQ_OK, WQ_ERR_ARG, WQ_ERR_UNSUPPORTED, WQ_ERR_NO_CONVERGENCE = 0, 1, 2, 3
-WQ_ERR_GEOMETRY, WQ_ERR_NONFINITE, WQ_ERR_CUDA, WQ_ERR_OOM, WQ_ERR_TIMEOUT = 4, 5, 6, 7, 8
+WQ_ERR_GEOMETRY, WQ_ERR_NONFINITE, WQ_ERR_CUDA, WQ_ERR_OOM, WQ_ERR_TIMEOUT, WQ_ERR_CHECK = 4, 5, 6, 7, 8, 9
 WQ_FP64, WQ_MIXED, WQ_DF64 = 0, 1, 2
 PRECISIONS = {"fp64": WQ_FP64, "mixed": WQ_MIXED, "df64": WQ_DF64}
 WQ_KIND_MASS, WQ_KIND_STIFFNESS, WQ_KIND_MIXED_DW, WQ_KIND_MIXED_WD = 0, 1, 2, 3

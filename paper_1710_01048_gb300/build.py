@@ -37,7 +37,7 @@ CXX_FLAGS = ["-O2", "-fPIC", "-std=c++17", "-ffp-contract=off", "-fno-fast-math"
 SOURCES = ["rules.cpp", "api.cu", "rows_p2_double.cu", "rows_p3_double.cu", "rows_p2_float.cu", "rows_p3_float.cu",
            "rows_p2_dd.cu", "rows_p3_dd.cu", "noalloc.cu", "batch.cu", "batch_double.cu", "batch_float.cu",
            "batch_dd.cu", "csr.cu", "general.cu", "tune_cache.cpp"]
-HEADERS = ["wq_internal.h", "assemble.cuh", "launch.cuh", "dd.cuh", "adjoint.cuh", "fold.cuh", "batch.cuh", "ukernel.cuh"]
+HEADERS = ["wq_internal.h", "checked.cuh", "assemble.cuh", "launch.cuh", "dd.cuh", "adjoint.cuh", "fold.cuh", "batch.cuh", "ukernel.cuh"]
 
 
 def _newest_dep():

@@ -371,8 +371,10 @@ __global__ void __launch_bounds__(32 * kRowsWarps, adj_min_blocks<R>()) adjoint_
       for (int s2 = 0; s2 < 2; s2++) {
         const int t = lane + 32 * s2;
         const int l3 = t % NL, l2 = t / NL;
-        if (t < NL * NL && l2 < nl2 && l3 < nl3) {
-          AA.partial[chunk_slot + ((long long)l3 * NL + l2) * AA.nl1max + l1] = r_to_double(cb[s2]);
+        const long long pidx = chunk_slot + ((long long)l3 * NL + l2) * AA.nl1max + l1;
+        if (t < NL * NL && l2 < nl2 && l3 < nl3 &&
+            check_range(A.status, pidx, 1, (long long)A.n[1] * A.n[2] * AA.nch_max * AA.blk)) {
+          AA.partial[pidx] = r_to_double(cb[s2]);
         }
       }
     } else {
@@ -405,7 +407,8 @@ __global__ void __launch_bounds__(32 * kRowsWarps, adj_min_blocks<R>()) adjoint_
             s = r_fma(wq[1 * LM + q2], sB23[(1 * LM + q2) * 4 + i], s);
           }
         }
-        AA.partial[chunk_slot + (long long)l2 * AA.nl1max + l1] = r_to_double(s);
+        const long long pidx = chunk_slot + (long long)l2 * AA.nl1max + l1;
+        if (check_range(A.status, pidx, 1, (long long)A.n[1] * AA.nch_max * AA.blk)) AA.partial[pidx] = r_to_double(s);
       }
       (void)cb;
     }

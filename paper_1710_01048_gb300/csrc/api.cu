@@ -632,6 +632,7 @@ const char *wq_status_string(wq_status s) {
     case WQ_ERR_CUDA: return "CUDA runtime error";
     case WQ_ERR_OOM: return "device allocation failed";
     case WQ_ERR_TIMEOUT: return "bounded device wait expired";
+    case WQ_ERR_CHECK: return "a device-side range check failed (checked build)";
   }
   return "unknown status";
 }
@@ -966,6 +967,7 @@ wq_status wq_status_check(const wq_rules *R, void *stream) {
   if (cudaMemcpy(&bits, R->dev_status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return WQ_ERR_CUDA;
   if (cudaMemset(R->dev_status, 0, sizeof(unsigned)) != cudaSuccess) return WQ_ERR_CUDA;
   if (bits & wq::kBitInternal) return WQ_ERR_UNSUPPORTED;
+  if (bits & wq::kBitChecked) return WQ_ERR_CHECK;
   if (bits & wq::kBitNonFinite) return WQ_ERR_NONFINITE;
   if (bits & wq::kBitGeometry) return WQ_ERR_GEOMETRY;
   return WQ_OK;

@@ -35,6 +35,7 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "checked.cuh"
 #include "dd.cuh"
 
 namespace wq {
@@ -686,8 +687,9 @@ __device__ __forceinline__ void rows_phase_b(const RowsArgs &A, const R *sU, con
         const int nent = ((nitems - ib0) < 32 * SUB ? (nitems - ib0) : 32 * SUB) * NB;
         fence_proxy_async();
         __syncwarp();
-        if constexpr (DO_M) stage_out(gM, sM, nent, lane, 0, 1);
-        if constexpr (DO_K) stage_out(gK, sK, nent, lane, 0, 8);
+        const bool inb = check_range(A.status, ochunk + (long long)ib0 * NB, nent, (A.row_end - A.row_begin) * BAND);
+        if constexpr (DO_M) if (inb) stage_out(gM, sM, nent, lane, 0, 1);
+        if constexpr (DO_K) if (inb) stage_out(gK, sK, nent, lane, 0, 8);
         if (lane == 0) bulk_commit();
       }
     } else {
@@ -698,7 +700,8 @@ __device__ __forceinline__ void rows_phase_b(const RowsArgs &A, const R *sU, con
         }
         __syncwarp();
         O *gM = static_cast<O *>(A.M) + ochunk + (long long)ib * NB;
-        for (int i = lane; i < nent; i += 32) gM[i] = r_out(wst[i]);
+        if (check_range(A.status, ochunk + (long long)ib * NB, nent, (A.row_end - A.row_begin) * BAND))
+          for (int i = lane; i < nent; i += 32) gM[i] = r_out(wst[i]);
         __syncwarp();
       }
       if constexpr (DO_K) {
@@ -708,7 +711,8 @@ __device__ __forceinline__ void rows_phase_b(const RowsArgs &A, const R *sU, con
         }
         __syncwarp();
         O *gK = static_cast<O *>(A.K) + ochunk + (long long)ib * NB;
-        for (int i = lane; i < nent; i += 32) gK[i] = r_out(wst[i]);
+        if (check_range(A.status, ochunk + (long long)ib * NB, nent, (A.row_end - A.row_begin) * BAND))
+          for (int i = lane; i < nent; i += 32) gK[i] = r_out(wst[i]);
         __syncwarp();
       }
     }
@@ -735,8 +739,10 @@ __device__ __forceinline__ void rows_phase_b(const RowsArgs &A, const R *sU, con
       }
       if (lane == 0) {
         const long long yi = base + a + rl - A.row_begin;
-        if (DO_M && A.M) static_cast<O *>(A.M)[yi] = r_out(sm);
-        if (DO_K && A.K) static_cast<O *>(A.K)[yi] = r_out(sk);
+        if (check_range(A.status, yi, 1, A.row_end - A.row_begin)) {
+          if (DO_M && A.M) static_cast<O *>(A.M)[yi] = r_out(sm);
+          if (DO_K && A.K) static_cast<O *>(A.K)[yi] = r_out(sk);
+        }
       }
     }
   }

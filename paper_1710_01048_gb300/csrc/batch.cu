@@ -426,6 +426,7 @@ wq_status wq_batch_status(wq_batch *B, void *stream) {
   unsigned bits = 0;
   if (cudaMemcpy(&bits, B->dev_status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return WQ_ERR_CUDA;
   if (cudaMemset(B->dev_status, 0, sizeof(unsigned)) != cudaSuccess) return WQ_ERR_CUDA;
+  if (bits & wq::kBitChecked) return WQ_ERR_CHECK;
   if (bits & wq::kBitNonFinite) return WQ_ERR_NONFINITE;
   if (bits & wq::kBitGeometry) return WQ_ERR_GEOMETRY;
   return WQ_OK;

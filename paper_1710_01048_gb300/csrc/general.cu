@@ -31,6 +31,7 @@
 #include <cstring>
 #include <vector>
 
+#include "checked.cuh"
 #include "wq_internal.h"
 
 namespace wq {
@@ -72,7 +73,7 @@ struct GmArgs {
   int slab_lo, slab_n;      // 3D: x3 points [slab_lo, slab_lo + slab_n); 2D: x2 points
   int ib_lo, ib_n;          // the slab's interior x3 planes (2D: x2 lines) [ib_lo, ib_lo + ib_n)
   int bp_lo, bp_hi;         // the slab's planes (2D: lines) [bp_lo, bp_hi]
-  long long row_begin, row_end, out_row0;
+  long long row_begin, row_end, out_row0, out_rows;  // slab rows; the call's first row and row count
   void *M, *K;              // bands, double or float
   unsigned *status;
 };
@@ -341,7 +342,10 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric3_kernel(c
           if (!isfinite(c)) bits |= kBitNonFinite;
         }
         const double f = metric3(grp.comp[gi], j0, j1, j2, c, bits);
-        static_cast<double *>(A.F)[grp.grid[gi] * A.fstride + myq + (long long)np1 * (q2 + (long long)np2 * q3l)] = f;
+        {
+          const long long fi = grp.grid[gi] * A.fstride + myq + (long long)np1 * (q2 + (long long)np2 * q3l);
+          if (check_range(A.status, fi, 1, (long long)kGmGrids * A.fstride)) static_cast<double *>(A.F)[fi] = f;
+        }
       }
     }
     __syncthreads();
@@ -435,8 +439,10 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric2_kernel(c
         for (int l = 0; l < 4; l++) c = fma(sE[4 * kGmCols + o + l], T1.beta[(size_t)myq * 4 + l], c);
         if (!isfinite(c)) bits |= kBitNonFinite;
       }
-      static_cast<double *>(A.F)[grp.grid[gi] * A.fstride + myq + (long long)np1 * q2l] =
-          metric2(grp.comp[gi], j0, j1, c, bits);
+      {
+        const long long fi = grp.grid[gi] * A.fstride + myq + (long long)np1 * q2l;
+        if (check_range(A.status, fi, 1, (long long)kGmGrids * A.fstride)) static_cast<double *>(A.F)[fi] = metric2(grp.comp[gi], j0, j1, c, bits);
+      }
     }
   }
   bits = __reduce_or_sync(0xffffffffu, bits);
@@ -678,7 +684,10 @@ template <int P> __global__ void __launch_bounds__(kGmChunk, 5) gm_metric3f_kern
           if (!isfinite(c)) bits |= kBitNonFinite;
         }
         const float f = metric3f(grp.comp[gi], j0, j1, j2, c, bits);
-        static_cast<float *>(A.F)[grp.grid[gi] * A.fstride + myq + (long long)np1 * (q2 + (long long)np2 * q3l)] = f;
+        {
+          const long long fi = grp.grid[gi] * A.fstride + myq + (long long)np1 * (q2 + (long long)np2 * q3l);
+          if (check_range(A.status, fi, 1, (long long)kGmGrids * A.fstride)) static_cast<float *>(A.F)[fi] = f;
+        }
       }
     }
     __syncthreads();
@@ -780,7 +789,10 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric2f_kernel(
         const float rb0 = b == 0 ? j1[1] : -j0[1], rb1 = b == 0 ? -j1[0] : j0[0];
         f = c * fmaf(ra0, rb0, ra1 * rb1) / adet;
       }
-      static_cast<float *>(A.F)[grp.grid[gi] * A.fstride + myq + (long long)np1 * q2l] = f;
+      {
+        const long long fi = grp.grid[gi] * A.fstride + myq + (long long)np1 * q2l;
+        if (check_range(A.status, fi, 1, (long long)kGmGrids * A.fstride)) static_cast<float *>(A.F)[fi] = f;
+      }
     }
   }
   bits = __reduce_or_sync(0xffffffffu, bits);
@@ -931,6 +943,11 @@ __global__ void __launch_bounds__(32 * WARPS) gm_rows_kernel(const GmArgs A) {
   const int *gstart = DIM == 3 ? c_group_start3 : c_group_start2;
   const long long ob = (row - A.out_row0) * NBAND;
   const long long s2 = A.np[0], s3 = (long long)A.np[0] * A.np[1];
+  // the row's factor box, first to last point, in every grid
+  if (!check_range(A.status, off[0] + s2 * off[1] + (DIM == 3 ? s3 * (off[2] - A.slab_lo) : -s2 * A.slab_lo),
+                   (L[0] - 1) + s2 * (L[1] - 1) + (DIM == 3 ? s3 * (L[2] - 1) : 0) + 1, A.fstride) ||
+      !check_range(A.status, ob, NBAND, A.out_rows * NBAND))
+    return;
   for (int grp = 0; grp < 5; grp++) {
     if (grp == 0 ? !A.M : !A.K) continue;
 #pragma unroll UR
@@ -1179,6 +1196,7 @@ extern "C" wq_status wq_assemble_general(const wq_rules *R, const double *net, c
   a.M = M;
   a.K = K;
   a.out_row0 = row_begin;
+  a.out_rows = row_end - row_begin;
   a.status = R->dev_status;
 
   // slabs of whole x3 planes (3D) or x2 lines (2D), their points' factors at most kGmScratchBytes

@@ -245,6 +245,7 @@ extern "C" wq_status wq_assemble_noalloc(const wq_rules *R, const double *const 
   if (cudaStreamSynchronize(s) != cudaSuccess) return WQ_ERR_CUDA;
   unsigned bits = 0;
   if (cudaMemcpy(&bits, status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return WQ_ERR_CUDA;
+  if (bits & wq::kBitChecked) return WQ_ERR_CHECK;
   if (bits & wq::kBitNonFinite) return WQ_ERR_NONFINITE;
   if (bits & wq::kBitGeometry) return WQ_ERR_GEOMETRY;
   return WQ_OK;

@@ -386,8 +386,11 @@ __device__ __forceinline__ void u_block(const UArgs &A, int bid, unsigned char *
       }
       fence_proxy_async();
       __syncwarp();
-      stage_out(dst[0], st[0], nent, lane, 0, 1);
-      stage_out(dst[1], st[1], nent, lane, 0, 8);
+      const long long utot = (long long)A.n[1] * A.n[2] * 2 * nc1 * NPAIR;
+      if (check_range(A.status, (((long long)(lid0 + b) * 2 + 0) * nc1 + l1a) * NPAIR + (long long)i0 * NB, nent, utot))
+        stage_out(dst[0], st[0], nent, lane, 0, 1);
+      if (check_range(A.status, (((long long)(lid0 + b) * 2 + 1) * nc1 + l1a) * NPAIR + (long long)i0 * NB, nent, utot))
+        stage_out(dst[1], st[1], nent, lane, 0, 8);
       if (lane == 0) bulk_commit();
     } else {
 #pragma unroll
@@ -398,7 +401,9 @@ __device__ __forceinline__ void u_block(const UArgs &A, int bid, unsigned char *
         }
         __syncwarp();
         R *dst = Ug + (((size_t)(lid0 + b) * 2 + u) * nc1 + l1a) * NPAIR + (size_t)i0 * NB;
-        for (int e = lane; e < nent; e += 32) dst[e] = wst[e];
+        if (check_range(A.status, (((long long)(lid0 + b) * 2 + u) * nc1 + l1a) * NPAIR + (long long)i0 * NB, nent,
+                        (long long)A.n[1] * A.n[2] * 2 * nc1 * NPAIR))
+          for (int e = lane; e < nent; e += 32) dst[e] = wst[e];
         __syncwarp();
       }
     }
@@ -466,7 +471,9 @@ __device__ __forceinline__ void rows_ug_block(const RowsArgs &A, int bid, unsign
   const int nc1 = A.nc[0];
 #pragma unroll
   for (int u = 0; u < L::NU; u++)
-    cp_async_n(sU + u * NL1 * NPAIR, Ug + (((size_t)line * 2 + u) * nc1 + l1lo) * NPAIR, nl1 * NPAIR, tid, NT);
+    if (check_range(A.status, (((long long)line * 2 + u) * nc1 + l1lo) * NPAIR, (long long)nl1 * NPAIR,
+                    (long long)A.n[1] * A.n[2] * 2 * nc1 * NPAIR))
+      cp_async_n(sU + u * NL1 * NPAIR, Ug + (((size_t)line * 2 + u) * nc1 + l1lo) * NPAIR, nl1 * NPAIR, tid, NT);
   cp_async_wait_all();
   __syncthreads();
   rows_phase_b<P, 3, L::MAXPTS1, NL1, false, DO_M, DO_K, R>(A, sU, sV1, sB1, sE1, sOff1, sW, a, T, l1lo, base);
@@ -579,7 +586,9 @@ __device__ __forceinline__ void apply_ug_block(const RowsArgs &A, int bid, unsig
   const int nc1 = A.nc[0];
 #pragma unroll
   for (int u = 0; u < L::NU; u++)
-    cp_async_n(sU + u * NL1 * NPAIR, Ug + (((size_t)line * 2 + u) * nc1 + l1lo) * NPAIR, nl1 * NPAIR, tid, NT);
+    if (check_range(A.status, (((long long)line * 2 + u) * nc1 + l1lo) * NPAIR, (long long)nl1 * NPAIR,
+                    (long long)A.n[1] * A.n[2] * 2 * nc1 * NPAIR))
+      cp_async_n(sU + u * NL1 * NPAIR, Ug + (((size_t)line * 2 + u) * nc1 + l1lo) * NPAIR, nl1 * NPAIR, tid, NT);
   stage_x<P, 3, XL>(A, line, a, T, sX);
   cp_async_wait_all();
   __syncthreads();

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/wq.h"
+#include "checked.cuh"
 
 namespace wq {
 
@@ -34,6 +35,7 @@ constexpr int kModeWQ = 0, kModeGL = 1, kModeNC = 2;
 constexpr unsigned kBitGeometry = 1u;
 constexpr unsigned kBitNonFinite = 2u;
 constexpr unsigned kBitInternal = 4u;  // a kernel met a size it was not built for (nothing written)
+// 8u: a failed range check of the checked build (kBitChecked, checked.cuh)
 
 // One direction and one kind (mass or stiffness) of the 1D row rules.
 // Point q of row r lies in element elem[q]; the p+1 B-splines acting there

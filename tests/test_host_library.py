@@ -38,7 +38,7 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_status_strings():
-    for s in range(9):
+    for s in range(10):
         assert len(wq.wq_status_string(s)) >= 2 and wq.wq_status_string(s) != "unknown status"
     assert wq.wq_version() >= 100
 
