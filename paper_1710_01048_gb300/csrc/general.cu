@@ -71,7 +71,6 @@ struct GmArgs {
   const float *coef32;      // FP32 path: the coefficients in FP32 (null: c = 1)
   long long fstride;
   int slab_lo, slab_n;      // 3D: x3 points [slab_lo, slab_lo + slab_n); 2D: x2 points
-  int ib_lo, ib_n;          // the slab's interior x3 planes (2D: x2 lines) [ib_lo, ib_lo + ib_n)
   int bp_lo, bp_hi;         // the slab's planes (2D: lines) [bp_lo, bp_hi]
   long long row_begin, row_end, out_row0, out_rows;  // slab rows; the call's first row and row count
   void *M, *K;              // bands, double or float
@@ -804,116 +803,184 @@ template <int P> __global__ void __launch_bounds__(kGmChunk) gm_metric2f_kernel(
 // Y [LM][NB^(DIM-1)] and the band row being written [NB^DIM]; LM = the most
 // points of a row in one direction (LC when the row class fixes it).
 template <int P> constexpr int nb_pad() { return ((2 * P + 1) + 3) / 4 * 4; }
-template <int P, int DIM, int LC> constexpr int rows_warp_elems() {
-  constexpr int NB = 2 * P + 1, LM = LC ? LC : P * (P + 1), NY = DIM == 3 ? NB * NB : NB;
-  return DIM * 4 * LM * nb_pad<P>() + (DIM == 3 ? LM * LM * NB : 0) + LM * NY + NY * NB;
+
+// Row classes of the row kernel: 0 interior (p+1 points in every
+// direction); 1, 2, 3: a face row, direction 0, 1 or 2 on Gauss-Legendre and
+// the others interior; 4: the rest (two or more directions on
+// Gauss-Legendre).  Points per row in direction d: p+1 where the class fixes
+// it, else read from the tables (at most p(p+1)).
+constexpr int kClsInt = 0, kClsRest = 4;
+template <int P, int CLS> constexpr int cls_l(int d) { return CLS == kClsRest ? 0 : (CLS == 1 + d ? 0 : P + 1); }
+template <int P, int CLS> constexpr int cls_lm(int d) { return cls_l<P, CLS>(d) ? P + 1 : P * (P + 1); }
+
+// Per-warp shared memory of the row kernel (elements of R): the weight-test
+// tables [d][4][LM_d][NBP] (rows padded to NBP), X [LM_0][LM_1][NB] (3D),
+// Y [LM_0][NB^(DIM-1)] and the band row being written [NB^DIM].
+template <int P, int DIM, int CLS> constexpr int rows_warp_elems() {
+  constexpr int NB = 2 * P + 1, NY = DIM == 3 ? NB * NB : NB;
+  constexpr int L0 = cls_lm<P, CLS>(0), L1 = cls_lm<P, CLS>(1), L2 = DIM == 3 ? cls_lm<P, CLS>(2) : 0;
+  return 4 * (L0 + L1 + L2) * nb_pad<P>() + (DIM == 3 ? L0 * L1 * NB : 0) + L0 * NY + NY * NB;
 }
 
-// One row per warp.  LC = P+1: the interior rows (every direction on its
-// weighted rule, p+1 points), taken from the interior box of the slab with
-// compile-time loop bounds; LC = 0: the other rows of the range (at least
-// one direction on Gauss-Legendre), the interior ones skipped.  Each lane
-// owns a run of outputs of every contraction (a row of NB columns, or half
-// of one), so the weight-test row of the contracted point is read once for
-// them all: X[q1][q2][.] = sum_q3 F[q1,q2,q3] A3[q3][.], then Y[q1][.][s3] +=
-// sum_q2 X[q1][q2][s3] A2[q2][.] over the terms of one direction-1 kind,
-// then band[.][s23] += sum_q1 Y[q1][s23] A1[q1][.]; the band row is staged
-// in shared memory and written with consecutive lanes on consecutive entries.
-template <int P, int DIM, int LC, int WARPS, typename R>
+// Rows of class CLS in the slab's planes (2D: lines) [bp_lo, bp_hi], item
+// idx of a gap-free enumeration; false past the end.  With the slab
+// direction's interior planes I = [max(bp_lo, p), min(bp_hi, N_s - 1)] and
+// the others B (those below p, then those from max(p, N_s) on), and in the
+// earlier directions the interior rows p .. N-1 (b of them) and the rest
+// (k -> k < p ? k : k + b):
+//   3D  interior: I x I1 x I2;  face 0: I x B1 x I2;  face 1: I x I1 x B2;
+//       face 2: B x I1 x I2;  rest: B x (rows with r1 or r2 outside), then
+//       I x B1 x B2;
+//   2D  interior: I x I1;  face 0: I x B1;  face 1: B x I1;  rest: B x B1.
+template <int P, int DIM, int CLS>
+__device__ __forceinline__ bool class_row(const GmArgs &A, long long j, int (&r)[3]) {
+  constexpr int SD = DIM - 1;
+  const int n1 = A.n[0], b1 = max(0, A.N[0] - P), o1 = n1 - b1;
+  const int n2 = A.n[1], b2 = DIM == 3 ? max(0, A.N[1] - P) : 0, o2 = n2 - b2;
+  const int pl0 = A.bp_lo, pl1 = A.bp_hi, Ns = A.N[SD];
+  const int nA = max(0, min(pl1, P - 1) - pl0 + 1);
+  const int bLo = max(pl0, P), nI = max(0, min(pl1, Ns - 1) - bLo + 1);
+  const int cLo = max(pl0, max(P, Ns)), nC = max(0, pl1 - cLo + 1);
+  auto bplane = [&](long long k) { return (int)(k < nA ? pl0 + k : cLo + (k - nA)); };
+  auto outer = [&](int k, int b) { return k < P ? k : k + b; };
+  r[0] = r[1] = r[2] = 0;
+  if constexpr (DIM == 3) {
+    if (CLS == kClsInt) {
+      const long long per = (long long)b1 * b2;
+      if (j >= per * nI) return false;
+      r[0] = P + (int)(j % b1);
+      r[1] = P + (int)((j / b1) % b2);
+      r[2] = bLo + (int)(j / per);
+    } else if (CLS == 1) {
+      const long long per = (long long)o1 * b2;
+      if (j >= per * nI) return false;
+      r[0] = outer((int)(j % o1), b1);
+      r[1] = P + (int)((j / o1) % b2);
+      r[2] = bLo + (int)(j / per);
+    } else if (CLS == 2) {
+      const long long per = (long long)b1 * o2;
+      if (j >= per * nI) return false;
+      r[0] = P + (int)(j % b1);
+      r[1] = outer((int)((j / b1) % o2), b2);
+      r[2] = bLo + (int)(j / per);
+    } else if (CLS == 3) {
+      const long long per = (long long)b1 * b2;
+      if (j >= per * (nA + nC)) return false;
+      r[0] = P + (int)(j % b1);
+      r[1] = P + (int)((j / b1) % b2);
+      r[2] = bplane(j / per);
+    } else {
+      const long long part = (long long)o2 * n1 + (long long)b2 * o1;
+      if (j < part * (nA + nC)) {
+        r[2] = bplane(j / part);
+        long long k = j % part;
+        if (k < (long long)o2 * n1) {
+          r[1] = outer((int)(k / n1), b2);
+          r[0] = (int)(k % n1);
+        } else {
+          k -= (long long)o2 * n1;
+          r[1] = P + (int)(k / o1);
+          r[0] = outer((int)(k % o1), b1);
+        }
+      } else {
+        j -= part * (nA + nC);
+        const long long per = (long long)o1 * o2;
+        if (j >= per * nI) return false;
+        r[0] = outer((int)(j % o1), b1);
+        r[1] = outer((int)((j / o1) % o2), b2);
+        r[2] = bLo + (int)(j / per);
+      }
+    }
+  } else {
+    if (CLS == kClsInt) {
+      if (j >= (long long)b1 * nI) return false;
+      r[0] = P + (int)(j % b1);
+      r[1] = bLo + (int)(j / b1);
+    } else if (CLS == 1) {
+      if (j >= (long long)o1 * nI) return false;
+      r[0] = outer((int)(j % o1), b1);
+      r[1] = bLo + (int)(j / o1);
+    } else if (CLS == 2) {
+      if (j >= (long long)b1 * (nA + nC)) return false;
+      r[0] = P + (int)(j % b1);
+      r[1] = bplane(j / b1);
+    } else {
+      if (j >= (long long)o1 * (nA + nC)) return false;
+      r[0] = outer((int)(j % o1), b1);
+      r[1] = bplane(j / o1);
+    }
+  }
+  return true;
+}
+
+// Rows of each class in the slab (host; the counts class_row enumerates).
+inline void class_counts(int dim, int P, const int *n, const int *N, int pl0, int pl1, long long cnt[5]) {
+  const long long n1 = n[0], b1 = std::max(0, N[0] - P), o1 = n1 - b1;
+  const long long n2 = n[1], b2 = dim == 3 ? std::max(0, N[1] - P) : 0, o2 = n2 - b2;
+  const int Ns = N[dim - 1];
+  const long long nA = std::max(0, std::min(pl1, P - 1) - pl0 + 1);
+  const int bLo = std::max(pl0, P);
+  const long long nI = std::max(0, std::min(pl1, Ns - 1) - bLo + 1);
+  const int cLo = std::max(pl0, std::max(P, Ns));
+  const long long nB = nA + std::max(0, pl1 - cLo + 1);
+  for (int c = 0; c < 5; c++) cnt[c] = 0;
+  if (dim == 3) {
+    cnt[0] = b1 * b2 * nI;
+    cnt[1] = o1 * b2 * nI;
+    cnt[2] = b1 * o2 * nI;
+    cnt[3] = b1 * b2 * nB;
+    cnt[4] = (o2 * n1 + b2 * o1) * nB + o1 * o2 * nI;
+  } else {
+    cnt[0] = b1 * nI;
+    cnt[1] = o1 * nI;
+    cnt[2] = b1 * nB;
+    cnt[4] = o1 * nB;
+  }
+}
+
+// One row per warp, rows of class CLS (compile-time point counts where the
+// class fixes them).  Each lane owns a run of outputs of every contraction
+// (a row of NB columns, or half of one), so the weight-test row of the
+// contracted point is read once for them all: X[q1][q2][.] = sum_q3
+// F[q1,q2,q3] A3[q3][.], then Y[q1][.][s3] += sum_q2 X[q1][q2][s3] A2[q2][.]
+// over the terms of one direction-1 kind, then band[.][s23] += sum_q1
+// Y[q1][s23] A1[q1][.]; the band row is staged in shared memory and written
+// with consecutive lanes on consecutive entries.
+template <int P, int DIM, int CLS, int WARPS, typename R>
 __global__ void __launch_bounds__(32 * WARPS) gm_rows_kernel(const GmArgs A) {
-  constexpr int NB = 2 * P + 1, NP = P + 1, NBP = nb_pad<P>(), LM = LC ? LC : P * (P + 1);
+  constexpr int NB = 2 * P + 1, NP = P + 1, NBP = nb_pad<P>();
+  constexpr int LC0 = cls_l<P, CLS>(0), LC1 = cls_l<P, CLS>(1), LC2 = DIM == 3 ? cls_l<P, CLS>(2) : 1;
+  constexpr int LM0 = cls_lm<P, CLS>(0), LM1 = cls_lm<P, CLS>(1), LM2 = DIM == 3 ? cls_lm<P, CLS>(2) : 0;
   constexpr int NY = DIM == 3 ? NB * NB : NB;  // columns of Y (s2, s3)
   constexpr int NBAND = NY * NB;
   constexpr int NK = (NY + 31) / 32;  // band columns s23 per lane
   constexpr int H1 = (NB + 1) / 2;    // the first half of the x3 columns
-  constexpr int UR = LC ? 64 : 1;     // unroll the row loops only where their bounds are compile-time
+  // unroll a row loop only where its bound is compile-time
+  constexpr int U0 = LC0 ? 64 : 1, U1 = LC1 ? 64 : 1, U2 = LC2 ? 64 : 1, U01 = (LC0 && LC1) ? 64 : 1;
   extern __shared__ __align__(16) unsigned char smrows[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  R *sA = reinterpret_cast<R *>(smrows) + warp * rows_warp_elems<P, DIM, LC>();  // [d][k][q][NBP]
-  R *sX = sA + DIM * 4 * LM * NBP;
-  R *sY = sX + (DIM == 3 ? LM * LM * NB : 0);
-  R *sO = sY + LM * NY;
-  const long long idx = (long long)blockIdx.x * WARPS + warp;
-  int r[3] = {0, 0, 0};
-  long long row;
-  if (LC) {
-    const int b1 = A.N[0] - P, b2 = DIM == 3 ? A.N[1] - P : A.ib_n;
-    if (idx >= (long long)b1 * b2 * (DIM == 3 ? A.ib_n : 1)) return;
-    r[0] = P + (int)(idx % b1);
-    if (DIM == 3) {
-      r[1] = P + (int)((idx / b1) % b2);
-      r[2] = A.ib_lo + (int)(idx / ((long long)b1 * b2));
-    } else {
-      r[1] = A.ib_lo + (int)(idx / b1);
-    }
-    row = r[0] + (long long)A.n[0] * (r[1] + (long long)A.n[1] * r[2]);
-    if (row < A.row_begin || row >= A.row_end) return;
-  } else {
-    // the slab's other rows, enumerated without gaps: the planes (2D:
-    // lines) of the slab direction outside the interior range in full, and
-    // in the interior ones the rows with an earlier direction outside its
-    // interior range (lines with r2 outside it first, then r1 outside it)
-    constexpr int SD = DIM - 1;
-    const int n1 = A.n[0], b1 = max(0, A.N[0] - P);
-    const long long full = DIM == 3 ? (long long)n1 * A.n[1] : n1;
-    const int b2 = DIM == 3 ? max(0, A.N[1] - P) : 0;
-    const long long part = DIM == 3 ? (long long)(A.n[1] - b2) * n1 + (long long)b2 * (n1 - b1) : n1 - b1;
-    const int pl0 = A.bp_lo, pl1 = A.bp_hi, Ns = A.N[SD];
-    const int nA = max(0, min(pl1, P - 1) - pl0 + 1);
-    const int bLo = max(pl0, P), bHi = min(pl1, Ns - 1), nB = max(0, bHi - bLo + 1);
-    const int cLo = max(pl0, max(P, Ns));
-    long long j = idx;
-    int plane;
-    bool whole;
-    if (j < nA * full) {
-      plane = pl0 + (int)(j / full);
-      j %= full;
-      whole = true;
-    } else if ((j -= nA * full) < nB * part) {
-      plane = bLo + (int)(j / part);
-      j %= part;
-      whole = false;
-    } else {
-      j -= nB * part;
-      plane = cLo + (int)(j / full);
-      if (plane > pl1) return;
-      j %= full;
-      whole = true;
-    }
-    r[SD] = plane;
-    if (whole) {
-      r[0] = (int)(j % n1);
-      if (DIM == 3) r[1] = (int)(j / n1);
-    } else if (DIM == 3) {
-      const long long lines_out = (long long)(A.n[1] - b2) * n1;
-      if (j < lines_out) {
-        const int m = (int)(j / n1);
-        r[1] = m < P ? m : m + b2;
-        r[0] = (int)(j % n1);
-      } else {
-        j -= lines_out;
-        r[1] = P + (int)(j / (n1 - b1));
-        const int k = (int)(j % (n1 - b1));
-        r[0] = k < P ? k : k + b1;
-      }
-    } else {
-      const int k = (int)j;
-      r[0] = k < P ? k : k + b1;
-    }
-    row = r[0] + (long long)n1 * (r[1] + (long long)A.n[1] * r[2]);
-    if (row < A.row_begin || row >= A.row_end) return;
-  }
+  R *sA = reinterpret_cast<R *>(smrows) + warp * rows_warp_elems<P, DIM, CLS>();  // [d][k][q][NBP]
+  R *sX = sA + 4 * (LM0 + LM1 + LM2) * NBP;
+  R *sY = sX + (DIM == 3 ? LM0 * LM1 * NB : 0);
+  R *sO = sY + LM0 * NY;
+  const int aoff[3] = {0, 4 * LM0 * NBP, 4 * (LM0 + LM1) * NBP};
+  const int lmd[3] = {LM0, LM1, LM2};
+  int r[3];
+  if (!class_row<P, DIM, CLS>(A, (long long)blockIdx.x * WARPS + warp, r)) return;
+  const long long row = r[0] + (long long)A.n[0] * (r[1] + (long long)A.n[1] * r[2]);
+  if (row < A.row_begin || row >= A.row_end) return;
   int off[3], L[3];
+  const int lc[3] = {LC0, LC1, LC2};
 #pragma unroll
   for (int d = 0; d < DIM; d++) {
     off[d] = A.off[d][r[d]];
-    L[d] = LC ? LC : A.off[d][r[d] + 1] - off[d];
+    L[d] = lc[d] ? lc[d] : A.off[d][r[d] + 1] - off[d];
   }
+  if (DIM == 2) L[2] = 1;
   // weight-test tables: A_d^k[q][j] = W(q) T(q, j - o), o = elem(q) - r + P
 #pragma unroll
   for (int d = 0; d < DIM; d++) {
     const int *elem = A.tab[d][0].elem;
-#pragma unroll UR
     for (int t = lane; t < 4 * L[d]; t += 32) {
       const int k = t / L[d], q = t - k * L[d];
       const int o = elem[off[d] + q] - r[d] + P;
@@ -922,7 +989,7 @@ __global__ void __launch_bounds__(32 * WARPS) gm_rows_kernel(const GmArgs A) {
       R v[NP];
 #pragma unroll
       for (int i = 0; i < NP; i++) v[i] = wt[i];
-      R *rowp = sA + ((d * 4 + k) * LM + q) * NBP;
+      R *rowp = sA + aoff[d] + (k * lmd[d] + q) * NBP;
 #pragma unroll
       for (int j = 0; j < NBP; j++) {
         R x = 0;
@@ -950,7 +1017,7 @@ __global__ void __launch_bounds__(32 * WARPS) gm_rows_kernel(const GmArgs A) {
     return;
   for (int grp = 0; grp < 5; grp++) {
     if (grp == 0 ? !A.M : !A.K) continue;
-#pragma unroll UR
+#pragma unroll U0
     for (int t = lane; t < L[0] * NY; t += 32) sY[t] = 0;
     __syncwarp();
     int k1 = 0;
@@ -958,12 +1025,12 @@ __global__ void __launch_bounds__(32 * WARPS) gm_rows_kernel(const GmArgs A) {
       const GmTerm &tm = terms[ti];
       k1 = tm.k[0];
       const R *F = static_cast<const R *>(A.F) + tm.grid * A.fstride;
-      const R *A2 = sA + ((1 * 4 + tm.k[1]) * LM) * NBP;
+      const R *A2 = sA + aoff[1] + (tm.k[1] * LM1) * NBP;
       if (DIM == 3) {
-        const R *A3 = sA + ((2 * 4 + tm.k[2]) * LM) * NBP;
+        const R *A3 = sA + aoff[2] + (tm.k[2] * LM2) * NBP;
         const R *F0 = F + off[0] + s2 * off[1] + s3 * (off[2] - A.slab_lo);
         // X: items (q1, q2, half of the x3 columns)
-#pragma unroll UR
+#pragma unroll U01
         for (int it = lane; it < 2 * L[0] * L[1]; it += 32) {
           const int pr = it >> 1, c0 = (it & 1) * H1;
           const int q1 = pr % L[0], q2 = pr / L[0];
@@ -971,7 +1038,7 @@ __global__ void __launch_bounds__(32 * WARPS) gm_rows_kernel(const GmArgs A) {
           R acc[H1];
 #pragma unroll
           for (int h = 0; h < H1; h++) acc[h] = 0;
-#pragma unroll UR
+#pragma unroll U2
           for (int q3 = 0; q3 < L[2]; q3++) {
             const R fv = f[s3 * q3];
             const R *a = A3 + q3 * NBP + c0;
@@ -985,13 +1052,13 @@ __global__ void __launch_bounds__(32 * WARPS) gm_rows_kernel(const GmArgs A) {
         }
         __syncwarp();
         // Y: items (q1, s3), all x2 columns
-#pragma unroll UR
+#pragma unroll U0
         for (int it = lane; it < L[0] * NB; it += 32) {
           const int q1 = it % L[0], c3 = it / L[0];
           R acc[NB];
 #pragma unroll
           for (int c = 0; c < NB; c++) acc[c] = 0;
-#pragma unroll UR
+#pragma unroll U1
           for (int q2 = 0; q2 < L[1]; q2++) {
             const R xv = sX[(q1 + L[0] * q2) * NB + c3];
             const R *a = A2 + q2 * NBP;
@@ -1006,12 +1073,12 @@ __global__ void __launch_bounds__(32 * WARPS) gm_rows_kernel(const GmArgs A) {
       } else {
         const R *F0 = F + off[0] + s2 * (off[1] - A.slab_lo);
         // Y: items q1, all x2 columns
-#pragma unroll UR
+#pragma unroll U0
         for (int it = lane; it < L[0]; it += 32) {
           R acc[NB];
 #pragma unroll
           for (int c = 0; c < NB; c++) acc[c] = 0;
-#pragma unroll UR
+#pragma unroll U1
           for (int q2 = 0; q2 < L[1]; q2++) {
             const R fv = F0[it + s2 * q2];
             const R *a = A2 + q2 * NBP;
@@ -1026,7 +1093,7 @@ __global__ void __launch_bounds__(32 * WARPS) gm_rows_kernel(const GmArgs A) {
       }
     }
     // band: items s23, all x1 columns
-    const R *A1 = sA + ((0 * 4 + k1) * LM) * NBP;
+    const R *A1 = sA + aoff[0] + (k1 * LM0) * NBP;
 #pragma unroll
     for (int c = 0; c < NK; c++) {
       const int s23 = lane + 32 * c;
@@ -1034,7 +1101,7 @@ __global__ void __launch_bounds__(32 * WARPS) gm_rows_kernel(const GmArgs A) {
         R acc[NB];
 #pragma unroll
         for (int s = 0; s < NB; s++) acc[s] = 0;
-#pragma unroll UR
+#pragma unroll U0
         for (int q1 = 0; q1 < L[0]; q1++) {
           const R yv = sY[q1 * NY + s23];
           const R *a = A1 + q1 * NBP;
@@ -1073,8 +1140,16 @@ __global__ void __launch_bounds__(32 * WARPS) gm_rows_kernel(const GmArgs A) {
 
 constexpr int kGmWarpsInt = 8;  // rows (warps) per CTA of the interior-row kernel
 
+template <int P, int DIM, int CLS, typename R> wq_status launch_rows_class(const GmArgs &a, long long n, cudaStream_t s) {
+  if (n <= 0) return WQ_OK;
+  constexpr int W = CLS == kClsInt ? kGmWarpsInt : kGmWarps;
+  const size_t smem = sizeof(R) * (size_t)rows_warp_elems<P, DIM, CLS>() * W;
+  gm_rows_kernel<P, DIM, CLS, W, R><<<(unsigned)((n + W - 1) / W), 32 * W, smem, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? WQ_OK : WQ_ERR_CUDA;
+}
+
 template <int P, int DIM, typename R>
-wq_status launch_slab(const GmArgs &a, long long nitems, long long nrows, long long nint, cudaStream_t s) {
+wq_status launch_slab(const GmArgs &a, long long nitems, const long long *ncls, cudaStream_t s) {
   constexpr bool F32 = std::is_same<R, float>::value;
   if (nitems > 0) {
     if (DIM == 3) {
@@ -1090,19 +1165,18 @@ wq_status launch_slab(const GmArgs &a, long long nitems, long long nrows, long l
     }
     if (cudaGetLastError() != cudaSuccess) return WQ_ERR_CUDA;
   }
-  if (nint > 0) {
-    const size_t smem = sizeof(R) * (size_t)rows_warp_elems<P, DIM, P + 1>() * kGmWarpsInt;
-    gm_rows_kernel<P, DIM, P + 1, kGmWarpsInt, R>
-        <<<(unsigned)((nint + kGmWarpsInt - 1) / kGmWarpsInt), 32 * kGmWarpsInt, smem, s>>>(a);
-    if (cudaGetLastError() != cudaSuccess) return WQ_ERR_CUDA;
-  }
-  if (nrows > 0) {
-    const size_t smem = sizeof(R) * (size_t)rows_warp_elems<P, DIM, 0>() * kGmWarps;
-    gm_rows_kernel<P, DIM, 0, kGmWarps, R>
-        <<<(unsigned)((nrows + kGmWarps - 1) / kGmWarps), 32 * kGmWarps, smem, s>>>(a);
-    if (cudaGetLastError() != cudaSuccess) return WQ_ERR_CUDA;
-  }
-  return WQ_OK;
+  wq_status st = launch_rows_class<P, DIM, 0, R>(a, ncls[0], s);
+  if (st == WQ_OK) st = launch_rows_class<P, DIM, 1, R>(a, ncls[1], s);
+  if (st == WQ_OK) st = launch_rows_class<P, DIM, 2, R>(a, ncls[2], s);
+  if (st == WQ_OK && DIM == 3) st = launch_rows_class<P, DIM, 3, R>(a, ncls[3], s);
+  if (st == WQ_OK) st = launch_rows_class<P, DIM, kClsRest, R>(a, ncls[4], s);
+  return st;
+}
+
+template <int P, int DIM, int CLS, typename R> cudaError_t set_rows_limit() {
+  constexpr int W = CLS == kClsInt ? kGmWarpsInt : kGmWarps;
+  return cudaFuncSetAttribute(gm_rows_kernel<P, DIM, CLS, W, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(sizeof(R) * rows_warp_elems<P, DIM, CLS>() * W));
 }
 
 template <int P, int DIM, typename R> cudaError_t set_smem_limits() {
@@ -1113,13 +1187,11 @@ template <int P, int DIM, typename R> cudaError_t set_smem_limits() {
                                    (int)(sizeof(float) * metric3f_smem_floats<P>()))
             : cudaFuncSetAttribute(gm_metric3_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)(sizeof(double) * metric3_smem_doubles<P>()));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(gm_rows_kernel<P, DIM, 0, kGmWarps, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(R) * rows_warp_elems<P, DIM, 0>() * kGmWarps));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(gm_rows_kernel<P, DIM, P + 1, kGmWarpsInt, R>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(R) * rows_warp_elems<P, DIM, P + 1>() * kGmWarpsInt));
+  if (e == cudaSuccess) e = set_rows_limit<P, DIM, 0, R>();
+  if (e == cudaSuccess) e = set_rows_limit<P, DIM, 1, R>();
+  if (e == cudaSuccess) e = set_rows_limit<P, DIM, 2, R>();
+  if (e == cudaSuccess && DIM == 3) e = set_rows_limit<P, DIM, 3, R>();
+  if (e == cudaSuccess) e = set_rows_limit<P, DIM, kClsRest, R>();
   return e;
 }
 
@@ -1129,12 +1201,9 @@ template <typename R> cudaError_t set_limits(int p, int dim) {
 }
 
 template <typename R>
-wq_status launch_any(int p, int dim, const GmArgs &a, long long nitems, long long nrows, long long nint,
-                     cudaStream_t s) {
-  return p == 2 ? (dim == 3 ? launch_slab<2, 3, R>(a, nitems, nrows, nint, s)
-                            : launch_slab<2, 2, R>(a, nitems, nrows, nint, s))
-                : (dim == 3 ? launch_slab<3, 3, R>(a, nitems, nrows, nint, s)
-                            : launch_slab<3, 2, R>(a, nitems, nrows, nint, s));
+wq_status launch_any(int p, int dim, const GmArgs &a, long long nitems, const long long *ncls, cudaStream_t s) {
+  return p == 2 ? (dim == 3 ? launch_slab<2, 3, R>(a, nitems, ncls, s) : launch_slab<2, 2, R>(a, nitems, ncls, s))
+                : (dim == 3 ? launch_slab<3, 3, R>(a, nitems, ncls, s) : launch_slab<3, 2, R>(a, nitems, ncls, s));
 }
 
 // Scratch budget of one slab's factor arrays.
@@ -1266,27 +1335,12 @@ extern "C" wq_status wq_assemble_general(const wq_rules *R, const double *net, c
     const int r2b = f32 ? kGmRows32 : kGmRows64;
     const long long nitems = dim == 3 ? 6LL * a.slab_n * ((R->n[1] + r2b - 1) / r2b) * nch1 : 3LL * a.slab_n * nch1;
     if (nitems > 0x7fffffffLL) return WQ_ERR_UNSUPPORTED;
-    long long nr = 0;
-    // interior planes of the slab: rows p .. nel-1 of the slab direction;
-    // the other rows of the slab's planes, counted as the boundary kernel
-    // enumerates them
+    // the rows of each class in the slab's planes (the row kernels enumerate them)
     a.bp_lo = sl.first;
     a.bp_hi = sl.second;
-    {
-      const long long n1 = R->n[0], b1 = std::max(0, R->nel[0] - p);
-      const long long full = dim == 3 ? n1 * R->n[1] : n1;
-      const long long b2 = dim == 3 ? std::max(0, R->nel[1] - p) : 0;
-      const long long part = dim == 3 ? (R->n[1] - b2) * n1 + b2 * (n1 - b1) : n1 - b1;
-      long long nb = 0;
-      for (int r = sl.first; r <= sl.second; r++) nb += (r >= p && r <= R->nel[sd] - 1) ? part : full;
-      nr = nb;
-    }
-    a.ib_lo = std::max(sl.first, p);
-    a.ib_n = std::max(0, std::min(sl.second, R->nel[sd] - 1) - a.ib_lo + 1);
-    long long nint = (long long)std::max(0, R->nel[0] - p) * a.ib_n;
-    if (dim == 3) nint *= std::max(0, R->nel[1] - p);
-    wq_status st = f32 ? launch_any<float>(p, dim, a, nitems, nr, nint, s)
-                       : launch_any<double>(p, dim, a, nitems, nr, nint, s);
+    long long ncls[5];
+    class_counts(dim, p, R->n, R->nel, sl.first, sl.second, ncls);
+    wq_status st = f32 ? launch_any<float>(p, dim, a, nitems, ncls, s) : launch_any<double>(p, dim, a, nitems, ncls, s);
     if (st != WQ_OK) return st;
   }
   return WQ_OK;
