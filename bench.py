@@ -254,6 +254,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-patch batch variant")
+    ap.add_argument("--only", default=None,
+                    help="comma list of variant groups to run: precisions, workloads, rules, adjoint, apply, "
+                         "general, batch (default: all)")
     ap.add_argument("--cpu-stride", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -508,6 +511,8 @@ def run_variants(args, wq, inputs, R, w, g, gd, cd, bands, sample, timed, stream
     hbm = peaks.get("hbm_gbs", 6800.0)
     variants = {}
     reps = max(3, min(args.steps, 10))
+    groups = None if args.only is None else set(args.only.split(","))
+    want = lambda k: groups is None or k in groups  # noqa: E731
 
     def assemble_timed(Rv, gdv, cdv, prec, out, n):
         fn = lambda: wq.assemble(Rv, gdv, cdv, prec, out=out, stream=stream, check=False)  # noqa: E731
@@ -530,229 +535,247 @@ def run_variants(args, wq, inputs, R, w, g, gd, cd, bands, sample, timed, stream
         return {"bound": "alu", "achieved": tf, "peak": pk, "unit": "TFLOP/s", "frac": tf / pk}
 
     # the other precisions of the headline workload, errors on the oracle's rows
-    for vp in ("fp64", "df64", "mixed"):
-        if vp == args.prec:
-            continue
-        vdt = torch.float32 if vp == "mixed" else torch.float64
-        if vdt == bands[0].dtype:
-            Mv, Kv = bands  # the headline's errors are already taken: reuse its buffers
-        else:
-            Mv = torch.empty((R.rows, R.band), dtype=vdt, device="cuda")
-            Kv = torch.empty((R.rows, R.band), dtype=vdt, device="cuda")
-        vm = assemble_timed(R, gd, cd, vp, (Mv, Kv), reps)
-        ev = {"ms_per_step": vm, "value": 2 * R.nnz / (vm * 1e-3), "unit": "nnz/s", "dtype": DTYPE[vp],
-              "roofline": roofline(R, vp, vm, 2 * R.rows * R.band * Mv.element_size())}
-        if sample:
-            ev["error_vs_oracle"] = errors_vs_oracle((Mv, Kv), sample)
-        variants[vp] = ev
-        del Mv, Kv
-    torch.cuda.empty_cache()
+    if want("precisions"):
+        for vp in ("fp64", "df64", "mixed"):
+            if vp == args.prec:
+                continue
+            vdt = torch.float32 if vp == "mixed" else torch.float64
+            if vdt == bands[0].dtype:
+                Mv, Kv = bands  # the headline's errors are already taken: reuse its buffers
+            else:
+                Mv = torch.empty((R.rows, R.band), dtype=vdt, device="cuda")
+                Kv = torch.empty((R.rows, R.band), dtype=vdt, device="cuda")
+            vm = assemble_timed(R, gd, cd, vp, (Mv, Kv), reps)
+            ev = {"ms_per_step": vm, "value": 2 * R.nnz / (vm * 1e-3), "unit": "nnz/s", "dtype": DTYPE[vp],
+                  "roofline": roofline(R, vp, vm, 2 * R.rows * R.band * Mv.element_size())}
+            if sample:
+                ev["error_vs_oracle"] = errors_vs_oracle((Mv, Kv), sample)
+            variants[vp] = ev
+            del Mv, Kv
+        torch.cuda.empty_cache()
 
     # the other workloads: 64^3 cubic and quadratic, 2D 32^2 cubic (c as
     # named, and c = 1), every precision, errors on oracle rows
-    others = [("3d_p3_64", 16), ("3d_p2_64", 16), ("2d_p3_32", 1), ("2d_p3_32_c1", 1)]
-    for name, stride in others:
-        if name == args.workload:
-            continue
-        wv, gv, cv = inputs.workload(name)
-        Rv = wq.Rules(wv["dim"], wv["p"], wv["nel"])
-        gdv = [torch.from_numpy(x).cuda() for x in gv]
-        cdv = torch.from_numpy(cv).cuda()
-        _, _, _, outs = run_oracle_sample(wv, gv, cv, stride)
-        ent = {"workload": name, "nel": list(wv["nel"]), "degree": wv["p"], "rows": int(Rv.rows),
-               "nnz_per_matrix": int(Rv.nnz),
-               "oracle_rows": int(sum(o[1] - o[0] for o in outs))}
-        for vp in ("fp64", "df64", "mixed"):
-            vdt = torch.float32 if vp == "mixed" else torch.float64
-            Mv = torch.empty((Rv.rows, Rv.band), dtype=vdt, device="cuda")
-            Kv = torch.empty((Rv.rows, Rv.band), dtype=vdt, device="cuda")
-            vm = assemble_timed(Rv, gdv, cdv, vp, (Mv, Kv), reps)
-            ent[vp] = {"ms_per_step": vm, "value": 2 * Rv.nnz / (vm * 1e-3), "unit": "nnz/s",
-                       "roofline": roofline(Rv, vp, vm, 2 * Rv.rows * Rv.band * Mv.element_size()),
-                       "error_vs_oracle": errors_vs_oracle((Mv, Kv), outs)}
-            del Mv, Kv
-        variants[name] = ent
-        Rv.close()
-    torch.cuda.empty_cache()
+    if want("workloads"):
+        others = [("3d_p3_64", 16), ("3d_p2_64", 16), ("2d_p3_32", 1), ("2d_p3_32_c1", 1)]
+        for name, stride in others:
+            if name == args.workload:
+                continue
+            wv, gv, cv = inputs.workload(name)
+            Rv = wq.Rules(wv["dim"], wv["p"], wv["nel"])
+            gdv = [torch.from_numpy(x).cuda() for x in gv]
+            cdv = torch.from_numpy(cv).cuda()
+            _, _, _, outs = run_oracle_sample(wv, gv, cv, stride)
+            ent = {"workload": name, "nel": list(wv["nel"]), "degree": wv["p"], "rows": int(Rv.rows),
+                   "nnz_per_matrix": int(Rv.nnz),
+                   "oracle_rows": int(sum(o[1] - o[0] for o in outs))}
+            for vp in ("fp64", "df64", "mixed"):
+                vdt = torch.float32 if vp == "mixed" else torch.float64
+                Mv = torch.empty((Rv.rows, Rv.band), dtype=vdt, device="cuda")
+                Kv = torch.empty((Rv.rows, Rv.band), dtype=vdt, device="cuda")
+                vm = assemble_timed(Rv, gdv, cdv, vp, (Mv, Kv), reps)
+                ent[vp] = {"ms_per_step": vm, "value": 2 * Rv.nnz / (vm * 1e-3), "unit": "nnz/s",
+                           "roofline": roofline(Rv, vp, vm, 2 * Rv.rows * Rv.band * Mv.element_size()),
+                           "error_vs_oracle": errors_vs_oracle((Mv, Kv), outs)}
+                del Mv, Kv
+            variants[name] = ent
+            Rv.close()
+        torch.cuda.empty_cache()
 
     # the comparison rules (FP64, same kernel's general-points class) on the
     # 64^3 cubic workload: Gauss-Legendre on every element of each row's
     # support, and the Newton-Cotes-type weighted rules; and the weighted
     # Gaussian rules with the boundary rows on their own weighted rules
     # ('wqb', the default kernels); with the quadrature-point counts
-    wc, gc, cc = inputs.workload("3d_p3_64")
-    gdc = [torch.from_numpy(x).cuda() for x in gc]
-    cdc = torch.from_numpy(cc).cuda()
-    points = {}
-    Mv = Kv = None
-    for mode in ("wq", "wqb", "nc", "gl"):
-        Rm = wq.Rules(3, wc["p"], wc["nel"], rule=mode)
-        total = 1
-        for a in range(3):
-            total *= sum(len(Rm.row(a, 0, r)[0]) for r in range(wc["nel"][a] + wc["p"]))
-        points[mode] = {"points_per_interior_row_and_direction": len(Rm.row(0, 0, wc["p"])[0]),
-                        "rule_points_total": total}
-        if Mv is None:
-            Mv = torch.empty((Rm.rows, Rm.band), dtype=torch.float64, device="cuda")
-            Kv = torch.empty((Rm.rows, Rm.band), dtype=torch.float64, device="cuda")
-        vm = assemble_timed(Rm, gdc, cdc, "fp64", (Mv, Kv), max(3, min(args.steps, 5)))
-        variants["3d_p3_64_fp64_" + mode + "_rule"] = {"ms_per_step": vm, "value": 2 * Rm.nnz / (vm * 1e-3),
-                                                        "unit": "nnz/s", "dtype": "f64", **points[mode]}
-        Rm.close()
-    variants["rule_points_3d_p3_64"] = points
-    del Mv, Kv
-    torch.cuda.empty_cache()
+    if want("rules") or want("apply"):
+        wc, gc, cc = inputs.workload("3d_p3_64")
+        gdc = [torch.from_numpy(x).cuda() for x in gc]
+        cdc = torch.from_numpy(cc).cuda()
+    if want("rules"):
+        points = {}
+        Mv = Kv = None
+        for mode in ("wq", "wqb", "nc", "gl"):
+            Rm = wq.Rules(3, wc["p"], wc["nel"], rule=mode)
+            total = 1
+            for a in range(3):
+                total *= sum(len(Rm.row(a, 0, r)[0]) for r in range(wc["nel"][a] + wc["p"]))
+            points[mode] = {"points_per_interior_row_and_direction": len(Rm.row(0, 0, wc["p"])[0]),
+                            "rule_points_total": total}
+            if Mv is None:
+                Mv = torch.empty((Rm.rows, Rm.band), dtype=torch.float64, device="cuda")
+                Kv = torch.empty((Rm.rows, Rm.band), dtype=torch.float64, device="cuda")
+            vm = assemble_timed(Rm, gdc, cdc, "fp64", (Mv, Kv), max(3, min(args.steps, 5)))
+            variants["3d_p3_64_fp64_" + mode + "_rule"] = {"ms_per_step": vm, "value": 2 * Rm.nnz / (vm * 1e-3),
+                                                            "unit": "nnz/s", "dtype": "f64", **points[mode]}
+            Rm.close()
+        variants["rule_points_3d_p3_64"] = points
+        del Mv, Kv
+        torch.cuda.empty_cache()
 
     # the adjoint (coefficient gradient of sum G*K + H*M) on the 96^3 cubic workload
-    w3, g3, c3 = inputs.workload("3d_p3_96")
-    R3 = wq.Rules(3, w3["p"], w3["nel"])
-    gd3 = [torch.from_numpy(x).cuda() for x in g3]
-    gen = torch.Generator(device="cuda").manual_seed(96)
-    adj = {"workload": "3d_p3_96", "ncoef": R3.ncoef}
-    for vp in ("fp64", "df64", "mixed"):
-        vdt = torch.float32 if vp == "mixed" else torch.float64
-        G = torch.randn((R3.rows, R3.band), dtype=vdt, device="cuda", generator=gen)
-        H = torch.randn((R3.rows, R3.band), dtype=vdt, device="cuda", generator=gen)
-        grad = torch.empty(R3.ncoef, dtype=torch.float64, device="cuda")
-        fn = lambda: wq.assemble_adjoint(R3, gd3, G, H, vp, out=grad, stream=stream, check=False)  # noqa: E731
-        for _ in range(3):
-            fn()
-        vm = float(np.mean(timed(fn, max(3, min(args.steps, 5)))))
-        fl, _ = R3.flops()
-        # per step the adjoint reads both weight bands (band entries per
-        # second); its transposed stages do the forward contraction's
-        # multiply-adds, counted as its algorithmic flops
-        pk = {"fp64": FP64_PEAK_TFLOPS, "df64": DF64_PEAK_TFLOPS, "mixed": FP32_PEAK_TFLOPS}[vp]
-        tf = fl / (vm * 1e-3) / 1e12
-        adj[vp] = {"ms_per_step": vm, "value": 2 * R3.nnz / (vm * 1e-3), "unit": "nnz/s (weights read)",
-                   "weights_gb_s": 2 * R3.rows * R3.band * G.element_size() / (vm * 1e-3) / 1e9,
-                   "roofline": {"bound": "alu", "achieved": tf, "peak": pk, "unit": "TFLOP/s", "frac": tf / pk,
-                                "flops_per_gradient": fl,
-                                "weight_bytes_per_gradient": 2 * R3.rows * R3.band * G.element_size()}}
-        del G, H, grad
-        torch.cuda.empty_cache()
-    st = wq.wq_status_check(R3.handle, wq._stream_handle(stream))
-    if st != wq.WQ_OK:
-        raise wq.WqError(st, "adjoint variant")
-    variants["adjoint_3d_p3_96"] = adj
-    R3.close()
+    if want("adjoint"):
+        w3, g3, c3 = inputs.workload("3d_p3_96")
+        R3 = wq.Rules(3, w3["p"], w3["nel"])
+        gd3 = [torch.from_numpy(x).cuda() for x in g3]
+        gen = torch.Generator(device="cuda").manual_seed(96)
+        adj = {"workload": "3d_p3_96", "ncoef": R3.ncoef}
+        for vp in ("fp64", "df64", "mixed"):
+            vdt = torch.float32 if vp == "mixed" else torch.float64
+            G = torch.randn((R3.rows, R3.band), dtype=vdt, device="cuda", generator=gen)
+            H = torch.randn((R3.rows, R3.band), dtype=vdt, device="cuda", generator=gen)
+            grad = torch.empty(R3.ncoef, dtype=torch.float64, device="cuda")
+            fn = lambda: wq.assemble_adjoint(R3, gd3, G, H, vp, out=grad, stream=stream, check=False)  # noqa: E731
+            for _ in range(3):
+                fn()
+            vm = float(np.mean(timed(fn, max(3, min(args.steps, 5)))))
+            fl, _ = R3.flops()
+            # per step the adjoint reads both weight bands (band entries per
+            # second); its transposed stages do the forward contraction's
+            # multiply-adds, counted as its algorithmic flops
+            pk = {"fp64": FP64_PEAK_TFLOPS, "df64": DF64_PEAK_TFLOPS, "mixed": FP32_PEAK_TFLOPS}[vp]
+            tf = fl / (vm * 1e-3) / 1e12
+            adj[vp] = {"ms_per_step": vm, "value": 2 * R3.nnz / (vm * 1e-3), "unit": "nnz/s (weights read)",
+                       "weights_gb_s": 2 * R3.rows * R3.band * G.element_size() / (vm * 1e-3) / 1e9,
+                       "roofline": {"bound": "alu", "achieved": tf, "peak": pk, "unit": "TFLOP/s", "frac": tf / pk,
+                                    "flops_per_gradient": fl,
+                                    "weight_bytes_per_gradient": 2 * R3.rows * R3.band * G.element_size()}}
+            del G, H, grad
+            torch.cuda.empty_cache()
+        st = wq.wq_status_check(R3.handle, wq._stream_handle(stream))
+        if st != wq.WQ_OK:
+            raise wq.WqError(st, "adjoint variant")
+        variants["adjoint_3d_p3_96"] = adj
+        R3.close()
 
     # matrix-free apply y = M x, y = K x (the band never stored) and the load
     # vector, on the 64^3 cubic workload
-    Ra = wq.Rules(3, wc["p"], wc["nel"])
-    gen = torch.Generator(device="cuda").manual_seed(64)
-    app = {"workload": "3d_p3_64", "nnz_per_step": 2 * Ra.nnz}
-    for vp in ("df64", "fp64", "mixed"):
-        vdt = torch.float32 if vp == "mixed" else torch.float64
-        xv = torch.randn(Ra.rows, dtype=torch.float64, device="cuda", generator=gen).to(vdt)
-        yM = torch.empty(Ra.rows, dtype=vdt, device="cuda")
-        yK = torch.empty(Ra.rows, dtype=vdt, device="cuda")
-        fn = lambda: wq.apply(Ra, gdc, xv, cdc, vp, out=(yM, yK), stream=stream, check=False)  # noqa: E731
-        for _ in range(3):
-            fn()
-        vm = float(np.mean(timed(fn, reps)))
-        # the contractions plus one multiply-add per band entry and matrix
-        fl_apply = Ra.flops()[0] + 2 * 2 * Ra.nnz
-        pk = {"fp64": FP64_PEAK_TFLOPS, "df64": DF64_PEAK_TFLOPS, "mixed": FP32_PEAK_TFLOPS}[vp]
-        tf = fl_apply / (vm * 1e-3) / 1e12
-        app[vp] = {"ms_per_step": vm, "value": 2 * Ra.nnz / (vm * 1e-3), "unit": "nnz/s (applied)",
-                   "roofline": {"bound": "alu", "achieved": tf, "peak": pk, "unit": "TFLOP/s", "frac": tf / pk}}
-        if vp == "df64":
-            bl = torch.empty(Ra.rows, dtype=vdt, device="cuda")
-            fl_ = lambda: wq.assemble_load(Ra, gdc, cdc, vp, out=bl, stream=stream, check=False)  # noqa: E731
+    if want("apply"):
+        Ra = wq.Rules(3, wc["p"], wc["nel"])
+        gen = torch.Generator(device="cuda").manual_seed(64)
+        app = {"workload": "3d_p3_64", "nnz_per_step": 2 * Ra.nnz}
+        for vp in ("df64", "fp64", "mixed"):
+            vdt = torch.float32 if vp == "mixed" else torch.float64
+            xv = torch.randn(Ra.rows, dtype=torch.float64, device="cuda", generator=gen).to(vdt)
+            yM = torch.empty(Ra.rows, dtype=vdt, device="cuda")
+            yK = torch.empty(Ra.rows, dtype=vdt, device="cuda")
+            fn = lambda: wq.apply(Ra, gdc, xv, cdc, vp, out=(yM, yK), stream=stream, check=False)  # noqa: E731
             for _ in range(3):
-                fl_()
-            app["load_vector_df64_ms"] = float(np.mean(timed(fl_, 5)))
-            del bl
-        del xv, yM, yK
-    sta = wq.wq_status_check(Ra.handle, wq._stream_handle(stream))
-    if sta != wq.WQ_OK:
-        raise wq.WqError(sta, "apply variant")
-    variants["apply_3d_p3_64"] = app
-    Ra.close()
+                fn()
+            vm = float(np.mean(timed(fn, reps)))
+            # the contractions plus one multiply-add per band entry and matrix
+            fl_apply = Ra.flops()[0] + 2 * 2 * Ra.nnz
+            pk = {"fp64": FP64_PEAK_TFLOPS, "df64": DF64_PEAK_TFLOPS, "mixed": FP32_PEAK_TFLOPS}[vp]
+            tf = fl_apply / (vm * 1e-3) / 1e12
+            app[vp] = {"ms_per_step": vm, "value": 2 * Ra.nnz / (vm * 1e-3), "unit": "nnz/s (applied)",
+                       "roofline": {"bound": "alu", "achieved": tf, "peak": pk, "unit": "TFLOP/s", "frac": tf / pk}}
+            if vp == "df64":
+                bl = torch.empty(Ra.rows, dtype=vdt, device="cuda")
+                fl_ = lambda: wq.assemble_load(Ra, gdc, cdc, vp, out=bl, stream=stream, check=False)  # noqa: E731
+                for _ in range(3):
+                    fl_()
+                app["load_vector_df64_ms"] = float(np.mean(timed(fl_, 5)))
+                del bl
+            del xv, yM, yK
+        sta = wq.wq_status_check(Ra.handle, wq._stream_handle(stream))
+        if sta != wq.WQ_OK:
+            raise wq.WqError(sta, "apply variant")
+        variants["apply_3d_p3_64"] = app
+        Ra.close()
 
     # maps given by a full control net (the off-diagonal metric terms with the
     # mixed-derivative rules): the warped 64^3 cubic workload, FP64 and FP32
     # (parity with the oracle is tested, not timed here)
-    gen_out = {}
-    for gname in ("3d_p3_64_warp",):
-        wn = inputs.NET_WORKLOADS[gname]
-        netn, cnn = inputs.make_net(wn["dim"], wn["p"], wn["nel"], wn["net"], wn["amp"], wn["coef"], wn["sigma"],
-                                    wn["seed"])
-        Rg = wq.Rules(wn["dim"], wn["p"], wn["nel"])
-        ndg, cdg = torch.from_numpy(netn).cuda(), torch.from_numpy(cnn).cuda()
-        rows_fl, met_fl, npts, b32 = general_counts(Rg, wn["dim"], wn["p"], wn["nel"], True)
-        ent = {"workload": gname, "nel": list(wn["nel"]), "degree": wn["p"], "rows": int(Rg.rows),
-               "nnz_per_matrix": int(Rg.nnz), "metric_points": npts, "flops_rows": rows_fl, "flops_metric": met_fl,
-               "fp32_algorithmic_bytes": b32}
-        for vp in ("fp64", "mixed"):
-            vdt = torch.float32 if vp == "mixed" else torch.float64
-            Mv = torch.empty((Rg.rows, Rg.band), dtype=vdt, device="cuda")
-            Kv = torch.empty((Rg.rows, Rg.band), dtype=vdt, device="cuda")
-            fn = lambda: wq.assemble_general(Rg, ndg, cdg, vp, out=(Mv, Kv), stream=stream,  # noqa: E731
-                                             check=False)
-            for _ in range(3):
-                fn()
-            vm = float(np.mean(timed(fn, max(3, min(args.steps, 5)))))
-            stg = wq.wq_status_check(Rg.handle, wq._stream_handle(stream))
-            if stg != wq.WQ_OK:
-                raise wq.WqError(stg, "general variant")
-            tf = (rows_fl + met_fl) / (vm * 1e-3) / 1e12
-            if vp == "fp64":
-                roof = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                        "frac": tf / FP64_PEAK_TFLOPS}
-            else:
-                bw = b32 / (vm * 1e-3) / 1e9
-                roof = {"bound": "hbm", "achieved": bw, "peak": hbm, "unit": "GB/s", "frac": bw / hbm,
-                        "fp32_tflops": tf, "fp32_frac": tf / FP32_PEAK_TFLOPS}
-            ent[vp] = {"ms_per_step": vm, "value": 2 * Rg.nnz / (vm * 1e-3), "unit": "nnz/s", "dtype": DTYPE[vp],
-                       "roofline": roof}
-            del Mv, Kv
-            torch.cuda.empty_cache()
-        gen_out[gname] = ent
-        Rg.close()
-    variants["general_map"] = gen_out
+    if want("general"):
+        gen_out = {}
+        for gname in ("3d_p3_64_warp",):
+            wn = inputs.NET_WORKLOADS[gname]
+            netn, cnn = inputs.make_net(wn["dim"], wn["p"], wn["nel"], wn["net"], wn["amp"], wn["coef"], wn["sigma"],
+                                        wn["seed"])
+            Rg = wq.Rules(wn["dim"], wn["p"], wn["nel"])
+            ndg, cdg = torch.from_numpy(netn).cuda(), torch.from_numpy(cnn).cuda()
+            rows_fl, met_fl, npts, b32 = general_counts(Rg, wn["dim"], wn["p"], wn["nel"], True)
+            ent = {"workload": gname, "nel": list(wn["nel"]), "degree": wn["p"], "rows": int(Rg.rows),
+                   "nnz_per_matrix": int(Rg.nnz), "metric_points": npts, "flops_rows": rows_fl, "flops_metric": met_fl,
+                   "fp32_algorithmic_bytes": b32}
+            for vp in ("fp64", "mixed"):
+                vdt = torch.float32 if vp == "mixed" else torch.float64
+                Mv = torch.empty((Rg.rows, Rg.band), dtype=vdt, device="cuda")
+                Kv = torch.empty((Rg.rows, Rg.band), dtype=vdt, device="cuda")
+                fn = lambda: wq.assemble_general(Rg, ndg, cdg, vp, out=(Mv, Kv), stream=stream,  # noqa: E731
+                                                 check=False)
+                for _ in range(3):
+                    fn()
+                vm = float(np.mean(timed(fn, max(3, min(args.steps, 5)))))
+                stg = wq.wq_status_check(Rg.handle, wq._stream_handle(stream))
+                if stg != wq.WQ_OK:
+                    raise wq.WqError(stg, "general variant")
+                tf = (rows_fl + met_fl) / (vm * 1e-3) / 1e12
+                if vp == "fp64":
+                    roof = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": tf / FP64_PEAK_TFLOPS}
+                else:
+                    bw = b32 / (vm * 1e-3) / 1e9
+                    roof = {"bound": "hbm", "achieved": bw, "peak": hbm, "unit": "GB/s", "frac": bw / hbm,
+                            "fp32_tflops": tf, "fp32_frac": tf / FP32_PEAK_TFLOPS}
+                ent[vp] = {"ms_per_step": vm, "value": 2 * Rg.nnz / (vm * 1e-3), "unit": "nnz/s", "dtype": DTYPE[vp],
+                           "roofline": roof}
+                del Mv, Kv
+                torch.cuda.empty_cache()
+            gen_out[gname] = ent
+            Rg.close()
+        variants["general_map"] = gen_out
 
     # the batch of 256 independent patches (8..48 elements per direction, p in {2, 3}):
     # one graph of two persistent launches, tuned, against one call per patch
-    if not args.no_batch:
-        specs = inputs.batch_patches(256, seed=0)
-        rules_cache, base = {}, []
-        for sp in specs:
-            key = (sp["p"], sp["nel"])
-            if key not in rules_cache:
-                rules_cache[key] = wq.Rules(3, sp["p"], sp["nel"])
-            base.append((rules_cache[key], [torch.from_numpy(x).cuda() for x in sp["geom"]],
-                         torch.from_numpy(sp["coef"]).cuda()))
-        bnnz = 2 * sum(Rb.nnz for Rb, _, _ in base)
-        bat = {"workload": "batch_256", "patches": 256, "nnz_per_step": bnnz}
-        for vp in ("fp64", "df64", "mixed"):
-            vdt = torch.float32 if vp == "mixed" else torch.float64
-            pts = [(Rb, gb, cb, torch.empty((Rb.rows, Rb.band), dtype=vdt, device="cuda"),
-                    torch.empty((Rb.rows, Rb.band), dtype=vdt, device="cuda")) for Rb, gb, cb in base]
-            Bp = wq.Batch(pts, vp)
-            Bp.tune(reps=1, stream=stream)
-            Bp.launch(stream)
-            tb = float(np.mean(timed(lambda: Bp.launch(stream), 5)))
-            stb = Bp.status(stream)
-            if stb != wq.WQ_OK:
-                raise wq.WqError(stb, "batch")
+    if want("batch"):
+        if not args.no_batch:
+            specs = inputs.batch_patches(256, seed=0)
+            rules_cache, base = {}, []
+            for sp in specs:
+                key = (sp["p"], sp["nel"])
+                if key not in rules_cache:
+                    rules_cache[key] = wq.Rules(3, sp["p"], sp["nel"])
+                base.append((rules_cache[key], [torch.from_numpy(x).cuda() for x in sp["geom"]],
+                             torch.from_numpy(sp["coef"]).cuda()))
+            bnnz = 2 * sum(Rb.nnz for Rb, _, _ in base)
+            bflops = sum(Rb.flops()[0] for Rb, _, _ in base)
+            bat = {"workload": "batch_256", "patches": 256, "nnz_per_step": bnnz, "flops_per_step": bflops}
+            for vp in ("fp64", "df64", "mixed"):
+                vdt = torch.float32 if vp == "mixed" else torch.float64
+                pts = [(Rb, gb, cb, torch.empty((Rb.rows, Rb.band), dtype=vdt, device="cuda"),
+                        torch.empty((Rb.rows, Rb.band), dtype=vdt, device="cuda")) for Rb, gb, cb in base]
+                Bp = wq.Batch(pts, vp)
+                Bp.tune(reps=1, stream=stream)
+                Bp.launch(stream)
+                tb = float(np.mean(timed(lambda: Bp.launch(stream), 5)))
+                stb = Bp.status(stream)
+                if stb != wq.WQ_OK:
+                    raise wq.WqError(stb, "batch")
 
-            def seq():
-                for Rb, gb, cb, Mb, Kb in pts:
-                    wq.assemble(Rb, gb, cb, vp, out=(Mb, Kb), stream=stream, check=False)
+                def seq():
+                    for Rb, gb, cb, Mb, Kb in pts:
+                        wq.assemble(Rb, gb, cb, vp, out=(Mb, Kb), stream=stream, check=False)
 
-            seq()
-            ts = float(np.mean(timed(seq, 2)))
-            bat[vp] = {"ms_per_step": tb, "value": bnnz / (tb * 1e-3), "unit": "nnz/s",
-                       "ms_one_call_per_patch": ts, "config": Bp.config}
-            Bp.close()
-            del pts
-            torch.cuda.empty_cache()
-        variants["batch_256"] = bat
-        for Rb in rules_cache.values():
-            Rb.close()
-        del base
+                seq()
+                ts = float(np.mean(timed(seq, 2)))
+                # the same algorithmic counts as the single-mesh line: contraction
+                # flops against the FP64 (df64) pipe, the band bytes against HBM for FP32
+                if vp == "mixed":
+                    bw = bnnz * 4 / (tb * 1e-3) / 1e9
+                    broof = {"bound": "hbm", "achieved": bw, "peak": hbm, "unit": "GB/s", "frac": bw / hbm}
+                else:
+                    pk = FP64_PEAK_TFLOPS if vp == "fp64" else DF64_PEAK_TFLOPS
+                    tf = bflops / (tb * 1e-3) / 1e12
+                    broof = {"bound": "alu", "achieved": tf, "peak": pk, "unit": "TFLOP/s", "frac": tf / pk}
+                bat[vp] = {"ms_per_step": tb, "value": bnnz / (tb * 1e-3), "unit": "nnz/s",
+                           "ms_one_call_per_patch": ts, "config": Bp.config, "roofline": broof}
+                Bp.close()
+                del pts
+                torch.cuda.empty_cache()
+            variants["batch_256"] = bat
+            for Rb in rules_cache.values():
+                Rb.close()
+            del base
     return variants
 
 
