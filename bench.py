@@ -254,6 +254,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-patch batch variant")
+    ap.add_argument("--batch-patches", type=int, default=256,
+                    help="patches of the batch variant (the workload is 256; fewer for profiling)")
+    ap.add_argument("--batch-precs", default="fp64,df64,mixed", help="precisions of the batch variant")
     ap.add_argument("--only", default=None,
                     help="comma list of variant groups to run: precisions, workloads, rules, adjoint, apply, "
                          "general, batch (default: all)")
@@ -729,7 +732,7 @@ def run_variants(args, wq, inputs, R, w, g, gd, cd, bands, sample, timed, stream
     # one graph of two persistent launches, tuned, against one call per patch
     if want("batch"):
         if not args.no_batch:
-            specs = inputs.batch_patches(256, seed=0)
+            specs = inputs.batch_patches(args.batch_patches, seed=0)
             rules_cache, base = {}, []
             for sp in specs:
                 key = (sp["p"], sp["nel"])
@@ -739,8 +742,8 @@ def run_variants(args, wq, inputs, R, w, g, gd, cd, bands, sample, timed, stream
                              torch.from_numpy(sp["coef"]).cuda()))
             bnnz = 2 * sum(Rb.nnz for Rb, _, _ in base)
             bflops = sum(Rb.flops()[0] for Rb, _, _ in base)
-            bat = {"workload": "batch_256", "patches": 256, "nnz_per_step": bnnz, "flops_per_step": bflops}
-            for vp in ("fp64", "df64", "mixed"):
+            bat = {"workload": f"batch_{args.batch_patches}", "patches": args.batch_patches, "nnz_per_step": bnnz, "flops_per_step": bflops}
+            for vp in args.batch_precs.split(","):
                 vdt = torch.float32 if vp == "mixed" else torch.float64
                 pts = [(Rb, gb, cb, torch.empty((Rb.rows, Rb.band), dtype=vdt, device="cuda"),
                         torch.empty((Rb.rows, Rb.band), dtype=vdt, device="cuda")) for Rb, gb, cb in base]
@@ -772,7 +775,7 @@ def run_variants(args, wq, inputs, R, w, g, gd, cd, bands, sample, timed, stream
                 Bp.close()
                 del pts
                 torch.cuda.empty_cache()
-            variants["batch_256"] = bat
+            variants[f"batch_{args.batch_patches}"] = bat
             for Rb in rules_cache.values():
                 Rb.close()
             del base

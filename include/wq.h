@@ -412,9 +412,12 @@ wq_status wq_batch_status(wq_batch *batch, void *stream);
  * Launch configuration: config[0] = chunk length of the row launch (1..32
  * rows of a line), config[1] = resident CTAs per SM of the persistent
  * partial-contraction launch (1..config[4]), config[2] = resident CTAs per SM
- * of the persistent row launch (1..config[5]), config[3] = item order (0:
- * patch order, 1: degree-3 patches first).  get writes config[0..5],
- * config[4] and config[5] being the most CTAs per SM the two kernels can hold;
+ * of the persistent row launch (1..config[5]), config[3] = schedule of the
+ * two degrees' launches (each degree has its own pair of kernels; 0: the
+ * degree-2 pair on a second stream beside the degree-3 pair, 1: degree 3
+ * then degree 2 on one stream; a batch of one degree ignores it).  The CTA
+ * counts are capped per kernel at what it can hold.  get writes config[0..5],
+ * config[4] and config[5] being the most CTAs per SM the kernels can hold;
  * set reads config[0..3], synchronises the device, rebuilds the work lists
  * and recaptures the graph.
  */
@@ -422,7 +425,7 @@ wq_status wq_batch_get_config(const wq_batch *batch, int *config);
 wq_status wq_batch_set_config(wq_batch *batch, const int *config);
 /*
  * Autotuner: times every configuration of a fixed candidate set (chunk
- * lengths 32/24/16, the two largest CTA counts of each kernel, both orders),
+ * lengths 32/24/16, the two largest CTA counts of each kernel, both schedules),
  * each `reps` times on `stream` after one warm-up (the plan's outputs are
  * written), keeps the fastest and recaptures the graph.  *best_ms (may be
  * NULL) receives its mean time.  Synchronises the device.
@@ -434,7 +437,7 @@ wq_status wq_batch_set_config(wq_batch *batch, const int *config);
  * configuration the plan accepts, applies it and returns its stored time
  * without timing anything.  On a miss it times as above and adds or
  * replaces the entry (the file is a JSON object, one entry per line:
- *   "<key>": {"config": [chunk, u_ctas, ctas, order], "ms": t}
+ *   "<key>": {"config": [chunk, u_ctas, ctas, schedule], "ms": t}
  * rewritten through a temporary file and a rename; a failed write is not
  * an error).
  */

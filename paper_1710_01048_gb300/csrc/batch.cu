@@ -54,21 +54,30 @@ struct wq_batch {
   int npatch = 0;
   wq_precision prec = WQ_FP64;
   int device = -1, nsm = 0, max_ctas = 1, max_uctas = 1;
+  int deg_uctas[2] = {1, 1}, deg_ctas[2] = {1, 1};  // per degree (index p - 2): resident CTAs per SM
   std::vector<wq_patch> patches;
   // device block: fold segments, batch segments, per-patch folded tables and
   // U buffers, counters, status
   void *dev_block = nullptr;
   BFold *dev_fold = nullptr;
   int nfold = 0, fold_total = 0;
+  // segments, degree 3 first; share[d] (d = p - 2) describes degree p's part
   wq::BatchUSeg *dev_usegs = nullptr;
   wq::BatchSeg *dev_segs = nullptr;
-  int nuseg = 0, nuitems = 0, nseg = 0, nitems = 0;
-  unsigned *dev_counter = nullptr, *dev_status = nullptr;  // counters [2], status
+  struct Share {
+    int useg0, nuseg, nuitems, seg0, nseg, nitems;
+    size_t umap0, map0;  // offsets of the item -> segment tables in dev_map
+  } share[2] = {};
+  int *dev_map = nullptr;  // item -> segment (within the share), both kernels, both degrees
+  size_t dev_map_cap = 0;
+  unsigned *dev_counter = nullptr, *dev_status = nullptr;  // counters [2 per degree], status
   std::vector<wq::RowsArgs> base_args;  // per patch, without chunking
   std::vector<wq::UArgs> base_uargs;    // per patch
-  // chunk length, CTAs per SM of the partial-contraction and of the row kernel, item order
+  // chunk length, CTAs per SM of the partial-contraction and of the row
+  // kernels, schedule of the two degrees (0: side by side, 1: degree 3 first)
   int config[4] = {wq::kUGChunk, 1, 1, 1};
-  cudaStream_t cap_stream = nullptr;
+  cudaStream_t cap_stream = nullptr, aux_stream = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
@@ -76,19 +85,24 @@ struct wq_batch {
 namespace {
 
 wq_status prepare(wq_batch *B) {
-  int uctas = 0, ctas = 0;
-  cudaError_t e = B->prec == WQ_FP64   ? wq::batch_prepare<double>(&uctas, &ctas)
-                  : B->prec == WQ_MIXED ? wq::batch_prepare<float>(&uctas, &ctas)
-                                        : wq::batch_prepare<wq::dd>(&uctas, &ctas);
-  if (e != cudaSuccess || ctas < 1 || uctas < 1) return WQ_ERR_CUDA;
-  B->max_ctas = ctas;
-  B->max_uctas = uctas;
+  int uctas[2] = {0, 0}, ctas[2] = {0, 0};
+  cudaError_t e = B->prec == WQ_FP64   ? wq::batch_prepare<double>(uctas, ctas)
+                  : B->prec == WQ_MIXED ? wq::batch_prepare<float>(uctas, ctas)
+                                        : wq::batch_prepare<wq::dd>(uctas, ctas);
+  if (e != cudaSuccess) return WQ_ERR_CUDA;
+  for (int d = 0; d < 2; d++) {
+    if (ctas[d] < 1 || uctas[d] < 1) return WQ_ERR_CUDA;
+    B->deg_uctas[d] = uctas[d];
+    B->deg_ctas[d] = ctas[d];
+  }
+  B->max_uctas = std::max(uctas[0], uctas[1]);
+  B->max_ctas = std::max(ctas[0], ctas[1]);
   return WQ_OK;
 }
 
 // Builds the two segment lists for the current configuration and uploads them.
 wq_status build_segments(wq_batch *B) {
-  const int tchunk = B->config[0], order = B->config[3];
+  const int tchunk = B->config[0];
   if (tchunk < 1 || tchunk > wq::kUGChunk) return WQ_ERR_ARG;
   std::vector<wq::BatchUSeg> usegs(B->npatch);
   std::vector<wq::BatchSeg> segs(B->npatch);
@@ -109,30 +123,89 @@ wq_status build_segments(wq_batch *B) {
     S.p = R->p;
     S.nitems = R->n[1] * R->n[2] * S.a.nch;
   }
-  if (order == 1) {  // degree 3 first: the costliest items start earliest
-    std::stable_sort(usegs.begin(), usegs.end(), [](const wq::BatchUSeg &x, const wq::BatchUSeg &y) { return x.p > y.p; });
-    std::stable_sort(segs.begin(), segs.end(), [](const wq::BatchSeg &x, const wq::BatchSeg &y) { return x.p > y.p; });
+  // degree 3 first, patch order within a degree; items numbered per degree
+  std::stable_sort(usegs.begin(), usegs.end(), [](const wq::BatchUSeg &x, const wq::BatchUSeg &y) { return x.p > y.p; });
+  std::stable_sort(segs.begin(), segs.end(), [](const wq::BatchSeg &x, const wq::BatchSeg &y) { return x.p > y.p; });
+  wq_batch::Share sh[2] = {};
+  for (int d = 0; d < 2; d++) {
+    const int p = d + 2;
+    long long utotal = 0, total = 0;
+    sh[d].useg0 = sh[d].seg0 = -1;
+    for (int i = 0; i < B->npatch; i++) {
+      if (usegs[i].p == p) {
+        if (sh[d].useg0 < 0) sh[d].useg0 = i;
+        sh[d].nuseg++;
+        usegs[i].first_item = (int)utotal;
+        utotal += usegs[i].nitems;
+      }
+      if (segs[i].p == p) {
+        if (sh[d].seg0 < 0) sh[d].seg0 = i;
+        sh[d].nseg++;
+        segs[i].first_item = (int)total;
+        total += segs[i].nitems;
+      }
+    }
+    if (total > 0x7fffffffLL || utotal > 0x7fffffffLL) return WQ_ERR_UNSUPPORTED;
+    if (sh[d].useg0 < 0) sh[d].useg0 = 0;
+    if (sh[d].seg0 < 0) sh[d].seg0 = 0;
+    sh[d].nuitems = (int)utotal;
+    sh[d].nitems = (int)total;
   }
-  long long utotal = 0, total = 0;
-  for (wq::BatchUSeg &U : usegs) {
-    U.first_item = (int)utotal;
-    utotal += U.nitems;
+  // the item -> segment tables: per degree, its u items, then its rows items
+  std::vector<int> map;
+  for (int d = 0; d < 2; d++) {
+    sh[d].umap0 = map.size();
+    for (int k = 0; k < sh[d].nuseg; k++) map.insert(map.end(), usegs[sh[d].useg0 + k].nitems, k);
+    sh[d].map0 = map.size();
+    for (int k = 0; k < sh[d].nseg; k++) map.insert(map.end(), segs[sh[d].seg0 + k].nitems, k);
   }
-  for (wq::BatchSeg &S : segs) {
-    S.first_item = (int)total;
-    total += S.nitems;
-  }
-  if (total > 0x7fffffffLL || utotal > 0x7fffffffLL) return WQ_ERR_UNSUPPORTED;
   if (cudaDeviceSynchronize() != cudaSuccess) return WQ_ERR_CUDA;  // no launch still reads the old lists
+  if (map.size() > B->dev_map_cap) {
+    if (B->dev_map) cudaFree(B->dev_map);
+    B->dev_map = nullptr;
+    B->dev_map_cap = 0;
+    if (cudaMalloc(&B->dev_map, map.size() * sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      return WQ_ERR_OOM;
+    }
+    B->dev_map_cap = map.size();
+  }
   if (cudaMemcpy(B->dev_usegs, usegs.data(), usegs.size() * sizeof(wq::BatchUSeg), cudaMemcpyHostToDevice) !=
           cudaSuccess ||
-      cudaMemcpy(B->dev_segs, segs.data(), segs.size() * sizeof(wq::BatchSeg), cudaMemcpyHostToDevice) != cudaSuccess)
+      cudaMemcpy(B->dev_segs, segs.data(), segs.size() * sizeof(wq::BatchSeg), cudaMemcpyHostToDevice) != cudaSuccess ||
+      (!map.empty() &&
+       cudaMemcpy(B->dev_map, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess))
     return WQ_ERR_CUDA;
-  B->nuseg = (int)usegs.size();
-  B->nuitems = (int)utotal;
-  B->nseg = (int)segs.size();
-  B->nitems = (int)total;
+  B->share[0] = sh[0];
+  B->share[1] = sh[1];
   return WQ_OK;
+}
+
+// Degree p's share with the current configuration's grids.
+wq::BatchShare share_of(const wq_batch *B, int p) {
+  const int d = p - 2;
+  const wq_batch::Share &h = B->share[d];
+  wq::BatchShare S;
+  S.usegs = B->dev_usegs + h.useg0;
+  S.segs = B->dev_segs + h.seg0;
+  S.useg_of = B->dev_map + h.umap0;
+  S.seg_of = B->dev_map + h.map0;
+  S.nuseg = h.nuseg;
+  S.nuitems = h.nuitems;
+  S.nseg = h.nseg;
+  S.nitems = h.nitems;
+  S.counters = B->dev_counter + 2 * d;
+  S.ugrid = B->nsm * std::min(B->config[1], B->deg_uctas[d]);
+  S.grid = B->nsm * std::min(B->config[2], B->deg_ctas[d]);
+  return S;
+}
+
+cudaError_t launch_share(const wq_batch *B, int p, cudaStream_t s) {
+  const wq::BatchShare S = share_of(B, p);
+  if (S.nuitems == 0 && S.nitems == 0) return cudaSuccess;
+  return B->prec == WQ_FP64    ? wq::launch_batch_share<double>(p, S, s)
+         : B->prec == WQ_MIXED ? wq::launch_batch_share<float>(p, S, s)
+                               : wq::launch_batch_share<wq::dd>(p, S, s);
 }
 
 wq_status enqueue(const wq_batch *B, cudaStream_t s) {
@@ -141,15 +214,21 @@ wq_status enqueue(const wq_batch *B, cudaStream_t s) {
     batch_fold_kernel<<<blocks, 256, 0, s>>>(B->dev_fold, B->nfold, B->fold_total, B->dev_status);
     if (cudaGetLastError() != cudaSuccess) return WQ_ERR_CUDA;
   }
-  if (cudaMemsetAsync(B->dev_counter, 0, 2 * sizeof(unsigned), s) != cudaSuccess) return WQ_ERR_CUDA;
-  const int ugrid = B->nsm * B->config[1], grid = B->nsm * B->config[2];
-  cudaError_t e =
-      B->prec == WQ_FP64   ? wq::launch_batch<double>(B->dev_usegs, B->nuseg, B->nuitems, B->dev_segs, B->nseg,
-                                                      B->nitems, B->dev_counter, ugrid, grid, s)
-      : B->prec == WQ_MIXED ? wq::launch_batch<float>(B->dev_usegs, B->nuseg, B->nuitems, B->dev_segs, B->nseg,
-                                                     B->nitems, B->dev_counter, ugrid, grid, s)
-                            : wq::launch_batch<wq::dd>(B->dev_usegs, B->nuseg, B->nuitems, B->dev_segs, B->nseg,
-                                                       B->nitems, B->dev_counter, ugrid, grid, s);
+  if (cudaMemsetAsync(B->dev_counter, 0, 4 * sizeof(unsigned), s) != cudaSuccess) return WQ_ERR_CUDA;
+  const bool both = B->share[0].nseg > 0 && B->share[1].nseg > 0;
+  cudaError_t e = cudaSuccess;
+  if (B->config[3] == 1 || !both) {
+    e = launch_share(B, 3, s);
+    if (e == cudaSuccess) e = launch_share(B, 2, s);
+  } else {
+    // degree 2 on the second stream, forked from and joined back into s
+    e = cudaEventRecord(B->fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(B->aux_stream, B->fork, 0);
+    if (e == cudaSuccess) e = launch_share(B, 3, s);
+    if (e == cudaSuccess) e = launch_share(B, 2, B->aux_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(B->join, B->aux_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, B->join, 0);
+  }
   return e == cudaSuccess ? WQ_OK : WQ_ERR_CUDA;
 }
 
@@ -199,7 +278,7 @@ wq_status apply_config(wq_batch *B, const int *cfg) {
 }
 
 // The autotuner cache's key: the GPU (name, compute capability, SMs), the
-// precision, the occupancy limits of this build's two kernels, the degree mix
+// precision, the occupancy limits of this build's four kernels, the degree mix
 // and a hash (64-bit FNV-1a) of the patches' shapes in plan order; empty on
 // a CUDA error.
 std::string cache_key(const wq_batch *B) {
@@ -223,10 +302,10 @@ std::string cache_key(const wq_batch *B) {
     mix(P.coef != nullptr);
   }
   char buf[384];
-  std::snprintf(buf, sizeof(buf), "v1|%s|cc%d.%d|sm%d|%s|occ%d,%d|p2x%d,p3x%d|rows%lld|shape%016llx", prop.name,
-                prop.major, prop.minor, prop.multiProcessorCount,
-                B->prec == WQ_FP64 ? "fp64" : B->prec == WQ_MIXED ? "mixed" : "df64", B->max_uctas, B->max_ctas, np2,
-                np3, rows, (unsigned long long)h);
+  std::snprintf(buf, sizeof(buf), "v2|%s|cc%d.%d|sm%d|%s|occ%d,%d,%d,%d|p2x%d,p3x%d|rows%lld|shape%016llx",
+                prop.name, prop.major, prop.minor, prop.multiProcessorCount,
+                B->prec == WQ_FP64 ? "fp64" : B->prec == WQ_MIXED ? "mixed" : "df64", B->deg_uctas[0],
+                B->deg_uctas[1], B->deg_ctas[0], B->deg_ctas[1], np2, np3, rows, (unsigned long long)h);
   return wq::tune_cache_clean_key(buf);
 }
 
@@ -234,7 +313,11 @@ void destroy(wq_batch *B) {
   if (!B) return;
   drop_graph(B);
   if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
+  if (B->aux_stream) cudaStreamDestroy(B->aux_stream);
+  if (B->fork) cudaEventDestroy(B->fork);
+  if (B->join) cudaEventDestroy(B->join);
   if (B->dev_block) cudaFree(B->dev_block);
+  if (B->dev_map) cudaFree(B->dev_map);
   delete B;
 }
 
@@ -280,7 +363,7 @@ wq_status wq_batch_create(const wq_patch *patches, int npatch, wq_precision prec
   const size_t seg_off = total;
   total += align_up(sizeof(wq::BatchSeg) * (size_t)npatch);
   const size_t cnt_off = total;
-  total += align_up(3 * sizeof(unsigned));
+  total += align_up(5 * sizeof(unsigned));
   const size_t elem_bytes = prec == WQ_MIXED ? sizeof(float) : sizeof(double);
   std::vector<size_t> tab_off(6 * (size_t)npatch), u_off(npatch);
   for (int i = 0; i < npatch; i++) {
@@ -307,7 +390,7 @@ wq_status wq_batch_create(const wq_patch *patches, int npatch, wq_precision prec
   B->dev_usegs = reinterpret_cast<wq::BatchUSeg *>(base + useg_off);
   B->dev_segs = reinterpret_cast<wq::BatchSeg *>(base + seg_off);
   B->dev_counter = reinterpret_cast<unsigned *>(base + cnt_off);
-  B->dev_status = B->dev_counter + 2;
+  B->dev_status = B->dev_counter + 4;
   std::vector<BFold> folds;
   int start = 0;
   B->base_args.resize(npatch);
@@ -385,8 +468,11 @@ wq_status wq_batch_create(const wq_patch *patches, int npatch, wq_precision prec
   B->nfold = (int)folds.size();
   B->fold_total = start;
   bool ok = cudaMemcpy(B->dev_fold, folds.data(), folds.size() * sizeof(BFold), cudaMemcpyHostToDevice) == cudaSuccess;
-  ok = ok && cudaMemset(B->dev_counter, 0, 3 * sizeof(unsigned)) == cudaSuccess;
+  ok = ok && cudaMemset(B->dev_counter, 0, 5 * sizeof(unsigned)) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&B->aux_stream, cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&B->join, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     destroy(B);
     return WQ_ERR_CUDA;
@@ -475,12 +561,12 @@ wq_status wq_batch_tune(wq_batch *B, void *stream, int reps, double *best_ms) {
   std::memcpy(best, B->config, sizeof(best));
   float best_t = -1.0f;
   wq_status st = WQ_OK;
-  for (int order = 0; order < 2 && st == WQ_OK; order++)
+  for (int sched = 0; sched < 2 && st == WQ_OK; sched++)
     for (int uc : uctas)
       for (int c : ctas)
         for (int t : chunks) {
           if (st != WQ_OK) break;
-          const int cfg[4] = {t, uc, c, order};
+          const int cfg[4] = {t, uc, c, sched};
           std::memcpy(B->config, cfg, sizeof(cfg));
           if (build_segments(B) != WQ_OK) continue;  // a chunk length this batch's tables do not fit
           st = enqueue(B, s);  // warm-up

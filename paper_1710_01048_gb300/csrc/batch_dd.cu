@@ -3,6 +3,5 @@
 
 namespace wq {
 template cudaError_t batch_prepare<dd>(int *, int *);
-template cudaError_t launch_batch<dd>(const BatchUSeg *, int, int, const BatchSeg *, int, int, unsigned *, int, int,
-                                      cudaStream_t);
+template cudaError_t launch_batch_share<dd>(int, const BatchShare &, cudaStream_t);
 }

@@ -3,6 +3,5 @@
 
 namespace wq {
 template cudaError_t batch_prepare<double>(int *, int *);
-template cudaError_t launch_batch<double>(const BatchUSeg *, int, int, const BatchSeg *, int, int, unsigned *, int, int,
-                                      cudaStream_t);
+template cudaError_t launch_batch_share<double>(int, const BatchShare &, cudaStream_t);
 }

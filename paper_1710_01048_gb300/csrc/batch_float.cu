@@ -3,6 +3,5 @@
 
 namespace wq {
 template cudaError_t batch_prepare<float>(int *, int *);
-template cudaError_t launch_batch<float>(const BatchUSeg *, int, int, const BatchSeg *, int, int, unsigned *, int, int,
-                                      cudaStream_t);
+template cudaError_t launch_batch_share<float>(int, const BatchShare &, cudaStream_t);
 }

@@ -2,7 +2,7 @@
 //
 // The file is a JSON object written with one entry per line:
 //   {
-//     "<key>": {"config": [chunk, u_ctas, ctas, order], "ms": mean_ms},
+//     "<key>": {"config": [chunk, u_ctas, ctas, schedule], "ms": mean_ms},
 //     ...
 //   }
 // The reader accepts exactly that shape (whitespace aside); a line it does
