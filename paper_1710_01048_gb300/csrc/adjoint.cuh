@@ -27,22 +27,25 @@ namespace wq {
 struct AdjArgs {
   RowsArgs rows;         // tables, sizes, row range, line list, chunking (M, K, coef unused)
   const void *G, *H;     // band weights, OutT<R>, rows [row_begin, row_end); either may be null
-  double *partial;       // chunk blocks: slot (line * nch_max + chunk) of blk values
+  double *partial;       // 2D: chunk blocks, slot (line * nch_max + chunk) of blk values
   int nch_max, nl1max;   // slots per line; the l1 extent of a block
-  long long blk;         // values per slot: NL * NL * nl1max (3D), NL * nl1max (2D)
+  long long blk;         // values per slot: NL * nl1max (2D)
+  void *ubar;            // 3D: chunk slots of Ubar in R, slot (line * nch_max + chunk) of ubar_slot values
+  long long ubar_slot;   // 2 * nl1max * (2P+1)^2: [u][column - the chunk's first column][(j3, j2)]
 };
 
 // The chunks of a line: its class's chunk length T (rows per chunk), clipped
 // to the call's rows, as the adjoint (and forward) kernels cut them.
 struct GatherArgs {
-  const double *partial;
+  const double *partial;  // 2D: chunk blocks; 3D: the line-block slots of adjoint_u_kernel
   double *grad;  // prod(nc_a) coefficients, overwritten
   int dim, p;
   int n[3], N[3], nc[3];
   long long row_begin, row_end;
-  int T_int, T_bnd;  // chunk lengths of interior and boundary lines
+  int T_int, T_bnd;  // chunk lengths of interior and boundary lines (2D)
   int nch_max, nl1max;
   long long blk;
+  int r3_lo, r3_hi, nblk2, nblk1;  // 3D: planes of the call, line and column blocks per plane
 };
 
 template <int P, int D, int LM, int TMAX, typename R>
@@ -119,6 +122,70 @@ __device__ __forceinline__ void adj_x1_row(R (&w0)[WN], R (&w1)[WN], const int r
   }
 }
 
+// The x1 stage transposed for the chunk of rows [a, a + T) of the line whose
+// first row is `base` (D = 2 or 3: a row has (2P+1)^(D-1) band fibres of
+// 2P+1 entries): Ubar (shared memory, [u][NL1][fibre], zeroed and
+// visible to the CTA on entry) receives, for window columns 0 .. nl1-1 (column
+// l1lo + c), the contributions of the chunk's rows and band fibres:
+//   yM = sum_i H[o+i] V1M[q][i], yK = sum_i G[o+i] V1M[q][i], yS = sum_i G[o+i] V1S[q][i]
+//   Ubar0[e+i] += b1M[q][i] yM + b1S[q][i] yS, Ubar1[e+i] += b1M[q][i] yK
+// per row and x1 point q (element e, band offset o = e - r1 + P).  A thread
+// takes one fibre of four consecutive rows and keeps its columns in a
+// register window; the windows are added to Ubar in three ordered rounds
+// (segments s, s+3, ... touch disjoint columns), so the result does not
+// depend on thread timing.  Every thread of the CTA must call it; it ends
+// with a barrier.
+template <int P, int D, int MAXPTS1, int NL1, int NT, typename R>
+__device__ __forceinline__ void adj_x1_stage(const AdjArgs &AA, const R *sV1, const R *sB1, const int *sE1,
+                                             const int *sOff1, R *sUb, int a, int T, long long base, int l1lo,
+                                             int nl1) {
+  using O = typename OutT<R>::type;
+  constexpr int NB = 2 * P + 1, NPAIR = (D == 3) ? NB * NB : NB, BAND = NPAIR * NB;
+  const RowsArgs &A = AA.rows;
+  const int tid = threadIdx.x;
+  const bool hasG = AA.G != nullptr, hasH = AA.H != nullptr;
+  R *Ub0 = sUb, *Ub1 = sUb + NL1 * NPAIR;
+  constexpr int RS = 4, WN = RS + P + 3;
+  const O *Hg = hasH ? static_cast<const O *>(AA.H) : nullptr;
+  const O *Gg = hasG ? static_cast<const O *>(AA.G) : nullptr;
+  const int nseg = (T + RS - 1) / RS, nitems = nseg * NPAIR;
+  for (int it0 = 0; it0 < nitems; it0 += NT) {  // uniform trip count: every thread meets the barriers
+    const int it = it0 + tid;
+    const bool act = it < nitems;
+    const int sg = it / NPAIR, pr = it - sg * NPAIR;
+    R w0[WN], w1[WN];
+#pragma unroll
+    for (int c = 0; c < WN; c++) {
+      w0[c] = r_zero<R>();
+      w1[c] = r_zero<R>();
+    }
+    if (act) {
+      const long long grow = (base + a + sg * RS - A.row_begin) * BAND + (long long)pr * NB;
+      const int rl = sg * RS;
+      static_assert(RS == 4, "four rows per segment");
+      adj_x1_row<P, 0, WN, MAXPTS1, BAND>(w0, w1, rl, T, a, Hg, Gg, grow, sOff1, sE1, sV1, sB1);
+      adj_x1_row<P, 1, WN, MAXPTS1, BAND>(w0, w1, rl, T, a, Hg, Gg, grow, sOff1, sE1, sV1, sB1);
+      adj_x1_row<P, 2, WN, MAXPTS1, BAND>(w0, w1, rl, T, a, Hg, Gg, grow, sOff1, sE1, sV1, sB1);
+      adj_x1_row<P, 3, WN, MAXPTS1, BAND>(w0, w1, rl, T, a, Hg, Gg, grow, sOff1, sE1, sV1, sB1);
+    }
+    // window column c is coefficient column a + sg*RS - P + c
+    const int cbase = a + sg * RS - P - l1lo;
+    for (int round = 0; round < 3; round++) {
+      if (act && sg % 3 == round) {
+#pragma unroll
+        for (int c = 0; c < WN; c++) {
+          const int col = cbase + c;
+          if (col >= 0 && col < nl1) {
+            Ub0[col * NPAIR + pr] = r_add(Ub0[col * NPAIR + pr], w0[c]);
+            Ub1[col * NPAIR + pr] = r_add(Ub1[col * NPAIR + pr], w1[c]);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // Resident CTAs per SM the register allocation is sized for (measured at
 // 96^3: four for float, three for double, two for double-float, whose
 // register windows spill at three).
@@ -137,12 +204,10 @@ template <typename R> constexpr int adj_min_blocks() {
 template <int P, int D, int LM, int TMAX, typename R>
 __global__ void __launch_bounds__(32 * kRowsWarps, adj_min_blocks<R>()) adjoint_kernel(const AdjArgs AA) {
   using L = AdjLayout<P, D, LM, TMAX, R>;
-  using O = typename OutT<R>::type;
   const RowsArgs &A = AA.rows;
   constexpr int NP = L::NP, NB = L::NB, NT = L::NT, NW = L::NW, NL = L::NL, NL1 = L::NL1;
-  constexpr int NPAIR = L::NPAIR, BAND = L::BAND;
+  constexpr int NPAIR = L::NPAIR;
   constexpr bool INNER_GAUSS = (LM == P + 1);
-  const bool hasG = AA.G != nullptr, hasH = AA.H != nullptr;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R *sV23 = reinterpret_cast<R *>(smem_raw);
@@ -241,47 +306,8 @@ __global__ void __launch_bounds__(32 * kRowsWarps, adj_min_blocks<R>()) adjoint_
   // are then added to Ubar in three ordered rounds (segments s, s+3, ... touch
   // disjoint columns), so the result does not depend on thread timing.
   R *Ub0 = sUb, *Ub1 = sUb + NL1 * NPAIR;
-  {
-    constexpr int RS = 4, WN = RS + P + 3;
-    const O *Hg = hasH ? static_cast<const O *>(AA.H) : nullptr;
-    const O *Gg = hasG ? static_cast<const O *>(AA.G) : nullptr;
-    const int nseg = (T + RS - 1) / RS, nitems = nseg * NPAIR;
-    for (int it0 = 0; it0 < nitems; it0 += NT) {  // uniform trip count: every thread meets the barriers
-      const int it = it0 + tid;
-      const bool act = it < nitems;
-      const int sg = it / NPAIR, pr = it - sg * NPAIR;
-      R w0[WN], w1[WN];
-#pragma unroll
-      for (int c = 0; c < WN; c++) {
-        w0[c] = r_zero<R>();
-        w1[c] = r_zero<R>();
-      }
-      if (act) {
-        const long long grow = (base + a + sg * RS - A.row_begin) * BAND + (long long)pr * NB;
-        const int rl = sg * RS;
-        static_assert(RS == 4, "four rows per segment");
-        adj_x1_row<P, 0, WN, L::MAXPTS1, BAND>(w0, w1, rl, T, a, Hg, Gg, grow, sOff1, sE1, sV1, sB1);
-        adj_x1_row<P, 1, WN, L::MAXPTS1, BAND>(w0, w1, rl, T, a, Hg, Gg, grow, sOff1, sE1, sV1, sB1);
-        adj_x1_row<P, 2, WN, L::MAXPTS1, BAND>(w0, w1, rl, T, a, Hg, Gg, grow, sOff1, sE1, sV1, sB1);
-        adj_x1_row<P, 3, WN, L::MAXPTS1, BAND>(w0, w1, rl, T, a, Hg, Gg, grow, sOff1, sE1, sV1, sB1);
-      }
-      // window column c is coefficient column a + sg*RS - P + c
-      const int cbase = a + sg * RS - P - l1lo;
-      for (int round = 0; round < 3; round++) {
-        if (act && sg % 3 == round) {
-#pragma unroll
-          for (int c = 0; c < WN; c++) {
-            const int col = cbase + c;
-            if (col >= 0 && col < nl1) {
-              Ub0[col * NPAIR + pr] = r_add(Ub0[col * NPAIR + pr], w0[c]);
-              Ub1[col * NPAIR + pr] = r_add(Ub1[col * NPAIR + pr], w1[c]);
-            }
-          }
-        }
-        __syncthreads();
-      }
-    }
-  }
+  static_assert(NPAIR == ((D == 3) ? NB * NB : NB), "fibres per row");
+  adj_x1_stage<P, D, L::MAXPTS1, NL1, NT, R>(AA, sV1, sB1, sE1, sOff1, sUb, a, T, base, l1lo, nl1);
 
   // ------------------------------------------------ 2. x2, x3 stages transposed, warp per column
   // this chunk's slot of the block scratch
@@ -420,6 +446,95 @@ template <int P, int D, int LM, int TMAX, typename R>
 cudaError_t launch_adjoint_one(const AdjArgs &a, int nblocks, cudaStream_t s) {
   using L = AdjLayout<P, D, LM, TMAX, R>;
   auto kern = adjoint_kernel<P, D, LM, TMAX, R>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (nblocks <= 0) return cudaSuccess;
+  kern<<<nblocks, L::NT, L::BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+// 3D: the x1 stage transposed of one chunk, its Ubar stored in the chunk's
+// slot of AA.ubar; the x2 and x3 stages run afterwards, once per block of
+// lines and coefficient columns (adjoint_u_kernel), instead of per chunk.
+template <int P, int TMAX, typename R> struct AdjX1Layout {
+  static constexpr int NP = P + 1, NB = 2 * P + 1, NPAIR = NB * NB;
+  static constexpr int NL1 = TMAX + P + 3;
+  static constexpr int MAXPTS1 = TMAX * NP + P * NP * (P - 1);
+  static constexpr int NT = 32 * kRowsWarps;
+  static constexpr int V1 = pad16<R>(2 * MAXPTS1 * NP);
+  static constexpr int B1 = pad16<R>(2 * MAXPTS1 * 4);
+  static constexpr int UB = pad16<R>(2 * NL1 * NPAIR);  // [u][NL1][pair]
+  static constexpr int R_TOTAL = V1 + B1 + UB;
+  static constexpr int I_TOTAL = MAXPTS1 + TMAX + 1;
+  static constexpr size_t BYTES = sizeof(R) * (size_t)R_TOTAL + sizeof(int) * (size_t)I_TOTAL;
+};
+
+template <int P, int TMAX, typename R>
+__global__ void __launch_bounds__(32 * kRowsWarps, adj_min_blocks<R>()) adjoint_x1_kernel(const AdjArgs AA) {
+  using L = AdjX1Layout<P, TMAX, R>;
+  const RowsArgs &A = AA.rows;
+  constexpr int NP = L::NP, NT = L::NT, NL1 = L::NL1, NPAIR = L::NPAIR;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R *sV1 = reinterpret_cast<R *>(smem_raw);
+  R *sB1 = sV1 + L::V1;
+  R *sUb = sB1 + L::B1;
+  int *sE1 = reinterpret_cast<int *>(smem_raw + sizeof(R) * (size_t)L::R_TOTAL);
+  int *sOff1 = sE1 + L::MAXPTS1;
+
+  const int tid = threadIdx.x;
+  const int line = A.lines[blockIdx.x / A.nch];
+  const int ch = blockIdx.x % A.nch;
+  const int n1 = A.n[0];
+  const long long base = (long long)line * n1;
+  long long lo = (long long)ch * A.T, hi = lo + A.T;
+  if (hi > n1) hi = n1;
+  if (lo < A.row_begin - base) lo = A.row_begin - base;
+  if (hi > A.row_end - base) hi = A.row_end - base;
+  if (lo >= hi) return;
+  const int a = (int)lo, b = (int)hi, T = b - a;
+
+  const int p1lo = A.off[0][0][a], p1hi = A.off[0][0][b];
+  const int np1 = p1hi - p1lo;
+  for (int t = tid; t <= T; t += NT) sOff1[t] = A.off[0][0][a + t] - p1lo;
+  const int elo1 = a - P < 0 ? 0 : a - P;
+  const int ehi1 = (b - 1) > A.N[0] - 1 ? A.N[0] - 1 : (b - 1);
+  const int l1lo = elo1, nl1 = ehi1 - elo1 + 4;
+  for (int t = tid; t < 2 * NL1 * NPAIR; t += NT) sUb[t] = r_zero<R>();
+  for (int t = tid; t < 2 * np1; t += NT) {
+    const int kind = t >= np1 ? 1 : 0, q = t - kind * np1;
+    const int gq = (kind ? A.off[0][1][a] : p1lo) + q;
+    const R *Vg = static_cast<const R *>(A.V[0][kind]);
+    const R *Bg = static_cast<const R *>(A.beta[0][kind]);
+#pragma unroll
+    for (int i = 0; i < NP; i++) sV1[(kind * L::MAXPTS1 + q) * NP + i] = Vg[(size_t)gq * NP + i];
+#pragma unroll
+    for (int i = 0; i < 4; i++) sB1[(kind * L::MAXPTS1 + q) * 4 + i] = Bg[(size_t)gq * 4 + i];
+    if (kind == 0) sE1[q] = A.elem[0][0][p1lo + q];
+  }
+  __syncthreads();
+
+  adj_x1_stage<P, 3, L::MAXPTS1, NL1, NT, R>(AA, sV1, sB1, sE1, sOff1, sUb, a, T, base, l1lo, nl1);
+
+  // the chunk's window columns to its slot, [u][column][pair]
+  R *Ug = static_cast<R *>(AA.ubar);
+  const long long slot = ((long long)line * AA.nch_max + ch) * AA.ubar_slot;
+  const long long total = (long long)A.n[1] * A.n[2] * AA.nch_max * AA.ubar_slot;
+  const int run = nl1 * NPAIR;
+  for (int t = tid; t < 2 * run; t += NT) {
+    const int u = t >= run ? 1 : 0, rem = t - u * run;
+    const long long di = slot + (long long)u * AA.nl1max * NPAIR + rem;
+    if (check_range(A.status, di, 1, total)) Ug[di] = sUb[u * NL1 * NPAIR + rem];
+  }
+}
+
+template <int P, int TMAX, typename R>
+cudaError_t launch_adjoint_x1_one(const AdjArgs &a, int nblocks, cudaStream_t s) {
+  using L = AdjX1Layout<P, TMAX, R>;
+  auto kern = adjoint_x1_kernel<P, TMAX, R>;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);

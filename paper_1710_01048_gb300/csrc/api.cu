@@ -128,6 +128,45 @@ __global__ void adjoint_gather_kernel(const wq::GatherArgs G) {
   G.grad[g] = s;
 }
 
+// 3D: dJ/dC of every coefficient (c1, c2, c3): the sum, over the planes r3
+// of the call whose x3 window holds c3 (ascending) and the line blocks of
+// that plane whose x2 window holds c2 (ascending), of the block slot's
+// entry [c1 - l1a][c2 - l2lo][c3 - l3lo] (adjoint_u_kernel; c1's column
+// block is unique).  One thread per coefficient.
+__global__ void adjoint_gather3_kernel(const wq::GatherArgs G) {
+  const long long ncoef = (long long)G.nc[0] * G.nc[1] * G.nc[2];
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= ncoef) return;
+  const int P = G.p, NL = P + 4, NL2 = wq::kAULines + P + 3;
+  const long long CBAR = (long long)wq::kAUCols * NL2 * NL;
+  const int c1 = (int)(g % G.nc[0]);
+  const int c2 = (int)((g / G.nc[0]) % G.nc[1]);
+  const int c3 = (int)(g / ((long long)G.nc[0] * G.nc[1]));
+  const int b1 = c1 / wq::kAUCols, l1 = c1 - b1 * wq::kAUCols;
+  int r3lo = c3 - 3 > G.r3_lo ? c3 - 3 : G.r3_lo;
+  int r3hi = c3 + P < G.r3_hi ? c3 + P : G.r3_hi;
+  int b2lo = (c2 - wq::kAULines - 3) / wq::kAULines;
+  if (b2lo < 0) b2lo = 0;
+  int b2hi = (c2 + P) / wq::kAULines;
+  if (b2hi > G.nblk2 - 1) b2hi = G.nblk2 - 1;
+  double s = 0.0;
+  for (int r3 = r3lo; r3 <= r3hi; r3++) {
+    const int l3lo = r3 - P > 0 ? r3 - P : 0;
+    const int l3hi = (r3 < G.N[2] - 1 ? r3 : G.N[2] - 1) + 3;
+    if (c3 < l3lo || c3 > l3hi) continue;
+    for (int b2 = b2lo; b2 <= b2hi; b2++) {
+      const int r2a = b2 * wq::kAULines;
+      const int r2e = (r2a + wq::kAULines - 1 < G.n[1] - 1 ? r2a + wq::kAULines - 1 : G.n[1] - 1);
+      const int l2lo = r2a - P > 0 ? r2a - P : 0;
+      const int l2hi = (r2e < G.N[1] - 1 ? r2e : G.N[1] - 1) + 3;
+      if (c2 < l2lo || c2 > l2hi) continue;
+      const long long blk = ((long long)(r3 - G.r3_lo) * G.nblk2 + b2) * G.nblk1 + b1;
+      s += G.partial[blk * CBAR + ((long long)l1 * NL2 + (c2 - l2lo)) * NL + (c3 - l3lo)];
+    }
+  }
+  G.grad[g] = s;
+}
+
 wq_status upload(wq_rules *R) {
   // fault injection for callers' error paths: the device allocation fails
   if (std::getenv("WQ_FAULT_DEVICE_ALLOC")) return WQ_ERR_OOM;
@@ -889,9 +928,18 @@ wq_status wq_assemble_adjoint(const wq_rules *R, const double *const *geom, wq_p
   const int T_bnd = wq::chunk_length(R, wq::kBoundaryChunk);
   const int nch_max = std::max((n1 + T_int - 1) / T_int, (n1 + T_bnd - 1) / T_bnd);
   const int nl1max = std::max(T_int, T_bnd) + p + 3, NL = p + 4;
-  const long long blk = (long long)(R->dim == 3 ? NL * NL : NL) * nl1max;
+  const long long blk = (long long)NL * nl1max;  // 2D chunk blocks
   const size_t nlines = (size_t)R->n[1] * R->n[2];
-  const size_t need = nlines * nch_max * (size_t)blk * sizeof(double);
+  // 3D: Ubar chunk slots (arithmetic type), then the line-block slots (double)
+  const int NB = 2 * p + 1, NPAIR = NB * NB;
+  const long long ubar_slot = 2LL * nl1max * NPAIR;
+  const size_t rbytes = prec == WQ_MIXED ? 4 : 8;
+  const size_t ubar_bytes = (nlines * nch_max * (size_t)ubar_slot * rbytes + 255) / 256 * 256;
+  const int nblk2 = (R->n[1] + wq::kAULines - 1) / wq::kAULines;
+  const int nblk1 = (R->nc[0] + wq::kAUCols - 1) / wq::kAUCols;
+  const size_t cbar_vals = (size_t)wq::kAUCols * (wq::kAULines + p + 3) * NL;
+  const size_t need = R->dim == 3 ? ubar_bytes + (size_t)R->n[2] * nblk2 * nblk1 * cbar_vals * sizeof(double)
+                                  : nlines * nch_max * (size_t)blk * sizeof(double);
   if (need > R->dev_adj_bytes) {
     // grown, never shrunk; the previous contents are not needed
     if (R->dev_adj && cudaStreamSynchronize(s) != cudaSuccess) return WQ_ERR_CUDA;
@@ -921,6 +969,11 @@ wq_status wq_assemble_adjoint(const wq_rules *R, const double *const *geom, wq_p
   aa.nch_max = nch_max;
   aa.nl1max = nl1max;
   aa.blk = blk;
+  double *cbar = reinterpret_cast<double *>(reinterpret_cast<char *>(R->dev_adj) + ubar_bytes);
+  if (R->dim == 3) {
+    aa.ubar = R->dev_adj;
+    aa.ubar_slot = ubar_slot;
+  }
   for (int cls = 0; cls < 2; cls++) {
     wq_status cst = WQ_OK;
     const int nblocks = chunk_class(R, cls, eb, row_begin, row_end, aa.rows, &cst);
@@ -935,6 +988,48 @@ wq_status wq_assemble_adjoint(const wq_rules *R, const double *const *geom, wq_p
       e = prec == WQ_FP64   ? wq::launch_adjoint<3, double>(R->dim, cls, aa, nblocks, s)
           : prec == WQ_MIXED ? wq::launch_adjoint<3, float>(R->dim, cls, aa, nblocks, s)
                              : wq::launch_adjoint<3, wq::dd>(R->dim, cls, aa, nblocks, s);
+    if (e != cudaSuccess) return WQ_ERR_CUDA;
+  }
+  const int n2 = R->n[1];
+  const int first_line = (int)(row_begin / n1), last_line = (int)((row_end - 1) / n1);
+  const int r3_lo = first_line / n2, r3_hi = last_line / n2;
+  if (R->dim == 3) {
+    wq::AdjUArgs ua;
+    std::memset(&ua, 0, sizeof(ua));
+    std::memcpy(ua.off, aa.rows.off, sizeof(ua.off));
+    std::memcpy(ua.elem, aa.rows.elem, sizeof(ua.elem));
+    std::memcpy(ua.V, aa.rows.V, sizeof(ua.V));
+    std::memcpy(ua.beta, aa.rows.beta, sizeof(ua.beta));
+    for (int a = 0; a < 3; a++) {
+      ua.n[a] = R->n[a];
+      ua.N[a] = R->nel[a];
+      ua.nc[a] = R->nc[a];
+    }
+    ua.ubar = R->dev_adj;
+    ua.ubar_slot = ubar_slot;
+    ua.nch_max = nch_max;
+    ua.nl1max = nl1max;
+    ua.T_int = T_int;
+    ua.T_bnd = T_bnd;
+    ua.row_begin = row_begin;
+    ua.row_end = row_end;
+    ua.line_lo = first_line;
+    ua.line_hi = last_line;
+    ua.r3_lo = r3_lo;
+    ua.nblk2 = nblk2;
+    ua.nblk1 = nblk1;
+    ua.cbar = cbar;
+    ua.status = R->dev_status;
+    const int nblocks = (r3_hi - r3_lo + 1) * nblk2 * nblk1;
+    cudaError_t e;
+    if (R->p == 2)
+      e = prec == WQ_FP64   ? wq::launch_adjoint_u<2, double>(ua, nblocks, s)
+          : prec == WQ_MIXED ? wq::launch_adjoint_u<2, float>(ua, nblocks, s)
+                             : wq::launch_adjoint_u<2, wq::dd>(ua, nblocks, s);
+    else
+      e = prec == WQ_FP64   ? wq::launch_adjoint_u<3, double>(ua, nblocks, s)
+          : prec == WQ_MIXED ? wq::launch_adjoint_u<3, float>(ua, nblocks, s)
+                             : wq::launch_adjoint_u<3, wq::dd>(ua, nblocks, s);
     if (e != cudaSuccess) return WQ_ERR_CUDA;
   }
   wq::GatherArgs ga;
@@ -955,7 +1050,16 @@ wq_status wq_assemble_adjoint(const wq_rules *R, const double *const *geom, wq_p
   ga.nch_max = nch_max;
   ga.nl1max = nl1max;
   ga.blk = blk;
-  adjoint_gather_kernel<<<(unsigned)((ncoef + 255) / 256), 256, 0, s>>>(ga);
+  if (R->dim == 3) {
+    ga.partial = cbar;
+    ga.r3_lo = r3_lo;
+    ga.r3_hi = r3_hi;
+    ga.nblk2 = nblk2;
+    ga.nblk1 = nblk1;
+    adjoint_gather3_kernel<<<(unsigned)((ncoef + 255) / 256), 256, 0, s>>>(ga);
+  } else {
+    adjoint_gather_kernel<<<(unsigned)((ncoef + 255) / 256), 256, 0, s>>>(ga);
+  }
   return check_launch(cudaGetLastError());
 }
 

@@ -6,6 +6,7 @@
 #pragma once
 
 #include "adjoint.cuh"
+#include "adjoint_u.cuh"
 #include "assemble.cuh"
 #include "ukernel.cuh"
 
@@ -108,8 +109,9 @@ cudaError_t launch_adjoint(int D, int cls, const AdjArgs &a, int nblocks, cudaSt
     if (cls == 0) return launch_adjoint_one<P, 2, P + 1, interior_chunk(P, sizeof(R)), R>(a, nblocks, s);
     return launch_adjoint_one<P, 2, P *(P + 1), kBoundaryChunk, R>(a, nblocks, s);
   }
-  if (cls == 0) return launch_adjoint_one<P, 3, P + 1, interior_chunk(P, sizeof(R)), R>(a, nblocks, s);
-  return launch_adjoint_one<P, 3, P *(P + 1), kBoundaryChunk, R>(a, nblocks, s);
+  // 3D: the x1 stage per chunk into Ubar slots; launch_adjoint_u does the rest
+  if (cls == 0) return launch_adjoint_x1_one<P, interior_chunk(P, sizeof(R)), R>(a, nblocks, s);
+  return launch_adjoint_x1_one<P, kBoundaryChunk, R>(a, nblocks, s);
 }
 
 extern template cudaError_t launch_u<2, double>(const UArgs &, int, cudaStream_t);
@@ -148,5 +150,11 @@ extern template cudaError_t launch_adjoint<2, float>(int, int, const AdjArgs &, 
 extern template cudaError_t launch_adjoint<3, float>(int, int, const AdjArgs &, int, cudaStream_t);
 extern template cudaError_t launch_adjoint<2, dd>(int, int, const AdjArgs &, int, cudaStream_t);
 extern template cudaError_t launch_adjoint<3, dd>(int, int, const AdjArgs &, int, cudaStream_t);
+extern template cudaError_t launch_adjoint_u<2, double>(const AdjUArgs &, int, cudaStream_t);
+extern template cudaError_t launch_adjoint_u<3, double>(const AdjUArgs &, int, cudaStream_t);
+extern template cudaError_t launch_adjoint_u<2, float>(const AdjUArgs &, int, cudaStream_t);
+extern template cudaError_t launch_adjoint_u<3, float>(const AdjUArgs &, int, cudaStream_t);
+extern template cudaError_t launch_adjoint_u<2, dd>(const AdjUArgs &, int, cudaStream_t);
+extern template cudaError_t launch_adjoint_u<3, dd>(const AdjUArgs &, int, cudaStream_t);
 
 }  // namespace wq
