@@ -257,6 +257,9 @@ def main():
     ap.add_argument("--batch-patches", type=int, default=256,
                     help="patches of the batch variant (the workload is 256; fewer for profiling)")
     ap.add_argument("--batch-precs", default="fp64,df64,mixed", help="precisions of the batch variant")
+    ap.add_argument("--adjoint-workload", default="3d_p3_96",
+                    help="workload of the adjoint variant (the configuration is 3d_p3_96; smaller for profiling)")
+    ap.add_argument("--adjoint-precs", default="fp64,df64,mixed", help="precisions of the adjoint variant")
     ap.add_argument("--only", default=None,
                     help="comma list of variant groups to run: precisions, workloads, rules, adjoint, apply, "
                          "general, batch (default: all)")
@@ -617,12 +620,12 @@ def run_variants(args, wq, inputs, R, w, g, gd, cd, bands, sample, timed, stream
 
     # the adjoint (coefficient gradient of sum G*K + H*M) on the 96^3 cubic workload
     if want("adjoint"):
-        w3, g3, c3 = inputs.workload("3d_p3_96")
+        w3, g3, c3 = inputs.workload(args.adjoint_workload)
         R3 = wq.Rules(3, w3["p"], w3["nel"])
         gd3 = [torch.from_numpy(x).cuda() for x in g3]
         gen = torch.Generator(device="cuda").manual_seed(96)
-        adj = {"workload": "3d_p3_96", "ncoef": R3.ncoef}
-        for vp in ("fp64", "df64", "mixed"):
+        adj = {"workload": args.adjoint_workload, "ncoef": R3.ncoef}
+        for vp in args.adjoint_precs.split(","):
             vdt = torch.float32 if vp == "mixed" else torch.float64
             G = torch.randn((R3.rows, R3.band), dtype=vdt, device="cuda", generator=gen)
             H = torch.randn((R3.rows, R3.band), dtype=vdt, device="cuda", generator=gen)
@@ -647,7 +650,7 @@ def run_variants(args, wq, inputs, R, w, g, gd, cd, bands, sample, timed, stream
         st = wq.wq_status_check(R3.handle, wq._stream_handle(stream))
         if st != wq.WQ_OK:
             raise wq.WqError(st, "adjoint variant")
-        variants["adjoint_3d_p3_96"] = adj
+        variants["adjoint_" + args.adjoint_workload] = adj
         R3.close()
 
     # matrix-free apply y = M x, y = K x (the band never stored) and the load

@@ -58,11 +58,15 @@ template <int P, typename R> struct AdjULayout {
   static constexpr int UWA = 2 * kAUCols * NPAIR, UWB = 2 * kAUCols * NL * NB;
   static constexpr int UW = pad16<R>(UWA > UWB ? UWA : UWB);
   static constexpr int UB = kAULines * UW;
-  static constexpr int CK = pad16<R>(2 * CBAR);      // [k3][l1][l2][l3]
-  static constexpr int R_TOTAL = V3 + B3 + V2 + B2 + UB + CK;
+  static constexpr int TB = pad16<R>(2 * kAUCols * NL2 * NB);  // the lines' sum [k3][l1][l2][j3]
+  static constexpr int CK = pad16<R>(2 * CBAR);                 // [k3][l1][l2][l3]
+  static constexpr int R_TOTAL = V3 + B3 + V2 + B2 + UB + TB + CK;
   // int region: e3[LM], L2[kAULines], ok[kAULines], e2[kAULines][LM]
   static constexpr int I_TOTAL = LM + 2 * kAULines + kAULines * LM;
-  static constexpr size_t BYTES = sizeof(R) * (size_t)R_TOTAL + sizeof(int) * (size_t)I_TOTAL;
+  // the Ubar sources of each (line, column): up to two slot offsets, -1 for none
+  static constexpr int SRC = kAULines * kAUCols * 2;
+  static constexpr size_t BYTES =
+      sizeof(R) * (size_t)R_TOTAL + sizeof(long long) * (size_t)SRC + sizeof(int) * (size_t)I_TOTAL;
 };
 
 // c = sum_i u[O + i] v[i], i = 0..P.
@@ -108,8 +112,19 @@ __device__ __forceinline__ void adj_spread(R (&acc)[N], R x, const R *b, R y, co
   }
 }
 
+// Resident CTAs per SM the register allocation is sized for (four for
+// float, three for double and double-float).
+#ifndef WQ_ADJU_MIN_BLOCKS
+#define WQ_ADJU_MIN_BLOCKS 3
+#endif
+#ifndef WQ_ADJU_MIN_BLOCKS_F32
+#define WQ_ADJU_MIN_BLOCKS_F32 4
+#endif
+template <typename R> constexpr int adju_min_blocks() {
+  return sizeof(R) == 4 ? WQ_ADJU_MIN_BLOCKS_F32 : WQ_ADJU_MIN_BLOCKS;
+}
 template <int P, typename R>
-__global__ void __launch_bounds__(256) adjoint_u_kernel(const AdjUArgs A) {
+__global__ void __launch_bounds__(256, adju_min_blocks<R>()) adjoint_u_kernel(const AdjUArgs A) {
   using L = AdjULayout<P, R>;
   constexpr int NP = L::NP, NB = L::NB, NPAIR = L::NPAIR, LM = L::LM, NL = L::NL, NL2 = L::NL2;
   constexpr int NT = 256;
@@ -121,8 +136,10 @@ __global__ void __launch_bounds__(256) adjoint_u_kernel(const AdjUArgs A) {
   R *sV2 = sB3 + L::B3;
   R *sB2 = sV2 + L::V2;
   R *sUw = sB2 + L::B2;
-  R *sCk = sUw + L::UB;
-  int *sE3 = reinterpret_cast<int *>(smem_raw + sizeof(R) * (size_t)L::R_TOTAL);
+  R *sTb = sUw + L::UB;
+  R *sCk = sTb + L::TB;
+  long long *sSrc = reinterpret_cast<long long *>(smem_raw + sizeof(R) * (size_t)L::R_TOTAL);
+  int *sE3 = reinterpret_cast<int *>(sSrc + L::SRC);
   int *sL2 = sE3 + LM;
   int *sOk = sL2 + kAULines;
   int *sE2 = sOk + kAULines;
@@ -178,36 +195,58 @@ __global__ void __launch_bounds__(256) adjoint_u_kernel(const AdjUArgs A) {
       sOk[b] = 0;
     }
   }
-  // Ubar of the block's lines at its columns: the sum, in chunk order, of
-  // the slots whose window holds the column
+  // the chunk slots whose window holds each (line, column), in chunk order,
+  // as the offset of the column's u = 0 run (a column lies in at most two
+  // windows when the chunk length is at least P + 3; more sets kBitInternal)
+  if (tid < kAULines * kAUCols) {
+    const int b = tid / kAUCols, l1 = tid % kAUCols;
+    long long src0 = -1, src1 = -1;
+    int ns = 0;
+    const int r2 = r2a + b;
+    const long long line = (long long)lid0 + b;
+    if (b < nlines && l1 < ncols && line >= A.line_lo && line <= A.line_hi) {
+      const int col = l1a + l1;
+      const bool in2 = r2 >= P && r2 <= A.N[1] - 1;
+      const int T = (in2 && in3) ? A.T_int : A.T_bnd;
+      const int nch = (n1 + T - 1) / T;
+      const long long base = line * n1;
+      int chlo = (col - 2) / T - 1, chhi = (col + P) / T;
+      if (chlo < 0) chlo = 0;
+      if (chhi > nch - 1) chhi = nch - 1;
+      for (int ch = chlo; ch <= chhi; ch++) {
+        long long lo = (long long)ch * T, hi = lo + T;
+        if (hi > n1) hi = n1;
+        if (lo < A.row_begin - base) lo = A.row_begin - base;
+        if (hi > A.row_end - base) hi = A.row_end - base;
+        if (lo >= hi) continue;
+        const int ca = (int)lo - P > 0 ? (int)lo - P : 0;
+        const int cb = ((int)hi - 1 < N1 - 1 ? (int)hi - 1 : N1 - 1) + 3;
+        if (col < ca || col > cb) continue;
+        const long long off = (line * A.nch_max + ch) * A.ubar_slot + (long long)(col - ca) * NPAIR;
+        if (ns == 0) src0 = off;
+        else if (ns == 1) src1 = off;
+        else atomicOr(A.status, kBitInternal);
+        ns++;
+      }
+    }
+    sSrc[tid * 2] = src0;
+    sSrc[tid * 2 + 1] = src1;
+  }
+  __syncthreads();
+  // Ubar of the block's lines at its columns: the sum of those slots' values
   {
     const R *Ug = static_cast<const R *>(A.ubar);
     const long long total = (long long)n2 * A.n[2] * A.nch_max * A.ubar_slot;
+    const long long uoff = (long long)A.nl1max * NPAIR;
     for (int t = tid; t < kAULines * 2 * kAUCols * NPAIR; t += NT) {
       const int pr = t % NPAIR, l1 = (t / NPAIR) % kAUCols, u = (t / (NPAIR * kAUCols)) % 2;
       const int b = t / (NPAIR * kAUCols * 2);
       R v = r_zero<R>();
-      const int r2 = r2a + b;
-      const long long line = (long long)lid0 + b;
-      if (b < nlines && l1 < ncols && line >= A.line_lo && line <= A.line_hi) {
-        const int col = l1a + l1;
-        const bool in2 = r2 >= P && r2 <= A.N[1] - 1;
-        const int T = (in2 && in3) ? A.T_int : A.T_bnd;
-        const int nch = (n1 + T - 1) / T;
-        const long long base = line * n1;
-        int chlo = (col - 2) / T - 1, chhi = (col + P) / T;
-        if (chlo < 0) chlo = 0;
-        if (chhi > nch - 1) chhi = nch - 1;
-        for (int ch = chlo; ch <= chhi; ch++) {
-          long long lo = (long long)ch * T, hi = lo + T;
-          if (hi > n1) hi = n1;
-          if (lo < A.row_begin - base) lo = A.row_begin - base;
-          if (hi > A.row_end - base) hi = A.row_end - base;
-          if (lo >= hi) continue;
-          const int ca = (int)lo - P > 0 ? (int)lo - P : 0;
-          const int cb = ((int)hi - 1 < N1 - 1 ? (int)hi - 1 : N1 - 1) + 3;
-          if (col < ca || col > cb) continue;
-          const long long si = (line * A.nch_max + ch) * A.ubar_slot + ((long long)u * A.nl1max + (col - ca)) * NPAIR + pr;
+#pragma unroll
+      for (int k = 0; k < 2; k++) {
+        const long long sb = sSrc[(b * kAUCols + l1) * 2 + k];
+        if (sb >= 0) {
+          const long long si = sb + u * uoff + pr;
           if (check_range(A.status, si, 1, total)) v = r_add(v, Ug[si]);
         }
       }
@@ -283,22 +322,25 @@ __global__ void __launch_bounds__(256) adjoint_u_kernel(const AdjUArgs A) {
   }
   __syncthreads();
 
-  // ------------------------------------------------ the lines' sum, then x3 stage transposed
+  // ------------------------------------------------ the lines' sum (line order), items (k3, l1, l2, j3)
+  for (int t = tid; t < 2 * kAUCols * NL2 * NB; t += NT) {
+    const int j = t % NB, m = (t / NB) % NL2, l1 = (t / (NB * NL2)) % kAUCols, k3 = t / (NB * NL2 * kAUCols);
+    R v = r_zero<R>();
+    for (int b = 0; b < nlines; b++) {
+      const int r2 = r2a + b;
+      const int k = m - (((r2 - P) > 0 ? (r2 - P) : 0) - l2lo);
+      if (sOk[b] && k >= 0 && k < NL) v = r_add(v, sUw[b * L::UW + ((k3 * kAUCols + l1) * NL + k) * NB + j]);
+    }
+    sTb[t] = v;
+  }
+  __syncthreads();
+
+  // ------------------------------------------------ x3 stage transposed, items (k3, l1, l2)
   for (int t = tid; t < 2 * kAUCols * NL2; t += NT) {
     const int m = t % NL2, l1 = (t / NL2) % kAUCols, k3 = t / (NL2 * kAUCols);
     R tb[NB];
 #pragma unroll
-    for (int j = 0; j < NB; j++) tb[j] = r_zero<R>();
-    for (int b = 0; b < nlines; b++) {
-      if (!sOk[b]) continue;
-      const int r2 = r2a + b;
-      const int db = ((r2 - P) > 0 ? (r2 - P) : 0) - l2lo;
-      const int k = m - db;
-      if (k < 0 || k >= NL) continue;
-      const R *src = &sUw[b * L::UW + ((k3 * kAUCols + l1) * NL + k) * NB];
-#pragma unroll
-      for (int j = 0; j < NB; j++) tb[j] = r_add(tb[j], src[j]);
-    }
+    for (int j = 0; j < NB; j++) tb[j] = sTb[t * NB + j];
     R cb[NL];
 #pragma unroll
     for (int j = 0; j < NL; j++) cb[j] = r_zero<R>();

@@ -1,4 +1,5 @@
-// Range checks of the checked build.  Compiled with -DWQ_CHECKED=1 (see
+// The status bits the kernels raise, and the range checks of the checked
+// build.  Compiled with -DWQ_CHECKED=1 (see
 // build.build's extra_nvcc), every guarded global access first checks that
 // [off, off + n) lies inside its buffer of `total` elements; a failed check
 // sets kBitChecked in the call's status word (wq_status_check then returns
@@ -10,7 +11,10 @@
 
 namespace wq {
 
-constexpr unsigned kBitChecked = 8u;
+constexpr unsigned kBitGeometry = 1u;
+constexpr unsigned kBitNonFinite = 2u;
+constexpr unsigned kBitInternal = 4u;  // a kernel met a size it was not built for
+constexpr unsigned kBitChecked = 8u;   // a failed range check of the checked build
 
 __device__ __forceinline__ bool check_range(unsigned *status, long long off, long long n, long long total) {
 #if defined(WQ_CHECKED) && WQ_CHECKED

@@ -31,11 +31,7 @@ constexpr int kMaxNel = 1 << 16;
 // Rule modes (wq_rules_build flags): the method, and the two comparison rules.
 constexpr int kModeWQ = 0, kModeGL = 1, kModeNC = 2;
 
-// Status bits raised by the kernels.
-constexpr unsigned kBitGeometry = 1u;
-constexpr unsigned kBitNonFinite = 2u;
-constexpr unsigned kBitInternal = 4u;  // a kernel met a size it was not built for (nothing written)
-// 8u: a failed range check of the checked build (kBitChecked, checked.cuh)
+// Status bits raised by the kernels: checked.cuh.
 
 // One direction and one kind (mass or stiffness) of the 1D row rules.
 // Point q of row r lies in element elem[q]; the p+1 B-splines acting there
