@@ -361,14 +361,21 @@ wq_status wq_assemble_load(const wq_rules *rules, const double *const *geom, con
  *              for WQ_FP64 and WQ_DF64, float for WQ_MIXED); either may be
  *              NULL (a zero weight);
  *   grad       device, prod(nel_a + 3) doubles, x fastest; overwritten.
- * Each chunk of rows writes its block of the gradient to its own slot of a
- * scratch array; a second kernel then sums, for every coefficient, the blocks
- * of the chunks that touch it in a fixed order, so repeated calls on the same
- * inputs return the same bits.  The scratch (FP64, about 50 values per row
- * of a 3D cubic mesh) belongs to the rules object: the first call that needs
- * it allocates it, a later call with more rows or other chunking may replace
- * it (synchronising `stream` first), and wq_rules_free releases it; the call
- * returns WQ_ERR_OOM if that allocation fails.
+ * Every partial result goes to its own slot of a scratch array and is summed
+ * in a fixed order, never by atomics, so repeated calls on the same inputs
+ * return the same bits: in 2D each chunk of rows writes its block of the
+ * gradient and a second kernel adds, per coefficient, the blocks that touch
+ * it; in 3D each chunk writes the gradient of its partial contractions
+ * (Ubar), a second kernel takes the x2 and x3 stages per block of 8 lines of
+ * a plane and 4 coefficient columns (summing the chunks of a column in chunk
+ * order and the block's lines in line order), and a third adds the blocks
+ * per coefficient.  The scratch belongs to the rules object (3D cubic: about
+ * 180 values of the arithmetic type per row, 1.5 GB at 96^3 in FP64): the
+ * first call that needs it allocates it, a later call with more rows or
+ * other chunking may replace it (synchronising `stream` first), and
+ * wq_rules_free releases it; the call returns WQ_ERR_OOM if that allocation
+ * fails, and WQ_ERR_UNSUPPORTED (from wq_status_check) if a build's chunk
+ * lengths are below p + 3 rows.
  * The same row-range, device and stream rules as the forward calls apply;
  * an empty range, or G and H both NULL, gives grad = 0.
  */

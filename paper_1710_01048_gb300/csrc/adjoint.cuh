@@ -2,22 +2,25 @@
 //   J(c) = sum_rows sum_band G .* K(c) + H .* M(c)
 // with respect to the coefficients C of the cubic spline c.  Every band entry
 // is linear in C, so dJ/dC = A^T applied to (G, H), where A is the forward
-// map of rows_kernel.  Per chunk of a line of rows the forward map factors as
-//   C block --(phase A: x3 then x2 stages)--> U --(phase B: x1 stage)--> bands,
+// map of the row kernels.  The forward map factors as
+//   C --(x3 then x2 stages)--> U --(x1 stage, per row)--> bands,
 // and the adjoint runs the transposed stages in reverse order:
-//   1. x1 stage transposed, per row and band fibre (j2, j3):
+//   1. x1 stage transposed, per chunk of a line's rows and band fibre:
 //        yM[q] = sum_j1 H[j1] V1M[q][j1],  yK[q] = sum_j1 G[j1] V1M[q][j1],
 //        yS[q] = sum_j1 G[j1] V1S[q][j1]
 //      accumulated into Ubar0[l1] += b1M[q][l1] yM[q] + b1S[q][l1] yS[q] and
 //      Ubar1[l1] += b1M[q][l1] yK[q]: each thread takes one fibre of four
 //      consecutive rows and keeps its columns in registers, and the threads'
-//      windows are added to Ubar in three ordered rounds.
-//   2. x2 then x3 stages transposed, one warp per coefficient column, giving
-//      the chunk's block of dJ/dC, stored in the chunk's own slot of a
-//      scratch array ([l3][l2][l1] from the block's first coefficient).
-// adjoint_gather_kernel then forms each coefficient's gradient as the sum of
-// the blocks of the chunks that touch it, in a fixed order (x3 row, x2 row,
-// chunk), so the result does not depend on the order in which CTAs ran.
+//      windows are added to Ubar in three ordered rounds (adj_x1_stage).
+//   2. 2D (adjoint_kernel, in the same CTA): the x2 stage transposed, one warp
+//      per coefficient column, giving the chunk's block of dJ/dC in its own
+//      slot of a scratch array; adjoint_gather_kernel adds the blocks of the
+//      chunks that touch each coefficient in a fixed order.
+//      3D (adjoint_x1_kernel): the chunk's Ubar goes to its own slot;
+//      adjoint_u_kernel (adjoint_u.cuh) runs the x2 and x3 stages transposed
+//      once per block of lines and columns, adjoint_gather3_kernel adds the
+//      blocks in a fixed order.
+// No step depends on the order in which CTAs ran.
 #pragma once
 
 #include "assemble.cuh"
@@ -203,9 +206,10 @@ template <typename R> constexpr int adj_min_blocks() {
 }
 template <int P, int D, int LM, int TMAX, typename R>
 __global__ void __launch_bounds__(32 * kRowsWarps, adj_min_blocks<R>()) adjoint_kernel(const AdjArgs AA) {
+  static_assert(D == 2, "3D runs adjoint_x1_kernel and adjoint_u_kernel");
   using L = AdjLayout<P, D, LM, TMAX, R>;
   const RowsArgs &A = AA.rows;
-  constexpr int NP = L::NP, NB = L::NB, NT = L::NT, NW = L::NW, NL = L::NL, NL1 = L::NL1;
+  constexpr int NP = L::NP, NB = L::NB, NT = L::NT, NW = L::NW, NL1 = L::NL1;
   constexpr int NPAIR = L::NPAIR;
   constexpr bool INNER_GAUSS = (LM == P + 1);
 
@@ -293,8 +297,8 @@ __global__ void __launch_bounds__(32 * kRowsWarps, adj_min_blocks<R>()) adjoint_
     for (int i = 0; i < 4; i++) sB1[(kind * L::MAXPTS1 + q) * 4 + i] = Bg[(size_t)gq * 4 + i];
     if (kind == 0) sE1[q] = A.elem[0][0][p1lo + q];
   }
-  const int L2 = L23[0], L3 = L23[1];
-  const int nl2 = nl23[0], nl3 = (D == 3) ? nl23[1] : 1;
+  const int L2 = L23[0];
+  const int nl2 = nl23[0];
   __syncthreads();
 
   // ------------------------------------------------ 1. x1 stage transposed, register windows
@@ -309,101 +313,12 @@ __global__ void __launch_bounds__(32 * kRowsWarps, adj_min_blocks<R>()) adjoint_
   static_assert(NPAIR == ((D == 3) ? NB * NB : NB), "fibres per row");
   adj_x1_stage<P, D, L::MAXPTS1, NL1, NT, R>(AA, sV1, sB1, sE1, sOff1, sUb, a, T, base, l1lo, nl1);
 
-  // ------------------------------------------------ 2. x2, x3 stages transposed, warp per column
+  // ------------------------------------------------ 2. x2 stage transposed, warp per column
   // this chunk's slot of the block scratch
   const long long chunk_slot = ((long long)line * AA.nch_max + ch) * AA.blk;
   R *wq = sW + warp * L::WS;  // Cqbar
-  R *wt = wq + L::WQ;         // T3bar
-  R *wz = wt + L::WT;         // Zbar
   for (int l1 = warp; l1 < nl1; l1 += NW) {
-    R cb[2];  // this lane's block entries (l2, l3) = lane, lane + 32
-    if constexpr (D == 3) {
-      // Cqbar[c][q2][j3] = sum_j2 Ubar[u(c)][l1][j3*NB+j2] V2_{k2(c)}[q2][j2 - o2];
-      // c = 0: (M, M) from Ubar0 with V2M; 1: (S, M) from Ubar1 with V2S; 2: (M, S) from Ubar1 with V2M
-      for (int t = lane; t < 3 * LM * NB; t += 32) {
-        const int j3 = t % NB, q2 = (t / NB) % LM, c = t / (NB * LM);
-        if (q2 < L2) {
-          const R *ub = (c == 0 ? Ub0 : Ub1) + l1 * NPAIR + j3 * NB;
-          const int k2 = (c == 1) ? 1 : 0;
-          const R *vd = INNER_GAUSS ? nullptr : &sV23d[(k2 * LM + q2) * NB];
-          R s = r_zero<R>();
-          if constexpr (INNER_GAUSS) {
-#pragma unroll
-            for (int i = 0; i < NP; i++) s = r_fma(ub[q2 + i], sV23[(k2 * LM + q2) * NP + i], s);
-          } else {
-#pragma unroll
-            for (int j = 0; j < NB; j++) s = r_fma(ub[j], vd[j], s);
-          }
-          wq[t] = s;
-        }
-      }
-      __syncwarp();
-      // T3bar[k3][l2][j3] = sum_{c: kind3(c) = k3} sum_q2 Cqbar[c][q2][j3] b2_{k2(c)}[q2][l2 - e2(q2)]
-      for (int t = lane; t < 2 * NL * NB; t += 32) {
-        const int j3 = t % NB, l2 = (t / NB) % NL, k3 = t / (NB * NL);
-        R s = r_zero<R>();
-        if (l2 < nl2) {
-          for (int q2 = 0; q2 < L2; q2++) {
-            const int i = l2 - (sE23[q2] - l23lo[0]);
-            if (i >= 0 && i < 4) {
-              if (k3 == 0) {
-                s = r_fma(wq[(0 * LM + q2) * NB + j3], sB23[((0 * 2 + 0) * LM + q2) * 4 + i], s);
-                s = r_fma(wq[(1 * LM + q2) * NB + j3], sB23[((0 * 2 + 1) * LM + q2) * 4 + i], s);
-              } else {
-                s = r_fma(wq[(2 * LM + q2) * NB + j3], sB23[((0 * 2 + 0) * LM + q2) * 4 + i], s);
-              }
-            }
-          }
-        }
-        wt[t] = s;
-      }
-      __syncwarp();
-      // Zbar[k3][l2][q3] = sum_j3 T3bar[k3][l2][j3] V3_k3[q3][j3 - o3]
-      for (int t = lane; t < 2 * NL * LM; t += 32) {
-        const int q3 = t % LM, l2 = (t / LM) % NL, k3 = t / (LM * NL);
-        if (q3 < L3 && l2 < nl2) {
-          const R *tb = &wt[(k3 * NL + l2) * NB];
-          R s = r_zero<R>();
-          if constexpr (INNER_GAUSS) {
-#pragma unroll
-            for (int i = 0; i < NP; i++) s = r_fma(tb[q3 + i], sV23[((1 * 2 + k3) * LM + q3) * NP + i], s);
-          } else {
-            const R *vd = &sV23d[((1 * 2 + k3) * LM + q3) * NB];
-#pragma unroll
-            for (int j = 0; j < NB; j++) s = r_fma(tb[j], vd[j], s);
-          }
-          wz[t] = s;
-        }
-      }
-      __syncwarp();
-      // Cbar[l2][l3] = sum_k3 sum_q3 Zbar[k3][l2][q3] b3_k3[q3][l3 - e3(q3)]
-#pragma unroll
-      for (int s2 = 0; s2 < 2; s2++) {
-        const int t = lane + 32 * s2;
-        const int l3 = t % NL, l2 = t / NL;
-        R s = r_zero<R>();
-        if (t < NL * NL && l2 < nl2 && l3 < nl3) {
-          for (int q3 = 0; q3 < L3; q3++) {
-            const int i = l3 - (sE23[LM + q3] - l23lo[1]);
-            if (i >= 0 && i < 4) {
-              s = r_fma(wz[(0 * NL + l2) * LM + q3], sB23[((1 * 2 + 0) * LM + q3) * 4 + i], s);
-              s = r_fma(wz[(1 * NL + l2) * LM + q3], sB23[((1 * 2 + 1) * LM + q3) * 4 + i], s);
-            }
-          }
-        }
-        cb[s2] = s;
-      }
-#pragma unroll
-      for (int s2 = 0; s2 < 2; s2++) {
-        const int t = lane + 32 * s2;
-        const int l3 = t % NL, l2 = t / NL;
-        const long long pidx = chunk_slot + ((long long)l3 * NL + l2) * AA.nl1max + l1;
-        if (t < NL * NL && l2 < nl2 && l3 < nl3 &&
-            check_range(A.status, pidx, 1, (long long)A.n[1] * A.n[2] * AA.nch_max * AA.blk)) {
-          AA.partial[pidx] = r_to_double(cb[s2]);
-        }
-      }
-    } else {
+    {
       // Cqbar[c][q2] = sum_j2 Ubar[c][l1][j2] V2_c[q2][j2 - o2], c = kind2
       for (int t = lane; t < 2 * LM; t += 32) {
         const int q2 = t % LM, c = t / LM;
@@ -436,7 +351,6 @@ __global__ void __launch_bounds__(32 * kRowsWarps, adj_min_blocks<R>()) adjoint_
         const long long pidx = chunk_slot + (long long)l2 * AA.nl1max + l1;
         if (check_range(A.status, pidx, 1, (long long)A.n[1] * AA.nch_max * AA.blk)) AA.partial[pidx] = r_to_double(s);
       }
-      (void)cb;
     }
     __syncwarp();
   }

@@ -109,7 +109,6 @@ __device__ __forceinline__ void u_block(const UArgs &A, int bid, unsigned char *
   int *sO3 = sE3 + LM;
   int *sL2 = sO3 + LM;
   int *sE2 = sL2 + kULines;
-  int *sO2 = sE2 + kULines * LM;
 
   const int tid = threadIdx.x;
   const int n2 = A.n[1], nc1 = A.nc[0], nc2 = A.nc[1];
