@@ -388,10 +388,11 @@ wq_status wq_assemble_adjoint(const wq_rules *rules, const double *const *geom, 
  * wq_assemble_mass_stiffness, with the weighted Gaussian rules of Sec. 3).
  * The paper treats one patch; the batch is a throughput form of the same
  * computation.  A plan (wq_batch) holds the patches' work lists, folded
- * tables and partial-contraction buffers, and a CUDA graph of one batched
- * geometry fold and two persistent launches (the partial contractions of
- * every patch, then the rows of every patch) whose CTAs take work items from
- * global counters.  Its results are bit-identical to one
+ * tables, converted coefficients and partial-contraction buffers, and a CUDA
+ * graph of one batched geometry fold, one batched coefficient check and
+ * conversion, and per degree two persistent launches (the partial
+ * contractions of that degree's patches, then their rows) whose CTAs take
+ * work items from global counters.  Its results are bit-identical to one
  * wq_assemble_mass_stiffness call per patch with the same precision.
  */
 typedef struct wq_batch wq_batch;

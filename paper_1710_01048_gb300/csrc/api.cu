@@ -56,19 +56,11 @@ __global__ void fold_kernel(const FoldArgs A) {
 // FP64 mode reads the caller's array directly).
 __global__ void coef_prepare_kernel(const double *__restrict__ c, size_t n, int prec, float *c32, float2 *cdd,
                                     unsigned *status) {
-  unsigned bad = 0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double v = c[i];
-    if (!isfinite(v)) bad = 1;
-    if (prec == WQ_MIXED) {
-      c32[i] = (float)v;
-    } else if (prec == WQ_DF64) {
-      const float h = (float)v;
-      cdd[i] = make_float2(h, (float)(v - (double)h));
-    }
-  }
-  bad = __reduce_or_sync(0xffffffffu, bad);
-  if (bad && (threadIdx.x & 31) == 0) atomicOr(status, wq::kBitNonFinite);
+  unsigned bits = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    bits |= wq::coef_point(c, i, prec, c32, cdd);
+  bits = __reduce_or_sync(0xffffffffu, bits);
+  if (bits && (threadIdx.x & 31) == 0) atomicOr(status, bits);
 }
 
 // dJ/dC of every coefficient: the sum, over the lines (x3 row ascending,

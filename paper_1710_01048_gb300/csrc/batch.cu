@@ -48,6 +48,32 @@ __global__ void batch_fold_kernel(const BFold *__restrict__ segs, int nseg, int 
 }
 
 
+// One patch's coefficients for the batched preparation: checked, and
+// converted to the arithmetic type (FP64 reads the caller's array).
+struct BCoef {
+  const double *c;
+  float *c32;
+  float2 *cdd;
+  long long start, n;
+};
+
+__global__ void batch_coef_kernel(const BCoef *__restrict__ segs, int nseg, long long total, int prec,
+                                  unsigned *status) {
+  unsigned bits = 0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (segs[mid].start <= t) lo = mid; else hi = mid - 1;
+    }
+    const BCoef &S = segs[lo];
+    bits |= wq::coef_point(S.c, (size_t)(t - S.start), prec, S.c32, S.cdd);
+  }
+  bits = __reduce_or_sync(0xffffffffu, bits);
+  if ((threadIdx.x & 31) == 0 && bits) atomicOr(status, bits);
+}
+
 }  // namespace
 
 struct wq_batch {
@@ -61,6 +87,9 @@ struct wq_batch {
   void *dev_block = nullptr;
   BFold *dev_fold = nullptr;
   int nfold = 0, fold_total = 0;
+  BCoef *dev_coef = nullptr;  // the patches' coefficient preparation
+  int ncoefseg = 0;
+  long long coef_total = 0;
   // segments, degree 3 first; share[d] (d = p - 2) describes degree p's part
   wq::BatchUSeg *dev_usegs = nullptr;
   wq::BatchSeg *dev_segs = nullptr;
@@ -214,6 +243,11 @@ wq_status enqueue(const wq_batch *B, cudaStream_t s) {
     batch_fold_kernel<<<blocks, 256, 0, s>>>(B->dev_fold, B->nfold, B->fold_total, B->dev_status);
     if (cudaGetLastError() != cudaSuccess) return WQ_ERR_CUDA;
   }
+  if (B->coef_total > 0) {
+    const int blocks = (int)std::min<long long>((B->coef_total + 255) / 256, (long long)B->nsm * 8);
+    batch_coef_kernel<<<blocks, 256, 0, s>>>(B->dev_coef, B->ncoefseg, B->coef_total, (int)B->prec, B->dev_status);
+    if (cudaGetLastError() != cudaSuccess) return WQ_ERR_CUDA;
+  }
   if (cudaMemsetAsync(B->dev_counter, 0, 4 * sizeof(unsigned), s) != cudaSuccess) return WQ_ERR_CUDA;
   const bool both = B->share[0].nseg > 0 && B->share[1].nseg > 0;
   cudaError_t e = cudaSuccess;
@@ -358,6 +392,8 @@ wq_status wq_batch_create(const wq_patch *patches, int npatch, wq_precision prec
   size_t total = 0;
   const size_t fold_off = total;
   total += align_up(sizeof(BFold) * 6 * (size_t)npatch);
+  const size_t coefseg_off = total;
+  total += align_up(sizeof(BCoef) * (size_t)npatch);
   const size_t useg_off = total;
   total += align_up(sizeof(wq::BatchUSeg) * (size_t)npatch);
   const size_t seg_off = total;
@@ -365,7 +401,7 @@ wq_status wq_batch_create(const wq_patch *patches, int npatch, wq_precision prec
   const size_t cnt_off = total;
   total += align_up(5 * sizeof(unsigned));
   const size_t elem_bytes = prec == WQ_MIXED ? sizeof(float) : sizeof(double);
-  std::vector<size_t> tab_off(6 * (size_t)npatch), u_off(npatch);
+  std::vector<size_t> tab_off(6 * (size_t)npatch), u_off(npatch), c_off(npatch, 0);
   for (int i = 0; i < npatch; i++) {
     const wq_rules *R = patches[i].rules;
     const size_t np = (size_t)R->p + 1;
@@ -379,6 +415,11 @@ wq_status wq_batch_create(const wq_patch *patches, int npatch, wq_precision prec
     const size_t nb = 2 * (size_t)R->p + 1;
     u_off[i] = total;
     total += align_up((size_t)R->n[1] * R->n[2] * 2 * R->nc[0] * nb * nb * elem_bytes);
+    // the patch's coefficients in the arithmetic type (FP64 reads the caller's)
+    if (patches[i].coef && prec != WQ_FP64) {
+      c_off[i] = total;
+      total += align_up((size_t)R->nc[0] * R->nc[1] * R->nc[2] * (prec == WQ_MIXED ? sizeof(float) : sizeof(float2)));
+    }
   }
   if (cudaMalloc(&B->dev_block, total) != cudaSuccess) {
     cudaGetLastError();
@@ -387,6 +428,8 @@ wq_status wq_batch_create(const wq_patch *patches, int npatch, wq_precision prec
   }
   char *base = static_cast<char *>(B->dev_block);
   B->dev_fold = reinterpret_cast<BFold *>(base + fold_off);
+  B->dev_coef = reinterpret_cast<BCoef *>(base + coefseg_off);
+  std::vector<BCoef> coefs;
   B->dev_usegs = reinterpret_cast<wq::BatchUSeg *>(base + useg_off);
   B->dev_segs = reinterpret_cast<wq::BatchSeg *>(base + seg_off);
   B->dev_counter = reinterpret_cast<unsigned *>(base + cnt_off);
@@ -435,7 +478,7 @@ wq_status wq_batch_create(const wq_patch *patches, int npatch, wq_precision prec
       ra.nc[a] = R->nc[a];
     }
     ra.coef = P.coef;
-    ra.coefR = nullptr;  // checked and converted inside the partial-contraction kernel
+    ra.coefR = nullptr;  // the row kernel reads U, not the coefficients
     ra.M = P.M;
     ra.K = P.K;
     ra.row_begin = 0;
@@ -457,6 +500,18 @@ wq_status wq_batch_create(const wq_patch *patches, int npatch, wq_precision prec
     }
     ua.coef = P.coef;
     ua.coefR = nullptr;
+    if (P.coef) {
+      const long long nco = (long long)R->nc[0] * R->nc[1] * R->nc[2];
+      BCoef C;
+      C.c = P.coef;
+      C.c32 = prec == WQ_MIXED ? reinterpret_cast<float *>(base + c_off[i]) : nullptr;
+      C.cdd = prec == WQ_DF64 ? reinterpret_cast<float2 *>(base + c_off[i]) : nullptr;
+      C.start = B->coef_total;
+      C.n = nco;
+      B->coef_total += nco;
+      coefs.push_back(C);
+      ua.coefR = prec == WQ_FP64 ? (const void *)P.coef : (const void *)(base + c_off[i]);
+    }
     ua.U = base + u_off[i];
     ua.line_lo = 0;
     ua.line_hi = R->n[1] * R->n[2] - 1;
@@ -467,7 +522,10 @@ wq_status wq_batch_create(const wq_patch *patches, int npatch, wq_precision prec
   }
   B->nfold = (int)folds.size();
   B->fold_total = start;
+  B->ncoefseg = (int)coefs.size();
   bool ok = cudaMemcpy(B->dev_fold, folds.data(), folds.size() * sizeof(BFold), cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && (coefs.empty() || cudaMemcpy(B->dev_coef, coefs.data(), coefs.size() * sizeof(BCoef),
+                                          cudaMemcpyHostToDevice) == cudaSuccess);
   ok = ok && cudaMemset(B->dev_counter, 0, 5 * sizeof(unsigned)) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&B->aux_stream, cudaStreamNonBlocking) == cudaSuccess;

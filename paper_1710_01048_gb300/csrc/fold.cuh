@@ -36,4 +36,19 @@ __device__ __forceinline__ unsigned fold_point(int q, int np, int kind, const in
   return bits;
 }
 
+// Coefficient i of the cubic coefficient spline in the arithmetic type of
+// the call (float for WQ_MIXED, a double-float pair for WQ_DF64; WQ_FP64
+// reads the double array itself); returns the non-finite bit for NaN/Inf.
+// Shared by the single-mesh and the batched preparation kernels.
+__device__ __forceinline__ unsigned coef_point(const double *c, size_t i, int prec, float *c32, float2 *cdd) {
+  const double v = c[i];
+  if (prec == WQ_MIXED) {
+    c32[i] = (float)v;
+  } else if (prec == WQ_DF64) {
+    const float h = (float)v;
+    cdd[i] = make_float2(h, (float)(v - (double)h));
+  }
+  return isfinite(v) ? 0u : kBitNonFinite;
+}
+
 }  // namespace wq
