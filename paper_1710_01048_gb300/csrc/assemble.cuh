@@ -456,6 +456,51 @@ __device__ __forceinline__ void rows_phase_b(const RowsArgs &A, const R *sU, con
             oM[j] = dd2_first(aMK[j]);
             oK[j] = dd2_second(aMK[j]);
           }
+        } else if constexpr (std::is_same<R, float>::value && DO_M && DO_K && NP == 4) {
+          // float with M and K side by side in packed pairs: (y_M, y_K) share
+          // b1M and (A_M, A_K) share V1M, one fma.rn.f32x2 each; y_S and the
+          // V1S y_S update stay scalar.  Every lane performs the scalar path's
+          // multiply-adds in its order (16 instead of 24 instructions a point).
+          const unsigned long long z = f2_pack(A.zero, A.zero);
+          unsigned long long w01[NP + 3], aMK[NB];
+          float w0[NP + 3];
+#pragma unroll
+          for (int i = 0; i < NP + 3; i++) {
+            w0[i] = U0[(kb + i) * LS + pr];
+            w01[i] = f2_pack(w0[i], U1[(kb + i) * LS + pr]);
+          }
+#pragma unroll
+          for (int j = 0; j < NB; j++) aMK[j] = z;
+          const float4 *b4m = reinterpret_cast<const float4 *>(&sB1[(0 * MAXPTS1 + q0) * 4]);
+          const float4 *b4s = reinterpret_cast<const float4 *>(&sB1[(1 * MAXPTS1 + q0) * 4]);
+          const float4 *v4m = reinterpret_cast<const float4 *>(&sV1[(0 * MAXPTS1 + q0) * NP]);
+          const float4 *v4s = reinterpret_cast<const float4 *>(&sV1[(1 * MAXPTS1 + q0) * NP]);
+#pragma unroll
+          for (int q = 0; q < NP; q++) {
+            const float4 xm = b4m[q], xs = b4s[q], ym = v4m[q], ys4 = v4s[q];
+            const float bm[4] = {xm.x, xm.y, xm.z, xm.w}, bs[4] = {xs.x, xs.y, xs.z, xs.w};
+            const float vm[4] = {ym.x, ym.y, ym.z, ym.w}, vs[4] = {ys4.x, ys4.y, ys4.z, ys4.w};
+            unsigned long long yMK = z;
+            float ys = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+              yMK = f2_fma(f2_pack(bm[i], bm[i]), w01[q + i], yMK);
+              ys = fmaf(bs[i], w0[q + i], ys);
+            }
+#pragma unroll
+            for (int i = 0; i < NP; i++) {
+              float m, k;
+              f2_unpack(f2_fma(f2_pack(vm[i], vm[i]), yMK, aMK[q + i]), m, k);
+              aMK[q + i] = f2_pack(m, fmaf(vs[i], ys, k));
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < NB; j++) {
+            float m, k;
+            f2_unpack(aMK[j], m, k);
+            oM[j] = m;
+            oK[j] = k;
+          }
         } else {
         R w0[NP + 3], w1[NP + 3], aM[NB], aK[NB];
 #pragma unroll
