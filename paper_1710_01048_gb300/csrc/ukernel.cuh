@@ -313,6 +313,48 @@ __device__ __forceinline__ void u_block(const UArgs &A, int bid, unsigned char *
           tm[i] = t3m[(e0 + i) * NB];
           ts[i] = t3s[(e0 + i) * NB];
         }
+        if constexpr (std::is_same<R, float>::value) {
+          // float: the pairs that share a table entry as packed fma.rn.f32x2,
+          // (s0, s2) += (tm, ts) b2M and (u0, u1) += (c0, c2) V2M, each lane
+          // in the scalar order below (u1 takes all of (S, M) first)
+          const unsigned long long z = f2_pack(A.zero, A.zero);
+          unsigned long long c02[NP];
+          float c1f[NP];
+#pragma unroll
+          for (int q2 = 0; q2 < NP; q2++) {
+            float bm[4], bs[4];
+            load_row4(bm, &b2[(0 * LM + q2) * 4]);
+            load_row4(bs, &b2[(1 * LM + q2) * 4]);
+            unsigned long long s02 = z;
+            float s1 = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+              s02 = f2_fma(f2_pack(tm[q2 + i], ts[q2 + i]), f2_pack(bm[i], bm[i]), s02);
+              s1 = fmaf(tm[q2 + i], bs[i], s1);
+            }
+            c02[q2] = s02;
+            c1f[q2] = s1;
+          }
+#pragma unroll
+          for (int q2 = 0; q2 < NP; q2++) {
+            float vs[NP];
+            load_row<NP>(vs, &v2[(1 * LM + q2) * NP]);
+#pragma unroll
+            for (int i = 0; i < NP; i++) u1[q2 + i] = fmaf(c1f[q2], vs[i], u1[q2 + i]);
+          }
+          unsigned long long u01[NB];
+#pragma unroll
+          for (int j = 0; j < NB; j++) u01[j] = f2_pack(A.zero, u1[j]);
+#pragma unroll
+          for (int q2 = 0; q2 < NP; q2++) {
+            float vm[NP];
+            load_row<NP>(vm, &v2[(0 * LM + q2) * NP]);
+#pragma unroll
+            for (int i = 0; i < NP; i++) u01[q2 + i] = f2_fma(c02[q2], f2_pack(vm[i], vm[i]), u01[q2 + i]);
+          }
+#pragma unroll
+          for (int j = 0; j < NB; j++) f2_unpack(u01[j], u0[j], u1[j]);
+        } else {
         R c0[NP], c1[NP], c2[NP];
 #pragma unroll
         for (int q2 = 0; q2 < NP; q2++) {
@@ -348,6 +390,7 @@ __device__ __forceinline__ void u_block(const UArgs &A, int bid, unsigned char *
         for (int q2 = 0; q2 < NP; q2++)
 #pragma unroll
           for (int i = 0; i < NP; i++) u1[q2 + i] = r_fma(c2[q2], vm[q2][i], u1[q2 + i]);
+        }
       } else {
         // boundary line: per point, (S, M) then (M, S)
         for (int q2 = 0; q2 < L2; q2++) {
