@@ -241,15 +241,12 @@ __global__ void __launch_bounds__(256, adju_min_blocks<R>()) adjoint_u_kernel(co
     for (int t = tid; t < kAULines * 2 * kAUCols * NPAIR; t += NT) {
       const int pr = t % NPAIR, l1 = (t / NPAIR) % kAUCols, u = (t / (NPAIR * kAUCols)) % 2;
       const int b = t / (NPAIR * kAUCols * 2);
+      // the first source's value, plus the second's where the column has two
+      // (no addition of a zero: the FP64 pipe is this kernel's bound)
       R v = r_zero<R>();
-#pragma unroll
-      for (int k = 0; k < 2; k++) {
-        const long long sb = sSrc[(b * kAUCols + l1) * 2 + k];
-        if (sb >= 0) {
-          const long long si = sb + u * uoff + pr;
-          if (check_range(A.status, si, 1, total)) v = r_add(v, Ug[si]);
-        }
-      }
+      const long long sb0 = sSrc[(b * kAUCols + l1) * 2], sb1 = sSrc[(b * kAUCols + l1) * 2 + 1];
+      if (sb0 >= 0 && check_range(A.status, sb0 + u * uoff + pr, 1, total)) v = Ug[sb0 + u * uoff + pr];
+      if (sb1 >= 0 && check_range(A.status, sb1 + u * uoff + pr, 1, total)) v = r_add(v, Ug[sb1 + u * uoff + pr]);
       sUw[b * L::UW + (u * kAUCols + l1) * NPAIR + pr] = v;
     }
   }
@@ -326,10 +323,15 @@ __global__ void __launch_bounds__(256, adju_min_blocks<R>()) adjoint_u_kernel(co
   for (int t = tid; t < 2 * kAUCols * NL2 * NB; t += NT) {
     const int j = t % NB, m = (t / NB) % NL2, l1 = (t / (NB * NL2)) % kAUCols, k3 = t / (NB * NL2 * kAUCols);
     R v = r_zero<R>();
+    bool first = true;
     for (int b = 0; b < nlines; b++) {
       const int r2 = r2a + b;
       const int k = m - (((r2 - P) > 0 ? (r2 - P) : 0) - l2lo);
-      if (sOk[b] && k >= 0 && k < NL) v = r_add(v, sUw[b * L::UW + ((k3 * kAUCols + l1) * NL + k) * NB + j]);
+      if (sOk[b] && k >= 0 && k < NL) {
+        const R x = sUw[b * L::UW + ((k3 * kAUCols + l1) * NL + k) * NB + j];
+        v = first ? x : r_add(v, x);
+        first = false;
+      }
     }
     sTb[t] = v;
   }
