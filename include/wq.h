@@ -514,7 +514,7 @@ wq_status wq_status_check(const wq_rules *rules, void *stream);
  * cudaFree or other allocating call; it copies the host tables into the
  * array with cudaMemcpyAsync on `stream` every time.  The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.
+ * that device current.
  * All calls on a device share the one array, which keeps the last call's
  * contents: calls whose work overlaps on the GPU (other streams, other host
  * threads) race and must be serialised by the caller.
