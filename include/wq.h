@@ -374,7 +374,7 @@ wq_status wq_assemble_load(const wq_rules *rules, const double *const *geom, con
  * first call that needs it allocates it, a later call with more rows or
  * other chunking may replace it (synchronising `stream` first), and
  * wq_rules_free releases it; the call returns WQ_ERR_OOM if that allocation
- * fails, and WQ_ERR_UNSUPPORTED (from wq_status_check) if a build's chunk
+ * fails, and WQ_ERR_UNSUPPORTED (from wq_status_check) if the library's compiled chunk
  * lengths are below p + 3 rows.
  * The same row-range, device and stream rules as the forward calls apply;
  * an empty range, or G and H both NULL, gives grad = 0.

@@ -312,9 +312,9 @@ wq_status apply_config(wq_batch *B, const int *cfg) {
 }
 
 // The autotuner cache's key: the GPU (name, compute capability, SMs), the
-// precision, the occupancy limits of this build's four kernels, the degree mix
-// and a hash (64-bit FNV-1a) of the patches' shapes in plan order; empty on
-// a CUDA error.
+// precision, the occupancy limits of the compiled library's four kernels,
+// the degree mix and a hash (64-bit FNV-1a) of the patches' shapes in plan
+// order; empty on a CUDA error.
 std::string cache_key(const wq_batch *B) {
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, B->device) != cudaSuccess) return std::string();
