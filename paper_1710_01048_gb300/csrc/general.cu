@@ -1015,6 +1015,23 @@ __global__ void __launch_bounds__(32 * WARPS) gm_rows_kernel(const GmArgs A) {
                    (L[0] - 1) + s2 * (L[1] - 1) + (DIM == 3 ? s3 * (L[2] - 1) : 0) + 1, A.fstride) ||
       !check_range(A.status, ob, NBAND, A.out_rows * NBAND))
     return;
+  // interior class in 3D: a lane's x3 stage item is the same (q1, q2, half) in
+  // every term, so the factors of the next term are loaded while the
+  // current one is contracted (the terms run in one contiguous range)
+  constexpr bool PF = DIM == 3 && LC0 && LC1 && LC2 && 2 * LC0 * LC1 <= 32;
+  const int t_first = A.M ? gstart[0] : gstart[1], t_end = A.K ? gstart[5] : gstart[1];
+  const bool pf_act = lane < 2 * LC0 * LC1;
+  const int pf_q1 = (lane >> 1) % (LC0 ? LC0 : 1), pf_q2 = (lane >> 1) / (LC0 ? LC0 : 1);
+  R fcur[PF ? LC2 : 1], fnxt[PF ? LC2 : 1];
+  auto load_f = [&](int ti, R (&v)[PF ? LC2 : 1]) {
+    if constexpr (PF) {
+      const R *f = static_cast<const R *>(A.F) + terms[ti].grid * A.fstride + off[0] + s2 * off[1] +
+                   s3 * (off[2] - A.slab_lo) + pf_q1 + s2 * pf_q2;
+#pragma unroll
+      for (int q3 = 0; q3 < LC2; q3++) v[q3] = pf_act ? f[s3 * q3] : R(0);
+    }
+  };
+  if (PF && t_first < t_end) load_f(t_first, fcur);
   for (int grp = 0; grp < 5; grp++) {
     if (grp == 0 ? !A.M : !A.K) continue;
 #pragma unroll U0
@@ -1029,6 +1046,27 @@ __global__ void __launch_bounds__(32 * WARPS) gm_rows_kernel(const GmArgs A) {
       if (DIM == 3) {
         const R *A3 = sA + aoff[2] + (tm.k[2] * LM2) * NBP;
         const R *F0 = F + off[0] + s2 * off[1] + s3 * (off[2] - A.slab_lo);
+        if constexpr (PF) {
+          if (ti + 1 < t_end) load_f(ti + 1, fnxt);
+          if (pf_act) {
+            const int c0 = (lane & 1) * H1;
+            R acc[H1];
+#pragma unroll
+            for (int h = 0; h < H1; h++) acc[h] = 0;
+#pragma unroll
+            for (int q3 = 0; q3 < LC2; q3++) {
+              const R *a = A3 + q3 * NBP + c0;
+#pragma unroll
+              for (int h = 0; h < H1; h++) acc[h] = fma(fcur[q3], a[h], acc[h]);
+            }
+            R *x = sX + (lane >> 1) * NB + c0;
+#pragma unroll
+            for (int h = 0; h < H1; h++)
+              if (c0 + h < NB) x[h] = acc[h];
+          }
+#pragma unroll
+          for (int q3 = 0; q3 < LC2; q3++) fcur[q3] = fnxt[q3];
+        } else
         // X: items (q1, q2, half of the x3 columns)
 #pragma unroll U01
         for (int it = lane; it < 2 * L[0] * L[1]; it += 32) {
