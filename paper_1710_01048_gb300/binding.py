@@ -555,11 +555,13 @@ class Batch:
     def config(self):
         c = (ctypes.c_int * 6)()
         _check(_lib().wq_batch_get_config(self.handle, c), "wq_batch_get_config")
-        return dict(chunk=c[0], u_ctas_per_sm=c[1], ctas_per_sm=c[2], order=c[3], max_u_ctas_per_sm=c[4],
+        return dict(chunk=c[0], u_ctas_per_sm=c[1], ctas_per_sm=c[2], schedule=c[3], max_u_ctas_per_sm=c[4],
                     max_ctas_per_sm=c[5])
 
-    def set_config(self, chunk, u_ctas_per_sm, ctas_per_sm, order):
-        c = (ctypes.c_int * 4)(chunk, u_ctas_per_sm, ctas_per_sm, order)
+    def set_config(self, chunk, u_ctas_per_sm, ctas_per_sm, schedule):
+        """schedule 0: the degree-2 kernels on a second stream beside the
+        degree-3 ones; 1: degree 3 then degree 2 on the launch stream."""
+        c = (ctypes.c_int * 4)(chunk, u_ctas_per_sm, ctas_per_sm, schedule)
         _check(_lib().wq_batch_set_config(self.handle, c), "wq_batch_set_config")
 
     def tune(self, reps=2, stream=None):

@@ -1,11 +1,11 @@
-"""Batched assembly (wq_batch_*): two persistent launches (partial
-contractions, rows) for many patches, replayed from a CUDA graph, with an
-autotuned launch configuration.
+"""Batched assembly (wq_batch_*): per degree two persistent launches
+(partial contractions, rows) for many patches, replayed from a CUDA graph,
+with an autotuned launch configuration.
 
 Every patch's bands must be bit-identical to a single-patch
 wq_assemble_mass_stiffness call in the same precision (the batch runs the
-same per-chunk arithmetic), whatever the chunk lengths, CTA count or item
-order; a few patches are also compared with the oracle."""
+same per-chunk arithmetic), whatever the chunk lengths, CTA counts or
+schedule; a few patches are also compared with the oracle."""
 import json
 
 import numpy as np
@@ -76,7 +76,7 @@ def test_batch_configurations_and_tuner(monkeypatch):
             K.fill_(float("nan"))
         B.set_config(*cfg)
         c = B.config
-        assert (c["chunk"], c["u_ctas_per_sm"], c["ctas_per_sm"], c["order"]) == cfg
+        assert (c["chunk"], c["u_ctas_per_sm"], c["ctas_per_sm"], c["schedule"]) == cfg
         B.launch()
         B.check()
         assert_matches_single(patches, "fp64")
@@ -96,7 +96,7 @@ def test_batch_configurations_and_tuner(monkeypatch):
 
 def _cfg(B):
     c = B.config
-    return [c["chunk"], c["u_ctas_per_sm"], c["ctas_per_sm"], c["order"]]
+    return [c["chunk"], c["u_ctas_per_sm"], c["ctas_per_sm"], c["schedule"]]
 
 
 def test_tuner_cache(tmp_path, monkeypatch):
