@@ -61,8 +61,8 @@ template <int P, typename R> struct AdjULayout {
   static constexpr int TB = pad16<R>(2 * kAUCols * NL2 * NB);  // the lines' sum [k3][l1][l2][j3]
   static constexpr int CK = pad16<R>(2 * CBAR);                 // [k3][l1][l2][l3]
   static constexpr int R_TOTAL = V3 + B3 + V2 + B2 + UB + TB + CK;
-  // int region: e3[LM], L2[kAULines], ok[kAULines], e2[kAULines][LM]
-  static constexpr int I_TOTAL = LM + 2 * kAULines + kAULines * LM;
+  // int region: e3[LM], L2[kAULines], ok[kAULines], e2[kAULines][LM], db[kAULines]
+  static constexpr int I_TOTAL = LM + 2 * kAULines + kAULines * LM + kAULines;
   // the Ubar sources of each (line, column): up to two slot offsets, -1 for none
   static constexpr int SRC = kAULines * kAUCols * 2;
   static constexpr size_t BYTES =
@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(256, adju_min_blocks<R>()) adjoint_u_kernel(co
   int *sL2 = sE3 + LM;
   int *sOk = sL2 + kAULines;
   int *sE2 = sOk + kAULines;
+  int *sDb = sE2 + kAULines * LM;  // a line's first coefficient row minus the block's; large: no line
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n1 = A.n[0], n2 = A.n[1], N1 = A.N[0], nc1 = A.nc[0];
@@ -179,6 +180,7 @@ __global__ void __launch_bounds__(256, adju_min_blocks<R>()) adjoint_u_kernel(co
       if (kind == 0 && q == 0) {
         sL2[b] = L2b;
         sOk[b] = (lid0 + b >= A.line_lo && lid0 + b <= A.line_hi) ? 1 : 0;
+        sDb[b] = sOk[b] ? ((r2 - P) > 0 ? (r2 - P) : 0) - l2lo : (1 << 20);
       }
       if (q < L2b) {
         const int gq = (kind ? A.off[1][1][r2] : off0) + q;
@@ -193,6 +195,7 @@ __global__ void __launch_bounds__(256, adju_min_blocks<R>()) adjoint_u_kernel(co
     } else if (kind == 0 && q == 0) {
       sL2[b] = 0;
       sOk[b] = 0;
+      sDb[b] = 1 << 20;
     }
   }
   // the chunk slots whose window holds each (line, column), in chunk order,
@@ -233,21 +236,25 @@ __global__ void __launch_bounds__(256, adju_min_blocks<R>()) adjoint_u_kernel(co
     sSrc[tid * 2 + 1] = src1;
   }
   __syncthreads();
-  // Ubar of the block's lines at its columns: the sum of those slots' values
+  // Ubar of the block's lines at its columns: the sum of those slots' values;
+  // a warp per (line, u, column) run of NPAIR values, lanes along the run
   {
     const R *Ug = static_cast<const R *>(A.ubar);
     const long long total = (long long)n2 * A.n[2] * A.nch_max * A.ubar_slot;
     const long long uoff = (long long)A.nl1max * NPAIR;
-    for (int t = tid; t < kAULines * 2 * kAUCols * NPAIR; t += NT) {
-      const int pr = t % NPAIR, l1 = (t / NPAIR) % kAUCols, u = (t / (NPAIR * kAUCols)) % 2;
-      const int b = t / (NPAIR * kAUCols * 2);
-      // the first source's value, plus the second's where the column has two
-      // (no addition of a zero: the FP64 pipe is this kernel's bound)
-      R v = r_zero<R>();
+    for (int c = warp; c < kAULines * 2 * kAUCols; c += NT / 32) {
+      const int b = c / (2 * kAUCols), u = (c / kAUCols) & 1, l1 = c % kAUCols;
       const long long sb0 = sSrc[(b * kAUCols + l1) * 2], sb1 = sSrc[(b * kAUCols + l1) * 2 + 1];
-      if (sb0 >= 0 && check_range(A.status, sb0 + u * uoff + pr, 1, total)) v = Ug[sb0 + u * uoff + pr];
-      if (sb1 >= 0 && check_range(A.status, sb1 + u * uoff + pr, 1, total)) v = r_add(v, Ug[sb1 + u * uoff + pr]);
-      sUw[b * L::UW + (u * kAUCols + l1) * NPAIR + pr] = v;
+      const long long o0 = sb0 + u * uoff, o1 = sb1 + u * uoff;
+      R *dst = sUw + b * L::UW + (u * kAUCols + l1) * NPAIR;
+      for (int pr = lane; pr < NPAIR; pr += 32) {
+        // the first source's value, plus the second's where the column has
+        // two (no addition of a zero: the FP64 pipe is this kernel's bound)
+        R v = r_zero<R>();
+        if (sb0 >= 0 && check_range(A.status, o0 + pr, 1, total)) v = Ug[o0 + pr];
+        if (sb1 >= 0 && check_range(A.status, o1 + pr, 1, total)) v = r_add(v, Ug[o1 + pr]);
+        dst[pr] = v;
+      }
     }
   }
   cp_async_wait_all();
@@ -324,11 +331,11 @@ __global__ void __launch_bounds__(256, adju_min_blocks<R>()) adjoint_u_kernel(co
     const int j = t % NB, m = (t / NB) % NL2, l1 = (t / (NB * NL2)) % kAUCols, k3 = t / (NB * NL2 * kAUCols);
     R v = r_zero<R>();
     bool first = true;
+    const R *src = sUw + (k3 * kAUCols + l1) * NL * NB + j;
     for (int b = 0; b < nlines; b++) {
-      const int r2 = r2a + b;
-      const int k = m - (((r2 - P) > 0 ? (r2 - P) : 0) - l2lo);
-      if (sOk[b] && k >= 0 && k < NL) {
-        const R x = sUw[b * L::UW + ((k3 * kAUCols + l1) * NL + k) * NB + j];
+      const int k = m - sDb[b];
+      if ((unsigned)k < (unsigned)NL) {
+        const R x = src[b * L::UW + k * NB];
         v = first ? x : r_add(v, x);
         first = false;
       }
